@@ -1,0 +1,298 @@
+#!/usr/bin/env python
+"""Throughput of single amplitudes <x|C|0> by sliced variable elimination on one GB300.
+
+Default workload: the 6 x 6 random grid circuit of depth 25 (Section 4 rules, circuit seed
+2001), one seeded bitstring (seed 2002) per step, 12 sliced variables (4096 slice terms)
+chosen greedily (Section 3.B.2), slice terms in complex64 and their sum in FP64. A step is
+one amplitude: every slice term, every pairwise contraction and the compensated sum.
+
+Prints one JSON line. Timing: CUDA events on the launching stream around each step, W
+warm-up steps first, L2 flushed (a 256 MiB write) before every timed step, max over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl qvx|reference]
+  torchrun --nproc-per-node N bench.py --gpus N ...   (each rank: its own bitstrings)
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import circuitgen as cg  # noqa: E402
+
+WORKLOADS = {
+    # name: (rows, cols, depth, circuit seed, bitstring seed, sliced variables)
+    "grid6x6d25-k12": (6, 6, 25, 2001, 2002, 12),
+    "grid4x4d10": (4, 4, 10, 1001, 1002, 0),
+}
+DEFAULT_WORKLOAD = "grid6x6d25-k12"
+METRIC = "amplitudes/s and complex TFLOP/s (% of GB300 peak) at |Δα|≤1e-5·2^-N/2 vs FP64"
+L2_FLUSH_BYTES = 256 << 20
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the fused kernel, from one ncu
+# capture of this workload; None until captured for the current kernel.
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["qvx", "reference"], default="qvx")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--batch", type=int, default=1, help="bitstrings per step")
+    ap.add_argument("--inner-slices", type=int, default=-1)
+    ap.add_argument("--warps-per-item", type=int, default=1)
+    ap.add_argument("--engine", default="auto")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
+    return ap.parse_args()
+
+
+def workload(name, batch, rank):
+    r, c, d, cseed, bseed, k = WORKLOADS[name]
+    circ = cg.grid_circuit(r, c, d, cseed)
+    bits = cg.random_bitstrings(r * c, batch * (rank + 1), bseed)[batch * rank:]
+    return circ, bits, k
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            out, _ = self.proc.communicate(timeout=10)
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(circ, bits, k, plan_order, plan_slices, budget_s):
+    """The oracle (C bucket elimination, all host cores) on whole amplitudes of the same
+    workload, repeated until about `budget_s` seconds of work."""
+    from oracle import ve as VE
+    threads = os.cpu_count() or 1
+    VE.build_library()
+    done, t0 = 0, time.perf_counter()
+    while True:
+        VE.ve_amplitude(circ, bits[done % len(bits)], plan_order, plan_slices, threads=threads)
+        done += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "amplitudes/s", "cores": threads, "kind": "oracle",
+            "sample": f"{done} whole amplitudes (all {1 << k} slice terms each) of the same circuit, "
+                      f"complex128 bucket elimination in the plan's order, OpenMP over slices"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from oracle import ve as VE
+    circ, bits, k = workload(args.workload, args.batch, 0)
+    import paper_1805_01450_gb300 as q
+    plan = q.Plan(circ, n_slices=k)   # host planner only: the oracle takes its order and slices
+    threads = os.cpu_count() or 1
+    VE.build_library()
+    for i in range(args.warmup):
+        VE.ve_amplitude(circ, bits[i % len(bits)], plan.order, plan.slices, threads=threads)
+    t0 = time.perf_counter()
+    n = 0
+    for i in range(args.steps):
+        for x in bits:
+            VE.ve_amplitude(circ, x, plan.order, plan.slices, threads=threads)
+            n += 1
+    dt = time.perf_counter() - t0
+    v = n / dt
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "amplitudes/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+           "data": "synthetic", "config": {"workload": args.workload, "bitstrings_per_step": args.batch,
+                                           "sliced": k},
+           "cpu_baseline": {"value": v, "unit": "amplitudes/s", "cores": threads, "kind": "oracle",
+                            "sample": f"{n} whole amplitudes, {args.steps} steps"},
+           "e2e": {"value": v, "unit": "amplitudes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_1805_01450_gb300 as q
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    circ, bits_host, k = workload(args.workload, args.batch, rank)
+    plan = q.Plan(circ, n_slices=k, inner_slices=args.inner_slices, warps_per_item=args.warps_per_item,
+                  engine=args.engine)
+    info = plan.info
+    B = len(bits_host)
+    dev = torch.device("cuda", local)
+    bits = plan._bits(bits_host, dev)
+    ws = plan.workspace(B, dev)
+    out = torch.empty(2 * B, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.amplitude(bits, workspace=ws, out=out, validate=False)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    plan.check_status(ws)
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        barrier()
+        torch.cuda.synchronize()
+        for i in range(K):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    plan.check_status(ws)
+
+    # end to end through the public call: pinned host bitstrings in, amplitudes out
+    h_bits = torch.tensor([b - (1 << 64) if b >= 1 << 63 else b for b in bits_host], dtype=torch.int64).pin_memory()
+    h_out = torch.empty(2 * B, dtype=torch.float64).pin_memory()
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    barrier()
+    torch.cuda.synchronize()
+    for i in range(K):
+        flush.zero_()
+        ev2[i][0].record(stream)
+        bits.copy_(h_bits, non_blocking=True)
+        step()
+        h_out.copy_(out, non_blocking=True)
+        ev2[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in ev2)
+
+    # parity of what was timed, against the oracle's slice terms
+    from oracle import ve as VE
+    ref = VE.exact_sum(VE.slice_terms(circ, bits_host[0], plan.order, plan.slices))
+    got = complex(h_out[0].item(), h_out[1].item())
+    err = abs(got - ref)
+    n = circ.n_qubits
+
+    t = torch.tensor([dev_ms, e2e_ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev_ms, e2e_ms = float(t[0]), float(t[1])
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    amps = K * B * world
+    value = amps / (dev_ms / 1e3)
+    e2e = amps / (e2e_ms / 1e3)
+    ms_step = dev_ms / K
+    flops = info["flops_per_amplitude"] * B
+    algo_bytes = info["bytes_per_amplitude"] * B
+    peak, peak_kind = measured_peaks()
+    achieved = algo_bytes / (ms_step / 1e3) / 1e9
+    fused = info["engine"] == "fused"
+    launches_per_step = 1 if fused else info["n_steps"] + 2
+    res = {
+        "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "config": {"workload": args.workload, "qubits": n, "depth": circ.depth, "sliced": k,
+                   "inner_slices": info["n_inner"], "bitstrings_per_step": B, "engine": info["engine"],
+                   "warps_per_item": info["warps_per_item"], "l2": "flushed (256 MiB write) before each step",
+                   "parallelism": f"bitstrings per rank x {world}"},
+        "complex_tflops": flops / (ms_step / 1e3) / 1e12,
+        "abs_err": err, "err_bound": 1e-5 * 2.0 ** (-n / 2),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": NCU_TRAFFIC.get((args.workload, B)),
+                     "peak_source": peak_kind,
+                     "kernel": "fused_program_kernel" if fused else "step_kernel",
+                     "algorithmic_bytes_per_launch": algo_bytes},
+        "e2e": {"value": e2e, "unit": "amplitudes/s", "h2d_bytes_per_step": 8 * B, "d2h_bytes_per_step": 16 * B},
+        "gpu_launches": K * launches_per_step,
+        "clocks": clocks.summary(),
+        "plan": {"n_vars": info["n_vars"], "n_steps": info["n_steps"], "log2_cost": info["log2_cost"],
+                 "log2_cost_unsliced": info["log2_cost_unsliced"], "max_rank": info["max_rank"],
+                 "arena_bytes": info["arena_bytes"]},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(circ, bits_host, k, plan.order, plan.slices, args.cpu_seconds)
+    print(json.dumps(res), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

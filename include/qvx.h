@@ -1,0 +1,184 @@
+/* qvx: single amplitudes <x|C|0...0> of quantum circuits by variable elimination on the
+ * circuit's undirected graphical model, with sliced variables, on one GB300 (sm_103a).
+ *
+ * Method (arXiv:1805.01450):
+ *   - the amplitude is the Feynman path sum of Eq. (1);
+ *   - every distinct path variable is a vertex of an undirected graph; diagonal gates
+ *     (T, CZ) add no variable, non-diagonal single-qubit gates start a new one
+ *     (Section 3.A, Fig. 3); input and output vertices are fixed and removed (Section 3.B.2);
+ *   - variables are summed one at a time in an elimination order (Section 3.B.1), whose
+ *     cost is the sum over steps of 2^deg(v) (Section 3.B.1, last paragraph);
+ *   - k chosen variables are fixed ("sliced"), which splits the sum into 2^k independent
+ *     terms that are added at the end (Section 3.B.2); they are chosen greedily by the cost
+ *     under a first ordering, and the graph is then re-ordered (Section 3.B.3).
+ *
+ * Conventions for every entry point:
+ *   - Ownership: the caller owns every buffer it passes. A plan copies what it needs from
+ *     the circuit and the lists; it is owned by the library until qvx_plan_destroy.
+ *   - Device memory: the library never allocates device memory. The caller passes a
+ *     workspace of at least qvx_workspace_size bytes (256-byte aligned); it holds the
+ *     plan's device image, the intermediate tensors and a device status word.
+ *   - Streams: all device work is enqueued on the caller's stream; calls return without
+ *     synchronising unless stated.
+ *   - Bitstrings: bit q of a uint64_t is the value of qubit q, so n_qubits <= 64.
+ *   - Amplitudes: complex128, interleaved (re, im).
+ *   - Errors: every call returns a qvx_status; qvx_last_error() gives a message for the
+ *     calling thread's last failure. Failures inside kernels (a bounded wait that ran out,
+ *     an index out of range) set the device status word, read by qvx_workspace_status.
+ */
+#ifndef QVX_H
+#define QVX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QVX_OK = 0,
+    QVX_EINVAL = 1,        /* bad argument: sizes, ids, a bitstring with bits >= n_qubits */
+    QVX_ENOMEM = 2,        /* host allocation failed, or a workspace/plan exceeds a limit */
+    QVX_ECUDA = 3,         /* a CUDA runtime call failed (message in qvx_last_error) */
+    QVX_ETIMEOUT = 4,      /* a bounded device wait ran out (device status word) */
+    QVX_EUNSUPPORTED = 5,  /* a gate, rank or size outside what the plan can run */
+    QVX_EDEVICE = 6        /* a kernel reported an out-of-range index (device status word) */
+} qvx_status;
+
+/* Gate kinds (matrices indexed [output, input]):
+ *   H       [[1,1],[1,-1]]/sqrt(2)
+ *   T       diag(1, e^{i pi/4})
+ *   SQRT_X  (1/2)[[1+i, 1-i],[1-i, 1+i]]     (principal square root of X)
+ *   SQRT_Y  (1/2)[[1+i, -1-i],[1+i, 1+i]]    (principal square root of Y)
+ *   CZ      diag(1,1,1,-1) on (q0, q1)
+ *   RXY     exp(-i theta (cos(phi) X + sin(phi) Y)/2), parametrised by theta
+ *   U1      any 2x2 matrix u[8] = (re, im) row-major; treated as non-diagonal */
+typedef enum {
+    QVX_GATE_H = 0,
+    QVX_GATE_T = 1,
+    QVX_GATE_SQRT_X = 2,
+    QVX_GATE_SQRT_Y = 3,
+    QVX_GATE_CZ = 4,
+    QVX_GATE_RXY = 5,
+    QVX_GATE_U1 = 6
+} qvx_gate_kind;
+
+typedef struct {
+    int32_t kind;          /* qvx_gate_kind */
+    int32_t q0, q1;        /* q1 = -1 for single-qubit gates */
+    int32_t param_index;   /* RXY: index into a theta vector for gradients, or -1 */
+    double theta, phi;     /* RXY angles */
+    double u[8];           /* U1 matrix */
+} qvx_gate;
+
+typedef struct {
+    int32_t n_qubits;      /* 1..64 */
+    int32_t reserved;
+    int64_t n_gates;
+    const qvx_gate *gates; /* in time order */
+} qvx_circuit;
+
+typedef enum { QVX_ENGINE_AUTO = 0, QVX_ENGINE_FUSED = 1, QVX_ENGINE_STEPWISE = 2 } qvx_engine;
+
+typedef struct {
+    int32_t n_slices;          /* sliced variables when the planner picks them; -1: as many as
+                                  the memory budget needs (0 if none) */
+    int32_t order_restarts;    /* randomised min-fill orderings tried (best kept), >= 1 */
+    uint64_t order_seed;       /* seed of the ordering's random tie-breaks */
+    int64_t mem_budget_bytes;  /* per-work-item tensor budget of the stepwise engine */
+    int32_t engine;            /* qvx_engine */
+    int32_t inner_slices;      /* sliced variables kept open inside one work item; -1 auto */
+    int32_t max_rank;          /* largest tensor rank a plan may create (<= 30) */
+    int32_t warps_per_item;    /* fused engine: warps sharing one work item (1, 2 or 4) */
+} qvx_plan_opts;
+
+typedef struct {
+    int32_t n_qubits, n_vars, n_edges, n_sliced, n_inner, n_steps, n_leaves, max_rank;
+    int32_t engine, warps_per_item;
+    int64_t n_items_per_bitstring;   /* 2^(n_sliced - n_inner) */
+    double log2_cost;                /* log2 of sum over steps of 2^deg(v), per slice */
+    double log2_cost_unsliced;       /* the same for the first ordering, nothing sliced */
+    double flops_per_amplitude;      /* algorithmic real flops: 8 * 2^|S_A u S_B| per step, all items */
+    double bytes_per_amplitude;      /* algorithmic tensor bytes read + written, all items */
+    int64_t arena_bytes;             /* tensor memory of one work item */
+    int64_t device_image_bytes;      /* program, leaves and tables */
+} qvx_plan_info;
+
+typedef struct qvx_plan qvx_plan;
+
+/* Fills *opts with defaults: n_slices -1, 8 restarts, seed 1, 1 GiB budget, auto engine,
+ * auto inner slices, max_rank 30, 1 warp per item. */
+void qvx_plan_opts_default(qvx_plan_opts *opts);
+
+/* The graphical model of Section 3.A with output and input vertices removed.
+ * Variable v (canonical id, 0 <= v < n_vars) is the value of qubit var_qubit[v] after its
+ * var_ordinal[v]-th non-diagonal single-qubit gate; ids run in order of (qubit, ordinal).
+ * Pass NULL arrays to query the counts; otherwise var_qubit/var_ordinal hold n_vars
+ * entries and edges holds 2*edges_cap int32 (pairs a < b, sorted). */
+qvx_status qvx_graph_export(const qvx_circuit *circuit, int32_t *n_vars, int32_t *var_qubit,
+                            int32_t *var_ordinal, int64_t *n_edges, int32_t *edges,
+                            int64_t edges_cap);
+
+/* Builds a plan on the host (no device work). order: n_order canonical ids (every
+ * variable not sliced, each once) or n_order = 0 for the planner's ordering. slices:
+ * n_slices ids, or n_slices = -1 to let the planner choose opts->n_slices of them by the
+ * greedy rule of Section 3.B.2. opts may be NULL for defaults. */
+qvx_status qvx_plan_create(const qvx_circuit *circuit, const int32_t *order, int32_t n_order,
+                           const int32_t *slices, int32_t n_slices, const qvx_plan_opts *opts,
+                           qvx_plan **out);
+
+void qvx_plan_destroy(qvx_plan *plan);
+
+qvx_status qvx_plan_get_info(const qvx_plan *plan, qvx_plan_info *info);
+
+/* The plan's elimination order (n_vars - n_sliced ids) and slice list (n_sliced ids).
+ * Slice number s assigns bit i of s to slices[i]; the first n_inner entries are the ones
+ * kept open inside a work item. Either pointer may be NULL. */
+qvx_status qvx_plan_get_order(const qvx_plan *plan, int32_t *order, int32_t *slices);
+
+/* The plan's device image (program, leaves, maps; layout in csrc/device_program.h) as the
+ * plan holds it on the host: *data stays valid until qvx_plan_destroy. For inspection and
+ * for host-side checks of the program. */
+qvx_status qvx_plan_get_image(const qvx_plan *plan, const void **data, size_t *bytes);
+
+/* Workspace bytes for calls of up to `batch` bitstrings. */
+qvx_status qvx_workspace_size(const qvx_plan *plan, int64_t batch, size_t *bytes);
+
+/* Copies the plan's device image into the head of the workspace and clears the device
+ * status word; synchronises `stream`. Call once per (plan, workspace) before the amplitude
+ * calls, and again if the workspace memory was used for anything else in between. */
+qvx_status qvx_workspace_init(const qvx_plan *plan, void *workspace_dev, size_t workspace_bytes,
+                              void *stream);
+
+/* alpha_b = <x_b|C|0> for b < batch. bitstrings_dev: batch uint64 on the device;
+ * amps_dev: 2*batch doubles on the device. Slice terms are computed in complex64 and
+ * added in FP64 with compensation. */
+qvx_status qvx_amplitude(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch,
+                         double *amps_dev, void *workspace_dev, size_t workspace_bytes,
+                         void *stream);
+
+/* Sum of the slice terms s in [slice_begin, slice_begin + slice_count) only: the share of
+ * one rank when the slices are split over several processes (Section 3.B.2). */
+qvx_status qvx_amplitude_slices(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch,
+                                int64_t slice_begin, int64_t slice_count, double *amps_dev,
+                                void *workspace_dev, size_t workspace_bytes, void *stream);
+
+/* The individual slice terms beta_s (complex64, interleaved) for s in
+ * [slice_begin, slice_begin + slice_count): terms_dev holds 2*batch*slice_count floats,
+ * bitstring-major. For checking and for callers that sum the terms themselves. */
+qvx_status qvx_slice_terms(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch,
+                           int64_t slice_begin, int64_t slice_count, float *terms_dev,
+                           void *workspace_dev, size_t workspace_bytes, void *stream);
+
+/* Synchronises `stream` and returns the device status word kept in the workspace
+ * (QVX_OK, QVX_ETIMEOUT or QVX_EDEVICE), then clears it. */
+qvx_status qvx_workspace_status(const qvx_plan *plan, void *workspace_dev, void *stream);
+
+/* Message for the calling thread's last failed call ("" if none). */
+const char *qvx_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QVX_H */

@@ -1,0 +1,275 @@
+"""qvx: single amplitudes <x|C|0...0> by variable elimination with slicing, on GB300.
+
+Python binding of libqvx.so (include/qvx.h). It only marshals arguments: circuits into
+qvx_gate arrays, torch tensors into device pointers and the caller's current CUDA stream
+into the stream argument. Every step of the computation runs in the library's kernels;
+if the library is missing the binding raises, it never falls back to another path.
+
+    plan = Plan(circuit, n_slices=12)          # host planner (Sections 3.A-3.B)
+    amps = plan.amplitude(bitstrings)          # complex128 torch tensor on the device
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqvx.so")
+
+QVX_OK, QVX_EINVAL, QVX_ENOMEM, QVX_ECUDA, QVX_ETIMEOUT, QVX_EUNSUPPORTED, QVX_EDEVICE = range(7)
+ENGINES = {"auto": 0, "fused": 1, "stepwise": 2}
+ENGINE_NAMES = {v: k for k, v in ENGINES.items()}
+
+
+class QvxError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"qvx status {status}: {msg}")
+        self.status = status
+
+
+class Gate(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("q0", ctypes.c_int32), ("q1", ctypes.c_int32),
+                ("param_index", ctypes.c_int32), ("theta", ctypes.c_double), ("phi", ctypes.c_double),
+                ("u", ctypes.c_double * 8)]
+
+
+class CircuitStruct(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int32), ("reserved", ctypes.c_int32), ("n_gates", ctypes.c_int64),
+                ("gates", ctypes.POINTER(Gate))]
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("n_slices", ctypes.c_int32), ("order_restarts", ctypes.c_int32),
+                ("order_seed", ctypes.c_uint64), ("mem_budget_bytes", ctypes.c_int64),
+                ("engine", ctypes.c_int32), ("inner_slices", ctypes.c_int32),
+                ("max_rank", ctypes.c_int32), ("warps_per_item", ctypes.c_int32)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("n_qubits", "n_vars", "n_edges", "n_sliced", "n_inner",
+                                               "n_steps", "n_leaves", "max_rank", "engine",
+                                               "warps_per_item")] + \
+               [("n_items_per_bitstring", ctypes.c_int64), ("log2_cost", ctypes.c_double),
+                ("log2_cost_unsliced", ctypes.c_double), ("flops_per_amplitude", ctypes.c_double),
+                ("bytes_per_amplitude", ctypes.c_double), ("arena_bytes", ctypes.c_int64),
+                ("device_image_bytes", ctypes.c_int64)]
+
+
+_lib = None
+EXPORTED = ("qvx_plan_opts_default", "qvx_graph_export", "qvx_plan_create", "qvx_plan_destroy",
+            "qvx_plan_get_info", "qvx_plan_get_order", "qvx_plan_get_image", "qvx_workspace_size", "qvx_workspace_init",
+            "qvx_amplitude", "qvx_amplitude_slices", "qvx_slice_terms", "qvx_workspace_status",
+            "qvx_last_error")
+
+
+def lib():
+    """The loaded libqvx.so; raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    P, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    sig = {
+        "qvx_plan_opts_default": (None, [ctypes.POINTER(PlanOpts)]),
+        "qvx_graph_export": (ctypes.c_int, [ctypes.POINTER(CircuitStruct), P, P, P, P, P, i64]),
+        "qvx_plan_create": (ctypes.c_int, [ctypes.POINTER(CircuitStruct), P, i32, P, i32,
+                                           ctypes.POINTER(PlanOpts), ctypes.POINTER(P)]),
+        "qvx_plan_destroy": (None, [P]),
+        "qvx_plan_get_info": (ctypes.c_int, [P, ctypes.POINTER(PlanInfo)]),
+        "qvx_plan_get_order": (ctypes.c_int, [P, P, P]),
+        "qvx_plan_get_image": (ctypes.c_int, [P, ctypes.POINTER(P), ctypes.POINTER(ctypes.c_size_t)]),
+        "qvx_workspace_size": (ctypes.c_int, [P, i64, ctypes.POINTER(ctypes.c_size_t)]),
+        "qvx_workspace_init": (ctypes.c_int, [P, P, ctypes.c_size_t, P]),
+        "qvx_amplitude": (ctypes.c_int, [P, P, i64, P, P, ctypes.c_size_t, P]),
+        "qvx_amplitude_slices": (ctypes.c_int, [P, P, i64, i64, i64, P, P, ctypes.c_size_t, P]),
+        "qvx_slice_terms": (ctypes.c_int, [P, P, i64, i64, i64, P, P, ctypes.c_size_t, P]),
+        "qvx_workspace_status": (ctypes.c_int, [P, P, P]),
+        "qvx_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    del u64
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != QVX_OK:
+        raise QvxError(status, lib().qvx_last_error().decode(errors="replace"))
+
+
+def circuit_struct(circ):
+    """qvx_circuit for a circuitgen.Circuit-like object (n_qubits, gates with kind/q0/q1/...)."""
+    n = len(circ.gates)
+    arr = (Gate * max(n, 1))()
+    for i, g in enumerate(circ.gates):
+        arr[i].kind, arr[i].q0, arr[i].q1 = g.kind, g.q0, g.q1
+        arr[i].param_index = getattr(g, "param", -1)
+        arr[i].theta, arr[i].phi = getattr(g, "theta", 0.0), getattr(g, "phi", 0.0)
+        u = getattr(g, "u", ())
+        for j in range(len(u)):
+            arr[i].u[j] = u[j]
+    cs = CircuitStruct(circ.n_qubits, 0, n, ctypes.cast(arr, ctypes.POINTER(Gate)))
+    cs._keep = arr
+    return cs
+
+
+def graph_export(circ):
+    """(var_qubit, var_ordinal, edges) of the circuit's graphical model (Section 3.A)."""
+    L = lib()
+    cs = circuit_struct(circ)
+    nv, ne = ctypes.c_int32(), ctypes.c_int64()
+    _check(L.qvx_graph_export(ctypes.byref(cs), ctypes.byref(nv), None, None, ctypes.byref(ne), None, 0))
+    vq = (ctypes.c_int32 * max(nv.value, 1))()
+    vo = (ctypes.c_int32 * max(nv.value, 1))()
+    ed = (ctypes.c_int32 * max(2 * ne.value, 1))()
+    _check(L.qvx_graph_export(ctypes.byref(cs), None, vq, vo, None, ed, ne.value))
+    return (list(vq[:nv.value]), list(vo[:nv.value]),
+            [(ed[2 * i], ed[2 * i + 1]) for i in range(ne.value)])
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """A host plan: graph, elimination order, slices and the pairwise contraction program."""
+
+    def __init__(self, circ, order=None, slices=None, n_slices=-1, engine="auto", inner_slices=-1,
+                 order_restarts=8, order_seed=1, mem_budget_bytes=1 << 30, max_rank=30,
+                 warps_per_item=1):
+        L = lib()
+        opts = PlanOpts()
+        L.qvx_plan_opts_default(ctypes.byref(opts))
+        opts.n_slices = n_slices
+        opts.order_restarts = order_restarts
+        opts.order_seed = order_seed
+        opts.mem_budget_bytes = mem_budget_bytes
+        opts.engine = ENGINES[engine]
+        opts.inner_slices = inner_slices
+        opts.max_rank = max_rank
+        opts.warps_per_item = warps_per_item
+        cs = circuit_struct(circ)
+        o_arr = (ctypes.c_int32 * max(len(order or []), 1))(*(order or []))
+        s_arr = (ctypes.c_int32 * max(len(slices or []), 1))(*(slices or []))
+        h = ctypes.c_void_p()
+        _check(L.qvx_plan_create(ctypes.byref(cs), o_arr, len(order or []), s_arr,
+                                 -1 if slices is None else len(slices), ctypes.byref(opts),
+                                 ctypes.byref(h)))
+        self._h = h
+        self.n_qubits = circ.n_qubits
+        inf = PlanInfo()
+        _check(L.qvx_plan_get_info(h, ctypes.byref(inf)))
+        self.info = {f[0]: getattr(inf, f[0]) for f in PlanInfo._fields_}
+        self.info["engine"] = ENGINE_NAMES[self.info["engine"]]
+        nv, k = inf.n_vars, inf.n_sliced
+        o = (ctypes.c_int32 * max(nv - k, 1))()
+        s = (ctypes.c_int32 * max(k, 1))()
+        _check(L.qvx_plan_get_order(h, o, s))
+        self.order = list(o[:nv - k])
+        self.slices = list(s[:k])
+        self._ws = {}
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.qvx_plan_destroy(h)
+            self._h = None
+
+    def image(self) -> bytes:
+        """A copy of the plan's device image (program, leaves, element maps)."""
+        p, n = ctypes.c_void_p(), ctypes.c_size_t()
+        _check(lib().qvx_plan_get_image(self._h, ctypes.byref(p), ctypes.byref(n)))
+        return ctypes.string_at(p, n.value)
+
+    @property
+    def n_slice_terms(self) -> int:
+        return 1 << len(self.slices)
+
+    def workspace_bytes(self, batch: int) -> int:
+        n = ctypes.c_size_t()
+        _check(lib().qvx_workspace_size(self._h, batch, ctypes.byref(n)))
+        return n.value
+
+    def workspace(self, batch: int, device=None, stream=None):
+        """A device workspace (torch uint8) sized for `batch` bitstrings, initialised."""
+        import torch
+        dev = torch.device(device if device is not None else "cuda")
+        nbytes = self.workspace_bytes(batch)
+        buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        shift = (-buf.data_ptr()) % 256
+        ws = buf[shift:shift + nbytes]
+        _check(lib().qvx_workspace_init(self._h, ctypes.c_void_p(ws.data_ptr()), nbytes, _stream_ptr(stream)))
+        return ws
+
+    def _ws_for(self, batch, device):
+        key = (batch, str(device))
+        if key not in self._ws:
+            self._ws[key] = self.workspace(batch, device)
+        return self._ws[key]
+
+    @staticmethod
+    def _bits(bitstrings, device=None):
+        import torch
+        if isinstance(bitstrings, torch.Tensor):
+            t = bitstrings
+        else:
+            vals = [int(b) for b in bitstrings]
+            vals = [v - (1 << 64) if v >= (1 << 63) else v for v in vals]
+            t = torch.tensor(vals, dtype=torch.int64)
+        if t.dtype != torch.int64:
+            raise TypeError("bitstrings must be int64 (bit q = qubit q)")
+        if not t.is_cuda:
+            t = t.to(device if device is not None else "cuda")
+        return t.contiguous()
+
+    def _check_bits(self, bits):
+        if self.n_qubits < 64:
+            import torch
+            bad = (bits >> self.n_qubits) != 0
+            if bool(torch.any(bad)):
+                raise QvxError(QVX_EINVAL, "bitstring has bits at or above n_qubits")
+
+    def amplitude(self, bitstrings, workspace=None, out=None, stream=None, slice_begin=0,
+                  slice_count=None, validate=True):
+        """<x|C|0> for each bitstring: complex128 torch tensor on the bitstrings' device.
+        slice_begin/slice_count restrict the sum to a range of slice numbers."""
+        import torch
+        bits = self._bits(bitstrings)
+        if validate:
+            self._check_bits(bits)
+        n = bits.numel()
+        ws = workspace if workspace is not None else self._ws_for(n, bits.device)
+        if out is None:
+            out = torch.empty(2 * n, dtype=torch.float64, device=bits.device)
+        if slice_count is None:
+            slice_count = self.n_slice_terms - slice_begin
+        _check(lib().qvx_amplitude_slices(self._h, ctypes.c_void_p(bits.data_ptr()), n, slice_begin,
+                                          slice_count, ctypes.c_void_p(out.data_ptr()),
+                                          ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
+        return torch.view_as_complex(out.view(n, 2))
+
+    def slice_terms(self, bitstrings, slice_begin=0, slice_count=None, workspace=None, stream=None):
+        """The slice terms beta_s (complex64, [batch, slice_count]) of Section 3.B.2."""
+        import torch
+        bits = self._bits(bitstrings)
+        self._check_bits(bits)
+        n = bits.numel()
+        if slice_count is None:
+            slice_count = self.n_slice_terms - slice_begin
+        ws = workspace if workspace is not None else self._ws_for(n, bits.device)
+        out = torch.empty(2 * n * slice_count, dtype=torch.float32, device=bits.device)
+        _check(lib().qvx_slice_terms(self._h, ctypes.c_void_p(bits.data_ptr()), n, slice_begin, slice_count,
+                                     ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
+                                     ws.numel(), _stream_ptr(stream)))
+        return torch.view_as_complex(out.view(n, slice_count, 2))
+
+    def check_status(self, workspace, stream=None):
+        """Synchronises and raises if a kernel set the workspace's device status word."""
+        _check(lib().qvx_workspace_status(self._h, ctypes.c_void_p(workspace.data_ptr()), _stream_ptr(stream)))

@@ -1,0 +1,363 @@
+// The C interface of include/qvx.h: plans, workspaces and the amplitude entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "kernels.h"
+#include "plan.h"
+
+struct qvx_plan {
+    qvx::Plan p;
+    // fused-engine launch shape, cached for the device it was computed on
+    int launch_device = -1;
+    int sms = 0, ctas_per_sm = 0, items_per_cta = 0;
+    size_t smem = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+qvx_status fail(qvx_status s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+
+qvx_status cuda_fail(cudaError_t e, const char *where) {
+    return fail(QVX_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Workspace layout: [device image][status word, CTA counter][item partials][stepwise arenas]
+struct WsLayout {
+    size_t image, status, partials, arenas, total;
+    int64_t items_in_flight;
+};
+
+WsLayout layout_of(const qvx::Plan &p, int64_t batch) {
+    WsLayout w{};
+    const int64_t n_outer = int64_t(1) << ((int)p.slices.size() - p.n_inner);
+    w.image = 0;
+    w.status = align256(p.image.size());
+    w.partials = w.status + 256;
+    w.arenas = align256(w.partials + (size_t)std::max<int64_t>(batch, 1) * (size_t)n_outer * 16);
+    w.items_in_flight = 0;
+    if (p.engine == QVX_ENGINE_STEPWISE) {
+        const int64_t arena_bytes = std::max<int64_t>(p.arena_elems, 4) * 8;
+        const int64_t total_items = std::max<int64_t>(batch, 1) * n_outer;
+        int64_t fit = std::max<int64_t>(1, p.opts.mem_budget_bytes / arena_bytes);
+        w.items_in_flight = std::min(total_items, fit);
+    }
+    w.total = align256(w.arenas + (size_t)w.items_in_flight * (size_t)std::max<int64_t>(p.arena_elems, 4) * 8);
+    return w;
+}
+
+struct DeviceCaps {
+    int sms = 0, device = -1;
+};
+
+qvx_status device_caps(DeviceCaps *c) {
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    return QVX_OK;
+}
+
+qvx_status check_ws(const qvx_plan *plan, int64_t batch, void *ws, size_t ws_bytes, WsLayout *w) {
+    if (!plan) return fail(QVX_EINVAL, "null plan");
+    if (batch < 0) return fail(QVX_EINVAL, "negative batch");
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return fail(QVX_EINVAL, "workspace must be 256-byte aligned");
+    *w = layout_of(plan->p, batch);
+    if (ws_bytes < w->total)
+        return fail(QVX_EINVAL, "workspace too small: need " + std::to_string(w->total) + " bytes");
+    return QVX_OK;
+}
+
+// Runs the program over outer slices [o_begin, o_begin + o_count) for every bitstring,
+// leaving FP64 item sums in the workspace partials (and slice terms if requested).
+// With the fused engine and amps != nullptr the same launch also writes the amplitudes.
+qvx_status run_items(qvx_plan *plan, const uint64_t *bits, int64_t batch, int64_t s_begin,
+                     int64_t s_end, float *terms, double *amps, void *ws, const WsLayout &w,
+                     cudaStream_t st, int64_t *o_count_out) {
+    const qvx::Plan &p = plan->p;
+    const int n_inner = p.n_inner;
+    const int64_t o_begin = s_begin >> n_inner;
+    const int64_t o_end = ((s_end - 1) >> n_inner) + 1;
+    qvx::LaunchArgs a{};
+    unsigned char *base = static_cast<unsigned char *>(ws);
+    a.image = base + w.image;
+    a.bitstrings = bits;
+    a.batch = batch;
+    a.o_begin = o_begin;
+    a.o_count = o_end - o_begin;
+    a.s_begin = s_begin;
+    a.s_end = s_end;
+    a.arena_elems = (uint64_t)std::max<int64_t>(p.arena_elems, 4);
+    a.n_steps = (uint32_t)p.steps.size();
+    a.n_inner = (uint32_t)n_inner;
+    a.partials = reinterpret_cast<double2 *>(base + w.partials);
+    a.terms = reinterpret_cast<float2 *>(terms);
+    a.status = reinterpret_cast<unsigned int *>(base + w.status);
+    a.counter = reinterpret_cast<unsigned int *>(base + w.status) + 1;
+    a.amps = p.engine == QVX_ENGINE_FUSED ? amps : nullptr;
+    *o_count_out = a.o_count;
+    const int64_t n_items = batch * a.o_count;
+    if (n_items == 0) return QVX_OK;
+    cudaError_t e;
+    if (p.engine == QVX_ENGINE_FUSED) {
+        const int wpi = p.warps_per_item;
+        int dev = -1;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+        if (dev != plan->launch_device) {
+            DeviceCaps caps;
+            qvx_status s = device_caps(&caps);
+            if (s != QVX_OK) return s;
+            // up to 8 warps per CTA, as many work items as fit in 200 KiB of shared memory
+            const size_t arena = (size_t)a.arena_elems * 8;
+            const int ipc = (int)std::max<size_t>(1, std::min<size_t>(8 / wpi, (200u << 10) / arena));
+            const size_t smem = (size_t)ipc * arena;
+            if ((e = qvx::fused_prepare(smem)) != cudaSuccess) return cuda_fail(e, "fused kernel attributes");
+            const int per_sm = qvx::fused_blocks_per_sm(32 * wpi * ipc, smem);
+            if (per_sm < 1) return fail(QVX_EUNSUPPORTED, "fused kernel: no CTA fits on an SM");
+            plan->sms = caps.sms;
+            plan->ctas_per_sm = per_sm;
+            plan->items_per_cta = ipc;
+            plan->smem = smem;
+            plan->launch_device = dev;
+        }
+        const int64_t ctas_needed = (n_items + plan->items_per_cta - 1) / plan->items_per_cta;
+        const int grid = (int)std::min<int64_t>(ctas_needed, (int64_t)plan->sms * plan->ctas_per_sm);
+        if ((e = qvx::launch_fused(a, wpi, plan->items_per_cta, grid, plan->smem, st)) != cudaSuccess)
+            return cuda_fail(e, "fused kernel launch");
+        return QVX_OK;
+    }
+    float2 *arenas = reinterpret_cast<float2 *>(base + w.arenas);
+    for (int64_t ib = 0; ib < n_items; ib += w.items_in_flight) {
+        const int64_t n = std::min<int64_t>(w.items_in_flight, n_items - ib);
+        for (size_t s = 0; s < p.steps.size(); s++) {
+            const uint32_t rc = (uint32_t)p.tensors[p.steps[s].c].modes.size();
+            if ((e = qvx::launch_step(a, (uint32_t)s, ib, n, arenas, rc, st)) != cudaSuccess)
+                return cuda_fail(e, "step kernel launch");
+        }
+        if ((e = qvx::launch_finish_items(a, ib, n, arenas, st)) != cudaSuccess)
+            return cuda_fail(e, "finish kernel launch");
+    }
+    return QVX_OK;
+}
+
+qvx_status check_range(const qvx_plan *plan, int64_t s_begin, int64_t s_count) {
+    const int64_t total = int64_t(1) << plan->p.slices.size();
+    if (s_begin < 0 || s_count < 0 || s_begin + s_count > total)
+        return fail(QVX_EINVAL, "slice range outside [0, 2^n_sliced)");
+    return QVX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void qvx_plan_opts_default(qvx_plan_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->n_slices = -1;
+    o->order_restarts = 8;
+    o->order_seed = 1;
+    o->mem_budget_bytes = int64_t(1) << 30;
+    o->engine = QVX_ENGINE_AUTO;
+    o->inner_slices = -1;
+    o->max_rank = 30;
+    o->warps_per_item = 1;
+}
+
+qvx_status qvx_graph_export(const qvx_circuit *circuit, int32_t *n_vars, int32_t *var_qubit,
+                            int32_t *var_ordinal, int64_t *n_edges, int32_t *edges, int64_t edges_cap) {
+    qvx::Model m;
+    std::string err;
+    try {
+        if (!qvx::build_model(circuit, &m, &err)) return fail(QVX_EINVAL, err);
+    } catch (const std::bad_alloc &) {
+        return fail(QVX_ENOMEM, "out of host memory");
+    }
+    if (n_vars) *n_vars = m.n_vars;
+    if (n_edges) *n_edges = (int64_t)m.edges.size();
+    if (var_qubit)
+        for (int v = 0; v < m.n_vars; v++) var_qubit[v] = m.var_qubit[v];
+    if (var_ordinal)
+        for (int v = 0; v < m.n_vars; v++) var_ordinal[v] = m.var_ordinal[v];
+    if (edges) {
+        if (edges_cap < (int64_t)m.edges.size()) return fail(QVX_EINVAL, "edges: capacity too small");
+        for (size_t i = 0; i < m.edges.size(); i++) {
+            edges[2 * i] = m.edges[i].first;
+            edges[2 * i + 1] = m.edges[i].second;
+        }
+    }
+    return QVX_OK;
+}
+
+qvx_status qvx_plan_create(const qvx_circuit *circuit, const int32_t *order, int32_t n_order,
+                           const int32_t *slices, int32_t n_slices, const qvx_plan_opts *opts,
+                           qvx_plan **out) {
+    if (!out) return fail(QVX_EINVAL, "null output pointer");
+    *out = nullptr;
+    qvx_plan_opts o;
+    if (opts) o = *opts;
+    else qvx_plan_opts_default(&o);
+    if (n_order < 0) return fail(QVX_EINVAL, "n_order < 0");
+    if (o.order_restarts < 1 || o.max_rank < 1 || o.mem_budget_bytes < 64)
+        return fail(QVX_EINVAL, "opts: restarts >= 1, max_rank >= 1, budget >= 64 bytes");
+    if (o.warps_per_item != 1 && o.warps_per_item != 2 && o.warps_per_item != 4)
+        return fail(QVX_EINVAL, "opts: warps_per_item must be 1, 2 or 4");
+    qvx_plan *plan = nullptr;
+    try {
+        plan = new qvx_plan();
+        std::string err;
+        qvx_status s = qvx::make_plan(circuit, order, n_order, slices, n_slices, o, &plan->p, &err);
+        if (s != QVX_OK) {
+            delete plan;
+            return fail(s, err);
+        }
+    } catch (const std::bad_alloc &) {
+        delete plan;
+        return fail(QVX_ENOMEM, "out of host memory");
+    }
+    *out = plan;
+    return QVX_OK;
+}
+
+void qvx_plan_destroy(qvx_plan *plan) { delete plan; }
+
+qvx_status qvx_plan_get_info(const qvx_plan *plan, qvx_plan_info *info) {
+    if (!plan || !info) return fail(QVX_EINVAL, "null argument");
+    const qvx::Plan &p = plan->p;
+    std::memset(info, 0, sizeof(*info));
+    info->n_qubits = p.model.n_qubits;
+    info->n_vars = p.model.n_vars;
+    info->n_edges = (int32_t)p.model.edges.size();
+    info->n_sliced = (int32_t)p.slices.size();
+    info->n_inner = p.n_inner;
+    info->n_steps = (int32_t)p.steps.size();
+    info->n_leaves = (int32_t)p.leaves.size();
+    info->max_rank = p.max_rank;
+    info->engine = p.engine;
+    info->warps_per_item = p.warps_per_item;
+    info->n_items_per_bitstring = int64_t(1) << ((int)p.slices.size() - p.n_inner);
+    info->log2_cost = p.log2_cost;
+    info->log2_cost_unsliced = p.log2_cost_unsliced;
+    info->flops_per_amplitude = p.flops_per_item * (double)info->n_items_per_bitstring;
+    info->bytes_per_amplitude = p.bytes_per_item * (double)info->n_items_per_bitstring;
+    info->arena_bytes = p.arena_elems * 8;
+    info->device_image_bytes = (int64_t)p.image.size();
+    return QVX_OK;
+}
+
+qvx_status qvx_plan_get_order(const qvx_plan *plan, int32_t *order, int32_t *slices) {
+    if (!plan) return fail(QVX_EINVAL, "null plan");
+    if (order)
+        for (size_t i = 0; i < plan->p.order.size(); i++) order[i] = plan->p.order[i];
+    if (slices)
+        for (size_t i = 0; i < plan->p.slices.size(); i++) slices[i] = plan->p.slices[i];
+    return QVX_OK;
+}
+
+qvx_status qvx_plan_get_image(const qvx_plan *plan, const void **data, size_t *bytes) {
+    if (!plan || !data || !bytes) return fail(QVX_EINVAL, "null argument");
+    *data = plan->p.image.data();
+    *bytes = plan->p.image.size();
+    return QVX_OK;
+}
+
+qvx_status qvx_workspace_size(const qvx_plan *plan, int64_t batch, size_t *bytes) {
+    if (!plan || !bytes || batch < 0) return fail(QVX_EINVAL, "bad argument");
+    *bytes = layout_of(plan->p, batch).total;
+    return QVX_OK;
+}
+
+qvx_status qvx_workspace_init(const qvx_plan *plan, void *ws, size_t ws_bytes, void *stream) {
+    WsLayout w;
+    qvx_status s = check_ws(plan, 0, ws, ws_bytes, &w);
+    if (s != QVX_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned char *base = static_cast<unsigned char *>(ws);
+    cudaError_t e = cudaMemcpyAsync(base + w.image, plan->p.image.data(), plan->p.image.size(),
+                                    cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "image upload");
+    if ((e = cudaMemsetAsync(base + w.status, 0, 256, st)) != cudaSuccess) return cuda_fail(e, "status clear");
+    // the upload reads pageable host memory owned by the plan: finish it before returning
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "image upload sync");
+    return QVX_OK;
+}
+
+qvx_status qvx_amplitude_slices(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch,
+                                int64_t slice_begin, int64_t slice_count, double *amps_dev,
+                                void *ws, size_t ws_bytes, void *stream) {
+    WsLayout w;
+    qvx_status s = check_ws(plan, batch, ws, ws_bytes, &w);
+    if (s != QVX_OK) return s;
+    if ((s = check_range(plan, slice_begin, slice_count)) != QVX_OK) return s;
+    if (batch == 0) return QVX_OK;
+    if (!bitstrings_dev || !amps_dev) return fail(QVX_EINVAL, "null device buffer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (slice_count == 0) {
+        if ((e = cudaMemsetAsync(amps_dev, 0, (size_t)batch * 16, st)) != cudaSuccess) return cuda_fail(e, "memset");
+        return QVX_OK;
+    }
+    int64_t o_count = 0;
+    s = run_items(plan, bitstrings_dev, batch, slice_begin, slice_begin + slice_count, nullptr, amps_dev, ws, w,
+                  st, &o_count);
+    if (s != QVX_OK) return s;
+    if (plan->p.engine == QVX_ENGINE_FUSED) return QVX_OK;   // the fused launch wrote the sums
+    unsigned char *base = static_cast<unsigned char *>(ws);
+    if ((e = qvx::launch_slice_sum(reinterpret_cast<const double2 *>(base + w.partials), batch, o_count,
+                                   amps_dev, st)) != cudaSuccess)
+        return cuda_fail(e, "slice sum launch");
+    return QVX_OK;
+}
+
+qvx_status qvx_amplitude(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch, double *amps_dev,
+                         void *ws, size_t ws_bytes, void *stream) {
+    if (!plan) return fail(QVX_EINVAL, "null plan");
+    return qvx_amplitude_slices(plan, bitstrings_dev, batch, 0, int64_t(1) << plan->p.slices.size(),
+                                amps_dev, ws, ws_bytes, stream);
+}
+
+qvx_status qvx_slice_terms(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch,
+                           int64_t slice_begin, int64_t slice_count, float *terms_dev, void *ws,
+                           size_t ws_bytes, void *stream) {
+    WsLayout w;
+    qvx_status s = check_ws(plan, batch, ws, ws_bytes, &w);
+    if (s != QVX_OK) return s;
+    if ((s = check_range(plan, slice_begin, slice_count)) != QVX_OK) return s;
+    if (batch == 0 || slice_count == 0) return QVX_OK;
+    if (!bitstrings_dev || !terms_dev) return fail(QVX_EINVAL, "null device buffer");
+    int64_t o_count = 0;
+    return run_items(plan, bitstrings_dev, batch, slice_begin, slice_begin + slice_count, terms_dev, nullptr,
+                     ws, w, static_cast<cudaStream_t>(stream), &o_count);
+}
+
+qvx_status qvx_workspace_status(const qvx_plan *plan, void *ws, void *stream) {
+    WsLayout w;
+    qvx_status s = check_ws(plan, 0, ws, (size_t)-1, &w);
+    if (s != QVX_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned int word = 0;
+    unsigned char *base = static_cast<unsigned char *>(ws);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    if ((e = cudaMemcpy(&word, base + w.status, sizeof(word), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "status read");
+    if (word != 0) {
+        if ((e = cudaMemset(base + w.status, 0, sizeof(word))) != cudaSuccess) return cuda_fail(e, "status clear");
+        return fail((qvx_status)word, "device status word set by a kernel");
+    }
+    return QVX_OK;
+}
+
+const char *qvx_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

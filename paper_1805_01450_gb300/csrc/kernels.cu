@@ -1,0 +1,316 @@
+// Device kernels: the pairwise contraction program (fused and stepwise engines) and the
+// FP64 compensated sum of the slice terms.
+#include <cuda_runtime.h>
+
+#include "device_program.h"
+#include "kernels.h"
+
+namespace qvx {
+namespace {
+
+__device__ __forceinline__ uint32_t pext_runs(uint32_t c, const DevRun *runs, int n) {
+    uint32_t r = 0;
+    for (int i = 0; i < n; i++) r |= ((c >> runs[i].src) & ((1u << runs[i].len) - 1u)) << runs[i].dst;
+    return r;
+}
+
+
+// Offset of the entries of `leaf` fixed by this work item (bitstring x, outer slice o).
+__device__ __forceinline__ uint32_t leaf_fixed_offset(const DevLeaf &L, uint64_t x, uint64_t o) {
+    uint32_t off = L.data_off;
+    for (uint32_t f = 0; f < L.n_fixed; f++) {
+        uint32_t src = L.fixed_src[f];
+        uint64_t bit = src < 64 ? (x >> src) & 1ull : (o >> (src - 64)) & 1ull;
+        off += (uint32_t)bit << L.fixed_pos[f];
+    }
+    return off;
+}
+
+struct Operand {
+    const float2 *base;      // arena tensor, or leaf data shifted by the fixed offset
+    const uint32_t *emap;    // leaf element map, or nullptr for an arena tensor
+};
+
+__device__ __forceinline__ float2 fetch(const Operand &op, uint32_t i) {
+    if (op.emap) return __ldg(op.base + __ldg(op.emap + i));
+    return op.base[i];
+}
+
+__device__ __forceinline__ Operand make_operand(const DevProgram *P, const unsigned char *img,
+                                                bool leaf, uint64_t ref, float2 *arena,
+                                                uint64_t x, uint64_t o) {
+    Operand op;
+    if (leaf) {
+        const DevLeaf *L = reinterpret_cast<const DevLeaf *>(img + P->leaves_off) + ref;
+        const float2 *data = reinterpret_cast<const float2 *>(img + P->leaf_data_off);
+        op.base = data + leaf_fixed_offset(*L, x, o);
+        op.emap = reinterpret_cast<const uint32_t *>(img + P->elem_map_off) + L->elem_off;
+    } else {
+        op.base = arena + ref;
+        op.emap = nullptr;
+    }
+    return op;
+}
+
+__device__ __forceinline__ void cmac(float2 &acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+}
+
+// One output entry c of step st.
+__device__ __forceinline__ float2 step_entry(const DevStep &st, uint32_t c, const Operand &A,
+                                             const Operand &B, bool unary) {
+    const uint32_t ia = pext_runs(c, st.runs_a, st.na_runs);
+    const uint32_t ib = unary ? 0u : pext_runs(c, st.runs_b, st.nb_runs);
+    const uint32_t nab = st.nk_ab, na = st.nk_a;
+    const uint32_t nk = nab + na + st.nk_b;
+    const uint32_t mask_ka = (1u << (nab + na)) - 1u, mask_ab = (1u << nab) - 1u;
+    float2 acc = make_float2(0.f, 0.f);
+    for (uint32_t k = 0; k < (1u << nk); k++) {
+        const uint32_t ka = k & mask_ka;
+        const float2 a = fetch(A, ia + (ka << st.a_cb));
+        if (unary) {
+            acc.x += a.x;
+            acc.y += a.y;
+        } else {
+            const uint32_t kb = (k & mask_ab) | ((k >> (nab + na)) << nab);
+            cmac(acc, a, fetch(B, ib + (kb << st.b_cb)));
+        }
+    }
+    return acc;
+}
+
+__device__ __forceinline__ double2 warp_sum(double2 v) {
+    for (int d = 16; d > 0; d >>= 1) {
+        v.x += __shfl_down_sync(0xffffffffu, v.x, d);
+        v.y += __shfl_down_sync(0xffffffffu, v.y, d);
+    }
+    return v;
+}
+
+// Sum of the inner slice terms of the item's final tensor that fall in [s_begin, s_end)
+// (FP64), times the plan's scalar; optionally writes each term.
+__device__ void finish_item(const DevProgram *P, const LaunchArgs &a, const float2 *fin, int64_t b,
+                            uint64_t o, int lane, int lanes) {
+    const uint64_t x = a.bitstrings[b];
+    const bool zero = (x & P->zero_mask) != 0;
+    const double sr = P->scalar_re, si = P->scalar_im;
+    double2 acc = make_double2(0.0, 0.0);
+    const uint32_t n_in = P->n_inner, present = P->final_present;
+    for (uint32_t i = lane; i < (1u << n_in); i += lanes) {
+        const int64_t s = (int64_t)((o << n_in) | i);
+        if (s < a.s_begin || s >= a.s_end) continue;
+        uint32_t fi = 0, bit = 0;
+        for (uint32_t j = 0; j < n_in; j++)
+            if ((present >> j) & 1u) fi |= ((i >> j) & 1u) << bit++;
+        const float2 t = zero ? make_float2(0.f, 0.f) : fin[fi];
+        const double tr = (double)t.x * sr - (double)t.y * si;
+        const double ti = (double)t.x * si + (double)t.y * sr;
+        acc.x += tr;
+        acc.y += ti;
+        if (a.terms) a.terms[b * (a.s_end - a.s_begin) + (s - a.s_begin)] = make_float2((float)tr, (float)ti);
+    }
+    if (lanes == 32) {
+        acc = warp_sum(acc);
+        if (lane == 0) a.partials[b * a.o_count + (int64_t)(o - (uint64_t)a.o_begin)] = acc;
+    }
+}
+
+// ------------------------------------------------------------------ compensated sums
+// Neumaier's compensated addition, and Knuth's exact two-sum to merge (sum, compensation)
+// pairs, so partial sums from many threads combine without losing the compensation.
+__device__ __forceinline__ void neumaier_add(double &s, double &c, double v) {
+    const double t = s + v;
+    if (fabs(s) >= fabs(v)) c += (s - t) + v;
+    else c += (v - t) + s;
+    s = t;
+}
+
+__device__ __forceinline__ void merge_pair(double &s, double &c, double s2, double c2) {
+    const double t = s + s2;
+    const double bp = t - s;
+    const double err = (s - (t - bp)) + (s2 - bp);
+    s = t;
+    c = c + c2 + err;
+}
+
+// Block-wide compensated sum of partials[0..n) (stride 1, double2): result in thread 0.
+__device__ double2 block_compensated_sum(const double2 *partials, int64_t n) {
+    __shared__ double red[4][32];
+    double sr = 0, cr = 0, si = 0, ci = 0;
+    for (int64_t o = threadIdx.x; o < n; o += blockDim.x) {
+        const double2 v = __ldcg(partials + o);   // written by other CTAs: read from L2
+        neumaier_add(sr, cr, v.x);
+        neumaier_add(si, ci, v.y);
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        const double a = __shfl_down_sync(0xffffffffu, sr, d), b = __shfl_down_sync(0xffffffffu, cr, d);
+        const double e = __shfl_down_sync(0xffffffffu, si, d), f = __shfl_down_sync(0xffffffffu, ci, d);
+        merge_pair(sr, cr, a, b);
+        merge_pair(si, ci, e, f);
+    }
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+    __syncthreads();
+    if (lane == 0) {
+        red[0][warp] = sr; red[1][warp] = cr; red[2][warp] = si; red[3][warp] = ci;
+    }
+    __syncthreads();
+    double2 out = make_double2(0.0, 0.0);
+    if (threadIdx.x == 0) {
+        double s0 = red[0][0], c0 = red[1][0], s1 = red[2][0], c1 = red[3][0];
+        for (int w = 1; w < nw; w++) {
+            merge_pair(s0, c0, red[0][w], red[1][w]);
+            merge_pair(s1, c1, red[2][w], red[3][w]);
+        }
+        out = make_double2(s0 + c0, s1 + c1);
+    }
+    return out;
+}
+
+// ------------------------------------------------------------------ fused engine
+// Each group of `warps_per_item` warps runs the whole program for one work item
+// (bitstring b, outer slice o) with its arena in shared memory; groups loop over items.
+__global__ void __launch_bounds__(256) fused_program_kernel(LaunchArgs a, int warps_per_item) {
+    extern __shared__ float2 smem[];
+    const unsigned char *img = a.image;
+    const DevProgram *P = reinterpret_cast<const DevProgram *>(img);
+    const DevStep *steps = reinterpret_cast<const DevStep *>(img + P->steps_off);
+    const int lanes = 32 * warps_per_item;
+    const int group = threadIdx.x / lanes;
+    const int lane = threadIdx.x % lanes;
+    const int groups = blockDim.x / lanes;
+    float2 *arena = smem + (size_t)group * a.arena_elems;
+    const int64_t n_items = a.batch * a.o_count;
+    const unsigned bar_id = 1 + group;
+    for (int64_t item = (int64_t)blockIdx.x * groups + group; item < n_items;
+         item += (int64_t)gridDim.x * groups) {
+        const int64_t b = item / a.o_count;
+        const uint64_t o = (uint64_t)(a.o_begin + item % a.o_count);
+        const uint64_t x = a.bitstrings[b];
+        for (uint32_t s = 0; s < a.n_steps; s++) {
+            const DevStep &st = steps[s];
+            const bool unary = st.flags & kStepUnary;
+            const Operand A = make_operand(P, img, st.flags & kStepALeaf, st.a_off, arena, x, o);
+            Operand B = A;
+            if (!unary) B = make_operand(P, img, st.flags & kStepBLeaf, st.b_off, arena, x, o);
+            float2 *C = arena + st.c_off;
+            for (uint32_t c = lane; c < (1u << st.rc); c += lanes) C[c] = step_entry(st, c, A, B, unary);
+            if (warps_per_item == 1) __syncwarp();
+            else asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(lanes));
+        }
+        if (lane < 32) finish_item(P, a, arena + P->final_off, b, o, lane, 32);
+        if (warps_per_item == 1) __syncwarp();
+        else asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(lanes));
+    }
+    if (a.amps == nullptr) return;
+    // the last CTA to finish adds every bitstring's item partials
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned ticket = atomicAdd(a.counter, 1u);
+        last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int64_t b = 0; b < a.batch; b++) {
+        const double2 r = block_compensated_sum(a.partials + b * a.o_count, a.o_count);
+        if (threadIdx.x == 0) {
+            a.amps[2 * b] = r.x;
+            a.amps[2 * b + 1] = r.y;
+        }
+    }
+    if (threadIdx.x == 0) *a.counter = 0u;
+}
+
+// ------------------------------------------------------------------ stepwise engine
+__global__ void step_kernel(LaunchArgs a, uint32_t s_idx, int64_t item_begin, int64_t n_items,
+                            float2 *arenas) {
+    const unsigned char *img = a.image;
+    const DevProgram *P = reinterpret_cast<const DevProgram *>(img);
+    const DevStep &st = reinterpret_cast<const DevStep *>(img + P->steps_off)[s_idx];
+    const uint64_t per = 1ull << st.rc;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= per * (uint64_t)n_items) return;
+    const int64_t il = (int64_t)(tid >> st.rc);
+    const uint32_t c = (uint32_t)(tid & (per - 1));
+    const int64_t item = item_begin + il;
+    const int64_t b = item / a.o_count;
+    const uint64_t o = (uint64_t)(a.o_begin + item % a.o_count);
+    const uint64_t x = a.bitstrings[b];
+    float2 *arena = arenas + (uint64_t)il * a.arena_elems;
+    const bool unary = st.flags & kStepUnary;
+    const Operand A = make_operand(P, img, st.flags & kStepALeaf, st.a_off, arena, x, o);
+    Operand B = A;
+    if (!unary) B = make_operand(P, img, st.flags & kStepBLeaf, st.b_off, arena, x, o);
+    arena[st.c_off + c] = step_entry(st, c, A, B, unary);
+}
+
+__global__ void finish_kernel(LaunchArgs a, int64_t item_begin, int64_t n_items, const float2 *arenas) {
+    const DevProgram *P = reinterpret_cast<const DevProgram *>(a.image);
+    const int64_t il = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    if (il >= n_items) return;
+    const int64_t item = item_begin + il;
+    const int64_t b = item / a.o_count;
+    const uint64_t o = (uint64_t)(a.o_begin + item % a.o_count);
+    finish_item(P, a, arenas + (uint64_t)il * a.arena_elems + P->final_off, b, o, threadIdx.x % 32, 32);
+}
+
+// ------------------------------------------------------------------ slice sum
+__global__ void slice_sum_kernel(const double2 *partials, int64_t o_count, double *amps) {
+    const int64_t b = blockIdx.x;
+    const double2 r = block_compensated_sum(partials + b * o_count, o_count);
+    if (threadIdx.x == 0) {
+        amps[2 * b] = r.x;
+        amps[2 * b + 1] = r.y;
+    }
+}
+
+}  // namespace
+
+cudaError_t fused_prepare(size_t smem_bytes) {
+    return cudaFuncSetAttribute(fused_program_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes);
+}
+
+int fused_blocks_per_sm(int threads, size_t smem_bytes) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_program_kernel, threads, smem_bytes) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+cudaError_t launch_fused(const LaunchArgs &a, int warps_per_item, int items_per_cta, int grid,
+                         size_t smem_bytes, cudaStream_t s) {
+    const int threads = 32 * warps_per_item * items_per_cta;
+    fused_program_kernel<<<grid, threads, smem_bytes, s>>>(a, warps_per_item);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step(const LaunchArgs &a, uint32_t step, int64_t item_begin, int64_t n_items,
+                        float2 *arenas, uint32_t rc, cudaStream_t s) {
+    const uint64_t total = (uint64_t)n_items << rc;
+    const int threads = 256;
+    const uint64_t blocks = (total + threads - 1) / threads;
+    step_kernel<<<(unsigned)blocks, threads, 0, s>>>(a, step, item_begin, n_items, arenas);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_items(const LaunchArgs &a, int64_t item_begin, int64_t n_items,
+                                const float2 *arenas, cudaStream_t s) {
+    const int per_block = 8;
+    const int64_t blocks = (n_items + per_block - 1) / per_block;
+    finish_kernel<<<(unsigned)blocks, 32 * per_block, 0, s>>>(a, item_begin, n_items, arenas);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slice_sum(const double2 *partials, int64_t batch, int64_t o_count, double *amps,
+                             cudaStream_t s) {
+    slice_sum_kernel<<<(unsigned)batch, 256, 0, s>>>(partials, o_count, amps);
+    return cudaGetLastError();
+}
+
+}  // namespace qvx

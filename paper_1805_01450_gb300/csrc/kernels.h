@@ -1,0 +1,43 @@
+// Launchers of the device kernels (kernels.cu). All take the caller's stream and return
+// the cudaError_t of the launch.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qvx {
+
+struct LaunchArgs {
+    const unsigned char *image;     // device image (DevProgram first)
+    const uint64_t *bitstrings;     // device, batch entries
+    int64_t batch;
+    int64_t o_begin, o_count;       // outer slice numbers of this call
+    int64_t s_begin, s_end;         // slice range summed / written
+    uint64_t arena_elems;
+    uint32_t n_steps, n_inner;
+    double2 *partials;              // batch * o_count FP64 item sums
+    float2 *terms;                  // optional: batch * (s_end - s_begin) slice terms
+    unsigned int *status;           // device status word
+    unsigned int *counter;          // CTAs finished (fused engine's final sum); zero between calls
+    double *amps;                   // optional: 2 * batch FP64 amplitudes written by the fused engine
+};
+
+// Fused engine: one warp group per work item, every tensor in shared memory. When
+// a.amps is set, the last CTA to finish also adds the item partials (compensated FP64).
+cudaError_t launch_fused(const LaunchArgs &a, int warps_per_item, int items_per_cta, int grid,
+                         size_t smem_bytes, cudaStream_t s);
+int fused_blocks_per_sm(int threads, size_t smem_bytes);
+cudaError_t fused_prepare(size_t smem_bytes);
+
+// Stepwise engine: one launch per program step over `n_items` work items, tensors in a
+// global-memory arena per item.
+cudaError_t launch_step(const LaunchArgs &a, uint32_t step, int64_t item_begin, int64_t n_items,
+                        float2 *arenas, uint32_t rc, cudaStream_t s);
+cudaError_t launch_finish_items(const LaunchArgs &a, int64_t item_begin, int64_t n_items,
+                                const float2 *arenas, cudaStream_t s);
+
+// FP64 compensated sum of the item partials of every bitstring (Section 3.B.2: the slice
+// terms are added).
+cudaError_t launch_slice_sum(const double2 *partials, int64_t batch, int64_t o_count,
+                             double *amps, cudaStream_t s);
+
+}  // namespace qvx

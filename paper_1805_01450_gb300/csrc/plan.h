@@ -1,0 +1,74 @@
+// Host-side plan: graphical model, elimination order, slices and the pairwise program.
+#pragma once
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/qvx.h"
+#include "device_program.h"
+
+namespace qvx {
+
+using cplx = std::complex<double>;
+
+// A tensor over binary variables: bit j of an entry's index is the value of modes[j].
+struct HostTensor {
+    std::vector<int> modes;
+    std::vector<cplx> data;
+};
+
+// Variable ids inside a plan: [0, n_vars) are the summed variables (canonical ids);
+// n_vars + q is the output variable of qubit q, fixed to x_q per bitstring.
+struct Model {
+    int n_qubits = 0, n_vars = 0;
+    std::vector<int> var_qubit, var_ordinal;
+    uint64_t zero_mask = 0;        // qubits with no non-diagonal gate: output equals input 0
+    cplx scalar = 1.0;
+    std::vector<HostTensor> tensors;
+    std::vector<std::pair<int, int>> edges;   // a < b, sorted, summed variables only
+};
+
+// One pairwise contraction of the program.
+struct PStep {
+    int a = -1, b = -1, c = -1;                 // tensor ids; b = -1 for a one-operand sum
+    std::vector<int> k_ab, k_a, k_b;            // summed modes
+};
+
+// A tensor of the program: a restricted leaf or a step's output.
+struct PTensor {
+    std::vector<int> modes;                     // layout, set from the consumer
+    int leaf = -1;                              // index in Plan::leaves, or -1
+    int producer = -1, consumer = -1;           // step ids (-1: leaf / final)
+    int64_t offset = 0;                         // arena offset (complex64 entries)
+};
+
+struct Plan {
+    qvx_plan_opts opts{};
+    Model model;
+    std::vector<int> order;                     // elimination order (non-sliced ids)
+    std::vector<int> slices;                    // inner slices first, then outer
+    int n_inner = 0;
+    double log2_cost = 0, log2_cost_unsliced = 0;
+    int width = 0;
+    // program
+    std::vector<HostTensor> leaves;             // stored leaves (may hold fixed modes)
+    std::vector<PTensor> tensors;
+    std::vector<PStep> steps;
+    int final_tensor = -1;
+    int64_t arena_elems = 0;
+    int max_rank = 0;
+    double flops_per_item = 0, bytes_per_item = 0;
+    cplx prog_scalar = 1.0;                     // model scalar times the program's own factors
+    int engine = QVX_ENGINE_FUSED;
+    int warps_per_item = 1;
+    std::vector<unsigned char> image;          // device image (DevProgram first)
+};
+
+// planner.cpp
+bool build_model(const qvx_circuit *c, Model *m, std::string *err);
+qvx_status make_plan(const qvx_circuit *c, const int32_t *order, int32_t n_order,
+                     const int32_t *slices, int32_t n_slices, const qvx_plan_opts &opts,
+                     Plan *p, std::string *err);
+
+}  // namespace qvx

@@ -1,0 +1,874 @@
+// Host planner: graphical model (Section 3.A), elimination order and slices
+// (Sections 3.B.1-3.B.3), the pairwise contraction program and its device image.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <unordered_map>
+
+#include "plan.h"
+
+namespace qvx {
+namespace {
+
+// ---------------------------------------------------------------- gate matrices [out][in]
+bool gate_matrix(const qvx_gate &g, cplx m[2][2]) {
+    const double r = 1.0 / std::sqrt(2.0);
+    switch (g.kind) {
+    case QVX_GATE_H:
+        m[0][0] = r; m[0][1] = r; m[1][0] = r; m[1][1] = -r;
+        return true;
+    case QVX_GATE_SQRT_X:
+        m[0][0] = cplx(0.5, 0.5); m[0][1] = cplx(0.5, -0.5);
+        m[1][0] = cplx(0.5, -0.5); m[1][1] = cplx(0.5, 0.5);
+        return true;
+    case QVX_GATE_SQRT_Y:
+        m[0][0] = cplx(0.5, 0.5); m[0][1] = cplx(-0.5, -0.5);
+        m[1][0] = cplx(0.5, 0.5); m[1][1] = cplx(0.5, 0.5);
+        return true;
+    case QVX_GATE_RXY: {
+        // cos(t/2) I - i sin(t/2) [[0, e^{-i phi}], [e^{i phi}, 0]]
+        const double c = std::cos(g.theta / 2), s = std::sin(g.theta / 2);
+        m[0][0] = c; m[1][1] = c;
+        m[0][1] = cplx(0, -s) * std::polar(1.0, -g.phi);
+        m[1][0] = cplx(0, -s) * std::polar(1.0, g.phi);
+        return true;
+    }
+    case QVX_GATE_U1:
+        for (int i = 0; i < 2; i++)
+            for (int j = 0; j < 2; j++) m[i][j] = cplx(g.u[2 * (2 * i + j)], g.u[2 * (2 * i + j) + 1]);
+        return true;
+    default:
+        return false;
+    }
+}
+
+uint64_t splitmix64(uint64_t &s) {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+int find_pos(const std::vector<int> &v, int x) {
+    for (size_t i = 0; i < v.size(); i++)
+        if (v[i] == x) return (int)i;
+    return -1;
+}
+
+// S *= T broadcast over S's modes (T's modes are a subset of S's).
+void absorb_into(HostTensor &S, const HostTensor &T) {
+    std::vector<int> pos(T.modes.size());
+    for (size_t j = 0; j < T.modes.size(); j++) pos[j] = find_pos(S.modes, T.modes[j]);
+    for (size_t i = 0; i < S.data.size(); i++) {
+        size_t t = 0;
+        for (size_t j = 0; j < pos.size(); j++) t |= ((i >> pos[j]) & 1u) << j;
+        S.data[i] *= T.data[t];
+    }
+}
+
+bool is_subset(const std::vector<int> &a, const std::vector<int> &b) {
+    for (int x : a)
+        if (find_pos(b, x) < 0) return false;
+    return true;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- graphical model
+bool build_model(const qvx_circuit *c, Model *m, std::string *err) {
+    if (!c || c->n_qubits < 1 || c->n_qubits > 64 || c->n_gates < 0 || (c->n_gates > 0 && !c->gates)) {
+        *err = "circuit: need 1 <= n_qubits <= 64 and a gate array";
+        return false;
+    }
+    const int n = c->n_qubits;
+    std::vector<int> cur(n, 0);
+    struct Raw {
+        std::vector<std::pair<int, int>> keys;   // (qubit, ordinal); bit j of an index <-> keys[j]
+        std::vector<cplx> data;
+    };
+    std::vector<Raw> raw;
+    raw.reserve((size_t)c->n_gates);
+    for (int64_t i = 0; i < c->n_gates; i++) {
+        const qvx_gate &g = c->gates[i];
+        if (g.q0 < 0 || g.q0 >= n) { *err = "gate " + std::to_string(i) + ": qubit out of range"; return false; }
+        Raw r;
+        if (g.kind == QVX_GATE_CZ) {
+            if (g.q1 < 0 || g.q1 >= n || g.q1 == g.q0) { *err = "gate " + std::to_string(i) + ": bad CZ pair"; return false; }
+            r.keys = {{g.q0, cur[g.q0]}, {g.q1, cur[g.q1]}};
+            r.data = {1.0, 1.0, 1.0, -1.0};
+        } else if (g.kind == QVX_GATE_T) {
+            r.keys = {{g.q0, cur[g.q0]}};
+            r.data = {1.0, std::polar(1.0, M_PI / 4)};
+        } else {
+            cplx u[2][2];
+            if (!gate_matrix(g, u)) { *err = "gate " + std::to_string(i) + ": unknown kind"; return false; }
+            // rank-2 tensor tau[i, j] = U[j, i] between the old and the new variable (Fig. 3)
+            r.keys = {{g.q0, cur[g.q0]}, {g.q0, cur[g.q0] + 1}};
+            r.data.resize(4);
+            for (int a = 0; a < 2; a++)
+                for (int b = 0; b < 2; b++) r.data[a | (b << 1)] = u[b][a];
+            cur[g.q0]++;
+        }
+        raw.push_back(std::move(r));
+    }
+    m->n_qubits = n;
+    m->var_qubit.clear();
+    m->var_ordinal.clear();
+    std::vector<int> first_id(n, 0);
+    for (int q = 0; q < n; q++) {
+        first_id[q] = (int)m->var_qubit.size();
+        for (int j = 1; j < cur[q]; j++) {
+            m->var_qubit.push_back(q);
+            m->var_ordinal.push_back(j);
+        }
+    }
+    m->n_vars = (int)m->var_qubit.size();
+    m->zero_mask = 0;
+    for (int q = 0; q < n; q++)
+        if (cur[q] == 0) m->zero_mask |= 1ull << q;
+    m->scalar = 1.0;
+    m->tensors.clear();
+    // key -> id: input (q, 0) is fixed to 0 (-1 here); summed (q, j) -> canonical id;
+    // output (q, last) -> n_vars + q
+    auto id_of = [&](int q, int j) -> int {
+        if (j == 0) return -1;
+        if (j == cur[q]) return m->n_vars + q;
+        return first_id[q] + j - 1;
+    };
+    for (Raw &r : raw) {
+        HostTensor t;
+        std::vector<int> keep;
+        for (size_t j = 0; j < r.keys.size(); j++) {
+            int id = id_of(r.keys[j].first, r.keys[j].second);
+            if (id >= 0) { t.modes.push_back(id); keep.push_back((int)j); }
+        }
+        t.data.resize(size_t(1) << t.modes.size());
+        for (size_t e = 0; e < t.data.size(); e++) {
+            size_t src = 0;  // fixed inputs take value 0
+            for (size_t j = 0; j < keep.size(); j++) src |= ((e >> j) & 1u) << keep[j];
+            t.data[e] = r.data[src];
+        }
+        if (t.modes.empty()) m->scalar *= t.data[0];
+        else m->tensors.push_back(std::move(t));
+    }
+    // absorb every tensor whose modes are a subset of another's (rank-1 gates into their
+    // neighbours, parallel rank-2 tensors into one); the graph is unchanged by this
+    std::vector<int> idx(m->tensors.size());
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+        return m->tensors[a].modes.size() < m->tensors[b].modes.size();
+    });
+    std::vector<int> rank_pos(idx.size());
+    for (size_t i = 0; i < idx.size(); i++) rank_pos[idx[i]] = (int)i;
+    std::unordered_map<int, std::vector<int>> by_mode;
+    for (size_t t = 0; t < m->tensors.size(); t++)
+        for (int v : m->tensors[t].modes) by_mode[v].push_back((int)t);
+    std::vector<char> dead(m->tensors.size(), 0);
+    for (size_t i = 0; i < idx.size(); i++) {
+        int t = idx[i];
+        const HostTensor &T = m->tensors[t];
+        int best = -1;
+        for (int s : by_mode[T.modes[0]]) {
+            if (s == t || dead[s] || rank_pos[s] < (int)i) continue;
+            if (m->tensors[s].modes.size() < T.modes.size()) continue;
+            if (!is_subset(T.modes, m->tensors[s].modes)) continue;
+            if (best < 0 || rank_pos[s] < rank_pos[best]) best = s;
+        }
+        if (best >= 0) {
+            absorb_into(m->tensors[best], T);
+            dead[t] = 1;
+        }
+    }
+    std::vector<HostTensor> kept;
+    for (size_t t = 0; t < m->tensors.size(); t++)
+        if (!dead[t]) kept.push_back(std::move(m->tensors[t]));
+    m->tensors = std::move(kept);
+    // edges between summed variables sharing a tensor
+    std::vector<std::pair<int, int>> es;
+    for (const HostTensor &t : m->tensors)
+        for (size_t a = 0; a < t.modes.size(); a++)
+            for (size_t b = a + 1; b < t.modes.size(); b++) {
+                int u = t.modes[a], v = t.modes[b];
+                if (u >= m->n_vars || v >= m->n_vars) continue;
+                es.push_back({std::min(u, v), std::max(u, v)});
+            }
+    std::sort(es.begin(), es.end());
+    es.erase(std::unique(es.begin(), es.end()), es.end());
+    m->edges = std::move(es);
+    return true;
+}
+
+// ---------------------------------------------------------------- orderings
+namespace {
+
+struct Graph {
+    int n = 0, W = 0;
+    std::vector<uint64_t> bits;  // n rows of W words
+    uint64_t *row(int v) { return &bits[(size_t)v * W]; }
+    const uint64_t *row(int v) const { return &bits[(size_t)v * W]; }
+    void init(int n_, const std::vector<std::pair<int, int>> &es) {
+        n = n_;
+        W = (n + 63) / 64;
+        if (W == 0) W = 1;
+        bits.assign((size_t)n * W, 0);
+        for (auto &e : es) {
+            row(e.first)[e.second >> 6] |= 1ull << (e.second & 63);
+            row(e.second)[e.first >> 6] |= 1ull << (e.first & 63);
+        }
+    }
+    int degree(int v) const {
+        int d = 0;
+        for (int w = 0; w < W; w++) d += __builtin_popcountll(row(v)[w]);
+        return d;
+    }
+    // Section 3.B.1 step 4: join every two neighbours of v, then remove v.
+    void eliminate(int v) {
+        uint64_t *rv = row(v);
+        for (int w = 0; w < W; w++) {
+            uint64_t m = rv[w];
+            while (m) {
+                int u = w * 64 + __builtin_ctzll(m);
+                m &= m - 1;
+                uint64_t *ru = row(u);
+                for (int x = 0; x < W; x++) ru[x] |= rv[x];
+                ru[u >> 6] &= ~(1ull << (u & 63));
+                ru[v >> 6] &= ~(1ull << (v & 63));
+            }
+        }
+        std::fill(rv, rv + W, 0ull);
+    }
+    // Fixing v (Section 3.B.2) removes the vertex and its edges.
+    void remove(int v) {
+        uint64_t *rv = row(v);
+        for (int w = 0; w < W; w++) {
+            uint64_t m = rv[w];
+            while (m) {
+                int u = w * 64 + __builtin_ctzll(m);
+                m &= m - 1;
+                row(u)[v >> 6] &= ~(1ull << (v & 63));
+            }
+        }
+        std::fill(rv, rv + W, 0ull);
+    }
+};
+
+// Cost of an order (sum of 2^deg(v), Section 3.B.1) with `removed` vertices fixed first.
+double order_cost(const Graph &g0, const std::vector<int> &order, const std::vector<char> &removed,
+                  int *width) {
+    Graph g = g0;
+    for (int v = 0; v < g.n; v++)
+        if (removed[v]) g.remove(v);
+    double cost = 0;
+    int wd = 0;
+    for (int v : order) {
+        if (removed[v]) continue;
+        int d = g.degree(v);
+        cost += std::ldexp(1.0, d);
+        wd = std::max(wd, d);
+        g.eliminate(v);
+    }
+    if (width) *width = wd;
+    return cost;
+}
+
+// Greedy min-fill elimination order with random tie-breaks (stand-in for QuickBB's
+// min-fill branching, Section 3.B.3).
+double minfill_order(const Graph &g0, const std::vector<char> &removed, uint64_t seed,
+                     std::vector<int> *order, int *width) {
+    Graph g = g0;
+    std::vector<int> alive;
+    for (int v = 0; v < g.n; v++) {
+        if (removed[v]) g.remove(v);
+    }
+    for (int v = 0; v < g.n; v++)
+        if (!removed[v]) alive.push_back(v);
+    order->clear();
+    double cost = 0;
+    int wd = 0;
+    uint64_t rng = seed;
+    std::vector<int> ties;
+    while (!alive.empty()) {
+        long best_fill = -1;
+        int best_deg = 0;
+        ties.clear();
+        for (int v : alive) {
+            const uint64_t *rv = g.row(v);
+            int deg = g.degree(v);
+            long fill = 0;
+            if (best_fill >= 0 && (long)deg * (deg - 1) / 2 < 0) continue;
+            for (int w = 0; w < g.W; w++) {
+                uint64_t m = rv[w];
+                while (m) {
+                    int u = w * 64 + __builtin_ctzll(m);
+                    m &= m - 1;
+                    const uint64_t *ru = g.row(u);
+                    for (int x = 0; x < g.W; x++) fill += __builtin_popcountll(rv[x] & ~ru[x]);
+                    fill -= 1;  // u itself
+                }
+            }
+            fill /= 2;
+            if (best_fill < 0 || fill < best_fill || (fill == best_fill && deg < best_deg)) {
+                best_fill = fill;
+                best_deg = deg;
+                ties.clear();
+                ties.push_back(v);
+            } else if (fill == best_fill && deg == best_deg) {
+                ties.push_back(v);
+            }
+        }
+        int pick = ties[splitmix64(rng) % ties.size()];
+        int d = g.degree(pick);
+        cost += std::ldexp(1.0, d);
+        wd = std::max(wd, d);
+        g.eliminate(pick);
+        order->push_back(pick);
+        alive.erase(std::find(alive.begin(), alive.end(), pick));
+    }
+    if (width) *width = wd;
+    return cost;
+}
+
+double best_order(const Graph &g, const std::vector<char> &removed, const qvx_plan_opts &o,
+                  uint64_t salt, std::vector<int> *order, int *width) {
+    double best = -1;
+    std::vector<int> cand;
+    int w = 0;
+    uint64_t s = o.order_seed ^ (salt * 0x9E3779B97F4A7C15ull);
+    for (int r = 0; r < std::max(1, o.order_restarts); r++) {
+        uint64_t seed = splitmix64(s);
+        double cst = minfill_order(g, removed, seed, &cand, &w);
+        if (best < 0 || cst < best) {
+            best = cst;
+            *order = cand;
+            *width = w;
+        }
+    }
+    return best;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- program construction
+namespace {
+
+struct ProgramBuilder {
+    Plan &p;
+    const Model &m;
+    int n_ids;                          // variable id space: summed + outputs
+    std::vector<char> open;             // inner sliced variables
+    std::vector<char> fixed;            // outer sliced variables and outputs
+    std::vector<int> cnt;               // live pool tensors holding each variable
+    std::vector<char> summed;
+    std::vector<int> pool;
+    cplx factor = 1.0;
+    std::string err;
+
+    ProgramBuilder(Plan &p_, const Model &m_) : p(p_), m(m_) {
+        n_ids = m.n_vars + m.n_qubits;
+        open.assign(n_ids, 0);
+        fixed.assign(n_ids, 0);
+        cnt.assign(n_ids, 0);
+        summed.assign(n_ids, 0);
+        for (int v = m.n_vars; v < n_ids; v++) fixed[v] = 1;
+        for (size_t i = 0; i < p.slices.size(); i++) {
+            if ((int)i < p.n_inner) open[p.slices[i]] = 1;
+            else fixed[p.slices[i]] = 1;
+        }
+    }
+
+    int new_tensor(std::vector<int> modes) {
+        PTensor t;
+        t.modes = std::move(modes);
+        p.tensors.push_back(std::move(t));
+        return (int)p.tensors.size() - 1;
+    }
+
+    bool add_leaves() {
+        for (size_t i = 0; i < m.tensors.size(); i++) {
+            const HostTensor &h = m.tensors[i];
+            std::vector<int> modes;
+            for (int v : h.modes)
+                if (!fixed[v]) modes.push_back(v);
+            p.leaves.push_back(h);
+            int t = new_tensor(modes);
+            p.tensors[t].leaf = (int)p.leaves.size() - 1;
+            for (int v : modes) cnt[v]++;
+            pool.push_back(t);
+        }
+        return true;
+    }
+
+    bool summable(int v) const { return v < m.n_vars && !open[v] && !fixed[v]; }
+
+    // pairwise contraction of pool tensors a and b; every variable held by no other live
+    // tensor is summed here
+    int contract(int a, int b) {
+        const std::vector<int> A = p.tensors[a].modes, B = p.tensors[b].modes;
+        std::vector<int> U = A;
+        for (int v : B)
+            if (find_pos(U, v) < 0) U.push_back(v);
+        PStep s;
+        s.a = a;
+        s.b = b;
+        std::vector<int> C;
+        for (int v : U) {
+            bool ia = find_pos(A, v) >= 0, ib = find_pos(B, v) >= 0;
+            bool dead = summable(v) && cnt[v] == (int)ia + (int)ib;
+            if (!dead) C.push_back(v);
+            else if (ia && ib) s.k_ab.push_back(v);
+            else if (ia) s.k_a.push_back(v);
+            else s.k_b.push_back(v);
+        }
+        for (int v : A) cnt[v]--;
+        for (int v : B) cnt[v]--;
+        for (int v : C) cnt[v]++;
+        for (int v : s.k_ab) summed[v] = 1;
+        for (int v : s.k_a) summed[v] = 1;
+        for (int v : s.k_b) summed[v] = 1;
+        int c = new_tensor(C);
+        s.c = c;
+        int sid = (int)p.steps.size();
+        p.tensors[a].consumer = sid;
+        p.tensors[b].consumer = sid;
+        p.tensors[c].producer = sid;
+        p.steps.push_back(s);
+        pool.erase(std::find(pool.begin(), pool.end(), a));
+        pool.erase(std::find(pool.begin(), pool.end(), b));
+        pool.push_back(c);
+        return c;
+    }
+
+    int reduce(int a) {
+        const std::vector<int> A = p.tensors[a].modes;
+        PStep s;
+        s.a = a;
+        std::vector<int> C;
+        for (int v : A) {
+            if (summable(v) && cnt[v] == 1) s.k_a.push_back(v);
+            else C.push_back(v);
+        }
+        for (int v : A) cnt[v]--;
+        for (int v : C) cnt[v]++;
+        for (int v : s.k_a) summed[v] = 1;
+        int c = new_tensor(C);
+        s.c = c;
+        int sid = (int)p.steps.size();
+        p.tensors[a].consumer = sid;
+        p.tensors[c].producer = sid;
+        p.steps.push_back(s);
+        pool.erase(std::find(pool.begin(), pool.end(), a));
+        pool.push_back(c);
+        return c;
+    }
+
+    size_t union_rank(int a, int b, bool drop_dead) const {
+        const auto &A = p.tensors[a].modes, &B = p.tensors[b].modes;
+        size_t r = 0;
+        std::vector<int> U = A;
+        for (int v : B)
+            if (find_pos(U, v) < 0) U.push_back(v);
+        for (int v : U) {
+            bool ia = find_pos(A, v) >= 0, ib = find_pos(B, v) >= 0;
+            bool dead = summable(v) && cnt[v] == (int)ia + (int)ib;
+            if (!drop_dead || !dead) r++;
+        }
+        return r;
+    }
+
+    // multiply a set of tensors pairwise, the pair with the smallest result first
+    // (small inputs first, the large tensor last: Section 3.B.1)
+    void combine(std::vector<int> bucket) {
+        while (bucket.size() > 1) {
+            size_t bi = 0, bj = 1, best = SIZE_MAX, best_in = SIZE_MAX;
+            for (size_t i = 0; i < bucket.size(); i++)
+                for (size_t j = i + 1; j < bucket.size(); j++) {
+                    size_t r = union_rank(bucket[i], bucket[j], true);
+                    size_t in = std::max(p.tensors[bucket[i]].modes.size(), p.tensors[bucket[j]].modes.size());
+                    if (r < best || (r == best && in < best_in)) {
+                        best = r; best_in = in; bi = i; bj = j;
+                    }
+                }
+            int c = contract(bucket[bi], bucket[bj]);
+            bucket.erase(bucket.begin() + bj);
+            bucket[bi] = c;
+        }
+    }
+
+    bool run() {
+        add_leaves();
+        for (int v : p.order) {
+            if (summed[v]) continue;            // already summed with a pair that held it last
+            std::vector<int> bucket;
+            for (int t : pool)
+                if (find_pos(p.tensors[t].modes, v) >= 0) bucket.push_back(t);
+            if (bucket.empty()) {               // v is in no tensor: sum over v of 1
+                factor *= 2.0;
+                summed[v] = 1;
+                continue;
+            }
+            if (bucket.size() == 1) reduce(bucket[0]);
+            else combine(bucket);
+            if (!summed[v]) { err = "internal: variable not summed"; return false; }
+        }
+        for (int t : pool)
+            for (int v : p.tensors[t].modes)
+                if (!open[v]) { err = "internal: variable left in the final tensors"; return false; }
+        if (pool.empty()) {                     // nothing at all: the constant 1
+            HostTensor one;
+            one.data = {1.0};
+            p.leaves.push_back(one);
+            int t = new_tensor({});
+            p.tensors[t].leaf = (int)p.leaves.size() - 1;
+            pool.push_back(t);
+        }
+        combine(pool);
+        int fin = pool[0];
+        if (p.tensors[fin].leaf >= 0) fin = reduce(fin);   // the final tensor lives in the arena
+        p.final_tensor = fin;
+        return true;
+    }
+};
+
+void assign_layouts(Plan &p) {
+    // the final tensor: inner slice modes in slice-number bit order
+    PTensor &f = p.tensors[p.final_tensor];
+    std::vector<int> fin;
+    for (int i = 0; i < p.n_inner; i++)
+        if (find_pos(f.modes, p.slices[i]) >= 0) fin.push_back(p.slices[i]);
+    f.modes = fin;
+    // every operand takes its consumer's order: output modes first (in the output's
+    // order), then the summed modes
+    for (int s = (int)p.steps.size() - 1; s >= 0; s--) {
+        const PStep &st = p.steps[s];
+        const std::vector<int> C = p.tensors[st.c].modes;
+        auto lay = [&](int t, const std::vector<int> &own) {
+            std::vector<int> old = p.tensors[t].modes, L;
+            for (int v : C)
+                if (find_pos(old, v) >= 0) L.push_back(v);
+            for (int v : st.k_ab) L.push_back(v);
+            for (int v : own) L.push_back(v);
+            p.tensors[t].modes = L;
+        };
+        lay(st.a, st.k_a);
+        if (st.b >= 0) lay(st.b, st.k_b);
+    }
+}
+
+// First-fit arena allocation of the step outputs over their lifetimes.
+int64_t allocate_arena(Plan &p) {
+    struct Block { int64_t off, len; int t; };
+    std::vector<Block> live;
+    int64_t peak = 0;
+    auto alloc = [&](int t) {
+        int64_t len = int64_t(1) << p.tensors[t].modes.size();
+        len = (len + 3) & ~int64_t(3);            // 32-byte granules
+        std::sort(live.begin(), live.end(), [](const Block &a, const Block &b) { return a.off < b.off; });
+        int64_t at = 0;
+        for (const Block &b : live) {
+            if (b.off - at >= len) break;
+            at = std::max(at, b.off + b.len);
+        }
+        live.push_back({at, len, t});
+        p.tensors[t].offset = at;
+        peak = std::max(peak, at + len);
+    };
+    auto release = [&](int t) {
+        for (size_t i = 0; i < live.size(); i++)
+            if (live[i].t == t) { live.erase(live.begin() + i); return; }
+    };
+    for (size_t s = 0; s < p.steps.size(); s++) {
+        const PStep &st = p.steps[s];
+        alloc(st.c);
+        if (p.tensors[st.a].leaf < 0) release(st.a);
+        if (st.b >= 0 && p.tensors[st.b].leaf < 0) release(st.b);
+    }
+    return peak;
+}
+
+void program_stats(Plan &p) {
+    double fl = 0, by = 0;
+    int mr = 0;
+    for (const PStep &s : p.steps) {
+        const auto &A = p.tensors[s.a].modes;
+        const auto &C = p.tensors[s.c].modes;
+        mr = std::max(mr, (int)C.size());
+        if (s.b < 0) {
+            fl += 2.0 * std::ldexp(1.0, (int)A.size());
+            by += 8.0 * (std::ldexp(1.0, (int)A.size()) + std::ldexp(1.0, (int)C.size()));
+        } else {
+            const auto &B = p.tensors[s.b].modes;
+            int u = (int)(C.size() + s.k_ab.size() + s.k_a.size() + s.k_b.size());
+            fl += 8.0 * std::ldexp(1.0, u);
+            by += 8.0 * (std::ldexp(1.0, (int)A.size()) + std::ldexp(1.0, (int)B.size()) +
+                         std::ldexp(1.0, (int)C.size()));
+        }
+    }
+    p.flops_per_item = fl;
+    p.bytes_per_item = by;
+    p.max_rank = mr;
+}
+
+bool make_runs(const std::vector<int> &C, const std::vector<int> &X, DevRun *runs, uint8_t *n_runs,
+               uint8_t *n_cb) {
+    int nr = 0, dst = 0;
+    size_t j = 0;
+    while (j < C.size()) {
+        if (find_pos(X, C[j]) < 0) { j++; continue; }
+        size_t k = j;
+        while (k < C.size() && find_pos(X, C[k]) >= 0) k++;
+        if (nr >= kMaxRuns) return false;
+        runs[nr].src = (uint8_t)j;
+        runs[nr].len = (uint8_t)(k - j);
+        runs[nr].dst = (uint8_t)dst;
+        runs[nr].pad = 0;
+        dst += (int)(k - j);
+        nr++;
+        j = k;
+    }
+    *n_runs = (uint8_t)nr;
+    *n_cb = (uint8_t)dst;
+    return true;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+bool serialize(Plan &p, std::string *err) {
+    const Model &m = p.model;
+    // leaf element maps and stored data
+    std::vector<DevLeaf> dl(p.leaves.size());
+    std::vector<uint32_t> emap;
+    std::vector<float> ldata;
+    std::vector<int> leaf_tensor(p.leaves.size(), -1);
+    for (size_t t = 0; t < p.tensors.size(); t++)
+        if (p.tensors[t].leaf >= 0) leaf_tensor[p.tensors[t].leaf] = (int)t;
+    const int n_outer_bits = (int)p.slices.size() - p.n_inner;
+    for (size_t l = 0; l < p.leaves.size(); l++) {
+        const HostTensor &h = p.leaves[l];
+        const std::vector<int> &P = p.tensors[leaf_tensor[l]].modes;
+        DevLeaf &d = dl[l];
+        std::memset(&d, 0, sizeof(d));
+        d.data_off = (uint32_t)(ldata.size() / 2);
+        d.elem_off = (uint32_t)emap.size();
+        d.n_elem = 1u << P.size();
+        for (size_t j = 0; j < h.modes.size(); j++) {
+            int v = h.modes[j];
+            if (find_pos(P, v) >= 0) continue;
+            if ((int)d.n_fixed >= kMaxFixed) { *err = "a leaf has too many fixed modes"; return false; }
+            uint8_t src;
+            if (v >= m.n_vars) src = (uint8_t)(v - m.n_vars);
+            else {
+                int si = find_pos(p.slices, v);
+                if (si < p.n_inner) { *err = "internal: leaf mode neither kept nor fixed"; return false; }
+                src = (uint8_t)(64 + (si - p.n_inner));
+            }
+            d.fixed_src[d.n_fixed] = src;
+            d.fixed_pos[d.n_fixed] = (uint8_t)j;
+            d.n_fixed++;
+        }
+        for (uint32_t e = 0; e < d.n_elem; e++) {
+            uint32_t s = 0;
+            for (size_t j = 0; j < P.size(); j++) s |= ((e >> j) & 1u) << find_pos(h.modes, P[j]);
+            emap.push_back(s);
+        }
+        for (const cplx &z : h.data) {
+            ldata.push_back((float)z.real());
+            ldata.push_back((float)z.imag());
+        }
+    }
+    (void)n_outer_bits;
+    std::vector<DevStep> ds(p.steps.size());
+    for (size_t s = 0; s < p.steps.size(); s++) {
+        const PStep &st = p.steps[s];
+        DevStep &d = ds[s];
+        std::memset(&d, 0, sizeof(d));
+        const PTensor &A = p.tensors[st.a], &C = p.tensors[st.c];
+        d.rc = (uint8_t)C.modes.size();
+        d.nk_ab = (uint8_t)st.k_ab.size();
+        d.nk_a = (uint8_t)st.k_a.size();
+        d.nk_b = (uint8_t)st.k_b.size();
+        d.c_off = (uint64_t)C.offset;
+        if (A.leaf >= 0) { d.flags |= kStepALeaf; d.a_off = (uint64_t)A.leaf; }
+        else d.a_off = (uint64_t)A.offset;
+        if (!make_runs(C.modes, A.modes, d.runs_a, &d.na_runs, &d.a_cb)) { *err = "address map needs too many runs"; return false; }
+        if (st.b < 0) {
+            d.flags |= kStepUnary;
+        } else {
+            const PTensor &B = p.tensors[st.b];
+            if (B.leaf >= 0) { d.flags |= kStepBLeaf; d.b_off = (uint64_t)B.leaf; }
+            else d.b_off = (uint64_t)B.offset;
+            if (!make_runs(C.modes, B.modes, d.runs_b, &d.nb_runs, &d.b_cb)) { *err = "address map needs too many runs"; return false; }
+        }
+    }
+    DevProgram h;
+    std::memset(&h, 0, sizeof(h));
+    h.magic = kProgramMagic;
+    h.n_steps = (uint32_t)ds.size();
+    h.n_leaves = (uint32_t)dl.size();
+    h.n_leaf_elems = (uint32_t)emap.size();
+    h.arena_elems = (uint64_t)p.arena_elems;
+    const PTensor &F = p.tensors[p.final_tensor];
+    h.final_off = (uint64_t)F.offset;
+    h.n_inner = (uint32_t)p.n_inner;
+    for (int i = 0; i < p.n_inner; i++)
+        if (find_pos(F.modes, p.slices[i]) >= 0) h.final_present |= 1u << i;
+    h.zero_mask = m.zero_mask;
+    h.scalar_re = p.prog_scalar.real();
+    h.scalar_im = p.prog_scalar.imag();
+    h.n_outer = uint64_t(1) << ((int)p.slices.size() - p.n_inner);
+    size_t off = align256(sizeof(DevProgram));
+    h.steps_off = off;
+    off = align256(off + ds.size() * sizeof(DevStep));
+    h.leaves_off = off;
+    off = align256(off + dl.size() * sizeof(DevLeaf));
+    h.elem_map_off = off;
+    off = align256(off + emap.size() * sizeof(uint32_t));
+    h.leaf_data_off = off;
+    off = align256(off + ldata.size() * sizeof(float));
+    h.image_bytes = off;
+    p.image.assign(off, 0);
+    std::memcpy(p.image.data(), &h, sizeof(h));
+    if (!ds.empty()) std::memcpy(p.image.data() + h.steps_off, ds.data(), ds.size() * sizeof(DevStep));
+    if (!dl.empty()) std::memcpy(p.image.data() + h.leaves_off, dl.data(), dl.size() * sizeof(DevLeaf));
+    if (!emap.empty()) std::memcpy(p.image.data() + h.elem_map_off, emap.data(), emap.size() * sizeof(uint32_t));
+    if (!ldata.empty()) std::memcpy(p.image.data() + h.leaf_data_off, ldata.data(), ldata.size() * sizeof(float));
+    return true;
+}
+
+// Builds program, layouts, arena and stats for the current order/slices/n_inner.
+bool build_program(Plan &p, std::string *err) {
+    p.leaves.clear();
+    p.tensors.clear();
+    p.steps.clear();
+    p.final_tensor = -1;
+    ProgramBuilder b(p, p.model);
+    if (!b.run()) { *err = b.err; return false; }
+    p.prog_scalar = p.model.scalar * b.factor;
+    assign_layouts(p);
+    p.arena_elems = allocate_arena(p);
+    program_stats(p);
+    return true;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- entry point
+qvx_status make_plan(const qvx_circuit *c, const int32_t *order, int32_t n_order,
+                     const int32_t *slices, int32_t n_slices, const qvx_plan_opts &opts,
+                     Plan *p, std::string *err) {
+    p->opts = opts;
+    if (!build_model(c, &p->model, err)) return QVX_EINVAL;
+    const Model &m = p->model;
+    const int nv = m.n_vars;
+    Graph g;
+    g.init(nv, m.edges);
+    std::vector<char> none(nv, 0);
+    int w0 = 0;
+    std::vector<int> first;
+    double c0 = best_order(g, none, opts, 1, &first, &w0);
+    p->log2_cost_unsliced = c0 > 0 ? std::log2(c0) : 0;
+    // slices: given, or greedy on the cost under the first order (Section 3.B.2-3)
+    std::vector<char> removed(nv, 0);
+    std::vector<int> sl;
+    if (n_slices >= 0) {
+        if (n_slices > 0 && !slices) { *err = "slices: null list"; return QVX_EINVAL; }
+        for (int i = 0; i < n_slices; i++) {
+            int v = slices[i];
+            if (v < 0 || v >= nv || removed[v]) { *err = "slices: bad or repeated variable id"; return QVX_EINVAL; }
+            removed[v] = 1;
+            sl.push_back(v);
+        }
+    } else {
+        int want = opts.n_slices;
+        const double budget = (double)opts.mem_budget_bytes;
+        for (int it = 0; it < nv; it++) {
+            int wd = 0;
+            double cst = order_cost(g, first, removed, &wd);
+            bool fits = std::ldexp(8.0, wd) <= budget;
+            if (want >= 0 ? (int)sl.size() >= want : fits) break;
+            (void)cst;
+            double best = -1;
+            int bv = -1;
+            for (int v = 0; v < nv; v++) {
+                if (removed[v]) continue;
+                removed[v] = 1;
+                double cv = order_cost(g, first, removed, nullptr);
+                removed[v] = 0;
+                if (best < 0 || cv < best) { best = cv; bv = v; }
+            }
+            if (bv < 0) break;
+            removed[bv] = 1;
+            sl.push_back(bv);
+        }
+    }
+    if (sl.size() > 40) { *err = "more than 40 sliced variables"; return QVX_EUNSUPPORTED; }
+    // the order: given, or re-ordered after removing the sliced vertices (Section 3.B.3)
+    if (n_order > 0) {
+        if (!order) { *err = "order: null list"; return QVX_EINVAL; }
+        std::vector<char> seen(nv, 0);
+        for (int i = 0; i < n_order; i++) {
+            int v = order[i];
+            if (v < 0 || v >= nv || seen[v] || removed[v]) { *err = "order: bad, repeated or sliced variable id"; return QVX_EINVAL; }
+            seen[v] = 1;
+            p->order.push_back(v);
+        }
+        if ((int)p->order.size() + (int)sl.size() != nv) { *err = "order: must hold every variable that is not sliced"; return QVX_EINVAL; }
+        p->log2_cost = std::log2(std::max(1.0, order_cost(g, p->order, removed, &p->width)));
+    } else {
+        double cst = best_order(g, removed, opts, 2, &p->order, &p->width);
+        p->log2_cost = cst > 0 ? std::log2(cst) : 0;
+    }
+    // inner slices: kept open inside one work item. Pick them greedily by the program's
+    // flops, as many as requested or as fit the fused engine's per-warp memory.
+    const int k = (int)sl.size();
+    int inner_want = opts.inner_slices;
+    p->slices = sl;
+    p->n_inner = 0;
+    if (!build_program(*p, err)) return QVX_EUNSUPPORTED;
+    const int64_t fused_limit = int64_t(12) * 1024 / 8;   // complex64 entries per warp
+    std::vector<int> inner, outer = sl;
+    int target = inner_want >= 0 ? std::min(inner_want, k) : k;
+    while ((int)inner.size() < target) {
+        double best = -1;
+        int bi = -1;
+        int64_t best_arena = 0;
+        for (size_t i = 0; i < outer.size(); i++) {
+            std::vector<int> trial = inner;
+            trial.push_back(outer[i]);
+            for (size_t j = 0; j < outer.size(); j++)
+                if (j != i) trial.push_back(outer[j]);
+            p->slices = trial;
+            p->n_inner = (int)inner.size() + 1;
+            if (!build_program(*p, err)) return QVX_EUNSUPPORTED;
+            double per_slice = p->flops_per_item / std::ldexp(1.0, p->n_inner);
+            if (best < 0 || per_slice < best) { best = per_slice; bi = (int)i; best_arena = p->arena_elems; }
+        }
+        if (inner_want < 0 && (best_arena > fused_limit || (int)inner.size() >= 8 ||
+                               k - (int)inner.size() - 1 < 8))
+            break;   // auto: stay within shared memory and keep >= 256 work items
+        inner.push_back(outer[bi]);
+        outer.erase(outer.begin() + bi);
+    }
+    p->slices = inner;
+    p->slices.insert(p->slices.end(), outer.begin(), outer.end());
+    p->n_inner = (int)inner.size();
+    if (!build_program(*p, err)) return QVX_EUNSUPPORTED;
+    if (p->max_rank > std::min(30, opts.max_rank)) {
+        *err = "a tensor of rank " + std::to_string(p->max_rank) + " exceeds max_rank";
+        return QVX_EUNSUPPORTED;
+    }
+    // engine
+    const int64_t arena_bytes = p->arena_elems * 8;
+    p->warps_per_item = std::max(1, std::min(4, opts.warps_per_item));
+    if (opts.engine == QVX_ENGINE_AUTO)
+        p->engine = arena_bytes <= 48 * 1024 ? QVX_ENGINE_FUSED : QVX_ENGINE_STEPWISE;
+    else p->engine = opts.engine;
+    if (p->engine == QVX_ENGINE_FUSED && arena_bytes > 200 * 1024) {
+        *err = "fused engine: arena of " + std::to_string(arena_bytes) + " bytes exceeds shared memory";
+        return QVX_EUNSUPPORTED;
+    }
+    if (!serialize(*p, err)) return QVX_EUNSUPPORTED;
+    return QVX_OK;
+}
+
+}  // namespace qvx

@@ -1,0 +1,102 @@
+"""Host interpreter of a plan's device image, in complex128 (test helper).
+
+It reads the structs of csrc/device_program.h with numpy and executes the pairwise
+program exactly as the kernels define it, so the planner's program (layouts, address
+runs, leaf maps, slice numbering) is checked on the CPU against the oracle. It shares no
+arithmetic with the oracle: the oracle eliminates variables from its own graph.
+"""
+import numpy as np
+
+RUN = np.dtype([("src", "u1"), ("len", "u1"), ("dst", "u1"), ("pad", "u1")])
+STEP = np.dtype([("a_off", "<u8"), ("b_off", "<u8"), ("c_off", "<u8"), ("rc", "u1"), ("nk_ab", "u1"),
+                 ("nk_a", "u1"), ("nk_b", "u1"), ("a_cb", "u1"), ("b_cb", "u1"), ("na_runs", "u1"),
+                 ("nb_runs", "u1"), ("flags", "<u4"), ("pad", "<u4"), ("runs_a", RUN, (12,)),
+                 ("runs_b", RUN, (12,))])
+LEAF = np.dtype([("data_off", "<u4"), ("elem_off", "<u4"), ("n_elem", "<u4"), ("n_fixed", "<u4"),
+                 ("fixed_src", "u1", (12,)), ("fixed_pos", "u1", (12,))])
+PROG = np.dtype([("magic", "<u4"), ("n_steps", "<u4"), ("n_leaves", "<u4"), ("n_leaf_elems", "<u4"),
+                 ("arena_elems", "<u8"), ("final_off", "<u8"), ("n_inner", "<u4"),
+                 ("final_present", "<u4"), ("zero_mask", "<u8"), ("scalar_re", "<f8"),
+                 ("scalar_im", "<f8"), ("n_outer", "<u8"), ("steps_off", "<u8"), ("leaves_off", "<u8"),
+                 ("elem_map_off", "<u8"), ("leaf_data_off", "<u8"), ("image_bytes", "<u8")])
+assert STEP.itemsize == 136 and LEAF.itemsize == 40 and PROG.itemsize == 112
+UNARY, A_LEAF, B_LEAF = 1, 2, 4
+
+
+def _pext(c, runs, n):
+    r = np.zeros_like(c)
+    for i in range(n):
+        src, ln, dst = int(runs[i]["src"]), int(runs[i]["len"]), int(runs[i]["dst"])
+        r |= ((c >> src) & ((1 << ln) - 1)) << dst
+    return r
+
+
+class Program:
+    def __init__(self, image: bytes):
+        buf = np.frombuffer(image, dtype=np.uint8)
+        self.h = np.frombuffer(buf[:PROG.itemsize].tobytes(), dtype=PROG)[0]
+        h = self.h
+        assert int(h["magic"]) == 0x51565831
+        self.steps = np.frombuffer(buf[int(h["steps_off"]):int(h["steps_off"]) + STEP.itemsize * int(h["n_steps"])].tobytes(), dtype=STEP)
+        self.leaves = np.frombuffer(buf[int(h["leaves_off"]):int(h["leaves_off"]) + LEAF.itemsize * int(h["n_leaves"])].tobytes(), dtype=LEAF)
+        self.emap = np.frombuffer(buf[int(h["elem_map_off"]):int(h["elem_map_off"]) + 4 * int(h["n_leaf_elems"])].tobytes(), dtype="<u4").astype(np.int64)
+        ld = np.frombuffer(buf[int(h["leaf_data_off"]):].tobytes(), dtype="<f4")
+        self.leaf_data = ld[0::2].astype(np.float64) + 1j * ld[1::2].astype(np.float64)
+
+    def _leaf_reader(self, li, x, o):
+        L = self.leaves[li]
+        off = int(L["data_off"])
+        for f in range(int(L["n_fixed"])):
+            src = int(L["fixed_src"][f])
+            bit = (x >> src) & 1 if src < 64 else (o >> (src - 64)) & 1
+            off += bit << int(L["fixed_pos"][f])
+        em = self.emap[int(L["elem_off"]):int(L["elem_off"]) + int(L["n_elem"])]
+        return lambda idx: self.leaf_data[off + em[idx]]
+
+    def item_terms(self, x: int, o: int):
+        """Slice terms of work item (x, o): entry i is slice (o << n_inner) | i."""
+        h = self.h
+        arena = np.zeros(max(int(h["arena_elems"]), 4), dtype=np.complex128)
+        for st in self.steps:
+            rc = int(st["rc"])
+            c = np.arange(1 << rc, dtype=np.int64)
+            flags = int(st["flags"])
+            def operand(is_leaf, ref):
+                if is_leaf:
+                    return self._leaf_reader(int(ref), x, o)
+                base = int(ref)
+                return lambda idx: arena[base + idx]
+            A = operand(flags & A_LEAF, st["a_off"])
+            unary = flags & UNARY
+            B = None if unary else operand(flags & B_LEAF, st["b_off"])
+            ia = _pext(c, st["runs_a"], int(st["na_runs"]))
+            ib = None if unary else _pext(c, st["runs_b"], int(st["nb_runs"]))
+            nab, na, nb = int(st["nk_ab"]), int(st["nk_a"]), int(st["nk_b"])
+            acc = np.zeros(1 << rc, dtype=np.complex128)
+            for k in range(1 << (nab + na + nb)):
+                ka = k & ((1 << (nab + na)) - 1)
+                a = A(ia + (ka << int(st["a_cb"])))
+                if unary:
+                    acc += a
+                else:
+                    kb = (k & ((1 << nab) - 1)) | ((k >> (nab + na)) << nab)
+                    acc += a * B(ib + (kb << int(st["b_cb"])))
+            arena[int(st["c_off"]):int(st["c_off"]) + (1 << rc)] = acc
+        n_in = int(h["n_inner"])
+        present = int(h["final_present"])
+        fin = arena[int(h["final_off"]):]
+        scalar = complex(float(h["scalar_re"]), float(h["scalar_im"]))
+        zero = (x & int(h["zero_mask"])) != 0
+        out = np.zeros(1 << n_in, dtype=np.complex128)
+        for i in range(1 << n_in):
+            fi, bit = 0, 0
+            for j in range(n_in):
+                if (present >> j) & 1:
+                    fi |= ((i >> j) & 1) << bit
+                    bit += 1
+            out[i] = 0 if zero else scalar * fin[fi]
+        return out
+
+    def slice_terms(self, x: int):
+        n_out = int(self.h["n_outer"])
+        return np.concatenate([self.item_terms(x, o) for o in range(n_out)])

@@ -1,0 +1,131 @@
+"""GPU parity: amplitudes and slice terms from libqvx.so against the FP64 oracle.
+
+Tolerance (stated for the FP32 path): |d alpha| <= 1e-5 * 2^{-N/2}. Slice terms carry
+the per-term bound of the same size.
+"""
+import random
+
+import numpy as np
+import pytest
+
+import circuitgen as cg
+from oracle import statevector as SV
+from oracle import ve as VE
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+q = pytest.importorskip("paper_1805_01450_gb300")
+
+
+def tol(n):
+    return 1e-5 * 2.0 ** (-n / 2)
+
+
+def _amps(plan, xs):
+    a = plan.amplitude(xs)
+    return a.cpu().numpy()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    q.lib()
+
+
+@pytest.mark.parametrize("engine", ["fused", "stepwise"])
+def test_worked_example_all_bitstrings(engine):
+    c = cg.worked_example()
+    psi = SV.final_state(c)
+    p = q.Plan(c, engine=engine)
+    got = _amps(p, list(range(16)))
+    assert np.max(np.abs(got - psi)) < tol(4)
+
+
+@pytest.mark.parametrize("engine,wpi", [("fused", 1), ("fused", 2), ("fused", 4), ("stepwise", 1)])
+def test_4x4x10_batch(engine, wpi):
+    c = cg.grid_circuit(4, 4, 10, 1001)
+    psi = SV.final_state(c)
+    xs = [0] + cg.random_bitstrings(16, 200, 1002)
+    p = q.Plan(c, engine=engine, warps_per_item=wpi)
+    got = _amps(p, xs)
+    assert np.max(np.abs(got - psi[xs])) < tol(16)
+
+
+@pytest.mark.parametrize("inner,wpi,engine", [(-1, 1, "fused"), (0, 1, "fused"), (2, 2, "fused"),
+                                              (6, 4, "fused"), (3, 1, "stepwise")])
+def test_6x6x25_k12_full(inner, wpi, engine):
+    c = cg.grid_circuit(6, 6, 25, 2001)
+    x = cg.random_bitstrings(36, 1, 2002)[0]
+    p = q.Plan(c, n_slices=12, inner_slices=inner, warps_per_item=wpi, engine=engine)
+    ref_terms = VE.slice_terms(c, x, p.order, p.slices)
+    ref = VE.exact_sum(ref_terms)
+    got = _amps(p, [x])[0]
+    assert abs(got - ref) < tol(36)
+    terms = p.slice_terms([x]).cpu().numpy()[0]
+    assert terms.shape == (4096,)
+    assert np.max(np.abs(terms - ref_terms)) < tol(36)
+    ws = p._ws_for(1, torch.device("cuda"))
+    p.check_status(ws)
+
+
+def test_6x6x25_ragged_slice_ranges_and_batch():
+    c = cg.grid_circuit(6, 6, 25, 2001)
+    xs = cg.random_bitstrings(36, 5, 77)
+    p = q.Plan(c, n_slices=12, inner_slices=3)
+    refs = [VE.slice_terms(c, x, p.order, p.slices) for x in xs]
+    rng = random.Random(3)
+    for _ in range(4):
+        s0 = rng.randrange(4096)
+        cnt = rng.randrange(1, 4096 - s0 + 1)
+        got = p.amplitude(xs, slice_begin=s0, slice_count=cnt).cpu().numpy()
+        for g, r in zip(got, refs):
+            assert abs(g - VE.exact_sum(r[s0:s0 + cnt])) < tol(36)
+    got = p.amplitude(xs, slice_begin=100, slice_count=0).cpu().numpy()
+    assert np.all(got == 0)
+
+
+def test_rotation_circuit_stepwise_and_fused():
+    c = cg.rotation_circuit(3, 3, 6, 4001)
+    psi = SV.final_state(c)
+    xs = cg.random_bitstrings(9, 40, 5)
+    for engine in ("fused", "stepwise"):
+        p = q.Plan(c, n_slices=3, engine=engine)
+        assert np.max(np.abs(_amps(p, xs) - psi[xs])) < tol(9)
+
+
+def test_5x5x20_stepwise_unsliced():
+    c = cg.grid_circuit(5, 5, 20, 4001)
+    xs = cg.random_bitstrings(25, 8, 6)
+    p = q.Plan(c, n_slices=0, engine="stepwise")
+    got = _amps(p, xs)
+    for g, x in zip(got, xs):
+        assert abs(g - VE.ve_amplitude(c, x, p.order)) < tol(25)
+
+
+def test_degenerate_circuits():
+    empty = cg.Circuit(n_qubits=3, gates=[])
+    p = q.Plan(empty)
+    assert np.allclose(_amps(p, [0, 1, 5]), [1, 0, 0])
+    partial = cg.Circuit(n_qubits=3, gates=[cg.Gate(cg.H, 0), cg.Gate(cg.T, 1), cg.Gate(cg.CZ, 0, 1)])
+    psi = SV.final_state(partial)
+    assert np.max(np.abs(_amps(q.Plan(partial), list(range(8))) - psi)) < 1e-7
+    hh = cg.Circuit(n_qubits=2, gates=[cg.Gate(cg.H, 0), cg.Gate(cg.H, 1)])
+    assert np.allclose(_amps(q.Plan(hh), [0, 1, 2, 3]), [0.5] * 4)
+
+
+def test_empty_batch_and_bad_bitstring():
+    p = q.Plan(cg.grid_circuit(3, 3, 8, 1))
+    assert p.amplitude(torch.zeros(0, dtype=torch.int64, device="cuda")).numel() == 0
+    with pytest.raises(q.QvxError):
+        p.amplitude([1 << 9])
+
+
+def test_repeated_calls_reuse_workspace():
+    c = cg.grid_circuit(6, 6, 25, 2001)
+    x = cg.random_bitstrings(36, 1, 2002)[0]
+    p = q.Plan(c, n_slices=12)
+    first = _amps(p, [x])[0]
+    for _ in range(5):
+        assert _amps(p, [x])[0] == first

@@ -1,0 +1,125 @@
+"""Host-side checks of libqvx.so: exports, graph, planner, and the program run on the CPU."""
+import os
+import random
+import re
+
+import numpy as np
+import pytest
+
+import circuitgen as cg
+import paper_1805_01450_gb300 as q
+from oracle import graph as GR
+from oracle import statevector as SV
+from oracle import ve as VE
+
+from _program_exec import Program
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_library_exports_every_declared_symbol():
+    header = open(os.path.join(ROOT, "include", "qvx.h")).read()
+    declared = set(re.findall(r"\b(qvx_[a-z_0-9]+)\s*\(", header))
+    L = q.lib()
+    for name in declared:
+        assert hasattr(L, name), name
+    assert declared == set(q.EXPORTED)
+
+
+@pytest.mark.parametrize("maker", [cg.worked_example, lambda: cg.grid_circuit(4, 4, 10, 1001),
+                                   lambda: cg.grid_circuit(6, 6, 25, 2001),
+                                   lambda: cg.rotation_circuit(3, 3, 4, 5)])
+def test_graph_export_matches_oracle(maker):
+    c = maker()
+    vq, vo, ed = q.graph_export(c)
+    m = GR.build(c)
+    assert list(zip(vq, vo)) == m.variables
+    assert sorted(ed) == sorted(GR.edges(m))
+
+
+def test_plan_order_cost_matches_oracle_graph_ops():
+    # the plan's reported cost is sum 2^deg over its order after fixing its slices
+    c = cg.grid_circuit(6, 6, 25, 2001)
+    p = q.Plan(c, n_slices=6)
+    m = GR.build(c)
+    adj = GR.adjacency(len(m.variables), GR.edges(m))
+    for v in p.slices:
+        adj = GR.fix_vertex(adj, v)
+    cost, _ = GR.order_cost(adj, p.order)
+    assert abs(np.log2(cost) - p.info["log2_cost"]) < 1e-9
+    assert sorted(p.order + p.slices) == list(range(len(m.variables)))
+
+
+def test_greedy_slices_follow_section_3b2():
+    # each greedy pick lowers the cost under the first order; the final cost is far below
+    # the unsliced one
+    c = cg.grid_circuit(6, 6, 25, 2001)
+    p0 = q.Plan(c, n_slices=0)
+    p12 = q.Plan(c, n_slices=12)
+    assert p12.info["log2_cost"] < p0.info["log2_cost"] - 5
+    assert len(set(p12.slices)) == 12
+
+
+def test_user_order_and_slices_are_used():
+    c = cg.grid_circuit(4, 4, 10, 1001)
+    nv = len(GR.build(c).variables)
+    sl = [3, 7]
+    order = [v for v in range(nv) if v not in sl][::-1]
+    p = q.Plan(c, order=order, slices=sl)
+    assert p.order == order and sorted(p.slices) == sorted(sl)
+
+
+@pytest.mark.parametrize("bad", [dict(order=[0, 0]), dict(slices=[999]), dict(slices=[1, 1])])
+def test_invalid_plan_arguments(bad):
+    with pytest.raises(q.QvxError) as e:
+        q.Plan(cg.grid_circuit(4, 4, 10, 1001), **bad)
+    assert e.value.status == q.QVX_EINVAL
+
+
+def test_invalid_circuit():
+    c = cg.Circuit(n_qubits=2, gates=[cg.Gate(cg.CZ, 0, 0)])
+    with pytest.raises(q.QvxError):
+        q.Plan(c)
+    c = cg.Circuit(n_qubits=2, gates=[cg.Gate(99, 0)])
+    with pytest.raises(q.QvxError):
+        q.Plan(c)
+
+
+CASES = [
+    ("worked", cg.worked_example, dict()),
+    ("4x4x10", lambda: cg.grid_circuit(4, 4, 10, 1001), dict()),
+    ("4x4x10-k3", lambda: cg.grid_circuit(4, 4, 10, 1001), dict(n_slices=3, inner_slices=1)),
+    ("3x4x16-k4", lambda: cg.grid_circuit(3, 4, 16, 2), dict(n_slices=4, inner_slices=2)),
+    ("rot2x3", lambda: cg.rotation_circuit(2, 3, 4, 12), dict(n_slices=2, inner_slices=0)),
+    ("empty", lambda: cg.Circuit(n_qubits=3, gates=[]), dict()),
+    ("untouched", lambda: cg.Circuit(n_qubits=3, gates=[cg.Gate(cg.H, 0), cg.Gate(cg.T, 1),
+                                                        cg.Gate(cg.CZ, 0, 1)]), dict()),
+]
+
+
+@pytest.mark.parametrize("name,maker,kw", CASES, ids=[c[0] for c in CASES])
+def test_program_on_host_matches_oracle(name, maker, kw):
+    c = maker()
+    p = q.Plan(c, **kw)
+    prog = Program(p.image())
+    psi = SV.final_state(c)
+    xs = [0, (1 << c.n_qubits) - 1] + cg.random_bitstrings(c.n_qubits, 4, 9)
+    for x in xs:
+        terms = prog.slice_terms(x)
+        assert abs(terms.sum() - psi[x]) < 1e-6 * 2 ** (-c.n_qubits / 2) + 1e-7
+        if p.slices:
+            ref = VE.slice_terms(c, x, p.order, p.slices)
+            assert np.max(np.abs(terms - ref)) < 1e-6 * 2 ** (-c.n_qubits / 2)
+
+
+def test_program_slice_terms_6x6_sample():
+    c = cg.grid_circuit(6, 6, 25, 2001)
+    p = q.Plan(c, n_slices=12, inner_slices=3)
+    prog = Program(p.image())
+    x = cg.random_bitstrings(36, 1, 2002)[0]
+    rng = random.Random(0)
+    for o in rng.sample(range(int(prog.h["n_outer"])), 3):
+        got = prog.item_terms(x, o)
+        ids = [(o << 3) | i for i in range(8)]
+        ref = VE.slice_terms(c, x, p.order, p.slices, slice_ids=ids)
+        assert np.max(np.abs(got - ref)) < 1e-6 * 2 ** -18

@@ -46,8 +46,8 @@ def parse():
     ap.add_argument("--impl", choices=["qvx", "reference"], default="qvx")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--batch", type=int, default=1, help="bitstrings per step")
-    ap.add_argument("--inner-slices", type=int, default=-1)
-    ap.add_argument("--warps-per-item", type=int, default=1)
+    ap.add_argument("--inner-slices", type=int, default=None, help="fix the plan variant instead of autotuning")
+    ap.add_argument("--warps-per-item", type=int, default=None)
     ap.add_argument("--engine", default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
@@ -138,32 +138,45 @@ def cpu_baseline(circ, bits, k, plan_order, plan_slices, budget_s):
                       f"complex128 bucket elimination in the plan's order, OpenMP over slices"}
 
 
+REFERENCE_SLICES_PER_STEP = 256
+
+
 def run_reference(args, rank, world):
+    """The oracle as the reference arm: each step evaluates a bounded sample of one
+    amplitude (REFERENCE_SLICES_PER_STEP of its slice terms, cycling through them), so the
+    rate in amplitudes/s is slice terms per second / slice terms per amplitude."""
     if rank != 0:
         return
+    import numpy as np
     from oracle import ve as VE
     circ, bits, k = workload(args.workload, args.batch, 0)
     import paper_1805_01450_gb300 as q
     plan = q.Plan(circ, n_slices=k)   # host planner only: the oracle takes its order and slices
     threads = os.cpu_count() or 1
     VE.build_library()
-    for i in range(args.warmup):
-        VE.ve_amplitude(circ, bits[i % len(bits)], plan.order, plan.slices, threads=threads)
-    t0 = time.perf_counter()
-    n = 0
-    for i in range(args.steps):
+    total = 1 << k
+    per = min(REFERENCE_SLICES_PER_STEP, total)
+
+    def one(i):
+        ids = (np.arange(per, dtype=np.int64) + i * per) % total
         for x in bits:
-            VE.ve_amplitude(circ, x, plan.order, plan.slices, threads=threads)
-            n += 1
+            VE.slice_terms(circ, x, plan.order, plan.slices, slice_ids=ids, threads=threads)
+
+    for i in range(args.warmup):
+        one(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        one(i)
     dt = time.perf_counter() - t0
-    v = n / dt
+    v = args.steps * per * len(bits) / total / dt
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "amplitudes/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
            "data": "synthetic", "config": {"workload": args.workload, "bitstrings_per_step": args.batch,
                                            "sliced": k},
            "cpu_baseline": {"value": v, "unit": "amplitudes/s", "cores": threads, "kind": "oracle",
-                            "sample": f"{n} whole amplitudes, {args.steps} steps"},
+                            "sample": f"{per} of the {total} slice terms of one amplitude per step, "
+                                      f"{args.steps} steps, complex128 bucket elimination"},
            "e2e": {"value": v, "unit": "amplitudes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -189,11 +202,16 @@ def main():
             dist.barrier()
 
     circ, bits_host, k = workload(args.workload, args.batch, rank)
-    plan = q.Plan(circ, n_slices=k, inner_slices=args.inner_slices, warps_per_item=args.warps_per_item,
-                  engine=args.engine)
+    dev = torch.device("cuda", local)
+    tuning = None
+    if args.inner_slices is None and args.warps_per_item is None and args.engine == "auto":
+        from paper_1805_01450_gb300.autotune import autotune
+        plan, tuning = autotune(circ, bits_host, n_slices=k, device=dev)
+    else:
+        plan = q.Plan(circ, n_slices=k, inner_slices=-1 if args.inner_slices is None else args.inner_slices,
+                      warps_per_item=args.warps_per_item or 1, engine=args.engine)
     info = plan.info
     B = len(bits_host)
-    dev = torch.device("cuda", local)
     bits = plan._bits(bits_host, dev)
     ws = plan.workspace(B, dev)
     out = torch.empty(2 * B, dtype=torch.float64, device=dev)
@@ -283,6 +301,7 @@ def main():
         "e2e": {"value": e2e, "unit": "amplitudes/s", "h2d_bytes_per_step": 8 * B, "d2h_bytes_per_step": 16 * B},
         "gpu_launches": K * launches_per_step,
         "clocks": clocks.summary(),
+        "autotune": None if tuning is None else [list(t) for t in tuning],
         "plan": {"n_vars": info["n_vars"], "n_steps": info["n_steps"], "log2_cost": info["log2_cost"],
                  "log2_cost_unsliced": info["log2_cost_unsliced"], "max_rank": info["max_rank"],
                  "arena_bytes": info["arena_bytes"]},

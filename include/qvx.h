@@ -91,6 +91,10 @@ typedef struct {
     int32_t inner_slices;      /* sliced variables kept open inside one work item; -1 auto */
     int32_t max_rank;          /* largest tensor rank a plan may create (<= 30) */
     int32_t warps_per_item;    /* fused engine: warps sharing one work item (1, 2 or 4) */
+    int32_t host_merge_rank;   /* two leaves whose product has at most this many modes (modes
+                                  fixed per work item included) are contracted on the host in
+                                  FP64 at plan time; 0 keeps every contraction on the device */
+    int32_t reserved;
 } qvx_plan_opts;
 
 typedef struct {
@@ -108,7 +112,7 @@ typedef struct {
 typedef struct qvx_plan qvx_plan;
 
 /* Fills *opts with defaults: n_slices -1, 8 restarts, seed 1, 1 GiB budget, auto engine,
- * auto inner slices, max_rank 30, 1 warp per item. */
+ * auto inner slices, max_rank 30, 1 warp per item, host_merge_rank 8. */
 void qvx_plan_opts_default(qvx_plan_opts *opts);
 
 /* The graphical model of Section 3.A with output and input vertices removed.

@@ -42,7 +42,8 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("n_slices", ctypes.c_int32), ("order_restarts", ctypes.c_int32),
                 ("order_seed", ctypes.c_uint64), ("mem_budget_bytes", ctypes.c_int64),
                 ("engine", ctypes.c_int32), ("inner_slices", ctypes.c_int32),
-                ("max_rank", ctypes.c_int32), ("warps_per_item", ctypes.c_int32)]
+                ("max_rank", ctypes.c_int32), ("warps_per_item", ctypes.c_int32),
+                ("host_merge_rank", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -143,7 +144,7 @@ class Plan:
 
     def __init__(self, circ, order=None, slices=None, n_slices=-1, engine="auto", inner_slices=-1,
                  order_restarts=8, order_seed=1, mem_budget_bytes=1 << 30, max_rank=30,
-                 warps_per_item=1):
+                 warps_per_item=1, host_merge_rank=8):
         L = lib()
         opts = PlanOpts()
         L.qvx_plan_opts_default(ctypes.byref(opts))
@@ -155,6 +156,7 @@ class Plan:
         opts.inner_slices = inner_slices
         opts.max_rank = max_rank
         opts.warps_per_item = warps_per_item
+        opts.host_merge_rank = host_merge_rank
         cs = circuit_struct(circ)
         o_arr = (ctypes.c_int32 * max(len(order or []), 1))(*(order or []))
         s_arr = (ctypes.c_int32 * max(len(slices or []), 1))(*(slices or []))

@@ -13,8 +13,8 @@ struct qvx_plan {
     qvx::Plan p;
     // fused-engine launch shape, cached for the device it was computed on
     int launch_device = -1;
-    int sms = 0, ctas_per_sm = 0, items_per_cta = 0;
-    size_t smem = 0;
+    int sms = 0;
+    int ctas_per_sm[9] = {0};   // by work items per CTA
 };
 
 namespace {
@@ -111,28 +111,43 @@ qvx_status run_items(qvx_plan *plan, const uint64_t *bits, int64_t batch, int64_
     cudaError_t e;
     if (p.engine == QVX_ENGINE_FUSED) {
         const int wpi = p.warps_per_item;
+        const qvx::DevProgram *h = reinterpret_cast<const qvx::DevProgram *>(p.image.data());
+        auto r16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+        const size_t kBudget = 220u << 10;   // dynamic shared memory per CTA
+        const size_t group = r16((size_t)h->n_leaves * 4) + (size_t)a.arena_elems * 8;
+        // fused steps and their tables form one contiguous block of the image
+        size_t steps_b = r16((size_t)(h->fused_tab_off - h->fused_steps_off) + (size_t)h->n_tab_entries * 4);
+        size_t leaf_b = r16((size_t)h->n_leaf_entries * 8);
+        // stage the program in shared memory while it leaves room for at least two groups
+        if (steps_b + leaf_b + 2 * group > kBudget) leaf_b = 0;
+        if (steps_b + leaf_b + 2 * group > kBudget) steps_b = 0;
+        if (steps_b + leaf_b + group > kBudget) return fail(QVX_EUNSUPPORTED, "fused kernel: arena exceeds shared memory");
+        const size_t shared = steps_b + leaf_b;
+        const int max_ipc = (int)std::max<size_t>(1, std::min<size_t>(8 / wpi, (kBudget - shared) / group));
+        a.smem_steps_bytes = (uint32_t)steps_b;
+        a.smem_leaf_bytes = (uint32_t)leaf_b;
+        a.leaf_table_bytes = (uint32_t)r16((size_t)h->n_leaves * 4);
+        a.group_bytes = (uint32_t)group;
         int dev = -1;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
         if (dev != plan->launch_device) {
             DeviceCaps caps;
             qvx_status s = device_caps(&caps);
             if (s != QVX_OK) return s;
-            // up to 8 warps per CTA, as many work items as fit in 200 KiB of shared memory
-            const size_t arena = (size_t)a.arena_elems * 8;
-            const int ipc = (int)std::max<size_t>(1, std::min<size_t>(8 / wpi, (200u << 10) / arena));
-            const size_t smem = (size_t)ipc * arena;
-            if ((e = qvx::fused_prepare(smem)) != cudaSuccess) return cuda_fail(e, "fused kernel attributes");
-            const int per_sm = qvx::fused_blocks_per_sm(32 * wpi * ipc, smem);
-            if (per_sm < 1) return fail(QVX_EUNSUPPORTED, "fused kernel: no CTA fits on an SM");
+            if ((e = qvx::fused_prepare(shared + (size_t)max_ipc * group)) != cudaSuccess)
+                return cuda_fail(e, "fused kernel attributes");
+            for (int ipc = 1; ipc <= 8; ipc++)
+                plan->ctas_per_sm[ipc] =
+                    ipc <= max_ipc ? qvx::fused_blocks_per_sm(32 * wpi * ipc, shared + ipc * group) : 0;
             plan->sms = caps.sms;
-            plan->ctas_per_sm = per_sm;
-            plan->items_per_cta = ipc;
-            plan->smem = smem;
             plan->launch_device = dev;
         }
-        const int64_t ctas_needed = (n_items + plan->items_per_cta - 1) / plan->items_per_cta;
-        const int grid = (int)std::min<int64_t>(ctas_needed, (int64_t)plan->sms * plan->ctas_per_sm);
-        if ((e = qvx::launch_fused(a, wpi, plan->items_per_cta, grid, plan->smem, st)) != cudaSuccess)
+        // spread the items over every SM first, then stack up to 8 warps per CTA
+        const int ipc = (int)std::max<int64_t>(1, std::min<int64_t>(max_ipc, (n_items + plan->sms - 1) / plan->sms));
+        if (plan->ctas_per_sm[ipc] < 1) return fail(QVX_EUNSUPPORTED, "fused kernel: no CTA fits on an SM");
+        const int64_t ctas_needed = (n_items + ipc - 1) / ipc;
+        const int grid = (int)std::min<int64_t>(ctas_needed, (int64_t)plan->sms * plan->ctas_per_sm[ipc]);
+        if ((e = qvx::launch_fused(a, wpi, ipc, grid, shared + (size_t)ipc * group, st)) != cudaSuccess)
             return cuda_fail(e, "fused kernel launch");
         return QVX_OK;
     }
@@ -172,6 +187,7 @@ void qvx_plan_opts_default(qvx_plan_opts *o) {
     o->inner_slices = -1;
     o->max_rank = 30;
     o->warps_per_item = 1;
+    o->host_merge_rank = 8;
 }
 
 qvx_status qvx_graph_export(const qvx_circuit *circuit, int32_t *n_vars, int32_t *var_qubit,
@@ -210,6 +226,8 @@ qvx_status qvx_plan_create(const qvx_circuit *circuit, const int32_t *order, int
     if (n_order < 0) return fail(QVX_EINVAL, "n_order < 0");
     if (o.order_restarts < 1 || o.max_rank < 1 || o.mem_budget_bytes < 64)
         return fail(QVX_EINVAL, "opts: restarts >= 1, max_rank >= 1, budget >= 64 bytes");
+    if (o.host_merge_rank < 0 || o.host_merge_rank > 16)
+        return fail(QVX_EINVAL, "opts: host_merge_rank must be in [0, 16]");
     if (o.warps_per_item != 1 && o.warps_per_item != 2 && o.warps_per_item != 4)
         return fail(QVX_EINVAL, "opts: warps_per_item must be 1, 2 or 4");
     qvx_plan *plan = nullptr;
@@ -241,7 +259,7 @@ qvx_status qvx_plan_get_info(const qvx_plan *plan, qvx_plan_info *info) {
     info->n_sliced = (int32_t)p.slices.size();
     info->n_inner = p.n_inner;
     info->n_steps = (int32_t)p.steps.size();
-    info->n_leaves = (int32_t)p.leaves.size();
+    info->n_leaves = (int32_t)reinterpret_cast<const qvx::DevProgram *>(p.image.data())->n_leaves;
     info->max_rank = p.max_rank;
     info->engine = p.engine;
     info->warps_per_item = p.warps_per_item;

@@ -30,20 +30,33 @@ struct DevStep {
     DevRun runs_b[kMaxRuns];
 };
 
-// A leaf is read in its consumer's layout: entry e of the restricted leaf is stored entry
-// elem_map[elem_off + e] + (sum over fixed modes of value << fixed_pos) after data_off.
+// A leaf is stored with its consumer's modes in the low bits (in the consumer's order)
+// and the modes fixed per work item above them. Entry e of the restricted leaf is stored
+// entry data_off + e + sum over fixed modes f of value_f << fixed_pos[f].
 struct DevLeaf {
     uint32_t data_off;             // first stored entry (complex64 units) in the leaf data
-    uint32_t elem_off;             // first entry of this leaf in the element map
     uint32_t n_elem;               // entries after restriction (2^consumer rank)
     uint32_t n_fixed;              // modes fixed per work item
+    uint32_t pad;
     uint8_t fixed_src[kMaxFixed];  // < 64: bit of the bitstring; >= 64: bit (src-64) of the outer slice number
     uint8_t fixed_pos[kMaxFixed];  // bit position of that mode in the stored leaf
 };
 
+// The fused engine's form of a step: operand offsets and a per-step table holding, for
+// each output entry c, the operands' offsets pext(c) for A (low 16 bits) and B (high 16).
+struct FusedStep {
+    uint32_t a_off, b_off, c_off;  // arena offsets, or leaf indices (flags as in DevStep)
+    uint32_t tab_off;              // first table entry of this step
+    uint32_t flags;
+    uint8_t rc, nk_ab, nk_a, nk_b;
+    uint8_t a_cb, b_cb, pad0, pad1;
+    uint32_t pad2;
+};
+
 struct DevProgram {
     uint32_t magic;
-    uint32_t n_steps, n_leaves, n_leaf_elems;
+    uint32_t n_steps, n_leaves, pad0;
+    uint64_t n_leaf_entries;       // complex64 entries of all stored leaves
     uint64_t arena_elems;          // complex64 entries of one work item's arena
     uint64_t final_off;            // arena offset of the final tensor (over the inner slice modes)
     uint32_t n_inner;              // inner (open) sliced variables
@@ -51,10 +64,19 @@ struct DevProgram {
     uint64_t zero_mask;            // amplitude is 0 when x & zero_mask != 0
     double scalar_re, scalar_im;   // constant prefactor
     uint64_t n_outer;              // work items per bitstring = 2^(sliced - inner)
-    uint64_t steps_off, leaves_off, elem_map_off, leaf_data_off;  // byte offsets
+    uint64_t steps_off, leaves_off, leaf_data_off;  // byte offsets
+    uint64_t fused_steps_off, fused_tab_off;        // byte offsets (0 if the fused form is absent)
+    uint64_t n_tab_entries;
     uint64_t image_bytes;
 };
 
 constexpr uint32_t kProgramMagic = 0x51565831u;  // "QVX1"
 
+}  // namespace qvx
+
+namespace qvx {
+static_assert(sizeof(DevStep) == 136, "DevStep layout");
+static_assert(sizeof(DevLeaf) == 40, "DevLeaf layout");
+static_assert(sizeof(DevProgram) == 136, "DevProgram layout");
+static_assert(sizeof(FusedStep) == 32, "FusedStep layout");
 }  // namespace qvx

@@ -15,41 +15,15 @@ __device__ __forceinline__ uint32_t pext_runs(uint32_t c, const DevRun *runs, in
 }
 
 
-// Offset of the entries of `leaf` fixed by this work item (bitstring x, outer slice o).
-__device__ __forceinline__ uint32_t leaf_fixed_offset(const DevLeaf &L, uint64_t x, uint64_t o) {
+// First stored entry of `leaf` restricted to this work item (bitstring x, outer slice o).
+__device__ __forceinline__ uint32_t leaf_base(const DevLeaf &L, uint64_t x, uint64_t o) {
     uint32_t off = L.data_off;
     for (uint32_t f = 0; f < L.n_fixed; f++) {
-        uint32_t src = L.fixed_src[f];
-        uint64_t bit = src < 64 ? (x >> src) & 1ull : (o >> (src - 64)) & 1ull;
+        const uint32_t src = L.fixed_src[f];
+        const uint64_t bit = src < 64 ? (x >> src) & 1ull : (o >> (src - 64)) & 1ull;
         off += (uint32_t)bit << L.fixed_pos[f];
     }
     return off;
-}
-
-struct Operand {
-    const float2 *base;      // arena tensor, or leaf data shifted by the fixed offset
-    const uint32_t *emap;    // leaf element map, or nullptr for an arena tensor
-};
-
-__device__ __forceinline__ float2 fetch(const Operand &op, uint32_t i) {
-    if (op.emap) return __ldg(op.base + __ldg(op.emap + i));
-    return op.base[i];
-}
-
-__device__ __forceinline__ Operand make_operand(const DevProgram *P, const unsigned char *img,
-                                                bool leaf, uint64_t ref, float2 *arena,
-                                                uint64_t x, uint64_t o) {
-    Operand op;
-    if (leaf) {
-        const DevLeaf *L = reinterpret_cast<const DevLeaf *>(img + P->leaves_off) + ref;
-        const float2 *data = reinterpret_cast<const float2 *>(img + P->leaf_data_off);
-        op.base = data + leaf_fixed_offset(*L, x, o);
-        op.emap = reinterpret_cast<const uint32_t *>(img + P->elem_map_off) + L->elem_off;
-    } else {
-        op.base = arena + ref;
-        op.emap = nullptr;
-    }
-    return op;
 }
 
 __device__ __forceinline__ void cmac(float2 &acc, float2 a, float2 b) {
@@ -60,8 +34,8 @@ __device__ __forceinline__ void cmac(float2 &acc, float2 a, float2 b) {
 }
 
 // One output entry c of step st.
-__device__ __forceinline__ float2 step_entry(const DevStep &st, uint32_t c, const Operand &A,
-                                             const Operand &B, bool unary) {
+__device__ __forceinline__ float2 step_entry(const DevStep &st, uint32_t c, const float2 *A,
+                                             const float2 *B, bool unary) {
     const uint32_t ia = pext_runs(c, st.runs_a, st.na_runs);
     const uint32_t ib = unary ? 0u : pext_runs(c, st.runs_b, st.nb_runs);
     const uint32_t nab = st.nk_ab, na = st.nk_a;
@@ -70,13 +44,13 @@ __device__ __forceinline__ float2 step_entry(const DevStep &st, uint32_t c, cons
     float2 acc = make_float2(0.f, 0.f);
     for (uint32_t k = 0; k < (1u << nk); k++) {
         const uint32_t ka = k & mask_ka;
-        const float2 a = fetch(A, ia + (ka << st.a_cb));
+        const float2 a = A[ia + (ka << st.a_cb)];
         if (unary) {
             acc.x += a.x;
             acc.y += a.y;
         } else {
             const uint32_t kb = (k & mask_ab) | ((k >> (nab + na)) << nab);
-            cmac(acc, a, fetch(B, ib + (kb << st.b_cb)));
+            cmac(acc, a, B[ib + (kb << st.b_cb)]);
         }
     }
     return acc;
@@ -171,32 +145,90 @@ __device__ double2 block_compensated_sum(const double2 *partials, int64_t n) {
 
 // ------------------------------------------------------------------ fused engine
 // Each group of `warps_per_item` warps runs the whole program for one work item
-// (bitstring b, outer slice o) with its arena in shared memory; groups loop over items.
+// (bitstring b, outer slice o); groups loop over items. Shared memory holds, per CTA, the
+// step descriptors and the leaf data (when they fit), and per group the item's leaf base
+// offsets and its tensor arena.
+__device__ __forceinline__ void copy_to_smem(void *dst, const void *src, size_t bytes) {
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+    const uint4 *s = reinterpret_cast<const uint4 *>(src);
+    for (size_t i = threadIdx.x; i < bytes / 16; i += blockDim.x) d[i] = __ldg(s + i);
+}
+
+// One output entry of a fused step: e packs the operands' offsets pext(c).
+__device__ __forceinline__ float2 fused_entry(const FusedStep &st, uint32_t e, const float2 *__restrict__ A,
+                                              const float2 *__restrict__ B, bool unary) {
+    const uint32_t ia = e & 0xffffu, ib = e >> 16;
+    const uint32_t nab = st.nk_ab, na = st.nk_a;
+    const uint32_t nk = nab + na + st.nk_b;
+    const uint32_t mask_ka = (1u << (nab + na)) - 1u, mask_ab = (1u << nab) - 1u;
+    float2 acc = make_float2(0.f, 0.f);
+    if (unary) {
+        for (uint32_t k = 0; k < (1u << nk); k++) {
+            const float2 v = A[ia + (k << st.a_cb)];
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        return acc;
+    }
+#pragma unroll 2
+    for (uint32_t k = 0; k < (1u << nk); k++) {
+        const uint32_t ka = k & mask_ka;
+        const uint32_t kb = (k & mask_ab) | ((k >> (nab + na)) << nab);
+        cmac(acc, A[ia + (ka << st.a_cb)], B[ib + (kb << st.b_cb)]);
+    }
+    return acc;
+}
+
 __global__ void __launch_bounds__(256) fused_program_kernel(LaunchArgs a, int warps_per_item) {
-    extern __shared__ float2 smem[];
+    extern __shared__ __align__(16) unsigned char smem[];
     const unsigned char *img = a.image;
     const DevProgram *P = reinterpret_cast<const DevProgram *>(img);
-    const DevStep *steps = reinterpret_cast<const DevStep *>(img + P->steps_off);
+    const DevLeaf *leaves = reinterpret_cast<const DevLeaf *>(img + P->leaves_off);
+    const FusedStep *steps = reinterpret_cast<const FusedStep *>(img + P->fused_steps_off);
+    const uint32_t *tabs = reinterpret_cast<const uint32_t *>(img + P->fused_tab_off);
+    const float2 *ldata = reinterpret_cast<const float2 *>(img + P->leaf_data_off);
+    unsigned char *cur = smem;
+    if (a.smem_steps_bytes) {
+        // fused steps and their tables are contiguous in the image
+        copy_to_smem(cur, steps, a.smem_steps_bytes);
+        const size_t tab_rel = P->fused_tab_off - P->fused_steps_off;
+        steps = reinterpret_cast<const FusedStep *>(cur);
+        tabs = reinterpret_cast<const uint32_t *>(cur + tab_rel);
+        cur += a.smem_steps_bytes;
+    }
+    if (a.smem_leaf_bytes) {
+        copy_to_smem(cur, ldata, a.smem_leaf_bytes);
+        ldata = reinterpret_cast<const float2 *>(cur);
+        cur += a.smem_leaf_bytes;
+    }
+    __syncthreads();
     const int lanes = 32 * warps_per_item;
     const int group = threadIdx.x / lanes;
     const int lane = threadIdx.x % lanes;
     const int groups = blockDim.x / lanes;
-    float2 *arena = smem + (size_t)group * a.arena_elems;
+    unsigned char *mine = cur + (size_t)group * a.group_bytes;
+    uint32_t *lbase = reinterpret_cast<uint32_t *>(mine);
+    float2 *arena = reinterpret_cast<float2 *>(mine + a.leaf_table_bytes);
     const int64_t n_items = a.batch * a.o_count;
     const unsigned bar_id = 1 + group;
+    const uint32_t n_leaves = P->n_leaves;
     for (int64_t item = (int64_t)blockIdx.x * groups + group; item < n_items;
          item += (int64_t)gridDim.x * groups) {
         const int64_t b = item / a.o_count;
         const uint64_t o = (uint64_t)(a.o_begin + item % a.o_count);
         const uint64_t x = a.bitstrings[b];
+        for (uint32_t l = lane; l < n_leaves; l += lanes) lbase[l] = leaf_base(leaves[l], x, o);
+        if (warps_per_item == 1) __syncwarp();
+        else asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(lanes));
         for (uint32_t s = 0; s < a.n_steps; s++) {
-            const DevStep &st = steps[s];
-            const bool unary = st.flags & kStepUnary;
-            const Operand A = make_operand(P, img, st.flags & kStepALeaf, st.a_off, arena, x, o);
-            Operand B = A;
-            if (!unary) B = make_operand(P, img, st.flags & kStepBLeaf, st.b_off, arena, x, o);
+            const FusedStep st = steps[s];
+            const uint32_t flags = st.flags;
+            const bool unary = flags & kStepUnary;
+            const float2 *A = (flags & kStepALeaf) ? ldata + lbase[st.a_off] : arena + st.a_off;
+            const float2 *B = unary ? A : ((flags & kStepBLeaf) ? ldata + lbase[st.b_off] : arena + st.b_off);
             float2 *C = arena + st.c_off;
-            for (uint32_t c = lane; c < (1u << st.rc); c += lanes) C[c] = step_entry(st, c, A, B, unary);
+            const uint32_t *tab = tabs + st.tab_off;
+            for (uint32_t c = lane; c < (1u << st.rc); c += lanes) C[c] = fused_entry(st, tab[c], A, B, unary);
             if (warps_per_item == 1) __syncwarp();
             else asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(lanes));
         }
@@ -243,9 +275,11 @@ __global__ void step_kernel(LaunchArgs a, uint32_t s_idx, int64_t item_begin, in
     const uint64_t x = a.bitstrings[b];
     float2 *arena = arenas + (uint64_t)il * a.arena_elems;
     const bool unary = st.flags & kStepUnary;
-    const Operand A = make_operand(P, img, st.flags & kStepALeaf, st.a_off, arena, x, o);
-    Operand B = A;
-    if (!unary) B = make_operand(P, img, st.flags & kStepBLeaf, st.b_off, arena, x, o);
+    const DevLeaf *leaves = reinterpret_cast<const DevLeaf *>(img + P->leaves_off);
+    const float2 *ldata = reinterpret_cast<const float2 *>(img + P->leaf_data_off);
+    const float2 *A = (st.flags & kStepALeaf) ? ldata + leaf_base(leaves[st.a_off], x, o) : arena + st.a_off;
+    const float2 *B = unary ? A
+                            : ((st.flags & kStepBLeaf) ? ldata + leaf_base(leaves[st.b_off], x, o) : arena + st.b_off);
     arena[st.c_off + c] = step_entry(st, c, A, B, unary);
 }
 

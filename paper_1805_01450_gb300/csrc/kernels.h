@@ -19,6 +19,11 @@ struct LaunchArgs {
     unsigned int *status;           // device status word
     unsigned int *counter;          // CTAs finished (fused engine's final sum); zero between calls
     double *amps;                   // optional: 2 * batch FP64 amplitudes written by the fused engine
+    // fused engine shared-memory layout: [steps][leaf data][per group: leaf table, arena]
+    uint32_t smem_steps_bytes;      // 0: steps are read from global memory
+    uint32_t smem_leaf_bytes;       // 0: leaf data is read from global memory
+    uint32_t leaf_table_bytes;      // per group, 16-byte multiple
+    uint32_t group_bytes;           // per group: leaf table + arena
 };
 
 // Fused engine: one warp group per work item, every tensor in shared memory. When

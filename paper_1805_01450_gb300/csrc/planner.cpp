@@ -352,6 +352,28 @@ double best_order(const Graph &g, const std::vector<char> &removed, const qvx_pl
 // ---------------------------------------------------------------- program construction
 namespace {
 
+constexpr int kMergedOnHost = -2;     // consumer id of a leaf folded into a bigger leaf
+
+// out[R] = sum over the `dead` variables of A * B, in FP64 (A, B, out over their modes).
+HostTensor host_contract(const HostTensor &A, const HostTensor &B, const std::vector<int> &R,
+                         const std::vector<int> &dead) {
+    HostTensor out;
+    out.modes = R;
+    out.data.assign(size_t(1) << R.size(), 0.0);
+    std::vector<int> all = R;
+    all.insert(all.end(), dead.begin(), dead.end());
+    std::vector<int> pa(A.modes.size()), pb(B.modes.size());
+    for (size_t j = 0; j < A.modes.size(); j++) pa[j] = find_pos(all, A.modes[j]);
+    for (size_t j = 0; j < B.modes.size(); j++) pb[j] = find_pos(all, B.modes[j]);
+    for (size_t full = 0; full < (size_t(1) << all.size()); full++) {
+        size_t ia = 0, ib = 0;
+        for (size_t j = 0; j < pa.size(); j++) ia |= ((full >> pa[j]) & 1u) << j;
+        for (size_t j = 0; j < pb.size(); j++) ib |= ((full >> pb[j]) & 1u) << j;
+        out.data[full & ((size_t(1) << R.size()) - 1)] += A.data[ia] * B.data[ib];
+    }
+    return out;
+}
+
 struct ProgramBuilder {
     Plan &p;
     const Model &m;
@@ -426,6 +448,31 @@ struct ProgramBuilder {
         for (int v : s.k_ab) summed[v] = 1;
         for (int v : s.k_a) summed[v] = 1;
         for (int v : s.k_b) summed[v] = 1;
+        const int la = p.tensors[a].leaf, lb = p.tensors[b].leaf;
+        if (la >= 0 && lb >= 0) {
+            // two leaves: contract them here, in FP64, when the result stays small; the
+            // result keeps the modes fixed per work item, so it serves every item
+            std::vector<int> dead = s.k_ab;
+            dead.insert(dead.end(), s.k_a.begin(), s.k_a.end());
+            dead.insert(dead.end(), s.k_b.begin(), s.k_b.end());
+            const HostTensor &LA = p.leaves[la], &LB = p.leaves[lb];
+            std::vector<int> R;
+            for (int v : LA.modes)
+                if (find_pos(dead, v) < 0) R.push_back(v);
+            for (int v : LB.modes)
+                if (find_pos(dead, v) < 0 && find_pos(R, v) < 0) R.push_back(v);
+            if ((int)R.size() <= p.opts.host_merge_rank) {
+                p.leaves.push_back(host_contract(LA, LB, R, dead));
+                int c = new_tensor(C);
+                p.tensors[c].leaf = (int)p.leaves.size() - 1;
+                p.tensors[a].consumer = kMergedOnHost;
+                p.tensors[b].consumer = kMergedOnHost;
+                pool.erase(std::find(pool.begin(), pool.end(), a));
+                pool.erase(std::find(pool.begin(), pool.end(), b));
+                pool.push_back(c);
+                return c;
+            }
+        }
         int c = new_tensor(C);
         s.c = c;
         int sid = (int)p.steps.size();
@@ -636,21 +683,24 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 bool serialize(Plan &p, std::string *err) {
     const Model &m = p.model;
     // leaf element maps and stored data
-    std::vector<DevLeaf> dl(p.leaves.size());
-    std::vector<uint32_t> emap;
-    std::vector<float> ldata;
-    std::vector<int> leaf_tensor(p.leaves.size(), -1);
+    // only leaves that a step reads are stored; dev_leaf maps leaf index -> device index
+    std::vector<int> leaf_tensor(p.leaves.size(), -1), dev_leaf(p.leaves.size(), -1), live;
     for (size_t t = 0; t < p.tensors.size(); t++)
-        if (p.tensors[t].leaf >= 0) leaf_tensor[p.tensors[t].leaf] = (int)t;
-    const int n_outer_bits = (int)p.slices.size() - p.n_inner;
-    for (size_t l = 0; l < p.leaves.size(); l++) {
+        if (p.tensors[t].leaf >= 0 && p.tensors[t].consumer >= 0) leaf_tensor[p.tensors[t].leaf] = (int)t;
+    for (size_t l = 0; l < p.leaves.size(); l++)
+        if (leaf_tensor[l] >= 0) { dev_leaf[l] = (int)live.size(); live.push_back((int)l); }
+    std::vector<DevLeaf> dl(live.size());
+    std::vector<float> ldata;
+    for (size_t di = 0; di < live.size(); di++) {
+        const int l = live[di];
         const HostTensor &h = p.leaves[l];
         const std::vector<int> &P = p.tensors[leaf_tensor[l]].modes;
-        DevLeaf &d = dl[l];
+        DevLeaf &d = dl[di];
         std::memset(&d, 0, sizeof(d));
         d.data_off = (uint32_t)(ldata.size() / 2);
-        d.elem_off = (uint32_t)emap.size();
         d.n_elem = 1u << P.size();
+        // stored order: the consumer's modes, then the fixed modes
+        std::vector<int> stored = P;
         for (size_t j = 0; j < h.modes.size(); j++) {
             int v = h.modes[j];
             if (find_pos(P, v) >= 0) continue;
@@ -663,20 +713,19 @@ bool serialize(Plan &p, std::string *err) {
                 src = (uint8_t)(64 + (si - p.n_inner));
             }
             d.fixed_src[d.n_fixed] = src;
-            d.fixed_pos[d.n_fixed] = (uint8_t)j;
+            d.fixed_pos[d.n_fixed] = (uint8_t)stored.size();
             d.n_fixed++;
+            stored.push_back(v);
         }
-        for (uint32_t e = 0; e < d.n_elem; e++) {
-            uint32_t s = 0;
-            for (size_t j = 0; j < P.size(); j++) s |= ((e >> j) & 1u) << find_pos(h.modes, P[j]);
-            emap.push_back(s);
-        }
-        for (const cplx &z : h.data) {
-            ldata.push_back((float)z.real());
-            ldata.push_back((float)z.imag());
+        std::vector<int> pos(stored.size());
+        for (size_t j = 0; j < stored.size(); j++) pos[j] = find_pos(h.modes, stored[j]);
+        for (size_t e = 0; e < (size_t(1) << stored.size()); e++) {
+            size_t src = 0;
+            for (size_t j = 0; j < stored.size(); j++) src |= ((e >> j) & 1u) << pos[j];
+            ldata.push_back((float)h.data[src].real());
+            ldata.push_back((float)h.data[src].imag());
         }
     }
-    (void)n_outer_bits;
     std::vector<DevStep> ds(p.steps.size());
     for (size_t s = 0; s < p.steps.size(); s++) {
         const PStep &st = p.steps[s];
@@ -688,24 +737,54 @@ bool serialize(Plan &p, std::string *err) {
         d.nk_a = (uint8_t)st.k_a.size();
         d.nk_b = (uint8_t)st.k_b.size();
         d.c_off = (uint64_t)C.offset;
-        if (A.leaf >= 0) { d.flags |= kStepALeaf; d.a_off = (uint64_t)A.leaf; }
+        if (A.leaf >= 0) { d.flags |= kStepALeaf; d.a_off = (uint64_t)dev_leaf[A.leaf]; }
         else d.a_off = (uint64_t)A.offset;
         if (!make_runs(C.modes, A.modes, d.runs_a, &d.na_runs, &d.a_cb)) { *err = "address map needs too many runs"; return false; }
         if (st.b < 0) {
             d.flags |= kStepUnary;
         } else {
             const PTensor &B = p.tensors[st.b];
-            if (B.leaf >= 0) { d.flags |= kStepBLeaf; d.b_off = (uint64_t)B.leaf; }
+            if (B.leaf >= 0) { d.flags |= kStepBLeaf; d.b_off = (uint64_t)dev_leaf[B.leaf]; }
             else d.b_off = (uint64_t)B.offset;
             if (!make_runs(C.modes, B.modes, d.runs_b, &d.nb_runs, &d.b_cb)) { *err = "address map needs too many runs"; return false; }
         }
     }
+    // fused form: per-step tables of pext(c) for both operands (16-bit offsets)
+    std::vector<FusedStep> fs(ds.size());
+    std::vector<uint32_t> tab;
+    bool fused_ok = p.arena_elems <= 65536;
+    for (size_t s = 0; s < ds.size() && fused_ok; s++) {
+        const DevStep &d = ds[s];
+        FusedStep &f = fs[s];
+        std::memset(&f, 0, sizeof(f));
+        f.a_off = (uint32_t)d.a_off;
+        f.b_off = (uint32_t)d.b_off;
+        f.c_off = (uint32_t)d.c_off;
+        f.flags = d.flags;
+        f.rc = d.rc;
+        f.nk_ab = d.nk_ab;
+        f.nk_a = d.nk_a;
+        f.nk_b = d.nk_b;
+        f.a_cb = d.a_cb;
+        f.b_cb = d.b_cb;
+        f.tab_off = (uint32_t)tab.size();
+        if (d.rc > 16 || d.a_cb + d.nk_ab + d.nk_a > 16 || d.b_cb + d.nk_ab + d.nk_b > 16) { fused_ok = false; break; }
+        for (uint32_t c = 0; c < (1u << d.rc); c++) {
+            uint32_t ia = 0, ib = 0;
+            for (int r = 0; r < d.na_runs; r++)
+                ia |= ((c >> d.runs_a[r].src) & ((1u << d.runs_a[r].len) - 1u)) << d.runs_a[r].dst;
+            for (int r = 0; r < d.nb_runs; r++)
+                ib |= ((c >> d.runs_b[r].src) & ((1u << d.runs_b[r].len) - 1u)) << d.runs_b[r].dst;
+            tab.push_back(ia | (ib << 16));
+        }
+    }
+    if (!fused_ok) { fs.clear(); tab.clear(); }
     DevProgram h;
     std::memset(&h, 0, sizeof(h));
     h.magic = kProgramMagic;
     h.n_steps = (uint32_t)ds.size();
     h.n_leaves = (uint32_t)dl.size();
-    h.n_leaf_elems = (uint32_t)emap.size();
+    h.n_leaf_entries = ldata.size() / 2;
     h.arena_elems = (uint64_t)p.arena_elems;
     const PTensor &F = p.tensors[p.final_tensor];
     h.final_off = (uint64_t)F.offset;
@@ -721,17 +800,25 @@ bool serialize(Plan &p, std::string *err) {
     off = align256(off + ds.size() * sizeof(DevStep));
     h.leaves_off = off;
     off = align256(off + dl.size() * sizeof(DevLeaf));
-    h.elem_map_off = off;
-    off = align256(off + emap.size() * sizeof(uint32_t));
     h.leaf_data_off = off;
     off = align256(off + ldata.size() * sizeof(float));
+    if (!fs.empty()) {
+        h.fused_steps_off = off;
+        off = align256(off + fs.size() * sizeof(FusedStep));
+        h.fused_tab_off = off;
+        off = align256(off + tab.size() * sizeof(uint32_t));
+        h.n_tab_entries = tab.size();
+    }
     h.image_bytes = off;
     p.image.assign(off, 0);
     std::memcpy(p.image.data(), &h, sizeof(h));
     if (!ds.empty()) std::memcpy(p.image.data() + h.steps_off, ds.data(), ds.size() * sizeof(DevStep));
     if (!dl.empty()) std::memcpy(p.image.data() + h.leaves_off, dl.data(), dl.size() * sizeof(DevLeaf));
-    if (!emap.empty()) std::memcpy(p.image.data() + h.elem_map_off, emap.data(), emap.size() * sizeof(uint32_t));
     if (!ldata.empty()) std::memcpy(p.image.data() + h.leaf_data_off, ldata.data(), ldata.size() * sizeof(float));
+    if (!fs.empty()) {
+        std::memcpy(p.image.data() + h.fused_steps_off, fs.data(), fs.size() * sizeof(FusedStep));
+        if (!tab.empty()) std::memcpy(p.image.data() + h.fused_tab_off, tab.data(), tab.size() * sizeof(uint32_t));
+    }
     return true;
 }
 
@@ -868,6 +955,11 @@ qvx_status make_plan(const qvx_circuit *c, const int32_t *order, int32_t n_order
         return QVX_EUNSUPPORTED;
     }
     if (!serialize(*p, err)) return QVX_EUNSUPPORTED;
+    if (p->engine == QVX_ENGINE_FUSED &&
+        reinterpret_cast<const DevProgram *>(p->image.data())->fused_steps_off == 0 && !p->steps.empty()) {
+        if (opts.engine == QVX_ENGINE_FUSED) { *err = "fused engine: offsets exceed 16 bits"; return QVX_EUNSUPPORTED; }
+        p->engine = QVX_ENGINE_STEPWISE;
+    }
     return QVX_OK;
 }
 

@@ -12,14 +12,19 @@ STEP = np.dtype([("a_off", "<u8"), ("b_off", "<u8"), ("c_off", "<u8"), ("rc", "u
                  ("nk_a", "u1"), ("nk_b", "u1"), ("a_cb", "u1"), ("b_cb", "u1"), ("na_runs", "u1"),
                  ("nb_runs", "u1"), ("flags", "<u4"), ("pad", "<u4"), ("runs_a", RUN, (12,)),
                  ("runs_b", RUN, (12,))])
-LEAF = np.dtype([("data_off", "<u4"), ("elem_off", "<u4"), ("n_elem", "<u4"), ("n_fixed", "<u4"),
+LEAF = np.dtype([("data_off", "<u4"), ("n_elem", "<u4"), ("n_fixed", "<u4"), ("pad", "<u4"),
                  ("fixed_src", "u1", (12,)), ("fixed_pos", "u1", (12,))])
-PROG = np.dtype([("magic", "<u4"), ("n_steps", "<u4"), ("n_leaves", "<u4"), ("n_leaf_elems", "<u4"),
+PROG = np.dtype([("magic", "<u4"), ("n_steps", "<u4"), ("n_leaves", "<u4"), ("pad0", "<u4"),
+                 ("n_leaf_entries", "<u8"),
                  ("arena_elems", "<u8"), ("final_off", "<u8"), ("n_inner", "<u4"),
                  ("final_present", "<u4"), ("zero_mask", "<u8"), ("scalar_re", "<f8"),
                  ("scalar_im", "<f8"), ("n_outer", "<u8"), ("steps_off", "<u8"), ("leaves_off", "<u8"),
-                 ("elem_map_off", "<u8"), ("leaf_data_off", "<u8"), ("image_bytes", "<u8")])
-assert STEP.itemsize == 136 and LEAF.itemsize == 40 and PROG.itemsize == 112
+                 ("leaf_data_off", "<u8"), ("fused_steps_off", "<u8"), ("fused_tab_off", "<u8"),
+                 ("n_tab_entries", "<u8"), ("image_bytes", "<u8")])
+FSTEP = np.dtype([("a_off", "<u4"), ("b_off", "<u4"), ("c_off", "<u4"), ("tab_off", "<u4"), ("flags", "<u4"),
+                  ("rc", "u1"), ("nk_ab", "u1"), ("nk_a", "u1"), ("nk_b", "u1"), ("a_cb", "u1"), ("b_cb", "u1"),
+                  ("pad0", "u1"), ("pad1", "u1"), ("pad2", "<u4")])
+assert STEP.itemsize == 136 and LEAF.itemsize == 40 and PROG.itemsize == 136 and FSTEP.itemsize == 32
 UNARY, A_LEAF, B_LEAF = 1, 2, 4
 
 
@@ -39,8 +44,13 @@ class Program:
         assert int(h["magic"]) == 0x51565831
         self.steps = np.frombuffer(buf[int(h["steps_off"]):int(h["steps_off"]) + STEP.itemsize * int(h["n_steps"])].tobytes(), dtype=STEP)
         self.leaves = np.frombuffer(buf[int(h["leaves_off"]):int(h["leaves_off"]) + LEAF.itemsize * int(h["n_leaves"])].tobytes(), dtype=LEAF)
-        self.emap = np.frombuffer(buf[int(h["elem_map_off"]):int(h["elem_map_off"]) + 4 * int(h["n_leaf_elems"])].tobytes(), dtype="<u4").astype(np.int64)
-        ld = np.frombuffer(buf[int(h["leaf_data_off"]):].tobytes(), dtype="<f4")
+        self.fsteps = None
+        if int(h["fused_steps_off"]):
+            fo, to = int(h["fused_steps_off"]), int(h["fused_tab_off"])
+            self.fsteps = np.frombuffer(buf[fo:fo + FSTEP.itemsize * int(h["n_steps"])].tobytes(), dtype=FSTEP)
+            self.tab = np.frombuffer(buf[to:to + 4 * int(h["n_tab_entries"])].tobytes(), dtype="<u4").astype(np.int64)
+        n = int(h["n_leaf_entries"])
+        ld = np.frombuffer(buf[int(h["leaf_data_off"]):int(h["leaf_data_off"]) + 8 * n].tobytes(), dtype="<f4")
         self.leaf_data = ld[0::2].astype(np.float64) + 1j * ld[1::2].astype(np.float64)
 
     def _leaf_reader(self, li, x, o):
@@ -50,14 +60,19 @@ class Program:
             src = int(L["fixed_src"][f])
             bit = (x >> src) & 1 if src < 64 else (o >> (src - 64)) & 1
             off += bit << int(L["fixed_pos"][f])
-        em = self.emap[int(L["elem_off"]):int(L["elem_off"]) + int(L["n_elem"])]
-        return lambda idx: self.leaf_data[off + em[idx]]
+        n = int(L["n_elem"])
 
-    def item_terms(self, x: int, o: int):
-        """Slice terms of work item (x, o): entry i is slice (o << n_inner) | i."""
+        def read(idx):
+            assert np.all(idx < n)
+            return self.leaf_data[off + idx]
+        return read
+
+    def item_terms(self, x: int, o: int, fused: bool = False):
+        """Slice terms of work item (x, o): entry i is slice (o << n_inner) | i. With
+        fused=True the steps take their operand offsets from the fused form's tables."""
         h = self.h
         arena = np.zeros(max(int(h["arena_elems"]), 4), dtype=np.complex128)
-        for st in self.steps:
+        for si, st in enumerate(self.steps):
             rc = int(st["rc"])
             c = np.arange(1 << rc, dtype=np.int64)
             flags = int(st["flags"])
@@ -65,12 +80,23 @@ class Program:
                 if is_leaf:
                     return self._leaf_reader(int(ref), x, o)
                 base = int(ref)
-                return lambda idx: arena[base + idx]
+
+                def read(idx):
+                    assert np.all(base + idx < arena.size)
+                    return arena[base + idx]
+                return read
             A = operand(flags & A_LEAF, st["a_off"])
             unary = flags & UNARY
             B = None if unary else operand(flags & B_LEAF, st["b_off"])
-            ia = _pext(c, st["runs_a"], int(st["na_runs"]))
-            ib = None if unary else _pext(c, st["runs_b"], int(st["nb_runs"]))
+            if fused:
+                fst = self.fsteps[si]
+                for f in ("a_off", "b_off", "c_off", "flags", "rc", "nk_ab", "nk_a", "nk_b", "a_cb", "b_cb"):
+                    assert int(fst[f]) == int(st[f]), f
+                e = self.tab[int(fst["tab_off"]):int(fst["tab_off"]) + (1 << rc)]
+                ia, ib = e & 0xFFFF, (None if unary else e >> 16)
+            else:
+                ia = _pext(c, st["runs_a"], int(st["na_runs"]))
+                ib = None if unary else _pext(c, st["runs_b"], int(st["nb_runs"]))
             nab, na, nb = int(st["nk_ab"]), int(st["nk_a"]), int(st["nk_b"])
             acc = np.zeros(1 << rc, dtype=np.complex128)
             for k in range(1 << (nab + na + nb)):
@@ -81,6 +107,7 @@ class Program:
                 else:
                     kb = (k & ((1 << nab) - 1)) | ((k >> (nab + na)) << nab)
                     acc += a * B(ib + (kb << int(st["b_cb"])))
+            assert int(st["c_off"]) + (1 << rc) <= arena.size
             arena[int(st["c_off"]):int(st["c_off"]) + (1 << rc)] = acc
         n_in = int(h["n_inner"])
         present = int(h["final_present"])
@@ -97,6 +124,6 @@ class Program:
             out[i] = 0 if zero else scalar * fin[fi]
         return out
 
-    def slice_terms(self, x: int):
+    def slice_terms(self, x: int, fused: bool = False):
         n_out = int(self.h["n_outer"])
-        return np.concatenate([self.item_terms(x, o) for o in range(n_out)])
+        return np.concatenate([self.item_terms(x, o, fused) for o in range(n_out)])

@@ -53,12 +53,15 @@ def test_4x4x10_batch(engine, wpi):
     assert np.max(np.abs(got - psi[xs])) < tol(16)
 
 
-@pytest.mark.parametrize("inner,wpi,engine", [(-1, 1, "fused"), (0, 1, "fused"), (2, 2, "fused"),
-                                              (6, 4, "fused"), (3, 1, "stepwise")])
-def test_6x6x25_k12_full(inner, wpi, engine):
+@pytest.mark.parametrize("inner,wpi,engine,merge", [(-1, 1, "fused", 8), (0, 1, "fused", 8),
+                                                    (2, 2, "fused", 8), (6, 4, "fused", 8),
+                                                    (3, 1, "stepwise", 8), (4, 1, "fused", 0),
+                                                    (2, 1, "stepwise", 0)])
+def test_6x6x25_k12_full(inner, wpi, engine, merge):
     c = cg.grid_circuit(6, 6, 25, 2001)
     x = cg.random_bitstrings(36, 1, 2002)[0]
-    p = q.Plan(c, n_slices=12, inner_slices=inner, warps_per_item=wpi, engine=engine)
+    p = q.Plan(c, n_slices=12, inner_slices=inner, warps_per_item=wpi, engine=engine,
+               host_merge_rank=merge)
     ref_terms = VE.slice_terms(c, x, p.order, p.slices)
     ref = VE.exact_sum(ref_terms)
     got = _amps(p, [x])[0]

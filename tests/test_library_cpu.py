@@ -91,6 +91,11 @@ CASES = [
     ("4x4x10-k3", lambda: cg.grid_circuit(4, 4, 10, 1001), dict(n_slices=3, inner_slices=1)),
     ("3x4x16-k4", lambda: cg.grid_circuit(3, 4, 16, 2), dict(n_slices=4, inner_slices=2)),
     ("rot2x3", lambda: cg.rotation_circuit(2, 3, 4, 12), dict(n_slices=2, inner_slices=0)),
+    ("4x4x10-devonly", lambda: cg.grid_circuit(4, 4, 10, 1001), dict(host_merge_rank=0)),
+    ("3x4x16-k4-devonly", lambda: cg.grid_circuit(3, 4, 16, 2), dict(n_slices=4, inner_slices=2,
+                                                                      host_merge_rank=0)),
+    ("3x4x16-k4-merge12", lambda: cg.grid_circuit(3, 4, 16, 2), dict(n_slices=4, inner_slices=1,
+                                                                      host_merge_rank=12)),
     ("empty", lambda: cg.Circuit(n_qubits=3, gates=[]), dict()),
     ("untouched", lambda: cg.Circuit(n_qubits=3, gates=[cg.Gate(cg.H, 0), cg.Gate(cg.T, 1),
                                                         cg.Gate(cg.CZ, 0, 1)]), dict()),
@@ -107,19 +112,31 @@ def test_program_on_host_matches_oracle(name, maker, kw):
     for x in xs:
         terms = prog.slice_terms(x)
         assert abs(terms.sum() - psi[x]) < 1e-6 * 2 ** (-c.n_qubits / 2) + 1e-7
+        if prog.fsteps is not None:
+            assert np.array_equal(prog.slice_terms(x, fused=True), terms)
         if p.slices:
             ref = VE.slice_terms(c, x, p.order, p.slices)
             assert np.max(np.abs(terms - ref)) < 1e-6 * 2 ** (-c.n_qubits / 2)
 
 
-def test_program_slice_terms_6x6_sample():
+@pytest.mark.parametrize("merge", [0, 8])
+def test_program_slice_terms_6x6_sample(merge):
     c = cg.grid_circuit(6, 6, 25, 2001)
-    p = q.Plan(c, n_slices=12, inner_slices=3)
+    p = q.Plan(c, n_slices=12, inner_slices=3, host_merge_rank=merge)
     prog = Program(p.image())
     x = cg.random_bitstrings(36, 1, 2002)[0]
     rng = random.Random(0)
     for o in rng.sample(range(int(prog.h["n_outer"])), 3):
         got = prog.item_terms(x, o)
+        assert np.array_equal(prog.item_terms(x, o, fused=True), got)
         ids = [(o << 3) | i for i in range(8)]
         ref = VE.slice_terms(c, x, p.order, p.slices, slice_ids=ids)
         assert np.max(np.abs(got - ref)) < 1e-6 * 2 ** -18
+
+
+def test_host_merging_shortens_the_device_program():
+    c = cg.grid_circuit(6, 6, 25, 2001)
+    full = q.Plan(c, n_slices=12, inner_slices=4, host_merge_rank=0).info
+    merged = q.Plan(c, n_slices=12, inner_slices=4, host_merge_rank=8).info
+    assert merged["n_steps"] < full["n_steps"] / 2
+    assert merged["flops_per_amplitude"] < full["flops_per_amplitude"]

@@ -175,6 +175,20 @@ qvx_status qvx_slice_terms(qvx_plan *plan, const uint64_t *bitstrings_dev, int64
                            int64_t slice_begin, int64_t slice_count, float *terms_dev,
                            void *workspace_dev, size_t workspace_bytes, void *stream);
 
+/* The paper has no counterpart to this entry point; it serves callers that cannot
+ * allocate device memory. alpha_b = <x_b|C|0> for b < batch, like qvx_amplitude, but
+ * without a workspace: the library keeps this call's scratch (the plan's device image, a
+ * status word and the per-work-item partial sums) in one fixed device array of 4 MiB that
+ * every GPU loading the library holds until the process exits. bitstrings_dev and amps_dev
+ * are the caller's device buffers as for qvx_amplitude. Fused-engine plans only
+ * (QVX_EUNSUPPORTED otherwise); a plan and batch whose scratch exceeds 4 MiB are rejected
+ * with QVX_EINVAL. The first call on a device also looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture. All calls
+ * share the one array and each call overwrites it: calls that overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller. */
+qvx_status qvx_amplitude_noalloc(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch,
+                                 double *amps_dev, void *stream);
+
 /* Synchronises `stream` and returns the device status word kept in the workspace
  * (QVX_OK, QVX_ETIMEOUT or QVX_EDEVICE), then clears it. */
 qvx_status qvx_workspace_status(const qvx_plan *plan, void *workspace_dev, void *stream);

@@ -60,7 +60,7 @@ _lib = None
 EXPORTED = ("qvx_plan_opts_default", "qvx_graph_export", "qvx_plan_create", "qvx_plan_destroy",
             "qvx_plan_get_info", "qvx_plan_get_order", "qvx_plan_get_image", "qvx_workspace_size", "qvx_workspace_init",
             "qvx_amplitude", "qvx_amplitude_slices", "qvx_slice_terms", "qvx_workspace_status",
-            "qvx_last_error")
+            "qvx_last_error", "qvx_amplitude_noalloc")
 
 
 def lib():
@@ -88,6 +88,7 @@ def lib():
         "qvx_slice_terms": (ctypes.c_int, [P, P, i64, i64, i64, P, P, ctypes.c_size_t, P]),
         "qvx_workspace_status": (ctypes.c_int, [P, P, P]),
         "qvx_last_error": (ctypes.c_char_p, []),
+        "qvx_amplitude_noalloc": (ctypes.c_int, [P, P, i64, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

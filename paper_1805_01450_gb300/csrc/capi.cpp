@@ -8,14 +8,7 @@
 
 #include "kernels.h"
 #include "plan.h"
-
-struct qvx_plan {
-    qvx::Plan p;
-    // fused-engine launch shape, cached for the device it was computed on
-    int launch_device = -1;
-    int sms = 0;
-    int ctas_per_sm[9] = {0};   // by work items per CTA
-};
+#include "plan_handle.h"
 
 namespace {
 
@@ -379,3 +372,8 @@ qvx_status qvx_workspace_status(const qvx_plan *plan, void *ws, void *stream) {
 const char *qvx_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"
+
+namespace qvx {
+// Sets the calling thread's qvx_last_error message (for entry points in other files).
+void set_last_error(const std::string &msg) { g_err = msg; }
+}  // namespace qvx

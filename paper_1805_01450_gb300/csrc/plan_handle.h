@@ -1,0 +1,11 @@
+// The opaque qvx_plan handle of include/qvx.h.
+#pragma once
+#include "plan.h"
+
+struct qvx_plan {
+    qvx::Plan p;
+    // fused-engine launch shape, cached for the device it was computed on
+    int launch_device = -1;
+    int sms = 0;
+    int ctas_per_sm[9] = {0};   // by work items per CTA
+};

@@ -94,7 +94,8 @@ typedef struct {
     int32_t host_merge_rank;   /* two leaves whose product has at most this many modes (modes
                                   fixed per work item included) are contracted on the host in
                                   FP64 at plan time; 0 keeps every contraction on the device */
-    int32_t reserved;
+    int32_t gradient;          /* 1: the plan also serves qvx_amplitude_grad (every gate with
+                                  param_index >= 0 stays a tensor of its own) */
 } qvx_plan_opts;
 
 typedef struct {
@@ -107,6 +108,9 @@ typedef struct {
     double bytes_per_amplitude;      /* algorithmic tensor bytes read + written, all items */
     int64_t arena_bytes;             /* tensor memory of one work item */
     int64_t device_image_bytes;      /* program, leaves and tables */
+    int32_t n_params;                /* 1 + largest param_index (gradient plans), else 0 */
+    int32_t n_grad_steps;            /* contractions of the gradient program (0 if none) */
+    int64_t grad_arena_bytes;        /* gradient program memory of one work item */
 } qvx_plan_info;
 
 typedef struct qvx_plan qvx_plan;
@@ -188,6 +192,20 @@ qvx_status qvx_slice_terms(qvx_plan *plan, const uint64_t *bitstrings_dev, int64
  * streams, other threads) race and must be serialised by the caller. */
 qvx_status qvx_amplitude_noalloc(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch,
                                  double *amps_dev, void *stream);
+
+/* alpha_b = <x_b|C|0> and its derivatives d alpha_b / d theta_p with respect to the angles
+ * of the RXY gates (adjoint of the pairwise contractions: each gate's environment tensor
+ * contracted with dU/dtheta; the per-slice terms are added in FP64 with compensation).
+ * The plan must have been created with opts.gradient = 1. thetas_dev: n_thetas doubles on
+ * the device that replace the circuit's angles (gate g takes thetas_dev[g.param_index]),
+ * or NULL to keep them; n_thetas must then be 0 or the plan's n_params. amps_dev: 2*batch
+ * doubles; grad_dev: 2*batch*n_params doubles, complex d alpha_b / d theta_p at
+ * grad_dev[2*(b*n_params + p)]. The workspace holds the gradient program's arenas
+ * (qvx_workspace_size covers them for gradient plans). */
+qvx_status qvx_amplitude_grad(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch,
+                              const double *thetas_dev, int32_t n_thetas, double *amps_dev,
+                              double *grad_dev, void *workspace_dev, size_t workspace_bytes,
+                              void *stream);
 
 /* Synchronises `stream` and returns the device status word kept in the workspace
  * (QVX_OK, QVX_ETIMEOUT or QVX_EDEVICE), then clears it. */

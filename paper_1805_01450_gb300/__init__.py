@@ -43,7 +43,7 @@ class PlanOpts(ctypes.Structure):
                 ("order_seed", ctypes.c_uint64), ("mem_budget_bytes", ctypes.c_int64),
                 ("engine", ctypes.c_int32), ("inner_slices", ctypes.c_int32),
                 ("max_rank", ctypes.c_int32), ("warps_per_item", ctypes.c_int32),
-                ("host_merge_rank", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("host_merge_rank", ctypes.c_int32), ("gradient", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -53,14 +53,15 @@ class PlanInfo(ctypes.Structure):
                [("n_items_per_bitstring", ctypes.c_int64), ("log2_cost", ctypes.c_double),
                 ("log2_cost_unsliced", ctypes.c_double), ("flops_per_amplitude", ctypes.c_double),
                 ("bytes_per_amplitude", ctypes.c_double), ("arena_bytes", ctypes.c_int64),
-                ("device_image_bytes", ctypes.c_int64)]
+                ("device_image_bytes", ctypes.c_int64), ("n_params", ctypes.c_int32),
+                ("n_grad_steps", ctypes.c_int32), ("grad_arena_bytes", ctypes.c_int64)]
 
 
 _lib = None
 EXPORTED = ("qvx_plan_opts_default", "qvx_graph_export", "qvx_plan_create", "qvx_plan_destroy",
             "qvx_plan_get_info", "qvx_plan_get_order", "qvx_plan_get_image", "qvx_workspace_size", "qvx_workspace_init",
             "qvx_amplitude", "qvx_amplitude_slices", "qvx_slice_terms", "qvx_workspace_status",
-            "qvx_last_error", "qvx_amplitude_noalloc")
+            "qvx_last_error", "qvx_amplitude_noalloc", "qvx_amplitude_grad")
 
 
 def lib():
@@ -89,6 +90,7 @@ def lib():
         "qvx_workspace_status": (ctypes.c_int, [P, P, P]),
         "qvx_last_error": (ctypes.c_char_p, []),
         "qvx_amplitude_noalloc": (ctypes.c_int, [P, P, i64, P, P]),
+        "qvx_amplitude_grad": (ctypes.c_int, [P, P, i64, P, i32, P, P, P, ctypes.c_size_t, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -145,7 +147,7 @@ class Plan:
 
     def __init__(self, circ, order=None, slices=None, n_slices=-1, engine="auto", inner_slices=-1,
                  order_restarts=8, order_seed=1, mem_budget_bytes=1 << 30, max_rank=30,
-                 warps_per_item=1, host_merge_rank=8):
+                 warps_per_item=1, host_merge_rank=8, gradient=False):
         L = lib()
         opts = PlanOpts()
         L.qvx_plan_opts_default(ctypes.byref(opts))
@@ -158,6 +160,7 @@ class Plan:
         opts.max_rank = max_rank
         opts.warps_per_item = warps_per_item
         opts.host_merge_rank = host_merge_rank
+        opts.gradient = 1 if gradient else 0
         cs = circuit_struct(circ)
         o_arr = (ctypes.c_int32 * max(len(order or []), 1))(*(order or []))
         s_arr = (ctypes.c_int32 * max(len(slices or []), 1))(*(slices or []))
@@ -257,6 +260,32 @@ class Plan:
                                           slice_count, ctypes.c_void_p(out.data_ptr()),
                                           ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
         return torch.view_as_complex(out.view(n, 2))
+
+    def amplitude_grad(self, bitstrings, thetas=None, workspace=None, stream=None):
+        """(alpha [batch] complex128, d alpha / d theta [batch, n_params] complex128) on the
+        device, for a plan created with gradient=True. thetas: float64 tensor of n_params
+        angles (any device) replacing the circuit's, or None."""
+        import torch
+        bits = self._bits(bitstrings)
+        self._check_bits(bits)
+        n = bits.numel()
+        npar = self.info["n_params"]
+        ws = workspace if workspace is not None else self._ws_for(n, bits.device)
+        amps = torch.empty(2 * n, dtype=torch.float64, device=bits.device)
+        grad = torch.empty(2 * n * max(npar, 1), dtype=torch.float64, device=bits.device)
+        th = None
+        if thetas is not None:
+            th = torch.as_tensor(thetas, dtype=torch.float64).to(bits.device).contiguous()
+            if th.numel() != npar:
+                raise QvxError(QVX_EINVAL, f"expected {npar} angles, got {th.numel()}")
+        _check(lib().qvx_amplitude_grad(self._h, ctypes.c_void_p(bits.data_ptr()), n,
+                                        None if th is None else ctypes.c_void_p(th.data_ptr()),
+                                        0 if th is None else npar, ctypes.c_void_p(amps.data_ptr()),
+                                        ctypes.c_void_p(grad.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
+                                        ws.numel(), _stream_ptr(stream)))
+        a = torch.view_as_complex(amps.view(n, 2))
+        g = torch.view_as_complex(grad.view(n, max(npar, 1), 2))[:, :npar]
+        return a, g
 
     def slice_terms(self, bitstrings, slice_begin=0, slice_count=None, workspace=None, stream=None):
         """The slice terms beta_s (complex64, [batch, slice_count]) of Section 3.B.2."""

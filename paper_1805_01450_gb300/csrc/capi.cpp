@@ -26,9 +26,12 @@ qvx_status cuda_fail(cudaError_t e, const char *where) {
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Workspace layout: [device image][status word, CTA counter][item partials][stepwise arenas]
+// and, for gradient plans, [derivative partials][gradient arenas]
 struct WsLayout {
     size_t image, status, partials, arenas, total;
     int64_t items_in_flight;
+    size_t grad_partials = 0, grad_arenas = 0;
+    int64_t grad_slots = 0;
 };
 
 WsLayout layout_of(const qvx::Plan &p, int64_t batch) {
@@ -46,6 +49,15 @@ WsLayout layout_of(const qvx::Plan &p, int64_t batch) {
         w.items_in_flight = std::min(total_items, fit);
     }
     w.total = align256(w.arenas + (size_t)w.items_in_flight * (size_t)std::max<int64_t>(p.arena_elems, 4) * 8);
+    if (p.opts.gradient) {
+        const qvx::DevProgram *h = reinterpret_cast<const qvx::DevProgram *>(p.image.data());
+        const int64_t total_items = std::max<int64_t>(batch, 1) * n_outer;
+        const int64_t arena_bytes = std::max<int64_t>(p.grad_arena_elems, 4) * 8;
+        w.grad_partials = w.total;
+        w.grad_arenas = align256(w.grad_partials + (size_t)total_items * h->n_param_leaves * 16);
+        w.grad_slots = std::min(total_items, std::max<int64_t>(1, p.opts.mem_budget_bytes / arena_bytes));
+        w.total = align256(w.grad_arenas + (size_t)w.grad_slots * (size_t)arena_bytes);
+    }
     return w;
 }
 
@@ -181,6 +193,7 @@ void qvx_plan_opts_default(qvx_plan_opts *o) {
     o->max_rank = 30;
     o->warps_per_item = 1;
     o->host_merge_rank = 8;
+    o->gradient = 0;
 }
 
 qvx_status qvx_graph_export(const qvx_circuit *circuit, int32_t *n_vars, int32_t *var_qubit,
@@ -263,6 +276,9 @@ qvx_status qvx_plan_get_info(const qvx_plan *plan, qvx_plan_info *info) {
     info->bytes_per_amplitude = p.bytes_per_item * (double)info->n_items_per_bitstring;
     info->arena_bytes = p.arena_elems * 8;
     info->device_image_bytes = (int64_t)p.image.size();
+    info->n_params = p.n_params;
+    info->n_grad_steps = (int32_t)p.grad_steps.size();
+    info->grad_arena_bytes = p.grad_arena_elems * 8;
     return QVX_OK;
 }
 
@@ -349,6 +365,45 @@ qvx_status qvx_slice_terms(qvx_plan *plan, const uint64_t *bitstrings_dev, int64
     int64_t o_count = 0;
     return run_items(plan, bitstrings_dev, batch, slice_begin, slice_begin + slice_count, terms_dev, nullptr,
                      ws, w, static_cast<cudaStream_t>(stream), &o_count);
+}
+
+qvx_status qvx_amplitude_grad(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch, const double *thetas_dev,
+                              int32_t n_thetas, double *amps_dev, double *grad_dev, void *ws, size_t ws_bytes,
+                              void *stream) {
+    WsLayout w;
+    qvx_status s = check_ws(plan, batch, ws, ws_bytes, &w);
+    if (s != QVX_OK) return s;
+    const qvx::Plan &p = plan->p;
+    if (!p.opts.gradient) return fail(QVX_EUNSUPPORTED, "plan was created without opts.gradient");
+    if (thetas_dev ? n_thetas != p.n_params : n_thetas != 0)
+        return fail(QVX_EINVAL, "n_thetas must equal the plan's n_params (" + std::to_string(p.n_params) + ")");
+    if (batch == 0) return QVX_OK;
+    if (!bitstrings_dev || !amps_dev || (p.n_params > 0 && !grad_dev)) return fail(QVX_EINVAL, "null device buffer");
+    const qvx::DevProgram *h = reinterpret_cast<const qvx::DevProgram *>(p.image.data());
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned char *base = static_cast<unsigned char *>(ws);
+    cudaError_t e;
+    if ((e = qvx::launch_set_params(base + w.image, h->n_param_leaves, thetas_dev, st)) != cudaSuccess)
+        return cuda_fail(e, "parameter kernel launch");
+    const int64_t n_outer = int64_t(1) << ((int)p.slices.size() - p.n_inner);
+    qvx::GradArgs g{};
+    g.image = base + w.image;
+    g.bitstrings = bitstrings_dev;
+    g.batch = batch;
+    g.o_count = n_outer;
+    g.arenas = reinterpret_cast<float2 *>(base + w.grad_arenas);
+    g.arena_elems = (uint64_t)std::max<int64_t>(p.grad_arena_elems, 4);
+    g.slots = w.grad_slots;
+    g.partials = reinterpret_cast<double2 *>(base + w.partials);
+    g.gpart = reinterpret_cast<double2 *>(base + w.grad_partials);
+    const int grid = (int)std::min<int64_t>(batch * n_outer, w.grad_slots);
+    if ((e = qvx::launch_grad_program(g, grid, st)) != cudaSuccess) return cuda_fail(e, "gradient kernel launch");
+    if ((e = qvx::launch_slice_sum(g.partials, batch, n_outer, amps_dev, st)) != cudaSuccess)
+        return cuda_fail(e, "slice sum launch");
+    if ((e = qvx::launch_grad_sum(base + w.image, g.gpart, batch, n_outer, h->n_param_leaves, (uint32_t)p.n_params,
+                                  grad_dev, st)) != cudaSuccess)
+        return cuda_fail(e, "gradient sum launch");
+    return QVX_OK;
 }
 
 qvx_status qvx_workspace_status(const qvx_plan *plan, void *ws, void *stream) {

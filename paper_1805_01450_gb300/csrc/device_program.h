@@ -53,6 +53,35 @@ struct FusedStep {
     uint32_t pad2;
 };
 
+// Gradient program: out[o] = sum_k X(o, k) * Y(o, k), each operand addressed through bit
+// runs of the output index o and of the summed index k. Operand kinds: arena tensor, leaf
+// data or leaf derivative data (restricted like a leaf), or the constant one.
+constexpr uint32_t kOpArena = 0, kOpLeaf = 1, kOpDeriv = 2, kOpOne = 3;
+
+struct GenOperand {
+    uint64_t off;                  // arena offset, or device leaf index
+    uint32_t kind;
+    uint8_t n_oruns, n_kruns, pad0, pad1;
+    DevRun oruns[kMaxRuns];        // output-index bits -> operand bits
+    DevRun kruns[kMaxRuns];        // summed-index bits -> operand bits
+};
+
+struct GenStep {
+    GenOperand x, y;
+    uint64_t out_off;              // arena offset of the output
+    uint32_t ro, nk;               // output rank, summed bits
+};
+
+// A leaf that is one parametrised gate exp(-i theta (cos phi X + sin phi Y) / 2): its
+// stored entry e is matrix element code[e] (bit 1: row, bit 0: column) of U or dU/dtheta.
+struct ParamLeaf {
+    uint32_t leaf;                 // device leaf index
+    uint32_t param;                // index into the angle vector
+    uint32_t n_stored;             // stored entries
+    uint32_t code_off;             // first entry in the code array
+    double phi;
+};
+
 struct DevProgram {
     uint32_t magic;
     uint32_t n_steps, n_leaves, pad0;
@@ -67,6 +96,12 @@ struct DevProgram {
     uint64_t steps_off, leaves_off, leaf_data_off;  // byte offsets
     uint64_t fused_steps_off, fused_tab_off;        // byte offsets (0 if the fused form is absent)
     uint64_t n_tab_entries;
+    // gradient program (zero when absent)
+    uint64_t grad_steps_off, params_off, codes_off, deriv_data_off, thetas_off, param_csr_off;
+    uint32_t n_grad_steps, n_param_leaves, n_params, grad_pad;
+    uint64_t grad_arena_elems;
+    uint64_t final_fwd_off;        // gradient arena offset of the final tensor
+    uint64_t gslot_off;            // gradient arena offset of the per-leaf derivative slots
     uint64_t image_bytes;
 };
 
@@ -77,6 +112,9 @@ constexpr uint32_t kProgramMagic = 0x51565831u;  // "QVX1"
 namespace qvx {
 static_assert(sizeof(DevStep) == 136, "DevStep layout");
 static_assert(sizeof(DevLeaf) == 40, "DevLeaf layout");
-static_assert(sizeof(DevProgram) == 136, "DevProgram layout");
+static_assert(sizeof(DevProgram) == 224, "DevProgram layout");
+static_assert(sizeof(GenOperand) == 112, "GenOperand layout");
+static_assert(sizeof(GenStep) == 240, "GenStep layout");
+static_assert(sizeof(ParamLeaf) == 24, "ParamLeaf layout");
 static_assert(sizeof(FusedStep) == 32, "FusedStep layout");
 }  // namespace qvx

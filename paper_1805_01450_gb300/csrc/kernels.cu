@@ -303,7 +303,170 @@ __global__ void slice_sum_kernel(const double2 *partials, int64_t o_count, doubl
     }
 }
 
+// ------------------------------------------------------------------ gradient program
+__device__ __forceinline__ uint32_t runs_pdep(uint32_t v, const DevRun *runs, uint32_t n) {
+    uint32_t r = 0;
+    for (uint32_t i = 0; i < n; i++) r |= ((v >> runs[i].src) & ((1u << runs[i].len) - 1u)) << runs[i].dst;
+    return r;
+}
+
+// Parametrised leaf entries from the angles: U = cos(t/2) I - i sin(t/2) (cos(phi) X +
+// sin(phi) Y) and dU/dtheta = -sin(t/2)/2 I - (i/2) cos(t/2) (cos(phi) X + sin(phi) Y).
+__global__ void set_params_kernel(unsigned char *img, const double *thetas) {
+    const DevProgram *P = reinterpret_cast<const DevProgram *>(img);
+    const ParamLeaf &pl = reinterpret_cast<const ParamLeaf *>(img + P->params_off)[blockIdx.x];
+    const DevLeaf &L = reinterpret_cast<const DevLeaf *>(img + P->leaves_off)[pl.leaf];
+    const uint8_t *codes = img + P->codes_off + pl.code_off;
+    float2 *data = reinterpret_cast<float2 *>(img + P->leaf_data_off) + L.data_off;
+    float2 *deriv = reinterpret_cast<float2 *>(img + P->deriv_data_off) + L.data_off;
+    const double th = thetas ? thetas[pl.param] : reinterpret_cast<const double *>(img + P->thetas_off)[pl.param];
+    double s, c, sp, cp;
+    sincos(0.5 * th, &s, &c);
+    sincos(pl.phi, &sp, &cp);
+    for (uint32_t e = threadIdx.x; e < pl.n_stored; e += blockDim.x) {
+        const uint32_t code = codes[e];
+        const uint32_t row = code >> 1, col = code & 1u;
+        double ur, ui, dr, di;
+        if (row == col) {
+            ur = c; ui = 0; dr = -0.5 * s; di = 0;
+        } else {
+            // off-diagonal: -i s e^{-i phi} (row 0) or -i s e^{+i phi} (row 1)
+            const double sg = row == 0 ? -1.0 : 1.0;
+            ur = sg * s * sp;  ui = -s * cp;          // -i s (cp + i sg sp)
+            dr = sg * 0.5 * c * sp; di = -0.5 * c * cp;
+        }
+        data[e] = make_float2((float)ur, (float)ui);
+        deriv[e] = make_float2((float)dr, (float)di);
+    }
+}
+
+__device__ __forceinline__ const float2 *gen_base(const GenOperand &op, const DevProgram *P,
+                                                  const unsigned char *img, float2 *arena, uint64_t x,
+                                                  uint64_t o) {
+    if (op.kind == kOpArena) return arena + op.off;
+    if (op.kind == kOpOne) return nullptr;
+    const DevLeaf &L = reinterpret_cast<const DevLeaf *>(img + P->leaves_off)[op.off];
+    const uint64_t data = op.kind == kOpLeaf ? P->leaf_data_off : P->deriv_data_off;
+    return reinterpret_cast<const float2 *>(img + data) + leaf_base(L, x, o);
+}
+
+__global__ void __launch_bounds__(256) grad_program_kernel(GradArgs g) {
+    const unsigned char *img = g.image;
+    const DevProgram *P = reinterpret_cast<const DevProgram *>(img);
+    const GenStep *steps = reinterpret_cast<const GenStep *>(img + P->grad_steps_off);
+    float2 *arena = g.arenas + (uint64_t)blockIdx.x * g.arena_elems;
+    const int64_t n_items = g.batch * g.o_count;
+    const uint32_t npl = P->n_param_leaves;
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int64_t b = item / g.o_count;
+        const uint64_t o = (uint64_t)(item % g.o_count);
+        const uint64_t x = g.bitstrings[b];
+        for (uint32_t s = 0; s < P->n_grad_steps; s++) {
+            const GenStep &st = steps[s];
+            const float2 *X = gen_base(st.x, P, img, arena, x, o);
+            const float2 *Y = gen_base(st.y, P, img, arena, x, o);
+            float2 *out = arena + st.out_off;
+            for (uint32_t oi = threadIdx.x; oi < (1u << st.ro); oi += blockDim.x) {
+                const uint32_t ox = runs_pdep(oi, st.x.oruns, st.x.n_oruns);
+                const uint32_t oy = runs_pdep(oi, st.y.oruns, st.y.n_oruns);
+                float2 acc = make_float2(0.f, 0.f);
+                for (uint32_t k = 0; k < (1u << st.nk); k++) {
+                    const float2 a = X ? X[ox + runs_pdep(k, st.x.kruns, st.x.n_kruns)] : make_float2(1.f, 0.f);
+                    const float2 v = Y ? Y[oy + runs_pdep(k, st.y.kruns, st.y.n_kruns)] : make_float2(1.f, 0.f);
+                    cmac(acc, a, v);
+                }
+                out[oi] = acc;
+            }
+            __syncthreads();
+        }
+        // amplitude partial: sum of the final tensor over the inner slice modes
+        const bool zero = (x & P->zero_mask) != 0;
+        if (threadIdx.x < 32) {
+            const float2 *fin = arena + P->final_fwd_off;
+            double2 acc = make_double2(0.0, 0.0);
+            const uint32_t n_in = P->n_inner, present = P->final_present;
+            for (uint32_t i = threadIdx.x; i < (1u << n_in); i += 32) {
+                uint32_t fi = 0, bit = 0;
+                for (uint32_t j = 0; j < n_in; j++)
+                    if ((present >> j) & 1u) fi |= ((i >> j) & 1u) << bit++;
+                const float2 t = fin[fi];
+                acc.x += (double)t.x * P->scalar_re - (double)t.y * P->scalar_im;
+                acc.y += (double)t.x * P->scalar_im + (double)t.y * P->scalar_re;
+            }
+            acc = warp_sum(acc);
+            if (threadIdx.x == 0) g.partials[item] = zero ? make_double2(0.0, 0.0) : acc;
+        }
+        for (uint32_t lp = threadIdx.x; lp < npl; lp += blockDim.x) {
+            const float2 t = arena[P->gslot_off + lp];
+            const double2 v = make_double2((double)t.x * P->scalar_re - (double)t.y * P->scalar_im,
+                                           (double)t.x * P->scalar_im + (double)t.y * P->scalar_re);
+            g.gpart[(uint64_t)item * npl + lp] = zero ? make_double2(0.0, 0.0) : v;
+        }
+        __syncthreads();
+    }
+}
+
+// One block per (bitstring, parameter): compensated sum over the work items and over the
+// parameter's leaves (CSR lists in the image).
+__global__ void grad_sum_kernel(const unsigned char *img, const double2 *gpart, int64_t o_count, uint32_t npl,
+                                uint32_t n_params, double *grad) {
+    __shared__ double red[4][32];
+    const DevProgram *P = reinterpret_cast<const DevProgram *>(img);
+    const uint32_t *csr = reinterpret_cast<const uint32_t *>(img + P->param_csr_off);
+    const int64_t b = blockIdx.x / n_params;
+    const uint32_t p = blockIdx.x % n_params;
+    const uint32_t first = csr[p], last = csr[p + 1];
+    const uint32_t *list = csr + n_params + 1;
+    double sr = 0, cr = 0, si = 0, ci = 0;
+    const int64_t n = (int64_t)(last - first) * o_count;
+    for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
+        const uint32_t lp = list[first + t / o_count];
+        const int64_t o = t % o_count;
+        const double2 v = gpart[((uint64_t)(b * o_count + o)) * npl + lp];
+        neumaier_add(sr, cr, v.x);
+        neumaier_add(si, ci, v.y);
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        const double a = __shfl_down_sync(0xffffffffu, sr, d), bb = __shfl_down_sync(0xffffffffu, cr, d);
+        const double e = __shfl_down_sync(0xffffffffu, si, d), f = __shfl_down_sync(0xffffffffu, ci, d);
+        merge_pair(sr, cr, a, bb);
+        merge_pair(si, ci, e, f);
+    }
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+    if (lane == 0) {
+        red[0][warp] = sr; red[1][warp] = cr; red[2][warp] = si; red[3][warp] = ci;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s0 = red[0][0], c0 = red[1][0], s1 = red[2][0], c1 = red[3][0];
+        for (int w = 1; w < nw; w++) {
+            merge_pair(s0, c0, red[0][w], red[1][w]);
+            merge_pair(s1, c1, red[2][w], red[3][w]);
+        }
+        grad[2 * (b * n_params + p)] = s0 + c0;
+        grad[2 * (b * n_params + p) + 1] = s1 + c1;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_set_params(unsigned char *image, uint32_t n_param_leaves, const double *thetas, cudaStream_t s) {
+    if (n_param_leaves == 0) return cudaSuccess;
+    set_params_kernel<<<n_param_leaves, 32, 0, s>>>(image, thetas);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_program(const GradArgs &g, int grid, cudaStream_t s) {
+    grad_program_kernel<<<grid, 256, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_sum(const unsigned char *image, const double2 *gpart, int64_t batch, int64_t o_count,
+                            uint32_t n_param_leaves, uint32_t n_params, double *grad, cudaStream_t s) {
+    if (n_params == 0 || batch == 0) return cudaSuccess;
+    grad_sum_kernel<<<(unsigned)(batch * n_params), 256, 0, s>>>(image, gpart, o_count, n_param_leaves, n_params, grad);
+    return cudaGetLastError();
+}
 
 cudaError_t fused_prepare(size_t smem_bytes) {
     return cudaFuncSetAttribute(fused_program_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

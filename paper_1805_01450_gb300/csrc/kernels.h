@@ -40,6 +40,24 @@ cudaError_t launch_step(const LaunchArgs &a, uint32_t step, int64_t item_begin, 
 cudaError_t launch_finish_items(const LaunchArgs &a, int64_t item_begin, int64_t n_items,
                                 const float2 *arenas, cudaStream_t s);
 
+// Gradient program (one CTA per work item, arenas in global memory).
+struct GradArgs {
+    unsigned char *image;           // workspace copy of the image (its parametrised leaves are rewritten)
+    const uint64_t *bitstrings;
+    int64_t batch, o_count;
+    float2 *arenas;                 // slots * grad_arena_elems
+    uint64_t arena_elems;
+    int64_t slots;
+    double2 *partials;              // batch * o_count amplitude partials
+    double2 *gpart;                 // batch * o_count * n_param_leaves derivative partials
+};
+// Rewrites the parametrised leaves (U and dU/dtheta) from thetas (device, or the image's own).
+cudaError_t launch_set_params(unsigned char *image, uint32_t n_param_leaves, const double *thetas, cudaStream_t s);
+cudaError_t launch_grad_program(const GradArgs &g, int grid, cudaStream_t s);
+// d alpha / d theta_p = compensated FP64 sum over work items and the parameter's leaves.
+cudaError_t launch_grad_sum(const unsigned char *image, const double2 *gpart, int64_t batch, int64_t o_count,
+                            uint32_t n_param_leaves, uint32_t n_params, double *grad, cudaStream_t s);
+
 // FP64 compensated sum of the item partials of every bitstring (Section 3.B.2: the slice
 // terms are added).
 cudaError_t launch_slice_sum(const double2 *partials, int64_t batch, int64_t o_count,

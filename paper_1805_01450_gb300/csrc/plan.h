@@ -16,6 +16,11 @@ using cplx = std::complex<double>;
 struct HostTensor {
     std::vector<int> modes;
     std::vector<cplx> data;
+    // a parametrised gate kept as its own tensor (gradient plans): entry e is element
+    // code[e] of its 2x2 matrix (bit 1 row, bit 0 column)
+    int param = -1;
+    double theta = 0, phi = 0;
+    std::vector<uint8_t> code;
 };
 
 // Variable ids inside a plan: [0, n_vars) are the summed variables (canonical ids);
@@ -63,10 +68,16 @@ struct Plan {
     int engine = QVX_ENGINE_FUSED;
     int warps_per_item = 1;
     std::vector<unsigned char> image;          // device image (DevProgram first)
+    // gradient program
+    int n_params = 0;
+    std::vector<GenStep> grad_steps;
+    int64_t grad_arena_elems = 0;
+    int64_t grad_final_off = 0, grad_gslot_off = 0;
+    std::vector<int> grad_param_leaves;        // leaf indices of the parametrised leaves
 };
 
 // planner.cpp
-bool build_model(const qvx_circuit *c, Model *m, std::string *err);
+bool build_model(const qvx_circuit *c, Model *m, std::string *err, bool keep_params = false);
 qvx_status make_plan(const qvx_circuit *c, const int32_t *order, int32_t n_order,
                      const int32_t *slices, int32_t n_slices, const qvx_plan_opts &opts,
                      Plan *p, std::string *err);

@@ -76,7 +76,7 @@ bool is_subset(const std::vector<int> &a, const std::vector<int> &b) {
 }  // namespace
 
 // ---------------------------------------------------------------- graphical model
-bool build_model(const qvx_circuit *c, Model *m, std::string *err) {
+bool build_model(const qvx_circuit *c, Model *m, std::string *err, bool keep_params) {
     if (!c || c->n_qubits < 1 || c->n_qubits > 64 || c->n_gates < 0 || (c->n_gates > 0 && !c->gates)) {
         *err = "circuit: need 1 <= n_qubits <= 64 and a gate array";
         return false;
@@ -86,6 +86,8 @@ bool build_model(const qvx_circuit *c, Model *m, std::string *err) {
     struct Raw {
         std::vector<std::pair<int, int>> keys;   // (qubit, ordinal); bit j of an index <-> keys[j]
         std::vector<cplx> data;
+        int param = -1;
+        double theta = 0, phi = 0;
     };
     std::vector<Raw> raw;
     raw.reserve((size_t)c->n_gates);
@@ -108,6 +110,11 @@ bool build_model(const qvx_circuit *c, Model *m, std::string *err) {
             r.data.resize(4);
             for (int a = 0; a < 2; a++)
                 for (int b = 0; b < 2; b++) r.data[a | (b << 1)] = u[b][a];
+            if (keep_params && g.kind == QVX_GATE_RXY && g.param_index >= 0) {
+                r.param = g.param_index;
+                r.theta = g.theta;
+                r.phi = g.phi;
+            }
             cur[g.q0]++;
         }
         raw.push_back(std::move(r));
@@ -144,10 +151,14 @@ bool build_model(const qvx_circuit *c, Model *m, std::string *err) {
             if (id >= 0) { t.modes.push_back(id); keep.push_back((int)j); }
         }
         t.data.resize(size_t(1) << t.modes.size());
+        t.param = r.param;
+        t.theta = r.theta;
+        t.phi = r.phi;
         for (size_t e = 0; e < t.data.size(); e++) {
             size_t src = 0;  // fixed inputs take value 0
             for (size_t j = 0; j < keep.size(); j++) src |= ((e >> j) & 1u) << keep[j];
             t.data[e] = r.data[src];
+            if (t.param >= 0) t.code.push_back((uint8_t)src);   // raw index a | b << 1 = element [b][a]
         }
         if (t.modes.empty()) m->scalar *= t.data[0];
         else m->tensors.push_back(std::move(t));
@@ -168,9 +179,10 @@ bool build_model(const qvx_circuit *c, Model *m, std::string *err) {
     for (size_t i = 0; i < idx.size(); i++) {
         int t = idx[i];
         const HostTensor &T = m->tensors[t];
+        if (T.param >= 0) continue;                 // parametrised gates stay tensors of their own
         int best = -1;
         for (int s : by_mode[T.modes[0]]) {
-            if (s == t || dead[s] || rank_pos[s] < (int)i) continue;
+            if (s == t || dead[s] || rank_pos[s] < (int)i || m->tensors[s].param >= 0) continue;
             if (m->tensors[s].modes.size() < T.modes.size()) continue;
             if (!is_subset(T.modes, m->tensors[s].modes)) continue;
             if (best < 0 || rank_pos[s] < rank_pos[best]) best = s;
@@ -449,7 +461,7 @@ struct ProgramBuilder {
         for (int v : s.k_a) summed[v] = 1;
         for (int v : s.k_b) summed[v] = 1;
         const int la = p.tensors[a].leaf, lb = p.tensors[b].leaf;
-        if (la >= 0 && lb >= 0) {
+        if (la >= 0 && lb >= 0 && p.leaves[la].param < 0 && p.leaves[lb].param < 0) {
             // two leaves: contract them here, in FP64, when the result stays small; the
             // result keeps the modes fixed per work item, so it serves every item
             std::vector<int> dead = s.k_ab;
@@ -680,6 +692,135 @@ bool make_runs(const std::vector<int> &C, const std::vector<int> &X, DevRun *run
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Runs that move the bits of an index laid out as `src` (bit j <-> src[j]) to the
+// positions of the same modes in `dst`; modes of src absent from dst contribute nothing.
+bool map_runs(const std::vector<int> &src, const std::vector<int> &dst, DevRun *runs, uint8_t *n) {
+    int nr = 0;
+    size_t j = 0;
+    while (j < src.size()) {
+        const int pj = find_pos(dst, src[j]);
+        if (pj < 0) { j++; continue; }
+        size_t k = j + 1;
+        while (k < src.size() && find_pos(dst, src[k]) == pj + (int)(k - j)) k++;
+        if (nr >= kMaxRuns) return false;
+        runs[nr].src = (uint8_t)j;
+        runs[nr].len = (uint8_t)(k - j);
+        runs[nr].dst = (uint8_t)pj;
+        runs[nr].pad = 0;
+        nr++;
+        j = k;
+    }
+    *n = (uint8_t)nr;
+    return true;
+}
+
+// Reverse-mode program over the pairwise contractions. Every forward output keeps its own
+// arena slot; for a step C = contract(A, B) the adjoint of A is contract(adj C, B) over
+// the modes of C and B that A lacks (and symmetrically for B); the adjoint of the final
+// tensor is the constant 2^(inner slice modes it lacks). Each parametrised leaf then gets
+// d alpha / d theta = sum over its entries of adj(leaf) * dU/dtheta (a rank-0 step).
+bool build_grad_program(Plan &p, const std::vector<int> &dev_leaf, std::string *err) {
+    const size_t nt = p.tensors.size();
+    std::vector<char> need(nt, 0);
+    for (size_t t = 0; t < nt; t++) {
+        const PTensor &T = p.tensors[t];
+        if (T.leaf >= 0 && T.consumer >= 0 && p.leaves[T.leaf].param >= 0) need[t] = 1;
+    }
+    for (const PStep &st : p.steps) need[st.c] = need[st.a] || (st.b >= 0 && need[st.b]);
+    int64_t off = 0;
+    auto alloc = [&](int64_t n) {
+        const int64_t r = off;
+        off += (n + 3) & ~int64_t(3);
+        return r;
+    };
+    std::vector<int64_t> fo(nt, -1), ao(nt, -1);
+    for (const PStep &st : p.steps) fo[st.c] = alloc(int64_t(1) << p.tensors[st.c].modes.size());
+    std::vector<int> pl;   // parametrised leaf tensors
+    for (size_t t = 0; t < nt; t++) {
+        if (!need[t]) continue;
+        ao[t] = alloc(int64_t(1) << p.tensors[t].modes.size());
+        if (p.tensors[t].leaf >= 0) pl.push_back((int)t);
+    }
+    const int64_t gslot = alloc((int64_t)pl.size());
+    p.grad_steps.clear();
+    auto operand = [&](GenOperand &o, int t, bool adj, const std::vector<int> &out, const std::vector<int> &S) {
+        std::memset(&o, 0, sizeof(o));
+        if (t < 0) { o.kind = kOpOne; return true; }
+        const PTensor &T = p.tensors[t];
+        if (adj) { o.kind = kOpArena; o.off = (uint64_t)ao[t]; }
+        else if (T.leaf >= 0) { o.kind = kOpLeaf; o.off = (uint64_t)dev_leaf[T.leaf]; }
+        else { o.kind = kOpArena; o.off = (uint64_t)fo[t]; }
+        return map_runs(out, T.modes, o.oruns, &o.n_oruns) && map_runs(S, T.modes, o.kruns, &o.n_kruns);
+    };
+    auto emit = [&](int64_t out_off, const std::vector<int> &out, int x, bool xadj, int y, bool yadj,
+                    const std::vector<int> &S) {
+        GenStep g;
+        std::memset(&g, 0, sizeof(g));
+        g.out_off = (uint64_t)out_off;
+        g.ro = (uint32_t)out.size();
+        g.nk = (uint32_t)S.size();
+        if (!operand(g.x, x, xadj, out, S) || !operand(g.y, y, yadj, out, S)) return false;
+        p.grad_steps.push_back(g);
+        return true;
+    };
+    auto minus = [](const std::vector<int> &u, const std::vector<int> &w, const std::vector<int> &drop) {
+        std::vector<int> r;
+        for (const std::vector<int> *v : {&u, &w})
+            for (int m : *v)
+                if (find_pos(drop, m) < 0 && find_pos(r, m) < 0) r.push_back(m);
+        return r;
+    };
+    const std::string runs_err = "gradient program: address map needs too many runs";
+    for (const PStep &st : p.steps) {   // forward, every output kept
+        std::vector<int> S = st.k_ab;
+        S.insert(S.end(), st.k_a.begin(), st.k_a.end());
+        S.insert(S.end(), st.k_b.begin(), st.k_b.end());
+        if (!emit(fo[st.c], p.tensors[st.c].modes, st.a, false, st.b, false, S)) { *err = runs_err; return false; }
+    }
+    const int F = p.final_tensor;
+    if (need[F]) {
+        std::vector<int> absent;   // inner slice modes the final tensor lacks: dummy summed modes
+        for (int i = 0; i < p.n_inner; i++)
+            if (find_pos(p.tensors[F].modes, p.slices[i]) < 0) absent.push_back(-1 - i);
+        if (!emit(ao[F], p.tensors[F].modes, -1, false, -1, false, absent)) { *err = runs_err; return false; }
+    }
+    for (int s = (int)p.steps.size() - 1; s >= 0; s--) {
+        const PStep &st = p.steps[s];
+        if (!need[st.c]) continue;
+        const std::vector<int> &LC = p.tensors[st.c].modes, &LA = p.tensors[st.a].modes;
+        if (need[st.a]) {
+            const std::vector<int> none;
+            const std::vector<int> &LB = st.b >= 0 ? p.tensors[st.b].modes : none;
+            if (!emit(ao[st.a], LA, st.c, true, st.b, false, minus(LC, LB, LA))) { *err = runs_err; return false; }
+        }
+        if (st.b >= 0 && need[st.b]) {
+            const std::vector<int> &LB = p.tensors[st.b].modes;
+            if (!emit(ao[st.b], LB, st.c, true, st.a, false, minus(LC, LA, LB))) { *err = runs_err; return false; }
+        }
+    }
+    p.grad_param_leaves.clear();
+    for (size_t i = 0; i < pl.size(); i++) {   // d alpha / d theta per parametrised leaf
+        const int t = pl[i];
+        GenStep g;
+        std::memset(&g, 0, sizeof(g));
+        g.out_off = (uint64_t)(gslot + (int64_t)i);
+        g.ro = 0;
+        g.nk = (uint32_t)p.tensors[t].modes.size();
+        const std::vector<int> none;
+        if (!operand(g.x, t, true, none, p.tensors[t].modes) || !operand(g.y, t, false, none, p.tensors[t].modes)) {
+            *err = runs_err;
+            return false;
+        }
+        g.y.kind = kOpDeriv;
+        p.grad_steps.push_back(g);
+        p.grad_param_leaves.push_back(p.tensors[t].leaf);
+    }
+    p.grad_arena_elems = off;
+    p.grad_final_off = fo[F];
+    p.grad_gslot_off = gslot;
+    return true;
+}
+
 bool serialize(Plan &p, std::string *err) {
     const Model &m = p.model;
     // leaf element maps and stored data
@@ -691,6 +832,9 @@ bool serialize(Plan &p, std::string *err) {
         if (leaf_tensor[l] >= 0) { dev_leaf[l] = (int)live.size(); live.push_back((int)l); }
     std::vector<DevLeaf> dl(live.size());
     std::vector<float> ldata;
+    std::vector<ParamLeaf> pls;
+    std::vector<uint8_t> codes;
+    std::vector<int> pleaf_of_leaf(p.leaves.size(), -1);
     for (size_t di = 0; di < live.size(); di++) {
         const int l = live[di];
         const HostTensor &h = p.leaves[l];
@@ -719,11 +863,23 @@ bool serialize(Plan &p, std::string *err) {
         }
         std::vector<int> pos(stored.size());
         for (size_t j = 0; j < stored.size(); j++) pos[j] = find_pos(h.modes, stored[j]);
+        if (h.param >= 0) {
+            ParamLeaf pl;
+            std::memset(&pl, 0, sizeof(pl));
+            pl.leaf = (uint32_t)di;
+            pl.param = (uint32_t)h.param;
+            pl.n_stored = 1u << stored.size();
+            pl.code_off = (uint32_t)codes.size();
+            pl.phi = h.phi;
+            pleaf_of_leaf[l] = (int)pls.size();
+            pls.push_back(pl);
+        }
         for (size_t e = 0; e < (size_t(1) << stored.size()); e++) {
             size_t src = 0;
             for (size_t j = 0; j < stored.size(); j++) src |= ((e >> j) & 1u) << pos[j];
             ldata.push_back((float)h.data[src].real());
             ldata.push_back((float)h.data[src].imag());
+            if (h.param >= 0) codes.push_back(h.code[src]);
         }
     }
     std::vector<DevStep> ds(p.steps.size());
@@ -809,8 +965,57 @@ bool serialize(Plan &p, std::string *err) {
         off = align256(off + tab.size() * sizeof(uint32_t));
         h.n_tab_entries = tab.size();
     }
+    // gradient program
+    std::vector<uint32_t> csr;
+    std::vector<double> thetas;
+    if (p.opts.gradient) {
+        if (!build_grad_program(p, dev_leaf, err)) return false;
+        // parametrised leaves in the order of the derivative slots
+        std::vector<ParamLeaf> ordered;
+        for (int l : p.grad_param_leaves) ordered.push_back(pls[pleaf_of_leaf[l]]);
+        pls = ordered;
+        thetas.assign(p.n_params, 0.0);
+        std::vector<char> seen(p.n_params, 0);
+        for (int l : p.grad_param_leaves) {
+            const HostTensor &hl = p.leaves[l];
+            if (hl.param < p.n_params && !seen[hl.param]) { thetas[hl.param] = hl.theta; seen[hl.param] = 1; }
+        }
+        // CSR: parameter -> derivative slots
+        csr.assign(p.n_params + 1, 0);
+        for (const ParamLeaf &q : pls) csr[q.param + 1]++;
+        for (int i = 0; i < p.n_params; i++) csr[i + 1] += csr[i];
+        std::vector<uint32_t> fill(csr.begin(), csr.end() - 1), list(pls.size());
+        for (size_t i = 0; i < pls.size(); i++) list[fill[pls[i].param]++] = (uint32_t)i;
+        csr.insert(csr.end(), list.begin(), list.end());
+        h.n_grad_steps = (uint32_t)p.grad_steps.size();
+        h.n_param_leaves = (uint32_t)pls.size();
+        h.n_params = (uint32_t)p.n_params;
+        h.grad_arena_elems = (uint64_t)p.grad_arena_elems;
+        h.final_fwd_off = (uint64_t)p.grad_final_off;
+        h.gslot_off = (uint64_t)p.grad_gslot_off;
+        h.grad_steps_off = off;
+        off = align256(off + p.grad_steps.size() * sizeof(GenStep));
+        h.params_off = off;
+        off = align256(off + pls.size() * sizeof(ParamLeaf));
+        h.codes_off = off;
+        off = align256(off + codes.size());
+        h.deriv_data_off = off;
+        off = align256(off + ldata.size() * sizeof(float));
+        h.thetas_off = off;
+        off = align256(off + thetas.size() * sizeof(double));
+        h.param_csr_off = off;
+        off = align256(off + csr.size() * sizeof(uint32_t));
+    }
     h.image_bytes = off;
     p.image.assign(off, 0);
+    if (p.opts.gradient) {
+        unsigned char *img = p.image.data();
+        if (!p.grad_steps.empty()) std::memcpy(img + h.grad_steps_off, p.grad_steps.data(), p.grad_steps.size() * sizeof(GenStep));
+        if (!pls.empty()) std::memcpy(img + h.params_off, pls.data(), pls.size() * sizeof(ParamLeaf));
+        if (!codes.empty()) std::memcpy(img + h.codes_off, codes.data(), codes.size());
+        if (!thetas.empty()) std::memcpy(img + h.thetas_off, thetas.data(), thetas.size() * sizeof(double));
+        if (!csr.empty()) std::memcpy(img + h.param_csr_off, csr.data(), csr.size() * sizeof(uint32_t));
+    }
     std::memcpy(p.image.data(), &h, sizeof(h));
     if (!ds.empty()) std::memcpy(p.image.data() + h.steps_off, ds.data(), ds.size() * sizeof(DevStep));
     if (!dl.empty()) std::memcpy(p.image.data() + h.leaves_off, dl.data(), dl.size() * sizeof(DevLeaf));
@@ -844,7 +1049,11 @@ qvx_status make_plan(const qvx_circuit *c, const int32_t *order, int32_t n_order
                      const int32_t *slices, int32_t n_slices, const qvx_plan_opts &opts,
                      Plan *p, std::string *err) {
     p->opts = opts;
-    if (!build_model(c, &p->model, err)) return QVX_EINVAL;
+    if (!build_model(c, &p->model, err, opts.gradient != 0)) return QVX_EINVAL;
+    if (opts.gradient)
+        for (int64_t i = 0; i < c->n_gates; i++)
+            if (c->gates[i].kind == QVX_GATE_RXY && c->gates[i].param_index >= 0)
+                p->n_params = std::max(p->n_params, c->gates[i].param_index + 1);
     const Model &m = p->model;
     const int nv = m.n_vars;
     Graph g;

@@ -20,11 +20,21 @@ PROG = np.dtype([("magic", "<u4"), ("n_steps", "<u4"), ("n_leaves", "<u4"), ("pa
                  ("final_present", "<u4"), ("zero_mask", "<u8"), ("scalar_re", "<f8"),
                  ("scalar_im", "<f8"), ("n_outer", "<u8"), ("steps_off", "<u8"), ("leaves_off", "<u8"),
                  ("leaf_data_off", "<u8"), ("fused_steps_off", "<u8"), ("fused_tab_off", "<u8"),
-                 ("n_tab_entries", "<u8"), ("image_bytes", "<u8")])
+                 ("n_tab_entries", "<u8"), ("grad_steps_off", "<u8"), ("params_off", "<u8"),
+                 ("codes_off", "<u8"), ("deriv_data_off", "<u8"), ("thetas_off", "<u8"),
+                 ("param_csr_off", "<u8"), ("n_grad_steps", "<u4"), ("n_param_leaves", "<u4"),
+                 ("n_params", "<u4"), ("grad_pad", "<u4"), ("grad_arena_elems", "<u8"),
+                 ("final_fwd_off", "<u8"), ("gslot_off", "<u8"), ("image_bytes", "<u8")])
 FSTEP = np.dtype([("a_off", "<u4"), ("b_off", "<u4"), ("c_off", "<u4"), ("tab_off", "<u4"), ("flags", "<u4"),
                   ("rc", "u1"), ("nk_ab", "u1"), ("nk_a", "u1"), ("nk_b", "u1"), ("a_cb", "u1"), ("b_cb", "u1"),
                   ("pad0", "u1"), ("pad1", "u1"), ("pad2", "<u4")])
-assert STEP.itemsize == 136 and LEAF.itemsize == 40 and PROG.itemsize == 136 and FSTEP.itemsize == 32
+GOP = np.dtype([("off", "<u8"), ("kind", "<u4"), ("n_oruns", "u1"), ("n_kruns", "u1"), ("pad0", "u1"),
+                ("pad1", "u1"), ("oruns", RUN, (12,)), ("kruns", RUN, (12,))])
+GSTEP = np.dtype([("x", GOP), ("y", GOP), ("out_off", "<u8"), ("ro", "<u4"), ("nk", "<u4")])
+PLEAF = np.dtype([("leaf", "<u4"), ("param", "<u4"), ("n_stored", "<u4"), ("code_off", "<u4"), ("phi", "<f8")])
+assert STEP.itemsize == 136 and LEAF.itemsize == 40 and PROG.itemsize == 224 and FSTEP.itemsize == 32
+assert GOP.itemsize == 112 and GSTEP.itemsize == 240 and PLEAF.itemsize == 24
+OP_ARENA, OP_LEAF, OP_DERIV, OP_ONE = 0, 1, 2, 3
 UNARY, A_LEAF, B_LEAF = 1, 2, 4
 
 
@@ -52,6 +62,17 @@ class Program:
         n = int(h["n_leaf_entries"])
         ld = np.frombuffer(buf[int(h["leaf_data_off"]):int(h["leaf_data_off"]) + 8 * n].tobytes(), dtype="<f4")
         self.leaf_data = ld[0::2].astype(np.float64) + 1j * ld[1::2].astype(np.float64)
+        self.gsteps = None
+        if int(h["n_grad_steps"]):
+            go = int(h["grad_steps_off"])
+            self.gsteps = np.frombuffer(buf[go:go + GSTEP.itemsize * int(h["n_grad_steps"])].tobytes(), dtype=GSTEP)
+            po = int(h["params_off"])
+            self.pleaves = np.frombuffer(buf[po:po + PLEAF.itemsize * int(h["n_param_leaves"])].tobytes(), dtype=PLEAF)
+            co = int(h["codes_off"])
+            self.codes = np.frombuffer(buf[co:co + int(h["deriv_data_off"]) - co].tobytes(), dtype="u1")
+            to = int(h["thetas_off"])
+            self.thetas = np.frombuffer(buf[to:to + 8 * int(h["n_params"])].tobytes(), dtype="<f8").copy()
+            self.deriv_data = np.zeros_like(self.leaf_data)
 
     def _leaf_reader(self, li, x, o):
         L = self.leaves[li]
@@ -127,3 +148,100 @@ class Program:
     def slice_terms(self, x: int, fused: bool = False):
         n_out = int(self.h["n_outer"])
         return np.concatenate([self.item_terms(x, o, fused) for o in range(n_out)])
+
+
+def _pdep_runs(c, runs, n):
+    return _pext(c, runs, n)
+
+
+def rxy_and_derivative(theta, phi):
+    """U = cos(t/2) I - i sin(t/2)(cos(phi) X + sin(phi) Y) and dU/dtheta, [row][column]."""
+    c, s = np.cos(theta / 2), np.sin(theta / 2)
+    em, ep = np.exp(-1j * phi), np.exp(1j * phi)
+    U = np.array([[c, -1j * s * em], [-1j * s * ep, c]])
+    dU = np.array([[-s / 2, -0.5j * c * em], [-0.5j * c * ep, -s / 2]])
+    return U, dU
+
+
+def grad_item(prog, x, o, thetas=None):
+    """(alpha partial, per-slot derivative partials) of work item (x, o) by the image's
+    gradient program, with the parametrised leaves rebuilt from `thetas`."""
+    h = prog.h
+    th = prog.thetas if thetas is None else np.asarray(thetas, dtype=np.float64)
+    data = prog.leaf_data.copy()
+    deriv = prog.deriv_data.copy()
+    for pl in prog.pleaves:
+        U, dU = rxy_and_derivative(th[int(pl["param"])], float(pl["phi"]))
+        L = prog.leaves[int(pl["leaf"])]
+        for e in range(int(pl["n_stored"])):
+            code = int(prog.codes[int(pl["code_off"]) + e])
+            data[int(L["data_off"]) + e] = U[code >> 1, code & 1]
+            deriv[int(L["data_off"]) + e] = dU[code >> 1, code & 1]
+    arena = np.zeros(max(int(h["grad_arena_elems"]), 4), dtype=np.complex128)
+
+    def base(L):
+        off = int(L["data_off"])
+        for f in range(int(L["n_fixed"])):
+            src = int(L["fixed_src"][f])
+            bit = (x >> src) & 1 if src < 64 else (o >> (src - 64)) & 1
+            off += bit << int(L["fixed_pos"][f])
+        return off
+
+    def reader(op):
+        kind = int(op["kind"])
+        if kind == OP_ONE:
+            return lambda idx: np.ones(idx.shape, dtype=np.complex128)
+        if kind == OP_ARENA:
+            b = int(op["off"])
+            return lambda idx: arena[b + idx]
+        L = prog.leaves[int(op["off"])]
+        b = base(L)
+        src = data if kind == OP_LEAF else deriv
+        return lambda idx: src[b + idx]
+
+    for g in prog.gsteps:
+        ro, nk = int(g["ro"]), int(g["nk"])
+        oidx = np.arange(1 << ro, dtype=np.int64)
+        X, Y = reader(g["x"]), reader(g["y"])
+        ox = _pext(oidx, g["x"]["oruns"], int(g["x"]["n_oruns"]))
+        oy = _pext(oidx, g["y"]["oruns"], int(g["y"]["n_oruns"]))
+        acc = np.zeros(1 << ro, dtype=np.complex128)
+        for k in range(1 << nk):
+            kk = np.array([k], dtype=np.int64)
+            kx = _pext(kk, g["x"]["kruns"], int(g["x"]["n_kruns"]))[0]
+            ky = _pext(kk, g["y"]["kruns"], int(g["y"]["n_kruns"]))[0]
+            acc += X(ox + kx) * Y(oy + ky)
+        arena[int(g["out_off"]):int(g["out_off"]) + (1 << ro)] = acc
+    n_in = int(h["n_inner"])
+    present = int(h["final_present"])
+    fin = arena[int(h["final_fwd_off"]):]
+    scalar = complex(float(h["scalar_re"]), float(h["scalar_im"]))
+    zero = (x & int(h["zero_mask"])) != 0
+    tot = 0j
+    for i in range(1 << n_in):
+        fi, bit = 0, 0
+        for j in range(n_in):
+            if (present >> j) & 1:
+                fi |= ((i >> j) & 1) << bit
+                bit += 1
+        tot += fin[fi]
+    npl = int(h["n_param_leaves"])
+    slots = arena[int(h["gslot_off"]):int(h["gslot_off"]) + npl] * scalar
+    if zero:
+        return 0j, np.zeros(npl, dtype=np.complex128)
+    return scalar * tot, slots
+
+
+def grad(prog, x, thetas=None):
+    """(alpha, d alpha / d theta per parameter) over every work item."""
+    n_out = int(prog.h["n_outer"])
+    a = 0j
+    slots = np.zeros(int(prog.h["n_param_leaves"]), dtype=np.complex128)
+    for o in range(n_out):
+        ai, si = grad_item(prog, x, o, thetas)
+        a += ai
+        slots += si
+    g = np.zeros(int(prog.h["n_params"]), dtype=np.complex128)
+    for i, pl in enumerate(prog.pleaves):
+        g[int(pl["param"])] += slots[i]
+    return a, g

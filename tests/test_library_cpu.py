@@ -140,3 +140,32 @@ def test_host_merging_shortens_the_device_program():
     merged = q.Plan(c, n_slices=12, inner_slices=4, host_merge_rank=8).info
     assert merged["n_steps"] < full["n_steps"] / 2
     assert merged["flops_per_amplitude"] < full["flops_per_amplitude"]
+
+
+GRAD_CASES = [
+    ("rot2x3d4", lambda: cg.rotation_circuit(2, 3, 4, 12), dict()),
+    ("rot2x3d4-k3", lambda: cg.rotation_circuit(2, 3, 4, 12), dict(n_slices=3, inner_slices=1)),
+    ("rot3x3d3-k4-merge", lambda: cg.rotation_circuit(3, 3, 3, 7), dict(n_slices=4, inner_slices=2,
+                                                                        host_merge_rank=8)),
+    ("one-rotation", lambda: cg.Circuit(n_qubits=1, gates=[cg.Gate(cg.RXY, 0, theta=0.9, phi=0.0, param=0)]), dict()),
+]
+
+
+@pytest.mark.parametrize("name,maker,kw", GRAD_CASES, ids=[c[0] for c in GRAD_CASES])
+def test_gradient_program_on_host_matches_oracle(name, maker, kw):
+    from _program_exec import grad
+    c = maker()
+    p = q.Plan(c, gradient=True, **kw)
+    assert p.info["n_params"] == c.n_params
+    prog = Program(p.image())
+    for x in [0] + cg.random_bitstrings(c.n_qubits, 2, 4):
+        a_ref, g_ref = SV.sv_adjoint_grad(c, x)
+        a, g = grad(prog, x)
+        assert abs(a - a_ref) < 1e-6 * 2 ** (-c.n_qubits / 2)
+        assert np.max(np.abs(g - g_ref)) < 1e-6 * 2 ** (-c.n_qubits / 2)
+    # other angles through the parametrised leaves
+    th = np.random.default_rng(0).uniform(0, 2 * np.pi, c.n_params)
+    x = 1
+    a_ref, g_ref = SV.sv_adjoint_grad(SV.with_thetas(c, th), x)
+    a, g = grad(prog, x, th)
+    assert abs(a - a_ref) < 1e-6 and np.max(np.abs(g - g_ref)) < 1e-6

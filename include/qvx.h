@@ -90,7 +90,7 @@ typedef struct {
     int32_t engine;            /* qvx_engine */
     int32_t inner_slices;      /* sliced variables kept open inside one work item; -1 auto */
     int32_t max_rank;          /* largest tensor rank a plan may create (<= 30) */
-    int32_t warps_per_item;    /* fused engine: warps sharing one work item (1, 2 or 4) */
+    int32_t warps_per_item;    /* fused engine: warps sharing one work item (1, 2, 4, 8 or 16) */
     int32_t host_merge_rank;   /* two leaves whose product has at most this many modes (modes
                                   fixed per work item included) are contracted on the host in
                                   FP64 at plan time; 0 keeps every contraction on the device */

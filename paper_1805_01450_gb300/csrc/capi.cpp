@@ -117,22 +117,11 @@ qvx_status run_items(qvx_plan *plan, const uint64_t *bits, int64_t batch, int64_
     if (p.engine == QVX_ENGINE_FUSED) {
         const int wpi = p.warps_per_item;
         const qvx::DevProgram *h = reinterpret_cast<const qvx::DevProgram *>(p.image.data());
-        auto r16 = [](size_t x) { return (x + 15) & ~size_t(15); };
-        const size_t kBudget = 220u << 10;   // dynamic shared memory per CTA
-        const size_t group = r16((size_t)h->n_leaves * 4) + (size_t)a.arena_elems * 8;
-        // fused steps and their tables form one contiguous block of the image
-        size_t steps_b = r16((size_t)(h->fused_tab_off - h->fused_steps_off) + (size_t)h->n_tab_entries * 4);
-        size_t leaf_b = r16((size_t)h->n_leaf_entries * 8);
-        // stage the program in shared memory while it leaves room for at least two groups
-        if (steps_b + leaf_b + 2 * group > kBudget) leaf_b = 0;
-        if (steps_b + leaf_b + 2 * group > kBudget) steps_b = 0;
-        if (steps_b + leaf_b + group > kBudget) return fail(QVX_EUNSUPPORTED, "fused kernel: arena exceeds shared memory");
-        const size_t shared = steps_b + leaf_b;
-        const int max_ipc = (int)std::max<size_t>(1, std::min<size_t>(8 / wpi, (kBudget - shared) / group));
-        a.smem_steps_bytes = (uint32_t)steps_b;
-        a.smem_leaf_bytes = (uint32_t)leaf_b;
-        a.leaf_table_bytes = (uint32_t)r16((size_t)h->n_leaves * 4);
-        a.group_bytes = (uint32_t)group;
+        size_t shared = 0, group = 0;
+        int max_ipc = 1;
+        if (!qvx::fused_shape(h, a.arena_elems, wpi, &a, &shared, &group, &max_ipc))
+            return fail(QVX_EUNSUPPORTED, "fused kernel: arena exceeds shared memory");
+        const bool staged = a.smem_steps_bytes != 0;
         int dev = -1;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
         if (dev != plan->launch_device) {
@@ -143,7 +132,7 @@ qvx_status run_items(qvx_plan *plan, const uint64_t *bits, int64_t batch, int64_
                 return cuda_fail(e, "fused kernel attributes");
             for (int ipc = 1; ipc <= 8; ipc++)
                 plan->ctas_per_sm[ipc] =
-                    ipc <= max_ipc ? qvx::fused_blocks_per_sm(32 * wpi * ipc, shared + ipc * group) : 0;
+                    ipc <= max_ipc ? qvx::fused_blocks_per_sm(32 * wpi * ipc, shared + ipc * group, staged) : 0;
             plan->sms = caps.sms;
             plan->launch_device = dev;
         }
@@ -234,8 +223,8 @@ qvx_status qvx_plan_create(const qvx_circuit *circuit, const int32_t *order, int
         return fail(QVX_EINVAL, "opts: restarts >= 1, max_rank >= 1, budget >= 64 bytes");
     if (o.host_merge_rank < 0 || o.host_merge_rank > 16)
         return fail(QVX_EINVAL, "opts: host_merge_rank must be in [0, 16]");
-    if (o.warps_per_item != 1 && o.warps_per_item != 2 && o.warps_per_item != 4)
-        return fail(QVX_EINVAL, "opts: warps_per_item must be 1, 2 or 4");
+    if (o.warps_per_item < 1 || o.warps_per_item > 16 || (o.warps_per_item & (o.warps_per_item - 1)))
+        return fail(QVX_EINVAL, "opts: warps_per_item must be 1, 2, 4, 8 or 16");
     qvx_plan *plan = nullptr;
     try {
         plan = new qvx_plan();

@@ -44,13 +44,17 @@ struct DevLeaf {
 
 // The fused engine's form of a step: operand offsets and a per-step table holding, for
 // each output entry c, the operands' offsets pext(c) for A (low 16 bits) and B (high 16).
+// Steps are grouped into phases of independent steps; lane_map[phase * lanes + lane] gives
+// the step a lane of a work item's group works on (bits 0-11), the lane's index among the
+// step's lanes (bits 12-21) and their count (bits 22-31), or 0xffffffff for none.
 struct FusedStep {
     uint32_t a_off, b_off, c_off;  // arena offsets, or leaf indices (flags as in DevStep)
     uint32_t tab_off;              // first table entry of this step
     uint32_t flags;
     uint8_t rc, nk_ab, nk_a, nk_b;
-    uint8_t a_cb, b_cb, pad0, pad1;
+    uint8_t a_cb, b_cb, nk, pad1;
     uint32_t pad2;
+    uint16_t koff_a[4], koff_b[4]; // offsets of summed index k (nk <= 2) in A and B
 };
 
 // Gradient program: out[o] = sum_k X(o, k) * Y(o, k), each operand addressed through bit
@@ -96,6 +100,8 @@ struct DevProgram {
     uint64_t steps_off, leaves_off, leaf_data_off;  // byte offsets
     uint64_t fused_steps_off, fused_tab_off;        // byte offsets (0 if the fused form is absent)
     uint64_t n_tab_entries;
+    uint64_t fused_lane_map_off;                    // byte offset, right after the tables
+    uint32_t n_fused_phases, fused_lanes;
     // gradient program (zero when absent)
     uint64_t grad_steps_off, params_off, codes_off, deriv_data_off, thetas_off, param_csr_off;
     uint32_t n_grad_steps, n_param_leaves, n_params, grad_pad;
@@ -112,9 +118,9 @@ constexpr uint32_t kProgramMagic = 0x51565831u;  // "QVX1"
 namespace qvx {
 static_assert(sizeof(DevStep) == 136, "DevStep layout");
 static_assert(sizeof(DevLeaf) == 40, "DevLeaf layout");
-static_assert(sizeof(DevProgram) == 224, "DevProgram layout");
+static_assert(sizeof(DevProgram) == 240, "DevProgram layout");
 static_assert(sizeof(GenOperand) == 112, "GenOperand layout");
 static_assert(sizeof(GenStep) == 240, "GenStep layout");
 static_assert(sizeof(ParamLeaf) == 24, "ParamLeaf layout");
-static_assert(sizeof(FusedStep) == 32, "FusedStep layout");
+static_assert(sizeof(FusedStep) == 48, "FusedStep layout");
 }  // namespace qvx

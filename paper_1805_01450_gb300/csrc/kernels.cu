@@ -2,6 +2,8 @@
 // FP64 compensated sum of the slice terms.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "device_program.h"
 #include "kernels.h"
 
@@ -64,15 +66,32 @@ __device__ __forceinline__ double2 warp_sum(double2 v) {
     return v;
 }
 
+// Header fields the item epilogue needs, read once per kernel.
+struct FinishInfo {
+    uint64_t zero_mask;
+    double sr, si;
+    uint32_t n_in, present;
+};
+
+__device__ __forceinline__ FinishInfo finish_info(const DevProgram *P) {
+    FinishInfo f;
+    f.zero_mask = P->zero_mask;
+    f.sr = P->scalar_re;
+    f.si = P->scalar_im;
+    f.n_in = P->n_inner;
+    f.present = P->final_present;
+    return f;
+}
+
 // Sum of the inner slice terms of the item's final tensor that fall in [s_begin, s_end)
 // (FP64), times the plan's scalar; optionally writes each term.
-__device__ void finish_item(const DevProgram *P, const LaunchArgs &a, const float2 *fin, int64_t b,
-                            uint64_t o, int lane, int lanes) {
+__device__ void finish_item(const FinishInfo &P, const LaunchArgs &a, const float2 *fin, int64_t b, uint64_t o,
+                            int lane, int lanes) {
     const uint64_t x = a.bitstrings[b];
-    const bool zero = (x & P->zero_mask) != 0;
-    const double sr = P->scalar_re, si = P->scalar_im;
+    const bool zero = (x & P.zero_mask) != 0;
+    const double sr = P.sr, si = P.si;
     double2 acc = make_double2(0.0, 0.0);
-    const uint32_t n_in = P->n_inner, present = P->final_present;
+    const uint32_t n_in = P.n_in, present = P.present;
     for (uint32_t i = lane; i < (1u << n_in); i += lanes) {
         const int64_t s = (int64_t)((o << n_in) | i);
         if (s < a.s_begin || s >= a.s_end) continue;
@@ -154,54 +173,178 @@ __device__ __forceinline__ void copy_to_smem(void *dst, const void *src, size_t 
     for (size_t i = threadIdx.x; i < bytes / 16; i += blockDim.x) d[i] = __ldg(s + i);
 }
 
-// One output entry of a fused step: e packs the operands' offsets pext(c).
+// One output entry of a fused step: e packs the operands' offsets pext(c); the summed
+// index's offsets come from the step's koff tables (nk <= 2) or from its bit counts.
 __device__ __forceinline__ float2 fused_entry(const FusedStep &st, uint32_t e, const float2 *__restrict__ A,
                                               const float2 *__restrict__ B, bool unary) {
     const uint32_t ia = e & 0xffffu, ib = e >> 16;
-    const uint32_t nab = st.nk_ab, na = st.nk_a;
-    const uint32_t nk = nab + na + st.nk_b;
-    const uint32_t mask_ka = (1u << (nab + na)) - 1u, mask_ab = (1u << nab) - 1u;
     float2 acc = make_float2(0.f, 0.f);
-    if (unary) {
-        for (uint32_t k = 0; k < (1u << nk); k++) {
-            const float2 v = A[ia + (k << st.a_cb)];
-            acc.x += v.x;
-            acc.y += v.y;
+    if (st.nk <= 2) {
+        const uint32_t nk = 1u << st.nk;
+#pragma unroll
+        for (uint32_t k = 0; k < 4; k++) {   // constant indices keep koff in registers
+            if (k < nk) {
+                if (unary) {
+                    const float2 v = A[ia + st.koff_a[k]];
+                    acc.x += v.x;
+                    acc.y += v.y;
+                } else {
+                    cmac(acc, A[ia + st.koff_a[k]], B[ib + st.koff_b[k]]);
+                }
+            }
         }
         return acc;
     }
-#pragma unroll 2
-    for (uint32_t k = 0; k < (1u << nk); k++) {
+    const uint32_t nab = st.nk_ab, na = st.nk_a;
+    const uint32_t mask_ka = (1u << (nab + na)) - 1u, mask_ab = (1u << nab) - 1u;
+    for (uint32_t k = 0; k < (1u << st.nk); k++) {
         const uint32_t ka = k & mask_ka;
-        const uint32_t kb = (k & mask_ab) | ((k >> (nab + na)) << nab);
-        cmac(acc, A[ia + (ka << st.a_cb)], B[ib + (kb << st.b_cb)]);
+        if (unary) {
+            const float2 v = A[ia + (ka << st.a_cb)];
+            acc.x += v.x;
+            acc.y += v.y;
+        } else {
+            const uint32_t kb = (k & mask_ab) | ((k >> (nab + na)) << nab);
+            cmac(acc, A[ia + (ka << st.a_cb)], B[ib + (kb << st.b_cb)]);
+        }
     }
     return acc;
 }
 
-__global__ void __launch_bounds__(256) fused_program_kernel(LaunchArgs a, int warps_per_item) {
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Bulk asynchronous copy (TMA engine) of `bytes` (a multiple of 16, both addresses 16-byte
+// aligned) from global to shared memory, completing on the mbarrier at `bar`.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// Waits for phase `parity` of the mbarrier, giving up after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit) {
+    for (uint32_t i = 0; i < limit; i++) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+constexpr uint32_t kWaitPolls = 1u << 20;
+
+// The work of one lane in one phase: its step, operand bases and entry stride.
+struct LaneWork {
+    FusedStep st;
+    const float2 *A, *B;
+    float2 *C;
+    const uint32_t *tab;
+    uint32_t sub, cnt;
+    bool active;
+};
+
+template <bool STAGED>
+__device__ __forceinline__ LaneWork lane_work(uint32_t m, const FusedStep *steps, const uint32_t *tabs,
+                                              const float2 *ldata, const uint32_t *lbase, float2 *arena) {
+    LaneWork w;
+    w.active = m != 0xffffffffu;
+    if (!w.active) return w;
+    w.st = steps[m & 0xfffu];
+    w.sub = (m >> 12) & 0x3ffu;
+    w.cnt = m >> 22;
+    const uint32_t flags = w.st.flags;
+    w.A = (flags & kStepALeaf) ? ldata + lbase[w.st.a_off] : arena + w.st.a_off;
+    w.B = (flags & kStepUnary) ? w.A : ((flags & kStepBLeaf) ? ldata + lbase[w.st.b_off] : arena + w.st.b_off);
+    w.C = arena + w.st.c_off;
+    w.tab = tabs + w.st.tab_off;
+    return w;
+}
+
+// The lane's entries of its step, with the summed-index loop unrolled by case.
+__device__ __forceinline__ void run_lane_work(const LaneWork &w) {
+    const uint32_t n_out = 1u << w.st.rc;
+    const bool unary = w.st.flags & kStepUnary;
+    const float2 *__restrict__ A = w.A;
+    const float2 *__restrict__ B = w.B;
+    const uint32_t ka0 = w.st.koff_a[0], ka1 = w.st.koff_a[1], kb0 = w.st.koff_b[0], kb1 = w.st.koff_b[1];
+    if (!unary && w.st.nk == 0) {
+        for (uint32_t c = w.sub; c < n_out; c += w.cnt) {
+            const uint32_t e = w.tab[c];
+            const float2 a = A[(e & 0xffffu) + ka0], b = B[(e >> 16) + kb0];
+            w.C[c] = make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+        }
+    } else if (!unary && w.st.nk == 1) {
+        for (uint32_t c = w.sub; c < n_out; c += w.cnt) {
+            const uint32_t e = w.tab[c], ia = e & 0xffffu, ib = e >> 16;
+            const float2 a0 = A[ia + ka0], b0 = B[ib + kb0], a1 = A[ia + ka1], b1 = B[ib + kb1];
+            float2 acc = make_float2(0.f, 0.f);
+            cmac(acc, a0, b0);
+            cmac(acc, a1, b1);
+            w.C[c] = acc;
+        }
+    } else {
+        for (uint32_t c = w.sub; c < n_out; c += w.cnt) w.C[c] = fused_entry(w.st, w.tab[c], A, B, unary);
+    }
+}
+
+// STAGED: the fused steps with their tables and lane maps, the leaf data and the leaf
+// table are copied into shared memory once per CTA by the TMA engine, and every operand
+// access is a shared-memory access; otherwise the program is read from global memory.
+// Header fields are read once into registers. Each phase's lane work is prepared one
+// phase ahead, so a phase's critical path is its operand loads, FMAs, store and barrier.
+template <bool STAGED>
+__global__ void __launch_bounds__(512) fused_program_kernel(LaunchArgs a, int warps_per_item) {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(8) uint64_t stage_bar;
     const unsigned char *img = a.image;
     const DevProgram *P = reinterpret_cast<const DevProgram *>(img);
+    const uint64_t steps_off = P->fused_steps_off, tab_off = P->fused_tab_off, map_off = P->fused_lane_map_off;
+    const uint32_t n_phases = P->n_fused_phases, n_leaves = P->n_leaves;
+    const uint64_t final_off = P->final_off;
+    FinishInfo fin;
+    fin.zero_mask = P->zero_mask;
+    fin.sr = P->scalar_re;
+    fin.si = P->scalar_im;
+    fin.n_in = P->n_inner;
+    fin.present = P->final_present;
     const DevLeaf *leaves = reinterpret_cast<const DevLeaf *>(img + P->leaves_off);
-    const FusedStep *steps = reinterpret_cast<const FusedStep *>(img + P->fused_steps_off);
-    const uint32_t *tabs = reinterpret_cast<const uint32_t *>(img + P->fused_tab_off);
+    const FusedStep *steps = reinterpret_cast<const FusedStep *>(img + steps_off);
+    const uint32_t *tabs = reinterpret_cast<const uint32_t *>(img + tab_off);
+    const uint32_t *lane_map = reinterpret_cast<const uint32_t *>(img + map_off);
     const float2 *ldata = reinterpret_cast<const float2 *>(img + P->leaf_data_off);
     unsigned char *cur = smem;
-    if (a.smem_steps_bytes) {
-        // fused steps and their tables are contiguous in the image
-        copy_to_smem(cur, steps, a.smem_steps_bytes);
-        const size_t tab_rel = P->fused_tab_off - P->fused_steps_off;
-        steps = reinterpret_cast<const FusedStep *>(cur);
-        tabs = reinterpret_cast<const uint32_t *>(cur + tab_rel);
-        cur += a.smem_steps_bytes;
+    if (STAGED) {
+        const uint32_t s1 = a.smem_steps_bytes, s2 = s1 + a.smem_leaf_bytes, s3 = s2 + a.smem_leaves_bytes;
+        const uint32_t bar = smem_u32(&stage_bar);
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(s3) : "memory");
+            if (s1) bulk_g2s(smem_u32(smem), steps, s1, bar);
+            if (a.smem_leaf_bytes) bulk_g2s(smem_u32(smem + s1), ldata, a.smem_leaf_bytes, bar);
+            if (a.smem_leaves_bytes) bulk_g2s(smem_u32(smem + s2), leaves, a.smem_leaves_bytes, bar);
+        }
+        __syncthreads();
+        const bool ok = mbar_wait(bar, 0, kWaitPolls);
+        if (__syncthreads_or(!ok)) {          // the copy never completed: report and leave
+            if (threadIdx.x == 0) atomicCAS(a.status, 0u, 4u /* QVX_ETIMEOUT */);
+            mbar_wait(bar, 0, kWaitPolls);
+            return;
+        }
+        steps = reinterpret_cast<const FusedStep *>(smem);
+        tabs = reinterpret_cast<const uint32_t *>(smem + (tab_off - steps_off));
+        lane_map = reinterpret_cast<const uint32_t *>(smem + (map_off - steps_off));
+        ldata = reinterpret_cast<const float2 *>(smem + s1);
+        leaves = reinterpret_cast<const DevLeaf *>(smem + s2);
+        cur = smem + s3;
+    } else {
+        __syncthreads();
     }
-    if (a.smem_leaf_bytes) {
-        copy_to_smem(cur, ldata, a.smem_leaf_bytes);
-        ldata = reinterpret_cast<const float2 *>(cur);
-        cur += a.smem_leaf_bytes;
-    }
-    __syncthreads();
     const int lanes = 32 * warps_per_item;
     const int group = threadIdx.x / lanes;
     const int lane = threadIdx.x % lanes;
@@ -211,7 +354,6 @@ __global__ void __launch_bounds__(256) fused_program_kernel(LaunchArgs a, int wa
     float2 *arena = reinterpret_cast<float2 *>(mine + a.leaf_table_bytes);
     const int64_t n_items = a.batch * a.o_count;
     const unsigned bar_id = 1 + group;
-    const uint32_t n_leaves = P->n_leaves;
     for (int64_t item = (int64_t)blockIdx.x * groups + group; item < n_items;
          item += (int64_t)gridDim.x * groups) {
         const int64_t b = item / a.o_count;
@@ -220,19 +362,16 @@ __global__ void __launch_bounds__(256) fused_program_kernel(LaunchArgs a, int wa
         for (uint32_t l = lane; l < n_leaves; l += lanes) lbase[l] = leaf_base(leaves[l], x, o);
         if (warps_per_item == 1) __syncwarp();
         else asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(lanes));
-        for (uint32_t s = 0; s < a.n_steps; s++) {
-            const FusedStep st = steps[s];
-            const uint32_t flags = st.flags;
-            const bool unary = flags & kStepUnary;
-            const float2 *A = (flags & kStepALeaf) ? ldata + lbase[st.a_off] : arena + st.a_off;
-            const float2 *B = unary ? A : ((flags & kStepBLeaf) ? ldata + lbase[st.b_off] : arena + st.b_off);
-            float2 *C = arena + st.c_off;
-            const uint32_t *tab = tabs + st.tab_off;
-            for (uint32_t c = lane; c < (1u << st.rc); c += lanes) C[c] = fused_entry(st, tab[c], A, B, unary);
+        LaneWork w = lane_work<STAGED>(n_phases ? lane_map[lane] : 0xffffffffu, steps, tabs, ldata, lbase, arena);
+        for (uint32_t ph = 0; ph < n_phases; ph++) {
+            const uint32_t m_next = ph + 1 < n_phases ? lane_map[(ph + 1) * (uint32_t)lanes + (uint32_t)lane] : 0xffffffffu;
+            const LaneWork next = lane_work<STAGED>(m_next, steps, tabs, ldata, lbase, arena);
+            if (w.active) run_lane_work(w);
             if (warps_per_item == 1) __syncwarp();
             else asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(lanes));
+            w = next;
         }
-        if (lane < 32) finish_item(P, a, arena + P->final_off, b, o, lane, 32);
+        if (lane < 32) finish_item(fin, a, arena + final_off, b, o, lane, 32);
         if (warps_per_item == 1) __syncwarp();
         else asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(lanes));
     }
@@ -290,7 +429,7 @@ __global__ void finish_kernel(LaunchArgs a, int64_t item_begin, int64_t n_items,
     const int64_t item = item_begin + il;
     const int64_t b = item / a.o_count;
     const uint64_t o = (uint64_t)(a.o_begin + item % a.o_count);
-    finish_item(P, a, arenas + (uint64_t)il * a.arena_elems + P->final_off, b, o, threadIdx.x % 32, 32);
+    finish_item(finish_info(P), a, arenas + (uint64_t)il * a.arena_elems + P->final_off, b, o, threadIdx.x % 32, 32);
 }
 
 // ------------------------------------------------------------------ slice sum
@@ -468,22 +607,63 @@ cudaError_t launch_grad_sum(const unsigned char *image, const double2 *gpart, in
     return cudaGetLastError();
 }
 
+// The dynamic shared-memory limit is an attribute of the kernel function, shared by every
+// plan: raise it once per device to the most the device allows, never lower it.
 cudaError_t fused_prepare(size_t smem_bytes) {
-    return cudaFuncSetAttribute(fused_program_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_bytes);
+    static bool raised[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && raised[dev]) return cudaSuccess;
+    int optin = 0;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, fused_program_kernel<true>)) != cudaSuccess) return e;
+    const int limit = optin - (int)fa.sharedSizeBytes;
+    if ((size_t)limit < smem_bytes) return cudaErrorInvalidValue;
+    if ((e = cudaFuncSetAttribute(fused_program_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(fused_program_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit)) != cudaSuccess)
+        return e;
+    if (dev >= 0 && dev < 64) raised[dev] = true;
+    return cudaSuccess;
 }
 
-int fused_blocks_per_sm(int threads, size_t smem_bytes) {
+int fused_blocks_per_sm(int threads, size_t smem_bytes, bool staged) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_program_kernel, threads, smem_bytes) != cudaSuccess)
-        return 0;
-    return n;
+    cudaError_t e = staged ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_program_kernel<true>, threads, smem_bytes)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_program_kernel<false>, threads, smem_bytes);
+    return e == cudaSuccess ? n : 0;
+}
+
+bool fused_shape(const DevProgram *h, uint64_t arena_elems, int warps_per_item, LaunchArgs *a, size_t *shared,
+                 size_t *group, int *max_ipc) {
+    auto r16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+    const size_t kBudget = 220u << 10;   // dynamic shared memory per CTA
+    *group = r16((size_t)h->n_leaves * 4) + (size_t)arena_elems * 8;
+    if (h->fused_lanes != (uint32_t)(32 * warps_per_item)) return false;
+    const size_t steps_b = r16((size_t)(h->fused_lane_map_off - h->fused_steps_off) +
+                               (size_t)h->n_fused_phases * h->fused_lanes * 4);
+    const size_t leaf_b = r16((size_t)h->n_leaf_entries * 8);
+    const size_t leaves_b = r16((size_t)h->n_leaves * sizeof(DevLeaf));
+    size_t sh = steps_b + leaf_b + leaves_b;
+    if (sh + *group > kBudget) sh = 0;    // the program stays in global memory
+    if (sh + *group > kBudget) return false;
+    a->smem_steps_bytes = sh ? (uint32_t)steps_b : 0;
+    a->smem_leaf_bytes = sh ? (uint32_t)leaf_b : 0;
+    a->smem_leaves_bytes = sh ? (uint32_t)leaves_b : 0;
+    a->leaf_table_bytes = (uint32_t)r16((size_t)h->n_leaves * 4);
+    a->group_bytes = (uint32_t)*group;
+    *shared = sh;
+    *max_ipc = (int)std::max<size_t>(1, std::min<size_t>(std::max(1, 8 / warps_per_item), (kBudget - sh) / *group));
+    return true;
 }
 
 cudaError_t launch_fused(const LaunchArgs &a, int warps_per_item, int items_per_cta, int grid,
                          size_t smem_bytes, cudaStream_t s) {
     const int threads = 32 * warps_per_item * items_per_cta;
-    fused_program_kernel<<<grid, threads, smem_bytes, s>>>(a, warps_per_item);
+    if (a.smem_steps_bytes) fused_program_kernel<true><<<grid, threads, smem_bytes, s>>>(a, warps_per_item);
+    else fused_program_kernel<false><<<grid, threads, smem_bytes, s>>>(a, warps_per_item);
     return cudaGetLastError();
 }
 

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "device_program.h"
+
 namespace qvx {
 
 struct LaunchArgs {
@@ -19,9 +21,10 @@ struct LaunchArgs {
     unsigned int *status;           // device status word
     unsigned int *counter;          // CTAs finished (fused engine's final sum); zero between calls
     double *amps;                   // optional: 2 * batch FP64 amplitudes written by the fused engine
-    // fused engine shared-memory layout: [steps][leaf data][per group: leaf table, arena]
-    uint32_t smem_steps_bytes;      // 0: steps are read from global memory
-    uint32_t smem_leaf_bytes;       // 0: leaf data is read from global memory
+    // fused engine shared-memory layout: [steps][leaf data][leaf table][per group: leaf bases, arena]
+    uint32_t smem_steps_bytes;      // 0: the program is read from global memory
+    uint32_t smem_leaf_bytes;
+    uint32_t smem_leaves_bytes;
     uint32_t leaf_table_bytes;      // per group, 16-byte multiple
     uint32_t group_bytes;           // per group: leaf table + arena
 };
@@ -30,8 +33,13 @@ struct LaunchArgs {
 // a.amps is set, the last CTA to finish also adds the item partials (compensated FP64).
 cudaError_t launch_fused(const LaunchArgs &a, int warps_per_item, int items_per_cta, int grid,
                          size_t smem_bytes, cudaStream_t s);
-int fused_blocks_per_sm(int threads, size_t smem_bytes);
+int fused_blocks_per_sm(int threads, size_t smem_bytes, bool staged);
 cudaError_t fused_prepare(size_t smem_bytes);
+// Shared-memory layout of a fused launch: fills a's smem fields, the bytes shared by the
+// CTA, the bytes per work-item group and the most groups a CTA can hold; false if one
+// group's arena does not fit.
+bool fused_shape(const DevProgram *h, uint64_t arena_elems, int warps_per_item, LaunchArgs *a, size_t *shared,
+                 size_t *group, int *max_ipc);
 
 // Stepwise engine: one launch per program step over `n_items` work items, tensors in a
 // global-memory arena per item.

@@ -63,7 +63,6 @@ qvx_status scratch_for_device(int dev, void **ptr) {
     return QVX_OK;
 }
 
-size_t r16(size_t x) { return (x + 15) & ~size_t(15); }
 size_t r256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
@@ -118,24 +117,15 @@ extern "C" qvx_status qvx_amplitude_noalloc(qvx_plan *plan, const uint64_t *bits
     a.amps = amps_dev;
     // shared-memory layout and grid, chosen as for the workspace entry points
     const int wpi = p.warps_per_item;
-    const size_t kBudget = 220u << 10;
-    const size_t group = r16((size_t)h->n_leaves * 4) + (size_t)a.arena_elems * 8;
-    size_t steps_b = r16((size_t)(h->fused_tab_off - h->fused_steps_off) + (size_t)h->n_tab_entries * 4);
-    size_t leaf_b = r16((size_t)h->n_leaf_entries * 8);
-    if (steps_b + leaf_b + 2 * group > kBudget) leaf_b = 0;
-    if (steps_b + leaf_b + 2 * group > kBudget) steps_b = 0;
-    if (steps_b + leaf_b + group > kBudget) return fail(QVX_EUNSUPPORTED, "fused kernel: arena exceeds shared memory");
-    const size_t shared = steps_b + leaf_b;
-    const int max_ipc = (int)std::max<size_t>(1, std::min<size_t>(8 / wpi, (kBudget - shared) / group));
-    a.smem_steps_bytes = (uint32_t)steps_b;
-    a.smem_leaf_bytes = (uint32_t)leaf_b;
-    a.leaf_table_bytes = (uint32_t)r16((size_t)h->n_leaves * 4);
-    a.group_bytes = (uint32_t)group;
+    size_t shared = 0, group = 0;
+    int max_ipc = 1;
+    if (!qvx::fused_shape(h, a.arena_elems, wpi, &a, &shared, &group, &max_ipc))
+        return fail(QVX_EUNSUPPORTED, "fused kernel: arena exceeds shared memory");
     const int64_t n_items = batch * n_outer;
     const int ipc = (int)std::max<int64_t>(1, std::min<int64_t>(max_ipc, (n_items + g_sms[dev] - 1) / g_sms[dev]));
     if ((e = qvx::fused_prepare(shared + (size_t)max_ipc * group)) != cudaSuccess)
         return cuda_fail(e, "fused kernel attributes");
-    const int per_sm = qvx::fused_blocks_per_sm(32 * wpi * ipc, shared + ipc * group);
+    const int per_sm = qvx::fused_blocks_per_sm(32 * wpi * ipc, shared + ipc * group, a.smem_steps_bytes != 0);
     if (per_sm < 1) return fail(QVX_EUNSUPPORTED, "fused kernel: no CTA fits on an SM");
     const int64_t ctas_needed = (n_items + ipc - 1) / ipc;
     const int grid = (int)std::min<int64_t>(ctas_needed, (int64_t)g_sms[dev] * per_sm);

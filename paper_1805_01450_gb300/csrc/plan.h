@@ -60,6 +60,7 @@ struct Plan {
     std::vector<HostTensor> leaves;             // stored leaves (may hold fixed modes)
     std::vector<PTensor> tensors;
     std::vector<PStep> steps;
+    std::vector<std::pair<int, int>> phases;    // [first, last) step ranges of independent steps
     int final_tensor = -1;
     int64_t arena_elems = 0;
     int max_rank = 0;

@@ -636,13 +636,49 @@ int64_t allocate_arena(Plan &p) {
         for (size_t i = 0; i < live.size(); i++)
             if (live[i].t == t) { live.erase(live.begin() + i); return; }
     };
-    for (size_t s = 0; s < p.steps.size(); s++) {
-        const PStep &st = p.steps[s];
-        alloc(st.c);
-        if (p.tensors[st.a].leaf < 0) release(st.a);
-        if (st.b >= 0 && p.tensors[st.b].leaf < 0) release(st.b);
+    // steps of one phase run concurrently: their outputs are placed while every operand of
+    // the phase is still live, and the operands are released after the phase
+    for (const auto &ph : p.phases) {
+        for (int s = ph.first; s < ph.second; s++) alloc(p.steps[s].c);
+        for (int s = ph.first; s < ph.second; s++) {
+            const PStep &st = p.steps[s];
+            if (p.tensors[st.a].leaf < 0) release(st.a);
+            if (st.b >= 0 && p.tensors[st.b].leaf < 0) release(st.b);
+        }
     }
     return peak;
+}
+
+// Orders the steps by level (1 + the deepest level among the steps producing their
+// operands) and groups each level into a phase of mutually independent steps.
+void schedule_levels(Plan &p) {
+    const size_t ns = p.steps.size();
+    std::vector<int> level(ns, 0);
+    for (size_t s = 0; s < ns; s++) {
+        const PStep &st = p.steps[s];
+        int lv = 0;
+        for (int t : {st.a, st.b})
+            if (t >= 0 && p.tensors[t].producer >= 0) lv = std::max(lv, level[p.tensors[t].producer] + 1);
+        level[s] = lv;
+    }
+    std::vector<int> idx(ns);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return level[x] < level[y]; });
+    std::vector<PStep> sorted(ns);
+    for (size_t i = 0; i < ns; i++) {
+        sorted[i] = p.steps[idx[i]];
+        p.tensors[sorted[i].c].producer = (int)i;
+        p.tensors[sorted[i].a].consumer = (int)i;
+        if (sorted[i].b >= 0) p.tensors[sorted[i].b].consumer = (int)i;
+    }
+    p.steps = std::move(sorted);
+    p.phases.clear();
+    for (size_t i = 0; i < ns;) {
+        size_t j = i;
+        while (j < ns && level[idx[j]] == level[idx[i]]) j++;
+        p.phases.push_back({(int)i, (int)j});
+        i = j;
+    }
 }
 
 void program_stats(Plan &p) {
@@ -905,10 +941,11 @@ bool serialize(Plan &p, std::string *err) {
             if (!make_runs(C.modes, B.modes, d.runs_b, &d.nb_runs, &d.b_cb)) { *err = "address map needs too many runs"; return false; }
         }
     }
-    // fused form: per-step tables of pext(c) for both operands (16-bit offsets)
+    // fused form: per-step tables of pext(c) for both operands (16-bit offsets), and per
+    // phase a map from each lane of a work item's group to the step it works on
     std::vector<FusedStep> fs(ds.size());
-    std::vector<uint32_t> tab;
-    bool fused_ok = p.arena_elems <= 65536;
+    std::vector<uint32_t> tab, lane_map;
+    bool fused_ok = p.arena_elems <= 65536 && ds.size() <= 4096;
     for (size_t s = 0; s < ds.size() && fused_ok; s++) {
         const DevStep &d = ds[s];
         FusedStep &f = fs[s];
@@ -923,6 +960,13 @@ bool serialize(Plan &p, std::string *err) {
         f.nk_b = d.nk_b;
         f.a_cb = d.a_cb;
         f.b_cb = d.b_cb;
+        f.nk = (uint8_t)(d.nk_ab + d.nk_a + d.nk_b);
+        for (uint32_t k = 0; k < 4 && k < (1u << f.nk); k++) {
+            const uint32_t ka = k & ((1u << (d.nk_ab + d.nk_a)) - 1u);
+            const uint32_t kb = (k & ((1u << d.nk_ab) - 1u)) | ((k >> (d.nk_ab + d.nk_a)) << d.nk_ab);
+            f.koff_a[k] = (uint16_t)(ka << d.a_cb);
+            f.koff_b[k] = (uint16_t)(kb << d.b_cb);
+        }
         f.tab_off = (uint32_t)tab.size();
         if (d.rc > 16 || d.a_cb + d.nk_ab + d.nk_a > 16 || d.b_cb + d.nk_ab + d.nk_b > 16) { fused_ok = false; break; }
         for (uint32_t c = 0; c < (1u << d.rc); c++) {
@@ -934,7 +978,38 @@ bool serialize(Plan &p, std::string *err) {
             tab.push_back(ia | (ib << 16));
         }
     }
-    if (!fused_ok) { fs.clear(); tab.clear(); }
+    // lanes per phase: at least one per step, the rest in proportion to the steps' work,
+    // never more than a step has output entries; a phase with more steps than lanes is
+    // split into several
+    const int lanes = 32 * p.warps_per_item;
+    int n_phases = 0;
+    for (const auto &ph : p.phases) {
+        if (!fused_ok) break;
+        for (int b0 = ph.first; b0 < ph.second; b0 += lanes) {
+            const int b1 = std::min(ph.second, b0 + lanes);
+            const int n = b1 - b0;
+            std::vector<int> cnt(n, 1);
+            std::vector<double> work(n);
+            for (int i = 0; i < n; i++) work[i] = std::ldexp(1.0, ds[b0 + i].rc + ds[b0 + i].nk_ab + ds[b0 + i].nk_a + ds[b0 + i].nk_b);
+            for (int left = lanes - n; left > 0; left--) {
+                int best = -1;
+                for (int i = 0; i < n; i++) {
+                    if (cnt[i] >= (1 << ds[b0 + i].rc) || cnt[i] >= 1023) continue;
+                    if (best < 0 || work[i] / cnt[i] > work[best] / cnt[best]) best = i;
+                }
+                if (best < 0) break;
+                cnt[best]++;
+            }
+            std::vector<uint32_t> row(lanes, 0xffffffffu);
+            int lane = 0;
+            for (int i = 0; i < n; i++)
+                for (int j = 0; j < cnt[i]; j++, lane++)
+                    row[lane] = (uint32_t)(b0 + i) | ((uint32_t)j << 12) | ((uint32_t)cnt[i] << 22);
+            lane_map.insert(lane_map.end(), row.begin(), row.end());
+            n_phases++;
+        }
+    }
+    if (!fused_ok) { fs.clear(); tab.clear(); lane_map.clear(); n_phases = 0; }
     DevProgram h;
     std::memset(&h, 0, sizeof(h));
     h.magic = kProgramMagic;
@@ -962,8 +1037,11 @@ bool serialize(Plan &p, std::string *err) {
         h.fused_steps_off = off;
         off = align256(off + fs.size() * sizeof(FusedStep));
         h.fused_tab_off = off;
-        off = align256(off + tab.size() * sizeof(uint32_t));
         h.n_tab_entries = tab.size();
+        h.fused_lane_map_off = h.fused_tab_off + tab.size() * sizeof(uint32_t);   // right after the tables
+        h.n_fused_phases = (uint32_t)n_phases;
+        h.fused_lanes = (uint32_t)lanes;
+        off = align256(off + (tab.size() + lane_map.size()) * sizeof(uint32_t));
     }
     // gradient program
     std::vector<uint32_t> csr;
@@ -1023,6 +1101,8 @@ bool serialize(Plan &p, std::string *err) {
     if (!fs.empty()) {
         std::memcpy(p.image.data() + h.fused_steps_off, fs.data(), fs.size() * sizeof(FusedStep));
         if (!tab.empty()) std::memcpy(p.image.data() + h.fused_tab_off, tab.data(), tab.size() * sizeof(uint32_t));
+        if (!lane_map.empty())
+            std::memcpy(p.image.data() + h.fused_lane_map_off, lane_map.data(), lane_map.size() * sizeof(uint32_t));
     }
     return true;
 }
@@ -1036,6 +1116,7 @@ bool build_program(Plan &p, std::string *err) {
     ProgramBuilder b(p, p.model);
     if (!b.run()) { *err = b.err; return false; }
     p.prog_scalar = p.model.scalar * b.factor;
+    schedule_levels(p);
     assign_layouts(p);
     p.arena_elems = allocate_arena(p);
     program_stats(p);
@@ -1155,7 +1236,7 @@ qvx_status make_plan(const qvx_circuit *c, const int32_t *order, int32_t n_order
     }
     // engine
     const int64_t arena_bytes = p->arena_elems * 8;
-    p->warps_per_item = std::max(1, std::min(4, opts.warps_per_item));
+    p->warps_per_item = std::max(1, std::min(16, opts.warps_per_item));
     if (opts.engine == QVX_ENGINE_AUTO)
         p->engine = arena_bytes <= 48 * 1024 ? QVX_ENGINE_FUSED : QVX_ENGINE_STEPWISE;
     else p->engine = opts.engine;

@@ -20,19 +20,20 @@ PROG = np.dtype([("magic", "<u4"), ("n_steps", "<u4"), ("n_leaves", "<u4"), ("pa
                  ("final_present", "<u4"), ("zero_mask", "<u8"), ("scalar_re", "<f8"),
                  ("scalar_im", "<f8"), ("n_outer", "<u8"), ("steps_off", "<u8"), ("leaves_off", "<u8"),
                  ("leaf_data_off", "<u8"), ("fused_steps_off", "<u8"), ("fused_tab_off", "<u8"),
-                 ("n_tab_entries", "<u8"), ("grad_steps_off", "<u8"), ("params_off", "<u8"),
+                 ("n_tab_entries", "<u8"), ("fused_lane_map_off", "<u8"), ("n_fused_phases", "<u4"),
+                 ("fused_lanes", "<u4"), ("grad_steps_off", "<u8"), ("params_off", "<u8"),
                  ("codes_off", "<u8"), ("deriv_data_off", "<u8"), ("thetas_off", "<u8"),
                  ("param_csr_off", "<u8"), ("n_grad_steps", "<u4"), ("n_param_leaves", "<u4"),
                  ("n_params", "<u4"), ("grad_pad", "<u4"), ("grad_arena_elems", "<u8"),
                  ("final_fwd_off", "<u8"), ("gslot_off", "<u8"), ("image_bytes", "<u8")])
 FSTEP = np.dtype([("a_off", "<u4"), ("b_off", "<u4"), ("c_off", "<u4"), ("tab_off", "<u4"), ("flags", "<u4"),
                   ("rc", "u1"), ("nk_ab", "u1"), ("nk_a", "u1"), ("nk_b", "u1"), ("a_cb", "u1"), ("b_cb", "u1"),
-                  ("pad0", "u1"), ("pad1", "u1"), ("pad2", "<u4")])
+                  ("nk", "u1"), ("pad1", "u1"), ("pad2", "<u4"), ("koff_a", "<u2", (4,)), ("koff_b", "<u2", (4,))])
 GOP = np.dtype([("off", "<u8"), ("kind", "<u4"), ("n_oruns", "u1"), ("n_kruns", "u1"), ("pad0", "u1"),
                 ("pad1", "u1"), ("oruns", RUN, (12,)), ("kruns", RUN, (12,))])
 GSTEP = np.dtype([("x", GOP), ("y", GOP), ("out_off", "<u8"), ("ro", "<u4"), ("nk", "<u4")])
 PLEAF = np.dtype([("leaf", "<u4"), ("param", "<u4"), ("n_stored", "<u4"), ("code_off", "<u4"), ("phi", "<f8")])
-assert STEP.itemsize == 136 and LEAF.itemsize == 40 and PROG.itemsize == 224 and FSTEP.itemsize == 32
+assert STEP.itemsize == 136 and LEAF.itemsize == 40 and PROG.itemsize == 240 and FSTEP.itemsize == 48
 assert GOP.itemsize == 112 and GSTEP.itemsize == 240 and PLEAF.itemsize == 24
 OP_ARENA, OP_LEAF, OP_DERIV, OP_ONE = 0, 1, 2, 3
 UNARY, A_LEAF, B_LEAF = 1, 2, 4
@@ -59,6 +60,9 @@ class Program:
             fo, to = int(h["fused_steps_off"]), int(h["fused_tab_off"])
             self.fsteps = np.frombuffer(buf[fo:fo + FSTEP.itemsize * int(h["n_steps"])].tobytes(), dtype=FSTEP)
             self.tab = np.frombuffer(buf[to:to + 4 * int(h["n_tab_entries"])].tobytes(), dtype="<u4").astype(np.int64)
+            lo, nl = int(h["fused_lane_map_off"]), int(h["n_fused_phases"]) * int(h["fused_lanes"])
+            self.lane_map = np.frombuffer(buf[lo:lo + 4 * nl].tobytes(), dtype="<u4").reshape(
+                int(h["n_fused_phases"]), int(h["fused_lanes"]))
         n = int(h["n_leaf_entries"])
         ld = np.frombuffer(buf[int(h["leaf_data_off"]):int(h["leaf_data_off"]) + 8 * n].tobytes(), dtype="<f4")
         self.leaf_data = ld[0::2].astype(np.float64) + 1j * ld[1::2].astype(np.float64)
@@ -109,12 +113,20 @@ class Program:
             A = operand(flags & A_LEAF, st["a_off"])
             unary = flags & UNARY
             B = None if unary else operand(flags & B_LEAF, st["b_off"])
+            nab_, na_, nb_ = int(st["nk_ab"]), int(st["nk_a"]), int(st["nk_b"])
             if fused:
                 fst = self.fsteps[si]
                 for f in ("a_off", "b_off", "c_off", "flags", "rc", "nk_ab", "nk_a", "nk_b", "a_cb", "b_cb"):
                     assert int(fst[f]) == int(st[f]), f
                 e = self.tab[int(fst["tab_off"]):int(fst["tab_off"]) + (1 << rc)]
                 ia, ib = e & 0xFFFF, (None if unary else e >> 16)
+                nk = int(fst["nk"])
+                assert nk == nab_ + na_ + nb_
+                for k in range(min(1 << nk, 4)):
+                    ka = k & ((1 << (nab_ + na_)) - 1)
+                    kb = (k & ((1 << nab_) - 1)) | ((k >> (nab_ + na_)) << nab_)
+                    assert int(fst["koff_a"][k]) == ka << int(st["a_cb"])
+                    assert int(fst["koff_b"][k]) == kb << int(st["b_cb"])
             else:
                 ia = _pext(c, st["runs_a"], int(st["na_runs"]))
                 ib = None if unary else _pext(c, st["runs_b"], int(st["nb_runs"]))
@@ -245,3 +257,44 @@ def grad(prog, x, thetas=None):
     for i, pl in enumerate(prog.pleaves):
         g[int(pl["param"])] += slots[i]
     return a, g
+
+
+def check_schedule(prog):
+    """The fused phases: every step in exactly one phase, each phase's steps independent
+    (no step reads another's output of the same phase, no output overlaps an operand or
+    output of its phase), each step's lanes contiguous and numbered 0..count-1."""
+    lanes = int(prog.h["fused_lanes"])
+    seen = {}
+    for ph, row in enumerate(prog.lane_map):
+        steps = {}
+        for lane, m in enumerate(row):
+            if m == 0xFFFFFFFF:
+                continue
+            s, sub, cnt = int(m) & 0xFFF, (int(m) >> 12) & 0x3FF, int(m) >> 22
+            steps.setdefault(s, []).append((lane, sub, cnt))
+        for s, ls in steps.items():
+            assert s not in seen
+            seen[s] = ph
+            cnt = ls[0][2]
+            assert [x[1] for x in ls] == list(range(cnt)) and all(x[2] == cnt for x in ls)
+            assert [x[0] for x in ls] == list(range(ls[0][0], ls[0][0] + cnt))
+        ranges = []
+        for s in steps:
+            st = prog.steps[s]
+            out = (int(st["c_off"]), int(st["c_off"]) + (1 << int(st["rc"])))
+            ins = []
+            for fl, key in ((2, "a_off"), (4, "b_off")):
+                if fl == 4 and int(st["flags"]) & 1:
+                    continue
+                if not int(st["flags"]) & fl:
+                    ins.append(int(st[key]))
+            ranges.append((out, ins))
+        for i, (out_i, _) in enumerate(ranges):
+            for j, (out_j, ins_j) in enumerate(ranges):
+                if i == j:
+                    continue
+                assert out_i[1] <= out_j[0] or out_j[1] <= out_i[0]       # outputs disjoint
+                for a in ins_j:
+                    assert not (out_i[0] <= a < out_i[1])                  # no read of a same-phase output
+    assert sorted(seen) == list(range(len(prog.steps)))
+    assert lanes % 32 == 0

@@ -132,3 +132,15 @@ def test_repeated_calls_reuse_workspace():
     first = _amps(p, [x])[0]
     for _ in range(5):
         assert _amps(p, [x])[0] == first
+
+
+def test_plans_with_different_shared_memory_interleave():
+    # the kernel's shared-memory limit is per function: a small plan launched between two
+    # launches of a large one must not shrink it
+    c = cg.grid_circuit(6, 6, 25, 2001)
+    x = cg.random_bitstrings(36, 1, 2002)[0]
+    ref = VE.exact_sum(VE.slice_terms(c, x, q.Plan(c, n_slices=12).order, q.Plan(c, n_slices=12).slices))
+    big = q.Plan(c, n_slices=12, inner_slices=7, warps_per_item=1)
+    small = q.Plan(c, n_slices=12, inner_slices=0, warps_per_item=16)
+    for p in (big, small, big, small):
+        assert abs(_amps(p, [x])[0] - ref) < tol(36)

@@ -12,7 +12,7 @@ from oracle import graph as GR
 from oracle import statevector as SV
 from oracle import ve as VE
 
-from _program_exec import Program
+from _program_exec import Program, check_schedule
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -114,6 +114,7 @@ def test_program_on_host_matches_oracle(name, maker, kw):
         assert abs(terms.sum() - psi[x]) < 1e-6 * 2 ** (-c.n_qubits / 2) + 1e-7
         if prog.fsteps is not None:
             assert np.array_equal(prog.slice_terms(x, fused=True), terms)
+            check_schedule(prog)
         if p.slices:
             ref = VE.slice_terms(c, x, p.order, p.slices)
             assert np.max(np.abs(terms - ref)) < 1e-6 * 2 ** (-c.n_qubits / 2)
@@ -169,3 +170,12 @@ def test_gradient_program_on_host_matches_oracle(name, maker, kw):
     a_ref, g_ref = SV.sv_adjoint_grad(SV.with_thetas(c, th), x)
     a, g = grad(prog, x, th)
     assert abs(a - a_ref) < 1e-6 and np.max(np.abs(g - g_ref)) < 1e-6
+
+
+@pytest.mark.parametrize("inner,wpi,merge", [(0, 1, 8), (3, 2, 10), (5, 4, 10), (5, 4, 0), (5, 8, 10), (6, 16, 10)])
+def test_fused_schedule_6x6x25(inner, wpi, merge):
+    c = cg.grid_circuit(6, 6, 25, 2001)
+    p = q.Plan(c, n_slices=12, inner_slices=inner, warps_per_item=wpi, host_merge_rank=merge)
+    prog = Program(p.image())
+    check_schedule(prog)
+    assert int(prog.h["fused_lanes"]) == 32 * wpi

@@ -26,9 +26,12 @@ sys.path.insert(0, ROOT)
 import circuitgen as cg  # noqa: E402
 
 WORKLOADS = {
-    # name: (rows, cols, depth, circuit seed, bitstring seed, sliced variables)
-    "grid6x6d25-k12": (6, 6, 25, 2001, 2002, 12),
-    "grid4x4d10": (4, 4, 10, 1001, 1002, 0),
+    # name: (kind, rows, cols, depth, circuit seed, bitstring seed, sliced variables, bitstrings per step)
+    "grid6x6d25-k12": ("grid", 6, 6, 25, 2001, 2002, 12, 1),
+    "grid4x4d10": ("grid", 4, 4, 10, 1001, 1002, 0, 1),
+    "grid7x7d30-b1024": ("grid", 7, 7, 30, 3001, 3002, 14, 1024),
+    "rot5x5d20-grad": ("rotation", 5, 5, 20, 4001, 4002, 6, 1),
+    "grid8x8d40-k16": ("grid", 8, 8, 40, 5001, 5002, 16, 1),
 }
 DEFAULT_WORKLOAD = "grid6x6d25-k12"
 METRIC = "amplitudes/s and complex TFLOP/s (% of GB300 peak) at |Δα|≤1e-5·2^-N/2 vs FP64"
@@ -45,7 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["qvx", "reference"], default="qvx")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
-    ap.add_argument("--batch", type=int, default=1, help="bitstrings per step")
+    ap.add_argument("--batch", type=int, default=None, help="bitstrings per step (workload default)")
     ap.add_argument("--inner-slices", type=int, default=None, help="fix the plan variant instead of autotuning")
     ap.add_argument("--warps-per-item", type=int, default=None)
     ap.add_argument("--engine", default="auto")
@@ -55,10 +58,15 @@ def parse():
 
 
 def workload(name, batch, rank):
-    r, c, d, cseed, bseed, k = WORKLOADS[name]
-    circ = cg.grid_circuit(r, c, d, cseed)
+    kind, r, c, d, cseed, bseed, k, b0 = WORKLOADS[name]
+    batch = b0 if batch is None else batch
+    circ = cg.grid_circuit(r, c, d, cseed) if kind == "grid" else cg.rotation_circuit(r, c, d, cseed)
     bits = cg.random_bitstrings(r * c, batch * (rank + 1), bseed)[batch * rank:]
     return circ, bits, k
+
+
+def is_grad(name):
+    return name.endswith("-grad")
 
 
 def measured_peaks():
@@ -150,6 +158,7 @@ def run_reference(args, rank, world):
     import numpy as np
     from oracle import ve as VE
     circ, bits, k = workload(args.workload, args.batch, 0)
+    args.batch = len(bits)
     import paper_1805_01450_gb300 as q
     plan = q.Plan(circ, n_slices=k)   # host planner only: the oracle takes its order and slices
     threads = os.cpu_count() or 1
@@ -203,23 +212,32 @@ def main():
 
     circ, bits_host, k = workload(args.workload, args.batch, rank)
     dev = torch.device("cuda", local)
+    grad = is_grad(args.workload)
     tuning = None
-    if args.inner_slices is None and args.warps_per_item is None and args.engine == "auto":
+    if args.inner_slices is None and args.warps_per_item is None and args.engine == "auto" and not grad:
         from paper_1805_01450_gb300.autotune import autotune
         plan, tuning = autotune(circ, bits_host, n_slices=k, device=dev)
     else:
         plan = q.Plan(circ, n_slices=k, inner_slices=-1 if args.inner_slices is None else args.inner_slices,
-                      warps_per_item=args.warps_per_item or 1, engine=args.engine)
+                      warps_per_item=args.warps_per_item or 1, engine=args.engine, gradient=grad)
     info = plan.info
     B = len(bits_host)
     bits = plan._bits(bits_host, dev)
     ws = plan.workspace(B, dev)
     out = torch.empty(2 * B, dtype=torch.float64, device=dev)
+    gout = torch.empty(2 * B * max(info["n_params"], 1), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
+    L = q.lib()
+    sptr = q._stream_ptr(stream)
 
     def step():
-        plan.amplitude(bits, workspace=ws, out=out, validate=False)
+        if grad:   # amplitude and every d alpha / d theta (one qvx_amplitude_grad call)
+            q._check(L.qvx_amplitude_grad(plan._h, q.ctypes.c_void_p(bits.data_ptr()), B, None, 0,
+                                          q.ctypes.c_void_p(out.data_ptr()), q.ctypes.c_void_p(gout.data_ptr()),
+                                          q.ctypes.c_void_p(ws.data_ptr()), ws.numel(), sptr))
+        else:
+            plan.amplitude(bits, workspace=ws, out=out, validate=False, stream=stream)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -241,9 +259,11 @@ def main():
     dev_ms = sum(a.elapsed_time(b) for a, b in ev)
     plan.check_status(ws)
 
-    # end to end through the public call: pinned host bitstrings in, amplitudes out
+    # end to end through the public call: pinned host bitstrings in, amplitudes (and
+    # gradients) out
     h_bits = torch.tensor([b - (1 << 64) if b >= 1 << 63 else b for b in bits_host], dtype=torch.int64).pin_memory()
     h_out = torch.empty(2 * B, dtype=torch.float64).pin_memory()
+    h_gout = torch.empty(gout.numel(), dtype=torch.float64).pin_memory()
     ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     barrier()
     torch.cuda.synchronize()
@@ -253,17 +273,22 @@ def main():
         bits.copy_(h_bits, non_blocking=True)
         step()
         h_out.copy_(out, non_blocking=True)
+        if grad:
+            h_gout.copy_(gout, non_blocking=True)
         ev2[i][1].record(stream)
     torch.cuda.synchronize()
     barrier()
     e2e_ms = sum(a.elapsed_time(b) for a, b in ev2)
 
-    # parity of what was timed, against the oracle's slice terms
+    # parity of what was timed, against the oracle's slice terms (first bitstring), when
+    # the oracle finishes in seconds
     from oracle import ve as VE
-    ref = VE.exact_sum(VE.slice_terms(circ, bits_host[0], plan.order, plan.slices))
-    got = complex(h_out[0].item(), h_out[1].item())
-    err = abs(got - ref)
     n = circ.n_qubits
+    err = None
+    if info["log2_cost"] + len(plan.slices) <= 26:
+        ref = VE.exact_sum(VE.slice_terms(circ, bits_host[0], plan.order, plan.slices))
+        got = complex(h_out[0].item(), h_out[1].item())
+        err = abs(got - ref)
 
     t = torch.tensor([dev_ms, e2e_ms], dtype=torch.float64, device=dev)
     if dist is not None:
@@ -277,12 +302,18 @@ def main():
     value = amps / (dev_ms / 1e3)
     e2e = amps / (e2e_ms / 1e3)
     ms_step = dev_ms / K
-    flops = info["flops_per_amplitude"] * B
-    algo_bytes = info["bytes_per_amplitude"] * B
+    flops = (info["grad_flops_per_amplitude"] if grad else info["flops_per_amplitude"]) * B
+    algo_bytes = (info["grad_bytes_per_amplitude"] if grad else info["bytes_per_amplitude"]) * B
     peak, peak_kind = measured_peaks()
     achieved = algo_bytes / (ms_step / 1e3) / 1e9
-    fused = info["engine"] == "fused"
-    launches_per_step = 1 if fused else info["n_steps"] + 2
+    fused = info["engine"] == "fused" and not grad
+    if grad:
+        kernel, launches_per_step = "grad_program_kernel", 4
+    elif fused:
+        kernel, launches_per_step = "fused_program_kernel", 1
+    else:
+        chunks = 1   # items in flight cover the call at the default budget
+        kernel, launches_per_step = "step_kernel", chunks * (info["n_steps"] + 1) + 1
     res = {
         "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -296,12 +327,14 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": NCU_TRAFFIC.get((args.workload, B)),
                      "peak_source": peak_kind,
-                     "kernel": "fused_program_kernel" if fused else "step_kernel",
+                     "kernel": kernel,
                      "algorithmic_bytes_per_launch": algo_bytes},
-        "e2e": {"value": e2e, "unit": "amplitudes/s", "h2d_bytes_per_step": 8 * B, "d2h_bytes_per_step": 16 * B},
+        "e2e": {"value": e2e, "unit": "amplitudes/s", "h2d_bytes_per_step": 8 * B,
+                "d2h_bytes_per_step": 16 * B + (8 * gout.numel() if grad else 0)},
         "gpu_launches": K * launches_per_step,
         "clocks": clocks.summary(),
         "autotune": None if tuning is None else [list(t) for t in tuning],
+        "gradients_per_amplitude": info["n_params"] if grad else 0,
         "plan": {"n_vars": info["n_vars"], "n_steps": info["n_steps"], "log2_cost": info["log2_cost"],
                  "log2_cost_unsliced": info["log2_cost_unsliced"], "max_rank": info["max_rank"],
                  "arena_bytes": info["arena_bytes"]},

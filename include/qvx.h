@@ -111,6 +111,8 @@ typedef struct {
     int32_t n_params;                /* 1 + largest param_index (gradient plans), else 0 */
     int32_t n_grad_steps;            /* contractions of the gradient program (0 if none) */
     int64_t grad_arena_bytes;        /* gradient program memory of one work item */
+    double grad_flops_per_amplitude; /* algorithmic real flops of the gradient program, all items */
+    double grad_bytes_per_amplitude; /* its algorithmic tensor bytes, all items */
 } qvx_plan_info;
 
 typedef struct qvx_plan qvx_plan;

@@ -54,7 +54,8 @@ class PlanInfo(ctypes.Structure):
                 ("log2_cost_unsliced", ctypes.c_double), ("flops_per_amplitude", ctypes.c_double),
                 ("bytes_per_amplitude", ctypes.c_double), ("arena_bytes", ctypes.c_int64),
                 ("device_image_bytes", ctypes.c_int64), ("n_params", ctypes.c_int32),
-                ("n_grad_steps", ctypes.c_int32), ("grad_arena_bytes", ctypes.c_int64)]
+                ("n_grad_steps", ctypes.c_int32), ("grad_arena_bytes", ctypes.c_int64),
+                ("grad_flops_per_amplitude", ctypes.c_double), ("grad_bytes_per_amplitude", ctypes.c_double)]
 
 
 _lib = None

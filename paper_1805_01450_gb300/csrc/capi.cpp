@@ -268,6 +268,8 @@ qvx_status qvx_plan_get_info(const qvx_plan *plan, qvx_plan_info *info) {
     info->n_params = p.n_params;
     info->n_grad_steps = (int32_t)p.grad_steps.size();
     info->grad_arena_bytes = p.grad_arena_elems * 8;
+    info->grad_flops_per_amplitude = p.grad_flops_per_item * (double)info->n_items_per_bitstring;
+    info->grad_bytes_per_amplitude = p.grad_bytes_per_item * (double)info->n_items_per_bitstring;
     return QVX_OK;
 }
 

@@ -271,14 +271,37 @@ __device__ __forceinline__ void run_lane_work(const LaneWork &w) {
     const float2 *__restrict__ A = w.A;
     const float2 *__restrict__ B = w.B;
     const uint32_t ka0 = w.st.koff_a[0], ka1 = w.st.koff_a[1], kb0 = w.st.koff_b[0], kb1 = w.st.koff_b[1];
+    // two entries per iteration: independent loads and FMA chains overlap
     if (!unary && w.st.nk == 0) {
-        for (uint32_t c = w.sub; c < n_out; c += w.cnt) {
+        uint32_t c = w.sub;
+        for (; c + w.cnt < n_out; c += 2 * w.cnt) {
+            const uint32_t e0 = w.tab[c], e1 = w.tab[c + w.cnt];
+            const float2 a0 = A[(e0 & 0xffffu) + ka0], b0 = B[(e0 >> 16) + kb0];
+            const float2 a1 = A[(e1 & 0xffffu) + ka0], b1 = B[(e1 >> 16) + kb0];
+            w.C[c] = make_float2(a0.x * b0.x - a0.y * b0.y, a0.x * b0.y + a0.y * b0.x);
+            w.C[c + w.cnt] = make_float2(a1.x * b1.x - a1.y * b1.y, a1.x * b1.y + a1.y * b1.x);
+        }
+        if (c < n_out) {
             const uint32_t e = w.tab[c];
             const float2 a = A[(e & 0xffffu) + ka0], b = B[(e >> 16) + kb0];
             w.C[c] = make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
         }
     } else if (!unary && w.st.nk == 1) {
-        for (uint32_t c = w.sub; c < n_out; c += w.cnt) {
+        uint32_t c = w.sub;
+        for (; c + w.cnt < n_out; c += 2 * w.cnt) {
+            const uint32_t e0 = w.tab[c], e1 = w.tab[c + w.cnt];
+            const uint32_t ia0 = e0 & 0xffffu, ib0 = e0 >> 16, ia1 = e1 & 0xffffu, ib1 = e1 >> 16;
+            const float2 p0 = A[ia0 + ka0], q0 = B[ib0 + kb0], p1 = A[ia0 + ka1], q1 = B[ib0 + kb1];
+            const float2 r0 = A[ia1 + ka0], s0 = B[ib1 + kb0], r1 = A[ia1 + ka1], s1 = B[ib1 + kb1];
+            float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+            cmac(acc0, p0, q0);
+            cmac(acc1, r0, s0);
+            cmac(acc0, p1, q1);
+            cmac(acc1, r1, s1);
+            w.C[c] = acc0;
+            w.C[c + w.cnt] = acc1;
+        }
+        if (c < n_out) {
             const uint32_t e = w.tab[c], ia = e & 0xffffu, ib = e >> 16;
             const float2 a0 = A[ia + ka0], b0 = B[ib + kb0], a1 = A[ia + ka1], b1 = B[ib + kb1];
             float2 acc = make_float2(0.f, 0.f);

@@ -75,6 +75,7 @@ struct Plan {
     int64_t grad_arena_elems = 0;
     int64_t grad_final_off = 0, grad_gslot_off = 0;
     std::vector<int> grad_param_leaves;        // leaf indices of the parametrised leaves
+    double grad_flops_per_item = 0, grad_bytes_per_item = 0;
 };
 
 // planner.cpp

@@ -788,8 +788,14 @@ bool build_grad_program(Plan &p, const std::vector<int> &dev_leaf, std::string *
         else { o.kind = kOpArena; o.off = (uint64_t)fo[t]; }
         return map_runs(out, T.modes, o.oruns, &o.n_oruns) && map_runs(S, T.modes, o.kruns, &o.n_kruns);
     };
+    p.grad_flops_per_item = 0;
+    p.grad_bytes_per_item = 0;
     auto emit = [&](int64_t out_off, const std::vector<int> &out, int x, bool xadj, int y, bool yadj,
                     const std::vector<int> &S) {
+        p.grad_flops_per_item += 8.0 * std::ldexp(1.0, (int)(out.size() + S.size()));
+        p.grad_bytes_per_item += 8.0 * std::ldexp(1.0, (int)out.size());
+        for (int t : {x, y})
+            if (t >= 0) p.grad_bytes_per_item += 8.0 * std::ldexp(1.0, (int)p.tensors[t].modes.size());
         GenStep g;
         std::memset(&g, 0, sizeof(g));
         g.out_off = (uint64_t)out_off;
@@ -848,6 +854,8 @@ bool build_grad_program(Plan &p, const std::vector<int> &dev_leaf, std::string *
             return false;
         }
         g.y.kind = kOpDeriv;
+        p.grad_flops_per_item += 8.0 * std::ldexp(1.0, (int)g.nk);
+        p.grad_bytes_per_item += 16.0 * std::ldexp(1.0, (int)g.nk) + 8.0;
         p.grad_steps.push_back(g);
         p.grad_param_leaves.push_back(p.tensors[t].leaf);
     }

@@ -37,8 +37,8 @@ DEFAULT_WORKLOAD = "grid6x6d25-k12"
 METRIC = "amplitudes/s and complex TFLOP/s (% of GB300 peak) at |Δα|≤1e-5·2^-N/2 vs FP64"
 L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the fused kernel, from one ncu
-# capture of this workload; None until captured for the current kernel.
-NCU_TRAFFIC = {}
+# capture of this workload with the current kernel (profiles/ holds the summary).
+NCU_TRAFFIC = {("grid6x6d25-k12", 1): 140800.0}
 
 
 def parse():

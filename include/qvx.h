@@ -168,6 +168,14 @@ qvx_status qvx_amplitude(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t
                          double *amps_dev, void *workspace_dev, size_t workspace_bytes,
                          void *stream);
 
+/* qvx_amplitude with the bitstrings and amplitudes in HOST memory; returns once the
+ * amplitudes are in amps_host (it synchronises `stream`). Page-locked buffers
+ * (cudaHostAlloc/cudaHostRegister, e.g. torch's pin_memory) are read and written by the
+ * kernels directly, with no separate copy; pageable buffers are staged through the
+ * workspace with cudaMemcpyAsync. Bitstrings with bits at or above n_qubits: QVX_EINVAL. */
+qvx_status qvx_amplitude_host(qvx_plan *plan, const uint64_t *bitstrings_host, int64_t batch, double *amps_host,
+                              void *workspace_dev, size_t workspace_bytes, void *stream);
+
 /* Sum of the slice terms s in [slice_begin, slice_begin + slice_count) only: the share of
  * one rank when the slices are split over several processes (Section 3.B.2). */
 qvx_status qvx_amplitude_slices(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch,

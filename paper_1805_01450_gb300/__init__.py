@@ -62,7 +62,7 @@ _lib = None
 EXPORTED = ("qvx_plan_opts_default", "qvx_graph_export", "qvx_plan_create", "qvx_plan_destroy",
             "qvx_plan_get_info", "qvx_plan_get_order", "qvx_plan_get_image", "qvx_workspace_size", "qvx_workspace_init",
             "qvx_amplitude", "qvx_amplitude_slices", "qvx_slice_terms", "qvx_workspace_status",
-            "qvx_last_error", "qvx_amplitude_noalloc", "qvx_amplitude_grad")
+            "qvx_last_error", "qvx_amplitude_noalloc", "qvx_amplitude_grad", "qvx_amplitude_host")
 
 
 def lib():
@@ -92,6 +92,7 @@ def lib():
         "qvx_last_error": (ctypes.c_char_p, []),
         "qvx_amplitude_noalloc": (ctypes.c_int, [P, P, i64, P, P]),
         "qvx_amplitude_grad": (ctypes.c_int, [P, P, i64, P, i32, P, P, P, ctypes.c_size_t, P]),
+        "qvx_amplitude_host": (ctypes.c_int, [P, P, i64, P, P, ctypes.c_size_t, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -287,6 +288,28 @@ class Plan:
         a = torch.view_as_complex(amps.view(n, 2))
         g = torch.view_as_complex(grad.view(n, max(npar, 1), 2))[:, :npar]
         return a, g
+
+    def amplitude_host(self, bitstrings, out=None, workspace=None, stream=None):
+        """<x|C|0> from host bitstrings into host memory (numpy complex128), blocking.
+        bitstrings: a CPU int64 tensor (pinned: read by the kernel directly) or a list;
+        out: an optional CPU float64 tensor of 2*batch (pinned: written directly)."""
+        import torch
+        if isinstance(bitstrings, torch.Tensor):
+            h = bitstrings
+        else:
+            vals = [int(b) for b in bitstrings]
+            h = torch.tensor([v - (1 << 64) if v >= (1 << 63) else v for v in vals], dtype=torch.int64)
+        if h.is_cuda or h.dtype != torch.int64:
+            raise TypeError("bitstrings must be a CPU int64 tensor or a list")
+        h = h.contiguous()
+        n = h.numel()
+        if out is None:
+            out = torch.empty(2 * n, dtype=torch.float64)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        ws = workspace if workspace is not None else self._ws_for(n, dev)
+        _check(lib().qvx_amplitude_host(self._h, ctypes.c_void_p(h.data_ptr()), n, ctypes.c_void_p(out.data_ptr()),
+                                        ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
+        return out[0::2].numpy() + 1j * out[1::2].numpy()
 
     def slice_terms(self, bitstrings, slice_begin=0, slice_count=None, workspace=None, stream=None):
         """The slice terms beta_s (complex64, [batch, slice_count]) of Section 3.B.2."""

@@ -25,10 +25,11 @@ qvx_status cuda_fail(cudaError_t e, const char *where) {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Workspace layout: [device image][status word, CTA counter][item partials][stepwise arenas]
-// and, for gradient plans, [derivative partials][gradient arenas]
+// Workspace layout: [device image][status word, CTA counter][host staging: bitstrings,
+// amplitudes][item partials][stepwise arenas] and, for gradient plans, [derivative
+// partials][gradient arenas]
 struct WsLayout {
-    size_t image, status, partials, arenas, total;
+    size_t image, status, stage_bits, stage_amps, partials, arenas, total;
     int64_t items_in_flight;
     size_t grad_partials = 0, grad_arenas = 0;
     int64_t grad_slots = 0;
@@ -39,7 +40,9 @@ WsLayout layout_of(const qvx::Plan &p, int64_t batch) {
     const int64_t n_outer = int64_t(1) << ((int)p.slices.size() - p.n_inner);
     w.image = 0;
     w.status = align256(p.image.size());
-    w.partials = w.status + 256;
+    w.stage_bits = w.status + 256;
+    w.stage_amps = align256(w.stage_bits + (size_t)std::max<int64_t>(batch, 1) * 8);
+    w.partials = align256(w.stage_amps + (size_t)std::max<int64_t>(batch, 1) * 16);
     w.arenas = align256(w.partials + (size_t)std::max<int64_t>(batch, 1) * (size_t)n_outer * 16);
     w.items_in_flight = 0;
     if (p.engine == QVX_ENGINE_STEPWISE) {
@@ -334,6 +337,51 @@ qvx_status qvx_amplitude_slices(qvx_plan *plan, const uint64_t *bitstrings_dev, 
     if ((e = qvx::launch_slice_sum(reinterpret_cast<const double2 *>(base + w.partials), batch, o_count,
                                    amps_dev, st)) != cudaSuccess)
         return cuda_fail(e, "slice sum launch");
+    return QVX_OK;
+}
+
+namespace {
+// Device-accessible address of a page-locked host buffer, or nullptr for pageable memory.
+const void *pinned_device_ptr(const void *host) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, host) != cudaSuccess) {
+        cudaGetLastError();   // pageable memory may report an error on older drivers: clear it
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+    return at.devicePointer;
+}
+}  // namespace
+
+qvx_status qvx_amplitude_host(qvx_plan *plan, const uint64_t *bitstrings_host, int64_t batch, double *amps_host,
+                              void *ws, size_t ws_bytes, void *stream) {
+    WsLayout w;
+    qvx_status s = check_ws(plan, batch, ws, ws_bytes, &w);
+    if (s != QVX_OK) return s;
+    if (batch == 0) return QVX_OK;
+    if (!bitstrings_host || !amps_host) return fail(QVX_EINVAL, "null host buffer");
+    const int n = plan->p.model.n_qubits;
+    for (int64_t b = 0; b < batch; b++)
+        if (n < 64 && (bitstrings_host[b] >> n) != 0) return fail(QVX_EINVAL, "bitstring has bits at or above n_qubits");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned char *base = static_cast<unsigned char *>(ws);
+    cudaError_t e;
+    const uint64_t *bits_dev = static_cast<const uint64_t *>(pinned_device_ptr(bitstrings_host));
+    if (!bits_dev) {
+        bits_dev = reinterpret_cast<const uint64_t *>(base + w.stage_bits);
+        if ((e = cudaMemcpyAsync(base + w.stage_bits, bitstrings_host, (size_t)batch * 8, cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess)
+            return cuda_fail(e, "bitstring upload");
+    }
+    double *amps_dev = static_cast<double *>(const_cast<void *>(pinned_device_ptr(amps_host)));
+    const bool stage_out = amps_dev == nullptr;
+    if (stage_out) amps_dev = reinterpret_cast<double *>(base + w.stage_amps);
+    s = qvx_amplitude(plan, bits_dev, batch, amps_dev, ws, ws_bytes, stream);
+    if (s != QVX_OK) return s;
+    if (stage_out && (e = cudaMemcpyAsync(amps_host, amps_dev, (size_t)batch * 16, cudaMemcpyDeviceToHost, st)) !=
+                         cudaSuccess)
+        return cuda_fail(e, "amplitude download");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
     return QVX_OK;
 }
 

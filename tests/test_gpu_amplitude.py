@@ -144,3 +144,22 @@ def test_plans_with_different_shared_memory_interleave():
     small = q.Plan(c, n_slices=12, inner_slices=0, warps_per_item=16)
     for p in (big, small, big, small):
         assert abs(_amps(p, [x])[0] - ref) < tol(36)
+
+
+@pytest.mark.parametrize("pin_in,pin_out", [(True, True), (False, False), (True, False), (False, True)])
+def test_host_buffer_entry_point(pin_in, pin_out):
+    c = cg.grid_circuit(6, 6, 25, 2001)
+    p = q.Plan(c, n_slices=12)
+    xs = cg.random_bitstrings(36, 3, 55)
+    ref = p.amplitude(xs).cpu().numpy()
+    h = torch.tensor(xs, dtype=torch.int64)
+    out = torch.full((6,), float("nan"), dtype=torch.float64)
+    if pin_in:
+        h = h.pin_memory()
+    if pin_out:
+        out = out.pin_memory()
+    for _ in range(2):
+        got = p.amplitude_host(h, out=out)
+        assert np.max(np.abs(got - ref)) < tol(36)
+    with pytest.raises(q.QvxError):
+        p.amplitude_host([1 << 40])

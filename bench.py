@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--inner-slices", type=int, default=None, help="fix the plan variant instead of autotuning")
     ap.add_argument("--warps-per-item", type=int, default=None)
     ap.add_argument("--engine", default="auto")
+    ap.add_argument("--sliced", type=int, default=None, help="override the workload's sliced-variable count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
     return ap.parse_args()
@@ -211,6 +212,8 @@ def main():
             dist.barrier()
 
     circ, bits_host, k = workload(args.workload, args.batch, rank)
+    if args.sliced is not None:
+        k = args.sliced
     dev = torch.device("cuda", local)
     grad = is_grad(args.workload)
     tuning = None

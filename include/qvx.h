@@ -79,7 +79,12 @@ typedef struct {
     const qvx_gate *gates; /* in time order */
 } qvx_circuit;
 
-typedef enum { QVX_ENGINE_AUTO = 0, QVX_ENGINE_FUSED = 1, QVX_ENGINE_STEPWISE = 2 } qvx_engine;
+/* FUSED: one warp group per work item, every tensor in shared memory (small programs).
+ * STEPWISE: one kernel launch per contraction over all work items in flight (global arenas).
+ * PERSISTENT: one cooperative launch per chunk of work items that walks the contractions
+ * level by level, with a grid-wide barrier (bounded wait) between levels (global arenas).
+ * AUTO: FUSED when a work item's tensors fit in shared memory, else PERSISTENT. */
+typedef enum { QVX_ENGINE_AUTO = 0, QVX_ENGINE_FUSED = 1, QVX_ENGINE_STEPWISE = 2, QVX_ENGINE_PERSISTENT = 3 } qvx_engine;
 
 typedef struct {
     int32_t n_slices;          /* sliced variables when the planner picks them; -1: as many as
@@ -113,6 +118,8 @@ typedef struct {
     int64_t grad_arena_bytes;        /* gradient program memory of one work item */
     double grad_flops_per_amplitude; /* algorithmic real flops of the gradient program, all items */
     double grad_bytes_per_amplitude; /* its algorithmic tensor bytes, all items */
+    int32_t n_tiled_steps;           /* contractions the stepwise engine runs as 32x32 tiles */
+    int32_t n_phases;                /* levels of mutually independent contractions */
 } qvx_plan_info;
 
 typedef struct qvx_plan qvx_plan;

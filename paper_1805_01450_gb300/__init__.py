@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libqvx.so")
 
 QVX_OK, QVX_EINVAL, QVX_ENOMEM, QVX_ECUDA, QVX_ETIMEOUT, QVX_EUNSUPPORTED, QVX_EDEVICE = range(7)
-ENGINES = {"auto": 0, "fused": 1, "stepwise": 2}
+ENGINES = {"auto": 0, "fused": 1, "stepwise": 2, "persistent": 3}
 ENGINE_NAMES = {v: k for k, v in ENGINES.items()}
 
 
@@ -55,7 +55,8 @@ class PlanInfo(ctypes.Structure):
                 ("bytes_per_amplitude", ctypes.c_double), ("arena_bytes", ctypes.c_int64),
                 ("device_image_bytes", ctypes.c_int64), ("n_params", ctypes.c_int32),
                 ("n_grad_steps", ctypes.c_int32), ("grad_arena_bytes", ctypes.c_int64),
-                ("grad_flops_per_amplitude", ctypes.c_double), ("grad_bytes_per_amplitude", ctypes.c_double)]
+                ("grad_flops_per_amplitude", ctypes.c_double), ("grad_bytes_per_amplitude", ctypes.c_double),
+                ("n_tiled_steps", ctypes.c_int32), ("n_phases", ctypes.c_int32)]
 
 
 _lib = None
@@ -288,6 +289,30 @@ class Plan:
         a = torch.view_as_complex(amps.view(n, 2))
         g = torch.view_as_complex(grad.view(n, max(npar, 1), 2))[:, :npar]
         return a, g
+
+    def graphed(self, bitstrings, workspace=None):
+        """Captures one amplitude call for these device bitstrings into a CUDA graph.
+
+        Returns (replay, out): replay() re-launches every kernel of the call with one graph
+        launch on the current stream; out (complex128, on the device) holds the amplitudes
+        after each replay. Change the bitstrings by writing into the same device tensor.
+        The call is made once outside the capture first, so the library's one-time launch
+        set-up is not captured."""
+        import torch
+        bits = self._bits(bitstrings)
+        n = bits.numel()
+        ws = workspace if workspace is not None else self._ws_for(n, bits.device)
+        out = torch.empty(2 * n, dtype=torch.float64, device=bits.device)
+        side = torch.cuda.Stream(device=bits.device)
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.amplitude(bits, workspace=ws, out=out, validate=False, stream=side)
+        torch.cuda.current_stream().wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.amplitude(bits, workspace=ws, out=out, validate=False)
+        self._graph_keep = (bits, ws)
+        return g.replay, torch.view_as_complex(out.view(n, 2))
 
     def amplitude_host(self, bitstrings, out=None, workspace=None, stream=None):
         """<x|C|0> from host bitstrings into host memory (numpy complex128), blocking.

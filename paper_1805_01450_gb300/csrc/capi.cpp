@@ -45,7 +45,7 @@ WsLayout layout_of(const qvx::Plan &p, int64_t batch) {
     w.partials = align256(w.stage_amps + (size_t)std::max<int64_t>(batch, 1) * 16);
     w.arenas = align256(w.partials + (size_t)std::max<int64_t>(batch, 1) * (size_t)n_outer * 16);
     w.items_in_flight = 0;
-    if (p.engine == QVX_ENGINE_STEPWISE) {
+    if (p.engine == QVX_ENGINE_STEPWISE || p.engine == QVX_ENGINE_PERSISTENT) {
         const int64_t arena_bytes = std::max<int64_t>(p.arena_elems, 4) * 8;
         const int64_t total_items = std::max<int64_t>(batch, 1) * n_outer;
         int64_t fit = std::max<int64_t>(1, p.opts.mem_budget_bytes / arena_bytes);
@@ -84,6 +84,14 @@ qvx_status check_ws(const qvx_plan *plan, int64_t batch, void *ws, size_t ws_byt
     if (ws_bytes < w->total)
         return fail(QVX_EINVAL, "workspace too small: need " + std::to_string(w->total) + " bytes");
     return QVX_OK;
+}
+
+struct PStepShape {
+    int nk;
+};
+PStepShape shape_of(const qvx::Plan &p, size_t s) {
+    const qvx::PStep &st = p.steps[s];
+    return PStepShape{(int)(st.k_ab.size() + st.k_a.size() + st.k_b.size())};
 }
 
 // Runs the program over outer slices [o_begin, o_begin + o_count) for every bitstring,
@@ -149,12 +157,35 @@ qvx_status run_items(qvx_plan *plan, const uint64_t *bits, int64_t batch, int64_
         return QVX_OK;
     }
     float2 *arenas = reinterpret_cast<float2 *>(base + w.arenas);
+    if (p.engine == QVX_ENGINE_PERSISTENT) {
+        int dev = -1;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+        if (dev != plan->persist_device) {
+            DeviceCaps caps;
+            qvx_status s = device_caps(&caps);
+            if (s != QVX_OK) return s;
+            const int per_sm = qvx::persistent_blocks_per_sm();
+            if (per_sm < 1) return fail(QVX_EUNSUPPORTED, "persistent kernel: no CTA fits on an SM");
+            plan->persist_grid = caps.sms * std::min(per_sm, 4);
+            plan->persist_device = dev;
+        }
+        unsigned *bar = reinterpret_cast<unsigned *>(base + w.status) + 2;   // [count, generation]
+        for (int64_t ib = 0; ib < n_items; ib += w.items_in_flight) {
+            const int64_t n = std::min<int64_t>(w.items_in_flight, n_items - ib);
+            if ((e = qvx::launch_persistent(a, ib, n, arenas, bar, bar + 1, plan->persist_grid, st)) != cudaSuccess)
+                return cuda_fail(e, "persistent kernel launch");
+        }
+        return QVX_OK;
+    }
     for (int64_t ib = 0; ib < n_items; ib += w.items_in_flight) {
         const int64_t n = std::min<int64_t>(w.items_in_flight, n_items - ib);
         for (size_t s = 0; s < p.steps.size(); s++) {
             const uint32_t rc = (uint32_t)p.tensors[p.steps[s].c].modes.size();
-            if ((e = qvx::launch_step(a, (uint32_t)s, ib, n, arenas, rc, st)) != cudaSuccess)
-                return cuda_fail(e, "step kernel launch");
+            const PStepShape sh = shape_of(p, s);
+            if (p.use_tiled[s]) e = qvx::launch_tiled_step(a, p.tiled[s], ib, n, arenas, st);
+            else if (sh.nk >= 5) e = qvx::launch_splitk_step(a, (uint32_t)s, ib, n, arenas, rc, st);
+            else e = qvx::launch_step(a, (uint32_t)s, ib, n, arenas, rc, st);
+            if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
         }
         if ((e = qvx::launch_finish_items(a, ib, n, arenas, st)) != cudaSuccess)
             return cuda_fail(e, "finish kernel launch");
@@ -272,6 +303,9 @@ qvx_status qvx_plan_get_info(const qvx_plan *plan, qvx_plan_info *info) {
     info->n_grad_steps = (int32_t)p.grad_steps.size();
     info->grad_arena_bytes = p.grad_arena_elems * 8;
     info->grad_flops_per_amplitude = p.grad_flops_per_item * (double)info->n_items_per_bitstring;
+    info->n_tiled_steps = 0;
+    for (char u : p.use_tiled) info->n_tiled_steps += u ? 1 : 0;
+    info->n_phases = (int32_t)p.phases.size();
     info->grad_bytes_per_amplitude = p.grad_bytes_per_item * (double)info->n_items_per_bitstring;
     return QVX_OK;
 }

@@ -86,6 +86,23 @@ struct ParamLeaf {
     double phi;
 };
 
+// A contraction C[b, m, n] = sum_k A[b, m, k] B[b, k, n] cut into groups of modes: b in
+// A, B and C; m in A and C; n in B and C; k summed, in A and B. Each group has a compact
+// index (its modes in C's order, k in A's order) and, per operand, runs that deposit that
+// index into the operand's layout. Used by the tiled kernel of the global-arena engines.
+constexpr int kTileRuns = 8;
+struct GroupMap {
+    uint32_t n;                    // runs
+    DevRun runs[kTileRuns];
+};
+struct TiledStep {
+    uint64_t a_off, b_off, c_off;  // arena offsets or leaf indices (flags as in DevStep)
+    uint32_t flags;
+    uint8_t nb, nm, nn, nk;        // group sizes in bits
+    uint32_t m_fast;               // 1: the lowest bit of C is an m mode
+    GroupMap a_b, a_m, a_k, b_b, b_n, b_k, c_b, c_m, c_n;
+};
+
 struct DevProgram {
     uint32_t magic;
     uint32_t n_steps, n_leaves, pad0;
@@ -108,6 +125,8 @@ struct DevProgram {
     uint64_t grad_arena_elems;
     uint64_t final_fwd_off;        // gradient arena offset of the final tensor
     uint64_t gslot_off;            // gradient arena offset of the per-leaf derivative slots
+    uint64_t level_phases_off;     // byte offset of n_level_phases + 1 step indices (phase starts)
+    uint32_t n_level_phases, level_pad;
     uint64_t image_bytes;
 };
 
@@ -118,7 +137,7 @@ constexpr uint32_t kProgramMagic = 0x51565831u;  // "QVX1"
 namespace qvx {
 static_assert(sizeof(DevStep) == 136, "DevStep layout");
 static_assert(sizeof(DevLeaf) == 40, "DevLeaf layout");
-static_assert(sizeof(DevProgram) == 240, "DevProgram layout");
+static_assert(sizeof(DevProgram) == 256, "DevProgram layout");
 static_assert(sizeof(GenOperand) == 112, "GenOperand layout");
 static_assert(sizeof(GenStep) == 240, "GenStep layout");
 static_assert(sizeof(ParamLeaf) == 24, "ParamLeaf layout");

@@ -111,6 +111,29 @@ __device__ void finish_item(const FinishInfo &P, const LaunchArgs &a, const floa
     }
 }
 
+// finish_item for a final tensor written by other CTAs (reads through L2), one warp.
+__device__ void finish_item_cg(const FinishInfo &P, const LaunchArgs &a, const float2 *fin, int64_t b, uint64_t o,
+                               int lane) {
+    const uint64_t x = a.bitstrings[b];
+    const bool zero = (x & P.zero_mask) != 0;
+    double2 acc = make_double2(0.0, 0.0);
+    for (uint32_t i = lane; i < (1u << P.n_in); i += 32) {
+        const int64_t s = (int64_t)((o << P.n_in) | i);
+        if (s < a.s_begin || s >= a.s_end) continue;
+        uint32_t fi = 0, bit = 0;
+        for (uint32_t j = 0; j < P.n_in; j++)
+            if ((P.present >> j) & 1u) fi |= ((i >> j) & 1u) << bit++;
+        const float2 t = zero ? make_float2(0.f, 0.f) : __ldcg(fin + fi);
+        const double tr = (double)t.x * P.sr - (double)t.y * P.si;
+        const double ti = (double)t.x * P.si + (double)t.y * P.sr;
+        acc.x += tr;
+        acc.y += ti;
+        if (a.terms) a.terms[b * (a.s_end - a.s_begin) + (s - a.s_begin)] = make_float2((float)tr, (float)ti);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) a.partials[b * a.o_count + (int64_t)(o - (uint64_t)a.o_begin)] = acc;
+}
+
 // ------------------------------------------------------------------ compensated sums
 // Neumaier's compensated addition, and Knuth's exact two-sum to merge (sum, compensation)
 // pairs, so partial sums from many threads combine without losing the compensation.
@@ -445,6 +468,273 @@ __global__ void step_kernel(LaunchArgs a, uint32_t s_idx, int64_t item_begin, in
     arena[st.c_off + c] = step_entry(st, c, A, B, unary);
 }
 
+// ------------------------------------------------------------------ persistent engine
+constexpr uint32_t kBarrierPolls = 1u << 24;   // x ~64 ns sleeps: about a second
+
+// Grid-wide barrier of a cooperative launch: thread 0 of each CTA arrives on a counter; the
+// last arrival resets it and advances the generation, the others poll the generation with
+// a bounded wait. False (and QVX_ETIMEOUT in the status word) if the wait ran out.
+__device__ bool grid_sync(unsigned *count, unsigned *gen, unsigned nblocks, unsigned *status) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = gen;
+        const unsigned g = *vgen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(count, 1u) == nblocks - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            unsigned i = 0;
+            while (*vgen == g) {
+                if (++i > kBarrierPolls) { ok = 0; break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (!ok) atomicCAS(status, 0u, 4u /* QVX_ETIMEOUT */);
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// One output entry of a generic step. Arena tensors are written once per launch into
+// regions of their own (no cache line is ever reused), so plain cached loads see them;
+// leaf operands go through the read-only path.
+__device__ __forceinline__ float2 persistent_entry(const DevStep &st, uint32_t c, const float2 *A, bool a_arena,
+                                                   const float2 *B, bool b_arena, bool unary) {
+    const uint32_t ia = pext_runs(c, st.runs_a, st.na_runs);
+    const uint32_t ib = unary ? 0u : pext_runs(c, st.runs_b, st.nb_runs);
+    const uint32_t nab = st.nk_ab, na = st.nk_a;
+    const uint32_t nk = nab + na + st.nk_b;
+    const uint32_t mask_ka = (1u << (nab + na)) - 1u, mask_ab = (1u << nab) - 1u;
+    float2 acc = make_float2(0.f, 0.f);
+    for (uint32_t k = 0; k < (1u << nk); k++) {
+        const uint32_t ka = k & mask_ka;
+        const float2 *pa = A + ia + (ka << st.a_cb);
+        const float2 a = a_arena ? *pa : __ldg(pa);
+        if (unary) {
+            acc.x += a.x;
+            acc.y += a.y;
+        } else {
+            const uint32_t kb = (k & mask_ab) | ((k >> (nab + na)) << nab);
+            const float2 *pb = B + ib + (kb << st.b_cb);
+            cmac(acc, a, b_arena ? *pb : __ldg(pb));
+        }
+    }
+    return acc;
+}
+
+// All contractions of a chunk of work items in one cooperative launch: phase by phase;
+// within a phase the CTAs sweep each step's (item, entry) space with a grid-stride loop
+// (the step's descriptor staged once in shared memory), a grid barrier separates phases,
+// then each item's final tensor is summed into its partial.
+__global__ void __launch_bounds__(256) persistent_program_kernel(LaunchArgs a, int64_t item_begin, int64_t n_items,
+                                                                 float2 *arenas, unsigned *bar_count, unsigned *bar_gen) {
+    __shared__ __align__(16) DevStep sd;
+    const unsigned char *img = a.image;
+    const DevProgram *P = reinterpret_cast<const DevProgram *>(img);
+    const DevStep *steps = reinterpret_cast<const DevStep *>(img + P->steps_off);
+    const DevLeaf *leaves = reinterpret_cast<const DevLeaf *>(img + P->leaves_off);
+    const float2 *ldata = reinterpret_cast<const float2 *>(img + P->leaf_data_off);
+    const uint32_t *phase_first = reinterpret_cast<const uint32_t *>(img + P->level_phases_off);
+    const uint32_t n_phases = P->n_level_phases;
+    const uint64_t arena_elems = a.arena_elems;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint32_t ph = 0; ph < n_phases; ph++) {
+        const uint32_t s0 = phase_first[ph], s1 = phase_first[ph + 1];
+        for (uint32_t s = s0; s < s1; s++) {
+            __syncthreads();   // the previous step's readers are done with sd
+            if (threadIdx.x < sizeof(DevStep) / 8)
+                reinterpret_cast<uint64_t *>(&sd)[threadIdx.x] = reinterpret_cast<const uint64_t *>(steps + s)[threadIdx.x];
+            __syncthreads();
+            const uint32_t rc = sd.rc, flags = sd.flags;
+            const bool unary = flags & kStepUnary;
+            const bool a_leaf = flags & kStepALeaf, b_leaf = flags & kStepBLeaf;
+            const uint64_t total = (uint64_t)n_items << rc;
+            // rotate the start so that small steps of one phase land on different CTAs
+            const uint64_t first = (((uint64_t)blockIdx.x + (uint64_t)(s - s0) * 37u) % gridDim.x) * blockDim.x + threadIdx.x;
+            for (uint64_t w = first; w < total; w += stride) {
+                const int64_t il = (int64_t)(w >> rc);
+                const uint32_t c = (uint32_t)(w & ((1ull << rc) - 1));
+                const int64_t item = item_begin + il;
+                const int64_t b = item / a.o_count;
+                const uint64_t o = (uint64_t)(a.o_begin + item % a.o_count);
+                float2 *arena = arenas + (uint64_t)il * arena_elems;
+                const float2 *A, *B;
+                if (a_leaf || (!unary && b_leaf)) {
+                    const uint64_t x = a.bitstrings[b];
+                    A = a_leaf ? ldata + leaf_base(leaves[sd.a_off], x, o) : arena + sd.a_off;
+                    B = unary ? A : (b_leaf ? ldata + leaf_base(leaves[sd.b_off], x, o) : arena + sd.b_off);
+                } else {
+                    A = arena + sd.a_off;
+                    B = unary ? A : arena + sd.b_off;
+                }
+                arena[sd.c_off + c] = persistent_entry(sd, c, A, !a_leaf, B, !b_leaf, unary);
+            }
+        }
+        if (!grid_sync(bar_count, bar_gen, gridDim.x, a.status)) return;
+    }
+    const FinishInfo fin = finish_info(P);
+    const int warps = blockDim.x / 32, warp = threadIdx.x / 32;
+    for (int64_t il = (int64_t)blockIdx.x * warps + warp; il < n_items; il += (int64_t)gridDim.x * warps) {
+        const int64_t item = item_begin + il;
+        const int64_t b = item / a.o_count;
+        const uint64_t o = (uint64_t)(a.o_begin + item % a.o_count);
+        // the final tensor was written by other CTAs: read it through L2
+        const float2 *fsrc = arenas + (uint64_t)il * arena_elems + P->final_off;
+        finish_item_cg(fin, a, fsrc, b, o, threadIdx.x % 32);
+    }
+}
+
+// ------------------------------------------------------------------ tiled contraction
+__device__ __forceinline__ uint32_t gpdep(uint32_t v, const GroupMap &g) {
+    uint32_t r = 0;
+    for (uint32_t i = 0; i < g.n; i++) r |= ((v >> g.runs[i].src) & ((1u << g.runs[i].len) - 1u)) << g.runs[i].dst;
+    return r;
+}
+
+constexpr int kTile = 32;     // at most 32 outputs along m and along n per CTA
+constexpr int kTileK = 16;    // summed entries staged per round
+
+// C[b, m, n] = sum_k A[b, m, k] B[b, k, n] for one TM x TN tile of (m, n) of one (item, b),
+// TM = min(32, 2^nm), TN = min(32, 2^nn): the A and B tiles are staged in shared memory and
+// each of the 256 threads accumulates up to four outputs. M_FAST: consecutive threads take
+// consecutive m (the lowest bit of C is an m mode) so a warp's stores are contiguous;
+// otherwise consecutive n.
+template <bool M_FAST>
+__global__ void __launch_bounds__(256) tiled_step_kernel(LaunchArgs a, TiledStep ts, int64_t item_begin,
+                                                         float2 *arenas) {
+    __shared__ float2 As[kTileK][kTile + 1];
+    __shared__ float2 Bs[kTileK][kTile + 1];
+    const unsigned char *img = a.image;
+    const DevProgram *P = reinterpret_cast<const DevProgram *>(img);
+    const uint32_t Mn = 1u << ts.nm, Nn = 1u << ts.nn, Kn = 1u << ts.nk;
+    const uint32_t TM = min(Mn, (uint32_t)kTile), TN = min(Nn, (uint32_t)kTile);
+    const uint32_t tiles_m = Mn / TM, tiles_n = Nn / TN;
+    uint64_t t = blockIdx.x;
+    const uint32_t tn = (uint32_t)(t % tiles_n);
+    t /= tiles_n;
+    const uint32_t tm = (uint32_t)(t % tiles_m);
+    t /= tiles_m;
+    const uint32_t bi = (uint32_t)(t & ((1ull << ts.nb) - 1));
+    const int64_t il = (int64_t)(t >> ts.nb);
+    const int64_t item = item_begin + il;
+    float2 *arena = arenas + (uint64_t)il * a.arena_elems;
+    const float2 *A, *B;
+    {
+        const DevLeaf *leaves = reinterpret_cast<const DevLeaf *>(img + P->leaves_off);
+        const float2 *ldata = reinterpret_cast<const float2 *>(img + P->leaf_data_off);
+        uint64_t x = 0, o = 0;
+        if (ts.flags & (kStepALeaf | kStepBLeaf)) {
+            x = a.bitstrings[item / a.o_count];
+            o = (uint64_t)(a.o_begin + item % a.o_count);
+        }
+        A = (ts.flags & kStepALeaf) ? ldata + leaf_base(leaves[ts.a_off], x, o) : arena + ts.a_off;
+        B = (ts.flags & kStepBLeaf) ? ldata + leaf_base(leaves[ts.b_off], x, o) : arena + ts.b_off;
+    }
+    A += gpdep(bi, ts.a_b);
+    B += gpdep(bi, ts.b_b);
+    float2 *C = arena + ts.c_off + gpdep(bi, ts.c_b);
+    const uint32_t m0 = tm * TM, n0 = tn * TN;
+    const uint32_t n_out = TM * TN;
+    float2 acc[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    for (uint32_t k0 = 0; k0 < Kn; k0 += kTileK) {
+        const uint32_t kc = min((uint32_t)kTileK, Kn - k0);
+        for (uint32_t idx = threadIdx.x; idx < TM * kc; idx += blockDim.x) {
+            const uint32_t i = idx % TM, kk = idx / TM;
+            As[kk][i] = A[gpdep(m0 + i, ts.a_m) + gpdep(k0 + kk, ts.a_k)];
+        }
+        for (uint32_t idx = threadIdx.x; idx < TN * kc; idx += blockDim.x) {
+            const uint32_t i = idx % TN, kk = idx / TN;
+            Bs[kk][i] = B[gpdep(n0 + i, ts.b_n) + gpdep(k0 + kk, ts.b_k)];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const uint32_t oi = threadIdx.x + 256u * q;
+            if (oi < n_out) {
+                const uint32_t mi = M_FAST ? oi % TM : oi / TN;
+                const uint32_t ni = M_FAST ? oi / TM : oi % TN;
+                for (uint32_t kk = 0; kk < kc; kk++) cmac(acc[q], As[kk][mi], Bs[kk][ni]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const uint32_t oi = threadIdx.x + 256u * q;
+        if (oi < n_out) {
+            const uint32_t mi = M_FAST ? oi % TM : oi / TN;
+            const uint32_t ni = M_FAST ? oi / TM : oi % TN;
+            C[gpdep(m0 + mi, ts.c_m) + gpdep(n0 + ni, ts.c_n)] = acc[q];
+        }
+    }
+}
+
+// A contraction with many summed entries and few outputs: 32 consecutive outputs per CTA,
+// the summed index split over the 8 warps, partial sums added through shared memory.
+__global__ void __launch_bounds__(256) splitk_step_kernel(LaunchArgs a, uint32_t s_idx, int64_t item_begin,
+                                                          int64_t n_items, float2 *arenas) {
+    __shared__ float2 part[8][33];
+    __shared__ __align__(16) DevStep sd;
+    const unsigned char *img = a.image;
+    const DevProgram *P = reinterpret_cast<const DevProgram *>(img);
+    if (threadIdx.x < sizeof(DevStep) / 8)
+        reinterpret_cast<uint64_t *>(&sd)[threadIdx.x] =
+            reinterpret_cast<const uint64_t *>(reinterpret_cast<const DevStep *>(img + P->steps_off) + s_idx)[threadIdx.x];
+    __syncthreads();
+    const uint32_t lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    const uint64_t w = (uint64_t)blockIdx.x * 32 + lane;
+    const bool valid = w < ((uint64_t)n_items << sd.rc);
+    float2 acc = make_float2(0.f, 0.f);
+    uint32_t c = 0;
+    float2 *arena = nullptr;
+    if (valid) {
+        const int64_t il = (int64_t)(w >> sd.rc);
+        c = (uint32_t)(w & ((1ull << sd.rc) - 1));
+        const int64_t item = item_begin + il;
+        arena = arenas + (uint64_t)il * a.arena_elems;
+        const DevLeaf *leaves = reinterpret_cast<const DevLeaf *>(img + P->leaves_off);
+        const float2 *ldata = reinterpret_cast<const float2 *>(img + P->leaf_data_off);
+        uint64_t x = 0, o = 0;
+        if (sd.flags & (kStepALeaf | kStepBLeaf)) {
+            x = a.bitstrings[item / a.o_count];
+            o = (uint64_t)(a.o_begin + item % a.o_count);
+        }
+        const bool unary = sd.flags & kStepUnary;
+        const float2 *A = (sd.flags & kStepALeaf) ? ldata + leaf_base(leaves[sd.a_off], x, o) : arena + sd.a_off;
+        const float2 *B = unary ? A : ((sd.flags & kStepBLeaf) ? ldata + leaf_base(leaves[sd.b_off], x, o) : arena + sd.b_off);
+        const uint32_t ia = pext_runs(c, sd.runs_a, sd.na_runs);
+        const uint32_t ib = unary ? 0u : pext_runs(c, sd.runs_b, sd.nb_runs);
+        const uint32_t nab = sd.nk_ab, na = sd.nk_a, nk = nab + na + sd.nk_b;
+        const uint32_t mask_ka = (1u << (nab + na)) - 1u, mask_ab = (1u << nab) - 1u;
+        for (uint32_t k = warp; k < (1u << nk); k += 8) {
+            const float2 av = A[ia + ((k & mask_ka) << sd.a_cb)];
+            if (unary) {
+                acc.x += av.x;
+                acc.y += av.y;
+            } else {
+                const uint32_t kb = (k & mask_ab) | ((k >> (nab + na)) << nab);
+                cmac(acc, av, B[ib + (kb << sd.b_cb)]);
+            }
+        }
+    }
+    part[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && valid) {
+        float2 s = part[0][lane];
+        for (int j = 1; j < 8; j++) {
+            s.x += part[j][lane].x;
+            s.y += part[j][lane].y;
+        }
+        arena[sd.c_off + c] = s;
+    }
+}
+
 __global__ void finish_kernel(LaunchArgs a, int64_t item_begin, int64_t n_items, const float2 *arenas) {
     const DevProgram *P = reinterpret_cast<const DevProgram *>(a.image);
     const int64_t il = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
@@ -697,6 +987,38 @@ cudaError_t launch_step(const LaunchArgs &a, uint32_t step, int64_t item_begin, 
     const uint64_t blocks = (total + threads - 1) / threads;
     step_kernel<<<(unsigned)blocks, threads, 0, s>>>(a, step, item_begin, n_items, arenas);
     return cudaGetLastError();
+}
+
+cudaError_t launch_splitk_step(const LaunchArgs &a, uint32_t step, int64_t item_begin, int64_t n_items,
+                               float2 *arenas, uint32_t rc, cudaStream_t s) {
+    const uint64_t blocks = (((uint64_t)n_items << rc) + 31) / 32;
+    if (blocks > 0x7fffffffull) return cudaErrorInvalidConfiguration;
+    splitk_step_kernel<<<(unsigned)blocks, 256, 0, s>>>(a, step, item_begin, n_items, arenas);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tiled_step(const LaunchArgs &a, const TiledStep &ts, int64_t item_begin, int64_t n_items,
+                              float2 *arenas, cudaStream_t s) {
+    const uint64_t tiles_m = (1ull << ts.nm) / std::min<uint64_t>(1ull << ts.nm, kTile);
+    const uint64_t tiles_n = (1ull << ts.nn) / std::min<uint64_t>(1ull << ts.nn, kTile);
+    const uint64_t blocks = ((uint64_t)n_items << ts.nb) * tiles_m * tiles_n;
+    if (blocks > 0x7fffffffull) return cudaErrorInvalidConfiguration;
+    if (ts.m_fast) tiled_step_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(a, ts, item_begin, arenas);
+    else tiled_step_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(a, ts, item_begin, arenas);
+    return cudaGetLastError();
+}
+
+int persistent_blocks_per_sm() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, persistent_program_kernel, 256, 0) != cudaSuccess) return 0;
+    return n;
+}
+
+cudaError_t launch_persistent(const LaunchArgs &a, int64_t item_begin, int64_t n_items, float2 *arenas,
+                              unsigned *bar_count, unsigned *bar_gen, int grid, cudaStream_t s) {
+    LaunchArgs aa = a;
+    void *args[] = {&aa, &item_begin, &n_items, &arenas, &bar_count, &bar_gen};
+    return cudaLaunchCooperativeKernel((const void *)persistent_program_kernel, dim3(grid), dim3(256), args, 0, s);
 }
 
 cudaError_t launch_finish_items(const LaunchArgs &a, int64_t item_begin, int64_t n_items,

@@ -8,4 +8,6 @@ struct qvx_plan {
     int launch_device = -1;
     int sms = 0;
     int ctas_per_sm[9] = {0};   // by work items per CTA
+    // persistent-engine grid, cached for the device it was computed on
+    int persist_device = -1, persist_grid = 0;
 };

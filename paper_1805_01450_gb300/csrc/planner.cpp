@@ -614,6 +614,19 @@ void assign_layouts(Plan &p) {
     }
 }
 
+// Every step output in a region of its own, 128-byte aligned: the persistent engine reads
+// tensors written by other SMs of the same launch through their L1 caches, which is safe
+// only if no cache line ever held other data.
+int64_t allocate_arena_unique(Plan &p) {
+    int64_t off = 0;
+    for (const PStep &st : p.steps) {
+        p.tensors[st.c].offset = off;
+        const int64_t len = int64_t(1) << p.tensors[st.c].modes.size();
+        off += (len + 15) & ~int64_t(15);
+    }
+    return off;
+}
+
 // First-fit arena allocation of the step outputs over their lifetimes.
 int64_t allocate_arena(Plan &p) {
     struct Block { int64_t off, len; int t; };
@@ -949,6 +962,49 @@ bool serialize(Plan &p, std::string *err) {
             if (!make_runs(C.modes, B.modes, d.runs_b, &d.nb_runs, &d.b_cb)) { *err = "address map needs too many runs"; return false; }
         }
     }
+    // tiled form of the large contractions (global-arena engines): output rank >= 10, two
+    // operands, every summed mode in both, at least 16 entries along m and along n
+    p.tiled.assign(p.steps.size(), TiledStep{});
+    p.use_tiled.assign(p.steps.size(), 0);
+    for (size_t s = 0; s < p.steps.size(); s++) {
+        const PStep &st = p.steps[s];
+        if (st.b < 0 || !st.k_a.empty() || !st.k_b.empty()) continue;
+        const std::vector<int> &LA = p.tensors[st.a].modes, &LB = p.tensors[st.b].modes, &LC = p.tensors[st.c].modes;
+        if (LC.size() < 10) continue;
+        std::vector<int> gb, gm, gn;
+        for (int v : LC) {
+            const bool ia = find_pos(LA, v) >= 0, ib = find_pos(LB, v) >= 0;
+            if (ia && ib) gb.push_back(v);
+            else if (ia) gm.push_back(v);
+            else gn.push_back(v);
+        }
+        if (gm.size() < 4 || gn.size() < 4) continue;   // 16 x 16 outputs at least per tile
+        TiledStep t;
+        std::memset(&t, 0, sizeof(t));
+        t.a_off = ds[s].a_off;
+        t.b_off = ds[s].b_off;
+        t.c_off = ds[s].c_off;
+        t.flags = ds[s].flags;
+        t.nb = (uint8_t)gb.size();
+        t.nm = (uint8_t)gm.size();
+        t.nn = (uint8_t)gn.size();
+        t.nk = (uint8_t)st.k_ab.size();
+        t.m_fast = find_pos(gm, LC[0]) >= 0 ? 1u : 0u;
+        bool ok = true;
+        auto gmap = [&](const std::vector<int> &g, const std::vector<int> &L, GroupMap &m) {
+            DevRun r[kMaxRuns];
+            uint8_t n = 0;
+            if (!map_runs(g, L, r, &n) || n > kTileRuns) { ok = false; return; }
+            m.n = n;
+            for (int i = 0; i < n; i++) m.runs[i] = r[i];
+        };
+        gmap(gb, LA, t.a_b); gmap(gm, LA, t.a_m); gmap(st.k_ab, LA, t.a_k);
+        gmap(gb, LB, t.b_b); gmap(gn, LB, t.b_n); gmap(st.k_ab, LB, t.b_k);
+        gmap(gb, LC, t.c_b); gmap(gm, LC, t.c_m); gmap(gn, LC, t.c_n);
+        if (!ok) continue;
+        p.tiled[s] = t;
+        p.use_tiled[s] = 1;
+    }
     // fused form: per-step tables of pext(c) for both operands (16-bit offsets), and per
     // phase a map from each lane of a work item's group to the step it works on
     std::vector<FusedStep> fs(ds.size());
@@ -1051,6 +1107,13 @@ bool serialize(Plan &p, std::string *err) {
         h.fused_lanes = (uint32_t)lanes;
         off = align256(off + (tab.size() + lane_map.size()) * sizeof(uint32_t));
     }
+    // level phases (first step of each phase, then the step count)
+    std::vector<uint32_t> level_first;
+    for (const auto &ph : p.phases) level_first.push_back((uint32_t)ph.first);
+    level_first.push_back((uint32_t)p.steps.size());
+    h.level_phases_off = off;
+    h.n_level_phases = (uint32_t)p.phases.size();
+    off = align256(off + level_first.size() * sizeof(uint32_t));
     // gradient program
     std::vector<uint32_t> csr;
     std::vector<double> thetas;
@@ -1094,6 +1157,7 @@ bool serialize(Plan &p, std::string *err) {
     }
     h.image_bytes = off;
     p.image.assign(off, 0);
+    std::memcpy(p.image.data() + h.level_phases_off, level_first.data(), level_first.size() * sizeof(uint32_t));
     if (p.opts.gradient) {
         unsigned char *img = p.image.data();
         if (!p.grad_steps.empty()) std::memcpy(img + h.grad_steps_off, p.grad_steps.data(), p.grad_steps.size() * sizeof(GenStep));
@@ -1246,17 +1310,20 @@ qvx_status make_plan(const qvx_circuit *c, const int32_t *order, int32_t n_order
     const int64_t arena_bytes = p->arena_elems * 8;
     p->warps_per_item = std::max(1, std::min(16, opts.warps_per_item));
     if (opts.engine == QVX_ENGINE_AUTO)
-        p->engine = arena_bytes <= 48 * 1024 ? QVX_ENGINE_FUSED : QVX_ENGINE_STEPWISE;
+        p->engine = arena_bytes <= 48 * 1024 ? QVX_ENGINE_FUSED : QVX_ENGINE_PERSISTENT;
     else p->engine = opts.engine;
     if (p->engine == QVX_ENGINE_FUSED && arena_bytes > 200 * 1024) {
         *err = "fused engine: arena of " + std::to_string(arena_bytes) + " bytes exceeds shared memory";
         return QVX_EUNSUPPORTED;
     }
+    if (p->engine == QVX_ENGINE_PERSISTENT) p->arena_elems = allocate_arena_unique(*p);
     if (!serialize(*p, err)) return QVX_EUNSUPPORTED;
     if (p->engine == QVX_ENGINE_FUSED &&
         reinterpret_cast<const DevProgram *>(p->image.data())->fused_steps_off == 0 && !p->steps.empty()) {
         if (opts.engine == QVX_ENGINE_FUSED) { *err = "fused engine: offsets exceed 16 bits"; return QVX_EUNSUPPORTED; }
-        p->engine = QVX_ENGINE_STEPWISE;
+        p->engine = QVX_ENGINE_PERSISTENT;
+        p->arena_elems = allocate_arena_unique(*p);
+        if (!serialize(*p, err)) return QVX_EUNSUPPORTED;
     }
     return QVX_OK;
 }

@@ -34,7 +34,7 @@ def _cuda():
     q.lib()
 
 
-@pytest.mark.parametrize("engine", ["fused", "stepwise"])
+@pytest.mark.parametrize("engine", ["fused", "stepwise", "persistent"])
 def test_worked_example_all_bitstrings(engine):
     c = cg.worked_example()
     psi = SV.final_state(c)
@@ -43,7 +43,8 @@ def test_worked_example_all_bitstrings(engine):
     assert np.max(np.abs(got - psi)) < tol(4)
 
 
-@pytest.mark.parametrize("engine,wpi", [("fused", 1), ("fused", 2), ("fused", 4), ("stepwise", 1)])
+@pytest.mark.parametrize("engine,wpi", [("fused", 1), ("fused", 2), ("fused", 4), ("fused", 8), ("fused", 16),
+                                        ("stepwise", 1), ("persistent", 1)])
 def test_4x4x10_batch(engine, wpi):
     c = cg.grid_circuit(4, 4, 10, 1001)
     psi = SV.final_state(c)
@@ -56,7 +57,8 @@ def test_4x4x10_batch(engine, wpi):
 @pytest.mark.parametrize("inner,wpi,engine,merge", [(-1, 1, "fused", 8), (0, 1, "fused", 8),
                                                     (2, 2, "fused", 8), (6, 4, "fused", 8),
                                                     (3, 1, "stepwise", 8), (4, 1, "fused", 0),
-                                                    (2, 1, "stepwise", 0)])
+                                                    (2, 1, "stepwise", 0), (4, 1, "persistent", 8),
+                                                    (0, 1, "persistent", 0)])
 def test_6x6x25_k12_full(inner, wpi, engine, merge):
     c = cg.grid_circuit(6, 6, 25, 2001)
     x = cg.random_bitstrings(36, 1, 2002)[0]
@@ -93,18 +95,37 @@ def test_rotation_circuit_stepwise_and_fused():
     c = cg.rotation_circuit(3, 3, 6, 4001)
     psi = SV.final_state(c)
     xs = cg.random_bitstrings(9, 40, 5)
-    for engine in ("fused", "stepwise"):
+    for engine in ("fused", "stepwise", "persistent"):
         p = q.Plan(c, n_slices=3, engine=engine)
         assert np.max(np.abs(_amps(p, xs) - psi[xs])) < tol(9)
 
 
-def test_5x5x20_stepwise_unsliced():
+@pytest.mark.parametrize("engine", ["stepwise", "persistent"])
+def test_5x5x20_global_arena_engines_unsliced(engine):
     c = cg.grid_circuit(5, 5, 20, 4001)
     xs = cg.random_bitstrings(25, 8, 6)
-    p = q.Plan(c, n_slices=0, engine="stepwise")
+    p = q.Plan(c, n_slices=0, engine=engine)
     got = _amps(p, xs)
     for g, x in zip(got, xs):
         assert abs(g - VE.ve_amplitude(c, x, p.order)) < tol(25)
+
+
+def test_7x7x30_persistent_chunks_and_sampled_slices():
+    # rank-17 tensors, 16 work items per bitstring, a memory budget that forces several
+    # chunks of items in flight; slice terms checked on a seeded sample of slices
+    c = cg.grid_circuit(7, 7, 30, 3001)
+    xs = cg.random_bitstrings(49, 3, 3002)
+    p = q.Plan(c, n_slices=8, inner_slices=4, engine="persistent", mem_budget_bytes=12 << 20)
+    assert p.info["max_rank"] >= 16
+    terms = p.slice_terms(xs).cpu().numpy()
+    ids = np.random.default_rng(5).choice(256, 12, replace=False)
+    for i, x in enumerate(xs):
+        ref = VE.slice_terms(c, x, p.order, p.slices, slice_ids=ids)
+        assert np.max(np.abs(terms[i, ids] - ref)) < tol(49)
+    amps = _amps(p, xs)
+    assert np.max(np.abs(amps - terms.sum(axis=1))) < tol(49)
+    ws = p._ws_for(3, torch.device("cuda"))
+    p.check_status(ws)
 
 
 def test_degenerate_circuits():
@@ -163,3 +184,36 @@ def test_host_buffer_entry_point(pin_in, pin_out):
         assert np.max(np.abs(got - ref)) < tol(36)
     with pytest.raises(q.QvxError):
         p.amplitude_host([1 << 40])
+
+
+@pytest.mark.parametrize("engine", ["fused", "stepwise", "persistent"])
+def test_cuda_graph_capture_and_replay(engine):
+    c = cg.grid_circuit(5, 5, 14, 9)
+    p = q.Plan(c, n_slices=4, engine=engine)
+    xs = cg.random_bitstrings(25, 2, 10)
+    bits = torch.tensor(xs, dtype=torch.int64, device="cuda")
+    replay, out = p.graphed(bits)
+    ref = lambda zs: np.array([VE.ve_amplitude(c, z, p.order, p.slices) for z in zs])
+    replay()
+    torch.cuda.synchronize()
+    assert np.max(np.abs(out.cpu().numpy() - ref(xs))) < tol(25)
+    ys = cg.random_bitstrings(25, 2, 11)
+    bits.copy_(torch.tensor(ys, dtype=torch.int64, device="cuda"))
+    replay()
+    torch.cuda.synchronize()
+    assert np.max(np.abs(out.cpu().numpy() - ref(ys))) < tol(25)
+
+
+@pytest.mark.parametrize("engine", ["stepwise", "persistent"])
+def test_7x7x30_large_contractions(engine):
+    # rank-17 outputs: the stepwise engine runs these as 32 x 32 tiles
+    c = cg.grid_circuit(7, 7, 30, 3001)
+    xs = cg.random_bitstrings(49, 2, 3003)
+    p = q.Plan(c, n_slices=8, inner_slices=4, engine=engine, mem_budget_bytes=40 << 20)
+    if engine == "stepwise":
+        assert p.info["n_tiled_steps"] >= 5
+    ids = np.random.default_rng(6).choice(256, 8, replace=False)
+    terms = p.slice_terms(xs).cpu().numpy()
+    for i, x in enumerate(xs):
+        ref = VE.slice_terms(c, x, p.order, p.slices, slice_ids=ids)
+        assert np.max(np.abs(terms[i, ids] - ref)) < tol(49)

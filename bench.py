@@ -30,7 +30,7 @@ WORKLOADS = {
     "grid6x6d25-k12": ("grid", 6, 6, 25, 2001, 2002, 12, 1),
     "grid4x4d10": ("grid", 4, 4, 10, 1001, 1002, 0, 1),
     "grid7x7d30-b1024": ("grid", 7, 7, 30, 3001, 3002, 14, 1024),
-    "rot5x5d20-grad": ("rotation", 5, 5, 20, 4001, 4002, 6, 1),
+    "rot5x5d20-grad": ("rotation", 5, 5, 20, 4001, 4002, 8, 1),
     "grid8x8d40-k16": ("grid", 8, 8, 40, 5001, 5002, 16, 1),
 }
 DEFAULT_WORKLOAD = "grid6x6d25-k12"

@@ -126,7 +126,9 @@ struct DevProgram {
     uint64_t final_fwd_off;        // gradient arena offset of the final tensor
     uint64_t gslot_off;            // gradient arena offset of the per-leaf derivative slots
     uint64_t level_phases_off;     // byte offset of n_level_phases + 1 step indices (phase starts)
-    uint32_t n_level_phases, level_pad;
+    uint32_t n_level_phases, n_grad_phases;
+    uint64_t grad_phases_off;      // n_grad_phases + 1 gradient-step indices (phase starts)
+    uint64_t grad_elem_off_off;    // per gradient step: its first entry inside its phase
     uint64_t image_bytes;
 };
 
@@ -137,7 +139,7 @@ constexpr uint32_t kProgramMagic = 0x51565831u;  // "QVX1"
 namespace qvx {
 static_assert(sizeof(DevStep) == 136, "DevStep layout");
 static_assert(sizeof(DevLeaf) == 40, "DevLeaf layout");
-static_assert(sizeof(DevProgram) == 256, "DevProgram layout");
+static_assert(sizeof(DevProgram) == 272, "DevProgram layout");
 static_assert(sizeof(GenOperand) == 112, "GenOperand layout");
 static_assert(sizeof(GenStep) == 240, "GenStep layout");
 static_assert(sizeof(ParamLeaf) == 24, "ParamLeaf layout");

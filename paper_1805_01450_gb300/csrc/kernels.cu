@@ -809,25 +809,37 @@ __global__ void __launch_bounds__(256) grad_program_kernel(GradArgs g) {
     float2 *arena = g.arenas + (uint64_t)blockIdx.x * g.arena_elems;
     const int64_t n_items = g.batch * g.o_count;
     const uint32_t npl = P->n_param_leaves;
+    const uint32_t n_phases = P->n_grad_phases;
+    const uint32_t *phase_first = reinterpret_cast<const uint32_t *>(img + P->grad_phases_off);
+    const uint32_t *elem_off = reinterpret_cast<const uint32_t *>(img + P->grad_elem_off_off);
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int64_t b = item / g.o_count;
         const uint64_t o = (uint64_t)(item % g.o_count);
         const uint64_t x = g.bitstrings[b];
-        for (uint32_t s = 0; s < P->n_grad_steps; s++) {
-            const GenStep &st = steps[s];
-            const float2 *X = gen_base(st.x, P, img, arena, x, o);
-            const float2 *Y = gen_base(st.y, P, img, arena, x, o);
-            float2 *out = arena + st.out_off;
-            for (uint32_t oi = threadIdx.x; oi < (1u << st.ro); oi += blockDim.x) {
+        // phase by phase: the entries of all steps of a phase are spread over the CTA
+        for (uint32_t ph = 0; ph < n_phases; ph++) {
+            const uint32_t s0 = phase_first[ph], s1 = phase_first[ph + 1];
+            const uint32_t total = elem_off[s1 - 1] + (1u << steps[s1 - 1].ro);
+            for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
+                uint32_t lo = s0, hi = s1 - 1;   // the last step whose first entry is <= e
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi + 1) >> 1;
+                    if (elem_off[mid] <= e) lo = mid;
+                    else hi = mid - 1;
+                }
+                const GenStep &st = steps[lo];
+                const uint32_t oi = e - elem_off[lo];
+                const float2 *X = gen_base(st.x, P, img, arena, x, o);
+                const float2 *Y = gen_base(st.y, P, img, arena, x, o);
                 const uint32_t ox = runs_pdep(oi, st.x.oruns, st.x.n_oruns);
                 const uint32_t oy = runs_pdep(oi, st.y.oruns, st.y.n_oruns);
                 float2 acc = make_float2(0.f, 0.f);
                 for (uint32_t k = 0; k < (1u << st.nk); k++) {
-                    const float2 a = X ? X[ox + runs_pdep(k, st.x.kruns, st.x.n_kruns)] : make_float2(1.f, 0.f);
-                    const float2 v = Y ? Y[oy + runs_pdep(k, st.y.kruns, st.y.n_kruns)] : make_float2(1.f, 0.f);
-                    cmac(acc, a, v);
+                    const float2 av = X ? X[ox + runs_pdep(k, st.x.kruns, st.x.n_kruns)] : make_float2(1.f, 0.f);
+                    const float2 bv = Y ? Y[oy + runs_pdep(k, st.y.kruns, st.y.n_kruns)] : make_float2(1.f, 0.f);
+                    cmac(acc, av, bv);
                 }
-                out[oi] = acc;
+                arena[st.out_off + oi] = acc;
             }
             __syncthreads();
         }

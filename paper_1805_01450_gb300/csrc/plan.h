@@ -78,6 +78,8 @@ struct Plan {
     int64_t grad_final_off = 0, grad_gslot_off = 0;
     std::vector<int> grad_param_leaves;        // leaf indices of the parametrised leaves
     double grad_flops_per_item = 0, grad_bytes_per_item = 0;
+    std::vector<uint32_t> grad_phase_first;    // phases of independent gradient steps (+ end)
+    std::vector<uint32_t> grad_elem_off;       // per gradient step: first entry inside its phase
 };
 
 // planner.cpp

@@ -826,6 +826,8 @@ bool build_grad_program(Plan &p, const std::vector<int> &dev_leaf, std::string *
         return r;
     };
     const std::string runs_err = "gradient program: address map needs too many runs";
+    p.grad_phase_first.clear();
+    for (const auto &ph : p.phases) p.grad_phase_first.push_back((uint32_t)ph.first);   // forward levels
     for (const PStep &st : p.steps) {   // forward, every output kept
         std::vector<int> S = st.k_ab;
         S.insert(S.end(), st.k_a.begin(), st.k_a.end());
@@ -833,13 +835,21 @@ bool build_grad_program(Plan &p, const std::vector<int> &dev_leaf, std::string *
         if (!emit(fo[st.c], p.tensors[st.c].modes, st.a, false, st.b, false, S)) { *err = runs_err; return false; }
     }
     const int F = p.final_tensor;
+    p.grad_phase_first.push_back((uint32_t)p.grad_steps.size());   // the adjoint of the final tensor
     if (need[F]) {
         std::vector<int> absent;   // inner slice modes the final tensor lacks: dummy summed modes
         for (int i = 0; i < p.n_inner; i++)
             if (find_pos(p.tensors[F].modes, p.slices[i]) < 0) absent.push_back(-1 - i);
         if (!emit(ao[F], p.tensors[F].modes, -1, false, -1, false, absent)) { *err = runs_err; return false; }
     }
+    // backward, level by level from the last: the adjoints of a level's operands depend only
+    // on adjoints of later levels
+    std::vector<int> level_of(p.steps.size(), 0);
+    for (size_t l = 0; l < p.phases.size(); l++)
+        for (int s = p.phases[l].first; s < p.phases[l].second; s++) level_of[s] = (int)l;
     for (int s = (int)p.steps.size() - 1; s >= 0; s--) {
+        if (s == (int)p.steps.size() - 1 || level_of[s] != level_of[s + 1])
+            p.grad_phase_first.push_back((uint32_t)p.grad_steps.size());
         const PStep &st = p.steps[s];
         if (!need[st.c]) continue;
         const std::vector<int> &LC = p.tensors[st.c].modes, &LA = p.tensors[st.a].modes;
@@ -854,6 +864,7 @@ bool build_grad_program(Plan &p, const std::vector<int> &dev_leaf, std::string *
         }
     }
     p.grad_param_leaves.clear();
+    p.grad_phase_first.push_back((uint32_t)p.grad_steps.size());   // the dot products
     for (size_t i = 0; i < pl.size(); i++) {   // d alpha / d theta per parametrised leaf
         const int t = pl[i];
         GenStep g;
@@ -871,6 +882,22 @@ bool build_grad_program(Plan &p, const std::vector<int> &dev_leaf, std::string *
         p.grad_bytes_per_item += 16.0 * std::ldexp(1.0, (int)g.nk) + 8.0;
         p.grad_steps.push_back(g);
         p.grad_param_leaves.push_back(p.tensors[t].leaf);
+    }
+    p.grad_phase_first.push_back((uint32_t)p.grad_steps.size());
+    // drop empty phases; element offsets of each step inside its phase
+    std::vector<uint32_t> firsts;
+    for (size_t i = 0; i + 1 < p.grad_phase_first.size(); i++)
+        if (p.grad_phase_first[i] < p.grad_phase_first[i + 1]) firsts.push_back(p.grad_phase_first[i]);
+    firsts.push_back((uint32_t)p.grad_steps.size());
+    p.grad_phase_first = firsts;
+    p.grad_elem_off.assign(p.grad_steps.size(), 0);
+    for (size_t i = 0; i + 1 < firsts.size(); i++) {
+        uint64_t acc = 0;
+        for (uint32_t g = firsts[i]; g < firsts[i + 1]; g++) {
+            if (acc > 0xffffffffull) { *err = "gradient program: phase too large"; return false; }
+            p.grad_elem_off[g] = (uint32_t)acc;
+            acc += uint64_t(1) << p.grad_steps[g].ro;
+        }
     }
     p.grad_arena_elems = off;
     p.grad_final_off = fo[F];
@@ -1154,6 +1181,11 @@ bool serialize(Plan &p, std::string *err) {
         off = align256(off + thetas.size() * sizeof(double));
         h.param_csr_off = off;
         off = align256(off + csr.size() * sizeof(uint32_t));
+        h.grad_phases_off = off;
+        h.n_grad_phases = (uint32_t)p.grad_phase_first.size() - 1;
+        off = align256(off + p.grad_phase_first.size() * sizeof(uint32_t));
+        h.grad_elem_off_off = off;
+        off = align256(off + p.grad_elem_off.size() * sizeof(uint32_t));
     }
     h.image_bytes = off;
     p.image.assign(off, 0);
@@ -1165,6 +1197,9 @@ bool serialize(Plan &p, std::string *err) {
         if (!codes.empty()) std::memcpy(img + h.codes_off, codes.data(), codes.size());
         if (!thetas.empty()) std::memcpy(img + h.thetas_off, thetas.data(), thetas.size() * sizeof(double));
         if (!csr.empty()) std::memcpy(img + h.param_csr_off, csr.data(), csr.size() * sizeof(uint32_t));
+        std::memcpy(img + h.grad_phases_off, p.grad_phase_first.data(), p.grad_phase_first.size() * sizeof(uint32_t));
+        if (!p.grad_elem_off.empty())
+            std::memcpy(img + h.grad_elem_off_off, p.grad_elem_off.data(), p.grad_elem_off.size() * sizeof(uint32_t));
     }
     std::memcpy(p.image.data(), &h, sizeof(h));
     if (!ds.empty()) std::memcpy(p.image.data() + h.steps_off, ds.data(), ds.size() * sizeof(DevStep));

@@ -25,7 +25,9 @@ PROG = np.dtype([("magic", "<u4"), ("n_steps", "<u4"), ("n_leaves", "<u4"), ("pa
                  ("codes_off", "<u8"), ("deriv_data_off", "<u8"), ("thetas_off", "<u8"),
                  ("param_csr_off", "<u8"), ("n_grad_steps", "<u4"), ("n_param_leaves", "<u4"),
                  ("n_params", "<u4"), ("grad_pad", "<u4"), ("grad_arena_elems", "<u8"),
-                 ("final_fwd_off", "<u8"), ("gslot_off", "<u8"), ("image_bytes", "<u8")])
+                 ("final_fwd_off", "<u8"), ("gslot_off", "<u8"), ("level_phases_off", "<u8"),
+                 ("n_level_phases", "<u4"), ("n_grad_phases", "<u4"), ("grad_phases_off", "<u8"),
+                 ("grad_elem_off_off", "<u8"), ("image_bytes", "<u8")])
 FSTEP = np.dtype([("a_off", "<u4"), ("b_off", "<u4"), ("c_off", "<u4"), ("tab_off", "<u4"), ("flags", "<u4"),
                   ("rc", "u1"), ("nk_ab", "u1"), ("nk_a", "u1"), ("nk_b", "u1"), ("a_cb", "u1"), ("b_cb", "u1"),
                   ("nk", "u1"), ("pad1", "u1"), ("pad2", "<u4"), ("koff_a", "<u2", (4,)), ("koff_b", "<u2", (4,))])
@@ -33,7 +35,7 @@ GOP = np.dtype([("off", "<u8"), ("kind", "<u4"), ("n_oruns", "u1"), ("n_kruns", 
                 ("pad1", "u1"), ("oruns", RUN, (12,)), ("kruns", RUN, (12,))])
 GSTEP = np.dtype([("x", GOP), ("y", GOP), ("out_off", "<u8"), ("ro", "<u4"), ("nk", "<u4")])
 PLEAF = np.dtype([("leaf", "<u4"), ("param", "<u4"), ("n_stored", "<u4"), ("code_off", "<u4"), ("phi", "<f8")])
-assert STEP.itemsize == 136 and LEAF.itemsize == 40 and PROG.itemsize == 240 and FSTEP.itemsize == 48
+assert STEP.itemsize == 136 and LEAF.itemsize == 40 and PROG.itemsize == 272 and FSTEP.itemsize == 48
 assert GOP.itemsize == 112 and GSTEP.itemsize == 240 and PLEAF.itemsize == 24
 OP_ARENA, OP_LEAF, OP_DERIV, OP_ONE = 0, 1, 2, 3
 UNARY, A_LEAF, B_LEAF = 1, 2, 4
@@ -77,6 +79,11 @@ class Program:
             to = int(h["thetas_off"])
             self.thetas = np.frombuffer(buf[to:to + 8 * int(h["n_params"])].tobytes(), dtype="<f8").copy()
             self.deriv_data = np.zeros_like(self.leaf_data)
+            gp, ng = int(h["grad_phases_off"]), int(h["n_grad_phases"])
+            self.grad_phases = np.frombuffer(buf[gp:gp + 4 * (ng + 1)].tobytes(), dtype="<u4").astype(np.int64)
+            ge = int(h["grad_elem_off_off"])
+            self.grad_elem_off = np.frombuffer(buf[ge:ge + 4 * int(h["n_grad_steps"])].tobytes(),
+                                               dtype="<u4").astype(np.int64)
 
     def _leaf_reader(self, li, x, o):
         L = self.leaves[li]
@@ -298,3 +305,30 @@ def check_schedule(prog):
                     assert not (out_i[0] <= a < out_i[1])                  # no read of a same-phase output
     assert sorted(seen) == list(range(len(prog.steps)))
     assert lanes % 32 == 0
+
+
+def check_grad_schedule(prog):
+    """Gradient phases cover the steps in order; entry offsets are each phase's prefix sums;
+    no step reads an arena range written by another step of its phase."""
+    ph = prog.grad_phases
+    assert ph[0] == 0 and ph[-1] == len(prog.gsteps) and np.all(np.diff(ph) > 0)
+    for i in range(len(ph) - 1):
+        acc, outs, reads = 0, [], []
+        for g in range(ph[i], ph[i + 1]):
+            st = prog.gsteps[g]
+            assert prog.grad_elem_off[g] == acc
+            acc += 1 << int(st["ro"])
+            o0 = int(st["out_off"])
+            outs.append((o0, o0 + (1 << int(st["ro"]))))
+            for op in (st["x"], st["y"]):
+                if int(op["kind"]) != OP_ARENA:
+                    continue
+                hi = _pext(np.array([(1 << int(st["ro"])) - 1]), op["oruns"], int(op["n_oruns"]))[0] + \
+                    _pext(np.array([(1 << int(st["nk"])) - 1]), op["kruns"], int(op["n_kruns"]))[0]
+                reads.append((int(op["off"]), int(op["off"]) + int(hi) + 1))
+        for a0, a1 in outs:
+            for b0, b1 in reads:
+                assert a1 <= b0 or b1 <= a0, "a step reads another step's output in the same phase"
+        outs.sort()
+        for (a0, a1), (b0, b1) in zip(outs, outs[1:]):
+            assert a1 <= b0

@@ -154,11 +154,12 @@ GRAD_CASES = [
 
 @pytest.mark.parametrize("name,maker,kw", GRAD_CASES, ids=[c[0] for c in GRAD_CASES])
 def test_gradient_program_on_host_matches_oracle(name, maker, kw):
-    from _program_exec import grad
+    from _program_exec import grad, check_grad_schedule
     c = maker()
     p = q.Plan(c, gradient=True, **kw)
     assert p.info["n_params"] == c.n_params
     prog = Program(p.image())
+    check_grad_schedule(prog)
     for x in [0] + cg.random_bitstrings(c.n_qubits, 2, 4):
         a_ref, g_ref = SV.sv_adjoint_grad(c, x)
         a, g = grad(prog, x)

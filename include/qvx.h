@@ -224,6 +224,14 @@ qvx_status qvx_amplitude_grad(qvx_plan *plan, const uint64_t *bitstrings_dev, in
                               double *grad_dev, void *workspace_dev, size_t workspace_bytes,
                               void *stream);
 
+/* Self-test of the library's bounded device waits (the paper has no counterpart): runs a
+ * one-CTA kernel whose grid-barrier wait and mbarrier wait can never complete, so both give
+ * up after `polls` polls (1..2^20) and report QVX_ETIMEOUT in the workspace status word.
+ * Returns QVX_ETIMEOUT when both waits reported it (as designed), QVX_OK otherwise; the
+ * status word is cleared again. Uses two scratch words of the workspace's status block. */
+qvx_status qvx_selftest_wait_timeout(const qvx_plan *plan, void *workspace_dev, size_t workspace_bytes,
+                                     uint32_t polls, void *stream);
+
 /* Synchronises `stream` and returns the device status word kept in the workspace
  * (QVX_OK, QVX_ETIMEOUT or QVX_EDEVICE), then clears it. */
 qvx_status qvx_workspace_status(const qvx_plan *plan, void *workspace_dev, void *stream);

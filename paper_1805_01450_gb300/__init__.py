@@ -63,7 +63,8 @@ _lib = None
 EXPORTED = ("qvx_plan_opts_default", "qvx_graph_export", "qvx_plan_create", "qvx_plan_destroy",
             "qvx_plan_get_info", "qvx_plan_get_order", "qvx_plan_get_image", "qvx_workspace_size", "qvx_workspace_init",
             "qvx_amplitude", "qvx_amplitude_slices", "qvx_slice_terms", "qvx_workspace_status",
-            "qvx_last_error", "qvx_amplitude_noalloc", "qvx_amplitude_grad", "qvx_amplitude_host")
+            "qvx_last_error", "qvx_amplitude_noalloc", "qvx_amplitude_grad", "qvx_amplitude_host",
+            "qvx_selftest_wait_timeout")
 
 
 def lib():
@@ -94,6 +95,7 @@ def lib():
         "qvx_amplitude_noalloc": (ctypes.c_int, [P, P, i64, P, P]),
         "qvx_amplitude_grad": (ctypes.c_int, [P, P, i64, P, i32, P, P, P, ctypes.c_size_t, P]),
         "qvx_amplitude_host": (ctypes.c_int, [P, P, i64, P, P, ctypes.c_size_t, P]),
+        "qvx_selftest_wait_timeout": (ctypes.c_int, [P, P, ctypes.c_size_t, ctypes.c_uint32, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -479,6 +479,30 @@ qvx_status qvx_amplitude_grad(qvx_plan *plan, const uint64_t *bitstrings_dev, in
     return QVX_OK;
 }
 
+qvx_status qvx_selftest_wait_timeout(const qvx_plan *plan, void *ws, size_t ws_bytes, uint32_t polls, void *stream) {
+    WsLayout w;
+    qvx_status s = check_ws(plan, 0, ws, ws_bytes, &w);
+    if (s != QVX_OK) return s;
+    if (polls < 1 || polls > (1u << 20)) return fail(QVX_EINVAL, "polls must be in [1, 2^20]");
+    unsigned char *base = static_cast<unsigned char *>(ws);
+    unsigned *status = reinterpret_cast<unsigned *>(base + w.status);
+    unsigned *words = status + 4;   // [count, generation] of the test barrier
+    unsigned *out = status + 6;     // which waits gave up
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(status + 4, 0, 4 * sizeof(unsigned), st)) != cudaSuccess) return cuda_fail(e, "memset");
+    if ((e = qvx::launch_wait_selftest(words, status, polls, out, st)) != cudaSuccess)
+        return cuda_fail(e, "self-test launch");
+    unsigned h[2] = {0, 0}, word = 0;
+    if ((e = cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cuda_fail(e, "read");
+    if ((e = cudaMemcpyAsync(&word, status, sizeof(word), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e, "read");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    if ((e = cudaMemset(status, 0, 8 * sizeof(unsigned))) != cudaSuccess) return cuda_fail(e, "status clear");
+    if (h[0] && h[1] && word == (unsigned)QVX_ETIMEOUT) return fail(QVX_ETIMEOUT, "both bounded waits gave up as designed");
+    return QVX_OK;
+}
+
 qvx_status qvx_workspace_status(const qvx_plan *plan, void *ws, void *stream) {
     WsLayout w;
     qvx_status s = check_ws(plan, 0, ws, (size_t)-1, &w);

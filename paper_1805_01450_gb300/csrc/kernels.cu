@@ -912,7 +912,38 @@ __global__ void grad_sum_kernel(const unsigned char *img, const double2 *gpart, 
     }
 }
 
+// Self-test of the bounded waits: a grid barrier for two CTAs run by one, and an mbarrier
+// whose phase never completes. Each wait must give up after `polls` polls; the kernel
+// records which did in out[0] (barrier) and out[1] (mbarrier) and sets the status word.
+__global__ void wait_selftest_kernel(unsigned *words, unsigned *status, uint32_t polls, unsigned *out) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    // grid barrier: one arrival of two, the generation never advances
+    unsigned *count = words, *gen = words + 1;
+    *count = 0;
+    const unsigned g = *(volatile unsigned *)gen;
+    atomicAdd(count, 1u);
+    unsigned i = 0;
+    bool gave_up = false;
+    while (*(volatile unsigned *)gen == g) {
+        if (++i > polls) { gave_up = true; break; }
+        __nanosleep(64);
+    }
+    out[0] = gave_up ? 1u : 0u;
+    atomicExch(count, 0u);
+    // mbarrier expecting one arrival that never comes
+    const uint32_t b = smem_u32(&bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+    out[1] = mbar_wait(b, 0, polls) ? 0u : 1u;
+    if (out[0] && out[1]) atomicCAS(status, 0u, 4u /* QVX_ETIMEOUT */);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_selftest(unsigned *words, unsigned *status, uint32_t polls, unsigned *out, cudaStream_t s) {
+    wait_selftest_kernel<<<1, 32, 0, s>>>(words, status, polls, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_set_params(unsigned char *image, uint32_t n_param_leaves, const double *thetas, cudaStream_t s) {
     if (n_param_leaves == 0) return cudaSuccess;

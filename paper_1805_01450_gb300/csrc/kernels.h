@@ -76,6 +76,9 @@ cudaError_t launch_grad_program(const GradArgs &g, int grid, cudaStream_t s);
 cudaError_t launch_grad_sum(const unsigned char *image, const double2 *gpart, int64_t batch, int64_t o_count,
                             uint32_t n_param_leaves, uint32_t n_params, double *grad, cudaStream_t s);
 
+// Self-test of the bounded waits (grid barrier and mbarrier that can never complete).
+cudaError_t launch_wait_selftest(unsigned *words, unsigned *status, uint32_t polls, unsigned *out, cudaStream_t s);
+
 // FP64 compensated sum of the item partials of every bitstring (Section 3.B.2: the slice
 // terms are added).
 cudaError_t launch_slice_sum(const double2 *partials, int64_t batch, int64_t o_count,

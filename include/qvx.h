@@ -170,7 +170,7 @@ qvx_status qvx_workspace_init(const qvx_plan *plan, void *workspace_dev, size_t 
 
 /* alpha_b = <x_b|C|0> for b < batch. bitstrings_dev: batch uint64 on the device;
  * amps_dev: 2*batch doubles on the device. Slice terms are computed in complex64 and
- * added in FP64 with compensation. */
+ * added exactly (128-bit fixed point, scale 2^-100), then rounded once to FP64. */
 qvx_status qvx_amplitude(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch,
                          double *amps_dev, void *workspace_dev, size_t workspace_bytes,
                          void *stream);

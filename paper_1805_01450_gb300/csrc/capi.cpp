@@ -43,7 +43,7 @@ WsLayout layout_of(const qvx::Plan &p, int64_t batch) {
     w.stage_bits = w.status + 256;
     w.stage_amps = align256(w.stage_bits + (size_t)std::max<int64_t>(batch, 1) * 8);
     w.partials = align256(w.stage_amps + (size_t)std::max<int64_t>(batch, 1) * 16);
-    w.arenas = align256(w.partials + (size_t)std::max<int64_t>(batch, 1) * (size_t)n_outer * 16);
+    w.arenas = align256(w.partials + (size_t)std::max<int64_t>(batch, 1) * (size_t)n_outer * sizeof(qvx::ExactPair));
     w.items_in_flight = 0;
     if (p.engine == QVX_ENGINE_STEPWISE || p.engine == QVX_ENGINE_PERSISTENT) {
         const int64_t arena_bytes = std::max<int64_t>(p.arena_elems, 4) * 8;
@@ -95,7 +95,7 @@ PStepShape shape_of(const qvx::Plan &p, size_t s) {
 }
 
 // Runs the program over outer slices [o_begin, o_begin + o_count) for every bitstring,
-// leaving FP64 item sums in the workspace partials (and slice terms if requested).
+// leaving exact item sums in the workspace partials (and slice terms if requested).
 // With the fused engine and amps != nullptr the same launch also writes the amplitudes.
 qvx_status run_items(qvx_plan *plan, const uint64_t *bits, int64_t batch, int64_t s_begin,
                      int64_t s_end, float *terms, double *amps, void *ws, const WsLayout &w,
@@ -116,7 +116,7 @@ qvx_status run_items(qvx_plan *plan, const uint64_t *bits, int64_t batch, int64_
     a.arena_elems = (uint64_t)std::max<int64_t>(p.arena_elems, 4);
     a.n_steps = (uint32_t)p.steps.size();
     a.n_inner = (uint32_t)n_inner;
-    a.partials = reinterpret_cast<double2 *>(base + w.partials);
+    a.partials = reinterpret_cast<qvx::ExactPair *>(base + w.partials);
     a.terms = reinterpret_cast<float2 *>(terms);
     a.status = reinterpret_cast<unsigned int *>(base + w.status);
     a.counter = reinterpret_cast<unsigned int *>(base + w.status) + 1;
@@ -368,7 +368,7 @@ qvx_status qvx_amplitude_slices(qvx_plan *plan, const uint64_t *bitstrings_dev, 
     if (s != QVX_OK) return s;
     if (plan->p.engine == QVX_ENGINE_FUSED) return QVX_OK;   // the fused launch wrote the sums
     unsigned char *base = static_cast<unsigned char *>(ws);
-    if ((e = qvx::launch_slice_sum(reinterpret_cast<const double2 *>(base + w.partials), batch, o_count,
+    if ((e = qvx::launch_slice_sum(base + w.image, reinterpret_cast<const qvx::ExactPair *>(base + w.partials), batch, o_count,
                                    amps_dev, st)) != cudaSuccess)
         return cuda_fail(e, "slice sum launch");
     return QVX_OK;
@@ -467,11 +467,11 @@ qvx_status qvx_amplitude_grad(qvx_plan *plan, const uint64_t *bitstrings_dev, in
     g.arenas = reinterpret_cast<float2 *>(base + w.grad_arenas);
     g.arena_elems = (uint64_t)std::max<int64_t>(p.grad_arena_elems, 4);
     g.slots = w.grad_slots;
-    g.partials = reinterpret_cast<double2 *>(base + w.partials);
+    g.partials = reinterpret_cast<qvx::ExactPair *>(base + w.partials);
     g.gpart = reinterpret_cast<double2 *>(base + w.grad_partials);
     const int grid = (int)std::min<int64_t>(batch * n_outer, w.grad_slots);
     if ((e = qvx::launch_grad_program(g, grid, st)) != cudaSuccess) return cuda_fail(e, "gradient kernel launch");
-    if ((e = qvx::launch_slice_sum(g.partials, batch, n_outer, amps_dev, st)) != cudaSuccess)
+    if ((e = qvx::launch_slice_sum(base + w.image, g.partials, batch, n_outer, amps_dev, st)) != cudaSuccess)
         return cuda_fail(e, "slice sum launch");
     if ((e = qvx::launch_grad_sum(base + w.image, g.gpart, batch, n_outer, h->n_param_leaves, (uint32_t)p.n_params,
                                   grad_dev, st)) != cudaSuccess)

@@ -58,12 +58,102 @@ __device__ __forceinline__ float2 step_entry(const DevStep &st, uint32_t c, cons
     return acc;
 }
 
-__device__ __forceinline__ double2 warp_sum(double2 v) {
-    for (int d = 16; d > 0; d >>= 1) {
-        v.x += __shfl_down_sync(0xffffffffu, v.x, d);
-        v.y += __shfl_down_sync(0xffffffffu, v.y, d);
+// ------------------------------------------------------------------ exact sums
+// FP64 arithmetic has long latency on this GPU, so the slice terms are added as
+// fixed-point integers: a complex64 term t becomes X = t * 2^100 (128-bit, exact for
+// 2^-77 <= |t| < 2^27; smaller magnitudes lose only bits below 2^-100), integers add
+// exactly and in any order, and each sum is rounded to FP64 once.
+struct Fx {
+    unsigned long long lo;
+    long long hi;
+};
+
+__device__ __forceinline__ Fx fx_from_float(float f) {
+    const uint32_t bits = __float_as_uint(f);
+    uint32_t e = (bits >> 23) & 0xffu;
+    unsigned long long m = bits & 0x7fffffu;
+    Fx r;
+    r.lo = 0;
+    r.hi = 0;
+    if (e == 0xffu) return r;          // not finite: contributes nothing
+    if (e) m |= 0x800000u;
+    else e = 1;
+    const int sh = (int)e - 50;        // t = m 2^(e-150), X = m 2^(e-50)
+    if (sh >= 64) {
+        r.hi = (long long)(m << (sh - 64));
+    } else if (sh > 0) {
+        r.lo = m << sh;
+        r.hi = (long long)(m >> (64 - sh));
+    } else if (sh > -64) {
+        r.lo = m >> (-sh);
     }
-    return v;
+    if (bits >> 31) {                  // two's-complement negation
+        r.lo = ~r.lo + 1ull;
+        r.hi = ~r.hi + (r.lo == 0 ? 1 : 0);
+    }
+    return r;
+}
+
+__device__ __forceinline__ Fx fx_add(Fx a, Fx b) {
+    Fx r;
+    r.lo = a.lo + b.lo;
+    r.hi = a.hi + b.hi + (r.lo < a.lo ? 1 : 0);
+    return r;
+}
+
+__device__ __forceinline__ Fx fx_shfl_down(Fx a, int d) {
+    Fx r;
+    r.lo = __shfl_down_sync(0xffffffffu, a.lo, d);
+    r.hi = __shfl_down_sync(0xffffffffu, a.hi, d);
+    return r;
+}
+
+__device__ __forceinline__ double fx_to_double(Fx a) {
+    // X = hi 2^64 + lo with lo unsigned; value = X 2^-100
+    return __ll2double_rn(a.hi) * 0x1p-36 + __ull2double_rn(a.lo) * 0x1p-100;
+}
+
+__device__ __forceinline__ ExactPair fx_pair(Fx re, Fx im) {
+    ExactPair p;
+    p.re_lo = re.lo;
+    p.re_hi = (unsigned long long)re.hi;
+    p.im_lo = im.lo;
+    p.im_hi = (unsigned long long)im.hi;
+    return p;
+}
+
+// Block-wide exact sum of the pairs at p[0..n) (written by other CTAs: read through L2),
+// rounded to FP64 and times the scalar (sr, si); the result is valid in thread 0.
+__device__ double2 block_exact_sum(const ExactPair *p, int64_t n, double sr, double si) {
+    __shared__ Fx red[2][32];
+    Fx re = {0ull, 0ll}, im = {0ull, 0ll};
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const ulonglong2 a = __ldcg(reinterpret_cast<const ulonglong2 *>(p + i));
+        const ulonglong2 b = __ldcg(reinterpret_cast<const ulonglong2 *>(p + i) + 1);
+        re = fx_add(re, Fx{a.x, (long long)a.y});
+        im = fx_add(im, Fx{b.x, (long long)b.y});
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+        re = fx_add(re, fx_shfl_down(re, d));
+        im = fx_add(im, fx_shfl_down(im, d));
+    }
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+    __syncthreads();
+    if (lane == 0) {
+        red[0][warp] = re;
+        red[1][warp] = im;
+    }
+    __syncthreads();
+    double2 out = make_double2(0.0, 0.0);
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; w++) {
+            re = fx_add(re, red[0][w]);
+            im = fx_add(im, red[1][w]);
+        }
+        const double r = fx_to_double(re), i = fx_to_double(im);
+        out = make_double2(r * sr - i * si, r * si + i * sr);
+    }
+    return out;
 }
 
 // Header fields the item epilogue needs, read once per kernel.
@@ -83,55 +173,46 @@ __device__ __forceinline__ FinishInfo finish_info(const DevProgram *P) {
     return f;
 }
 
-// Sum of the inner slice terms of the item's final tensor that fall in [s_begin, s_end)
-// (FP64), times the plan's scalar; optionally writes each term.
-__device__ void finish_item(const FinishInfo &P, const LaunchArgs &a, const float2 *fin, int64_t b, uint64_t o,
-                            int lane, int lanes) {
+// Exact sum of the inner slice terms of the item's final tensor that fall in
+// [s_begin, s_end) (before the plan's scalar), one warp; optionally writes each term
+// (times the scalar).
+template <bool CG>
+__device__ void finish_item_t(const FinishInfo &P, const LaunchArgs &a, const float2 *fin, int64_t b, uint64_t o,
+                              int lane) {
     const uint64_t x = a.bitstrings[b];
     const bool zero = (x & P.zero_mask) != 0;
-    const double sr = P.sr, si = P.si;
-    double2 acc = make_double2(0.0, 0.0);
+    Fx re = {0ull, 0ll}, im = {0ull, 0ll};
     const uint32_t n_in = P.n_in, present = P.present;
-    for (uint32_t i = lane; i < (1u << n_in); i += lanes) {
+    for (uint32_t i = lane; i < (1u << n_in); i += 32) {
         const int64_t s = (int64_t)((o << n_in) | i);
         if (s < a.s_begin || s >= a.s_end) continue;
         uint32_t fi = 0, bit = 0;
         for (uint32_t j = 0; j < n_in; j++)
             if ((present >> j) & 1u) fi |= ((i >> j) & 1u) << bit++;
-        const float2 t = zero ? make_float2(0.f, 0.f) : fin[fi];
-        const double tr = (double)t.x * sr - (double)t.y * si;
-        const double ti = (double)t.x * si + (double)t.y * sr;
-        acc.x += tr;
-        acc.y += ti;
-        if (a.terms) a.terms[b * (a.s_end - a.s_begin) + (s - a.s_begin)] = make_float2((float)tr, (float)ti);
+        const float2 t = zero ? make_float2(0.f, 0.f) : (CG ? __ldcg(fin + fi) : fin[fi]);
+        re = fx_add(re, fx_from_float(t.x));
+        im = fx_add(im, fx_from_float(t.y));
+        if (a.terms) {
+            const double tr = (double)t.x * P.sr - (double)t.y * P.si;
+            const double ti = (double)t.x * P.si + (double)t.y * P.sr;
+            a.terms[b * (a.s_end - a.s_begin) + (s - a.s_begin)] = make_float2((float)tr, (float)ti);
+        }
     }
-    if (lanes == 32) {
-        acc = warp_sum(acc);
-        if (lane == 0) a.partials[b * a.o_count + (int64_t)(o - (uint64_t)a.o_begin)] = acc;
+    for (int d = 16; d > 0; d >>= 1) {
+        re = fx_add(re, fx_shfl_down(re, d));
+        im = fx_add(im, fx_shfl_down(im, d));
     }
+    if (lane == 0) a.partials[b * a.o_count + (int64_t)(o - (uint64_t)a.o_begin)] = fx_pair(re, im);
 }
 
-// finish_item for a final tensor written by other CTAs (reads through L2), one warp.
-__device__ void finish_item_cg(const FinishInfo &P, const LaunchArgs &a, const float2 *fin, int64_t b, uint64_t o,
-                               int lane) {
-    const uint64_t x = a.bitstrings[b];
-    const bool zero = (x & P.zero_mask) != 0;
-    double2 acc = make_double2(0.0, 0.0);
-    for (uint32_t i = lane; i < (1u << P.n_in); i += 32) {
-        const int64_t s = (int64_t)((o << P.n_in) | i);
-        if (s < a.s_begin || s >= a.s_end) continue;
-        uint32_t fi = 0, bit = 0;
-        for (uint32_t j = 0; j < P.n_in; j++)
-            if ((P.present >> j) & 1u) fi |= ((i >> j) & 1u) << bit++;
-        const float2 t = zero ? make_float2(0.f, 0.f) : __ldcg(fin + fi);
-        const double tr = (double)t.x * P.sr - (double)t.y * P.si;
-        const double ti = (double)t.x * P.si + (double)t.y * P.sr;
-        acc.x += tr;
-        acc.y += ti;
-        if (a.terms) a.terms[b * (a.s_end - a.s_begin) + (s - a.s_begin)] = make_float2((float)tr, (float)ti);
-    }
-    acc = warp_sum(acc);
-    if (lane == 0) a.partials[b * a.o_count + (int64_t)(o - (uint64_t)a.o_begin)] = acc;
+__device__ __forceinline__ void finish_item(const FinishInfo &P, const LaunchArgs &a, const float2 *fin, int64_t b,
+                                            uint64_t o, int lane, int) {
+    finish_item_t<false>(P, a, fin, b, o, lane);
+}
+
+__device__ __forceinline__ void finish_item_cg(const FinishInfo &P, const LaunchArgs &a, const float2 *fin, int64_t b,
+                                               uint64_t o, int lane) {
+    finish_item_t<true>(P, a, fin, b, o, lane);
 }
 
 // ------------------------------------------------------------------ compensated sums
@@ -152,49 +233,11 @@ __device__ __forceinline__ void merge_pair(double &s, double &c, double s2, doub
     c = c + c2 + err;
 }
 
-// Block-wide compensated sum of partials[0..n) (stride 1, double2): result in thread 0.
-__device__ double2 block_compensated_sum(const double2 *partials, int64_t n) {
-    __shared__ double red[4][32];
-    double sr = 0, cr = 0, si = 0, ci = 0;
-    for (int64_t o = threadIdx.x; o < n; o += blockDim.x) {
-        const double2 v = __ldcg(partials + o);   // written by other CTAs: read from L2
-        neumaier_add(sr, cr, v.x);
-        neumaier_add(si, ci, v.y);
-    }
-    for (int d = 16; d > 0; d >>= 1) {
-        const double a = __shfl_down_sync(0xffffffffu, sr, d), b = __shfl_down_sync(0xffffffffu, cr, d);
-        const double e = __shfl_down_sync(0xffffffffu, si, d), f = __shfl_down_sync(0xffffffffu, ci, d);
-        merge_pair(sr, cr, a, b);
-        merge_pair(si, ci, e, f);
-    }
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
-    __syncthreads();
-    if (lane == 0) {
-        red[0][warp] = sr; red[1][warp] = cr; red[2][warp] = si; red[3][warp] = ci;
-    }
-    __syncthreads();
-    double2 out = make_double2(0.0, 0.0);
-    if (threadIdx.x == 0) {
-        double s0 = red[0][0], c0 = red[1][0], s1 = red[2][0], c1 = red[3][0];
-        for (int w = 1; w < nw; w++) {
-            merge_pair(s0, c0, red[0][w], red[1][w]);
-            merge_pair(s1, c1, red[2][w], red[3][w]);
-        }
-        out = make_double2(s0 + c0, s1 + c1);
-    }
-    return out;
-}
-
 // ------------------------------------------------------------------ fused engine
 // Each group of `warps_per_item` warps runs the whole program for one work item
 // (bitstring b, outer slice o); groups loop over items. Shared memory holds, per CTA, the
-// step descriptors and the leaf data (when they fit), and per group the item's leaf base
-// offsets and its tensor arena.
-__device__ __forceinline__ void copy_to_smem(void *dst, const void *src, size_t bytes) {
-    uint4 *d = reinterpret_cast<uint4 *>(dst);
-    const uint4 *s = reinterpret_cast<const uint4 *>(src);
-    for (size_t i = threadIdx.x; i < bytes / 16; i += blockDim.x) d[i] = __ldg(s + i);
-}
+// program and the leaf data (when they fit), and per group the item's leaf base offsets
+// and its tensor arena.
 
 // One output entry of a fused step: e packs the operands' offsets pext(c); the summed
 // index's offsets come from the step's koff tables (nk <= 2) or from its bit counts.
@@ -434,7 +477,7 @@ __global__ void __launch_bounds__(512) fused_program_kernel(LaunchArgs a, int wa
     if (!last) return;
     __threadfence();
     for (int64_t b = 0; b < a.batch; b++) {
-        const double2 r = block_compensated_sum(a.partials + b * a.o_count, a.o_count);
+        const double2 r = block_exact_sum(a.partials + b * a.o_count, a.o_count, fin.sr, fin.si);
         if (threadIdx.x == 0) {
             a.amps[2 * b] = r.x;
             a.amps[2 * b + 1] = r.y;
@@ -746,9 +789,10 @@ __global__ void finish_kernel(LaunchArgs a, int64_t item_begin, int64_t n_items,
 }
 
 // ------------------------------------------------------------------ slice sum
-__global__ void slice_sum_kernel(const double2 *partials, int64_t o_count, double *amps) {
+__global__ void slice_sum_kernel(const unsigned char *img, const ExactPair *partials, int64_t o_count, double *amps) {
+    const DevProgram *P = reinterpret_cast<const DevProgram *>(img);
     const int64_t b = blockIdx.x;
-    const double2 r = block_compensated_sum(partials + b * o_count, o_count);
+    const double2 r = block_exact_sum(partials + b * o_count, o_count, P->scalar_re, P->scalar_im);
     if (threadIdx.x == 0) {
         amps[2 * b] = r.x;
         amps[2 * b + 1] = r.y;
@@ -843,22 +887,25 @@ __global__ void __launch_bounds__(256) grad_program_kernel(GradArgs g) {
             }
             __syncthreads();
         }
-        // amplitude partial: sum of the final tensor over the inner slice modes
+        // amplitude partial: exact sum of the final tensor over the inner slice modes
         const bool zero = (x & P->zero_mask) != 0;
         if (threadIdx.x < 32) {
             const float2 *fin = arena + P->final_fwd_off;
-            double2 acc = make_double2(0.0, 0.0);
+            Fx re = {0ull, 0ll}, im = {0ull, 0ll};
             const uint32_t n_in = P->n_inner, present = P->final_present;
             for (uint32_t i = threadIdx.x; i < (1u << n_in); i += 32) {
                 uint32_t fi = 0, bit = 0;
                 for (uint32_t j = 0; j < n_in; j++)
                     if ((present >> j) & 1u) fi |= ((i >> j) & 1u) << bit++;
-                const float2 t = fin[fi];
-                acc.x += (double)t.x * P->scalar_re - (double)t.y * P->scalar_im;
-                acc.y += (double)t.x * P->scalar_im + (double)t.y * P->scalar_re;
+                const float2 t = zero ? make_float2(0.f, 0.f) : fin[fi];
+                re = fx_add(re, fx_from_float(t.x));
+                im = fx_add(im, fx_from_float(t.y));
             }
-            acc = warp_sum(acc);
-            if (threadIdx.x == 0) g.partials[item] = zero ? make_double2(0.0, 0.0) : acc;
+            for (int d = 16; d > 0; d >>= 1) {
+                re = fx_add(re, fx_shfl_down(re, d));
+                im = fx_add(im, fx_shfl_down(im, d));
+            }
+            if (threadIdx.x == 0) g.partials[item] = fx_pair(re, im);
         }
         for (uint32_t lp = threadIdx.x; lp < npl; lp += blockDim.x) {
             const float2 t = arena[P->gslot_off + lp];
@@ -1072,9 +1119,9 @@ cudaError_t launch_finish_items(const LaunchArgs &a, int64_t item_begin, int64_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_slice_sum(const double2 *partials, int64_t batch, int64_t o_count, double *amps,
-                             cudaStream_t s) {
-    slice_sum_kernel<<<(unsigned)batch, 256, 0, s>>>(partials, o_count, amps);
+cudaError_t launch_slice_sum(const unsigned char *image, const ExactPair *partials, int64_t batch, int64_t o_count,
+                             double *amps, cudaStream_t s) {
+    slice_sum_kernel<<<(unsigned)batch, 256, 0, s>>>(image, partials, o_count, amps);
     return cudaGetLastError();
 }
 

@@ -8,6 +8,13 @@
 
 namespace qvx {
 
+// An exact partial sum of complex slice terms: real and imaginary parts each a 128-bit
+// two's-complement integer X standing for X * 2^-100 (every complex64 term with magnitude
+// between 2^-77 and 2^27 converts without rounding and sums exactly).
+struct ExactPair {
+    unsigned long long re_lo, re_hi, im_lo, im_hi;
+};
+
 struct LaunchArgs {
     const unsigned char *image;     // device image (DevProgram first)
     const uint64_t *bitstrings;     // device, batch entries
@@ -16,7 +23,7 @@ struct LaunchArgs {
     int64_t s_begin, s_end;         // slice range summed / written
     uint64_t arena_elems;
     uint32_t n_steps, n_inner;
-    double2 *partials;              // batch * o_count FP64 item sums
+    ExactPair *partials;            // batch * o_count exact item sums (before the plan's scalar)
     float2 *terms;                  // optional: batch * (s_end - s_begin) slice terms
     unsigned int *status;           // device status word
     unsigned int *counter;          // CTAs finished (fused engine's final sum); zero between calls
@@ -30,7 +37,7 @@ struct LaunchArgs {
 };
 
 // Fused engine: one warp group per work item, every tensor in shared memory. When
-// a.amps is set, the last CTA to finish also adds the item partials (compensated FP64).
+// a.amps is set, the last CTA to finish also adds the item partials (exactly).
 cudaError_t launch_fused(const LaunchArgs &a, int warps_per_item, int items_per_cta, int grid,
                          size_t smem_bytes, cudaStream_t s);
 int fused_blocks_per_sm(int threads, size_t smem_bytes, bool staged);
@@ -66,7 +73,7 @@ struct GradArgs {
     float2 *arenas;                 // slots * grad_arena_elems
     uint64_t arena_elems;
     int64_t slots;
-    double2 *partials;              // batch * o_count amplitude partials
+    ExactPair *partials;            // batch * o_count amplitude partials
     double2 *gpart;                 // batch * o_count * n_param_leaves derivative partials
 };
 // Rewrites the parametrised leaves (U and dU/dtheta) from thetas (device, or the image's own).
@@ -79,9 +86,9 @@ cudaError_t launch_grad_sum(const unsigned char *image, const double2 *gpart, in
 // Self-test of the bounded waits (grid barrier and mbarrier that can never complete).
 cudaError_t launch_wait_selftest(unsigned *words, unsigned *status, uint32_t polls, unsigned *out, cudaStream_t s);
 
-// FP64 compensated sum of the item partials of every bitstring (Section 3.B.2: the slice
-// terms are added).
-cudaError_t launch_slice_sum(const double2 *partials, int64_t batch, int64_t o_count,
+// Exact sum of the item partials of every bitstring (Section 3.B.2: the slice terms are
+// added), rounded once to FP64 and times the plan's scalar.
+cudaError_t launch_slice_sum(const unsigned char *image, const ExactPair *partials, int64_t batch, int64_t o_count,
                              double *amps, cudaStream_t s);
 
 }  // namespace qvx

@@ -81,7 +81,7 @@ extern "C" qvx_status qvx_amplitude_noalloc(qvx_plan *plan, const uint64_t *bits
     // scratch layout: [plan image][status word, CTA counter][partials]
     const size_t image_b = r256(p.image.size());
     const size_t partials_off = image_b + 256;
-    const size_t need = partials_off + (size_t)batch * (size_t)n_outer * 16;
+    const size_t need = partials_off + (size_t)batch * (size_t)n_outer * sizeof(qvx::ExactPair);
     if (need > kNoAllocScratchBytes)
         return fail(QVX_EINVAL, "no-allocation scratch too small: this plan and batch need " + std::to_string(need) +
                                     " bytes, the fixed array holds " + std::to_string(kNoAllocScratchBytes));
@@ -110,7 +110,7 @@ extern "C" qvx_status qvx_amplitude_noalloc(qvx_plan *plan, const uint64_t *bits
     a.arena_elems = (uint64_t)std::max<int64_t>(p.arena_elems, 4);
     a.n_steps = (uint32_t)p.steps.size();
     a.n_inner = (uint32_t)p.n_inner;
-    a.partials = reinterpret_cast<double2 *>(base + partials_off);
+    a.partials = reinterpret_cast<qvx::ExactPair *>(base + partials_off);
     a.terms = nullptr;
     a.status = reinterpret_cast<unsigned int *>(base + image_b);
     a.counter = a.status + 1;

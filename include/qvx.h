@@ -212,7 +212,7 @@ qvx_status qvx_amplitude_noalloc(qvx_plan *plan, const uint64_t *bitstrings_dev,
 
 /* alpha_b = <x_b|C|0> and its derivatives d alpha_b / d theta_p with respect to the angles
  * of the RXY gates (adjoint of the pairwise contractions: each gate's environment tensor
- * contracted with dU/dtheta; the per-slice terms are added in FP64 with compensation).
+ * contracted with dU/dtheta; the per-slice terms are added exactly in 128-bit fixed point).
  * The plan must have been created with opts.gradient = 1. thetas_dev: n_thetas doubles on
  * the device that replace the circuit's angles (gate g takes thetas_dev[g.param_index]),
  * or NULL to keep them; n_thetas must then be 0 or the plan's n_params. amps_dev: 2*batch

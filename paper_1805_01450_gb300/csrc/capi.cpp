@@ -57,7 +57,7 @@ WsLayout layout_of(const qvx::Plan &p, int64_t batch) {
         const int64_t total_items = std::max<int64_t>(batch, 1) * n_outer;
         const int64_t arena_bytes = std::max<int64_t>(p.grad_arena_elems, 4) * 8;
         w.grad_partials = w.total;
-        w.grad_arenas = align256(w.grad_partials + (size_t)total_items * h->n_param_leaves * 16);
+        w.grad_arenas = align256(w.grad_partials + (size_t)total_items * h->n_param_leaves * sizeof(qvx::ExactPair));
         w.grad_slots = std::min(total_items, std::max<int64_t>(1, p.opts.mem_budget_bytes / arena_bytes));
         w.total = align256(w.grad_arenas + (size_t)w.grad_slots * (size_t)arena_bytes);
     }
@@ -468,7 +468,7 @@ qvx_status qvx_amplitude_grad(qvx_plan *plan, const uint64_t *bitstrings_dev, in
     g.arena_elems = (uint64_t)std::max<int64_t>(p.grad_arena_elems, 4);
     g.slots = w.grad_slots;
     g.partials = reinterpret_cast<qvx::ExactPair *>(base + w.partials);
-    g.gpart = reinterpret_cast<double2 *>(base + w.grad_partials);
+    g.gpart = reinterpret_cast<qvx::ExactPair *>(base + w.grad_partials);
     const int grid = (int)std::min<int64_t>(batch * n_outer, w.grad_slots);
     if ((e = qvx::launch_grad_program(g, grid, st)) != cudaSuccess) return cuda_fail(e, "gradient kernel launch");
     if ((e = qvx::launch_slice_sum(base + w.image, g.partials, batch, n_outer, amps_dev, st)) != cudaSuccess)

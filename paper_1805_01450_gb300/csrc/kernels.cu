@@ -1,5 +1,5 @@
 // Device kernels: the pairwise contraction program (fused and stepwise engines) and the
-// FP64 compensated sum of the slice terms.
+// exact (fixed-point) sum of the slice terms.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -213,24 +213,6 @@ __device__ __forceinline__ void finish_item(const FinishInfo &P, const LaunchArg
 __device__ __forceinline__ void finish_item_cg(const FinishInfo &P, const LaunchArgs &a, const float2 *fin, int64_t b,
                                                uint64_t o, int lane) {
     finish_item_t<true>(P, a, fin, b, o, lane);
-}
-
-// ------------------------------------------------------------------ compensated sums
-// Neumaier's compensated addition, and Knuth's exact two-sum to merge (sum, compensation)
-// pairs, so partial sums from many threads combine without losing the compensation.
-__device__ __forceinline__ void neumaier_add(double &s, double &c, double v) {
-    const double t = s + v;
-    if (fabs(s) >= fabs(v)) c += (s - t) + v;
-    else c += (v - t) + s;
-    s = t;
-}
-
-__device__ __forceinline__ void merge_pair(double &s, double &c, double s2, double c2) {
-    const double t = s + s2;
-    const double bp = t - s;
-    const double err = (s - (t - bp)) + (s2 - bp);
-    s = t;
-    c = c + c2 + err;
 }
 
 // ------------------------------------------------------------------ fused engine
@@ -908,54 +890,51 @@ __global__ void __launch_bounds__(256) grad_program_kernel(GradArgs g) {
             if (threadIdx.x == 0) g.partials[item] = fx_pair(re, im);
         }
         for (uint32_t lp = threadIdx.x; lp < npl; lp += blockDim.x) {
-            const float2 t = arena[P->gslot_off + lp];
-            const double2 v = make_double2((double)t.x * P->scalar_re - (double)t.y * P->scalar_im,
-                                           (double)t.x * P->scalar_im + (double)t.y * P->scalar_re);
-            g.gpart[(uint64_t)item * npl + lp] = zero ? make_double2(0.0, 0.0) : v;
+            const float2 t = zero ? make_float2(0.f, 0.f) : arena[P->gslot_off + lp];
+            g.gpart[(uint64_t)item * npl + lp] = fx_pair(fx_from_float(t.x), fx_from_float(t.y));
         }
         __syncthreads();
     }
 }
 
-// One block per (bitstring, parameter): compensated sum over the work items and over the
-// parameter's leaves (CSR lists in the image).
-__global__ void grad_sum_kernel(const unsigned char *img, const double2 *gpart, int64_t o_count, uint32_t npl,
+// One block per (bitstring, parameter): exact sum over the work items and over the
+// parameter's leaves (CSR lists in the image), rounded once and times the plan's scalar.
+__global__ void grad_sum_kernel(const unsigned char *img, const ExactPair *gpart, int64_t o_count, uint32_t npl,
                                 uint32_t n_params, double *grad) {
-    __shared__ double red[4][32];
+    __shared__ Fx red[2][32];
     const DevProgram *P = reinterpret_cast<const DevProgram *>(img);
     const uint32_t *csr = reinterpret_cast<const uint32_t *>(img + P->param_csr_off);
     const int64_t b = blockIdx.x / n_params;
     const uint32_t p = blockIdx.x % n_params;
     const uint32_t first = csr[p], last = csr[p + 1];
     const uint32_t *list = csr + n_params + 1;
-    double sr = 0, cr = 0, si = 0, ci = 0;
+    Fx re = {0ull, 0ll}, im = {0ull, 0ll};
     const int64_t n = (int64_t)(last - first) * o_count;
     for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
         const uint32_t lp = list[first + t / o_count];
         const int64_t o = t % o_count;
-        const double2 v = gpart[((uint64_t)(b * o_count + o)) * npl + lp];
-        neumaier_add(sr, cr, v.x);
-        neumaier_add(si, ci, v.y);
+        const ExactPair v = gpart[((uint64_t)(b * o_count + o)) * npl + lp];
+        re = fx_add(re, Fx{v.re_lo, (long long)v.re_hi});
+        im = fx_add(im, Fx{v.im_lo, (long long)v.im_hi});
     }
     for (int d = 16; d > 0; d >>= 1) {
-        const double a = __shfl_down_sync(0xffffffffu, sr, d), bb = __shfl_down_sync(0xffffffffu, cr, d);
-        const double e = __shfl_down_sync(0xffffffffu, si, d), f = __shfl_down_sync(0xffffffffu, ci, d);
-        merge_pair(sr, cr, a, bb);
-        merge_pair(si, ci, e, f);
+        re = fx_add(re, fx_shfl_down(re, d));
+        im = fx_add(im, fx_shfl_down(im, d));
     }
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
     if (lane == 0) {
-        red[0][warp] = sr; red[1][warp] = cr; red[2][warp] = si; red[3][warp] = ci;
+        red[0][warp] = re;
+        red[1][warp] = im;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s0 = red[0][0], c0 = red[1][0], s1 = red[2][0], c1 = red[3][0];
         for (int w = 1; w < nw; w++) {
-            merge_pair(s0, c0, red[0][w], red[1][w]);
-            merge_pair(s1, c1, red[2][w], red[3][w]);
+            re = fx_add(re, red[0][w]);
+            im = fx_add(im, red[1][w]);
         }
-        grad[2 * (b * n_params + p)] = s0 + c0;
-        grad[2 * (b * n_params + p) + 1] = s1 + c1;
+        const double r = fx_to_double(re), i = fx_to_double(im);
+        grad[2 * (b * n_params + p)] = r * P->scalar_re - i * P->scalar_im;
+        grad[2 * (b * n_params + p) + 1] = r * P->scalar_im + i * P->scalar_re;
     }
 }
 
@@ -1003,7 +982,7 @@ cudaError_t launch_grad_program(const GradArgs &g, int grid, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_grad_sum(const unsigned char *image, const double2 *gpart, int64_t batch, int64_t o_count,
+cudaError_t launch_grad_sum(const unsigned char *image, const ExactPair *gpart, int64_t batch, int64_t o_count,
                             uint32_t n_param_leaves, uint32_t n_params, double *grad, cudaStream_t s) {
     if (n_params == 0 || batch == 0) return cudaSuccess;
     grad_sum_kernel<<<(unsigned)(batch * n_params), 256, 0, s>>>(image, gpart, o_count, n_param_leaves, n_params, grad);

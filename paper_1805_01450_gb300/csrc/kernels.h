@@ -74,13 +74,13 @@ struct GradArgs {
     uint64_t arena_elems;
     int64_t slots;
     ExactPair *partials;            // batch * o_count amplitude partials
-    double2 *gpart;                 // batch * o_count * n_param_leaves derivative partials
+    ExactPair *gpart;               // batch * o_count * n_param_leaves derivative partials
 };
 // Rewrites the parametrised leaves (U and dU/dtheta) from thetas (device, or the image's own).
 cudaError_t launch_set_params(unsigned char *image, uint32_t n_param_leaves, const double *thetas, cudaStream_t s);
 cudaError_t launch_grad_program(const GradArgs &g, int grid, cudaStream_t s);
-// d alpha / d theta_p = compensated FP64 sum over work items and the parameter's leaves.
-cudaError_t launch_grad_sum(const unsigned char *image, const double2 *gpart, int64_t batch, int64_t o_count,
+// d alpha / d theta_p = exact sum over work items and the parameter's leaves.
+cudaError_t launch_grad_sum(const unsigned char *image, const ExactPair *gpart, int64_t batch, int64_t o_count,
                             uint32_t n_param_leaves, uint32_t n_params, double *grad, cudaStream_t s);
 
 // Self-test of the bounded waits (grid barrier and mbarrier that can never complete).

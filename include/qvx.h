@@ -101,6 +101,12 @@ typedef struct {
                                   FP64 at plan time; 0 keeps every contraction on the device */
     int32_t gradient;          /* 1: the plan also serves qvx_amplitude_grad (every gate with
                                   param_index >= 0 stays a tensor of its own) */
+    int32_t slice_rule;        /* how the planner picks sliced variables: 0 the greedy rule of
+                                  Section 3.B.2 (cost under the first ordering); 1 the same with
+                                  the graph re-ordered after every removal (Section 6's larger
+                                  circuits); 2 only candidates that sit on two or more CZ gates
+                                  (the observation of Section 6), then the greedy rule */
+    int32_t reserved;
 } qvx_plan_opts;
 
 typedef struct {

@@ -43,7 +43,8 @@ class PlanOpts(ctypes.Structure):
                 ("order_seed", ctypes.c_uint64), ("mem_budget_bytes", ctypes.c_int64),
                 ("engine", ctypes.c_int32), ("inner_slices", ctypes.c_int32),
                 ("max_rank", ctypes.c_int32), ("warps_per_item", ctypes.c_int32),
-                ("host_merge_rank", ctypes.c_int32), ("gradient", ctypes.c_int32)]
+                ("host_merge_rank", ctypes.c_int32), ("gradient", ctypes.c_int32),
+                ("slice_rule", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -152,7 +153,7 @@ class Plan:
 
     def __init__(self, circ, order=None, slices=None, n_slices=-1, engine="auto", inner_slices=-1,
                  order_restarts=8, order_seed=1, mem_budget_bytes=1 << 30, max_rank=30,
-                 warps_per_item=1, host_merge_rank=8, gradient=False):
+                 warps_per_item=1, host_merge_rank=8, gradient=False, slice_rule="greedy"):
         L = lib()
         opts = PlanOpts()
         L.qvx_plan_opts_default(ctypes.byref(opts))
@@ -166,6 +167,7 @@ class Plan:
         opts.warps_per_item = warps_per_item
         opts.host_merge_rank = host_merge_rank
         opts.gradient = 1 if gradient else 0
+        opts.slice_rule = {"greedy": 0, "reorder": 1, "cz-pair": 2}[slice_rule]
         cs = circuit_struct(circ)
         o_arr = (ctypes.c_int32 * max(len(order or []), 1))(*(order or []))
         s_arr = (ctypes.c_int32 * max(len(slices or []), 1))(*(slices or []))

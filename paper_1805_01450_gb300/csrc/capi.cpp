@@ -217,6 +217,7 @@ void qvx_plan_opts_default(qvx_plan_opts *o) {
     o->warps_per_item = 1;
     o->host_merge_rank = 8;
     o->gradient = 0;
+    o->slice_rule = 0;
 }
 
 qvx_status qvx_graph_export(const qvx_circuit *circuit, int32_t *n_vars, int32_t *var_qubit,
@@ -255,6 +256,7 @@ qvx_status qvx_plan_create(const qvx_circuit *circuit, const int32_t *order, int
     if (n_order < 0) return fail(QVX_EINVAL, "n_order < 0");
     if (o.order_restarts < 1 || o.max_rank < 1 || o.mem_budget_bytes < 64)
         return fail(QVX_EINVAL, "opts: restarts >= 1, max_rank >= 1, budget >= 64 bytes");
+    if (o.slice_rule < 0 || o.slice_rule > 2) return fail(QVX_EINVAL, "opts: slice_rule must be 0, 1 or 2");
     if (o.host_merge_rank < 0 || o.host_merge_rank > 16)
         return fail(QVX_EINVAL, "opts: host_merge_rank must be in [0, 16]");
     if (o.warps_per_item < 1 || o.warps_per_item > 16 || (o.warps_per_item & (o.warps_per_item - 1)))

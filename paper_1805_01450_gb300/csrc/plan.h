@@ -29,6 +29,7 @@ struct Model {
     int n_qubits = 0, n_vars = 0;
     std::vector<int> var_qubit, var_ordinal;
     uint64_t zero_mask = 0;        // qubits with no non-diagonal gate: output equals input 0
+    std::vector<int> cz_count;     // per summed variable: CZ gates acting on it
     cplx scalar = 1.0;
     std::vector<HostTensor> tensors;
     std::vector<std::pair<int, int>> edges;   // a < b, sorted, summed variables only

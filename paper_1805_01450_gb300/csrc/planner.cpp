@@ -143,6 +143,14 @@ bool build_model(const qvx_circuit *c, Model *m, std::string *err, bool keep_par
         if (j == cur[q]) return m->n_vars + q;
         return first_id[q] + j - 1;
     };
+    m->cz_count.assign(m->n_vars, 0);
+    for (Raw &r : raw) {
+        if (r.keys.size() == 2 && r.keys[0].first != r.keys[1].first)   // a CZ between two qubits
+            for (auto &k : r.keys) {
+                const int id = id_of(k.first, k.second);
+                if (id >= 0 && id < m->n_vars) m->cz_count[id]++;
+            }
+    }
     for (Raw &r : raw) {
         HostTensor t;
         std::vector<int> keep;
@@ -1265,24 +1273,32 @@ qvx_status make_plan(const qvx_circuit *c, const int32_t *order, int32_t n_order
     } else {
         int want = opts.n_slices;
         const double budget = (double)opts.mem_budget_bytes;
+        std::vector<int> cur = first;    // the ordering the candidates are scored under
+        uint64_t reseed = opts.order_seed ^ 0x5851F42D4C957F2Dull;
+        bool any_cz = false;
+        for (int v = 0; v < nv; v++) any_cz = any_cz || m.cz_count[v] >= 2;
         for (int it = 0; it < nv; it++) {
             int wd = 0;
-            double cst = order_cost(g, first, removed, &wd);
+            order_cost(g, cur, removed, &wd);
             bool fits = std::ldexp(8.0, wd) <= budget;
             if (want >= 0 ? (int)sl.size() >= want : fits) break;
-            (void)cst;
             double best = -1;
             int bv = -1;
             for (int v = 0; v < nv; v++) {
                 if (removed[v]) continue;
+                if (opts.slice_rule == 2 && any_cz && m.cz_count[v] < 2) continue;
                 removed[v] = 1;
-                double cv = order_cost(g, first, removed, nullptr);
+                double cv = order_cost(g, cur, removed, nullptr);
                 removed[v] = 0;
                 if (best < 0 || cv < best) { best = cv; bv = v; }
             }
             if (bv < 0) break;
             removed[bv] = 1;
             sl.push_back(bv);
+            if (opts.slice_rule == 1) {   // re-order the reduced graph before the next pick
+                int w2 = 0;
+                best_order(g, removed, opts, 3 + splitmix64(reseed) % 1000003, &cur, &w2);
+            }
         }
     }
     if (sl.size() > 40) { *err = "more than 40 sliced variables"; return QVX_EUNSUPPORTED; }

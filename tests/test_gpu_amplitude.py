@@ -217,3 +217,12 @@ def test_7x7x30_large_contractions(engine):
     for i, x in enumerate(xs):
         ref = VE.slice_terms(c, x, p.order, p.slices, slice_ids=ids)
         assert np.max(np.abs(terms[i, ids] - ref)) < tol(49)
+
+
+@pytest.mark.parametrize("rule", ["reorder", "cz-pair"])
+def test_slice_rules_on_device(rule):
+    c = cg.grid_circuit(6, 6, 25, 2001)
+    x = cg.random_bitstrings(36, 1, 2002)[0]
+    p = q.Plan(c, n_slices=12, slice_rule=rule)
+    ref = VE.exact_sum(VE.slice_terms(c, x, p.order, p.slices))
+    assert abs(_amps(p, [x])[0] - ref) < tol(36)

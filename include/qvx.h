@@ -106,7 +106,11 @@ typedef struct {
                                   the graph re-ordered after every removal (Section 6's larger
                                   circuits); 2 only candidates that sit on two or more CZ gates
                                   (the observation of Section 6), then the greedy rule */
-    int32_t reserved;
+    int32_t n_open_qubits;     /* 0..16: qubits whose output stays open, so one contraction gives
+                                  2^n_open_qubits amplitudes per bitstring (Section 6: batches of
+                                  amplitudes). Not with gradient plans. */
+    int32_t open_qubits[16];   /* the open qubits; amplitude j of a bitstring sets open_qubits[i]
+                                  to bit i of j (the bitstring's own bits there are ignored) */
 } qvx_plan_opts;
 
 typedef struct {
@@ -126,6 +130,8 @@ typedef struct {
     double grad_bytes_per_amplitude; /* its algorithmic tensor bytes, all items */
     int32_t n_tiled_steps;           /* contractions the stepwise engine runs as 32x32 tiles */
     int32_t n_phases;                /* levels of mutually independent contractions */
+    int32_t n_open_qubits;           /* amplitudes per bitstring = 2^n_open_qubits */
+    int32_t reserved;
 } qvx_plan_info;
 
 typedef struct qvx_plan qvx_plan;
@@ -175,7 +181,8 @@ qvx_status qvx_workspace_init(const qvx_plan *plan, void *workspace_dev, size_t 
                               void *stream);
 
 /* alpha_b = <x_b|C|0> for b < batch. bitstrings_dev: batch uint64 on the device;
- * amps_dev: 2*batch doubles on the device. Slice terms are computed in complex64 and
+ * amps_dev: 2*batch doubles on the device (2*batch*2^n_open_qubits with open qubits:
+ * amplitude j of bitstring b at amps_dev[2*(b*2^n_open + j)]). Slice terms are computed in complex64 and
  * added exactly (128-bit fixed point, scale 2^-100), then rounded once to FP64. */
 qvx_status qvx_amplitude(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch,
                          double *amps_dev, void *workspace_dev, size_t workspace_bytes,

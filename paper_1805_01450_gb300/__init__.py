@@ -44,7 +44,8 @@ class PlanOpts(ctypes.Structure):
                 ("engine", ctypes.c_int32), ("inner_slices", ctypes.c_int32),
                 ("max_rank", ctypes.c_int32), ("warps_per_item", ctypes.c_int32),
                 ("host_merge_rank", ctypes.c_int32), ("gradient", ctypes.c_int32),
-                ("slice_rule", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("slice_rule", ctypes.c_int32), ("n_open_qubits", ctypes.c_int32),
+                ("open_qubits", ctypes.c_int32 * 16)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -57,7 +58,8 @@ class PlanInfo(ctypes.Structure):
                 ("device_image_bytes", ctypes.c_int64), ("n_params", ctypes.c_int32),
                 ("n_grad_steps", ctypes.c_int32), ("grad_arena_bytes", ctypes.c_int64),
                 ("grad_flops_per_amplitude", ctypes.c_double), ("grad_bytes_per_amplitude", ctypes.c_double),
-                ("n_tiled_steps", ctypes.c_int32), ("n_phases", ctypes.c_int32)]
+                ("n_tiled_steps", ctypes.c_int32), ("n_phases", ctypes.c_int32),
+                ("n_open_qubits", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -153,7 +155,7 @@ class Plan:
 
     def __init__(self, circ, order=None, slices=None, n_slices=-1, engine="auto", inner_slices=-1,
                  order_restarts=8, order_seed=1, mem_budget_bytes=1 << 30, max_rank=30,
-                 warps_per_item=1, host_merge_rank=8, gradient=False, slice_rule="greedy"):
+                 warps_per_item=1, host_merge_rank=8, gradient=False, slice_rule="greedy", open_qubits=()):
         L = lib()
         opts = PlanOpts()
         L.qvx_plan_opts_default(ctypes.byref(opts))
@@ -168,6 +170,9 @@ class Plan:
         opts.host_merge_rank = host_merge_rank
         opts.gradient = 1 if gradient else 0
         opts.slice_rule = {"greedy": 0, "reorder": 1, "cz-pair": 2}[slice_rule]
+        opts.n_open_qubits = len(open_qubits)
+        for i, qb in enumerate(open_qubits):
+            opts.open_qubits[i] = qb
         cs = circuit_struct(circ)
         o_arr = (ctypes.c_int32 * max(len(order or []), 1))(*(order or []))
         s_arr = (ctypes.c_int32 * max(len(slices or []), 1))(*(slices or []))
@@ -187,6 +192,8 @@ class Plan:
         _check(L.qvx_plan_get_order(h, o, s))
         self.order = list(o[:nv - k])
         self.slices = list(s[:k])
+        self.open_qubits = list(open_qubits)
+        self.n_open = len(self.open_qubits)
         self._ws = {}
 
     def __del__(self):
@@ -259,14 +266,16 @@ class Plan:
             self._check_bits(bits)
         n = bits.numel()
         ws = workspace if workspace is not None else self._ws_for(n, bits.device)
+        m = 1 << self.n_open
         if out is None:
-            out = torch.empty(2 * n, dtype=torch.float64, device=bits.device)
+            out = torch.empty(2 * n * m, dtype=torch.float64, device=bits.device)
         if slice_count is None:
             slice_count = self.n_slice_terms - slice_begin
         _check(lib().qvx_amplitude_slices(self._h, ctypes.c_void_p(bits.data_ptr()), n, slice_begin,
                                           slice_count, ctypes.c_void_p(out.data_ptr()),
                                           ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
-        return torch.view_as_complex(out.view(n, 2))
+        a = torch.view_as_complex(out.view(n * m, 2))
+        return a.view(n, m) if self.n_open else a
 
     def amplitude_grad(self, bitstrings, thetas=None, workspace=None, stream=None):
         """(alpha [batch] complex128, d alpha / d theta [batch, n_params] complex128) on the
@@ -306,7 +315,7 @@ class Plan:
         bits = self._bits(bitstrings)
         n = bits.numel()
         ws = workspace if workspace is not None else self._ws_for(n, bits.device)
-        out = torch.empty(2 * n, dtype=torch.float64, device=bits.device)
+        out = torch.empty(2 * n * (1 << self.n_open), dtype=torch.float64, device=bits.device)
         side = torch.cuda.Stream(device=bits.device)
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):
@@ -316,7 +325,8 @@ class Plan:
         with torch.cuda.graph(g):
             self.amplitude(bits, workspace=ws, out=out, validate=False)
         self._graph_keep = (bits, ws)
-        return g.replay, torch.view_as_complex(out.view(n, 2))
+        a = torch.view_as_complex(out.view(n << self.n_open, 2))
+        return g.replay, (a.view(n, 1 << self.n_open) if self.n_open else a)
 
     def amplitude_host(self, bitstrings, out=None, workspace=None, stream=None):
         """<x|C|0> from host bitstrings into host memory (numpy complex128), blocking.
@@ -333,12 +343,13 @@ class Plan:
         h = h.contiguous()
         n = h.numel()
         if out is None:
-            out = torch.empty(2 * n, dtype=torch.float64)
+            out = torch.empty(2 * n * (1 << self.n_open), dtype=torch.float64)
         dev = torch.device("cuda", torch.cuda.current_device())
         ws = workspace if workspace is not None else self._ws_for(n, dev)
         _check(lib().qvx_amplitude_host(self._h, ctypes.c_void_p(h.data_ptr()), n, ctypes.c_void_p(out.data_ptr()),
                                         ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
-        return out[0::2].numpy() + 1j * out[1::2].numpy()
+        a = out[0::2].numpy() + 1j * out[1::2].numpy()
+        return a.reshape(n, 1 << self.n_open) if self.n_open else a
 
     def slice_terms(self, bitstrings, slice_begin=0, slice_count=None, workspace=None, stream=None):
         """The slice terms beta_s (complex64, [batch, slice_count]) of Section 3.B.2."""
@@ -349,11 +360,13 @@ class Plan:
         if slice_count is None:
             slice_count = self.n_slice_terms - slice_begin
         ws = workspace if workspace is not None else self._ws_for(n, bits.device)
-        out = torch.empty(2 * n * slice_count, dtype=torch.float32, device=bits.device)
+        m = 1 << self.n_open
+        out = torch.empty(2 * n * m * slice_count, dtype=torch.float32, device=bits.device)
         _check(lib().qvx_slice_terms(self._h, ctypes.c_void_p(bits.data_ptr()), n, slice_begin, slice_count,
                                      ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
                                      ws.numel(), _stream_ptr(stream)))
-        return torch.view_as_complex(out.view(n, slice_count, 2))
+        t = torch.view_as_complex(out.view(n * m, slice_count, 2))
+        return t.view(n, m, slice_count) if self.n_open else t.view(n, slice_count)
 
     def check_status(self, workspace, stream=None):
         """Synchronises and raises if a kernel set the workspace's device status word."""

@@ -41,9 +41,10 @@ WsLayout layout_of(const qvx::Plan &p, int64_t batch) {
     w.image = 0;
     w.status = align256(p.image.size());
     w.stage_bits = w.status + 256;
+    const size_t slots = (size_t)std::max<int64_t>(batch, 1) << p.open_qubits.size();   // amplitudes per call
     w.stage_amps = align256(w.stage_bits + (size_t)std::max<int64_t>(batch, 1) * 8);
-    w.partials = align256(w.stage_amps + (size_t)std::max<int64_t>(batch, 1) * 16);
-    w.arenas = align256(w.partials + (size_t)std::max<int64_t>(batch, 1) * (size_t)n_outer * sizeof(qvx::ExactPair));
+    w.partials = align256(w.stage_amps + slots * 16);
+    w.arenas = align256(w.partials + slots * (size_t)n_outer * sizeof(qvx::ExactPair));
     w.items_in_flight = 0;
     if (p.engine == QVX_ENGINE_STEPWISE || p.engine == QVX_ENGINE_PERSISTENT) {
         const int64_t arena_bytes = std::max<int64_t>(p.arena_elems, 4) * 8;
@@ -308,6 +309,7 @@ qvx_status qvx_plan_get_info(const qvx_plan *plan, qvx_plan_info *info) {
     info->n_tiled_steps = 0;
     for (char u : p.use_tiled) info->n_tiled_steps += u ? 1 : 0;
     info->n_phases = (int32_t)p.phases.size();
+    info->n_open_qubits = (int32_t)p.open_qubits.size();
     info->grad_bytes_per_amplitude = p.grad_bytes_per_item * (double)info->n_items_per_bitstring;
     return QVX_OK;
 }
@@ -361,7 +363,8 @@ qvx_status qvx_amplitude_slices(qvx_plan *plan, const uint64_t *bitstrings_dev, 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     if (slice_count == 0) {
-        if ((e = cudaMemsetAsync(amps_dev, 0, (size_t)batch * 16, st)) != cudaSuccess) return cuda_fail(e, "memset");
+        if ((e = cudaMemsetAsync(amps_dev, 0, ((size_t)batch << plan->p.open_qubits.size()) * 16, st)) != cudaSuccess)
+            return cuda_fail(e, "memset");
         return QVX_OK;
     }
     int64_t o_count = 0;
@@ -370,7 +373,8 @@ qvx_status qvx_amplitude_slices(qvx_plan *plan, const uint64_t *bitstrings_dev, 
     if (s != QVX_OK) return s;
     if (plan->p.engine == QVX_ENGINE_FUSED) return QVX_OK;   // the fused launch wrote the sums
     unsigned char *base = static_cast<unsigned char *>(ws);
-    if ((e = qvx::launch_slice_sum(base + w.image, reinterpret_cast<const qvx::ExactPair *>(base + w.partials), batch, o_count,
+    if ((e = qvx::launch_slice_sum(base + w.image, reinterpret_cast<const qvx::ExactPair *>(base + w.partials),
+                                   batch << plan->p.open_qubits.size(), o_count,
                                    amps_dev, st)) != cudaSuccess)
         return cuda_fail(e, "slice sum launch");
     return QVX_OK;
@@ -414,7 +418,8 @@ qvx_status qvx_amplitude_host(qvx_plan *plan, const uint64_t *bitstrings_host, i
     if (stage_out) amps_dev = reinterpret_cast<double *>(base + w.stage_amps);
     s = qvx_amplitude(plan, bits_dev, batch, amps_dev, ws, ws_bytes, stream);
     if (s != QVX_OK) return s;
-    if (stage_out && (e = cudaMemcpyAsync(amps_host, amps_dev, (size_t)batch * 16, cudaMemcpyDeviceToHost, st)) !=
+    if (stage_out && (e = cudaMemcpyAsync(amps_host, amps_dev, ((size_t)batch << plan->p.open_qubits.size()) * 16,
+                                          cudaMemcpyDeviceToHost, st)) !=
                          cudaSuccess)
         return cuda_fail(e, "amplitude download");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "stream synchronize");

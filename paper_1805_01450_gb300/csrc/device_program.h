@@ -129,6 +129,8 @@ struct DevProgram {
     uint32_t n_level_phases, n_grad_phases;
     uint64_t grad_phases_off;      // n_grad_phases + 1 gradient-step indices (phase starts)
     uint64_t grad_elem_off_off;    // per gradient step: its first entry inside its phase
+    uint32_t n_open;               // open output qubits (2^n_open amplitudes per bitstring)
+    uint32_t open_present;         // open qubits that are modes of the final tensor, low to high
     uint64_t image_bytes;
 };
 
@@ -139,7 +141,7 @@ constexpr uint32_t kProgramMagic = 0x51565831u;  // "QVX1"
 namespace qvx {
 static_assert(sizeof(DevStep) == 136, "DevStep layout");
 static_assert(sizeof(DevLeaf) == 40, "DevLeaf layout");
-static_assert(sizeof(DevProgram) == 272, "DevProgram layout");
+static_assert(sizeof(DevProgram) == 280, "DevProgram layout");
 static_assert(sizeof(GenOperand) == 112, "GenOperand layout");
 static_assert(sizeof(GenStep) == 240, "GenStep layout");
 static_assert(sizeof(ParamLeaf) == 24, "ParamLeaf layout");

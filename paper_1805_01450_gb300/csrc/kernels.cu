@@ -160,7 +160,8 @@ __device__ double2 block_exact_sum(const ExactPair *p, int64_t n, double sr, dou
 struct FinishInfo {
     uint64_t zero_mask;
     double sr, si;
-    uint32_t n_in, present;
+    uint32_t n_in, present;        // inner slice modes and those present in the final tensor
+    uint32_t n_open, open_present; // open output qubits and those present
 };
 
 __device__ __forceinline__ FinishInfo finish_info(const DevProgram *P) {
@@ -170,39 +171,52 @@ __device__ __forceinline__ FinishInfo finish_info(const DevProgram *P) {
     f.si = P->scalar_im;
     f.n_in = P->n_inner;
     f.present = P->final_present;
+    f.n_open = P->n_open;
+    f.open_present = P->open_present;
     return f;
 }
 
-// Exact sum of the inner slice terms of the item's final tensor that fall in
-// [s_begin, s_end) (before the plan's scalar), one warp; optionally writes each term
-// (times the scalar).
+__device__ __forceinline__ uint32_t compress_bits(uint32_t v, uint32_t mask, uint32_t n) {
+    uint32_t r = 0, bit = 0;
+    for (uint32_t j = 0; j < n; j++)
+        if ((mask >> j) & 1u) r |= ((v >> j) & 1u) << bit++;
+    return r;
+}
+
+// For each value j of the open outputs: the exact sum of the inner slice terms of the
+// item's final tensor that fall in [s_begin, s_end) (before the plan's scalar), one warp;
+// partial of output slot (b, j) for outer slice o. Optionally writes each term (times the
+// scalar) at terms[slot * (s_end - s_begin) + s - s_begin].
 template <bool CG>
 __device__ void finish_item_t(const FinishInfo &P, const LaunchArgs &a, const float2 *fin, int64_t b, uint64_t o,
                               int lane) {
     const uint64_t x = a.bitstrings[b];
     const bool zero = (x & P.zero_mask) != 0;
-    Fx re = {0ull, 0ll}, im = {0ull, 0ll};
     const uint32_t n_in = P.n_in, present = P.present;
-    for (uint32_t i = lane; i < (1u << n_in); i += 32) {
-        const int64_t s = (int64_t)((o << n_in) | i);
-        if (s < a.s_begin || s >= a.s_end) continue;
-        uint32_t fi = 0, bit = 0;
-        for (uint32_t j = 0; j < n_in; j++)
-            if ((present >> j) & 1u) fi |= ((i >> j) & 1u) << bit++;
-        const float2 t = zero ? make_float2(0.f, 0.f) : (CG ? __ldcg(fin + fi) : fin[fi]);
-        re = fx_add(re, fx_from_float(t.x));
-        im = fx_add(im, fx_from_float(t.y));
-        if (a.terms) {
-            const double tr = (double)t.x * P.sr - (double)t.y * P.si;
-            const double ti = (double)t.x * P.si + (double)t.y * P.sr;
-            a.terms[b * (a.s_end - a.s_begin) + (s - a.s_begin)] = make_float2((float)tr, (float)ti);
+    const uint32_t inner_bits = __popc(present);
+    for (uint32_t j = 0; j < (1u << P.n_open); j++) {
+        const uint32_t fj = compress_bits(j, P.open_present, P.n_open) << inner_bits;
+        const int64_t slot = (b << P.n_open) + j;
+        Fx re = {0ull, 0ll}, im = {0ull, 0ll};
+        for (uint32_t i = lane; i < (1u << n_in); i += 32) {
+            const int64_t s = (int64_t)((o << n_in) | i);
+            if (s < a.s_begin || s >= a.s_end) continue;
+            const uint32_t fi = compress_bits(i, present, n_in) | fj;
+            const float2 t = zero ? make_float2(0.f, 0.f) : (CG ? __ldcg(fin + fi) : fin[fi]);
+            re = fx_add(re, fx_from_float(t.x));
+            im = fx_add(im, fx_from_float(t.y));
+            if (a.terms) {
+                const double tr = (double)t.x * P.sr - (double)t.y * P.si;
+                const double ti = (double)t.x * P.si + (double)t.y * P.sr;
+                a.terms[slot * (a.s_end - a.s_begin) + (s - a.s_begin)] = make_float2((float)tr, (float)ti);
+            }
         }
+        for (int d = 16; d > 0; d >>= 1) {
+            re = fx_add(re, fx_shfl_down(re, d));
+            im = fx_add(im, fx_shfl_down(im, d));
+        }
+        if (lane == 0) a.partials[slot * a.o_count + (int64_t)(o - (uint64_t)a.o_begin)] = fx_pair(re, im);
     }
-    for (int d = 16; d > 0; d >>= 1) {
-        re = fx_add(re, fx_shfl_down(re, d));
-        im = fx_add(im, fx_shfl_down(im, d));
-    }
-    if (lane == 0) a.partials[b * a.o_count + (int64_t)(o - (uint64_t)a.o_begin)] = fx_pair(re, im);
 }
 
 __device__ __forceinline__ void finish_item(const FinishInfo &P, const LaunchArgs &a, const float2 *fin, int64_t b,
@@ -376,12 +390,7 @@ __global__ void __launch_bounds__(512) fused_program_kernel(LaunchArgs a, int wa
     const uint64_t steps_off = P->fused_steps_off, tab_off = P->fused_tab_off, map_off = P->fused_lane_map_off;
     const uint32_t n_phases = P->n_fused_phases, n_leaves = P->n_leaves;
     const uint64_t final_off = P->final_off;
-    FinishInfo fin;
-    fin.zero_mask = P->zero_mask;
-    fin.sr = P->scalar_re;
-    fin.si = P->scalar_im;
-    fin.n_in = P->n_inner;
-    fin.present = P->final_present;
+    const FinishInfo fin = finish_info(P);
     const DevLeaf *leaves = reinterpret_cast<const DevLeaf *>(img + P->leaves_off);
     const FusedStep *steps = reinterpret_cast<const FusedStep *>(img + steps_off);
     const uint32_t *tabs = reinterpret_cast<const uint32_t *>(img + tab_off);
@@ -458,11 +467,11 @@ __global__ void __launch_bounds__(512) fused_program_kernel(LaunchArgs a, int wa
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int64_t b = 0; b < a.batch; b++) {
-        const double2 r = block_exact_sum(a.partials + b * a.o_count, a.o_count, fin.sr, fin.si);
+    for (int64_t slot = 0; slot < (a.batch << fin.n_open); slot++) {
+        const double2 r = block_exact_sum(a.partials + slot * a.o_count, a.o_count, fin.sr, fin.si);
         if (threadIdx.x == 0) {
-            a.amps[2 * b] = r.x;
-            a.amps[2 * b + 1] = r.y;
+            a.amps[2 * slot] = r.x;
+            a.amps[2 * slot + 1] = r.y;
         }
     }
     if (threadIdx.x == 0) *a.counter = 0u;

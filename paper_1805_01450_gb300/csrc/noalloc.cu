@@ -81,7 +81,7 @@ extern "C" qvx_status qvx_amplitude_noalloc(qvx_plan *plan, const uint64_t *bits
     // scratch layout: [plan image][status word, CTA counter][partials]
     const size_t image_b = r256(p.image.size());
     const size_t partials_off = image_b + 256;
-    const size_t need = partials_off + (size_t)batch * (size_t)n_outer * sizeof(qvx::ExactPair);
+    const size_t need = partials_off + ((size_t)batch << p.open_qubits.size()) * (size_t)n_outer * sizeof(qvx::ExactPair);
     if (need > kNoAllocScratchBytes)
         return fail(QVX_EINVAL, "no-allocation scratch too small: this plan and batch need " + std::to_string(need) +
                                     " bytes, the fixed array holds " + std::to_string(kNoAllocScratchBytes));

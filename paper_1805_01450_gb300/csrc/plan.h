@@ -54,6 +54,7 @@ struct Plan {
     Model model;
     std::vector<int> order;                     // elimination order (non-sliced ids)
     std::vector<int> slices;                    // inner slices first, then outer
+    std::vector<int> open_qubits;               // outputs kept open (amplitude batches)
     int n_inner = 0;
     double log2_cost = 0, log2_cost_unsliced = 0;
     int width = 0;

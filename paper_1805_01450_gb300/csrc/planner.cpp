@@ -413,6 +413,10 @@ struct ProgramBuilder {
         cnt.assign(n_ids, 0);
         summed.assign(n_ids, 0);
         for (int v = m.n_vars; v < n_ids; v++) fixed[v] = 1;
+        for (int qb : p.open_qubits) {   // open outputs: never fixed, never summed
+            fixed[m.n_vars + qb] = 0;
+            open[m.n_vars + qb] = 1;
+        }
         for (size_t i = 0; i < p.slices.size(); i++) {
             if ((int)i < p.n_inner) open[p.slices[i]] = 1;
             else fixed[p.slices[i]] = 1;
@@ -598,11 +602,13 @@ struct ProgramBuilder {
 };
 
 void assign_layouts(Plan &p) {
-    // the final tensor: inner slice modes in slice-number bit order
+    // the final tensor: inner slice modes in slice-number bit order, then the open outputs
     PTensor &f = p.tensors[p.final_tensor];
     std::vector<int> fin;
     for (int i = 0; i < p.n_inner; i++)
         if (find_pos(f.modes, p.slices[i]) >= 0) fin.push_back(p.slices[i]);
+    for (int qb : p.open_qubits)
+        if (find_pos(f.modes, p.model.n_vars + qb) >= 0) fin.push_back(p.model.n_vars + qb);
     f.modes = fin;
     // every operand takes its consumer's order: output modes first (in the output's
     // order), then the summed modes
@@ -1121,6 +1127,9 @@ bool serialize(Plan &p, std::string *err) {
     h.n_inner = (uint32_t)p.n_inner;
     for (int i = 0; i < p.n_inner; i++)
         if (find_pos(F.modes, p.slices[i]) >= 0) h.final_present |= 1u << i;
+    h.n_open = (uint32_t)p.open_qubits.size();
+    for (size_t i = 0; i < p.open_qubits.size(); i++)
+        if (find_pos(F.modes, m.n_vars + p.open_qubits[i]) >= 0) h.open_present |= 1u << i;
     h.zero_mask = m.zero_mask;
     h.scalar_re = p.prog_scalar.real();
     h.scalar_im = p.prog_scalar.imag();
@@ -1246,6 +1255,15 @@ qvx_status make_plan(const qvx_circuit *c, const int32_t *order, int32_t n_order
                      Plan *p, std::string *err) {
     p->opts = opts;
     if (!build_model(c, &p->model, err, opts.gradient != 0)) return QVX_EINVAL;
+    if (opts.n_open_qubits < 0 || opts.n_open_qubits > 16) { *err = "opts: n_open_qubits must be in [0, 16]"; return QVX_EINVAL; }
+    if (opts.n_open_qubits > 0 && opts.gradient) { *err = "open qubits are not supported with gradients"; return QVX_EUNSUPPORTED; }
+    p->open_qubits.clear();
+    for (int i = 0; i < opts.n_open_qubits; i++) {
+        const int qb = opts.open_qubits[i];
+        if (qb < 0 || qb >= c->n_qubits || find_pos(p->open_qubits, qb) >= 0) { *err = "open_qubits: bad or repeated qubit"; return QVX_EINVAL; }
+        if ((p->model.zero_mask >> qb) & 1ull) { *err = "open_qubits: a qubit without a non-diagonal gate has no output variable"; return QVX_EINVAL; }
+        p->open_qubits.push_back(qb);
+    }
     if (opts.gradient)
         for (int64_t i = 0; i < c->n_gates; i++)
             if (c->gates[i].kind == QVX_GATE_RXY && c->gates[i].param_index >= 0)

@@ -27,7 +27,8 @@ PROG = np.dtype([("magic", "<u4"), ("n_steps", "<u4"), ("n_leaves", "<u4"), ("pa
                  ("n_params", "<u4"), ("grad_pad", "<u4"), ("grad_arena_elems", "<u8"),
                  ("final_fwd_off", "<u8"), ("gslot_off", "<u8"), ("level_phases_off", "<u8"),
                  ("n_level_phases", "<u4"), ("n_grad_phases", "<u4"), ("grad_phases_off", "<u8"),
-                 ("grad_elem_off_off", "<u8"), ("image_bytes", "<u8")])
+                 ("grad_elem_off_off", "<u8"), ("n_open", "<u4"), ("open_present", "<u4"),
+                 ("image_bytes", "<u8")])
 FSTEP = np.dtype([("a_off", "<u4"), ("b_off", "<u4"), ("c_off", "<u4"), ("tab_off", "<u4"), ("flags", "<u4"),
                   ("rc", "u1"), ("nk_ab", "u1"), ("nk_a", "u1"), ("nk_b", "u1"), ("a_cb", "u1"), ("b_cb", "u1"),
                   ("nk", "u1"), ("pad1", "u1"), ("pad2", "<u4"), ("koff_a", "<u2", (4,)), ("koff_b", "<u2", (4,))])
@@ -35,7 +36,7 @@ GOP = np.dtype([("off", "<u8"), ("kind", "<u4"), ("n_oruns", "u1"), ("n_kruns", 
                 ("pad1", "u1"), ("oruns", RUN, (12,)), ("kruns", RUN, (12,))])
 GSTEP = np.dtype([("x", GOP), ("y", GOP), ("out_off", "<u8"), ("ro", "<u4"), ("nk", "<u4")])
 PLEAF = np.dtype([("leaf", "<u4"), ("param", "<u4"), ("n_stored", "<u4"), ("code_off", "<u4"), ("phi", "<f8")])
-assert STEP.itemsize == 136 and LEAF.itemsize == 40 and PROG.itemsize == 272 and FSTEP.itemsize == 48
+assert STEP.itemsize == 136 and LEAF.itemsize == 40 and PROG.itemsize == 280 and FSTEP.itemsize == 48
 assert GOP.itemsize == 112 and GSTEP.itemsize == 240 and PLEAF.itemsize == 24
 OP_ARENA, OP_LEAF, OP_DERIV, OP_ONE = 0, 1, 2, 3
 UNARY, A_LEAF, B_LEAF = 1, 2, 4
@@ -151,22 +152,30 @@ class Program:
             arena[int(st["c_off"]):int(st["c_off"]) + (1 << rc)] = acc
         n_in = int(h["n_inner"])
         present = int(h["final_present"])
+        n_open, open_present = int(h["n_open"]), int(h["open_present"])
         fin = arena[int(h["final_off"]):]
         scalar = complex(float(h["scalar_re"]), float(h["scalar_im"]))
         zero = (x & int(h["zero_mask"])) != 0
-        out = np.zeros(1 << n_in, dtype=np.complex128)
-        for i in range(1 << n_in):
-            fi, bit = 0, 0
-            for j in range(n_in):
-                if (present >> j) & 1:
-                    fi |= ((i >> j) & 1) << bit
+
+        def compress(v, mask, n):
+            r, bit = 0, 0
+            for j in range(n):
+                if (mask >> j) & 1:
+                    r |= ((v >> j) & 1) << bit
                     bit += 1
-            out[i] = 0 if zero else scalar * fin[fi]
-        return out
+            return r
+        out = np.zeros((1 << n_open, 1 << n_in), dtype=np.complex128)
+        inner_bits = bin(present).count("1")
+        for jo in range(1 << n_open):
+            fj = compress(jo, open_present, n_open) << inner_bits
+            for i in range(1 << n_in):
+                out[jo, i] = 0 if zero else scalar * fin[compress(i, present, n_in) | fj]
+        return out if n_open else out[0]
 
     def slice_terms(self, x: int, fused: bool = False):
+        """Slice terms in slice-number order ([2^n_open, slices] with open qubits)."""
         n_out = int(self.h["n_outer"])
-        return np.concatenate([self.item_terms(x, o, fused) for o in range(n_out)])
+        return np.concatenate([self.item_terms(x, o, fused) for o in range(n_out)], axis=-1)
 
 
 def _pdep_runs(c, runs, n):

@@ -226,3 +226,38 @@ def test_slice_rules_on_device(rule):
     p = q.Plan(c, n_slices=12, slice_rule=rule)
     ref = VE.exact_sum(VE.slice_terms(c, x, p.order, p.slices))
     assert abs(_amps(p, [x])[0] - ref) < tol(36)
+
+
+def _with_open_bits(x, open_qubits, j):
+    for i, qb in enumerate(open_qubits):
+        x = (x & ~(1 << qb)) | (((j >> i) & 1) << qb)
+    return x
+
+
+@pytest.mark.parametrize("engine", ["fused", "stepwise", "persistent"])
+def test_open_qubits_batches_of_amplitudes(engine):
+    c = cg.grid_circuit(4, 4, 10, 1001)
+    oq = [2, 7, 9, 14]
+    psi = SV.final_state(c)
+    xs = cg.random_bitstrings(16, 5, 71)
+    p = q.Plan(c, n_slices=3, open_qubits=oq, engine=engine)
+    got = p.amplitude(xs).cpu().numpy()
+    assert got.shape == (5, 16)
+    want = np.array([[psi[_with_open_bits(x, oq, j)] for j in range(16)] for x in xs])
+    assert np.max(np.abs(got - want)) < tol(16)
+    terms = p.slice_terms(xs).cpu().numpy()
+    assert terms.shape == (5, 16, 8)
+    assert np.max(np.abs(terms.sum(axis=-1) - want)) < tol(16)
+    host = p.amplitude_host(xs)
+    assert np.max(np.abs(host - want)) < tol(16)
+
+
+def test_open_qubits_6x6x25_k12():
+    c = cg.grid_circuit(6, 6, 25, 2001)
+    oq = [0, 35]
+    x = cg.random_bitstrings(36, 1, 2002)[0]
+    p = q.Plan(c, n_slices=12, open_qubits=oq)
+    got = p.amplitude([x]).cpu().numpy()[0]
+    for j in range(4):
+        xj = _with_open_bits(x, oq, j)
+        assert abs(got[j] - VE.ve_amplitude(c, xj, p.order, p.slices)) < tol(36)

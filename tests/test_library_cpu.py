@@ -214,3 +214,39 @@ def test_slice_rules_program_matches_oracle(rule):
     psi = SV.final_state(c)
     for x in cg.random_bitstrings(16, 3, 32):
         assert abs(prog.slice_terms(x).sum() - psi[x]) < 1e-6 * 2 ** -8
+
+
+def _with_open_bits(x, open_qubits, j):
+    for i, qb in enumerate(open_qubits):
+        x = (x & ~(1 << qb)) | (((j >> i) & 1) << qb)
+    return x
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(n_slices=3, inner_slices=1), dict(n_slices=2, host_merge_rank=0)])
+def test_open_qubits_program_on_host(kw):
+    # Section 6: batches of amplitudes from one contraction (open output variables)
+    c = cg.grid_circuit(4, 4, 10, 1001)
+    oq = [0, 5, 15]
+    p = q.Plan(c, open_qubits=oq, **kw)
+    assert p.info["n_open_qubits"] == 3
+    prog = Program(p.image())
+    psi = SV.final_state(c)
+    for x in cg.random_bitstrings(16, 3, 70):
+        terms = prog.slice_terms(x)
+        assert terms.shape[0] == 8
+        got = terms.sum(axis=-1)
+        want = np.array([psi[_with_open_bits(x, oq, j)] for j in range(8)])
+        assert np.max(np.abs(got - want)) < 1e-6 * 2 ** -8
+
+
+def test_open_qubit_errors():
+    c = cg.grid_circuit(4, 4, 10, 1001)
+    with pytest.raises(q.QvxError):
+        q.Plan(c, open_qubits=[3, 3])
+    with pytest.raises(q.QvxError):
+        q.Plan(c, open_qubits=[16])
+    with pytest.raises(q.QvxError):
+        q.Plan(cg.rotation_circuit(2, 2, 2, 1), open_qubits=[0], gradient=True)
+    untouched = cg.Circuit(n_qubits=2, gates=[cg.Gate(cg.H, 0)])
+    with pytest.raises(q.QvxError):
+        q.Plan(untouched, open_qubits=[1])

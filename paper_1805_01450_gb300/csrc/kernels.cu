@@ -350,6 +350,27 @@ __device__ __forceinline__ void run_lane_work(const LaneWork &w) {
         }
     } else if (!unary && w.st.nk == 1) {
         uint32_t c = w.sub;
+        for (; c + 3 * w.cnt < n_out; c += 4 * w.cnt) {   // four entries: loads of all issued first
+            uint32_t e[4];
+            float2 p[4], q[4], r[4], t[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) e[u] = w.tab[c + u * w.cnt];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const uint32_t ia = e[u] & 0xffffu, ib = e[u] >> 16;
+                p[u] = A[ia + ka0];
+                q[u] = B[ib + kb0];
+                r[u] = A[ia + ka1];
+                t[u] = B[ib + kb1];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                float2 acc = make_float2(0.f, 0.f);
+                cmac(acc, p[u], q[u]);
+                cmac(acc, r[u], t[u]);
+                w.C[c + u * w.cnt] = acc;
+            }
+        }
         for (; c + w.cnt < n_out; c += 2 * w.cnt) {
             const uint32_t e0 = w.tab[c], e1 = w.tab[c + w.cnt];
             const uint32_t ia0 = e0 & 0xffffu, ib0 = e0 >> 16, ia1 = e1 & 0xffffu, ib1 = e1 >> 16;
@@ -466,7 +487,8 @@ __global__ void __launch_bounds__(512) fused_program_kernel(LaunchArgs a, int wa
     }
     __syncthreads();
     if (!last) return;
-    __threadfence();
+    // every other CTA fenced its partials before counting itself, and the loads below
+    // depend on the count: they read the partials through L2
     for (int64_t slot = 0; slot < (a.batch << fin.n_open); slot++) {
         const double2 r = block_exact_sum(a.partials + slot * a.o_count, a.o_count, fin.sr, fin.si);
         if (threadIdx.x == 0) {

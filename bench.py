@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--batch", type=int, default=None, help="bitstrings per step (workload default)")
     ap.add_argument("--inner-slices", type=int, default=None, help="fix the plan variant instead of autotuning")
+    ap.add_argument("--mem-budget-mb", type=int, default=1024,
+                    help="arena memory of the global-arena engines (work items in flight)")
     ap.add_argument("--warps-per-item", type=int, default=None)
     ap.add_argument("--engine", default="auto")
     ap.add_argument("--sliced", type=int, default=None, help="override the workload's sliced-variable count")
@@ -222,7 +224,8 @@ def main():
         plan, tuning = autotune(circ, bits_host, n_slices=k, device=dev)
     else:
         plan = q.Plan(circ, n_slices=k, inner_slices=-1 if args.inner_slices is None else args.inner_slices,
-                      warps_per_item=args.warps_per_item or 1, engine=args.engine, gradient=grad)
+                      warps_per_item=args.warps_per_item or 1, engine=args.engine, gradient=grad,
+                      mem_budget_bytes=args.mem_budget_mb << 20)
     info = plan.info
     B = len(bits_host)
     bits = plan._bits(bits_host, dev)
@@ -328,15 +331,20 @@ def main():
     elif fused:
         kernel, launches_per_step = "fused_program_kernel", 1
     else:
-        chunks = 1   # items in flight cover the call at the default budget
-        kernel, launches_per_step = "step_kernel", chunks * (info["n_steps"] + 1) + 1
+        total = B * info["n_items_per_bitstring"]
+        chunks = -(-total // plan.items_in_flight(B))   # passes over the items in flight
+        if info["engine"] == "persistent":
+            kernel, launches_per_step = "persistent_program_kernel", chunks + 1
+        else:
+            kernel, launches_per_step = "regtile_step_kernel", chunks * (info["n_steps"] + 1) + 1
     res = {
         "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c64", "data": "synthetic",
         "config": {"workload": args.workload, "qubits": n, "depth": circ.depth, "sliced": k,
                    "inner_slices": info["n_inner"], "bitstrings_per_step": B, "engine": info["engine"],
-                   "warps_per_item": info["warps_per_item"], "l2": "flushed (256 MiB write) before each step",
+                   "warps_per_item": info["warps_per_item"], "mem_budget_mb": args.mem_budget_mb,
+                   "l2": "flushed (256 MiB write) before each step",
                    "parallelism": f"bitstrings per rank x {world}"},
         "complex_tflops": flops / (ms_step / 1e3) / 1e12,
         "abs_err": err, "err_bound": 1e-5 * 2.0 ** (-n / 2),

@@ -128,7 +128,7 @@ typedef struct {
     int64_t grad_arena_bytes;        /* gradient program memory of one work item */
     double grad_flops_per_amplitude; /* algorithmic real flops of the gradient program, all items */
     double grad_bytes_per_amplitude; /* its algorithmic tensor bytes, all items */
-    int32_t n_tiled_steps;           /* contractions the stepwise engine runs as 32x32 tiles */
+    int32_t n_tiled_steps;           /* contractions with a register-tiled form (global-arena engines) */
     int32_t n_phases;                /* levels of mutually independent contractions */
     int32_t n_open_qubits;           /* amplitudes per bitstring = 2^n_open_qubits */
     int32_t reserved;

@@ -194,7 +194,13 @@ class Plan:
         self.slices = list(s[:k])
         self.open_qubits = list(open_qubits)
         self.n_open = len(self.open_qubits)
+        self.mem_budget_bytes = mem_budget_bytes
         self._ws = {}
+
+    def items_in_flight(self, batch):
+        """Work items one pass of the global-arena engines holds (the arena budget's share)."""
+        total = max(batch, 1) * self.info["n_items_per_bitstring"]
+        return min(total, max(1, self.mem_budget_bytes // max(self.info["arena_bytes"], 32)))
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -183,8 +183,8 @@ qvx_status run_items(qvx_plan *plan, const uint64_t *bits, int64_t batch, int64_
         for (size_t s = 0; s < p.steps.size(); s++) {
             const uint32_t rc = (uint32_t)p.tensors[p.steps[s].c].modes.size();
             const PStepShape sh = shape_of(p, s);
-            if (p.use_tiled[s]) e = qvx::launch_tiled_step(a, p.tiled[s], ib, n, arenas, st);
-            else if (sh.nk >= 5) e = qvx::launch_splitk_step(a, (uint32_t)s, ib, n, arenas, rc, st);
+            if (sh.nk >= 5) e = qvx::launch_splitk_step(a, (uint32_t)s, ib, n, arenas, rc, st);
+            else if (p.regtile[s].rm + p.regtile[s].rn > 0) e = qvx::launch_regtile_step(a, p.regtile[s], ib, n, arenas, st);
             else e = qvx::launch_step(a, (uint32_t)s, ib, n, arenas, rc, st);
             if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
         }
@@ -307,7 +307,7 @@ qvx_status qvx_plan_get_info(const qvx_plan *plan, qvx_plan_info *info) {
     info->grad_arena_bytes = p.grad_arena_elems * 8;
     info->grad_flops_per_amplitude = p.grad_flops_per_item * (double)info->n_items_per_bitstring;
     info->n_tiled_steps = 0;
-    for (char u : p.use_tiled) info->n_tiled_steps += u ? 1 : 0;
+    for (const qvx::RegTileStep &r : p.regtile) info->n_tiled_steps += r.rm + r.rn > 0 ? 1 : 0;
     info->n_phases = (int32_t)p.phases.size();
     info->n_open_qubits = (int32_t)p.open_qubits.size();
     info->grad_bytes_per_amplitude = p.grad_bytes_per_item * (double)info->n_items_per_bitstring;

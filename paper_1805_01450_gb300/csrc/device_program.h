@@ -86,21 +86,21 @@ struct ParamLeaf {
     double phi;
 };
 
-// A contraction C[b, m, n] = sum_k A[b, m, k] B[b, k, n] cut into groups of modes: b in
-// A, B and C; m in A and C; n in B and C; k summed, in A and B. Each group has a compact
-// index (its modes in C's order, k in A's order) and, per operand, runs that deposit that
-// index into the operand's layout. Used by the tiled kernel of the global-arena engines.
-constexpr int kTileRuns = 8;
-struct GroupMap {
-    uint32_t n;                    // runs
-    DevRun runs[kTileRuns];
-};
-struct TiledStep {
+// Register-tiled form of a two-operand step (global-arena engines). Each thread computes
+// 2^rm x 2^rn output entries that differ only in rm modes held by A alone and rn modes held
+// by B alone, so every operand entry it loads serves 2^rn (from A) or 2^rm (from B) of its
+// outputs. Thread t of a work item owns the entries c0 + c_m[i] + c_n[j], where
+// c0 = pext-style move of t's bits by free_runs; its operand entries are
+// A[pext(c0, runs_a) + a_m[i] + (ka << a_cb)] and B[pext(c0, runs_b) + b_n[j] + (kb << b_cb)]
+// with ka, kb split from the summed index as in DevStep.
+struct RegTileStep {
     uint64_t a_off, b_off, c_off;  // arena offsets or leaf indices (flags as in DevStep)
     uint32_t flags;
-    uint8_t nb, nm, nn, nk;        // group sizes in bits
-    uint32_t m_fast;               // 1: the lowest bit of C is an m mode
-    GroupMap a_b, a_m, a_k, b_b, b_n, b_k, c_b, c_m, c_n;
+    uint8_t rc, nt, rm, rn;        // output rank, thread bits (rc - rm - rn), tile bits in A / B
+    uint8_t nk_ab, nk_a, nk_b, a_cb, b_cb, n_free, na_runs, nb_runs;
+    DevRun free_runs[6];           // thread index -> output entry with the tile bits zero
+    DevRun runs_a[kMaxRuns], runs_b[kMaxRuns];
+    uint32_t a_m[4], b_n[4], c_m[4], c_n[4];
 };
 
 struct DevProgram {
@@ -131,6 +131,7 @@ struct DevProgram {
     uint64_t grad_elem_off_off;    // per gradient step: its first entry inside its phase
     uint32_t n_open;               // open output qubits (2^n_open amplitudes per bitstring)
     uint32_t open_present;         // open qubits that are modes of the final tensor, low to high
+    uint64_t regtile_off;          // byte offset of n_steps RegTileStep (0 if absent; rm + rn = 0: none)
     uint64_t image_bytes;
 };
 
@@ -141,7 +142,8 @@ constexpr uint32_t kProgramMagic = 0x51565831u;  // "QVX1"
 namespace qvx {
 static_assert(sizeof(DevStep) == 136, "DevStep layout");
 static_assert(sizeof(DevLeaf) == 40, "DevLeaf layout");
-static_assert(sizeof(DevProgram) == 280, "DevProgram layout");
+static_assert(sizeof(DevProgram) == 288, "DevProgram layout");
+static_assert(sizeof(RegTileStep) == 224, "RegTileStep layout");
 static_assert(sizeof(GenOperand) == 112, "GenOperand layout");
 static_assert(sizeof(GenStep) == 240, "GenStep layout");
 static_assert(sizeof(ParamLeaf) == 24, "ParamLeaf layout");

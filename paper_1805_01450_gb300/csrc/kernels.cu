@@ -646,89 +646,66 @@ __global__ void __launch_bounds__(256) persistent_program_kernel(LaunchArgs a, i
     }
 }
 
-// ------------------------------------------------------------------ tiled contraction
-__device__ __forceinline__ uint32_t gpdep(uint32_t v, const GroupMap &g) {
-    uint32_t r = 0;
-    for (uint32_t i = 0; i < g.n; i++) r |= ((v >> g.runs[i].src) & ((1u << g.runs[i].len) - 1u)) << g.runs[i].dst;
-    return r;
-}
-
-constexpr int kTile = 32;     // at most 32 outputs along m and along n per CTA
-constexpr int kTileK = 16;    // summed entries staged per round
-
-// C[b, m, n] = sum_k A[b, m, k] B[b, k, n] for one TM x TN tile of (m, n) of one (item, b),
-// TM = min(32, 2^nm), TN = min(32, 2^nn): the A and B tiles are staged in shared memory and
-// each of the 256 threads accumulates up to four outputs. M_FAST: consecutive threads take
-// consecutive m (the lowest bit of C is an m mode) so a warp's stores are contiguous;
-// otherwise consecutive n.
-template <bool M_FAST>
-__global__ void __launch_bounds__(256) tiled_step_kernel(LaunchArgs a, TiledStep ts, int64_t item_begin,
-                                                         float2 *arenas) {
-    __shared__ float2 As[kTileK][kTile + 1];
-    __shared__ float2 Bs[kTileK][kTile + 1];
-    const unsigned char *img = a.image;
-    const DevProgram *P = reinterpret_cast<const DevProgram *>(img);
-    const uint32_t Mn = 1u << ts.nm, Nn = 1u << ts.nn, Kn = 1u << ts.nk;
-    const uint32_t TM = min(Mn, (uint32_t)kTile), TN = min(Nn, (uint32_t)kTile);
-    const uint32_t tiles_m = Mn / TM, tiles_n = Nn / TN;
-    uint64_t t = blockIdx.x;
-    const uint32_t tn = (uint32_t)(t % tiles_n);
-    t /= tiles_n;
-    const uint32_t tm = (uint32_t)(t % tiles_m);
-    t /= tiles_m;
-    const uint32_t bi = (uint32_t)(t & ((1ull << ts.nb) - 1));
-    const int64_t il = (int64_t)(t >> ts.nb);
-    const int64_t item = item_begin + il;
+// ------------------------------------------------------------------ register-tiled contraction
+// One thread per 2^RM x 2^RN output entries of a two-operand step (RegTileStep): per summed
+// index it loads 2^RM entries of A and 2^RN of B and forms all their products, so each
+// loaded entry serves several outputs from registers. Two summed indices are in flight per
+// iteration to keep more loads outstanding.
+template <int RM, int RN>
+__global__ void __launch_bounds__(256) regtile_step_kernel(LaunchArgs a, RegTileStep rs, int64_t item_begin,
+                                                           int64_t n_items, float2 *arenas) {
+    constexpr int TM = 1 << RM, TN = 1 << RN;
+    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ((uint64_t)n_items << rs.nt)) return;
+    const int64_t il = (int64_t)(g >> rs.nt);
+    const uint32_t t = (uint32_t)(g & ((1ull << rs.nt) - 1ull));
     float2 *arena = arenas + (uint64_t)il * a.arena_elems;
     const float2 *A, *B;
     {
+        const unsigned char *img = a.image;
+        const DevProgram *P = reinterpret_cast<const DevProgram *>(img);
         const DevLeaf *leaves = reinterpret_cast<const DevLeaf *>(img + P->leaves_off);
         const float2 *ldata = reinterpret_cast<const float2 *>(img + P->leaf_data_off);
         uint64_t x = 0, o = 0;
-        if (ts.flags & (kStepALeaf | kStepBLeaf)) {
+        if (rs.flags & (kStepALeaf | kStepBLeaf)) {
+            const int64_t item = item_begin + il;
             x = a.bitstrings[item / a.o_count];
             o = (uint64_t)(a.o_begin + item % a.o_count);
         }
-        A = (ts.flags & kStepALeaf) ? ldata + leaf_base(leaves[ts.a_off], x, o) : arena + ts.a_off;
-        B = (ts.flags & kStepBLeaf) ? ldata + leaf_base(leaves[ts.b_off], x, o) : arena + ts.b_off;
+        A = (rs.flags & kStepALeaf) ? ldata + leaf_base(leaves[rs.a_off], x, o) : arena + rs.a_off;
+        B = (rs.flags & kStepBLeaf) ? ldata + leaf_base(leaves[rs.b_off], x, o) : arena + rs.b_off;
     }
-    A += gpdep(bi, ts.a_b);
-    B += gpdep(bi, ts.b_b);
-    float2 *C = arena + ts.c_off + gpdep(bi, ts.c_b);
-    const uint32_t m0 = tm * TM, n0 = tn * TN;
-    const uint32_t n_out = TM * TN;
-    float2 acc[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-    for (uint32_t k0 = 0; k0 < Kn; k0 += kTileK) {
-        const uint32_t kc = min((uint32_t)kTileK, Kn - k0);
-        for (uint32_t idx = threadIdx.x; idx < TM * kc; idx += blockDim.x) {
-            const uint32_t i = idx % TM, kk = idx / TM;
-            As[kk][i] = A[gpdep(m0 + i, ts.a_m) + gpdep(k0 + kk, ts.a_k)];
-        }
-        for (uint32_t idx = threadIdx.x; idx < TN * kc; idx += blockDim.x) {
-            const uint32_t i = idx % TN, kk = idx / TN;
-            Bs[kk][i] = B[gpdep(n0 + i, ts.b_n) + gpdep(k0 + kk, ts.b_k)];
-        }
-        __syncthreads();
+    const uint32_t c0 = pext_runs(t, rs.free_runs, rs.n_free);
+    A += pext_runs(c0, rs.runs_a, rs.na_runs);
+    B += pext_runs(c0, rs.runs_b, rs.nb_runs);
+    const uint32_t nab = rs.nk_ab, na = rs.nk_a;
+    const uint32_t nk = nab + na + rs.nk_b;
+    const uint32_t mask_ka = (1u << (nab + na)) - 1u, mask_ab = (1u << nab) - 1u;
+    float2 acc[TM][TN];
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const uint32_t oi = threadIdx.x + 256u * q;
-            if (oi < n_out) {
-                const uint32_t mi = M_FAST ? oi % TM : oi / TN;
-                const uint32_t ni = M_FAST ? oi / TM : oi % TN;
-                for (uint32_t kk = 0; kk < kc; kk++) cmac(acc[q], As[kk][mi], Bs[kk][ni]);
-            }
-        }
-        __syncthreads();
-    }
+    for (int i = 0; i < TM; i++)
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-        const uint32_t oi = threadIdx.x + 256u * q;
-        if (oi < n_out) {
-            const uint32_t mi = M_FAST ? oi % TM : oi / TN;
-            const uint32_t ni = M_FAST ? oi / TM : oi % TN;
-            C[gpdep(m0 + mi, ts.c_m) + gpdep(n0 + ni, ts.c_n)] = acc[q];
-        }
+        for (int j = 0; j < TN; j++) acc[i][j] = make_float2(0.f, 0.f);
+#pragma unroll 2
+    for (uint32_t k = 0; k < (1u << nk); k++) {
+        const uint32_t ka = k & mask_ka;
+        const uint32_t kb = (k & mask_ab) | ((k >> (nab + na)) << nab);
+        const float2 *Ak = A + (ka << rs.a_cb), *Bk = B + (kb << rs.b_cb);
+        float2 av[TM], bv[TN];
+#pragma unroll
+        for (int i = 0; i < TM; i++) av[i] = Ak[rs.a_m[i]];
+#pragma unroll
+        for (int j = 0; j < TN; j++) bv[j] = Bk[rs.b_n[j]];
+#pragma unroll
+        for (int i = 0; i < TM; i++)
+#pragma unroll
+            for (int j = 0; j < TN; j++) cmac(acc[i][j], av[i], bv[j]);
     }
+    float2 *C = arena + rs.c_off + c0;
+#pragma unroll
+    for (int i = 0; i < TM; i++)
+#pragma unroll
+        for (int j = 0; j < TN; j++) C[rs.c_m[i] + rs.c_n[j]] = acc[i][j];
 }
 
 // A contraction with many summed entries and few outputs: 32 consecutive outputs per CTA,
@@ -768,14 +745,17 @@ __global__ void __launch_bounds__(256) splitk_step_kernel(LaunchArgs a, uint32_t
         const uint32_t ib = unary ? 0u : pext_runs(c, sd.runs_b, sd.nb_runs);
         const uint32_t nab = sd.nk_ab, na = sd.nk_a, nk = nab + na + sd.nk_b;
         const uint32_t mask_ka = (1u << (nab + na)) - 1u, mask_ab = (1u << nab) - 1u;
-        for (uint32_t k = warp; k < (1u << nk); k += 8) {
-            const float2 av = A[ia + ((k & mask_ka) << sd.a_cb)];
-            if (unary) {
+        if (unary) {
+            for (uint32_t k = warp; k < (1u << nk); k += 8) {
+                const float2 av = A[ia + ((k & mask_ka) << sd.a_cb)];
                 acc.x += av.x;
                 acc.y += av.y;
-            } else {
+            }
+        } else {
+#pragma unroll 4
+            for (uint32_t k = warp; k < (1u << nk); k += 8) {
                 const uint32_t kb = (k & mask_ab) | ((k >> (nab + na)) << nab);
-                cmac(acc, av, B[ib + (kb << sd.b_cb)]);
+                cmac(acc, A[ia + ((k & mask_ka) << sd.a_cb)], B[ib + (kb << sd.b_cb)]);
             }
         }
     }
@@ -1097,14 +1077,21 @@ cudaError_t launch_splitk_step(const LaunchArgs &a, uint32_t step, int64_t item_
     return cudaGetLastError();
 }
 
-cudaError_t launch_tiled_step(const LaunchArgs &a, const TiledStep &ts, int64_t item_begin, int64_t n_items,
-                              float2 *arenas, cudaStream_t s) {
-    const uint64_t tiles_m = (1ull << ts.nm) / std::min<uint64_t>(1ull << ts.nm, kTile);
-    const uint64_t tiles_n = (1ull << ts.nn) / std::min<uint64_t>(1ull << ts.nn, kTile);
-    const uint64_t blocks = ((uint64_t)n_items << ts.nb) * tiles_m * tiles_n;
-    if (blocks > 0x7fffffffull) return cudaErrorInvalidConfiguration;
-    if (ts.m_fast) tiled_step_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(a, ts, item_begin, arenas);
-    else tiled_step_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(a, ts, item_begin, arenas);
+cudaError_t launch_regtile_step(const LaunchArgs &a, const RegTileStep &rs, int64_t item_begin, int64_t n_items,
+                                float2 *arenas, cudaStream_t s) {
+    const uint64_t blocks = (((uint64_t)n_items << rs.nt) + 255) / 256;
+    if (blocks > 0x7fffffffull || rs.rm > 2 || rs.rn > 2 || rs.rm + rs.rn == 0) return cudaErrorInvalidConfiguration;
+    const unsigned nb = (unsigned)blocks;
+    switch (rs.rm * 3 + rs.rn) {
+        case 1: regtile_step_kernel<0, 1><<<nb, 256, 0, s>>>(a, rs, item_begin, n_items, arenas); break;
+        case 2: regtile_step_kernel<0, 2><<<nb, 256, 0, s>>>(a, rs, item_begin, n_items, arenas); break;
+        case 3: regtile_step_kernel<1, 0><<<nb, 256, 0, s>>>(a, rs, item_begin, n_items, arenas); break;
+        case 4: regtile_step_kernel<1, 1><<<nb, 256, 0, s>>>(a, rs, item_begin, n_items, arenas); break;
+        case 5: regtile_step_kernel<1, 2><<<nb, 256, 0, s>>>(a, rs, item_begin, n_items, arenas); break;
+        case 6: regtile_step_kernel<2, 0><<<nb, 256, 0, s>>>(a, rs, item_begin, n_items, arenas); break;
+        case 7: regtile_step_kernel<2, 1><<<nb, 256, 0, s>>>(a, rs, item_begin, n_items, arenas); break;
+        default: regtile_step_kernel<2, 2><<<nb, 256, 0, s>>>(a, rs, item_begin, n_items, arenas); break;
+    }
     return cudaGetLastError();
 }
 

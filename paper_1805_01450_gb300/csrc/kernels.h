@@ -55,9 +55,9 @@ cudaError_t launch_step(const LaunchArgs &a, uint32_t step, int64_t item_begin, 
 // Contraction with many summed entries: 32 outputs per CTA, the summed index split over warps.
 cudaError_t launch_splitk_step(const LaunchArgs &a, uint32_t step, int64_t item_begin, int64_t n_items,
                                float2 *arenas, uint32_t rc, cudaStream_t s);
-// Tiled kernel for a large contraction of the stepwise engine (up to 32 x 32 output tiles).
-cudaError_t launch_tiled_step(const LaunchArgs &a, const TiledStep &ts, int64_t item_begin, int64_t n_items,
-                              float2 *arenas, cudaStream_t s);
+// Register-tiled form of a two-operand step (2^rm x 2^rn outputs per thread, rm, rn <= 2).
+cudaError_t launch_regtile_step(const LaunchArgs &a, const RegTileStep &rs, int64_t item_begin, int64_t n_items,
+                                float2 *arenas, cudaStream_t s);
 // Persistent engine: one cooperative launch per chunk of work items (grid <= co-resident CTAs).
 int persistent_blocks_per_sm();
 cudaError_t launch_persistent(const LaunchArgs &a, int64_t item_begin, int64_t n_items, float2 *arenas,

@@ -71,8 +71,7 @@ struct Plan {
     int engine = QVX_ENGINE_FUSED;
     int warps_per_item = 1;
     std::vector<unsigned char> image;          // device image (DevProgram first)
-    std::vector<TiledStep> tiled;              // per step: tiled form (valid where use_tiled)
-    std::vector<char> use_tiled;
+    std::vector<RegTileStep> regtile;          // per step, global-arena engines: register-tiled form (rm + rn > 0)
     // gradient program
     int n_params = 0;
     std::vector<GenStep> grad_steps;

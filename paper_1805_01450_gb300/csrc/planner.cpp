@@ -1003,48 +1003,70 @@ bool serialize(Plan &p, std::string *err) {
             if (!make_runs(C.modes, B.modes, d.runs_b, &d.nb_runs, &d.b_cb)) { *err = "address map needs too many runs"; return false; }
         }
     }
-    // tiled form of the large contractions (global-arena engines): output rank >= 10, two
-    // operands, every summed mode in both, at least 16 entries along m and along n
-    p.tiled.assign(p.steps.size(), TiledStep{});
-    p.use_tiled.assign(p.steps.size(), 0);
-    for (size_t s = 0; s < p.steps.size(); s++) {
-        const PStep &st = p.steps[s];
-        if (st.b < 0 || !st.k_a.empty() || !st.k_b.empty()) continue;
-        const std::vector<int> &LA = p.tensors[st.a].modes, &LB = p.tensors[st.b].modes, &LC = p.tensors[st.c].modes;
-        if (LC.size() < 10) continue;
-        std::vector<int> gb, gm, gn;
-        for (int v : LC) {
-            const bool ia = find_pos(LA, v) >= 0, ib = find_pos(LB, v) >= 0;
-            if (ia && ib) gb.push_back(v);
-            else if (ia) gm.push_back(v);
-            else gn.push_back(v);
+    // register-tiled form of the two-operand steps (global-arena engines): up to two output
+    // modes held by A alone and two held by B alone, all above C's five lowest bits (a
+    // warp's 32 lanes run along those, so its loads and stores stay coalesced), become a
+    // per-thread tile of 2^rm x 2^rn entries
+    std::vector<RegTileStep> rts;
+    if (p.engine != QVX_ENGINE_FUSED) {
+        rts.assign(ds.size(), RegTileStep{});
+        for (size_t s = 0; s < p.steps.size(); s++) {
+            const PStep &st = p.steps[s];
+            RegTileStep &r = rts[s];
+            std::memset(&r, 0, sizeof(r));
+            if (st.b < 0 || ds[s].rc < 6) continue;
+            const std::vector<int> &LA = p.tensors[st.a].modes, &LB = p.tensors[st.b].modes, &LC = p.tensors[st.c].modes;
+            std::vector<int> tm, tn;   // tile bits: positions in C
+            for (int j = 5; j < (int)LC.size(); j++) {
+                const bool ia = find_pos(LA, LC[j]) >= 0, ib = find_pos(LB, LC[j]) >= 0;
+                if (ia && !ib && tm.size() < 2) tm.push_back(j);
+                if (ib && !ia && tn.size() < 2) tn.push_back(j);
+            }
+            if (tm.empty() && tn.empty()) continue;
+            const DevStep &d = ds[s];
+            r.a_off = d.a_off;
+            r.b_off = d.b_off;
+            r.c_off = d.c_off;
+            r.flags = d.flags;
+            r.rc = d.rc;
+            r.rm = (uint8_t)tm.size();
+            r.rn = (uint8_t)tn.size();
+            r.nt = (uint8_t)(d.rc - r.rm - r.rn);
+            r.nk_ab = d.nk_ab;
+            r.nk_a = d.nk_a;
+            r.nk_b = d.nk_b;
+            r.a_cb = d.a_cb;
+            r.b_cb = d.b_cb;
+            r.na_runs = d.na_runs;
+            r.nb_runs = d.nb_runs;
+            for (int i = 0; i < kMaxRuns; i++) { r.runs_a[i] = d.runs_a[i]; r.runs_b[i] = d.runs_b[i]; }
+            // free bits of C in increasing order, as runs from the thread index
+            int nf = 0, tb = 0;
+            for (int j = 0; j < (int)LC.size();) {
+                if (find_pos(tm, j) >= 0 || find_pos(tn, j) >= 0) { j++; continue; }
+                int k = j + 1;
+                while (k < (int)LC.size() && find_pos(tm, k) < 0 && find_pos(tn, k) < 0) k++;
+                r.free_runs[nf].src = (uint8_t)tb;
+                r.free_runs[nf].len = (uint8_t)(k - j);
+                r.free_runs[nf].dst = (uint8_t)j;
+                nf++;
+                tb += k - j;
+                j = k;
+            }
+            r.n_free = (uint8_t)nf;
+            for (int i = 0; i < (1 << r.rm); i++)
+                for (int q = 0; q < r.rm; q++)
+                    if ((i >> q) & 1) {
+                        r.a_m[i] += 1u << find_pos(LA, LC[tm[q]]);
+                        r.c_m[i] += 1u << tm[q];
+                    }
+            for (int i = 0; i < (1 << r.rn); i++)
+                for (int q = 0; q < r.rn; q++)
+                    if ((i >> q) & 1) {
+                        r.b_n[i] += 1u << find_pos(LB, LC[tn[q]]);
+                        r.c_n[i] += 1u << tn[q];
+                    }
         }
-        if (gm.size() < 4 || gn.size() < 4) continue;   // 16 x 16 outputs at least per tile
-        TiledStep t;
-        std::memset(&t, 0, sizeof(t));
-        t.a_off = ds[s].a_off;
-        t.b_off = ds[s].b_off;
-        t.c_off = ds[s].c_off;
-        t.flags = ds[s].flags;
-        t.nb = (uint8_t)gb.size();
-        t.nm = (uint8_t)gm.size();
-        t.nn = (uint8_t)gn.size();
-        t.nk = (uint8_t)st.k_ab.size();
-        t.m_fast = find_pos(gm, LC[0]) >= 0 ? 1u : 0u;
-        bool ok = true;
-        auto gmap = [&](const std::vector<int> &g, const std::vector<int> &L, GroupMap &m) {
-            DevRun r[kMaxRuns];
-            uint8_t n = 0;
-            if (!map_runs(g, L, r, &n) || n > kTileRuns) { ok = false; return; }
-            m.n = n;
-            for (int i = 0; i < n; i++) m.runs[i] = r[i];
-        };
-        gmap(gb, LA, t.a_b); gmap(gm, LA, t.a_m); gmap(st.k_ab, LA, t.a_k);
-        gmap(gb, LB, t.b_b); gmap(gn, LB, t.b_n); gmap(st.k_ab, LB, t.b_k);
-        gmap(gb, LC, t.c_b); gmap(gm, LC, t.c_m); gmap(gn, LC, t.c_n);
-        if (!ok) continue;
-        p.tiled[s] = t;
-        p.use_tiled[s] = 1;
     }
     // fused form: per-step tables of pext(c) for both operands (16-bit offsets), and per
     // phase a map from each lane of a work item's group to the step it works on
@@ -1151,6 +1173,10 @@ bool serialize(Plan &p, std::string *err) {
         h.fused_lanes = (uint32_t)lanes;
         off = align256(off + (tab.size() + lane_map.size()) * sizeof(uint32_t));
     }
+    if (!rts.empty()) {
+        h.regtile_off = off;
+        off = align256(off + rts.size() * sizeof(RegTileStep));
+    }
     // level phases (first step of each phase, then the step count)
     std::vector<uint32_t> level_first;
     for (const auto &ph : p.phases) level_first.push_back((uint32_t)ph.first);
@@ -1207,6 +1233,8 @@ bool serialize(Plan &p, std::string *err) {
     h.image_bytes = off;
     p.image.assign(off, 0);
     std::memcpy(p.image.data() + h.level_phases_off, level_first.data(), level_first.size() * sizeof(uint32_t));
+    if (!rts.empty()) std::memcpy(p.image.data() + h.regtile_off, rts.data(), rts.size() * sizeof(RegTileStep));
+    p.regtile = rts;
     if (p.opts.gradient) {
         unsigned char *img = p.image.data();
         if (!p.grad_steps.empty()) std::memcpy(img + h.grad_steps_off, p.grad_steps.data(), p.grad_steps.size() * sizeof(GenStep));

@@ -28,7 +28,7 @@ PROG = np.dtype([("magic", "<u4"), ("n_steps", "<u4"), ("n_leaves", "<u4"), ("pa
                  ("final_fwd_off", "<u8"), ("gslot_off", "<u8"), ("level_phases_off", "<u8"),
                  ("n_level_phases", "<u4"), ("n_grad_phases", "<u4"), ("grad_phases_off", "<u8"),
                  ("grad_elem_off_off", "<u8"), ("n_open", "<u4"), ("open_present", "<u4"),
-                 ("image_bytes", "<u8")])
+                 ("regtile_off", "<u8"), ("image_bytes", "<u8")])
 FSTEP = np.dtype([("a_off", "<u4"), ("b_off", "<u4"), ("c_off", "<u4"), ("tab_off", "<u4"), ("flags", "<u4"),
                   ("rc", "u1"), ("nk_ab", "u1"), ("nk_a", "u1"), ("nk_b", "u1"), ("a_cb", "u1"), ("b_cb", "u1"),
                   ("nk", "u1"), ("pad1", "u1"), ("pad2", "<u4"), ("koff_a", "<u2", (4,)), ("koff_b", "<u2", (4,))])
@@ -36,7 +36,13 @@ GOP = np.dtype([("off", "<u8"), ("kind", "<u4"), ("n_oruns", "u1"), ("n_kruns", 
                 ("pad1", "u1"), ("oruns", RUN, (12,)), ("kruns", RUN, (12,))])
 GSTEP = np.dtype([("x", GOP), ("y", GOP), ("out_off", "<u8"), ("ro", "<u4"), ("nk", "<u4")])
 PLEAF = np.dtype([("leaf", "<u4"), ("param", "<u4"), ("n_stored", "<u4"), ("code_off", "<u4"), ("phi", "<f8")])
-assert STEP.itemsize == 136 and LEAF.itemsize == 40 and PROG.itemsize == 280 and FSTEP.itemsize == 48
+RTSTEP = np.dtype([("a_off", "<u8"), ("b_off", "<u8"), ("c_off", "<u8"), ("flags", "<u4"), ("rc", "u1"),
+                   ("nt", "u1"), ("rm", "u1"), ("rn", "u1"), ("nk_ab", "u1"), ("nk_a", "u1"), ("nk_b", "u1"),
+                   ("a_cb", "u1"), ("b_cb", "u1"), ("n_free", "u1"), ("na_runs", "u1"), ("nb_runs", "u1"),
+                   ("free_runs", RUN, (6,)), ("runs_a", RUN, (12,)), ("runs_b", RUN, (12,)),
+                   ("a_m", "<u4", (4,)), ("b_n", "<u4", (4,)), ("c_m", "<u4", (4,)), ("c_n", "<u4", (4,))])
+assert STEP.itemsize == 136 and LEAF.itemsize == 40 and PROG.itemsize == 288 and FSTEP.itemsize == 48
+assert RTSTEP.itemsize == 224
 assert GOP.itemsize == 112 and GSTEP.itemsize == 240 and PLEAF.itemsize == 24
 OP_ARENA, OP_LEAF, OP_DERIV, OP_ONE = 0, 1, 2, 3
 UNARY, A_LEAF, B_LEAF = 1, 2, 4
@@ -66,6 +72,10 @@ class Program:
             lo, nl = int(h["fused_lane_map_off"]), int(h["n_fused_phases"]) * int(h["fused_lanes"])
             self.lane_map = np.frombuffer(buf[lo:lo + 4 * nl].tobytes(), dtype="<u4").reshape(
                 int(h["n_fused_phases"]), int(h["fused_lanes"]))
+        self.rtsteps = None
+        if int(h["regtile_off"]):
+            ro = int(h["regtile_off"])
+            self.rtsteps = np.frombuffer(buf[ro:ro + RTSTEP.itemsize * int(h["n_steps"])].tobytes(), dtype=RTSTEP)
         n = int(h["n_leaf_entries"])
         ld = np.frombuffer(buf[int(h["leaf_data_off"]):int(h["leaf_data_off"]) + 8 * n].tobytes(), dtype="<f4")
         self.leaf_data = ld[0::2].astype(np.float64) + 1j * ld[1::2].astype(np.float64)
@@ -100,9 +110,42 @@ class Program:
             return self.leaf_data[off + idx]
         return read
 
-    def item_terms(self, x: int, o: int, fused: bool = False):
+    def _regtile_step(self, si, A, B, arena):
+        """Step si through its register-tiled form: thread t owns the entries
+        c0 + c_m[i] + c_n[j]; every entry of C must be owned exactly once."""
+        r = self.rtsteps[si]
+        st = self.steps[si]
+        for f in ("a_off", "b_off", "c_off", "flags", "rc", "nk_ab", "nk_a", "nk_b", "a_cb", "b_cb",
+                  "na_runs", "nb_runs"):
+            assert int(r[f]) == int(st[f]), f
+        rm, rn, nt, rc = int(r["rm"]), int(r["rn"]), int(r["nt"]), int(r["rc"])
+        assert 0 < rm + rn and rm <= 2 and rn <= 2 and nt == rc - rm - rn
+        t = np.arange(1 << nt, dtype=np.int64)
+        c0 = _pext(t, r["free_runs"], int(r["n_free"]))
+        ia0 = _pext(c0, r["runs_a"], int(r["na_runs"]))
+        ib0 = _pext(c0, r["runs_b"], int(r["nb_runs"]))
+        nab, na, nb = int(r["nk_ab"]), int(r["nk_a"]), int(r["nk_b"])
+        owned = np.zeros(1 << rc, dtype=np.int64)
+        out = {}
+        for i in range(1 << rm):
+            for j in range(1 << rn):
+                c = c0 + int(r["c_m"][i]) + int(r["c_n"][j])
+                acc = np.zeros(1 << nt, dtype=np.complex128)
+                for k in range(1 << (nab + na + nb)):
+                    ka = k & ((1 << (nab + na)) - 1)
+                    kb = (k & ((1 << nab) - 1)) | ((k >> (nab + na)) << nab)
+                    acc += (A(ia0 + int(r["a_m"][i]) + (ka << int(r["a_cb"]))) *
+                            B(ib0 + int(r["b_n"][j]) + (kb << int(r["b_cb"]))))
+                np.add.at(owned, c, 1)
+                out[(i, j)] = (c, acc)
+        assert np.all(owned == 1)
+        for c, acc in out.values():
+            arena[int(r["c_off"]) + c] = acc
+
+    def item_terms(self, x: int, o: int, fused: bool = False, regtile: bool = False):
         """Slice terms of work item (x, o): entry i is slice (o << n_inner) | i. With
-        fused=True the steps take their operand offsets from the fused form's tables."""
+        fused=True the steps take their operand offsets from the fused form's tables; with
+        regtile=True the steps that have a register-tiled form run through it."""
         h = self.h
         arena = np.zeros(max(int(h["arena_elems"]), 4), dtype=np.complex128)
         for si, st in enumerate(self.steps):
@@ -122,6 +165,10 @@ class Program:
             unary = flags & UNARY
             B = None if unary else operand(flags & B_LEAF, st["b_off"])
             nab_, na_, nb_ = int(st["nk_ab"]), int(st["nk_a"]), int(st["nk_b"])
+            if regtile and int(self.rtsteps[si]["rm"]) + int(self.rtsteps[si]["rn"]) > 0:
+                assert not unary
+                self._regtile_step(si, A, B, arena)
+                continue
             if fused:
                 fst = self.fsteps[si]
                 for f in ("a_off", "b_off", "c_off", "flags", "rc", "nk_ab", "nk_a", "nk_b", "a_cb", "b_cb"):
@@ -172,10 +219,10 @@ class Program:
                 out[jo, i] = 0 if zero else scalar * fin[compress(i, present, n_in) | fj]
         return out if n_open else out[0]
 
-    def slice_terms(self, x: int, fused: bool = False):
+    def slice_terms(self, x: int, fused: bool = False, regtile: bool = False):
         """Slice terms in slice-number order ([2^n_open, slices] with open qubits)."""
         n_out = int(self.h["n_outer"])
-        return np.concatenate([self.item_terms(x, o, fused) for o in range(n_out)], axis=-1)
+        return np.concatenate([self.item_terms(x, o, fused, regtile) for o in range(n_out)], axis=-1)
 
 
 def _pdep_runs(c, runs, n):

@@ -206,12 +206,12 @@ def test_cuda_graph_capture_and_replay(engine):
 
 @pytest.mark.parametrize("engine", ["stepwise", "persistent"])
 def test_7x7x30_large_contractions(engine):
-    # rank-17 outputs: the stepwise engine runs these as 32 x 32 tiles
+    # rank-17 outputs: the stepwise engine runs most contractions in register-tiled form
     c = cg.grid_circuit(7, 7, 30, 3001)
     xs = cg.random_bitstrings(49, 2, 3003)
     p = q.Plan(c, n_slices=8, inner_slices=4, engine=engine, mem_budget_bytes=40 << 20)
     if engine == "stepwise":
-        assert p.info["n_tiled_steps"] >= 5
+        assert p.info["n_tiled_steps"] >= 50
     ids = np.random.default_rng(6).choice(256, 8, replace=False)
     terms = p.slice_terms(xs).cpu().numpy()
     for i, x in enumerate(xs):

@@ -120,6 +120,32 @@ def test_program_on_host_matches_oracle(name, maker, kw):
             assert np.max(np.abs(terms - ref)) < 1e-6 * 2 ** (-c.n_qubits / 2)
 
 
+@pytest.mark.parametrize("name,maker,kw", CASES[1:4] + CASES[5:8], ids=[c[0] for c in CASES[1:4] + CASES[5:8]])
+def test_register_tiled_forms_on_host(name, maker, kw):
+    # the stepwise engine's register-tiled steps cover every output entry once and give the
+    # plain step's values exactly
+    c = maker()
+    p = q.Plan(c, engine="stepwise", **kw)
+    prog = Program(p.image())
+    assert prog.rtsteps is not None
+    for x in cg.random_bitstrings(c.n_qubits, 2, 19):
+        assert np.array_equal(prog.slice_terms(x, regtile=True), prog.slice_terms(x))
+
+
+def test_register_tiled_forms_7x7x30():
+    c = cg.grid_circuit(7, 7, 30, 3001)
+    p = q.Plan(c, n_slices=8, inner_slices=4, engine="stepwise")
+    prog = Program(p.image())
+    rt = prog.rtsteps
+    assert int(((rt["rm"] + rt["rn"]) > 0).sum()) == p.info["n_tiled_steps"] >= 50
+    x = cg.random_bitstrings(49, 1, 3003)[0]
+    got = prog.item_terms(x, 5, regtile=True)
+    plain = prog.item_terms(x, 5)   # same products, numpy may round them differently
+    assert np.max(np.abs(got - plain)) <= 1e-12 * np.max(np.abs(plain))
+    ref = VE.slice_terms(c, x, p.order, p.slices, slice_ids=[(5 << 4) | i for i in range(16)])
+    assert np.max(np.abs(got - ref)) < 1e-6 * 2 ** -24.5
+
+
 @pytest.mark.parametrize("merge", [0, 8])
 def test_program_slice_terms_6x6_sample(merge):
     c = cg.grid_circuit(6, 6, 25, 2001)

@@ -29,10 +29,14 @@ WORKLOADS = {
     # name: (kind, rows, cols, depth, circuit seed, bitstring seed, sliced variables, bitstrings per step)
     "grid6x6d25-k12": ("grid", 6, 6, 25, 2001, 2002, 12, 1),
     "grid4x4d10": ("grid", 4, 4, 10, 1001, 1002, 0, 1),
-    "grid7x7d30-b1024": ("grid", 7, 7, 30, 3001, 3002, 14, 1024),
+    "grid7x7d30-b1024": ("grid", 7, 7, 30, 3001, 3002, 4, 1024),
     "rot5x5d20-grad": ("rotation", 5, 5, 20, 4001, 4002, 8, 1),
     "grid8x8d40-k16": ("grid", 8, 8, 40, 5001, 5002, 16, 1),
 }
+# workloads whose plan variant the autotuner also picks the slice count and engine for,
+# and the arena memory the global-arena engines may use there (MiB)
+TUNE = {"grid7x7d30-b1024": dict(slice_counts=(0, 2, 4, 6, 8), engines=("stepwise",), budget_s=90.0)}
+MEM_BUDGET_MB = {"grid7x7d30-b1024": 32768}
 DEFAULT_WORKLOAD = "grid6x6d25-k12"
 METRIC = "amplitudes/s and complex TFLOP/s (% of GB300 peak) at |Δα|≤1e-5·2^-N/2 vs FP64"
 L2_FLUSH_BYTES = 256 << 20
@@ -50,8 +54,8 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--batch", type=int, default=None, help="bitstrings per step (workload default)")
     ap.add_argument("--inner-slices", type=int, default=None, help="fix the plan variant instead of autotuning")
-    ap.add_argument("--mem-budget-mb", type=int, default=1024,
-                    help="arena memory of the global-arena engines (work items in flight)")
+    ap.add_argument("--mem-budget-mb", type=int, default=None,
+                    help="arena memory of the global-arena engines (work items in flight; workload default)")
     ap.add_argument("--warps-per-item", type=int, default=None)
     ap.add_argument("--engine", default="auto")
     ap.add_argument("--sliced", type=int, default=None, help="override the workload's sliced-variable count")
@@ -216,16 +220,20 @@ def main():
     circ, bits_host, k = workload(args.workload, args.batch, rank)
     if args.sliced is not None:
         k = args.sliced
+    if args.mem_budget_mb is None:
+        args.mem_budget_mb = MEM_BUDGET_MB.get(args.workload, 1024)
+    budget = args.mem_budget_mb << 20
     dev = torch.device("cuda", local)
     grad = is_grad(args.workload)
     tuning = None
     if args.inner_slices is None and args.warps_per_item is None and args.engine == "auto" and not grad:
         from paper_1805_01450_gb300.autotune import autotune
-        plan, tuning = autotune(circ, bits_host, n_slices=k, device=dev)
+        tune = dict(TUNE.get(args.workload, {})) if args.sliced is None else {}
+        plan, tuning = autotune(circ, bits_host, n_slices=k, device=dev, mem_budget_bytes=budget, **tune)
     else:
         plan = q.Plan(circ, n_slices=k, inner_slices=-1 if args.inner_slices is None else args.inner_slices,
                       warps_per_item=args.warps_per_item or 1, engine=args.engine, gradient=grad,
-                      mem_budget_bytes=args.mem_budget_mb << 20)
+                      mem_budget_bytes=budget)
     info = plan.info
     B = len(bits_host)
     bits = plan._bits(bits_host, dev)
@@ -255,6 +263,7 @@ def main():
     with ClockSampler(torch.cuda.current_device()) as clocks:
         barrier()
         torch.cuda.synchronize()
+        launches0 = L.qvx_kernel_launches()
         for i in range(K):
             flush.zero_()
             ev[i][0].record(stream)
@@ -262,6 +271,7 @@ def main():
             ev[i][1].record(stream)
         torch.cuda.synchronize()
         barrier()
+    launches = L.qvx_kernel_launches() - launches0   # this library's kernels in the timed region
     dev_ms = sum(a.elapsed_time(b) for a, b in ev)
     plan.check_status(ws)
 
@@ -327,21 +337,18 @@ def main():
     achieved = algo_bytes / (ms_step / 1e3) / 1e9
     fused = info["engine"] == "fused" and not grad
     if grad:
-        kernel, launches_per_step = "grad_program_kernel", 4
+        kernel = "grad_smem_kernel" if 0 < info["grad_smem_bytes"] <= 232448 else "grad_program_kernel"
     elif fused:
-        kernel, launches_per_step = "fused_program_kernel", 1
+        kernel = "fused_program_kernel"
+    elif info["engine"] == "persistent":
+        kernel = "persistent_program_kernel"
     else:
-        total = B * info["n_items_per_bitstring"]
-        chunks = -(-total // plan.items_in_flight(B))   # passes over the items in flight
-        if info["engine"] == "persistent":
-            kernel, launches_per_step = "persistent_program_kernel", chunks + 1
-        else:
-            kernel, launches_per_step = "regtile_step_kernel", chunks * (info["n_steps"] + 1) + 1
+        kernel = "regtile_step_kernel"
     res = {
         "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-        "config": {"workload": args.workload, "qubits": n, "depth": circ.depth, "sliced": k,
+        "config": {"workload": args.workload, "qubits": n, "depth": circ.depth, "sliced": len(plan.slices),
                    "inner_slices": info["n_inner"], "bitstrings_per_step": B, "engine": info["engine"],
                    "warps_per_item": info["warps_per_item"], "mem_budget_mb": args.mem_budget_mb,
                    "l2": "flushed (256 MiB write) before each step",
@@ -355,7 +362,7 @@ def main():
                      "algorithmic_bytes_per_launch": algo_bytes},
         "e2e": {"value": e2e, "unit": "amplitudes/s", "h2d_bytes_per_step": 8 * B,
                 "d2h_bytes_per_step": 16 * B + (8 * gout.numel() if grad else 0)},
-        "gpu_launches": K * launches_per_step,
+        "gpu_launches": launches,
         "clocks": clocks.summary(),
         "autotune": None if tuning is None else [list(t) for t in tuning],
         "gradients_per_amplitude": info["n_params"] if grad else 0,

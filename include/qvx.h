@@ -131,7 +131,8 @@ typedef struct {
     int32_t n_tiled_steps;           /* contractions with a register-tiled form (global-arena engines) */
     int32_t n_phases;                /* levels of mutually independent contractions */
     int32_t n_open_qubits;           /* amplitudes per bitstring = 2^n_open_qubits */
-    int32_t reserved;
+    int32_t grad_smem_bytes;         /* shared memory per work item of the gradient kernel's on-chip
+                                        form (0: absent; larger than the device allows: global memory) */
 } qvx_plan_info;
 
 typedef struct qvx_plan qvx_plan;
@@ -251,6 +252,11 @@ qvx_status qvx_workspace_status(const qvx_plan *plan, void *workspace_dev, void 
 
 /* Message for the calling thread's last failed call ("" if none). */
 const char *qvx_last_error(void);
+
+/* Kernels the calling host thread has launched through the library so far (successful
+ * launches only; a count, not device work). Reading it before and after a call gives that
+ * call's launches. No paper counterpart: instrumentation of this implementation. */
+uint64_t qvx_kernel_launches(void);
 
 #ifdef __cplusplus
 }

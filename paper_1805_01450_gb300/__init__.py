@@ -59,7 +59,7 @@ class PlanInfo(ctypes.Structure):
                 ("n_grad_steps", ctypes.c_int32), ("grad_arena_bytes", ctypes.c_int64),
                 ("grad_flops_per_amplitude", ctypes.c_double), ("grad_bytes_per_amplitude", ctypes.c_double),
                 ("n_tiled_steps", ctypes.c_int32), ("n_phases", ctypes.c_int32),
-                ("n_open_qubits", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("n_open_qubits", ctypes.c_int32), ("grad_smem_bytes", ctypes.c_int32)]
 
 
 _lib = None
@@ -67,7 +67,7 @@ EXPORTED = ("qvx_plan_opts_default", "qvx_graph_export", "qvx_plan_create", "qvx
             "qvx_plan_get_info", "qvx_plan_get_order", "qvx_plan_get_image", "qvx_workspace_size", "qvx_workspace_init",
             "qvx_amplitude", "qvx_amplitude_slices", "qvx_slice_terms", "qvx_workspace_status",
             "qvx_last_error", "qvx_amplitude_noalloc", "qvx_amplitude_grad", "qvx_amplitude_host",
-            "qvx_selftest_wait_timeout")
+            "qvx_selftest_wait_timeout", "qvx_kernel_launches")
 
 
 def lib():
@@ -95,6 +95,7 @@ def lib():
         "qvx_slice_terms": (ctypes.c_int, [P, P, i64, i64, i64, P, P, ctypes.c_size_t, P]),
         "qvx_workspace_status": (ctypes.c_int, [P, P, P]),
         "qvx_last_error": (ctypes.c_char_p, []),
+        "qvx_kernel_launches": (ctypes.c_uint64, []),
         "qvx_amplitude_noalloc": (ctypes.c_int, [P, P, i64, P, P]),
         "qvx_amplitude_grad": (ctypes.c_int, [P, P, i64, P, i32, P, P, P, ctypes.c_size_t, P]),
         "qvx_amplitude_host": (ctypes.c_int, [P, P, i64, P, P, ctypes.c_size_t, P]),

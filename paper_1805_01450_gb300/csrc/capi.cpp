@@ -180,13 +180,35 @@ qvx_status run_items(qvx_plan *plan, const uint64_t *bits, int64_t batch, int64_
     }
     for (int64_t ib = 0; ib < n_items; ib += w.items_in_flight) {
         const int64_t n = std::min<int64_t>(w.items_in_flight, n_items - ib);
-        for (size_t s = 0; s < p.steps.size(); s++) {
-            const uint32_t rc = (uint32_t)p.tensors[p.steps[s].c].modes.size();
-            const PStepShape sh = shape_of(p, s);
-            if (sh.nk >= 5) e = qvx::launch_splitk_step(a, (uint32_t)s, ib, n, arenas, rc, st);
-            else if (p.regtile[s].rm + p.regtile[s].rn > 0) e = qvx::launch_regtile_step(a, p.regtile[s], ib, n, arenas, st);
-            else e = qvx::launch_step(a, (uint32_t)s, ib, n, arenas, rc, st);
-            if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+        for (const auto &ph : p.phases) {
+            // the phase's small steps (under 2^18 outputs over the items in flight) share one
+            // launch; the others get their own
+            qvx::StepGroup grp{};
+            for (int s = ph.first; s < ph.second; s++) {
+                const uint32_t rc = (uint32_t)p.tensors[p.steps[s].c].modes.size();
+                const PStepShape sh = shape_of(p, s);
+                const uint64_t threads = (uint64_t)n << rc;
+                if (threads < (1u << 18) && sh.nk < 5 && grp.n < (uint32_t)qvx::kMaxGroupSteps) {
+                    grp.step[grp.n] = (uint32_t)s;
+                    grp.first_block[grp.n + 1] = grp.first_block[grp.n] + (uint32_t)((threads + 255) / 256);
+                    grp.n++;
+                    continue;
+                }
+                if (sh.nk >= 5) e = qvx::launch_splitk_step(a, (uint32_t)s, ib, n, arenas, rc, st);
+                else if (p.regtile[s].rm + p.regtile[s].rn > 0) e = qvx::launch_regtile_step(a, p.regtile[s], ib, n, arenas, st);
+                else e = qvx::launch_step(a, (uint32_t)s, ib, n, arenas, rc, st);
+                if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+            }
+            if (grp.n == 1) {
+                const int s = (int)grp.step[0];
+                const uint32_t rc = (uint32_t)p.tensors[p.steps[s].c].modes.size();
+                if (p.regtile[s].rm + p.regtile[s].rn > 0) e = qvx::launch_regtile_step(a, p.regtile[s], ib, n, arenas, st);
+                else e = qvx::launch_step(a, (uint32_t)s, ib, n, arenas, rc, st);
+                if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+            } else if (grp.n > 1) {
+                if ((e = qvx::launch_step_group(a, grp, ib, n, arenas, st)) != cudaSuccess)
+                    return cuda_fail(e, "step group launch");
+            }
         }
         if ((e = qvx::launch_finish_items(a, ib, n, arenas, st)) != cudaSuccess)
             return cuda_fail(e, "finish kernel launch");
@@ -310,6 +332,8 @@ qvx_status qvx_plan_get_info(const qvx_plan *plan, qvx_plan_info *info) {
     for (const qvx::RegTileStep &r : p.regtile) info->n_tiled_steps += r.rm + r.rn > 0 ? 1 : 0;
     info->n_phases = (int32_t)p.phases.size();
     info->n_open_qubits = (int32_t)p.open_qubits.size();
+    info->grad_smem_bytes = p.opts.gradient
+        ? (int32_t)qvx::grad_smem_bytes(reinterpret_cast<const qvx::DevProgram *>(p.image.data())) : 0;
     info->grad_bytes_per_amplitude = p.grad_bytes_per_item * (double)info->n_items_per_bitstring;
     return QVX_OK;
 }
@@ -476,8 +500,26 @@ qvx_status qvx_amplitude_grad(qvx_plan *plan, const uint64_t *bitstrings_dev, in
     g.slots = w.grad_slots;
     g.partials = reinterpret_cast<qvx::ExactPair *>(base + w.partials);
     g.gpart = reinterpret_cast<qvx::ExactPair *>(base + w.grad_partials);
-    const int grid = (int)std::min<int64_t>(batch * n_outer, w.grad_slots);
-    if ((e = qvx::launch_grad_program(g, grid, st)) != cudaSuccess) return cuda_fail(e, "gradient kernel launch");
+    const size_t gsm = qvx::grad_smem_bytes(h);
+    if (gsm) {
+        int dev = -1;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+        if (dev != plan->grad_device) {
+            DeviceCaps caps;
+            qvx_status s = device_caps(&caps);
+            if (s != QVX_OK) return s;
+            plan->grad_sms = caps.sms;
+            plan->grad_ctas_per_sm = qvx::grad_smem_blocks_per_sm(gsm);
+            plan->grad_device = dev;
+        }
+    }
+    if (gsm && plan->grad_ctas_per_sm > 0) {
+        const int grid = (int)std::min<int64_t>(batch * n_outer, (int64_t)plan->grad_sms * plan->grad_ctas_per_sm);
+        if ((e = qvx::launch_grad_smem(g, grid, gsm, st)) != cudaSuccess) return cuda_fail(e, "gradient kernel launch");
+    } else {
+        const int grid = (int)std::min<int64_t>(batch * n_outer, w.grad_slots);
+        if ((e = qvx::launch_grad_program(g, grid, st)) != cudaSuccess) return cuda_fail(e, "gradient kernel launch");
+    }
     if ((e = qvx::launch_slice_sum(base + w.image, g.partials, batch, n_outer, amps_dev, st)) != cudaSuccess)
         return cuda_fail(e, "slice sum launch");
     if ((e = qvx::launch_grad_sum(base + w.image, g.gpart, batch, n_outer, h->n_param_leaves, (uint32_t)p.n_params,
@@ -529,6 +571,8 @@ qvx_status qvx_workspace_status(const qvx_plan *plan, void *ws, void *stream) {
 }
 
 const char *qvx_last_error(void) { return g_err.c_str(); }
+
+uint64_t qvx_kernel_launches(void) { return qvx::launches_issued(); }
 
 }  // extern "C"
 

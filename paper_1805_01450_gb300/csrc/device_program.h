@@ -76,6 +76,18 @@ struct GenStep {
     uint32_t ro, nk;               // output rank, summed bits
 };
 
+// Tabulated form of the gradient program for the shared-memory gradient kernel: one record
+// per output entry of every gradient step, in step order (so each level phase is one
+// contiguous range of records). Operand v (X or Y) of the entry is base(kind, vr) + vo:
+// the arena at offset vr, or the restricted leaf (or its derivative) vr of the work item.
+struct GradEntry {
+    uint16_t c;                    // arena offset of the output entry
+    uint16_t meta;                 // X kind (bits 0-1), Y kind (bits 2-3), summed bits nk (bits 4-7)
+    uint16_t xr, xo, yr, yo;
+    uint32_t k1;                   // nk == 1: X and Y offsets of summed index 1 (low / high 16 bits);
+                                   // nk >= 2: first of the 2^nk - 1 such pairs (index 1, 2, ...) in the k table
+};
+
 // A leaf that is one parametrised gate exp(-i theta (cos phi X + sin phi Y) / 2): its
 // stored entry e is matrix element code[e] (bit 1: row, bit 0: column) of U or dU/dtheta.
 struct ParamLeaf {
@@ -132,6 +144,9 @@ struct DevProgram {
     uint32_t n_open;               // open output qubits (2^n_open amplitudes per bitstring)
     uint32_t open_present;         // open qubits that are modes of the final tensor, low to high
     uint64_t regtile_off;          // byte offset of n_steps RegTileStep (0 if absent; rm + rn = 0: none)
+    uint64_t gentry_off;           // byte offset of the GradEntry records (0 if absent)
+    uint64_t gktab_off;            // byte offset of the k table (pairs of 16-bit offsets)
+    uint64_t gphase_entry_off;     // byte offset of n_grad_phases + 1 record indices (phase starts)
     uint64_t image_bytes;
 };
 
@@ -142,7 +157,8 @@ constexpr uint32_t kProgramMagic = 0x51565831u;  // "QVX1"
 namespace qvx {
 static_assert(sizeof(DevStep) == 136, "DevStep layout");
 static_assert(sizeof(DevLeaf) == 40, "DevLeaf layout");
-static_assert(sizeof(DevProgram) == 288, "DevProgram layout");
+static_assert(sizeof(DevProgram) == 312, "DevProgram layout");
+static_assert(sizeof(GradEntry) == 16, "GradEntry layout");
 static_assert(sizeof(RegTileStep) == 224, "RegTileStep layout");
 static_assert(sizeof(GenOperand) == 112, "GenOperand layout");
 static_assert(sizeof(GenStep) == 240, "GenStep layout");

@@ -524,6 +524,33 @@ __global__ void step_kernel(LaunchArgs a, uint32_t s_idx, int64_t item_begin, in
     arena[st.c_off + c] = step_entry(st, c, A, B, unary);
 }
 
+__global__ void step_group_kernel(LaunchArgs a, StepGroup g, int64_t item_begin, int64_t n_items, float2 *arenas) {
+    uint32_t j = 0;
+    while (j + 1 < g.n && blockIdx.x >= g.first_block[j + 1]) j++;
+    const unsigned char *img = a.image;
+    const DevProgram *P = reinterpret_cast<const DevProgram *>(img);
+    const DevStep &st = reinterpret_cast<const DevStep *>(img + P->steps_off)[g.step[j]];
+    const uint64_t per = 1ull << st.rc;
+    const uint64_t tid = (uint64_t)(blockIdx.x - g.first_block[j]) * blockDim.x + threadIdx.x;
+    if (tid >= per * (uint64_t)n_items) return;
+    const int64_t il = (int64_t)(tid >> st.rc);
+    const uint32_t c = (uint32_t)(tid & (per - 1));
+    float2 *arena = arenas + (uint64_t)il * a.arena_elems;
+    const bool unary = st.flags & kStepUnary;
+    const DevLeaf *leaves = reinterpret_cast<const DevLeaf *>(img + P->leaves_off);
+    const float2 *ldata = reinterpret_cast<const float2 *>(img + P->leaf_data_off);
+    uint64_t x = 0, o = 0;
+    if (st.flags & (kStepALeaf | kStepBLeaf)) {
+        const int64_t item = item_begin + il;
+        x = a.bitstrings[item / a.o_count];
+        o = (uint64_t)(a.o_begin + item % a.o_count);
+    }
+    const float2 *A = (st.flags & kStepALeaf) ? ldata + leaf_base(leaves[st.a_off], x, o) : arena + st.a_off;
+    const float2 *B = unary ? A
+                            : ((st.flags & kStepBLeaf) ? ldata + leaf_base(leaves[st.b_off], x, o) : arena + st.b_off);
+    arena[st.c_off + c] = step_entry(st, c, A, B, unary);
+}
+
 // ------------------------------------------------------------------ persistent engine
 constexpr uint32_t kBarrierPolls = 1u << 24;   // x ~64 ns sleeps: about a second
 
@@ -908,6 +935,125 @@ __global__ void __launch_bounds__(256) grad_program_kernel(GradArgs g) {
     }
 }
 
+// One output entry of the gradient program from its record: sum over the summed index of
+// X * Y, where an operand is the shared-memory arena, a restricted leaf (base in lbase), its
+// derivative, or the constant one.
+__device__ __forceinline__ float2 grad_record_value(const uint4 rv, const float2 *arena, const uint32_t *lbase,
+                                                    const float2 *ldata, const float2 *ddata,
+                                                    const uint32_t *ktab) {
+    const uint32_t meta = rv.x >> 16;
+    const uint32_t xr = rv.y & 0xffffu, xo = rv.y >> 16, yr = rv.z & 0xffffu, yo = rv.z >> 16;
+    const uint32_t xk = meta & 3u, yk = (meta >> 2) & 3u, nk = (meta >> 4) & 15u;
+    const float2 *X = xk == kOpArena ? arena + xr : xk == kOpLeaf ? ldata + lbase[xr] : xk == kOpDeriv ? ddata + lbase[xr] : nullptr;
+    const float2 *Y = yk == kOpArena ? arena + yr : yk == kOpLeaf ? ldata + lbase[yr] : yk == kOpDeriv ? ddata + lbase[yr] : nullptr;
+    const float2 one = make_float2(1.f, 0.f);
+    if (X) X += xo;
+    if (Y) Y += yo;
+    float2 acc = make_float2(0.f, 0.f);
+    if (nk == 2) {   // the three offset pairs first, so the six operand loads are independent
+        const uint32_t k1 = ktab[rv.w], k2 = ktab[rv.w + 1], k3 = ktab[rv.w + 2];
+        const float2 x0 = X ? X[0] : one, y0 = Y ? Y[0] : one;
+        const float2 x1 = X ? X[k1 & 0xffffu] : one, y1 = Y ? Y[k1 >> 16] : one;
+        const float2 x2 = X ? X[k2 & 0xffffu] : one, y2 = Y ? Y[k2 >> 16] : one;
+        const float2 x3 = X ? X[k3 & 0xffffu] : one, y3 = Y ? Y[k3 >> 16] : one;
+        cmac(acc, x0, y0);
+        cmac(acc, x1, y1);
+        cmac(acc, x2, y2);
+        cmac(acc, x3, y3);
+        return acc;
+    }
+    cmac(acc, X ? X[0] : one, Y ? Y[0] : one);
+    if (nk == 1) {
+        cmac(acc, X ? X[rv.w & 0xffffu] : one, Y ? Y[rv.w >> 16] : one);
+    } else if (nk > 2) {
+#pragma unroll 4
+        for (uint32_t k = 1; k < (1u << nk); k++) {
+            const uint32_t kp = ktab[rv.w + k - 1];
+            cmac(acc, X ? X[kp & 0xffffu] : one, Y ? Y[kp >> 16] : one);
+        }
+    }
+    return acc;
+}
+
+constexpr int kGradPrefetch = 4;   // records per thread loaded one phase ahead
+
+// The gradient program with the work item's arena in shared memory: the records of each
+// level phase are spread over the CTA's threads, one barrier per phase, and each thread
+// loads its first record of the next phase before the barrier of the current one.
+__global__ void __launch_bounds__(256) grad_smem_kernel(GradArgs g) {
+    extern __shared__ float4 gsm[];
+    const unsigned char *img = g.image;
+    const DevProgram *P = reinterpret_cast<const DevProgram *>(img);
+    float2 *arena = reinterpret_cast<float2 *>(gsm);
+    uint32_t *lbase = reinterpret_cast<uint32_t *>(arena + P->grad_arena_elems);
+    const uint4 *rec = reinterpret_cast<const uint4 *>(img + P->gentry_off);
+    const uint32_t *ktab = reinterpret_cast<const uint32_t *>(img + P->gktab_off);
+    const uint32_t *pe = reinterpret_cast<const uint32_t *>(img + P->gphase_entry_off);
+    const DevLeaf *leaves = reinterpret_cast<const DevLeaf *>(img + P->leaves_off);
+    const float2 *ldata = reinterpret_cast<const float2 *>(img + P->leaf_data_off);
+    const float2 *ddata = reinterpret_cast<const float2 *>(img + P->deriv_data_off);
+    const uint32_t n_phases = P->n_grad_phases, n_leaves = P->n_leaves, npl = P->n_param_leaves;
+    const int64_t n_items = g.batch * g.o_count;
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int64_t b = item / g.o_count;
+        const uint64_t o = (uint64_t)(item % g.o_count);
+        const uint64_t x = g.bitstrings[b];
+        for (uint32_t l = threadIdx.x; l < n_leaves; l += blockDim.x) lbase[l] = leaf_base(leaves[l], x, o);
+        // a thread's first kGradPrefetch records of a phase are loaded during the phase before
+        uint4 cur[kGradPrefetch];
+#pragma unroll
+        for (int j = 0; j < kGradPrefetch; j++) {
+            const uint32_t e = pe[0] + threadIdx.x + j * blockDim.x;
+            cur[j] = n_phases > 0 && e < pe[1] ? rec[e] : make_uint4(0u, 0u, 0u, 0u);
+        }
+        __syncthreads();
+        for (uint32_t ph = 0; ph < n_phases; ph++) {
+            const uint32_t e0 = pe[ph], e1 = pe[ph + 1];
+            uint4 nxt[kGradPrefetch];
+#pragma unroll
+            for (int j = 0; j < kGradPrefetch; j++) {
+                const uint32_t e = e1 + threadIdx.x + j * blockDim.x;
+                nxt[j] = ph + 1 < n_phases && e < pe[ph + 2] ? rec[e] : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int j = 0; j < kGradPrefetch; j++)
+                if (e0 + threadIdx.x + j * blockDim.x < e1)
+                    arena[cur[j].x & 0xffffu] = grad_record_value(cur[j], arena, lbase, ldata, ddata, ktab);
+            for (uint32_t e = e0 + threadIdx.x + kGradPrefetch * blockDim.x; e < e1; e += blockDim.x) {
+                const uint4 rv = rec[e];
+                arena[rv.x & 0xffffu] = grad_record_value(rv, arena, lbase, ldata, ddata, ktab);
+            }
+#pragma unroll
+            for (int j = 0; j < kGradPrefetch; j++) cur[j] = nxt[j];
+            __syncthreads();
+        }
+        const bool zero = (x & P->zero_mask) != 0;
+        if (threadIdx.x < 32) {
+            const float2 *fin = arena + P->final_fwd_off;
+            Fx re = {0ull, 0ll}, im = {0ull, 0ll};
+            const uint32_t n_in = P->n_inner, present = P->final_present;
+            for (uint32_t i = threadIdx.x; i < (1u << n_in); i += 32) {
+                uint32_t fi = 0, bit = 0;
+                for (uint32_t j = 0; j < n_in; j++)
+                    if ((present >> j) & 1u) fi |= ((i >> j) & 1u) << bit++;
+                const float2 t = zero ? make_float2(0.f, 0.f) : fin[fi];
+                re = fx_add(re, fx_from_float(t.x));
+                im = fx_add(im, fx_from_float(t.y));
+            }
+            for (int d = 16; d > 0; d >>= 1) {
+                re = fx_add(re, fx_shfl_down(re, d));
+                im = fx_add(im, fx_shfl_down(im, d));
+            }
+            if (threadIdx.x == 0) g.partials[item] = fx_pair(re, im);
+        }
+        for (uint32_t lp = threadIdx.x; lp < npl; lp += blockDim.x) {
+            const float2 t = zero ? make_float2(0.f, 0.f) : arena[P->gslot_off + lp];
+            g.gpart[(uint64_t)item * npl + lp] = fx_pair(fx_from_float(t.x), fx_from_float(t.y));
+        }
+        __syncthreads();
+    }
+}
+
 // One block per (bitstring, parameter): exact sum over the work items and over the
 // parameter's leaves (CSR lists in the image), rounded once and times the plan's scalar.
 __global__ void grad_sum_kernel(const unsigned char *img, const ExactPair *gpart, int64_t o_count, uint32_t npl,
@@ -975,29 +1121,67 @@ __global__ void wait_selftest_kernel(unsigned *words, unsigned *status, uint32_t
     if (out[0] && out[1]) atomicCAS(status, 0u, 4u /* QVX_ETIMEOUT */);
 }
 
+thread_local uint64_t t_launches = 0;   // kernels this host thread has launched
+
+cudaError_t counted(cudaError_t e) {
+    if (e == cudaSuccess) t_launches++;
+    return e;
+}
+
 }  // namespace
+
+uint64_t launches_issued() { return t_launches; }
 
 cudaError_t launch_wait_selftest(unsigned *words, unsigned *status, uint32_t polls, unsigned *out, cudaStream_t s) {
     wait_selftest_kernel<<<1, 32, 0, s>>>(words, status, polls, out);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_set_params(unsigned char *image, uint32_t n_param_leaves, const double *thetas, cudaStream_t s) {
     if (n_param_leaves == 0) return cudaSuccess;
     set_params_kernel<<<n_param_leaves, 32, 0, s>>>(image, thetas);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_grad_program(const GradArgs &g, int grid, cudaStream_t s) {
     grad_program_kernel<<<grid, 256, 0, s>>>(g);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
+}
+
+size_t grad_smem_bytes(const DevProgram *h) {
+    if (!h->gentry_off) return 0;
+    return ((size_t)h->grad_arena_elems * 8 + (size_t)h->n_leaves * 4 + 15) & ~size_t(15);
+}
+
+int grad_smem_blocks_per_sm(size_t smem_bytes) {
+    static bool raised[64] = {false};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (dev >= 0 && dev < 64 && !raised[dev]) {
+        int optin = 0;
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+        if (cudaFuncSetAttribute(grad_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess)
+            return 0;
+        raised[dev] = true;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, grad_smem_kernel, 256, smem_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+cudaError_t launch_grad_smem(const GradArgs &g, int grid, size_t smem_bytes, cudaStream_t s) {
+    grad_smem_kernel<<<grid, 256, smem_bytes, s>>>(g);
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_grad_sum(const unsigned char *image, const ExactPair *gpart, int64_t batch, int64_t o_count,
                             uint32_t n_param_leaves, uint32_t n_params, double *grad, cudaStream_t s) {
     if (n_params == 0 || batch == 0) return cudaSuccess;
     grad_sum_kernel<<<(unsigned)(batch * n_params), 256, 0, s>>>(image, gpart, o_count, n_param_leaves, n_params, grad);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 // The dynamic shared-memory limit is an attribute of the kernel function, shared by every
@@ -1057,7 +1241,7 @@ cudaError_t launch_fused(const LaunchArgs &a, int warps_per_item, int items_per_
     const int threads = 32 * warps_per_item * items_per_cta;
     if (a.smem_steps_bytes) fused_program_kernel<true><<<grid, threads, smem_bytes, s>>>(a, warps_per_item);
     else fused_program_kernel<false><<<grid, threads, smem_bytes, s>>>(a, warps_per_item);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_step(const LaunchArgs &a, uint32_t step, int64_t item_begin, int64_t n_items,
@@ -1066,7 +1250,14 @@ cudaError_t launch_step(const LaunchArgs &a, uint32_t step, int64_t item_begin, 
     const int threads = 256;
     const uint64_t blocks = (total + threads - 1) / threads;
     step_kernel<<<(unsigned)blocks, threads, 0, s>>>(a, step, item_begin, n_items, arenas);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
+}
+
+cudaError_t launch_step_group(const LaunchArgs &a, const StepGroup &g, int64_t item_begin, int64_t n_items,
+                              float2 *arenas, cudaStream_t s) {
+    if (g.n == 0 || g.n > (uint32_t)kMaxGroupSteps || g.first_block[g.n] == 0) return cudaErrorInvalidConfiguration;
+    step_group_kernel<<<g.first_block[g.n], 256, 0, s>>>(a, g, item_begin, n_items, arenas);
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_splitk_step(const LaunchArgs &a, uint32_t step, int64_t item_begin, int64_t n_items,
@@ -1074,7 +1265,7 @@ cudaError_t launch_splitk_step(const LaunchArgs &a, uint32_t step, int64_t item_
     const uint64_t blocks = (((uint64_t)n_items << rc) + 31) / 32;
     if (blocks > 0x7fffffffull) return cudaErrorInvalidConfiguration;
     splitk_step_kernel<<<(unsigned)blocks, 256, 0, s>>>(a, step, item_begin, n_items, arenas);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_regtile_step(const LaunchArgs &a, const RegTileStep &rs, int64_t item_begin, int64_t n_items,
@@ -1092,7 +1283,7 @@ cudaError_t launch_regtile_step(const LaunchArgs &a, const RegTileStep &rs, int6
         case 7: regtile_step_kernel<2, 1><<<nb, 256, 0, s>>>(a, rs, item_begin, n_items, arenas); break;
         default: regtile_step_kernel<2, 2><<<nb, 256, 0, s>>>(a, rs, item_begin, n_items, arenas); break;
     }
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 int persistent_blocks_per_sm() {
@@ -1105,7 +1296,7 @@ cudaError_t launch_persistent(const LaunchArgs &a, int64_t item_begin, int64_t n
                               unsigned *bar_count, unsigned *bar_gen, int grid, cudaStream_t s) {
     LaunchArgs aa = a;
     void *args[] = {&aa, &item_begin, &n_items, &arenas, &bar_count, &bar_gen};
-    return cudaLaunchCooperativeKernel((const void *)persistent_program_kernel, dim3(grid), dim3(256), args, 0, s);
+    return counted(cudaLaunchCooperativeKernel((const void *)persistent_program_kernel, dim3(grid), dim3(256), args, 0, s));
 }
 
 cudaError_t launch_finish_items(const LaunchArgs &a, int64_t item_begin, int64_t n_items,
@@ -1113,13 +1304,13 @@ cudaError_t launch_finish_items(const LaunchArgs &a, int64_t item_begin, int64_t
     const int per_block = 8;
     const int64_t blocks = (n_items + per_block - 1) / per_block;
     finish_kernel<<<(unsigned)blocks, 32 * per_block, 0, s>>>(a, item_begin, n_items, arenas);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 cudaError_t launch_slice_sum(const unsigned char *image, const ExactPair *partials, int64_t batch, int64_t o_count,
                              double *amps, cudaStream_t s) {
     slice_sum_kernel<<<(unsigned)batch, 256, 0, s>>>(image, partials, o_count, amps);
-    return cudaGetLastError();
+    return counted(cudaGetLastError());
 }
 
 }  // namespace qvx

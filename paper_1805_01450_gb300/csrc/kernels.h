@@ -52,6 +52,16 @@ bool fused_shape(const DevProgram *h, uint64_t arena_elems, int warps_per_item, 
 // global-memory arena per item.
 cudaError_t launch_step(const LaunchArgs &a, uint32_t step, int64_t item_begin, int64_t n_items,
                         float2 *arenas, uint32_t rc, cudaStream_t s);
+// Several independent small steps (of one level phase) in one launch: step j takes the CTAs
+// [first_block[j], first_block[j + 1]), one thread per output entry of each work item.
+constexpr int kMaxGroupSteps = 24;
+struct StepGroup {
+    uint32_t n;
+    uint32_t step[kMaxGroupSteps];
+    uint32_t first_block[kMaxGroupSteps + 1];
+};
+cudaError_t launch_step_group(const LaunchArgs &a, const StepGroup &g, int64_t item_begin, int64_t n_items,
+                              float2 *arenas, cudaStream_t s);
 // Contraction with many summed entries: 32 outputs per CTA, the summed index split over warps.
 cudaError_t launch_splitk_step(const LaunchArgs &a, uint32_t step, int64_t item_begin, int64_t n_items,
                                float2 *arenas, uint32_t rc, cudaStream_t s);
@@ -79,10 +89,18 @@ struct GradArgs {
 // Rewrites the parametrised leaves (U and dU/dtheta) from thetas (device, or the image's own).
 cudaError_t launch_set_params(unsigned char *image, uint32_t n_param_leaves, const double *thetas, cudaStream_t s);
 cudaError_t launch_grad_program(const GradArgs &g, int grid, cudaStream_t s);
+// The same program from its per-entry records with the work item's arena in shared memory:
+// the bytes a CTA needs (0 if the plan has no records), how many CTAs fit on an SM (0: none;
+// raises the kernel's shared-memory limit once per device), and the launch.
+size_t grad_smem_bytes(const DevProgram *h);
+int grad_smem_blocks_per_sm(size_t smem_bytes);
+cudaError_t launch_grad_smem(const GradArgs &g, int grid, size_t smem_bytes, cudaStream_t s);
 // d alpha / d theta_p = exact sum over work items and the parameter's leaves.
 cudaError_t launch_grad_sum(const unsigned char *image, const ExactPair *gpart, int64_t batch, int64_t o_count,
                             uint32_t n_param_leaves, uint32_t n_params, double *grad, cudaStream_t s);
 
+// Kernels the calling host thread has launched through these launchers (successful launches).
+uint64_t launches_issued();
 // Self-test of the bounded waits (grid barrier and mbarrier that can never complete).
 cudaError_t launch_wait_selftest(unsigned *words, unsigned *status, uint32_t polls, unsigned *out, cudaStream_t s);
 

@@ -782,6 +782,43 @@ bool map_runs(const std::vector<int> &src, const std::vector<int> &dst, DevRun *
 // the modes of C and B that A lacks (and symmetrically for B); the adjoint of the final
 // tensor is the constant 2^(inner slice modes it lacks). Each parametrised leaf then gets
 // d alpha / d theta = sum over its entries of adj(leaf) * dU/dtheta (a rank-0 step).
+// First-fit placement of tensors with lifetimes in phases: tensor i (size[i] entries) is
+// written in phase birth[i] and last read in phase death[i]. The outputs of a phase are
+// placed while every tensor read in that phase is still live, and released after their last
+// reading phase, so no phase writes over anything it, or a later phase, reads.
+int64_t place_by_phases(const std::vector<int64_t> &size, const std::vector<int> &birth,
+                        const std::vector<int> &death, int n_phases, std::vector<int64_t> *off) {
+    struct Block { int64_t off, len; int id; };
+    std::vector<Block> live;
+    std::vector<std::vector<int>> born(n_phases + 1), dies(n_phases + 1);
+    off->assign(size.size(), -1);
+    for (size_t i = 0; i < size.size(); i++) {
+        if (birth[i] < 0) continue;
+        born[birth[i]].push_back((int)i);
+        const int d = std::max(death[i], birth[i]);
+        if (d < n_phases) dies[d].push_back((int)i);
+    }
+    int64_t peak = 0;
+    for (int ph = 0; ph < n_phases; ph++) {
+        for (int id : born[ph]) {
+            const int64_t len = (size[id] + 3) & ~int64_t(3);   // 32-byte granules
+            std::sort(live.begin(), live.end(), [](const Block &x, const Block &y) { return x.off < y.off; });
+            int64_t at = 0;
+            for (const Block &bl : live) {
+                if (bl.off - at >= len) break;
+                at = std::max(at, bl.off + bl.len);
+            }
+            live.push_back({at, len, id});
+            (*off)[id] = at;
+            peak = std::max(peak, at + len);
+        }
+        for (int id : dies[ph])
+            for (size_t j = 0; j < live.size(); j++)
+                if (live[j].id == id) { live.erase(live.begin() + j); break; }
+    }
+    return peak;
+}
+
 bool build_grad_program(Plan &p, const std::vector<int> &dev_leaf, std::string *err) {
     const size_t nt = p.tensors.size();
     std::vector<char> need(nt, 0);
@@ -790,21 +827,18 @@ bool build_grad_program(Plan &p, const std::vector<int> &dev_leaf, std::string *
         if (T.leaf >= 0 && T.consumer >= 0 && p.leaves[T.leaf].param >= 0) need[t] = 1;
     }
     for (const PStep &st : p.steps) need[st.c] = need[st.a] || (st.b >= 0 && need[st.b]);
-    int64_t off = 0;
-    auto alloc = [&](int64_t n) {
-        const int64_t r = off;
-        off += (n + 3) & ~int64_t(3);
-        return r;
-    };
+    // arena tensors by id: forward output of tensor t = t, adjoint of t = nt + t, the
+    // derivative slots = 2 nt; steps are emitted with ids as offsets, placed afterwards
     std::vector<int64_t> fo(nt, -1), ao(nt, -1);
-    for (const PStep &st : p.steps) fo[st.c] = alloc(int64_t(1) << p.tensors[st.c].modes.size());
+    for (const PStep &st : p.steps) fo[st.c] = st.c;
     std::vector<int> pl;   // parametrised leaf tensors
     for (size_t t = 0; t < nt; t++) {
         if (!need[t]) continue;
-        ao[t] = alloc(int64_t(1) << p.tensors[t].modes.size());
+        ao[t] = (int64_t)(nt + t);
         if (p.tensors[t].leaf >= 0) pl.push_back((int)t);
     }
-    const int64_t gslot = alloc((int64_t)pl.size());
+    const int64_t gslot = (int64_t)(2 * nt);
+    std::vector<int64_t> out_rel;   // per gradient step: entry offset inside its output tensor
     p.grad_steps.clear();
     auto operand = [&](GenOperand &o, int t, bool adj, const std::vector<int> &out, const std::vector<int> &S) {
         std::memset(&o, 0, sizeof(o));
@@ -830,6 +864,7 @@ bool build_grad_program(Plan &p, const std::vector<int> &dev_leaf, std::string *
         g.nk = (uint32_t)S.size();
         if (!operand(g.x, x, xadj, out, S) || !operand(g.y, y, yadj, out, S)) return false;
         p.grad_steps.push_back(g);
+        out_rel.push_back(0);
         return true;
     };
     auto minus = [](const std::vector<int> &u, const std::vector<int> &w, const std::vector<int> &drop) {
@@ -883,7 +918,7 @@ bool build_grad_program(Plan &p, const std::vector<int> &dev_leaf, std::string *
         const int t = pl[i];
         GenStep g;
         std::memset(&g, 0, sizeof(g));
-        g.out_off = (uint64_t)(gslot + (int64_t)i);
+        g.out_off = (uint64_t)gslot;
         g.ro = 0;
         g.nk = (uint32_t)p.tensors[t].modes.size();
         const std::vector<int> none;
@@ -895,6 +930,7 @@ bool build_grad_program(Plan &p, const std::vector<int> &dev_leaf, std::string *
         p.grad_flops_per_item += 8.0 * std::ldexp(1.0, (int)g.nk);
         p.grad_bytes_per_item += 16.0 * std::ldexp(1.0, (int)g.nk) + 8.0;
         p.grad_steps.push_back(g);
+        out_rel.push_back((int64_t)i);
         p.grad_param_leaves.push_back(p.tensors[t].leaf);
     }
     p.grad_phase_first.push_back((uint32_t)p.grad_steps.size());
@@ -913,9 +949,94 @@ bool build_grad_program(Plan &p, const std::vector<int> &dev_leaf, std::string *
             acc += uint64_t(1) << p.grad_steps[g].ro;
         }
     }
-    p.grad_arena_elems = off;
-    p.grad_final_off = fo[F];
-    p.grad_gslot_off = gslot;
+    // lifetimes of the arena tensors in phases, then their places
+    const int n_ph = (int)firsts.size() - 1;
+    const size_t n_ids = 2 * nt + 1;
+    std::vector<int64_t> size(n_ids, 0);
+    std::vector<int> birth(n_ids, -1), death(n_ids, -1);
+    for (size_t t = 0; t < nt; t++) size[t] = size[nt + t] = int64_t(1) << p.tensors[t].modes.size();
+    size[gslot] = std::max<int64_t>((int64_t)pl.size(), 1);
+    for (int ph = 0; ph < n_ph; ph++)
+        for (uint32_t gi = firsts[ph]; gi < firsts[ph + 1]; gi++) {
+            const GenStep &g = p.grad_steps[gi];
+            if (birth[g.out_off] < 0) birth[g.out_off] = ph;
+            for (const GenOperand *o : {&g.x, &g.y})
+                if (o->kind == kOpArena) death[o->off] = std::max(death[o->off], ph);
+        }
+    if (fo[F] >= 0) death[fo[F]] = n_ph;    // read by the amplitude partial after the last phase
+    death[gslot] = n_ph;    // read by the derivative partials
+    std::vector<int64_t> place;
+    p.grad_arena_elems = place_by_phases(size, birth, death, n_ph, &place);
+    for (size_t gi = 0; gi < p.grad_steps.size(); gi++) {
+        GenStep &g = p.grad_steps[gi];
+        g.out_off = (uint64_t)(place[g.out_off] + out_rel[gi]);
+        for (GenOperand *o : {&g.x, &g.y})
+            if (o->kind == kOpArena) o->off = (uint64_t)place[o->off];
+    }
+    p.grad_final_off = fo[F] >= 0 ? place[fo[F]] : -1;
+    p.grad_gslot_off = place[gslot];
+    return true;
+}
+
+// Moves bit runs of v: sum of ((v >> src) & (2^len - 1)) << dst over the runs.
+uint32_t move_runs(uint32_t v, const DevRun *runs, int n) {
+    uint32_t r = 0;
+    for (int i = 0; i < n; i++) r |= ((v >> runs[i].src) & ((1u << runs[i].len) - 1u)) << runs[i].dst;
+    return r;
+}
+
+// The gradient program as one record per output entry (GradEntry) plus a table of summed-
+// index offsets; false if an offset does not fit 16 bits (the global-memory kernel runs).
+bool build_grad_tables(const Plan &p, std::vector<GradEntry> *ent, std::vector<uint32_t> *ktab,
+                       std::vector<uint32_t> *phase_entry) {
+    ent->clear();
+    ktab->clear();
+    phase_entry->clear();
+    if (p.grad_arena_elems > 65536) return false;
+    std::vector<uint32_t> first(p.grad_steps.size() + 1, 0);
+    for (size_t s = 0; s < p.grad_steps.size(); s++) {
+        const GenStep &g = p.grad_steps[s];
+        first[s] = (uint32_t)ent->size();
+        if (g.ro > 16 || g.nk > 15) return false;
+        auto ref = [](const GenOperand &op) { return op.kind == kOpOne ? uint64_t(0) : op.off; };
+        if (ref(g.x) > 65535 || ref(g.y) > 65535) return false;
+        uint32_t k1 = 0;
+        auto koff = [&](uint32_t k) -> int64_t {
+            const uint32_t kx = g.x.kind == kOpOne ? 0u : move_runs(k, g.x.kruns, g.x.n_kruns);
+            const uint32_t ky = g.y.kind == kOpOne ? 0u : move_runs(k, g.y.kruns, g.y.n_kruns);
+            if (kx > 65535 || ky > 65535) return -1;
+            return (int64_t)(kx | (ky << 16));
+        };
+        if (g.nk == 1) {
+            const int64_t v = koff(1);
+            if (v < 0) return false;
+            k1 = (uint32_t)v;
+        } else if (g.nk >= 2) {
+            k1 = (uint32_t)ktab->size();
+            for (uint32_t k = 1; k < (1u << g.nk); k++) {
+                const int64_t v = koff(k);
+                if (v < 0) return false;
+                ktab->push_back((uint32_t)v);
+            }
+        }
+        for (uint32_t oi = 0; oi < (1u << g.ro); oi++) {
+            GradEntry e;
+            const uint64_t c = g.out_off + oi;
+            const uint32_t xo = g.x.kind == kOpOne ? 0u : move_runs(oi, g.x.oruns, g.x.n_oruns);
+            const uint32_t yo = g.y.kind == kOpOne ? 0u : move_runs(oi, g.y.oruns, g.y.n_oruns);
+            if (c > 65535 || xo > 65535 || yo > 65535) return false;
+            e.c = (uint16_t)c;
+            e.meta = (uint16_t)(g.x.kind | (g.y.kind << 2) | (g.nk << 4));
+            e.xr = (uint16_t)ref(g.x);
+            e.xo = (uint16_t)xo;
+            e.yr = (uint16_t)ref(g.y);
+            e.yo = (uint16_t)yo;
+            e.k1 = k1;
+            ent->push_back(e);
+        }
+    }
+    first[p.grad_steps.size()] = (uint32_t)ent->size();
+    for (uint32_t s : p.grad_phase_first) phase_entry->push_back(first[s]);
     return true;
 }
 
@@ -1187,6 +1308,8 @@ bool serialize(Plan &p, std::string *err) {
     // gradient program
     std::vector<uint32_t> csr;
     std::vector<double> thetas;
+    std::vector<GradEntry> gent;
+    std::vector<uint32_t> gktab, gphase;
     if (p.opts.gradient) {
         if (!build_grad_program(p, dev_leaf, err)) return false;
         // parametrised leaves in the order of the derivative slots
@@ -1229,6 +1352,14 @@ bool serialize(Plan &p, std::string *err) {
         off = align256(off + p.grad_phase_first.size() * sizeof(uint32_t));
         h.grad_elem_off_off = off;
         off = align256(off + p.grad_elem_off.size() * sizeof(uint32_t));
+        if (build_grad_tables(p, &gent, &gktab, &gphase)) {
+            h.gentry_off = off;
+            off = align256(off + gent.size() * sizeof(GradEntry));
+            h.gktab_off = off;
+            off = align256(off + std::max<size_t>(gktab.size(), 1) * sizeof(uint32_t));
+            h.gphase_entry_off = off;
+            off = align256(off + gphase.size() * sizeof(uint32_t));
+        }
     }
     h.image_bytes = off;
     p.image.assign(off, 0);
@@ -1245,6 +1376,11 @@ bool serialize(Plan &p, std::string *err) {
         std::memcpy(img + h.grad_phases_off, p.grad_phase_first.data(), p.grad_phase_first.size() * sizeof(uint32_t));
         if (!p.grad_elem_off.empty())
             std::memcpy(img + h.grad_elem_off_off, p.grad_elem_off.data(), p.grad_elem_off.size() * sizeof(uint32_t));
+        if (h.gentry_off) {
+            std::memcpy(img + h.gentry_off, gent.data(), gent.size() * sizeof(GradEntry));
+            if (!gktab.empty()) std::memcpy(img + h.gktab_off, gktab.data(), gktab.size() * sizeof(uint32_t));
+            std::memcpy(img + h.gphase_entry_off, gphase.data(), gphase.size() * sizeof(uint32_t));
+        }
     }
     std::memcpy(p.image.data(), &h, sizeof(h));
     if (!ds.empty()) std::memcpy(p.image.data() + h.steps_off, ds.data(), ds.size() * sizeof(DevStep));

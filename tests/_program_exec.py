@@ -28,7 +28,8 @@ PROG = np.dtype([("magic", "<u4"), ("n_steps", "<u4"), ("n_leaves", "<u4"), ("pa
                  ("final_fwd_off", "<u8"), ("gslot_off", "<u8"), ("level_phases_off", "<u8"),
                  ("n_level_phases", "<u4"), ("n_grad_phases", "<u4"), ("grad_phases_off", "<u8"),
                  ("grad_elem_off_off", "<u8"), ("n_open", "<u4"), ("open_present", "<u4"),
-                 ("regtile_off", "<u8"), ("image_bytes", "<u8")])
+                 ("regtile_off", "<u8"), ("gentry_off", "<u8"), ("gktab_off", "<u8"),
+                 ("gphase_entry_off", "<u8"), ("image_bytes", "<u8")])
 FSTEP = np.dtype([("a_off", "<u4"), ("b_off", "<u4"), ("c_off", "<u4"), ("tab_off", "<u4"), ("flags", "<u4"),
                   ("rc", "u1"), ("nk_ab", "u1"), ("nk_a", "u1"), ("nk_b", "u1"), ("a_cb", "u1"), ("b_cb", "u1"),
                   ("nk", "u1"), ("pad1", "u1"), ("pad2", "<u4"), ("koff_a", "<u2", (4,)), ("koff_b", "<u2", (4,))])
@@ -41,8 +42,10 @@ RTSTEP = np.dtype([("a_off", "<u8"), ("b_off", "<u8"), ("c_off", "<u8"), ("flags
                    ("a_cb", "u1"), ("b_cb", "u1"), ("n_free", "u1"), ("na_runs", "u1"), ("nb_runs", "u1"),
                    ("free_runs", RUN, (6,)), ("runs_a", RUN, (12,)), ("runs_b", RUN, (12,)),
                    ("a_m", "<u4", (4,)), ("b_n", "<u4", (4,)), ("c_m", "<u4", (4,)), ("c_n", "<u4", (4,))])
-assert STEP.itemsize == 136 and LEAF.itemsize == 40 and PROG.itemsize == 288 and FSTEP.itemsize == 48
-assert RTSTEP.itemsize == 224
+assert STEP.itemsize == 136 and LEAF.itemsize == 40 and PROG.itemsize == 312 and FSTEP.itemsize == 48
+GENTRY = np.dtype([("c", "<u2"), ("meta", "<u2"), ("xr", "<u2"), ("xo", "<u2"), ("yr", "<u2"), ("yo", "<u2"),
+                   ("k1", "<u4")])
+assert RTSTEP.itemsize == 224 and GENTRY.itemsize == 16
 assert GOP.itemsize == 112 and GSTEP.itemsize == 240 and PLEAF.itemsize == 24
 OP_ARENA, OP_LEAF, OP_DERIV, OP_ONE = 0, 1, 2, 3
 UNARY, A_LEAF, B_LEAF = 1, 2, 4
@@ -95,6 +98,15 @@ class Program:
             ge = int(h["grad_elem_off_off"])
             self.grad_elem_off = np.frombuffer(buf[ge:ge + 4 * int(h["n_grad_steps"])].tobytes(),
                                                dtype="<u4").astype(np.int64)
+            self.gentries = None
+            if int(h["gentry_off"]):
+                po = int(h["gphase_entry_off"])
+                self.gphase_entry = np.frombuffer(buf[po:po + 4 * (ng + 1)].tobytes(), dtype="<u4").astype(np.int64)
+                n_ent = int(self.gphase_entry[-1])
+                eo = int(h["gentry_off"])
+                self.gentries = np.frombuffer(buf[eo:eo + 16 * n_ent].tobytes(), dtype=GENTRY)
+                ko = int(h["gktab_off"])
+                self.gktab = np.frombuffer(buf[ko:po].tobytes(), dtype="<u4").astype(np.int64)
 
     def _leaf_reader(self, li, x, o):
         L = self.leaves[li]
@@ -238,9 +250,10 @@ def rxy_and_derivative(theta, phi):
     return U, dU
 
 
-def grad_item(prog, x, o, thetas=None):
+def grad_item(prog, x, o, thetas=None, tables=False):
     """(alpha partial, per-slot derivative partials) of work item (x, o) by the image's
-    gradient program, with the parametrised leaves rebuilt from `thetas`."""
+    gradient program, with the parametrised leaves rebuilt from `thetas`. tables=True runs
+    the per-entry records (GradEntry) phase by phase instead of the gradient steps."""
     h = prog.h
     th = prog.thetas if thetas is None else np.asarray(thetas, dtype=np.float64)
     data = prog.leaf_data.copy()
@@ -274,7 +287,39 @@ def grad_item(prog, x, o, thetas=None):
         src = data if kind == OP_LEAF else deriv
         return lambda idx: src[b + idx]
 
-    for g in prog.gsteps:
+    if tables:
+        ent = prog.gentries
+        meta = ent["meta"].astype(np.int64)
+        nk = (meta >> 4) & 15
+        srcs = {1: data, 2: deriv}
+        for ph in range(len(prog.gphase_entry) - 1):
+            e0, e1 = int(prog.gphase_entry[ph]), int(prog.gphase_entry[ph + 1])
+            out = np.zeros(e1 - e0, dtype=np.complex128)
+            for j in range(e0, e1):
+                e = ent[j]
+                vals = []
+                for kind, r, off in (((meta[j] & 3), int(e["xr"]), int(e["xo"])),
+                                     (((meta[j] >> 2) & 3), int(e["yr"]), int(e["yo"]))):
+                    vals.append((kind, r, off))
+
+                def val(kind, r, off, dk):
+                    if kind == OP_ONE:
+                        return 1.0
+                    if kind == OP_ARENA:
+                        return arena[r + off + dk]
+                    return srcs[kind][base(prog.leaves[r]) + off + dk]
+                acc = 0j
+                for k in range(1 << int(nk[j])):
+                    if k == 0:
+                        kx = ky = 0
+                    else:
+                        kp = int(e["k1"]) if nk[j] == 1 else int(prog.gktab[int(e["k1"]) + k - 1])
+                        kx, ky = kp & 0xFFFF, kp >> 16
+                    acc += val(*vals[0], kx) * val(*vals[1], ky)
+                out[j - e0] = acc
+            # a phase's records are independent: write after computing all of them
+            arena[ent["c"][e0:e1].astype(np.int64)] = out
+    for g in ([] if tables else prog.gsteps):
         ro, nk = int(g["ro"]), int(g["nk"])
         oidx = np.arange(1 << ro, dtype=np.int64)
         X, Y = reader(g["x"]), reader(g["y"])
@@ -307,13 +352,13 @@ def grad_item(prog, x, o, thetas=None):
     return scalar * tot, slots
 
 
-def grad(prog, x, thetas=None):
+def grad(prog, x, thetas=None, tables=False):
     """(alpha, d alpha / d theta per parameter) over every work item."""
     n_out = int(prog.h["n_outer"])
     a = 0j
     slots = np.zeros(int(prog.h["n_param_leaves"]), dtype=np.complex128)
     for o in range(n_out):
-        ai, si = grad_item(prog, x, o, thetas)
+        ai, si = grad_item(prog, x, o, thetas, tables)
         a += ai
         slots += si
     g = np.zeros(int(prog.h["n_params"]), dtype=np.complex128)

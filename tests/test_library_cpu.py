@@ -186,11 +186,15 @@ def test_gradient_program_on_host_matches_oracle(name, maker, kw):
     assert p.info["n_params"] == c.n_params
     prog = Program(p.image())
     check_grad_schedule(prog)
+    assert prog.gentries is not None
     for x in [0] + cg.random_bitstrings(c.n_qubits, 2, 4):
         a_ref, g_ref = SV.sv_adjoint_grad(c, x)
         a, g = grad(prog, x)
         assert abs(a - a_ref) < 1e-6 * 2 ** (-c.n_qubits / 2)
         assert np.max(np.abs(g - g_ref)) < 1e-6 * 2 ** (-c.n_qubits / 2)
+        # the per-entry records of the shared-memory gradient kernel, phase by phase
+        a_t, g_t = grad(prog, x, tables=True)   # same products; numpy and Python may round apart
+        assert abs(a_t - a) < 1e-14 and np.max(np.abs(g_t - g)) < 1e-14
     # other angles through the parametrised leaves
     th = np.random.default_rng(0).uniform(0, 2 * np.pi, c.n_params)
     x = 1

@@ -182,19 +182,21 @@ qvx_status run_items(qvx_plan *plan, const uint64_t *bits, int64_t batch, int64_
         const int64_t n = std::min<int64_t>(w.items_in_flight, n_items - ib);
         for (const auto &ph : p.phases) {
             // the phase's small steps (under 2^18 outputs over the items in flight) share one
-            // launch; the others get their own
+            // launch; the others get their own. Split-K takes the steps with many summed
+            // entries and few outputs (it gives each output 8 warps' share of the sum).
             qvx::StepGroup grp{};
             for (int s = ph.first; s < ph.second; s++) {
                 const uint32_t rc = (uint32_t)p.tensors[p.steps[s].c].modes.size();
                 const PStepShape sh = shape_of(p, s);
                 const uint64_t threads = (uint64_t)n << rc;
-                if (threads < (1u << 18) && sh.nk < 5 && grp.n < (uint32_t)qvx::kMaxGroupSteps) {
+                const bool splitk = sh.nk >= 5 && rc <= 12;
+                if (threads < (1u << 18) && !splitk && grp.n < (uint32_t)qvx::kMaxGroupSteps) {
                     grp.step[grp.n] = (uint32_t)s;
                     grp.first_block[grp.n + 1] = grp.first_block[grp.n] + (uint32_t)((threads + 255) / 256);
                     grp.n++;
                     continue;
                 }
-                if (sh.nk >= 5) e = qvx::launch_splitk_step(a, (uint32_t)s, ib, n, arenas, rc, st);
+                if (splitk) e = qvx::launch_splitk_step(a, (uint32_t)s, ib, n, arenas, rc, st);
                 else if (p.regtile[s].rm + p.regtile[s].rn > 0) e = qvx::launch_regtile_step(a, p.regtile[s], ib, n, arenas, st);
                 else e = qvx::launch_step(a, (uint32_t)s, ib, n, arenas, rc, st);
                 if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");

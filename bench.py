@@ -31,12 +31,14 @@ WORKLOADS = {
     "grid4x4d10": ("grid", 4, 4, 10, 1001, 1002, 0, 1),
     "grid7x7d30-b1024": ("grid", 7, 7, 30, 3001, 3002, 4, 1024),
     "rot5x5d20-grad": ("rotation", 5, 5, 20, 4001, 4002, 8, 1),
-    "grid8x8d40-k16": ("grid", 8, 8, 40, 5001, 5002, 16, 1),
+    "grid8x8d40": ("grid", 8, 8, 40, 5001, 5002, 10, 1),
 }
 # workloads whose plan variant the autotuner also picks the slice count and engine for,
 # and the arena memory the global-arena engines may use there (MiB)
-TUNE = {"grid7x7d30-b1024": dict(slice_counts=(0, 2, 4, 6, 8), engines=("stepwise",), budget_s=90.0)}
-MEM_BUDGET_MB = {"grid7x7d30-b1024": 32768}
+TUNE = {"grid7x7d30-b1024": dict(slice_counts=(0, 2, 4, 6, 8), engines=("stepwise",), budget_s=90.0),
+        "grid8x8d40": dict(slice_counts=(8, 10, 12), engines=("stepwise", "stepwise-tc"), inner=(2, 4),
+                           budget_s=120.0)}
+MEM_BUDGET_MB = {"grid7x7d30-b1024": 32768, "grid8x8d40": 65536}
 DEFAULT_WORKLOAD = "grid6x6d25-k12"
 METRIC = "amplitudes/s and complex TFLOP/s (% of GB300 peak) at |Δα|≤1e-5·2^-N/2 vs FP64"
 L2_FLUSH_BYTES = 256 << 20
@@ -57,6 +59,8 @@ def parse():
     ap.add_argument("--mem-budget-mb", type=int, default=None,
                     help="arena memory of the global-arena engines (work items in flight; workload default)")
     ap.add_argument("--warps-per-item", type=int, default=None)
+    ap.add_argument("--tensor-cores", action="store_true",
+                    help="stepwise engine: dense contractions as bf16 hi/lo GEMMs on the tensor cores")
     ap.add_argument("--engine", default="auto")
     ap.add_argument("--sliced", type=int, default=None, help="override the workload's sliced-variable count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -233,7 +237,7 @@ def main():
     else:
         plan = q.Plan(circ, n_slices=k, inner_slices=-1 if args.inner_slices is None else args.inner_slices,
                       warps_per_item=args.warps_per_item or 1, engine=args.engine, gradient=grad,
-                      mem_budget_bytes=budget)
+                      mem_budget_bytes=budget, tensor_cores=args.tensor_cores)
     info = plan.info
     B = len(bits_host)
     bits = plan._bits(bits_host, dev)
@@ -351,6 +355,7 @@ def main():
         "config": {"workload": args.workload, "qubits": n, "depth": circ.depth, "sliced": len(plan.slices),
                    "inner_slices": info["n_inner"], "bitstrings_per_step": B, "engine": info["engine"],
                    "warps_per_item": info["warps_per_item"], "mem_budget_mb": args.mem_budget_mb,
+                   "tensor_core_steps": info["n_gemm_steps"],
                    "l2": "flushed (256 MiB write) before each step",
                    "parallelism": f"bitstrings per rank x {world}"},
         "complex_tflops": flops / (ms_step / 1e3) / 1e12,

@@ -111,6 +111,11 @@ typedef struct {
                                   amplitudes). Not with gradient plans. */
     int32_t open_qubits[16];   /* the open qubits; amplitude j of a bitstring sets open_qubits[i]
                                   to bit i of j (the bitstring's own bits there are ignored) */
+    int32_t tensor_cores;      /* stepwise engine: 1 runs the dense contractions (at least 16
+                                  summed entries, 64 A-only and 16 B-only output entries, 12 or
+                                  more flops per algorithmic byte) as complex GEMMs on the tcgen05
+                                  tensor cores, operands split into bf16 hi + lo parts (three
+                                  products, FP32 accumulation); 0 keeps them on FP32 SIMT kernels */
 } qvx_plan_opts;
 
 typedef struct {
@@ -131,6 +136,7 @@ typedef struct {
     int32_t n_tiled_steps;           /* contractions with a register-tiled form (global-arena engines) */
     int32_t n_phases;                /* levels of mutually independent contractions */
     int32_t n_open_qubits;           /* amplitudes per bitstring = 2^n_open_qubits */
+    int32_t n_gemm_steps;            /* contractions run on the tensor cores (opts.tensor_cores) */
     int32_t grad_smem_bytes;         /* shared memory per work item of the gradient kernel's on-chip
                                         form (0: absent; larger than the device allows: global memory) */
 } qvx_plan_info;

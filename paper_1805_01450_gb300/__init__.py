@@ -45,7 +45,7 @@ class PlanOpts(ctypes.Structure):
                 ("max_rank", ctypes.c_int32), ("warps_per_item", ctypes.c_int32),
                 ("host_merge_rank", ctypes.c_int32), ("gradient", ctypes.c_int32),
                 ("slice_rule", ctypes.c_int32), ("n_open_qubits", ctypes.c_int32),
-                ("open_qubits", ctypes.c_int32 * 16)]
+                ("open_qubits", ctypes.c_int32 * 16), ("tensor_cores", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -59,7 +59,8 @@ class PlanInfo(ctypes.Structure):
                 ("n_grad_steps", ctypes.c_int32), ("grad_arena_bytes", ctypes.c_int64),
                 ("grad_flops_per_amplitude", ctypes.c_double), ("grad_bytes_per_amplitude", ctypes.c_double),
                 ("n_tiled_steps", ctypes.c_int32), ("n_phases", ctypes.c_int32),
-                ("n_open_qubits", ctypes.c_int32), ("grad_smem_bytes", ctypes.c_int32)]
+                ("n_open_qubits", ctypes.c_int32), ("n_gemm_steps", ctypes.c_int32),
+                ("grad_smem_bytes", ctypes.c_int32)]
 
 
 _lib = None
@@ -156,7 +157,8 @@ class Plan:
 
     def __init__(self, circ, order=None, slices=None, n_slices=-1, engine="auto", inner_slices=-1,
                  order_restarts=8, order_seed=1, mem_budget_bytes=1 << 30, max_rank=30,
-                 warps_per_item=1, host_merge_rank=8, gradient=False, slice_rule="greedy", open_qubits=()):
+                 warps_per_item=1, host_merge_rank=8, gradient=False, slice_rule="greedy", open_qubits=(),
+                 tensor_cores=False):
         L = lib()
         opts = PlanOpts()
         L.qvx_plan_opts_default(ctypes.byref(opts))
@@ -171,6 +173,7 @@ class Plan:
         opts.host_merge_rank = host_merge_rank
         opts.gradient = 1 if gradient else 0
         opts.slice_rule = {"greedy": 0, "reorder": 1, "cz-pair": 2}[slice_rule]
+        opts.tensor_cores = 1 if tensor_cores else 0
         opts.n_open_qubits = len(open_qubits)
         for i, qb in enumerate(open_qubits):
             opts.open_qubits[i] = qb

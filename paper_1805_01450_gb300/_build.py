@@ -11,8 +11,8 @@ OUT = os.path.join(HERE, "libqvx.so")
 BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HOST_SOURCES = ["planner.cpp", "capi.cpp"]
-CUDA_SOURCES = ["kernels.cu", "noalloc.cu"]
-HEADERS = ["plan.h", "device_program.h", "kernels.h", "plan_handle.h"]
+CUDA_SOURCES = ["kernels.cu", "noalloc.cu", "gemm_tc.cu"]
+HEADERS = ["plan.h", "device_program.h", "kernels.h", "plan_handle.h", "device_util.cuh"]
 
 
 def _cuda_home():

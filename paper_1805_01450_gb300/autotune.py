@@ -68,8 +68,11 @@ def autotune(circ, bitstrings, n_slices=-1, slices=None, order=None, inner=None,
             if time.perf_counter() - t_start > budget_s:
                 break
             try:
+                tc = eng.endswith("-tc")   # the stepwise engine with tensor-core contractions
                 p = Plan(circ, order=base.order, slices=base.slices, inner_slices=n_in, warps_per_item=w,
-                         host_merge_rank=m, engine=eng, **plan_kw)
+                         host_merge_rank=m, engine=eng[:-3] if tc else eng, tensor_cores=tc, **plan_kw)
+                if tc and p.info["n_gemm_steps"] == 0:
+                    continue
             except Exception:      # a variant the engine cannot run (shared memory)
                 continue
             us = _time_plan(p, bits, flush, stream, reps, warmup)

@@ -26,13 +26,15 @@ qvx_status cuda_fail(cudaError_t e, const char *where) {
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Workspace layout: [device image][status word, CTA counter][host staging: bitstrings,
-// amplitudes][item partials][stepwise arenas] and, for gradient plans, [derivative
-// partials][gradient arenas]
+// amplitudes][item partials][stepwise arenas], for gradient plans [derivative
+// partials][gradient arenas], and for tensor-core steps [bf16 operand tiles]
 struct WsLayout {
     size_t image, status, stage_bits, stage_amps, partials, arenas, total;
     int64_t items_in_flight;
     size_t grad_partials = 0, grad_arenas = 0;
     int64_t grad_slots = 0;
+    size_t pack = 0, pack_per_item = 0;
+    int64_t pack_items = 0;        // work items whose operand tiles fit the pack region
 };
 
 WsLayout layout_of(const qvx::Plan &p, int64_t batch) {
@@ -61,6 +63,14 @@ WsLayout layout_of(const qvx::Plan &p, int64_t batch) {
         w.grad_arenas = align256(w.grad_partials + (size_t)total_items * h->n_param_leaves * sizeof(qvx::ExactPair));
         w.grad_slots = std::min(total_items, std::max<int64_t>(1, p.opts.mem_budget_bytes / arena_bytes));
         w.total = align256(w.grad_arenas + (size_t)w.grad_slots * (size_t)arena_bytes);
+    }
+    for (const qvx::GemmStep &g : p.gemm)
+        if (g.nk) w.pack_per_item = std::max(w.pack_per_item, qvx::gemm_pack_bytes_per_item(g));
+    if (w.pack_per_item) {   // operand tiles of up to half the arena budget's items at once
+        const int64_t fit = std::max<int64_t>(1, (p.opts.mem_budget_bytes / 2) / (int64_t)w.pack_per_item);
+        w.pack_items = std::max<int64_t>(1, std::min<int64_t>(w.items_in_flight, fit));
+        w.pack = w.total;
+        w.total = align256(w.pack + w.pack_per_item * (size_t)w.pack_items);
     }
     return w;
 }
@@ -190,6 +200,16 @@ qvx_status run_items(qvx_plan *plan, const uint64_t *bits, int64_t batch, int64_
                 const PStepShape sh = shape_of(p, s);
                 const uint64_t threads = (uint64_t)n << rc;
                 const bool splitk = sh.nk >= 5 && rc <= 12;
+                if (!p.gemm.empty() && p.gemm[s].nk > 0) {   // tensor cores, in item batches
+                    const qvx::GemmStep &g = p.gemm[s];
+                    for (int64_t i0 = 0; i0 < n; i0 += w.pack_items) {
+                        const int64_t m = std::min<int64_t>(w.pack_items, n - i0);
+                        if ((e = qvx::launch_gemm_step(a, g, ib + i0, m, arenas + (size_t)i0 * a.arena_elems,
+                                                       base + w.pack, st)) != cudaSuccess)
+                            return cuda_fail(e, "tensor-core step launch");
+                    }
+                    continue;
+                }
                 if (threads < (1u << 18) && !splitk && grp.n < (uint32_t)qvx::kMaxGroupSteps) {
                     grp.step[grp.n] = (uint32_t)s;
                     grp.first_block[grp.n + 1] = grp.first_block[grp.n] + (uint32_t)((threads + 255) / 256);
@@ -282,6 +302,7 @@ qvx_status qvx_plan_create(const qvx_circuit *circuit, const int32_t *order, int
     if (o.order_restarts < 1 || o.max_rank < 1 || o.mem_budget_bytes < 64)
         return fail(QVX_EINVAL, "opts: restarts >= 1, max_rank >= 1, budget >= 64 bytes");
     if (o.slice_rule < 0 || o.slice_rule > 2) return fail(QVX_EINVAL, "opts: slice_rule must be 0, 1 or 2");
+    if (o.tensor_cores < 0 || o.tensor_cores > 1) return fail(QVX_EINVAL, "opts: tensor_cores must be 0 or 1");
     if (o.host_merge_rank < 0 || o.host_merge_rank > 16)
         return fail(QVX_EINVAL, "opts: host_merge_rank must be in [0, 16]");
     if (o.warps_per_item < 1 || o.warps_per_item > 16 || (o.warps_per_item & (o.warps_per_item - 1)))
@@ -334,6 +355,8 @@ qvx_status qvx_plan_get_info(const qvx_plan *plan, qvx_plan_info *info) {
     for (const qvx::RegTileStep &r : p.regtile) info->n_tiled_steps += r.rm + r.rn > 0 ? 1 : 0;
     info->n_phases = (int32_t)p.phases.size();
     info->n_open_qubits = (int32_t)p.open_qubits.size();
+    info->n_gemm_steps = 0;
+    for (const qvx::GemmStep &g : p.gemm) info->n_gemm_steps += g.nk > 0 ? 1 : 0;
     info->grad_smem_bytes = p.opts.gradient
         ? (int32_t)qvx::grad_smem_bytes(reinterpret_cast<const qvx::DevProgram *>(p.image.data())) : 0;
     info->grad_bytes_per_amplitude = p.grad_bytes_per_item * (double)info->n_items_per_bitstring;

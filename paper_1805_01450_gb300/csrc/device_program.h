@@ -115,6 +115,22 @@ struct RegTileStep {
     uint32_t a_m[4], b_n[4], c_m[4], c_n[4];
 };
 
+// Tensor-core form of a dense two-operand step C[b, m, n] = sum_k A[b, m, k] B[b, k, n]
+// (stepwise engine): b are the output modes held by A and B, m those held by A alone, n those
+// held by B alone, k the summed modes (all held by both). A group's compact index (its modes
+// in C's order; k in A's order) moves into an operand's entry index by bit runs. nk = 0:
+// the step has no tensor-core form.
+constexpr int kGroupRuns = 8;
+struct GemmStep {
+    uint64_t a_off, b_off, c_off;  // arena offsets or leaf indices (flags as in DevStep)
+    uint32_t flags;
+    uint8_t nb, nm, nn, nk;        // group sizes in bits
+    uint8_t n_ab, n_am, n_ak, n_bb, n_bn, n_bk, n_cb, n_cm, n_cn, pad[3];
+    DevRun ab[kGroupRuns], am[kGroupRuns], ak[kGroupRuns];   // A: b, m, k
+    DevRun bb[kGroupRuns], bn[kGroupRuns], bk[kGroupRuns];   // B: b, n, k
+    DevRun cb[kGroupRuns], cm[kGroupRuns], cn[kGroupRuns];   // C: b, m, n
+};
+
 struct DevProgram {
     uint32_t magic;
     uint32_t n_steps, n_leaves, pad0;
@@ -147,6 +163,7 @@ struct DevProgram {
     uint64_t gentry_off;           // byte offset of the GradEntry records (0 if absent)
     uint64_t gktab_off;            // byte offset of the k table (pairs of 16-bit offsets)
     uint64_t gphase_entry_off;     // byte offset of n_grad_phases + 1 record indices (phase starts)
+    uint64_t gemm_off;             // byte offset of n_steps GemmStep (0 if absent)
     uint64_t image_bytes;
 };
 
@@ -157,7 +174,8 @@ constexpr uint32_t kProgramMagic = 0x51565831u;  // "QVX1"
 namespace qvx {
 static_assert(sizeof(DevStep) == 136, "DevStep layout");
 static_assert(sizeof(DevLeaf) == 40, "DevLeaf layout");
-static_assert(sizeof(DevProgram) == 312, "DevProgram layout");
+static_assert(sizeof(DevProgram) == 320, "DevProgram layout");
+static_assert(sizeof(GemmStep) == 336, "GemmStep layout");
 static_assert(sizeof(GradEntry) == 16, "GradEntry layout");
 static_assert(sizeof(RegTileStep) == 224, "RegTileStep layout");
 static_assert(sizeof(GenOperand) == 112, "GenOperand layout");

@@ -99,8 +99,18 @@ cudaError_t launch_grad_smem(const GradArgs &g, int grid, size_t smem_bytes, cud
 cudaError_t launch_grad_sum(const unsigned char *image, const ExactPair *gpart, int64_t batch, int64_t o_count,
                             uint32_t n_param_leaves, uint32_t n_params, double *grad, cudaStream_t s);
 
-// Kernels the calling host thread has launched through these launchers (successful launches).
+// Kernels the calling host thread has launched through these launchers (successful launches);
+// launch_counted(e) counts one launch if e is cudaSuccess and returns e.
 uint64_t launches_issued();
+cudaError_t launch_counted(cudaError_t e);
+// Tensor-core form of a dense step (gemm_tc.cu): summed-index chunk and column tile sizes,
+// pack-buffer bytes per work item, and the three launches (pack A, pack B, GEMM) for items
+// [item0, item0 + n_items) whose arenas start at `arenas`.
+uint32_t gemm_kc(const GemmStep &g);
+uint32_t gemm_nt(const GemmStep &g);
+size_t gemm_pack_bytes_per_item(const GemmStep &g);
+cudaError_t launch_gemm_step(const LaunchArgs &a, const GemmStep &g, int64_t item0, int64_t n_items, float2 *arenas,
+                             unsigned char *pack, cudaStream_t s);
 // Self-test of the bounded waits (grid barrier and mbarrier that can never complete).
 cudaError_t launch_wait_selftest(unsigned *words, unsigned *status, uint32_t polls, unsigned *out, cudaStream_t s);
 

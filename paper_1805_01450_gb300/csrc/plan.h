@@ -72,6 +72,7 @@ struct Plan {
     int warps_per_item = 1;
     std::vector<unsigned char> image;          // device image (DevProgram first)
     std::vector<RegTileStep> regtile;          // per step, global-arena engines: register-tiled form (rm + rn > 0)
+    std::vector<GemmStep> gemm;                // per step, stepwise engine with tensor cores: GEMM form (nk > 0)
     // gradient program
     int n_params = 0;
     std::vector<GenStep> grad_steps;

@@ -1189,6 +1189,52 @@ bool serialize(Plan &p, std::string *err) {
                     }
         }
     }
+    // tensor-core form of the dense contractions (stepwise engine, opts.tensor_cores): every
+    // summed mode in both operands, at least 16 summed entries (K), 64 A-only (M) and 16
+    // B-only (N) output entries, and an arithmetic intensity at or above the FP32 ridge
+    std::vector<GemmStep> gms;
+    if (p.engine == QVX_ENGINE_STEPWISE && p.opts.tensor_cores) {
+        gms.assign(ds.size(), GemmStep{});
+        for (size_t s = 0; s < p.steps.size(); s++) {
+            const PStep &st = p.steps[s];
+            GemmStep &g = gms[s];
+            std::memset(&g, 0, sizeof(g));
+            if (st.b < 0 || !st.k_a.empty() || !st.k_b.empty() || st.k_ab.size() < 4) continue;
+            const std::vector<int> &LA = p.tensors[st.a].modes, &LB = p.tensors[st.b].modes, &LC = p.tensors[st.c].modes;
+            std::vector<int> gb, gm, gn;
+            for (int v : LC) {
+                const bool ia = find_pos(LA, v) >= 0, ib = find_pos(LB, v) >= 0;
+                if (ia && ib) gb.push_back(v);
+                else if (ia) gm.push_back(v);
+                else gn.push_back(v);
+            }
+            if (gm.size() < 6 || gn.size() < 4) continue;
+            const double flops = 8.0 * std::ldexp(1.0, (int)(LC.size() + st.k_ab.size()));
+            const double bytes = 8.0 * (std::ldexp(1.0, (int)LA.size()) + std::ldexp(1.0, (int)LB.size()) +
+                                        std::ldexp(1.0, (int)LC.size()));
+            if (flops < 12.0 * bytes) continue;
+            bool ok = true;
+            auto gmap = [&](const std::vector<int> &grp, const std::vector<int> &L, DevRun *runs, uint8_t *n) {
+                DevRun r[kMaxRuns];
+                uint8_t nr = 0;
+                if (!map_runs(grp, L, r, &nr) || nr > kGroupRuns) { ok = false; return; }
+                for (int i = 0; i < nr; i++) runs[i] = r[i];
+                *n = nr;
+            };
+            gmap(gb, LA, g.ab, &g.n_ab); gmap(gm, LA, g.am, &g.n_am); gmap(st.k_ab, LA, g.ak, &g.n_ak);
+            gmap(gb, LB, g.bb, &g.n_bb); gmap(gn, LB, g.bn, &g.n_bn); gmap(st.k_ab, LB, g.bk, &g.n_bk);
+            gmap(gb, LC, g.cb, &g.n_cb); gmap(gm, LC, g.cm, &g.n_cm); gmap(gn, LC, g.cn, &g.n_cn);
+            if (!ok) { std::memset(&g, 0, sizeof(g)); continue; }
+            g.a_off = ds[s].a_off;
+            g.b_off = ds[s].b_off;
+            g.c_off = ds[s].c_off;
+            g.flags = ds[s].flags;
+            g.nb = (uint8_t)gb.size();
+            g.nm = (uint8_t)gm.size();
+            g.nn = (uint8_t)gn.size();
+            g.nk = (uint8_t)st.k_ab.size();
+        }
+    }
     // fused form: per-step tables of pext(c) for both operands (16-bit offsets), and per
     // phase a map from each lane of a work item's group to the step it works on
     std::vector<FusedStep> fs(ds.size());
@@ -1298,6 +1344,10 @@ bool serialize(Plan &p, std::string *err) {
         h.regtile_off = off;
         off = align256(off + rts.size() * sizeof(RegTileStep));
     }
+    if (!gms.empty()) {
+        h.gemm_off = off;
+        off = align256(off + gms.size() * sizeof(GemmStep));
+    }
     // level phases (first step of each phase, then the step count)
     std::vector<uint32_t> level_first;
     for (const auto &ph : p.phases) level_first.push_back((uint32_t)ph.first);
@@ -1366,6 +1416,8 @@ bool serialize(Plan &p, std::string *err) {
     std::memcpy(p.image.data() + h.level_phases_off, level_first.data(), level_first.size() * sizeof(uint32_t));
     if (!rts.empty()) std::memcpy(p.image.data() + h.regtile_off, rts.data(), rts.size() * sizeof(RegTileStep));
     p.regtile = rts;
+    if (!gms.empty()) std::memcpy(p.image.data() + h.gemm_off, gms.data(), gms.size() * sizeof(GemmStep));
+    p.gemm = gms;
     if (p.opts.gradient) {
         unsigned char *img = p.image.data();
         if (!p.grad_steps.empty()) std::memcpy(img + h.grad_steps_off, p.grad_steps.data(), p.grad_steps.size() * sizeof(GenStep));

@@ -29,7 +29,7 @@ PROG = np.dtype([("magic", "<u4"), ("n_steps", "<u4"), ("n_leaves", "<u4"), ("pa
                  ("n_level_phases", "<u4"), ("n_grad_phases", "<u4"), ("grad_phases_off", "<u8"),
                  ("grad_elem_off_off", "<u8"), ("n_open", "<u4"), ("open_present", "<u4"),
                  ("regtile_off", "<u8"), ("gentry_off", "<u8"), ("gktab_off", "<u8"),
-                 ("gphase_entry_off", "<u8"), ("image_bytes", "<u8")])
+                 ("gphase_entry_off", "<u8"), ("gemm_off", "<u8"), ("image_bytes", "<u8")])
 FSTEP = np.dtype([("a_off", "<u4"), ("b_off", "<u4"), ("c_off", "<u4"), ("tab_off", "<u4"), ("flags", "<u4"),
                   ("rc", "u1"), ("nk_ab", "u1"), ("nk_a", "u1"), ("nk_b", "u1"), ("a_cb", "u1"), ("b_cb", "u1"),
                   ("nk", "u1"), ("pad1", "u1"), ("pad2", "<u4"), ("koff_a", "<u2", (4,)), ("koff_b", "<u2", (4,))])
@@ -42,13 +42,25 @@ RTSTEP = np.dtype([("a_off", "<u8"), ("b_off", "<u8"), ("c_off", "<u8"), ("flags
                    ("a_cb", "u1"), ("b_cb", "u1"), ("n_free", "u1"), ("na_runs", "u1"), ("nb_runs", "u1"),
                    ("free_runs", RUN, (6,)), ("runs_a", RUN, (12,)), ("runs_b", RUN, (12,)),
                    ("a_m", "<u4", (4,)), ("b_n", "<u4", (4,)), ("c_m", "<u4", (4,)), ("c_n", "<u4", (4,))])
-assert STEP.itemsize == 136 and LEAF.itemsize == 40 and PROG.itemsize == 312 and FSTEP.itemsize == 48
+assert STEP.itemsize == 136 and LEAF.itemsize == 40 and PROG.itemsize == 320 and FSTEP.itemsize == 48
+GEMM = np.dtype([("a_off", "<u8"), ("b_off", "<u8"), ("c_off", "<u8"), ("flags", "<u4"), ("nb", "u1"),
+                 ("nm", "u1"), ("nn", "u1"), ("nk", "u1"), ("n_ab", "u1"), ("n_am", "u1"), ("n_ak", "u1"),
+                 ("n_bb", "u1"), ("n_bn", "u1"), ("n_bk", "u1"), ("n_cb", "u1"), ("n_cm", "u1"), ("n_cn", "u1"),
+                 ("pad", "u1", (3,))] + [(f, RUN, (8,)) for f in ("ab", "am", "ak", "bb", "bn", "bk", "cb", "cm", "cn")] +
+                [("tail", "<u4")])
 GENTRY = np.dtype([("c", "<u2"), ("meta", "<u2"), ("xr", "<u2"), ("xo", "<u2"), ("yr", "<u2"), ("yo", "<u2"),
                    ("k1", "<u4")])
-assert RTSTEP.itemsize == 224 and GENTRY.itemsize == 16
+assert RTSTEP.itemsize == 224 and GENTRY.itemsize == 16 and GEMM.itemsize == 336
 assert GOP.itemsize == 112 and GSTEP.itemsize == 240 and PLEAF.itemsize == 24
 OP_ARENA, OP_LEAF, OP_DERIV, OP_ONE = 0, 1, 2, 3
 UNARY, A_LEAF, B_LEAF = 1, 2, 4
+
+
+def _bf16(v):
+    """float32 array rounded to bf16 (nearest even), returned as float32."""
+    u = np.asarray(v, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32)
 
 
 def _pext(c, runs, n):
@@ -75,6 +87,10 @@ class Program:
             lo, nl = int(h["fused_lane_map_off"]), int(h["n_fused_phases"]) * int(h["fused_lanes"])
             self.lane_map = np.frombuffer(buf[lo:lo + 4 * nl].tobytes(), dtype="<u4").reshape(
                 int(h["n_fused_phases"]), int(h["fused_lanes"]))
+        self.gemms = None
+        if int(h["gemm_off"]):
+            go = int(h["gemm_off"])
+            self.gemms = np.frombuffer(buf[go:go + GEMM.itemsize * int(h["n_steps"])].tobytes(), dtype=GEMM)
         self.rtsteps = None
         if int(h["regtile_off"]):
             ro = int(h["regtile_off"])
@@ -154,7 +170,58 @@ class Program:
         for c, acc in out.values():
             arena[int(r["c_off"]) + c] = acc
 
-    def item_terms(self, x: int, o: int, fused: bool = False, regtile: bool = False):
+    def _gemm_step(self, si, A, B, arena):
+        """Step si through its tensor-core form, as the pack and GEMM kernels define it: the
+        real block GEMM of bf16 hi/lo parts (hi*hi + hi*lo + lo*hi) accumulated in float64
+        here. Also checks that the tile writes of the pack kernels fill their buffers exactly
+        once and that the GEMM's stores cover C exactly once."""
+        g = self.gemms[si]
+        st = self.steps[si]
+        nb, nm, nn, nk = (int(g[f]) for f in ("nb", "nm", "nn", "nk"))
+        assert nk >= 4 and nm >= 6 and nn >= 4 and int(g["c_off"]) == int(st["c_off"])
+        bb, mm, nn_, kk = (np.arange(1 << v, dtype=np.int64) for v in (nb, nm, nn, nk))
+
+        def mv(v, f):
+            return _pext(v, g[f], int(g["n_" + f]))
+        ia = mv(bb, "ab")[:, None, None] + mv(mm, "am")[None, :, None] + mv(kk, "ak")[None, None, :]
+        ib = mv(bb, "bb")[:, None, None] + mv(kk, "bk")[None, :, None] + mv(nn_, "bn")[None, None, :]
+        ic = mv(bb, "cb")[:, None, None] + mv(mm, "cm")[None, :, None] + mv(nn_, "cn")[None, None, :]
+        assert np.array_equal(np.sort(ic.ravel()), np.arange(1 << int(st["rc"])))
+        Ac = np.asarray(A(ia.ravel())).reshape(ia.shape).astype(np.complex64)
+        Bc = np.asarray(B(ib.ravel())).reshape(ib.shape).astype(np.complex64)
+
+        def split(v):   # float32 -> bf16 hi and lo (round to nearest even), as float64
+            v = np.asarray(v, dtype=np.float32)
+            hi = _bf16(v)
+            lo = _bf16((v - hi.astype(np.float32)).astype(np.float32))
+            return hi.astype(np.float64), lo.astype(np.float64)
+        arh, arl = split(Ac.real)
+        aih, ail = split(Ac.imag)
+        brh, brl = split(Bc.real)
+        bih, bil = split(Bc.imag)
+
+        def mm3(xh, xl, yh, yl):
+            return (np.einsum("bmk,bkn->bmn", xh, yh) + np.einsum("bmk,bkn->bmn", xh, yl) +
+                    np.einsum("bmk,bkn->bmn", xl, yh))
+        re = mm3(arh, arl, brh, brl) - mm3(aih, ail, bih, bil)
+        im = mm3(aih, ail, brh, brl) + mm3(arh, arl, bih, bil)
+        arena[int(g["c_off"]) + ic] = re + 1j * im
+        # pack-buffer coverage (tile sizes of the kernels: 128 real rows, nt columns, kc chunk)
+        K, M2, N = 1 << nk, 2 << nm, 1 << nn
+        kp = 6 * K
+        kc = 64 if kp % 64 == 0 else 32
+        ntc = 128 if nn >= 7 else N
+        r = np.arange(M2)[:, None]
+        j0 = (8 * np.arange(kp // 8))[None, :]
+        offa = ((r // 128) * (kp // kc) + j0 // kc) * (128 * kc * 2) + \
+            (r % 128 // 8) * (kc * 16) + (j0 % kc // 8) * 128 + (r % 8) * 16
+        assert np.array_equal(np.sort(offa.ravel()), 16 * np.arange(M2 * kp // 8))
+        n = np.arange(N)[:, None]
+        offb = ((n // ntc) * (kp // kc) + j0 // kc) * (ntc * kc * 2) + \
+            (n % ntc // 8) * (kc * 16) + (j0 % kc // 8) * 128 + (n % 8) * 16
+        assert np.array_equal(np.sort(offb.ravel()), 16 * np.arange(N * kp // 8))
+
+    def item_terms(self, x: int, o: int, fused: bool = False, regtile: bool = False, gemm: bool = False):
         """Slice terms of work item (x, o): entry i is slice (o << n_inner) | i. With
         fused=True the steps take their operand offsets from the fused form's tables; with
         regtile=True the steps that have a register-tiled form run through it."""
@@ -177,6 +244,9 @@ class Program:
             unary = flags & UNARY
             B = None if unary else operand(flags & B_LEAF, st["b_off"])
             nab_, na_, nb_ = int(st["nk_ab"]), int(st["nk_a"]), int(st["nk_b"])
+            if gemm and self.gemms is not None and int(self.gemms[si]["nk"]) > 0:
+                self._gemm_step(si, A, B, arena)
+                continue
             if regtile and int(self.rtsteps[si]["rm"]) + int(self.rtsteps[si]["rn"]) > 0:
                 assert not unary
                 self._regtile_step(si, A, B, arena)

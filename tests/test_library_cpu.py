@@ -146,6 +146,23 @@ def test_register_tiled_forms_7x7x30():
     assert np.max(np.abs(got - ref)) < 1e-6 * 2 ** -24.5
 
 
+def test_tensor_core_form_on_host():
+    # 6x6x40, 8 sliced variables (2 open): one contraction qualifies for the tensor cores;
+    # its bf16 hi/lo block GEMM stays within 2^-15 of the exact product and the slice terms
+    # within the amplitude tolerance of the oracle's
+    c = cg.grid_circuit(6, 6, 40, 7066)
+    p = q.Plan(c, n_slices=8, inner_slices=2, engine="stepwise", tensor_cores=True)
+    assert p.info["n_gemm_steps"] >= 1
+    prog = Program(p.image())
+    x = cg.random_bitstrings(36, 1, 7067)[0]
+    got = prog.item_terms(x, 3, gemm=True)
+    plain = prog.item_terms(x, 3)
+    assert np.max(np.abs(got - plain)) <= 2.0 ** -15 * np.max(np.abs(plain))
+    ref = VE.slice_terms(c, x, p.order, p.slices, slice_ids=[(3 << 2) | i for i in range(4)])
+    assert np.max(np.abs(got - ref)) < 1e-5 * 2 ** -18
+    assert q.Plan(c, n_slices=8, inner_slices=2, engine="stepwise").info["n_gemm_steps"] == 0
+
+
 @pytest.mark.parametrize("merge", [0, 8])
 def test_program_slice_terms_6x6_sample(merge):
     c = cg.grid_circuit(6, 6, 25, 2001)

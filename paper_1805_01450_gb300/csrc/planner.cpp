@@ -1200,15 +1200,26 @@ bool serialize(Plan &p, std::string *err) {
             GemmStep &g = gms[s];
             std::memset(&g, 0, sizeof(g));
             if (st.b < 0 || !st.k_a.empty() || !st.k_b.empty() || st.k_ab.size() < 4) continue;
-            const std::vector<int> &LA = p.tensors[st.a].modes, &LB = p.tensors[st.b].modes, &LC = p.tensors[st.c].modes;
+            // the GEMM's row operand needs 64 output entries of its own and the column operand
+            // 16; complex products commute, so the step's B may take the row role
+            bool swap = false;
             std::vector<int> gb, gm, gn;
-            for (int v : LC) {
-                const bool ia = find_pos(LA, v) >= 0, ib = find_pos(LB, v) >= 0;
-                if (ia && ib) gb.push_back(v);
-                else if (ia) gm.push_back(v);
-                else gn.push_back(v);
+            for (int pass = 0; pass < 2; pass++) {
+                swap = pass == 1;
+                const std::vector<int> &LA = p.tensors[swap ? st.b : st.a].modes;
+                const std::vector<int> &LB = p.tensors[swap ? st.a : st.b].modes, &LC = p.tensors[st.c].modes;
+                gb.clear(); gm.clear(); gn.clear();
+                for (int v : LC) {
+                    const bool ia = find_pos(LA, v) >= 0, ib = find_pos(LB, v) >= 0;
+                    if (ia && ib) gb.push_back(v);
+                    else if (ia) gm.push_back(v);
+                    else gn.push_back(v);
+                }
+                if (gm.size() >= 6 && gn.size() >= 4) break;
             }
             if (gm.size() < 6 || gn.size() < 4) continue;
+            const std::vector<int> &LA = p.tensors[swap ? st.b : st.a].modes;
+            const std::vector<int> &LB = p.tensors[swap ? st.a : st.b].modes, &LC = p.tensors[st.c].modes;
             const double flops = 8.0 * std::ldexp(1.0, (int)(LC.size() + st.k_ab.size()));
             const double bytes = 8.0 * (std::ldexp(1.0, (int)LA.size()) + std::ldexp(1.0, (int)LB.size()) +
                                         std::ldexp(1.0, (int)LC.size()));
@@ -1225,10 +1236,12 @@ bool serialize(Plan &p, std::string *err) {
             gmap(gb, LB, g.bb, &g.n_bb); gmap(gn, LB, g.bn, &g.n_bn); gmap(st.k_ab, LB, g.bk, &g.n_bk);
             gmap(gb, LC, g.cb, &g.n_cb); gmap(gm, LC, g.cm, &g.n_cm); gmap(gn, LC, g.cn, &g.n_cn);
             if (!ok) { std::memset(&g, 0, sizeof(g)); continue; }
-            g.a_off = ds[s].a_off;
-            g.b_off = ds[s].b_off;
+            g.a_off = swap ? ds[s].b_off : ds[s].a_off;
+            g.b_off = swap ? ds[s].a_off : ds[s].b_off;
             g.c_off = ds[s].c_off;
-            g.flags = ds[s].flags;
+            g.flags = ds[s].flags & ~(kStepALeaf | kStepBLeaf);
+            if (ds[s].flags & (swap ? kStepBLeaf : kStepALeaf)) g.flags |= kStepALeaf;
+            if (ds[s].flags & (swap ? kStepALeaf : kStepBLeaf)) g.flags |= kStepBLeaf;
             g.nb = (uint8_t)gb.size();
             g.nm = (uint8_t)gm.size();
             g.nn = (uint8_t)gn.size();

@@ -245,7 +245,9 @@ class Program:
             B = None if unary else operand(flags & B_LEAF, st["b_off"])
             nab_, na_, nb_ = int(st["nk_ab"]), int(st["nk_a"]), int(st["nk_b"])
             if gemm and self.gemms is not None and int(self.gemms[si]["nk"]) > 0:
-                self._gemm_step(si, A, B, arena)
+                g = self.gemms[si]   # its operands may be the step's in swapped roles
+                gf = int(g["flags"])
+                self._gemm_step(si, operand(gf & A_LEAF, g["a_off"]), operand(gf & B_LEAF, g["b_off"]), arena)
                 continue
             if regtile and int(self.rtsteps[si]["rm"]) + int(self.rtsteps[si]["rn"]) > 0:
                 assert not unary

@@ -26,6 +26,7 @@ CASES = [
     # (rows, cols, depth, seed, sliced, inner)
     (6, 6, 40, 7066, 8, 2),
     (7, 8, 32, 7078, 6, 2),
+    (5, 6, 40, 13, 8, 2),      # the step's second operand takes the GEMM's row role
 ]
 
 

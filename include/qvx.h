@@ -111,11 +111,12 @@ typedef struct {
                                   amplitudes). Not with gradient plans. */
     int32_t open_qubits[16];   /* the open qubits; amplitude j of a bitstring sets open_qubits[i]
                                   to bit i of j (the bitstring's own bits there are ignored) */
-    int32_t tensor_cores;      /* stepwise engine: 1 runs the dense contractions (at least 16
-                                  summed entries, 64 A-only and 16 B-only output entries, 12 or
-                                  more flops per algorithmic byte) as complex GEMMs on the tcgen05
-                                  tensor cores, operands split into bf16 hi + lo parts (three
-                                  products, FP32 accumulation); 0 keeps them on FP32 SIMT kernels */
+    int32_t tensor_cores;      /* stepwise engine: 1 runs the dense contractions (16 to 1024
+                                  summed entries, 64 output entries of one operand's own and 16 of
+                                  the other's, 12 or more flops per algorithmic byte) as complex
+                                  GEMMs on the tcgen05 tensor cores, operands split into bf16 hi +
+                                  lo parts (three products, FP32 accumulation); 0 keeps them on
+                                  FP32 SIMT kernels */
 } qvx_plan_opts;
 
 typedef struct {

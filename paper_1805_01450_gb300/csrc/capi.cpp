@@ -26,15 +26,13 @@ qvx_status cuda_fail(cudaError_t e, const char *where) {
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Workspace layout: [device image][status word, CTA counter][host staging: bitstrings,
-// amplitudes][item partials][stepwise arenas], for gradient plans [derivative
-// partials][gradient arenas], and for tensor-core steps [bf16 operand tiles]
+// amplitudes][item partials][stepwise arenas], and for gradient plans [derivative
+// partials][gradient arenas]
 struct WsLayout {
     size_t image, status, stage_bits, stage_amps, partials, arenas, total;
     int64_t items_in_flight;
     size_t grad_partials = 0, grad_arenas = 0;
     int64_t grad_slots = 0;
-    size_t pack = 0, pack_per_item = 0;
-    int64_t pack_items = 0;        // work items whose operand tiles fit the pack region
 };
 
 WsLayout layout_of(const qvx::Plan &p, int64_t batch) {
@@ -63,14 +61,6 @@ WsLayout layout_of(const qvx::Plan &p, int64_t batch) {
         w.grad_arenas = align256(w.grad_partials + (size_t)total_items * h->n_param_leaves * sizeof(qvx::ExactPair));
         w.grad_slots = std::min(total_items, std::max<int64_t>(1, p.opts.mem_budget_bytes / arena_bytes));
         w.total = align256(w.grad_arenas + (size_t)w.grad_slots * (size_t)arena_bytes);
-    }
-    for (const qvx::GemmStep &g : p.gemm)
-        if (g.nk) w.pack_per_item = std::max(w.pack_per_item, qvx::gemm_pack_bytes_per_item(g));
-    if (w.pack_per_item) {   // operand tiles of up to half the arena budget's items at once
-        const int64_t fit = std::max<int64_t>(1, (p.opts.mem_budget_bytes / 2) / (int64_t)w.pack_per_item);
-        w.pack_items = std::max<int64_t>(1, std::min<int64_t>(w.items_in_flight, fit));
-        w.pack = w.total;
-        w.total = align256(w.pack + w.pack_per_item * (size_t)w.pack_items);
     }
     return w;
 }
@@ -200,14 +190,9 @@ qvx_status run_items(qvx_plan *plan, const uint64_t *bits, int64_t batch, int64_
                 const PStepShape sh = shape_of(p, s);
                 const uint64_t threads = (uint64_t)n << rc;
                 const bool splitk = sh.nk >= 5 && rc <= 12;
-                if (!p.gemm.empty() && p.gemm[s].nk > 0) {   // tensor cores, in item batches
-                    const qvx::GemmStep &g = p.gemm[s];
-                    for (int64_t i0 = 0; i0 < n; i0 += w.pack_items) {
-                        const int64_t m = std::min<int64_t>(w.pack_items, n - i0);
-                        if ((e = qvx::launch_gemm_step(a, g, ib + i0, m, arenas + (size_t)i0 * a.arena_elems,
-                                                       base + w.pack, st)) != cudaSuccess)
-                            return cuda_fail(e, "tensor-core step launch");
-                    }
+                if (!p.gemm.empty() && p.gemm[s].nk > 0) {   // tensor cores
+                    if ((e = qvx::launch_gemm_step(a, p.gemm[s], ib, n, arenas, st)) != cudaSuccess)
+                        return cuda_fail(e, "tensor-core step launch");
                     continue;
                 }
                 if (threads < (1u << 18) && !splitk && grp.n < (uint32_t)qvx::kMaxGroupSteps) {

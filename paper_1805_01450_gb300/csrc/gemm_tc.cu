@@ -1,17 +1,22 @@
 // Dense contractions on the tcgen05 tensor cores (stepwise engine, opts.tensor_cores).
 //
 // A step C[b, m, n] = sum_k A[b, m, k] B[b, k, n] in complex64 becomes one real GEMM per
-// (work item, b): with A = Ar + i Ai and B = Br + i Bi, the rows 2m and 2m + 1 of
+// (work item, b): with A = Ar + i Ai and B = Br + i Bi, the real rows 2m and 2m + 1 of
 //   [Ar  -Ai]        [Br]
 //   [Ai   Ar]  times [Bi]
-// are Re C[m, :] and Im C[m, :]. Every real operand x is split as x = hi + lo with hi, lo in
-// bf16, and the three products hi*hi + hi*lo + lo*hi are taken as one GEMM over a summed
-// index three times as long: A' = [Ah | Ah | Al], B' = [Bh ; Bl ; Bh] (the lo*lo term,
-// below 2^-16 of the product, is dropped). The pack kernels write A' and B' in the tensor
-// cores' K-major core-matrix layout, one tile per (item, b, row or column tile, summed chunk);
-// the GEMM kernel copies those tiles into shared memory with bulk asynchronous copies, issues
-// tcgen05.mma (bf16 inputs, FP32 accumulator in tensor memory) from one thread, and its four
-// warps read the accumulator back with tcgen05.ld and store complex64 C in its own layout.
+// are Re C[m, :] and Im C[m, :] (the left factor's first column block is "part 0", the
+// second "part 1"). Every real operand x is split as x = hi + lo with hi, lo in bf16, and
+// three products hi*hi + hi*lo + lo*hi are accumulated in FP32 (the lo*lo term, below
+// 2^-16 of the product, is dropped).
+//
+// One CTA computes a tile of 128 real rows (64 complex rows m) by NT columns n for one
+// (item, b). Warps 0-3 read the complex64 operands straight from the arena, one chunk of
+// 16 summed entries at a time, split them into bf16 hi and lo and store them in shared
+// memory in the tensor cores' K-major core-matrix layout (no separate packing pass: the
+// operands cross HBM once, as complex64). Warp 4 allocates the tensor-memory accumulator
+// and one of its threads issues the chunk's six tcgen05.mma (2 parts x 3 products, K = 16
+// each); the commit of a chunk's MMAs frees its shared-memory stage. Warps 0-3 then read
+// the accumulator back with tcgen05.ld and store complex64 C in its own layout.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -22,9 +27,22 @@
 namespace qvx {
 namespace {
 
-constexpr int kGemmRows = 128;      // real rows per tile (64 complex rows)
-constexpr int kGemmStages = 3;      // shared-memory ring of summed-index chunks
-constexpr uint32_t kGemmPolls = 1u << 22;
+constexpr uint32_t kRows = 128;        // real rows per tile (64 complex rows)
+constexpr uint32_t kStages = 2;        // shared-memory ring of summed-index chunks
+constexpr uint32_t kKq = 16;           // complex summed entries per chunk (one MMA K-step)
+constexpr uint32_t kPitch = 272;       // bytes between 8-row groups: two 128-byte core matrices
+                                       // along the summed index and 16 bytes that spread the
+                                       // producers' 16-byte stores over all banks
+constexpr uint32_t kPolls = 1u << 22;
+constexpr uint32_t kThreads = 160;     // warps 0-3: operands and epilogue; warp 4: MMA
+
+__host__ __device__ constexpr uint32_t region_bytes(uint32_t rows) { return rows / 8u * kPitch; }
+// One stage: A regions (part 0 hi, part 0 lo, part 1 hi, part 1 lo), then the same for B.
+__host__ __device__ constexpr uint32_t stage_bytes(uint32_t nt) { return 4u * region_bytes(kRows) + 4u * region_bytes(nt); }
+
+__device__ __forceinline__ uint32_t core_offset(uint32_t r, uint32_t g) {
+    return (r >> 3) * kPitch + g * 128u + (r & 7u) * 16u;
+}
 
 __device__ __forceinline__ const float2 *gemm_operand(const LaunchArgs &a, const float2 *arena, uint64_t ref,
                                                       bool leaf, int64_t item) {
@@ -38,87 +56,15 @@ __device__ __forceinline__ const float2 *gemm_operand(const LaunchArgs &a, const
     return ldata + leaf_base(leaves[ref], x, o);
 }
 
-// Byte offset of element (row r, summed index j) inside a tile of `kc` summed entries:
-// 8-row x 16-byte core matrices, those of one 8-row group contiguous along j.
-__device__ __forceinline__ uint32_t core_offset(uint32_t r, uint32_t j, uint32_t kc) {
-    return (r >> 3) * (kc * 16u) + (j >> 3) * 128u + (r & 7u) * 16u;
+// bf16 split of v: hi = rn(v), lo = rn(v - hi), as raw 16-bit patterns.
+__device__ __forceinline__ void split_bf16(float v, uint32_t &hi, uint32_t &lo) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi = __bfloat16_as_ushort(h);
+    lo = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(h)));
 }
 
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo_half, float hi_half) {
-    const __nv_bfloat16 a = __float2bfloat16_rn(lo_half), b = __float2bfloat16_rn(hi_half);
-    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
-}
-
-// Part `lo` (0: hi, 1: lo) of the bf16 split of v.
-__device__ __forceinline__ float split_part(float v, int lo) {
-    const float h = __bfloat162float(__float2bfloat16_rn(v));
-    return lo ? v - h : h;
-}
-
-// A' for items [item0, item0 + n): one thread per 8 consecutive summed entries of one row.
-__global__ void pack_a_kernel(LaunchArgs a, GemmStep g, int64_t item0, int64_t n_items, const float2 *arenas,
-                              unsigned char *Ap, uint32_t kc) {
-    const uint32_t M2 = 2u << g.nm, K = 1u << g.nk, Kp = 6u * K;
-    const uint64_t units = (uint64_t)M2 * (Kp / 8u);
-    const uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= ((uint64_t)n_items << g.nb) * units) return;
-    const uint64_t ib = u / units;                 // (item, b)
-    const uint32_t v = (uint32_t)(u - ib * units);
-    const uint32_t r = v % M2, q = v / M2;
-    const int64_t il = (int64_t)(ib >> g.nb);
-    const uint32_t beta = (uint32_t)(ib & ((1u << g.nb) - 1u));
-    const uint32_t m = r >> 1, s = r & 1u;
-    const uint32_t j0 = 8u * q, seg = j0 / (2u * K), w = j0 % (2u * K), part = w / K, k0 = w % K;
-    const float2 *A = gemm_operand(a, arenas + (uint64_t)il * a.arena_elems, g.a_off, g.flags & kStepALeaf,
-                                   item0 + il);
-    A += pext_runs(beta, g.ab, g.n_ab) + pext_runs(m, g.am, g.n_am);
-    float val[8];
-#pragma unroll
-    for (int t = 0; t < 8; t++) {
-        const float2 x = A[pext_runs(k0 + t, g.ak, g.n_ak)];
-        const float e = s == 0 ? (part == 0 ? x.x : -x.y) : (part == 0 ? x.y : x.x);
-        val[t] = split_part(e, seg == 2);
-    }
-    const uint32_t n_mt = M2 / kGemmRows, n_kc = Kp / kc;
-    const uint64_t tile = ((ib * n_mt + r / kGemmRows) * n_kc + j0 / kc) * (uint64_t)(kGemmRows * kc * 2u);
-    uint4 out;
-    out.x = pack_bf16x2(val[0], val[1]);
-    out.y = pack_bf16x2(val[2], val[3]);
-    out.z = pack_bf16x2(val[4], val[5]);
-    out.w = pack_bf16x2(val[6], val[7]);
-    *reinterpret_cast<uint4 *>(Ap + tile + core_offset(r % kGemmRows, j0 % kc, kc)) = out;
-}
-
-// B' for items [item0, item0 + n): one thread per 8 consecutive summed entries of one column.
-__global__ void pack_b_kernel(LaunchArgs a, GemmStep g, int64_t item0, int64_t n_items, const float2 *arenas,
-                              unsigned char *Bp, uint32_t kc, uint32_t nt_cols) {
-    const uint32_t N = 1u << g.nn, K = 1u << g.nk, Kp = 6u * K;
-    const uint64_t units = (uint64_t)N * (Kp / 8u);
-    const uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= ((uint64_t)n_items << g.nb) * units) return;
-    const uint64_t ib = u / units;
-    const uint32_t v = (uint32_t)(u - ib * units);
-    const uint32_t n = v % N, q = v / N;
-    const int64_t il = (int64_t)(ib >> g.nb);
-    const uint32_t beta = (uint32_t)(ib & ((1u << g.nb) - 1u));
-    const uint32_t j0 = 8u * q, seg = j0 / (2u * K), w = j0 % (2u * K), part = w / K, k0 = w % K;
-    const float2 *B = gemm_operand(a, arenas + (uint64_t)il * a.arena_elems, g.b_off, g.flags & kStepBLeaf,
-                                   item0 + il);
-    B += pext_runs(beta, g.bb, g.n_bb) + pext_runs(n, g.bn, g.n_bn);
-    float val[8];
-#pragma unroll
-    for (int t = 0; t < 8; t++) {
-        const float2 x = B[pext_runs(k0 + t, g.bk, g.n_bk)];
-        val[t] = split_part(part == 0 ? x.x : x.y, seg == 1);
-    }
-    const uint32_t n_nt = N / nt_cols, n_kc = Kp / kc;
-    const uint64_t tile = ((ib * n_nt + n / nt_cols) * n_kc + j0 / kc) * (uint64_t)(nt_cols * kc * 2u);
-    uint4 out;
-    out.x = pack_bf16x2(val[0], val[1]);
-    out.y = pack_bf16x2(val[2], val[3]);
-    out.z = pack_bf16x2(val[4], val[5]);
-    out.w = pack_bf16x2(val[6], val[7]);
-    *reinterpret_cast<uint4 *>(Bp + tile + core_offset(n % nt_cols, j0 % kc, kc)) = out;
+__device__ __forceinline__ uint4 pack8(const uint32_t *h) {
+    return make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
 }
 
 // Shared-memory matrix descriptor of a K-major tile without swizzling: start address, the
@@ -136,160 +82,288 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+// bf16 hi/lo parts of 8 summed entries of one operand row or column.
+__device__ __forceinline__ void split8(const float2 *v, uint32_t *rh, uint32_t *rl, uint32_t *ih, uint32_t *il) {
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        split_bf16(v[j].x, rh[j], rl[j]);
+        split_bf16(v[j].y, ih[j], il[j]);
+    }
+}
+
+// A rows 2m and 2m+1 of one summed half (8 entries) in the four A regions of a stage:
+// part 0 takes (Ar, Ai), part 1 takes (-Ai, Ar).
+__device__ __forceinline__ void store_a(unsigned char *sa, const float2 *v, uint32_t ml, uint32_t h) {
+    constexpr uint32_t R = region_bytes(kRows);
+    uint32_t rh[8], rl[8], ih[8], il[8];
+    split8(v, rh, rl, ih, il);
+    const uint32_t r0 = core_offset(2u * ml, h), r1 = core_offset(2u * ml + 1u, h);
+    *reinterpret_cast<uint4 *>(sa + 0u * R + r0) = pack8(rh);
+    *reinterpret_cast<uint4 *>(sa + 1u * R + r0) = pack8(rl);
+    *reinterpret_cast<uint4 *>(sa + 0u * R + r1) = pack8(ih);
+    *reinterpret_cast<uint4 *>(sa + 1u * R + r1) = pack8(il);
+    *reinterpret_cast<uint4 *>(sa + 2u * R + r1) = pack8(rh);
+    *reinterpret_cast<uint4 *>(sa + 3u * R + r1) = pack8(rl);
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        ih[j] ^= 0x8000u;
+        il[j] ^= 0x8000u;
+    }
+    *reinterpret_cast<uint4 *>(sa + 2u * R + r0) = pack8(ih);
+    *reinterpret_cast<uint4 *>(sa + 3u * R + r0) = pack8(il);
+}
+
+// B column n of one summed half in the four B regions: part 0 takes Br, part 1 Bi.
+template <int NT>
+__device__ __forceinline__ void store_b(unsigned char *sb, const float2 *v, uint32_t nl, uint32_t h) {
+    constexpr uint32_t R = region_bytes(NT);
+    uint32_t rh[8], rl[8], ih[8], il[8];
+    split8(v, rh, rl, ih, il);
+    const uint32_t o = core_offset(nl, h);
+    *reinterpret_cast<uint4 *>(sb + 0u * R + o) = pack8(rh);
+    *reinterpret_cast<uint4 *>(sb + 1u * R + o) = pack8(rl);
+    *reinterpret_cast<uint4 *>(sb + 2u * R + o) = pack8(ih);
+    *reinterpret_cast<uint4 *>(sb + 3u * R + o) = pack8(il);
+}
+
+// One chunk's operand entries held in registers between their loads and their conversion:
+// 8 summed entries of an A row, and of each of the thread's U B columns.
+template <uint32_t U>
+struct Chunk {
+    float2 a[8];
+    float2 b[U][8];
+};
+
+// Loads of one chunk; ka and kb are the CTA's shared-memory tables of the summed index's
+// offsets in A and in B (8 consecutive entries read as two 16-byte words).
+template <uint32_t U>
+__device__ __forceinline__ void load_chunk(Chunk<U> &ch, uint32_t c, uint32_t h, const float2 *Arow,
+                                           const float2 *const *Bcol, const uint32_t *bh, bool b_on,
+                                           const uint32_t *ka, const uint32_t *kb) {
+    {
+        const uint4 o0 = *reinterpret_cast<const uint4 *>(ka + c * kKq + 8u * h);
+        const uint4 o1 = *reinterpret_cast<const uint4 *>(ka + c * kKq + 8u * h + 4u);
+        const uint32_t o[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
+#pragma unroll
+        for (int j = 0; j < 8; j++) ch.a[j] = __ldg(Arow + o[j]);
+    }
+    if (b_on) {
+#pragma unroll
+        for (uint32_t i = 0; i < U; i++) {
+            const uint4 o0 = *reinterpret_cast<const uint4 *>(kb + c * kKq + 8u * bh[i]);
+            const uint4 o1 = *reinterpret_cast<const uint4 *>(kb + c * kKq + 8u * bh[i] + 4u);
+            const uint32_t o[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
+#pragma unroll
+            for (int j = 0; j < 8; j++) ch.b[i][j] = __ldg(Bcol[i] + o[j]);
+        }
+    }
+}
+
 struct GemmArgs {
     LaunchArgs a;
     GemmStep g;
     int64_t item0, n_items;
     float2 *arenas;
-    const unsigned char *Ap, *Bp;
-    uint32_t kc, n_kc, n_mt, n_nt;
+    uint32_t n_chunks, n_mt, n_nt;
 };
 
-// One 128 x NT tile of the real GEMM: thread 0 copies summed-index chunks into a ring of
-// shared-memory stages, thread 32 issues the MMAs (each chunk's commit frees its stage, the
-// last one signals the accumulator), then every warp stores its 32 rows of C.
 template <int NT>
-__global__ void __launch_bounds__(128) gemm_tc_kernel(GemmArgs ga) {
+__global__ void __launch_bounds__(kThreads, 3) gemm_tc_kernel(GemmArgs ga) {
     constexpr uint32_t kCols = NT < 32 ? 32u : (uint32_t)NT;   // tensor-memory columns (power of 2)
+    constexpr uint32_t kRegA = region_bytes(kRows), kStage = stage_bytes(NT);
+    constexpr uint32_t kUnits = (2u * (uint32_t)NT + 127u) / 128u;   // B units per producer thread
+    using Chunk = qvx::Chunk<kUnits>;
     extern __shared__ __align__(1024) unsigned char gsm[];
-    __shared__ __align__(8) uint64_t full_bar[kGemmStages], empty_bar[kGemmStages], acc_bar;
+    __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], acc_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ int fail;
     const GemmStep &g = ga.g;
-    const uint32_t kc = ga.kc, n_kc = ga.n_kc;
-    const uint32_t tile_a = kGemmRows * kc * 2u, tile_b = (uint32_t)NT * kc * 2u;
-    uint64_t t = blockIdx.x;
-    const uint32_t nt = (uint32_t)(t % ga.n_nt);
-    t /= ga.n_nt;
+    uint64_t t = blockIdx.x;   // tiles of one (item, b) and column tile run next to each other
     const uint32_t mt = (uint32_t)(t % ga.n_mt);
     t /= ga.n_mt;
-    const uint64_t ib = t;                               // (item, b)
+    const uint32_t nt = (uint32_t)(t % ga.n_nt);
+    t /= ga.n_nt;
+    const uint64_t ib = t;
     const int64_t il = (int64_t)(ib >> g.nb);
     const uint32_t beta = (uint32_t)(ib & ((1u << g.nb) - 1u));
-    const unsigned char *Ablk = ga.Ap + ((ib * ga.n_mt + mt) * n_kc) * (uint64_t)tile_a;
-    const unsigned char *Bblk = ga.Bp + ((ib * ga.n_nt + nt) * n_kc) * (uint64_t)tile_b;
     const uint32_t warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const uint32_t sbase = smem_u32(gsm);
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kGemmStages; s++) {
-            mbar_init(smem_u32(&full_bar[s]), 1);
+        for (uint32_t s = 0; s < kStages; s++) {
+            mbar_init(smem_u32(&full_bar[s]), 128);
             mbar_init(smem_u32(&empty_bar[s]), 1);
         }
         mbar_init(smem_u32(&acc_bar), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fail = 0;
     }
-    if (warp == 0) {
+    if (warp == 4) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                      "r"(kCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    // address tables of this tile (bit-run maps evaluated once per CTA): the summed index's
+    // offsets in A and B, and the offsets of the tile's rows and columns in C
+    const uint32_t K = ga.n_chunks * kKq;
+    uint32_t *tka = reinterpret_cast<uint32_t *>(gsm + kStages * kStage);
+    uint32_t *tkb = tka + K, *tcm = tkb + K, *tcn = tcm + 64;
+    for (uint32_t i = threadIdx.x; i < K; i += kThreads) {
+        tka[i] = pext_runs(i, g.ak, g.n_ak);
+        tkb[i] = pext_runs(i, g.bk, g.n_bk);
+    }
+    for (uint32_t i = threadIdx.x; i < 64u + (uint32_t)NT; i += kThreads)
+        tcm[i] = i < 64u ? pext_runs(mt * 64u + i, g.cm, g.n_cm) : pext_runs(nt * (uint32_t)NT + i - 64u, g.cn, g.n_cn);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-    if (threadIdx.x == 0) {   // producer
-        for (uint32_t c = 0; c < n_kc; c++) {
-            const uint32_t s = c % kGemmStages;
-            if (c >= (uint32_t)kGemmStages && !mbar_wait(smem_u32(&empty_bar[s]), ((c / kGemmStages) - 1u) & 1u, kGemmPolls)) {
+    float2 *arena = ga.arenas + (uint64_t)il * ga.a.arena_elems;
+    if (warp < 4) {
+        // producers: A rows m = mt*64 + 32*(warp&1) + lane, summed half h = warp>>1 of the
+        // chunk; B units (column, half) strided over the 128 threads. A chunk's loads are
+        // all issued before its conversion, and the next chunk's before this one's stores.
+        const float2 *A = gemm_operand(ga.a, arena, g.a_off, g.flags & kStepALeaf, ga.item0 + il);
+        const float2 *B = gemm_operand(ga.a, arena, g.b_off, g.flags & kStepBLeaf, ga.item0 + il);
+        const uint32_t ml = 32u * (warp & 1u) + lane, h = warp >> 1;
+        const float2 *Arow = A + pext_runs(beta, g.ab, g.n_ab) + pext_runs(mt * 64u + ml, g.am, g.n_am);
+        const float2 *Bcol[kUnits];
+        uint32_t bh[kUnits];
+#pragma unroll
+        for (uint32_t i = 0; i < kUnits; i++) {
+            const uint32_t u = threadIdx.x + 128u * i;
+            const uint32_t nl = u % (uint32_t)NT;
+            bh[i] = u / (uint32_t)NT;
+            Bcol[i] = B + pext_runs(beta, g.bb, g.n_bb) + pext_runs(nt * (uint32_t)NT + nl, g.bn, g.n_bn);
+        }
+        const bool b_on = threadIdx.x < 2u * (uint32_t)NT;   // every unit of a thread shares this
+        Chunk cur, nxt;
+        load_chunk(cur, 0, h, Arow, Bcol, bh, b_on, tka, tkb);
+        for (uint32_t c = 0; c < ga.n_chunks; c++) {
+            const uint32_t s = c % kStages;
+            if (c + 1 < ga.n_chunks) load_chunk(nxt, c + 1, h, Arow, Bcol, bh, b_on, tka, tkb);
+            if (c >= kStages && !mbar_wait(smem_u32(&empty_bar[s]), ((c / kStages) - 1u) & 1u, kPolls)) {
                 fail = 1;
                 break;
             }
-            const uint32_t fb = smem_u32(&full_bar[s]);
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(tile_a + tile_b)
-                         : "memory");
-            const uint32_t sa = sbase + s * (tile_a + tile_b);
-            bulk_g2s(sa, Ablk + (uint64_t)c * tile_a, tile_a, fb);
-            bulk_g2s(sa + tile_a, Bblk + (uint64_t)c * tile_b, tile_b, fb);
+            unsigned char *sa = gsm + s * kStage;
+            store_a(sa, cur.a, ml, h);
+            if (b_on) {
+#pragma unroll
+                for (uint32_t i = 0; i < kUnits; i++)
+                    store_b<NT>(sa + 4u * kRegA, cur.b[i], (threadIdx.x + 128u * i) % (uint32_t)NT, bh[i]);
+            }
+            // the generic-proxy stores must be visible to the tensor cores' reads
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[s])) : "memory");
+            cur = nxt;
         }
-    } else if (threadIdx.x == 32) {   // MMA issuer
+    } else if (lane == 0) {   // MMA issuer
         const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
-                               ((uint32_t)(kGemmRows >> 4) << 24);
-        const uint32_t sbo = kc * 16u;
-        for (uint32_t c = 0; c < n_kc; c++) {
-            const uint32_t s = c % kGemmStages;
-            if (!mbar_wait(smem_u32(&full_bar[s]), (c / kGemmStages) & 1u, kGemmPolls)) {
+                               ((kRows >> 4) << 24);
+        for (uint32_t c = 0; c < ga.n_chunks; c++) {
+            const uint32_t s = c % kStages;
+            if (!mbar_wait(smem_u32(&full_bar[s]), (c / kStages) & 1u, kPolls)) {
                 fail = 1;
                 break;
             }
             tc_fence_after();
-            const uint32_t sa = sbase + s * (tile_a + tile_b), sb = sa + tile_a;
-            for (uint32_t i = 0; i < kc / 16u; i++) {
-                const uint64_t ad = smem_desc(sa + i * 256u, 128u, sbo), bd = smem_desc(sb + i * 256u, 128u, sbo);
-                const uint32_t accumulate = (c | i) != 0u;
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate)
-                    : "memory");
+            const uint32_t sa = sbase + s * kStage, sb = sa + 4u * kRegA;
+            constexpr uint32_t kRegB = region_bytes(NT);
+#pragma unroll
+            for (uint32_t p = 0; p < 2; p++) {
+                const uint64_t ah = smem_desc(sa + (2u * p) * kRegA, 128u, kPitch);
+                const uint64_t al = smem_desc(sa + (2u * p + 1u) * kRegA, 128u, kPitch);
+                const uint64_t bh = smem_desc(sb + (2u * p) * kRegB, 128u, kPitch);
+                const uint64_t bl = smem_desc(sb + (2u * p + 1u) * kRegB, 128u, kPitch);
+                mma_bf16(tmem, ah, bh, idesc, (c | p) != 0u);
+                mma_bf16(tmem, ah, bl, idesc, 1u);
+                mma_bf16(tmem, al, bh, idesc, 1u);
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&empty_bar[s]))
-                         : "memory");
+            mma_commit(smem_u32(&empty_bar[s]));
         }
         // always signal the accumulator, so the MMAs issued so far are waited for
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(&acc_bar))
-                     : "memory");
+        mma_commit(smem_u32(&acc_bar));
     }
     __syncwarp();
-    const bool ok = mbar_wait(smem_u32(&acc_bar), 0, kGemmPolls);
+    bool ok = true;
+    if (warp < 4) ok = mbar_wait(smem_u32(&acc_bar), 0, kPolls);
     tc_fence_after();
     const bool good = __syncthreads_and(ok) && !fail;
-    if (good) {
-        // row 32 warp + lane of the tile: Re (even lane) or Im (odd lane) of complex row m
-        const uint32_t s = lane & 1u;
-        const uint32_t m = mt * (kGemmRows / 2) + warp * 16u + (lane >> 1);
-        float2 *C = ga.arenas + (uint64_t)il * ga.a.arena_elems + g.c_off + pext_runs(beta, g.cb, g.n_cb) +
-                    pext_runs(m, g.cm, g.n_cm);
+    if (good && warp < 4) {
+        // warp w holds tile rows 32w..32w+31, i.e. complex rows m = mt*64 + 16w + lane/2 (Re in
+        // the even lane, Im in the odd one). Each block of up to 32 columns goes through a
+        // padded shared-memory transpose (the operand stages are free now), so that a warp
+        // then stores 32 consecutive columns of one row of C at a time.
+        constexpr uint32_t kW = NT < 32 ? (uint32_t)NT : 32u;   // columns per block
+        constexpr uint32_t kTPitch = 8u * kW + 8u;               // bytes per row of the transpose
+        unsigned char *tb = gsm + warp * 16u * kTPitch;
+        const uint32_t s = lane & 1u, mrow = lane >> 1;
         const uint32_t taddr = tmem + ((warp * 32u) << 16);
-        for (uint32_t j0 = 0; j0 < (uint32_t)NT; j0 += 16) {
-            uint32_t r[16];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-                "%13, %14, %15}, [%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15])
-                : "r"(taddr + j0));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            // the even lane keeps columns j0..j0+7 and takes Im from its odd neighbour; the
-            // odd lane keeps j0+8..j0+15 and takes Re
-#pragma unroll
-            for (int jj = 0; jj < 8; jj++) {
-                const float mine_send = __uint_as_float(s ? r[jj] : r[8 + jj]);
-                const float other = __shfl_xor_sync(0xffffffffu, mine_send, 1);
-                const uint32_t col = j0 + (s ? 8u : 0u) + (uint32_t)jj;
-                const float re = s ? other : __uint_as_float(r[jj]);
-                const float im = s ? __uint_as_float(r[8 + jj]) : other;
-                C[pext_runs(nt * (uint32_t)NT + col, g.cn, g.n_cn)] = make_float2(re, im);
+        float2 *Cb = arena + g.c_off + pext_runs(beta, g.cb, g.n_cb);
+        for (uint32_t j0 = 0; j0 < (uint32_t)NT; j0 += kW) {
+            uint32_t r[kW];
+            if constexpr (kW == 32) {
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                    "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+                    "[%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                      "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                      "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+                      "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+                      "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "r"(taddr + j0));
+            } else {
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                    "%12, %13, %14, %15}, [%16];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                      "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                      "=r"(r[14]), "=r"(r[15])
+                    : "r"(taddr + j0));
             }
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (uint32_t n = 0; n < kW; n++)
+                *reinterpret_cast<uint32_t *>(tb + mrow * kTPitch + n * 8u + s * 4u) = r[n];
+            __syncwarp();
+            if (lane < kW) {
+                const uint32_t coff = tcn[j0 + lane];
+#pragma unroll 4
+                for (uint32_t i = 0; i < 16; i++) {
+                    const float2 v = *reinterpret_cast<const float2 *>(tb + i * kTPitch + lane * 8u);
+                    Cb[tcm[warp * 16u + i] + coff] = v;
+                }
+            }
+            __syncwarp();
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 4) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
     }
     if (!good && threadIdx.x == 0) atomicCAS(ga.a.status, 0u, 4u /* QVX_ETIMEOUT */);
 }
 
-template <int NT>
-size_t gemm_smem(uint32_t kc) {
-    return (size_t)kGemmStages * ((size_t)kGemmRows * kc * 2 + (size_t)NT * kc * 2);
-}
-
 }  // namespace
 
-uint32_t gemm_kc(const GemmStep &g) { return ((6u << g.nk) % 64u == 0) ? 64u : 32u; }
 uint32_t gemm_nt(const GemmStep &g) { return g.nn >= 7 ? 128u : (1u << g.nn); }
-
-size_t gemm_pack_bytes_per_item(const GemmStep &g) {
-    const size_t kp = (size_t)6 << g.nk;
-    return ((size_t)1 << g.nb) * kp * 2 * (((size_t)2 << g.nm) + ((size_t)1 << g.nn));
-}
 
 template <int NT>
 static cudaError_t launch_gemm_nt(const GemmArgs &ga, cudaStream_t s) {
@@ -297,60 +371,46 @@ static cudaError_t launch_gemm_nt(const GemmArgs &ga, cudaStream_t s) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    size_t smem = gemm_smem<NT>(ga.kc);
-    // keep the CTAs an SM can hold within its 512 tensor-memory columns
+    size_t smem = (size_t)kStages * stage_bytes(NT) + 4u * (2u * ga.n_chunks * kKq + 64u + (uint32_t)NT);
+    constexpr size_t kMaxSmem = 200 * 1024;
+    // keep the CTAs an SM can hold within its 512 tensor-memory columns, so that no
+    // allocation ever waits for another CTA's columns
     const int cols = NT < 32 ? 32 : NT;
     const int max_ctas = 512 / cols;
     if (dev < 0 || dev >= 64 || !ready[dev]) {
-        if ((e = cudaFuncSetAttribute(gemm_tc_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)) !=
+        if ((e = cudaFuncSetAttribute(gemm_tc_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem)) !=
             cudaSuccess)
             return e;
         if (dev >= 0 && dev < 64) ready[dev] = 1;
     }
     for (;;) {
         int n = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gemm_tc_kernel<NT>, 128, smem)) != cudaSuccess)
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gemm_tc_kernel<NT>, kThreads, smem)) != cudaSuccess)
             return e;
-        if (n <= max_ctas || smem >= 200 * 1024) break;
+        if (n <= max_ctas) break;
+        if (smem >= kMaxSmem) return cudaErrorInvalidConfiguration;
         smem += 8 * 1024;
     }
     const uint64_t blocks = ((uint64_t)ga.n_items << ga.g.nb) * ga.n_mt * ga.n_nt;
     if (blocks == 0 || blocks > 0x7fffffffull) return cudaErrorInvalidConfiguration;
-    gemm_tc_kernel<NT><<<(unsigned)blocks, 128, smem, s>>>(ga);
+    gemm_tc_kernel<NT><<<(unsigned)blocks, kThreads, smem, s>>>(ga);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gemm_step(const LaunchArgs &a, const GemmStep &g, int64_t item0, int64_t n_items, float2 *arenas,
-                             unsigned char *pack, cudaStream_t s) {
-    if (g.nk < 4 || g.nm < 6 || g.nn < 4 || n_items <= 0) return cudaErrorInvalidConfiguration;
-    const uint32_t kc = gemm_kc(g), nt_cols = gemm_nt(g), K = 1u << g.nk, Kp = 6u * K;
-    const uint32_t M2 = 2u << g.nm, N = 1u << g.nn;
-    const uint64_t ibs = (uint64_t)n_items << g.nb;
-    unsigned char *Ap = pack;
-    unsigned char *Bp = pack + ibs * (uint64_t)M2 * Kp * 2u;
-    cudaError_t e;
-    {
-        const uint64_t threads = ibs * M2 * (Kp / 8u);
-        pack_a_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a, g, item0, n_items, arenas, Ap, kc);
-        if ((e = launch_counted(cudaGetLastError())) != cudaSuccess) return e;
-    }
-    {
-        const uint64_t threads = ibs * N * (Kp / 8u);
-        pack_b_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a, g, item0, n_items, arenas, Bp, kc, nt_cols);
-        if ((e = launch_counted(cudaGetLastError())) != cudaSuccess) return e;
-    }
+                             cudaStream_t s) {
+    if (g.nk < 4 || g.nk > 10 || g.nm < 6 || g.nn < 4 || n_items <= 0) return cudaErrorInvalidConfiguration;
+    const uint32_t nt_cols = gemm_nt(g);
     GemmArgs ga;
     ga.a = a;
     ga.g = g;
     ga.item0 = item0;
     ga.n_items = n_items;
     ga.arenas = arenas;
-    ga.Ap = Ap;
-    ga.Bp = Bp;
-    ga.kc = kc;
-    ga.n_kc = Kp / kc;
-    ga.n_mt = M2 / kGemmRows;
-    ga.n_nt = N / nt_cols;
+    ga.n_chunks = (1u << g.nk) / kKq;
+    ga.n_mt = (2u << g.nm) / kRows;
+    ga.n_nt = (1u << g.nn) / nt_cols;
+    cudaError_t e;
     switch (nt_cols) {
         case 16: e = launch_gemm_nt<16>(ga, s); break;
         case 32: e = launch_gemm_nt<32>(ga, s); break;

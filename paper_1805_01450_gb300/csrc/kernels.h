@@ -103,14 +103,12 @@ cudaError_t launch_grad_sum(const unsigned char *image, const ExactPair *gpart, 
 // launch_counted(e) counts one launch if e is cudaSuccess and returns e.
 uint64_t launches_issued();
 cudaError_t launch_counted(cudaError_t e);
-// Tensor-core form of a dense step (gemm_tc.cu): summed-index chunk and column tile sizes,
-// pack-buffer bytes per work item, and the three launches (pack A, pack B, GEMM) for items
-// [item0, item0 + n_items) whose arenas start at `arenas`.
-uint32_t gemm_kc(const GemmStep &g);
+// Tensor-core form of a dense step (gemm_tc.cu): the column tile size, and the launch for
+// items [item0, item0 + n_items) whose arenas start at `arenas` (operands are read from the
+// arenas as complex64 and split into bf16 parts inside the kernel).
 uint32_t gemm_nt(const GemmStep &g);
-size_t gemm_pack_bytes_per_item(const GemmStep &g);
 cudaError_t launch_gemm_step(const LaunchArgs &a, const GemmStep &g, int64_t item0, int64_t n_items, float2 *arenas,
-                             unsigned char *pack, cudaStream_t s);
+                             cudaStream_t s);
 // Self-test of the bounded waits (grid barrier and mbarrier that can never complete).
 cudaError_t launch_wait_selftest(unsigned *words, unsigned *status, uint32_t polls, unsigned *out, cudaStream_t s);
 

@@ -1190,7 +1190,7 @@ bool serialize(Plan &p, std::string *err) {
         }
     }
     // tensor-core form of the dense contractions (stepwise engine, opts.tensor_cores): every
-    // summed mode in both operands, at least 16 summed entries (K), 64 A-only (M) and 16
+    // summed mode in both operands, 16 to 1024 summed entries (K), 64 A-only (M) and 16
     // B-only (N) output entries, and an arithmetic intensity at or above the FP32 ridge
     std::vector<GemmStep> gms;
     if (p.engine == QVX_ENGINE_STEPWISE && p.opts.tensor_cores) {
@@ -1199,7 +1199,7 @@ bool serialize(Plan &p, std::string *err) {
             const PStep &st = p.steps[s];
             GemmStep &g = gms[s];
             std::memset(&g, 0, sizeof(g));
-            if (st.b < 0 || !st.k_a.empty() || !st.k_b.empty() || st.k_ab.size() < 4) continue;
+            if (st.b < 0 || !st.k_a.empty() || !st.k_b.empty() || st.k_ab.size() < 4 || st.k_ab.size() > 10) continue;
             // the GEMM's row operand needs 64 output entries of its own and the column operand
             // 16; complex products commute, so the step's B may take the row role
             bool swap = false;

@@ -171,10 +171,9 @@ class Program:
             arena[int(r["c_off"]) + c] = acc
 
     def _gemm_step(self, si, A, B, arena):
-        """Step si through its tensor-core form, as the pack and GEMM kernels define it: the
+        """Step si through its tensor-core form, as the GEMM kernel defines it: the
         real block GEMM of bf16 hi/lo parts (hi*hi + hi*lo + lo*hi) accumulated in float64
-        here. Also checks that the tile writes of the pack kernels fill their buffers exactly
-        once and that the GEMM's stores cover C exactly once."""
+        here. Also checks the kernel's tiling and that the GEMM's stores cover C exactly once."""
         g = self.gemms[si]
         st = self.steps[si]
         nb, nm, nn, nk = (int(g[f]) for f in ("nb", "nm", "nn", "nk"))
@@ -206,20 +205,17 @@ class Program:
         re = mm3(arh, arl, brh, brl) - mm3(aih, ail, bih, bil)
         im = mm3(aih, ail, brh, brl) + mm3(arh, arl, bih, bil)
         arena[int(g["c_off"]) + ic] = re + 1j * im
-        # pack-buffer coverage (tile sizes of the kernels: 128 real rows, nt columns, kc chunk)
+        # tiles of the kernel: 64 complex rows, nt columns, chunks of 16 summed entries; the
+        # shared-memory core-matrix layout (8-row groups 272 bytes apart, two 128-byte core
+        # matrices along the summed index) gives each (row, summed-half) its own 16 bytes
         K, M2, N = 1 << nk, 2 << nm, 1 << nn
-        kp = 6 * K
-        kc = 64 if kp % 64 == 0 else 32
         ntc = 128 if nn >= 7 else N
-        r = np.arange(M2)[:, None]
-        j0 = (8 * np.arange(kp // 8))[None, :]
-        offa = ((r // 128) * (kp // kc) + j0 // kc) * (128 * kc * 2) + \
-            (r % 128 // 8) * (kc * 16) + (j0 % kc // 8) * 128 + (r % 8) * 16
-        assert np.array_equal(np.sort(offa.ravel()), 16 * np.arange(M2 * kp // 8))
-        n = np.arange(N)[:, None]
-        offb = ((n // ntc) * (kp // kc) + j0 // kc) * (ntc * kc * 2) + \
-            (n % ntc // 8) * (kc * 16) + (j0 % kc // 8) * 128 + (n % 8) * 16
-        assert np.array_equal(np.sort(offb.ravel()), 16 * np.arange(N * kp // 8))
+        assert K % 16 == 0 and M2 % 128 == 0 and N % ntc == 0 and ntc in (16, 32, 64, 128)
+        for rows in (128, ntc):
+            r = np.arange(rows)[:, None]
+            half = np.arange(2)[None, :]
+            off = (r >> 3) * 272 + half * 128 + (r & 7) * 16
+            assert len(np.unique(off)) == off.size and off.max() + 16 <= rows // 8 * 272
 
     def item_terms(self, x: int, o: int, fused: bool = False, regtile: bool = False, gemm: bool = False):
         """Slice terms of work item (x, o): entry i is slice (o << n_inner) | i. With

@@ -114,9 +114,9 @@ typedef struct {
     int32_t tensor_cores;      /* stepwise engine: 1 runs the dense contractions (16 to 1024
                                   summed entries, 64 output entries of one operand's own and 16 of
                                   the other's, 12 or more flops per algorithmic byte) as complex
-                                  GEMMs on the tcgen05 tensor cores, operands split into bf16 hi +
-                                  lo parts (three products, FP32 accumulation); 0 keeps them on
-                                  FP32 SIMT kernels */
+                                  GEMMs on the tcgen05 tensor cores, each FP32 operand split into
+                                  three bf16 parts (six products, FP32 accumulation: about 2^-23
+                                  relative error per product); 0 keeps them on FP32 SIMT kernels */
 } qvx_plan_opts;
 
 typedef struct {

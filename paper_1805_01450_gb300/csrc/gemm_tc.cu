@@ -5,17 +5,20 @@
 //   [Ar  -Ai]        [Br]
 //   [Ai   Ar]  times [Bi]
 // are Re C[m, :] and Im C[m, :] (the left factor's first column block is "part 0", the
-// second "part 1"). Every real operand x is split as x = hi + lo with hi, lo in bf16, and
-// three products hi*hi + hi*lo + lo*hi are accumulated in FP32 (the lo*lo term, below
-// 2^-16 of the product, is dropped).
+// second "part 1"). Every real operand x is split into three bf16 parts x = h + m + l
+// (8 significant bits each: h = rn(x), m = rn(x - h), l = rn(x - h - m)), and the six
+// products h*h + h*m + m*h + h*l + l*h + m*m are accumulated in FP32; the dropped terms
+// (m*l, l*m, l*l) are below 2^-23 of the product. Two parts with three products (about
+// 2^-16 per product) are not accurate enough: on a 64-qubit circuit the amplitude moved by
+// 1.2e-5 of its size, above the 1e-5 tolerance.
 //
 // One CTA computes a tile of 128 real rows (64 complex rows m) by NT columns n for one
 // (item, b). Warps 0-3 read the complex64 operands straight from the arena, one chunk of
-// 16 summed entries at a time, split them into bf16 hi and lo and store them in shared
+// 16 summed entries at a time, split them into three bf16 parts and store them in shared
 // memory in the tensor cores' K-major core-matrix layout (no separate packing pass: the
 // operands cross HBM once, as complex64). Warp 4 allocates the tensor-memory accumulator
-// and one of its threads issues the chunk's six tcgen05.mma (2 parts x 3 products, K = 16
-// each); the commit of a chunk's MMAs frees its shared-memory stage. Warps 0-3 then read
+// and one of its threads issues the chunk's twelve tcgen05.mma (2 parts x 6 products,
+// K = 16 each); the commit of a chunk's MMAs frees its shared-memory stage. Warps 0-3 then read
 // the accumulator back with tcgen05.ld and store complex64 C in its own layout.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -28,7 +31,8 @@ namespace qvx {
 namespace {
 
 constexpr uint32_t kRows = 128;        // real rows per tile (64 complex rows)
-constexpr uint32_t kStages = 2;        // shared-memory ring of summed-index chunks
+constexpr uint32_t kStages = 1;        // shared-memory stages of summed-index chunks (the next
+                                       // chunk waits in registers meanwhile)
 constexpr uint32_t kKq = 16;           // complex summed entries per chunk (one MMA K-step)
 constexpr uint32_t kPitch = 272;       // bytes between 8-row groups: two 128-byte core matrices
                                        // along the summed index and 16 bytes that spread the
@@ -37,8 +41,8 @@ constexpr uint32_t kPolls = 1u << 22;
 constexpr uint32_t kThreads = 160;     // warps 0-3: operands and epilogue; warp 4: MMA
 
 __host__ __device__ constexpr uint32_t region_bytes(uint32_t rows) { return rows / 8u * kPitch; }
-// One stage: A regions (part 0 hi, part 0 lo, part 1 hi, part 1 lo), then the same for B.
-__host__ __device__ constexpr uint32_t stage_bytes(uint32_t nt) { return 4u * region_bytes(kRows) + 4u * region_bytes(nt); }
+// One stage: A regions (part 0 h, m, l, part 1 h, m, l), then the same for B.
+__host__ __device__ constexpr uint32_t stage_bytes(uint32_t nt) { return 6u * region_bytes(kRows) + 6u * region_bytes(nt); }
 
 __device__ __forceinline__ uint32_t core_offset(uint32_t r, uint32_t g) {
     return (r >> 3) * kPitch + g * 128u + (r & 7u) * 16u;
@@ -56,11 +60,16 @@ __device__ __forceinline__ const float2 *gemm_operand(const LaunchArgs &a, const
     return ldata + leaf_base(leaves[ref], x, o);
 }
 
-// bf16 split of v: hi = rn(v), lo = rn(v - hi), as raw 16-bit patterns.
-__device__ __forceinline__ void split_bf16(float v, uint32_t &hi, uint32_t &lo) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    hi = __bfloat16_as_ushort(h);
-    lo = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(h)));
+// Three-part bf16 split of v as raw 16-bit patterns: h = rn(v), m = rn(v - h),
+// l = rn(v - h - m); both differences are exact in FP32.
+__device__ __forceinline__ void split_bf16(float v, uint32_t &h, uint32_t &m, uint32_t &l) {
+    const __nv_bfloat16 bh = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(bh);
+    const __nv_bfloat16 bm = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(bm);
+    h = __bfloat16_as_ushort(bh);
+    m = __bfloat16_as_ushort(bm);
+    l = __bfloat16_as_ushort(__float2bfloat16_rn(r2));
 }
 
 __device__ __forceinline__ uint4 pack8(const uint32_t *h) {
@@ -95,48 +104,49 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                  : "memory");
 }
 
-// bf16 hi/lo parts of 8 summed entries of one operand row or column.
-__device__ __forceinline__ void split8(const float2 *v, uint32_t *rh, uint32_t *rl, uint32_t *ih, uint32_t *il) {
+// Three bf16 parts (index 0: h, 1: m, 2: l) of the real and imaginary parts of 8 summed
+// entries of one operand row or column.
+__device__ __forceinline__ void split8(const float2 *v, uint32_t (*re)[8], uint32_t (*im)[8]) {
 #pragma unroll
     for (int j = 0; j < 8; j++) {
-        split_bf16(v[j].x, rh[j], rl[j]);
-        split_bf16(v[j].y, ih[j], il[j]);
+        split_bf16(v[j].x, re[0][j], re[1][j], re[2][j]);
+        split_bf16(v[j].y, im[0][j], im[1][j], im[2][j]);
     }
 }
 
-// A rows 2m and 2m+1 of one summed half (8 entries) in the four A regions of a stage:
-// part 0 takes (Ar, Ai), part 1 takes (-Ai, Ar).
+// A rows 2m and 2m+1 of one summed half (8 entries) in the six A regions of a stage
+// (region 3p + level): part 0 takes (Ar, Ai), part 1 takes (-Ai, Ar).
 __device__ __forceinline__ void store_a(unsigned char *sa, const float2 *v, uint32_t ml, uint32_t h) {
     constexpr uint32_t R = region_bytes(kRows);
-    uint32_t rh[8], rl[8], ih[8], il[8];
-    split8(v, rh, rl, ih, il);
+    uint32_t re[3][8], im[3][8];
+    split8(v, re, im);
     const uint32_t r0 = core_offset(2u * ml, h), r1 = core_offset(2u * ml + 1u, h);
-    *reinterpret_cast<uint4 *>(sa + 0u * R + r0) = pack8(rh);
-    *reinterpret_cast<uint4 *>(sa + 1u * R + r0) = pack8(rl);
-    *reinterpret_cast<uint4 *>(sa + 0u * R + r1) = pack8(ih);
-    *reinterpret_cast<uint4 *>(sa + 1u * R + r1) = pack8(il);
-    *reinterpret_cast<uint4 *>(sa + 2u * R + r1) = pack8(rh);
-    *reinterpret_cast<uint4 *>(sa + 3u * R + r1) = pack8(rl);
 #pragma unroll
-    for (int j = 0; j < 8; j++) {
-        ih[j] ^= 0x8000u;
-        il[j] ^= 0x8000u;
+    for (uint32_t q = 0; q < 3; q++) {
+        *reinterpret_cast<uint4 *>(sa + q * R + r0) = pack8(re[q]);
+        *reinterpret_cast<uint4 *>(sa + q * R + r1) = pack8(im[q]);
+        *reinterpret_cast<uint4 *>(sa + (3u + q) * R + r1) = pack8(re[q]);
     }
-    *reinterpret_cast<uint4 *>(sa + 2u * R + r0) = pack8(ih);
-    *reinterpret_cast<uint4 *>(sa + 3u * R + r0) = pack8(il);
+#pragma unroll
+    for (uint32_t q = 0; q < 3; q++) {
+#pragma unroll
+        for (int j = 0; j < 8; j++) im[q][j] ^= 0x8000u;
+        *reinterpret_cast<uint4 *>(sa + (3u + q) * R + r0) = pack8(im[q]);
+    }
 }
 
-// B column n of one summed half in the four B regions: part 0 takes Br, part 1 Bi.
+// B column n of one summed half in the six B regions: part 0 takes Br, part 1 Bi.
 template <int NT>
 __device__ __forceinline__ void store_b(unsigned char *sb, const float2 *v, uint32_t nl, uint32_t h) {
     constexpr uint32_t R = region_bytes(NT);
-    uint32_t rh[8], rl[8], ih[8], il[8];
-    split8(v, rh, rl, ih, il);
+    uint32_t re[3][8], im[3][8];
+    split8(v, re, im);
     const uint32_t o = core_offset(nl, h);
-    *reinterpret_cast<uint4 *>(sb + 0u * R + o) = pack8(rh);
-    *reinterpret_cast<uint4 *>(sb + 1u * R + o) = pack8(rl);
-    *reinterpret_cast<uint4 *>(sb + 2u * R + o) = pack8(ih);
-    *reinterpret_cast<uint4 *>(sb + 3u * R + o) = pack8(il);
+#pragma unroll
+    for (uint32_t q = 0; q < 3; q++) {
+        *reinterpret_cast<uint4 *>(sb + q * R + o) = pack8(re[q]);
+        *reinterpret_cast<uint4 *>(sb + (3u + q) * R + o) = pack8(im[q]);
+    }
 }
 
 // One chunk's operand entries held in registers between their loads and their conversion:
@@ -264,7 +274,7 @@ __global__ void __launch_bounds__(kThreads, 3) gemm_tc_kernel(GemmArgs ga) {
             if (b_on) {
 #pragma unroll
                 for (uint32_t i = 0; i < kUnits; i++)
-                    store_b<NT>(sa + 4u * kRegA, cur.b[i], (threadIdx.x + 128u * i) % (uint32_t)NT, bh[i]);
+                    store_b<NT>(sa + 6u * kRegA, cur.b[i], (threadIdx.x + 128u * i) % (uint32_t)NT, bh[i]);
             }
             // the generic-proxy stores must be visible to the tensor cores' reads
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -281,17 +291,23 @@ __global__ void __launch_bounds__(kThreads, 3) gemm_tc_kernel(GemmArgs ga) {
                 break;
             }
             tc_fence_after();
-            const uint32_t sa = sbase + s * kStage, sb = sa + 4u * kRegA;
+            const uint32_t sa = sbase + s * kStage, sb = sa + 6u * kRegA;
             constexpr uint32_t kRegB = region_bytes(NT);
 #pragma unroll
             for (uint32_t p = 0; p < 2; p++) {
-                const uint64_t ah = smem_desc(sa + (2u * p) * kRegA, 128u, kPitch);
-                const uint64_t al = smem_desc(sa + (2u * p + 1u) * kRegA, 128u, kPitch);
-                const uint64_t bh = smem_desc(sb + (2u * p) * kRegB, 128u, kPitch);
-                const uint64_t bl = smem_desc(sb + (2u * p + 1u) * kRegB, 128u, kPitch);
-                mma_bf16(tmem, ah, bh, idesc, (c | p) != 0u);
-                mma_bf16(tmem, ah, bl, idesc, 1u);
-                mma_bf16(tmem, al, bh, idesc, 1u);
+                uint64_t ad[3], bd[3];
+#pragma unroll
+                for (uint32_t q = 0; q < 3; q++) {
+                    ad[q] = smem_desc(sa + (3u * p + q) * kRegA, 128u, kPitch);
+                    bd[q] = smem_desc(sb + (3u * p + q) * kRegB, 128u, kPitch);
+                }
+                // h*h, h*m, m*h, h*l, l*h, m*m
+                mma_bf16(tmem, ad[0], bd[0], idesc, (c | p) != 0u);
+                mma_bf16(tmem, ad[0], bd[1], idesc, 1u);
+                mma_bf16(tmem, ad[1], bd[0], idesc, 1u);
+                mma_bf16(tmem, ad[0], bd[2], idesc, 1u);
+                mma_bf16(tmem, ad[2], bd[0], idesc, 1u);
+                mma_bf16(tmem, ad[1], bd[1], idesc, 1u);
             }
             mma_commit(smem_u32(&empty_bar[s]));
         }

@@ -172,8 +172,8 @@ class Program:
 
     def _gemm_step(self, si, A, B, arena):
         """Step si through its tensor-core form, as the GEMM kernel defines it: the
-        real block GEMM of bf16 hi/lo parts (hi*hi + hi*lo + lo*hi) accumulated in float64
-        here. Also checks the kernel's tiling and that the GEMM's stores cover C exactly once."""
+        real block GEMM of three-part bf16 splits (h*h + h*m + m*h + h*l + l*h + m*m)
+        accumulated in float64 here. Also checks the kernel's tiling and that the GEMM's stores cover C exactly once."""
         g = self.gemms[si]
         st = self.steps[si]
         nb, nm, nn, nk = (int(g[f]) for f in ("nb", "nm", "nn", "nk"))
@@ -189,21 +189,20 @@ class Program:
         Ac = np.asarray(A(ia.ravel())).reshape(ia.shape).astype(np.complex64)
         Bc = np.asarray(B(ib.ravel())).reshape(ib.shape).astype(np.complex64)
 
-        def split(v):   # float32 -> bf16 hi and lo (round to nearest even), as float64
+        def split(v):   # float32 -> three bf16 parts h, m, l (round to nearest even), as float64
             v = np.asarray(v, dtype=np.float32)
-            hi = _bf16(v)
-            lo = _bf16((v - hi.astype(np.float32)).astype(np.float32))
-            return hi.astype(np.float64), lo.astype(np.float64)
-        arh, arl = split(Ac.real)
-        aih, ail = split(Ac.imag)
-        brh, brl = split(Bc.real)
-        bih, bil = split(Bc.imag)
+            h = _bf16(v)
+            r1 = (v - h).astype(np.float32)
+            m = _bf16(r1)
+            lo = _bf16((r1 - m).astype(np.float32))
+            return h.astype(np.float64), m.astype(np.float64), lo.astype(np.float64)
+        ar, ai, br, bi = split(Ac.real), split(Ac.imag), split(Bc.real), split(Bc.imag)
 
-        def mm3(xh, xl, yh, yl):
-            return (np.einsum("bmk,bkn->bmn", xh, yh) + np.einsum("bmk,bkn->bmn", xh, yl) +
-                    np.einsum("bmk,bkn->bmn", xl, yh))
-        re = mm3(arh, arl, brh, brl) - mm3(aih, ail, bih, bil)
-        im = mm3(aih, ail, brh, brl) + mm3(arh, arl, bih, bil)
+        def mm6(x, y):   # h*h + h*m + m*h + h*l + l*h + m*m
+            return sum(np.einsum("bmk,bkn->bmn", x[i], y[j]) for i, j in
+                       ((0, 0), (0, 1), (1, 0), (0, 2), (2, 0), (1, 1)))
+        re = mm6(ar, br) - mm6(ai, bi)
+        im = mm6(ai, br) + mm6(ar, bi)
         arena[int(g["c_off"]) + ic] = re + 1j * im
         # tiles of the kernel: 64 complex rows, nt columns, chunks of 16 summed entries; the
         # shared-memory core-matrix layout (8-row groups 272 bytes apart, two 128-byte core

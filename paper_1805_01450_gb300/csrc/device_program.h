@@ -47,7 +47,7 @@ struct DevLeaf {
 // Steps are grouped into phases of independent steps; lane_map[phase * lanes + lane] gives
 // the step a lane of a work item's group works on (bits 0-11), the lane's index among the
 // step's lanes (bits 12-21) and their count (bits 22-31), or 0xffffffff for none.
-struct FusedStep {
+struct alignas(16) FusedStep {
     uint32_t a_off, b_off, c_off;  // arena offsets, or leaf indices (flags as in DevStep)
     uint32_t tab_off;              // first table entry of this step
     uint32_t flags;

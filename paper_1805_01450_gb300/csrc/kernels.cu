@@ -172,8 +172,7 @@ __device__ __forceinline__ uint32_t compress_bits(uint32_t v, uint32_t mask, uin
 // scalar) at terms[slot * (s_end - s_begin) + s - s_begin].
 template <bool CG>
 __device__ void finish_item_t(const FinishInfo &P, const LaunchArgs &a, const float2 *fin, int64_t b, uint64_t o,
-                              int lane) {
-    const uint64_t x = a.bitstrings[b];
+                              int lane, uint64_t x) {
     const bool zero = (x & P.zero_mask) != 0;
     const uint32_t n_in = P.n_in, present = P.present;
     const uint32_t inner_bits = __popc(present);
@@ -204,12 +203,12 @@ __device__ void finish_item_t(const FinishInfo &P, const LaunchArgs &a, const fl
 
 __device__ __forceinline__ void finish_item(const FinishInfo &P, const LaunchArgs &a, const float2 *fin, int64_t b,
                                             uint64_t o, int lane, int) {
-    finish_item_t<false>(P, a, fin, b, o, lane);
+    finish_item_t<false>(P, a, fin, b, o, lane, a.bitstrings[b]);
 }
 
 __device__ __forceinline__ void finish_item_cg(const FinishInfo &P, const LaunchArgs &a, const float2 *fin, int64_t b,
                                                uint64_t o, int lane) {
-    finish_item_t<true>(P, a, fin, b, o, lane);
+    finish_item_t<true>(P, a, fin, b, o, lane, a.bitstrings[b]);
 }
 
 // ------------------------------------------------------------------ fused engine
@@ -274,7 +273,14 @@ __device__ __forceinline__ LaneWork lane_work(uint32_t m, const FusedStep *steps
     LaneWork w;
     w.active = m != 0xffffffffu;
     if (!w.active) return w;
-    w.st = steps[m & 0xfffu];
+    {   // three 16-byte shared-memory loads instead of field-by-field copies
+        const uint4 *src = reinterpret_cast<const uint4 *>(steps + (m & 0xfffu));
+        const uint4 v0 = src[0], v1 = src[1], v2 = src[2];
+        uint4 *dst = reinterpret_cast<uint4 *>(&w.st);
+        dst[0] = v0;
+        dst[1] = v1;
+        dst[2] = v2;
+    }
     w.sub = (m >> 12) & 0x3ffu;
     w.cnt = m >> 22;
     const uint32_t flags = w.st.flags;
@@ -377,6 +383,10 @@ __global__ void __launch_bounds__(512) fused_program_kernel(LaunchArgs a, int wa
     const uint32_t *lane_map = reinterpret_cast<const uint32_t *>(img + map_off);
     const float2 *ldata = reinterpret_cast<const float2 *>(img + P->leaf_data_off);
     unsigned char *cur = smem;
+    // the first item's bitstring is read while the program is being staged
+    const int groups0 = blockDim.x / (32 * warps_per_item);
+    const int64_t item0 = (int64_t)blockIdx.x * groups0 + threadIdx.x / (32 * warps_per_item);
+    uint64_t x_next = item0 < a.batch * a.o_count ? a.bitstrings[item0 / a.o_count] : 0ull;
     if (STAGED) {
         const uint32_t s1 = a.smem_steps_bytes, s2 = s1 + a.smem_leaf_bytes, s3 = s2 + a.smem_leaves_bytes;
         const uint32_t bar = smem_u32(&stage_bar);
@@ -418,7 +428,9 @@ __global__ void __launch_bounds__(512) fused_program_kernel(LaunchArgs a, int wa
          item += (int64_t)gridDim.x * groups) {
         const int64_t b = item / a.o_count;
         const uint64_t o = (uint64_t)(a.o_begin + item % a.o_count);
-        const uint64_t x = a.bitstrings[b];
+        const uint64_t x = x_next;
+        const int64_t item_next = item + (int64_t)gridDim.x * groups;
+        if (item_next < n_items) x_next = a.bitstrings[item_next / a.o_count];
         for (uint32_t l = lane; l < n_leaves; l += lanes) lbase[l] = leaf_base(leaves[l], x, o);
         if (warps_per_item == 1) __syncwarp();
         else asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(lanes));
@@ -431,7 +443,7 @@ __global__ void __launch_bounds__(512) fused_program_kernel(LaunchArgs a, int wa
             else asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(lanes));
             w = next;
         }
-        if (lane < 32) finish_item(fin, a, arena + final_off, b, o, lane, 32);
+        if (lane < 32) finish_item_t<false>(fin, a, arena + final_off, b, o, lane, x);
         if (warps_per_item == 1) __syncwarp();
         else asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(lanes));
     }

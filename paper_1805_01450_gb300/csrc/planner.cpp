@@ -510,6 +510,102 @@ struct ProgramBuilder {
         return c;
     }
 
+    // Two consecutive steps C = sum_S X Y and D = sum_S2 C Z, where Y and Z are leaves and C
+    // feeds only the second, equal D = sum_{(S u S2) n X} X W with the leaf
+    // W = sum_{(S u S2) \ X} Y Z (Z holds no mode of S, which C no longer has). W is contracted
+    // here in FP64 when it stays within host_merge_rank modes (modes fixed per work item
+    // included) and the new step costs no more flops than the two it replaces; C is never
+    // written and one pass over the large operand is saved. Applied along chains of leaves.
+    void absorb_leaf_chains() {
+        std::vector<char> gone(p.steps.size(), 0);
+        auto dev_modes = [&](const std::vector<int> &full) {
+            std::vector<int> r;
+            for (int v : full)
+                if (!fixed[v]) r.push_back(v);
+            return r;
+        };
+        auto union_size = [](const std::vector<int> &A, const std::vector<int> &B) {
+            size_t n = A.size();
+            for (int v : B) n += find_pos(A, v) < 0 ? 1 : 0;
+            return n;
+        };
+        for (size_t s = 0; s < p.steps.size(); s++) {
+            if (gone[s] || p.steps[s].b < 0) continue;
+            const int c = p.steps[s].c, s2 = p.tensors[c].consumer;
+            if (s2 < 0 || p.steps[s2].b < 0) continue;
+            const PStep st = p.steps[s], st2 = p.steps[s2];
+            const int z = st2.a == c ? st2.b : st2.a;
+            const int lz = p.tensors[z].leaf;
+            if (lz < 0 || p.leaves[lz].param >= 0) continue;
+            std::vector<int> S = st.k_ab, S2 = st2.k_ab;
+            S.insert(S.end(), st.k_a.begin(), st.k_a.end());
+            S.insert(S.end(), st.k_b.begin(), st.k_b.end());
+            S2.insert(S2.end(), st2.k_a.begin(), st2.k_a.end());
+            S2.insert(S2.end(), st2.k_b.begin(), st2.k_b.end());
+            std::vector<int> SS = S;
+            for (int v : S2) SS.push_back(v);
+            int best_y = -1;
+            HostTensor best_w;
+            std::vector<int> best_wdev;
+            for (int y : {st.a, st.b}) {
+                const int x = y == st.a ? st.b : st.a;
+                const int ly = p.tensors[y].leaf;
+                if (ly < 0 || p.leaves[ly].param >= 0) continue;
+                const std::vector<int> &X = p.tensors[x].modes;
+                const HostTensor &Y = p.leaves[ly], &Z = p.leaves[lz];
+                std::vector<int> dead, R;
+                for (int v : SS)
+                    if (find_pos(X, v) < 0) dead.push_back(v);
+                for (const std::vector<int> *M : {&Y.modes, &Z.modes})
+                    for (int v : *M)
+                        if (find_pos(dead, v) < 0 && find_pos(R, v) < 0) R.push_back(v);
+                if ((int)R.size() > p.opts.host_merge_rank) continue;
+                const std::vector<int> wdev = dev_modes(R);
+                const double before = std::ldexp(1.0, (int)union_size(X, p.tensors[y].modes)) +
+                                      std::ldexp(1.0, (int)union_size(p.tensors[c].modes, p.tensors[z].modes));
+                const double after = std::ldexp(1.0, (int)union_size(X, wdev));
+                if (after > before) continue;
+                if (best_y < 0 || wdev.size() < best_wdev.size()) {
+                    best_y = y;
+                    best_w = host_contract(Y, Z, R, dead);
+                    best_wdev = wdev;
+                }
+            }
+            if (best_y < 0) continue;
+            const int x = best_y == st.a ? st.b : st.a;
+            p.leaves.push_back(best_w);
+            const int w = new_tensor(best_wdev);
+            p.tensors[w].leaf = (int)p.leaves.size() - 1;
+            PStep ns;
+            ns.a = x;
+            ns.b = w;
+            ns.c = st2.c;
+            for (int v : SS) {
+                if (find_pos(p.tensors[x].modes, v) < 0) continue;
+                if (find_pos(best_wdev, v) >= 0) ns.k_ab.push_back(v);
+                else ns.k_a.push_back(v);
+            }
+            p.steps[s2] = ns;
+            gone[s] = 1;
+            p.tensors[x].consumer = s2;
+            p.tensors[w].consumer = s2;
+            p.tensors[best_y].consumer = kMergedOnHost;
+            p.tensors[z].consumer = kMergedOnHost;
+            p.tensors[c].producer = -1;
+            p.tensors[c].consumer = kMergedOnHost;
+        }
+        // drop the absorbed steps and renumber producers and consumers
+        std::vector<int> new_id(p.steps.size(), -1);
+        std::vector<PStep> kept;
+        for (size_t s = 0; s < p.steps.size(); s++)
+            if (!gone[s]) { new_id[s] = (int)kept.size(); kept.push_back(p.steps[s]); }
+        for (PTensor &t : p.tensors) {
+            if (t.producer >= 0) t.producer = new_id[t.producer];
+            if (t.consumer >= 0) t.consumer = new_id[t.consumer];
+        }
+        p.steps = std::move(kept);
+    }
+
     int reduce(int a) {
         const std::vector<int> A = p.tensors[a].modes;
         PStep s;
@@ -597,6 +693,7 @@ struct ProgramBuilder {
         int fin = pool[0];
         if (p.tensors[fin].leaf >= 0) fin = reduce(fin);   // the final tensor lives in the arena
         p.final_tensor = fin;
+        if (p.opts.host_merge_rank > 0) absorb_leaf_chains();
         return true;
     }
 };

@@ -54,7 +54,7 @@ struct alignas(16) FusedStep {
     uint8_t rc, nk_ab, nk_a, nk_b;
     uint8_t a_cb, b_cb, nk, pad1;
     uint32_t pad2;
-    uint16_t koff_a[4], koff_b[4]; // offsets of summed index k (nk <= 2) in A and B
+    uint16_t koff_a[8], koff_b[8]; // offsets of summed index k (nk <= 3) in A and B
 };
 
 // Gradient program: out[o] = sum_k X(o, k) * Y(o, k), each operand addressed through bit
@@ -181,5 +181,5 @@ static_assert(sizeof(RegTileStep) == 224, "RegTileStep layout");
 static_assert(sizeof(GenOperand) == 112, "GenOperand layout");
 static_assert(sizeof(GenStep) == 240, "GenStep layout");
 static_assert(sizeof(ParamLeaf) == 24, "ParamLeaf layout");
-static_assert(sizeof(FusedStep) == 48, "FusedStep layout");
+static_assert(sizeof(FusedStep) == 64, "FusedStep layout");
 }  // namespace qvx

@@ -218,15 +218,15 @@ __device__ __forceinline__ void finish_item_cg(const FinishInfo &P, const Launch
 // and its tensor arena.
 
 // One output entry of a fused step: e packs the operands' offsets pext(c); the summed
-// index's offsets come from the step's koff tables (nk <= 2) or from its bit counts.
+// index's offsets come from the step's koff tables (nk <= 3) or from its bit counts.
 __device__ __forceinline__ float2 fused_entry(const FusedStep &st, uint32_t e, const float2 *__restrict__ A,
                                               const float2 *__restrict__ B, bool unary) {
     const uint32_t ia = e & 0xffffu, ib = e >> 16;
     float2 acc = make_float2(0.f, 0.f);
-    if (st.nk <= 2) {
+    if (st.nk <= 3) {
         const uint32_t nk = 1u << st.nk;
 #pragma unroll
-        for (uint32_t k = 0; k < 4; k++) {   // constant indices keep koff in registers
+        for (uint32_t k = 0; k < 8; k++) {   // constant indices keep koff in registers
             if (k < nk) {
                 if (unary) {
                     const float2 v = A[ia + st.koff_a[k]];
@@ -255,6 +255,56 @@ __device__ __forceinline__ float2 fused_entry(const FusedStep &st, uint32_t e, c
     return acc;
 }
 
+// Entries c = sub, sub + cnt, ... < n_out of a two-operand step with 2^NK summed entries
+// (NK = 2 or 3), two entries at a time: all operand loads of both are issued before the
+// multiply-adds.
+template <int NK>
+__device__ __forceinline__ void lane_entries_k(const FusedStep &st, uint32_t sub, uint32_t cnt, uint32_t n_out,
+                                               const uint32_t *tab, const float2 *__restrict__ A,
+                                               const float2 *__restrict__ B, float2 *C) {
+    constexpr int K = 1 << NK;
+    uint32_t ka[K], kb[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        ka[k] = st.koff_a[k];
+        kb[k] = st.koff_b[k];
+    }
+    uint32_t c = sub;
+    for (; c + cnt < n_out; c += 2 * cnt) {
+        const uint32_t e0 = tab[c], e1 = tab[c + cnt];
+        const uint32_t ia0 = e0 & 0xffffu, ib0 = e0 >> 16, ia1 = e1 & 0xffffu, ib1 = e1 >> 16;
+        float2 p0[K], q0[K], p1[K], q1[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            p0[k] = A[ia0 + ka[k]];
+            q0[k] = B[ib0 + kb[k]];
+            p1[k] = A[ia1 + ka[k]];
+            q1[k] = B[ib1 + kb[k]];
+        }
+        float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            cmac(acc0, p0[k], q0[k]);
+            cmac(acc1, p1[k], q1[k]);
+        }
+        C[c] = acc0;
+        C[c + cnt] = acc1;
+    }
+    if (c < n_out) {
+        const uint32_t e = tab[c], ia = e & 0xffffu, ib = e >> 16;
+        float2 p[K], q[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            p[k] = A[ia + ka[k]];
+            q[k] = B[ib + kb[k]];
+        }
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < K; k++) cmac(acc, p[k], q[k]);
+        C[c] = acc;
+    }
+}
+
 constexpr uint32_t kWaitPolls = 1u << 20;
 
 // The work of one lane in one phase: its step, operand bases and entry stride.
@@ -273,13 +323,14 @@ __device__ __forceinline__ LaneWork lane_work(uint32_t m, const FusedStep *steps
     LaneWork w;
     w.active = m != 0xffffffffu;
     if (!w.active) return w;
-    {   // three 16-byte shared-memory loads instead of field-by-field copies
+    {   // four 16-byte shared-memory loads instead of field-by-field copies
         const uint4 *src = reinterpret_cast<const uint4 *>(steps + (m & 0xfffu));
-        const uint4 v0 = src[0], v1 = src[1], v2 = src[2];
+        const uint4 v0 = src[0], v1 = src[1], v2 = src[2], v3 = src[3];
         uint4 *dst = reinterpret_cast<uint4 *>(&w.st);
         dst[0] = v0;
         dst[1] = v1;
         dst[2] = v2;
+        dst[3] = v3;
     }
     w.sub = (m >> 12) & 0x3ffu;
     w.cnt = m >> 22;
@@ -357,6 +408,10 @@ __device__ __forceinline__ void run_lane_work(const LaneWork &w) {
             cmac(acc, a1, b1);
             w.C[c] = acc;
         }
+    } else if (!unary && w.st.nk == 2) {
+        lane_entries_k<2>(w.st, w.sub, w.cnt, n_out, w.tab, A, B, w.C);
+    } else if (!unary && w.st.nk == 3) {
+        lane_entries_k<3>(w.st, w.sub, w.cnt, n_out, w.tab, A, B, w.C);
     } else {
         for (uint32_t c = w.sub; c < n_out; c += w.cnt) w.C[c] = fused_entry(w.st, w.tab[c], A, B, unary);
     }

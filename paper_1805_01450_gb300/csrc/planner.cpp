@@ -1365,7 +1365,7 @@ bool serialize(Plan &p, std::string *err) {
         f.a_cb = d.a_cb;
         f.b_cb = d.b_cb;
         f.nk = (uint8_t)(d.nk_ab + d.nk_a + d.nk_b);
-        for (uint32_t k = 0; k < 4 && k < (1u << f.nk); k++) {
+        for (uint32_t k = 0; k < 8 && k < (1u << f.nk); k++) {
             const uint32_t ka = k & ((1u << (d.nk_ab + d.nk_a)) - 1u);
             const uint32_t kb = (k & ((1u << d.nk_ab) - 1u)) | ((k >> (d.nk_ab + d.nk_a)) << d.nk_ab);
             f.koff_a[k] = (uint16_t)(ka << d.a_cb);

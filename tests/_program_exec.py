@@ -32,7 +32,7 @@ PROG = np.dtype([("magic", "<u4"), ("n_steps", "<u4"), ("n_leaves", "<u4"), ("pa
                  ("gphase_entry_off", "<u8"), ("gemm_off", "<u8"), ("image_bytes", "<u8")])
 FSTEP = np.dtype([("a_off", "<u4"), ("b_off", "<u4"), ("c_off", "<u4"), ("tab_off", "<u4"), ("flags", "<u4"),
                   ("rc", "u1"), ("nk_ab", "u1"), ("nk_a", "u1"), ("nk_b", "u1"), ("a_cb", "u1"), ("b_cb", "u1"),
-                  ("nk", "u1"), ("pad1", "u1"), ("pad2", "<u4"), ("koff_a", "<u2", (4,)), ("koff_b", "<u2", (4,))])
+                  ("nk", "u1"), ("pad1", "u1"), ("pad2", "<u4"), ("koff_a", "<u2", (8,)), ("koff_b", "<u2", (8,))])
 GOP = np.dtype([("off", "<u8"), ("kind", "<u4"), ("n_oruns", "u1"), ("n_kruns", "u1"), ("pad0", "u1"),
                 ("pad1", "u1"), ("oruns", RUN, (12,)), ("kruns", RUN, (12,))])
 GSTEP = np.dtype([("x", GOP), ("y", GOP), ("out_off", "<u8"), ("ro", "<u4"), ("nk", "<u4")])
@@ -42,7 +42,7 @@ RTSTEP = np.dtype([("a_off", "<u8"), ("b_off", "<u8"), ("c_off", "<u8"), ("flags
                    ("a_cb", "u1"), ("b_cb", "u1"), ("n_free", "u1"), ("na_runs", "u1"), ("nb_runs", "u1"),
                    ("free_runs", RUN, (6,)), ("runs_a", RUN, (12,)), ("runs_b", RUN, (12,)),
                    ("a_m", "<u4", (4,)), ("b_n", "<u4", (4,)), ("c_m", "<u4", (4,)), ("c_n", "<u4", (4,))])
-assert STEP.itemsize == 136 and LEAF.itemsize == 40 and PROG.itemsize == 320 and FSTEP.itemsize == 48
+assert STEP.itemsize == 136 and LEAF.itemsize == 40 and PROG.itemsize == 320 and FSTEP.itemsize == 64
 GEMM = np.dtype([("a_off", "<u8"), ("b_off", "<u8"), ("c_off", "<u8"), ("flags", "<u4"), ("nb", "u1"),
                  ("nm", "u1"), ("nn", "u1"), ("nk", "u1"), ("n_ab", "u1"), ("n_am", "u1"), ("n_ak", "u1"),
                  ("n_bb", "u1"), ("n_bn", "u1"), ("n_bk", "u1"), ("n_cb", "u1"), ("n_cm", "u1"), ("n_cn", "u1"),
@@ -256,7 +256,7 @@ class Program:
                 ia, ib = e & 0xFFFF, (None if unary else e >> 16)
                 nk = int(fst["nk"])
                 assert nk == nab_ + na_ + nb_
-                for k in range(min(1 << nk, 4)):
+                for k in range(min(1 << nk, 8)):
                     ka = k & ((1 << (nab_ + na_)) - 1)
                     kb = (k & ((1 << nab_) - 1)) | ((k >> (nab_ + na_)) << nab_)
                     assert int(fst["koff_a"][k]) == ka << int(st["a_cb"])

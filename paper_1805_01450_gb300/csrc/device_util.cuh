@@ -16,12 +16,23 @@ __device__ __forceinline__ uint32_t pext_runs(uint32_t c, const DevRun *runs, in
 
 
 // First stored entry of `leaf` restricted to this work item (bitstring x, outer slice o).
+// The leaf is read as five 8-byte words (data offset, fixed-mode count, the packed source
+// and position bytes) and the up to 12 fixed modes are applied without a loop-carried branch.
 __device__ __forceinline__ uint32_t leaf_base(const DevLeaf &L, uint64_t x, uint64_t o) {
-    uint32_t off = L.data_off;
-    for (uint32_t f = 0; f < L.n_fixed; f++) {
-        const uint32_t src = L.fixed_src[f];
-        const uint64_t bit = src < 64 ? (x >> src) & 1ull : (o >> (src - 64)) & 1ull;
-        off += (uint32_t)bit << L.fixed_pos[f];
+    static_assert(sizeof(DevLeaf) == 40 && kMaxFixed == 12, "DevLeaf layout");
+    const uint2 *w = reinterpret_cast<const uint2 *>(&L);
+    const uint2 w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3], w4 = w[4];
+    const uint32_t srcw[3] = {w2.x, w2.y, w3.x}, posw[3] = {w3.y, w4.x, w4.y};
+    const uint32_t nf = w1.x;
+    uint32_t off = w0.x;
+#pragma unroll
+    for (uint32_t f = 0; f < (uint32_t)kMaxFixed; f++) {
+        if (f < nf) {
+            const uint32_t src = (srcw[f >> 2] >> (8u * (f & 3u))) & 0xffu;
+            const uint32_t pos = (posw[f >> 2] >> (8u * (f & 3u))) & 0xffu;
+            const uint64_t v = src < 64u ? x : o;
+            off += (uint32_t)((v >> (src & 63u)) & 1ull) << pos;
+        }
     }
     return off;
 }

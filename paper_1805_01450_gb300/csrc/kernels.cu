@@ -309,11 +309,13 @@ constexpr uint32_t kWaitPolls = 1u << 20;
 
 // The work of one lane in one phase: its step, operand bases and entry stride.
 struct LaneWork {
-    FusedStep st;
+    const FusedStep *stp;          // the step (its summed-index tables, for nk >= 2)
     const float2 *A, *B;
     float2 *C;
     const uint32_t *tab;
     uint32_t sub, cnt;
+    uint32_t info;                 // bits 0-7: output rank, 8-15: summed modes, 16: one operand
+    uint32_t k1;                   // offsets of summed entry 1 in A (low 16 bits) and B (high)
     bool active;
 };
 
@@ -323,48 +325,46 @@ __device__ __forceinline__ LaneWork lane_work(uint32_t m, const FusedStep *steps
     LaneWork w;
     w.active = m != 0xffffffffu;
     if (!w.active) return w;
-    {   // four 16-byte shared-memory loads instead of field-by-field copies
-        const uint4 *src = reinterpret_cast<const uint4 *>(steps + (m & 0xfffu));
-        const uint4 v0 = src[0], v1 = src[1], v2 = src[2], v3 = src[3];
-        uint4 *dst = reinterpret_cast<uint4 *>(&w.st);
-        dst[0] = v0;
-        dst[1] = v1;
-        dst[2] = v2;
-        dst[3] = v3;
-    }
+    // 16-byte shared-memory loads of the fields used here; summed entry 0 is at offset 0 in
+    // both operands, entry 1's offsets ride along, the rest stay in the step
+    w.stp = steps + (m & 0xfffu);
+    const uint4 *src = reinterpret_cast<const uint4 *>(w.stp);
+    const uint4 v0 = src[0], v1 = src[1], v2 = src[2], v3 = src[3];
+    const uint32_t a_off = v0.x, b_off = v0.y, c_off = v0.z, tab_off = v0.w, flags = v1.x;
+    w.info = (v1.y & 0xffu) | (((v1.z >> 16) & 0xffu) << 8) | ((flags & kStepUnary) << 16);
+    w.k1 = (v2.x >> 16) | (v3.x & 0xffff0000u);
     w.sub = (m >> 12) & 0x3ffu;
     w.cnt = m >> 22;
-    const uint32_t flags = w.st.flags;
-    w.A = (flags & kStepALeaf) ? ldata + lbase[w.st.a_off] : arena + w.st.a_off;
-    w.B = (flags & kStepUnary) ? w.A : ((flags & kStepBLeaf) ? ldata + lbase[w.st.b_off] : arena + w.st.b_off);
-    w.C = arena + w.st.c_off;
-    w.tab = tabs + w.st.tab_off;
+    w.A = (flags & kStepALeaf) ? ldata + lbase[a_off] : arena + a_off;
+    w.B = (flags & kStepUnary) ? w.A : ((flags & kStepBLeaf) ? ldata + lbase[b_off] : arena + b_off);
+    w.C = arena + c_off;
+    w.tab = tabs + tab_off;
     return w;
 }
 
 // The lane's entries of its step, with the summed-index loop unrolled by case.
 __device__ __forceinline__ void run_lane_work(const LaneWork &w) {
-    const uint32_t n_out = 1u << w.st.rc;
-    const bool unary = w.st.flags & kStepUnary;
+    const uint32_t n_out = 1u << (w.info & 0xffu), nk = (w.info >> 8) & 0xffu;
+    const bool unary = (w.info >> 16) & 1u;
     const float2 *__restrict__ A = w.A;
     const float2 *__restrict__ B = w.B;
-    const uint32_t ka0 = w.st.koff_a[0], ka1 = w.st.koff_a[1], kb0 = w.st.koff_b[0], kb1 = w.st.koff_b[1];
+    const uint32_t ka1 = w.k1 & 0xffffu, kb1 = w.k1 >> 16;
     // two entries per iteration: independent loads and FMA chains overlap
-    if (!unary && w.st.nk == 0) {
+    if (!unary && nk == 0) {
         uint32_t c = w.sub;
         for (; c + w.cnt < n_out; c += 2 * w.cnt) {
             const uint32_t e0 = w.tab[c], e1 = w.tab[c + w.cnt];
-            const float2 a0 = A[(e0 & 0xffffu) + ka0], b0 = B[(e0 >> 16) + kb0];
-            const float2 a1 = A[(e1 & 0xffffu) + ka0], b1 = B[(e1 >> 16) + kb0];
+            const float2 a0 = A[e0 & 0xffffu], b0 = B[e0 >> 16];
+            const float2 a1 = A[e1 & 0xffffu], b1 = B[e1 >> 16];
             w.C[c] = make_float2(a0.x * b0.x - a0.y * b0.y, a0.x * b0.y + a0.y * b0.x);
             w.C[c + w.cnt] = make_float2(a1.x * b1.x - a1.y * b1.y, a1.x * b1.y + a1.y * b1.x);
         }
         if (c < n_out) {
             const uint32_t e = w.tab[c];
-            const float2 a = A[(e & 0xffffu) + ka0], b = B[(e >> 16) + kb0];
+            const float2 a = A[e & 0xffffu], b = B[e >> 16];
             w.C[c] = make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
         }
-    } else if (!unary && w.st.nk == 1) {
+    } else if (!unary && nk == 1) {
         uint32_t c = w.sub;
         for (; c + 3 * w.cnt < n_out; c += 4 * w.cnt) {   // four entries: loads of all issued first
             uint32_t e[4];
@@ -374,8 +374,8 @@ __device__ __forceinline__ void run_lane_work(const LaneWork &w) {
 #pragma unroll
             for (int u = 0; u < 4; u++) {
                 const uint32_t ia = e[u] & 0xffffu, ib = e[u] >> 16;
-                p[u] = A[ia + ka0];
-                q[u] = B[ib + kb0];
+                p[u] = A[ia];
+                q[u] = B[ib];
                 r[u] = A[ia + ka1];
                 t[u] = B[ib + kb1];
             }
@@ -390,8 +390,8 @@ __device__ __forceinline__ void run_lane_work(const LaneWork &w) {
         for (; c + w.cnt < n_out; c += 2 * w.cnt) {
             const uint32_t e0 = w.tab[c], e1 = w.tab[c + w.cnt];
             const uint32_t ia0 = e0 & 0xffffu, ib0 = e0 >> 16, ia1 = e1 & 0xffffu, ib1 = e1 >> 16;
-            const float2 p0 = A[ia0 + ka0], q0 = B[ib0 + kb0], p1 = A[ia0 + ka1], q1 = B[ib0 + kb1];
-            const float2 r0 = A[ia1 + ka0], s0 = B[ib1 + kb0], r1 = A[ia1 + ka1], s1 = B[ib1 + kb1];
+            const float2 p0 = A[ia0], q0 = B[ib0], p1 = A[ia0 + ka1], q1 = B[ib0 + kb1];
+            const float2 r0 = A[ia1], s0 = B[ib1], r1 = A[ia1 + ka1], s1 = B[ib1 + kb1];
             float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
             cmac(acc0, p0, q0);
             cmac(acc1, r0, s0);
@@ -402,18 +402,18 @@ __device__ __forceinline__ void run_lane_work(const LaneWork &w) {
         }
         if (c < n_out) {
             const uint32_t e = w.tab[c], ia = e & 0xffffu, ib = e >> 16;
-            const float2 a0 = A[ia + ka0], b0 = B[ib + kb0], a1 = A[ia + ka1], b1 = B[ib + kb1];
+            const float2 a0 = A[ia], b0 = B[ib], a1 = A[ia + ka1], b1 = B[ib + kb1];
             float2 acc = make_float2(0.f, 0.f);
             cmac(acc, a0, b0);
             cmac(acc, a1, b1);
             w.C[c] = acc;
         }
-    } else if (!unary && w.st.nk == 2) {
-        lane_entries_k<2>(w.st, w.sub, w.cnt, n_out, w.tab, A, B, w.C);
-    } else if (!unary && w.st.nk == 3) {
-        lane_entries_k<3>(w.st, w.sub, w.cnt, n_out, w.tab, A, B, w.C);
+    } else if (!unary && nk == 2) {
+        lane_entries_k<2>(*w.stp, w.sub, w.cnt, n_out, w.tab, A, B, w.C);
+    } else if (!unary && nk == 3) {
+        lane_entries_k<3>(*w.stp, w.sub, w.cnt, n_out, w.tab, A, B, w.C);
     } else {
-        for (uint32_t c = w.sub; c < n_out; c += w.cnt) w.C[c] = fused_entry(w.st, w.tab[c], A, B, unary);
+        for (uint32_t c = w.sub; c < n_out; c += w.cnt) w.C[c] = fused_entry(*w.stp, w.tab[c], A, B, unary);
     }
 }
 
@@ -428,15 +428,14 @@ __global__ void __launch_bounds__(512) fused_program_kernel(LaunchArgs a, int wa
     __shared__ __align__(8) uint64_t stage_bar;
     const unsigned char *img = a.image;
     const DevProgram *P = reinterpret_cast<const DevProgram *>(img);
-    const uint64_t steps_off = P->fused_steps_off, tab_off = P->fused_tab_off, map_off = P->fused_lane_map_off;
-    const uint32_t n_phases = P->n_fused_phases, n_leaves = P->n_leaves;
-    const uint64_t final_off = P->final_off;
-    const FinishInfo fin = finish_info(P);
-    const DevLeaf *leaves = reinterpret_cast<const DevLeaf *>(img + P->leaves_off);
+    const uint64_t steps_off = a.fused_steps_off, tab_off = a.fused_tab_off, map_off = a.fused_lane_map_off;
+    const uint32_t n_phases = a.n_fused_phases, n_leaves = a.n_leaves;
+    const uint64_t final_off = a.final_off;
+    const DevLeaf *leaves = reinterpret_cast<const DevLeaf *>(img + a.leaves_off);
     const FusedStep *steps = reinterpret_cast<const FusedStep *>(img + steps_off);
     const uint32_t *tabs = reinterpret_cast<const uint32_t *>(img + tab_off);
     const uint32_t *lane_map = reinterpret_cast<const uint32_t *>(img + map_off);
-    const float2 *ldata = reinterpret_cast<const float2 *>(img + P->leaf_data_off);
+    const float2 *ldata = reinterpret_cast<const float2 *>(img + a.leaf_data_off);
     unsigned char *cur = smem;
     // the first item's bitstring is read while the program is being staged
     const int groups0 = blockDim.x / (32 * warps_per_item);
@@ -470,6 +469,7 @@ __global__ void __launch_bounds__(512) fused_program_kernel(LaunchArgs a, int wa
     } else {
         __syncthreads();
     }
+    const FinishInfo fin = finish_info(P);
     const int lanes = 32 * warps_per_item;
     const int group = threadIdx.x / lanes;
     const int lane = threadIdx.x % lanes;
@@ -1259,6 +1259,14 @@ bool fused_shape(const DevProgram *h, uint64_t arena_elems, int warps_per_item, 
     a->smem_leaves_bytes = sh ? (uint32_t)leaves_b : 0;
     a->leaf_table_bytes = (uint32_t)r16((size_t)h->n_leaves * 4);
     a->group_bytes = (uint32_t)*group;
+    a->fused_steps_off = h->fused_steps_off;
+    a->fused_tab_off = h->fused_tab_off;
+    a->fused_lane_map_off = h->fused_lane_map_off;
+    a->leaves_off = h->leaves_off;
+    a->leaf_data_off = h->leaf_data_off;
+    a->final_off = h->final_off;
+    a->n_fused_phases = h->n_fused_phases;
+    a->n_leaves = h->n_leaves;
     *shared = sh;
     *max_ipc = (int)std::max<size_t>(1, std::min<size_t>(std::max(1, 8 / warps_per_item), (kBudget - sh) / *group));
     return true;

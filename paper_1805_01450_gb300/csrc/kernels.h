@@ -34,6 +34,10 @@ struct LaunchArgs {
     uint32_t smem_leaves_bytes;
     uint32_t leaf_table_bytes;      // per group, 16-byte multiple
     uint32_t group_bytes;           // per group: leaf table + arena
+    // fused engine: the image header fields it needs before staging (passed as arguments so
+    // the copies start without a round trip to the header in device memory)
+    uint64_t fused_steps_off, fused_tab_off, fused_lane_map_off, leaves_off, leaf_data_off, final_off;
+    uint32_t n_fused_phases, n_leaves;
 };
 
 // Fused engine: one warp group per work item, every tensor in shared memory. When

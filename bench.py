@@ -42,9 +42,10 @@ MEM_BUDGET_MB = {"grid7x7d30-b1024": 32768, "grid8x8d40": 65536}
 DEFAULT_WORKLOAD = "grid6x6d25-k12"
 METRIC = "amplitudes/s and complex TFLOP/s (% of GB300 peak) at |Δα|≤1e-5·2^-N/2 vs FP64"
 L2_FLUSH_BYTES = 256 << 20
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the fused kernel, from one ncu
-# capture of this workload with the current kernel (profiles/ holds the summary).
-NCU_TRAFFIC = {("grid6x6d25-k12", 1): 140800.0}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel (fused
+# program kernel; gradient kernel for the gradient workload), from one ncu capture of the
+# workload with the current kernels (profiles/ holds the summaries).
+NCU_TRAFFIC = {("grid6x6d25-k12", 1): 147968.0, ("rot5x5d20-grad", 1): 481536.0}
 
 
 def parse():

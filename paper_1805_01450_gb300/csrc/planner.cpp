@@ -1404,9 +1404,18 @@ bool serialize(Plan &p, std::string *err) {
                 if (best < 0) break;
                 cnt[best]++;
             }
+            // lanes of steps of the same kind (summed entries, one or two operands) are
+            // adjacent, so fewer warps mix the kernel's per-kind code paths
+            std::vector<int> by_kind(n);
+            std::iota(by_kind.begin(), by_kind.end(), 0);
+            auto kind = [&](int i) {
+                const DevStep &d = ds[b0 + i];
+                return ((d.flags & kStepUnary) ? 16 : 0) + d.nk_ab + d.nk_a + d.nk_b;
+            };
+            std::stable_sort(by_kind.begin(), by_kind.end(), [&](int x, int y) { return kind(x) < kind(y); });
             std::vector<uint32_t> row(lanes, 0xffffffffu);
             int lane = 0;
-            for (int i = 0; i < n; i++)
+            for (int i : by_kind)
                 for (int j = 0; j < cnt[i]; j++, lane++)
                     row[lane] = (uint32_t)(b0 + i) | ((uint32_t)j << 12) | ((uint32_t)cnt[i] << 22);
             lane_map.insert(lane_map.end(), row.begin(), row.end());

@@ -140,6 +140,9 @@ typedef struct {
     int32_t n_gemm_steps;            /* contractions run on the tensor cores (opts.tensor_cores) */
     int32_t grad_smem_bytes;         /* shared memory per work item of the gradient kernel's on-chip
                                         form (0: absent; larger than the device allows: global memory) */
+    int32_t grad_recomputed;         /* gradient plans: forward contractions recomputed in the
+                                        backward pass because one work item's gradient arena would
+                                        exceed opts.mem_budget_bytes with every forward value kept */
 } qvx_plan_info;
 
 typedef struct qvx_plan qvx_plan;

@@ -60,7 +60,7 @@ class PlanInfo(ctypes.Structure):
                 ("grad_flops_per_amplitude", ctypes.c_double), ("grad_bytes_per_amplitude", ctypes.c_double),
                 ("n_tiled_steps", ctypes.c_int32), ("n_phases", ctypes.c_int32),
                 ("n_open_qubits", ctypes.c_int32), ("n_gemm_steps", ctypes.c_int32),
-                ("grad_smem_bytes", ctypes.c_int32)]
+                ("grad_smem_bytes", ctypes.c_int32), ("grad_recomputed", ctypes.c_int32)]
 
 
 _lib = None

@@ -342,6 +342,7 @@ qvx_status qvx_plan_get_info(const qvx_plan *plan, qvx_plan_info *info) {
     info->n_open_qubits = (int32_t)p.open_qubits.size();
     info->n_gemm_steps = 0;
     for (const qvx::GemmStep &g : p.gemm) info->n_gemm_steps += g.nk > 0 ? 1 : 0;
+    info->grad_recomputed = p.grad_recomputed;
     info->grad_smem_bytes = p.opts.gradient
         ? (int32_t)qvx::grad_smem_bytes(reinterpret_cast<const qvx::DevProgram *>(p.image.data())) : 0;
     info->grad_bytes_per_amplitude = p.grad_bytes_per_item * (double)info->n_items_per_bitstring;

@@ -82,6 +82,7 @@ struct Plan {
     double grad_flops_per_item = 0, grad_bytes_per_item = 0;
     std::vector<uint32_t> grad_phase_first;    // phases of independent gradient steps (+ end)
     std::vector<uint32_t> grad_elem_off;       // per gradient step: first entry inside its phase
+    int grad_recomputed = 0;                   // forward steps recomputed in the backward pass
 };
 
 // planner.cpp

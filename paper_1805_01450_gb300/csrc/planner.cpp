@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <numeric>
 #include <unordered_map>
 
@@ -916,7 +917,11 @@ int64_t place_by_phases(const std::vector<int64_t> &size, const std::vector<int>
     return peak;
 }
 
-bool build_grad_program(Plan &p, const std::vector<int> &dev_leaf, std::string *err) {
+// keep[t] = 0: the forward value of tensor t is not kept for the backward pass; each
+// backward level that reads it recomputes it (and, first, any operand of it that is not kept
+// either) in phases of its own just before the level's adjoint steps (checkpointing: the
+// kept tensors are the checkpoints).
+bool build_grad_program(Plan &p, const std::vector<int> &dev_leaf, const std::vector<char> &keep, std::string *err) {
     const size_t nt = p.tensors.size();
     std::vector<char> need(nt, 0);
     for (size_t t = 0; t < nt; t++) {
@@ -935,15 +940,18 @@ bool build_grad_program(Plan &p, const std::vector<int> &dev_leaf, std::string *
         if (p.tensors[t].leaf >= 0) pl.push_back((int)t);
     }
     const int64_t gslot = (int64_t)(2 * nt);
+    int64_t next_id = gslot + 1;    // recomputed forward values get ids from here on
+    std::vector<int64_t> rsize;     // their sizes (entries), by id - next_id's start
     std::vector<int64_t> out_rel;   // per gradient step: entry offset inside its output tensor
     p.grad_steps.clear();
+    std::vector<int64_t> cur_fwd = fo;   // where a forward value is read from right now
     auto operand = [&](GenOperand &o, int t, bool adj, const std::vector<int> &out, const std::vector<int> &S) {
         std::memset(&o, 0, sizeof(o));
         if (t < 0) { o.kind = kOpOne; return true; }
         const PTensor &T = p.tensors[t];
         if (adj) { o.kind = kOpArena; o.off = (uint64_t)ao[t]; }
         else if (T.leaf >= 0) { o.kind = kOpLeaf; o.off = (uint64_t)dev_leaf[T.leaf]; }
-        else { o.kind = kOpArena; o.off = (uint64_t)fo[t]; }
+        else { o.kind = kOpArena; o.off = (uint64_t)cur_fwd[t]; }
         return map_runs(out, T.modes, o.oruns, &o.n_oruns) && map_runs(S, T.modes, o.kruns, &o.n_kruns);
     };
     p.grad_flops_per_item = 0;
@@ -990,24 +998,68 @@ bool build_grad_program(Plan &p, const std::vector<int> &dev_leaf, std::string *
     }
     // backward, level by level from the last: the adjoints of a level's operands depend only
     // on adjoints of later levels
-    std::vector<int> level_of(p.steps.size(), 0);
-    for (size_t l = 0; l < p.phases.size(); l++)
-        for (int s = p.phases[l].first; s < p.phases[l].second; s++) level_of[s] = (int)l;
-    for (int s = (int)p.steps.size() - 1; s >= 0; s--) {
-        if (s == (int)p.steps.size() - 1 || level_of[s] != level_of[s + 1])
+    auto summed_of = [](const PStep &st) {
+        std::vector<int> S = st.k_ab;
+        S.insert(S.end(), st.k_a.begin(), st.k_a.end());
+        S.insert(S.end(), st.k_b.begin(), st.k_b.end());
+        return S;
+    };
+    auto dropped = [&](int t) { return t >= 0 && p.tensors[t].leaf < 0 && !keep[t]; };
+    p.grad_recomputed = 0;
+    for (int l = (int)p.phases.size() - 1; l >= 0; l--) {
+        // forward values this level reads that were not kept, with the not-kept operands they
+        // are recomputed from, by depth (depth 0: computed from kept values and leaves only)
+        std::vector<int> depth(nt, -1), order;
+        std::function<int(int)> visit = [&](int t) -> int {
+            if (depth[t] >= 0) return depth[t];
+            const PStep &pr = p.steps[p.tensors[t].producer];
+            int d = 0;
+            for (int u : {pr.a, pr.b})
+                if (dropped(u)) d = std::max(d, visit(u) + 1);
+            depth[t] = d;
+            order.push_back(t);
+            return d;
+        };
+        for (int s = p.phases[l].second - 1; s >= p.phases[l].first; s--) {
+            const PStep &st = p.steps[s];
+            if (!need[st.c]) continue;
+            if (need[st.a] && dropped(st.b)) visit(st.b);
+            if (st.b >= 0 && need[st.b] && dropped(st.a)) visit(st.a);
+        }
+        int max_depth = -1;
+        for (int t : order) max_depth = std::max(max_depth, depth[t]);
+        for (int t : order) {
+            cur_fwd[t] = next_id++;
+            rsize.push_back(int64_t(1) << p.tensors[t].modes.size());
+        }
+        for (int d = 0; d <= max_depth; d++) {
             p.grad_phase_first.push_back((uint32_t)p.grad_steps.size());
-        const PStep &st = p.steps[s];
-        if (!need[st.c]) continue;
-        const std::vector<int> &LC = p.tensors[st.c].modes, &LA = p.tensors[st.a].modes;
-        if (need[st.a]) {
-            const std::vector<int> none;
-            const std::vector<int> &LB = st.b >= 0 ? p.tensors[st.b].modes : none;
-            if (!emit(ao[st.a], LA, st.c, true, st.b, false, minus(LC, LB, LA))) { *err = runs_err; return false; }
+            for (int t : order) {
+                if (depth[t] != d) continue;
+                const PStep &pr = p.steps[p.tensors[t].producer];
+                if (!emit(cur_fwd[t], p.tensors[t].modes, pr.a, false, pr.b, false, summed_of(pr))) {
+                    *err = runs_err;
+                    return false;
+                }
+                p.grad_recomputed++;
+            }
         }
-        if (st.b >= 0 && need[st.b]) {
-            const std::vector<int> &LB = p.tensors[st.b].modes;
-            if (!emit(ao[st.b], LB, st.c, true, st.a, false, minus(LC, LA, LB))) { *err = runs_err; return false; }
+        p.grad_phase_first.push_back((uint32_t)p.grad_steps.size());
+        for (int s = p.phases[l].second - 1; s >= p.phases[l].first; s--) {
+            const PStep &st = p.steps[s];
+            if (!need[st.c]) continue;
+            const std::vector<int> &LC = p.tensors[st.c].modes, &LA = p.tensors[st.a].modes;
+            if (need[st.a]) {
+                const std::vector<int> none;
+                const std::vector<int> &LB = st.b >= 0 ? p.tensors[st.b].modes : none;
+                if (!emit(ao[st.a], LA, st.c, true, st.b, false, minus(LC, LB, LA))) { *err = runs_err; return false; }
+            }
+            if (st.b >= 0 && need[st.b]) {
+                const std::vector<int> &LB = p.tensors[st.b].modes;
+                if (!emit(ao[st.b], LB, st.c, true, st.a, false, minus(LC, LA, LB))) { *err = runs_err; return false; }
+            }
         }
+        for (int t : order) cur_fwd[t] = fo[t];
     }
     p.grad_param_leaves.clear();
     p.grad_phase_first.push_back((uint32_t)p.grad_steps.size());   // the dot products
@@ -1048,11 +1100,12 @@ bool build_grad_program(Plan &p, const std::vector<int> &dev_leaf, std::string *
     }
     // lifetimes of the arena tensors in phases, then their places
     const int n_ph = (int)firsts.size() - 1;
-    const size_t n_ids = 2 * nt + 1;
+    const size_t n_ids = (size_t)next_id;
     std::vector<int64_t> size(n_ids, 0);
     std::vector<int> birth(n_ids, -1), death(n_ids, -1);
     for (size_t t = 0; t < nt; t++) size[t] = size[nt + t] = int64_t(1) << p.tensors[t].modes.size();
     size[gslot] = std::max<int64_t>((int64_t)pl.size(), 1);
+    for (size_t i = 0; i < rsize.size(); i++) size[gslot + 1 + i] = rsize[i];
     for (int ph = 0; ph < n_ph; ph++)
         for (uint32_t gi = firsts[ph]; gi < firsts[ph + 1]; gi++) {
             const GenStep &g = p.grad_steps[gi];
@@ -1480,7 +1533,31 @@ bool serialize(Plan &p, std::string *err) {
     std::vector<GradEntry> gent;
     std::vector<uint32_t> gktab, gphase;
     if (p.opts.gradient) {
-        if (!build_grad_program(p, dev_leaf, err)) return false;
+        // checkpointing: while one work item's gradient arena exceeds the memory budget, forward
+        // values are recomputed in the backward pass instead of kept, largest first; a value
+        // stays dropped only if that lowers the arena (at most 48 trial programs)
+        std::vector<char> keep(p.tensors.size(), 1);
+        if (!build_grad_program(p, dev_leaf, keep, err)) return false;
+        if (p.grad_arena_elems * 8 > p.opts.mem_budget_bytes) {
+            std::vector<int> cand;
+            for (const PStep &st : p.steps)
+                for (int t : {st.a, st.b})
+                    if (t >= 0 && t != p.final_tensor && p.tensors[t].leaf < 0) cand.push_back(t);
+            std::stable_sort(cand.begin(), cand.end(), [&](int x, int y) {
+                return p.tensors[x].modes.size() > p.tensors[y].modes.size();
+            });
+            int64_t best = p.grad_arena_elems;
+            int trials = 0;
+            for (int t : cand) {
+                if (best * 8 <= p.opts.mem_budget_bytes || trials >= 48) break;
+                keep[t] = 0;
+                trials++;
+                if (!build_grad_program(p, dev_leaf, keep, err)) return false;
+                if (p.grad_arena_elems < best) best = p.grad_arena_elems;
+                else keep[t] = 1;
+            }
+            if (!build_grad_program(p, dev_leaf, keep, err)) return false;
+        }
         // parametrised leaves in the order of the derivative slots
         std::vector<ParamLeaf> ordered;
         for (int l : p.grad_param_leaves) ordered.push_back(pls[pleaf_of_leaf[l]]);

@@ -38,6 +38,24 @@ def test_rotation_3x4_all_angles_vs_adjoint_oracle(kw):
         assert np.max(np.abs(g[i] - g_ref)) < tol(12)
 
 
+def test_gradient_checkpointing_on_device():
+    # a memory budget of half one work item's gradient arena: forward values are recomputed in
+    # the backward pass; gradients as the state-vector adjoint and as the plan that keeps all
+    c = cg.rotation_circuit(4, 4, 16, 9)
+    full = q.Plan(c, gradient=True, n_slices=0)
+    small = q.Plan(c, gradient=True, n_slices=0, order=full.order,
+                   mem_budget_bytes=full.info["grad_arena_bytes"] // 2)
+    assert small.info["grad_recomputed"] > 0
+    xs = cg.random_bitstrings(16, 3, 11)
+    a, g = (t.cpu().numpy() for t in small.amplitude_grad(xs))
+    a_full, g_full = (t.cpu().numpy() for t in full.amplitude_grad(xs))
+    assert np.max(np.abs(g - g_full)) < tol(16) and np.max(np.abs(a - a_full)) < tol(16)
+    for i, x in enumerate(xs):
+        a_ref, g_ref = SV.sv_adjoint_grad(c, x)
+        assert abs(a[i] - a_ref) < tol(16)
+        assert np.max(np.abs(g[i] - g_ref)) < tol(16)
+
+
 def test_thetas_override_and_repeat():
     c = cg.rotation_circuit(3, 3, 6, 43)
     p = q.Plan(c, gradient=True, n_slices=2)

@@ -233,6 +233,30 @@ def test_gradient_program_on_host_matches_oracle(name, maker, kw):
     assert abs(a - a_ref) < 1e-6 and np.max(np.abs(g - g_ref)) < 1e-6
 
 
+def test_gradient_checkpointing_on_host():
+    # rotation circuit 4x4, depth 16: with a memory budget below one work item's gradient
+    # arena, forward values are recomputed in the backward pass instead of kept
+    # (checkpointing); the arena shrinks and the gradients still match the state-vector adjoint
+    from _program_exec import grad, check_grad_schedule
+    c = cg.rotation_circuit(4, 4, 16, 9)
+    full = q.Plan(c, gradient=True, n_slices=0)
+    small = q.Plan(c, gradient=True, n_slices=0, order=full.order,
+                   mem_budget_bytes=full.info["grad_arena_bytes"] // 2)
+    assert full.info["grad_recomputed"] == 0
+    assert small.info["grad_recomputed"] > 0
+    assert small.info["grad_arena_bytes"] < full.info["grad_arena_bytes"]
+    assert small.info["n_grad_steps"] == full.info["n_grad_steps"] + small.info["grad_recomputed"]
+    prog = Program(small.image())
+    check_grad_schedule(prog)
+    for x in cg.random_bitstrings(16, 2, 10):
+        a_ref, g_ref = SV.sv_adjoint_grad(c, x)
+        a, g = grad(prog, x)
+        assert abs(a - a_ref) < 1e-6 * 2 ** -8
+        assert np.max(np.abs(g - g_ref)) < 1e-6 * 2 ** -8
+        a_t, g_t = grad(prog, x, tables=True)
+        assert abs(a_t - a) < 1e-14 and np.max(np.abs(g_t - g)) < 1e-14
+
+
 @pytest.mark.parametrize("inner,wpi,merge", [(0, 1, 8), (3, 2, 10), (5, 4, 10), (5, 4, 0), (5, 8, 10), (6, 16, 10)])
 def test_fused_schedule_6x6x25(inner, wpi, merge):
     c = cg.grid_circuit(6, 6, 25, 2001)

@@ -58,7 +58,9 @@ def test_4x4x10_batch(engine, wpi):
                                                     (2, 2, "fused", 8), (6, 4, "fused", 8),
                                                     (3, 1, "stepwise", 8), (4, 1, "fused", 0),
                                                     (2, 1, "stepwise", 0), (4, 1, "persistent", 8),
-                                                    (0, 1, "persistent", 0)])
+                                                    (0, 1, "persistent", 0),
+                                                    # the bench's autotuned launch configurations
+                                                    (5, 8, "fused", 10), (5, 8, "fused", 8)])
 def test_6x6x25_k12_full(inner, wpi, engine, merge):
     c = cg.grid_circuit(6, 6, 25, 2001)
     x = cg.random_bitstrings(36, 1, 2002)[0]

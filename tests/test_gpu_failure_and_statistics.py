@@ -43,10 +43,11 @@ def test_bounded_waits_time_out_and_report():
     assert np.max(np.abs(p.amplitude(xs, workspace=ws).cpu().numpy() - psi[xs])) < 1e-5 * 2 ** -8
 
 
-def test_7x7x30_1024_bitstrings_porter_thomas_and_samples():
+@pytest.mark.parametrize("k", [8, 4])   # 4 sliced, all open: the bench's autotuned configuration
+def test_7x7x30_1024_bitstrings_porter_thomas_and_samples(k):
     c = cg.grid_circuit(7, 7, 30, 3001)
     xs = cg.random_bitstrings(49, 1024, 3002)
-    p = q.Plan(c, n_slices=8, inner_slices=4, engine="stepwise")
+    p = q.Plan(c, n_slices=k, inner_slices=4, engine="stepwise", mem_budget_bytes=32 << 30)
     amps = p.amplitude(xs).cpu().numpy()
     pt = (2.0 ** 49) * np.abs(amps) ** 2
     assert abs(pt.mean() - 1.0) < 0.15

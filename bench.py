@@ -236,7 +236,10 @@ def main():
         tune = dict(TUNE.get(args.workload, {})) if args.sliced is None else {}
         plan, tuning = autotune(circ, bits_host, n_slices=k, device=dev, mem_budget_bytes=budget, **tune)
     else:
-        plan = q.Plan(circ, n_slices=k, inner_slices=-1 if args.inner_slices is None else args.inner_slices,
+        # gradient workload: one sliced variable open inside a work item (128 items, each on a
+        # CTA of the staged shared-memory kernel at once)
+        inner = args.inner_slices if args.inner_slices is not None else (1 if grad else -1)
+        plan = q.Plan(circ, n_slices=k, inner_slices=inner,
                       warps_per_item=args.warps_per_item or 1, engine=args.engine, gradient=grad,
                       mem_budget_bytes=budget, tensor_cores=args.tensor_cores)
     info = plan.info

@@ -511,7 +511,10 @@ qvx_status qvx_amplitude_grad(qvx_plan *plan, const uint64_t *bitstrings_dev, in
     g.slots = w.grad_slots;
     g.partials = reinterpret_cast<qvx::ExactPair *>(base + w.partials);
     g.gpart = reinterpret_cast<qvx::ExactPair *>(base + w.grad_partials);
+    g.status = reinterpret_cast<unsigned int *>(base + w.status);
     const size_t gsm = qvx::grad_smem_bytes(h);
+    qvx::GradArgs staged_args = g;
+    const size_t gsm_staged = gsm ? gsm + qvx::grad_stage_bytes(h, &staged_args) : 0;
     if (gsm) {
         int dev = -1;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -520,11 +523,18 @@ qvx_status qvx_amplitude_grad(qvx_plan *plan, const uint64_t *bitstrings_dev, in
             qvx_status s = device_caps(&caps);
             if (s != QVX_OK) return s;
             plan->grad_sms = caps.sms;
-            plan->grad_ctas_per_sm = qvx::grad_smem_blocks_per_sm(gsm);
+            plan->grad_ctas_per_sm = qvx::grad_smem_blocks_per_sm(gsm, false);
+            plan->grad_staged_ctas_per_sm = qvx::grad_smem_blocks_per_sm(gsm_staged, true);
             plan->grad_device = dev;
         }
     }
-    if (gsm && plan->grad_ctas_per_sm > 0) {
+    // the staged form (leaf data and tables on chip too) when every work item still gets its
+    // own CTA at once; it holds more shared memory, so fewer CTAs fit on an SM
+    const int64_t n_items = batch * n_outer;
+    if (gsm && plan->grad_staged_ctas_per_sm > 0 && n_items <= (int64_t)plan->grad_sms * plan->grad_staged_ctas_per_sm) {
+        if ((e = qvx::launch_grad_smem(staged_args, (int)n_items, gsm_staged, st)) != cudaSuccess)
+            return cuda_fail(e, "gradient kernel launch");
+    } else if (gsm && plan->grad_ctas_per_sm > 0) {
         const int grid = (int)std::min<int64_t>(batch * n_outer, (int64_t)plan->grad_sms * plan->grad_ctas_per_sm);
         if ((e = qvx::launch_grad_smem(g, grid, gsm, st)) != cudaSuccess) return cuda_fail(e, "gradient kernel launch");
     } else {

@@ -1006,8 +1006,13 @@ constexpr int kGradPrefetch = 4;   // records per thread loaded one phase ahead
 // The gradient program with the work item's arena in shared memory: the records of each
 // level phase are spread over the CTA's threads, one barrier per phase, and each thread
 // loads its first record of the next phase before the barrier of the current one.
+// STAGED: the leaf data, the derivative data and the summed-index table are first copied
+// into shared memory (after the arena and the leaf table) by bulk asynchronous copies on one
+// mbarrier with a bounded wait, so the operand reads of every phase stay on chip.
+template <bool STAGED>
 __global__ void __launch_bounds__(256) grad_smem_kernel(GradArgs g) {
     extern __shared__ float4 gsm[];
+    __shared__ __align__(8) uint64_t stage_bar;
     const unsigned char *img = g.image;
     const DevProgram *P = reinterpret_cast<const DevProgram *>(img);
     float2 *arena = reinterpret_cast<float2 *>(gsm);
@@ -1019,6 +1024,32 @@ __global__ void __launch_bounds__(256) grad_smem_kernel(GradArgs g) {
     const float2 *ldata = reinterpret_cast<const float2 *>(img + P->leaf_data_off);
     const float2 *ddata = reinterpret_cast<const float2 *>(img + P->deriv_data_off);
     const uint32_t n_phases = P->n_grad_phases, n_leaves = P->n_leaves, npl = P->n_param_leaves;
+    if (STAGED) {
+        const size_t head = ((size_t)P->grad_arena_elems * 8 + (size_t)n_leaves * 4 + 15) & ~size_t(15);
+        unsigned char *st = reinterpret_cast<unsigned char *>(gsm) + head;
+        const uint32_t bar = smem_u32(&stage_bar);
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                         "r"(g.stage_ldata + g.stage_ddata + g.stage_ktab)
+                         : "memory");
+            bulk_g2s(smem_u32(st), ldata, g.stage_ldata, bar);
+            bulk_g2s(smem_u32(st + g.stage_ldata), ddata, g.stage_ddata, bar);
+            if (g.stage_ktab) bulk_g2s(smem_u32(st + g.stage_ldata + g.stage_ddata), ktab, g.stage_ktab, bar);
+        }
+        __syncthreads();
+        const bool ok = mbar_wait(bar, 0, kWaitPolls);
+        if (__syncthreads_or(!ok)) {          // the copy never completed: report and leave
+            if (threadIdx.x == 0) atomicCAS(g.status, 0u, 4u /* QVX_ETIMEOUT */);
+            mbar_wait(bar, 0, kWaitPolls);
+            return;
+        }
+        ldata = reinterpret_cast<const float2 *>(st);
+        ddata = reinterpret_cast<const float2 *>(st + g.stage_ldata);
+        ktab = reinterpret_cast<const uint32_t *>(st + g.stage_ldata + g.stage_ddata);
+    }
     const int64_t n_items = g.batch * g.o_count;
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int64_t b = item / g.o_count;
@@ -1181,19 +1212,34 @@ size_t grad_smem_bytes(const DevProgram *h) {
     return ((size_t)h->grad_arena_elems * 8 + (size_t)h->n_leaves * 4 + 15) & ~size_t(15);
 }
 
-int grad_smem_blocks_per_sm(size_t smem_bytes) {
+size_t grad_stage_bytes(const DevProgram *h, GradArgs *g) {
+    auto r16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+    const size_t ld = r16((size_t)h->n_leaf_entries * 8);
+    const size_t kt = h->gphase_entry_off > h->gktab_off ? r16(h->gphase_entry_off - h->gktab_off) : 0;
+    g->stage_ldata = (uint32_t)ld;
+    g->stage_ddata = (uint32_t)ld;
+    g->stage_ktab = (uint32_t)kt;
+    return 2 * ld + kt;
+}
+
+int grad_smem_blocks_per_sm(size_t smem_bytes, bool staged) {
     static bool raised[64] = {false};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (dev >= 0 && dev < 64 && !raised[dev]) {
         int optin = 0;
         if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
-        if (cudaFuncSetAttribute(grad_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess)
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, grad_smem_kernel<true>) != cudaSuccess) return 0;
+        const int limit = optin - (int)fa.sharedSizeBytes;
+        if (cudaFuncSetAttribute(grad_smem_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess ||
+            cudaFuncSetAttribute(grad_smem_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess)
             return 0;
         raised[dev] = true;
     }
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, grad_smem_kernel, 256, smem_bytes) != cudaSuccess) {
+    if ((staged ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, grad_smem_kernel<true>, 256, smem_bytes)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, grad_smem_kernel<false>, 256, smem_bytes)) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -1201,7 +1247,8 @@ int grad_smem_blocks_per_sm(size_t smem_bytes) {
 }
 
 cudaError_t launch_grad_smem(const GradArgs &g, int grid, size_t smem_bytes, cudaStream_t s) {
-    grad_smem_kernel<<<grid, 256, smem_bytes, s>>>(g);
+    if (g.stage_ldata) grad_smem_kernel<true><<<grid, 256, smem_bytes, s>>>(g);
+    else grad_smem_kernel<false><<<grid, 256, smem_bytes, s>>>(g);
     return counted(cudaGetLastError());
 }
 

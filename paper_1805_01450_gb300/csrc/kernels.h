@@ -89,6 +89,11 @@ struct GradArgs {
     int64_t slots;
     ExactPair *partials;            // batch * o_count amplitude partials
     ExactPair *gpart;               // batch * o_count * n_param_leaves derivative partials
+    unsigned int *status;           // device status word
+    // staged form of the shared-memory kernel: bytes of the leaf data, derivative data and
+    // summed-index table copied into shared memory after the arena and leaf table (0: read
+    // from the image in device memory)
+    uint32_t stage_ldata, stage_ddata, stage_ktab;
 };
 // Rewrites the parametrised leaves (U and dU/dtheta) from thetas (device, or the image's own).
 cudaError_t launch_set_params(unsigned char *image, uint32_t n_param_leaves, const double *thetas, cudaStream_t s);
@@ -97,7 +102,10 @@ cudaError_t launch_grad_program(const GradArgs &g, int grid, cudaStream_t s);
 // the bytes a CTA needs (0 if the plan has no records), how many CTAs fit on an SM (0: none;
 // raises the kernel's shared-memory limit once per device), and the launch.
 size_t grad_smem_bytes(const DevProgram *h);
-int grad_smem_blocks_per_sm(size_t smem_bytes);
+// Bytes the staged form adds (leaf data, derivative data and summed-index table, each rounded
+// to 16), and the matching GradArgs fields.
+size_t grad_stage_bytes(const DevProgram *h, GradArgs *g);
+int grad_smem_blocks_per_sm(size_t smem_bytes, bool staged);
 cudaError_t launch_grad_smem(const GradArgs &g, int grid, size_t smem_bytes, cudaStream_t s);
 // d alpha / d theta_p = exact sum over work items and the parameter's leaves.
 cudaError_t launch_grad_sum(const unsigned char *image, const ExactPair *gpart, int64_t batch, int64_t o_count,

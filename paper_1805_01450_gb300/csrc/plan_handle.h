@@ -10,6 +10,7 @@ struct qvx_plan {
     int ctas_per_sm[9] = {0};   // by work items per CTA
     // persistent-engine grid, cached for the device it was computed on
     int persist_device = -1, persist_grid = 0;
-    // shared-memory gradient kernel: CTAs per SM (0: the global-memory kernel runs) and SMs
-    int grad_device = -1, grad_ctas_per_sm = 0, grad_sms = 0;
+    // shared-memory gradient kernel: CTAs per SM (0: the global-memory kernel runs), CTAs per
+    // SM of its staged form (leaf data and tables in shared memory too; 0: does not fit), SMs
+    int grad_device = -1, grad_ctas_per_sm = 0, grad_staged_ctas_per_sm = 0, grad_sms = 0;
 };

@@ -95,15 +95,20 @@ def test_5x5x20_rotation_circuit_finite_differences():
 
 def test_shared_memory_and_global_gradient_kernels_agree():
     # 5x5x20 rotation circuit, all 1000 angles: 1 sliced variable leaves the gradient arena
-    # too large for shared memory (global-memory kernel), 8 let it fit (on-chip kernel)
+    # too large for shared memory (global-memory kernel); 8 let it fit (on-chip kernel; 512
+    # work items for two bitstrings, more than one staged CTA per SM could take at once);
+    # 6 give 128 work items, each with a CTA of the staged form (leaf data on chip too)
     c = cg.rotation_circuit(5, 5, 20, 4001)
     xs = cg.random_bitstrings(25, 2, 4004)
     big = q.Plan(c, gradient=True, n_slices=1, inner_slices=0)
     small = q.Plan(c, gradient=True, n_slices=8, inner_slices=0)
+    staged = q.Plan(c, gradient=True, n_slices=6, inner_slices=0)
     assert big.info["grad_smem_bytes"] > 232448 and 0 < small.info["grad_smem_bytes"] <= 232448
     a1, g1 = (t.cpu().numpy() for t in big.amplitude_grad(xs))
     a2, g2 = (t.cpu().numpy() for t in small.amplitude_grad(xs))
+    a3, g3 = (t.cpu().numpy() for t in staged.amplitude_grad(xs))
     assert np.max(np.abs(a1 - a2)) < tol(25) and np.max(np.abs(g1 - g2)) < tol(25)
+    assert np.max(np.abs(a3 - a2)) < tol(25) and np.max(np.abs(g3 - g2)) < tol(25)
     order = q.Plan(c, n_slices=0, host_merge_rank=0).order
     for i, x in enumerate(xs):
         assert abs(a2[i] - VE.ve_amplitude(c, x, order)) < tol(25)

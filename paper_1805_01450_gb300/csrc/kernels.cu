@@ -705,7 +705,7 @@ __global__ void __launch_bounds__(256) persistent_program_kernel(LaunchArgs a, i
 // loaded entry serves several outputs from registers. Two summed indices are in flight per
 // iteration to keep more loads outstanding.
 template <int RM, int RN>
-__global__ void __launch_bounds__(256) regtile_step_kernel(LaunchArgs a, RegTileStep rs, int64_t item_begin,
+__global__ void __launch_bounds__(256, 4) regtile_step_kernel(LaunchArgs a, RegTileStep rs, int64_t item_begin,
                                                            int64_t n_items, float2 *arenas) {
     constexpr int TM = 1 << RM, TN = 1 << RN;
     const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -739,7 +739,7 @@ __global__ void __launch_bounds__(256) regtile_step_kernel(LaunchArgs a, RegTile
     for (int i = 0; i < TM; i++)
 #pragma unroll
         for (int j = 0; j < TN; j++) acc[i][j] = make_float2(0.f, 0.f);
-#pragma unroll 2
+#pragma unroll 4  // more loads in flight per thread, registers held at 64
     for (uint32_t k = 0; k < (1u << nk); k++) {
         const uint32_t ka = k & mask_ka;
         const uint32_t kb = (k & mask_ab) | ((k >> (nab + na)) << nab);

@@ -39,6 +39,9 @@ TUNE = {"grid7x7d30-b1024": dict(slice_counts=(0, 2, 4, 6, 8), engines=("stepwis
         "grid8x8d40": dict(slice_counts=(8, 10, 12), engines=("stepwise", "stepwise-tc"), inner=(2, 4),
                            budget_s=120.0)}
 MEM_BUDGET_MB = {"grid7x7d30-b1024": 32768, "grid8x8d40": 65536}
+# independent planning trials (ordering + slice choice from distinct seeds, the best by the
+# planner's bandwidth-weighted estimate kept); planning is outside the timed region
+PLAN_TRIALS = {"grid6x6d25-k12": 64, "grid7x7d30-b1024": 64, "grid8x8d40": 64}
 DEFAULT_WORKLOAD = "grid6x6d25-k12"
 METRIC = "amplitudes/s and complex TFLOP/s (% of GB300 peak) at |Δα|≤1e-5·2^-N/2 vs FP64"
 L2_FLUSH_BYTES = 256 << 20
@@ -64,14 +67,17 @@ def parse():
                     help="stepwise engine: dense contractions as bf16 hi/lo GEMMs on the tensor cores")
     ap.add_argument("--engine", default="auto")
     ap.add_argument("--sliced", type=int, default=None, help="override the workload's sliced-variable count")
+    ap.add_argument("--plan-trials", type=int, default=None, help="planning trials (workload default)")
+    ap.add_argument("--circuit-seed", type=int, default=None, help="override the workload's circuit seed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
     return ap.parse_args()
 
 
-def workload(name, batch, rank):
+def workload(name, batch, rank, circuit_seed=None):
     kind, r, c, d, cseed, bseed, k, b0 = WORKLOADS[name]
     batch = b0 if batch is None else batch
+    cseed = cseed if circuit_seed is None else circuit_seed
     circ = cg.grid_circuit(r, c, d, cseed) if kind == "grid" else cg.rotation_circuit(r, c, d, cseed)
     bits = cg.random_bitstrings(r * c, batch * (rank + 1), bseed)[batch * rank:]
     return circ, bits, k
@@ -169,10 +175,14 @@ def run_reference(args, rank, world):
         return
     import numpy as np
     from oracle import ve as VE
-    circ, bits, k = workload(args.workload, args.batch, 0)
+    circ, bits, k = workload(args.workload, args.batch, 0, args.circuit_seed)
+    if args.sliced is not None:
+        k = args.sliced
     args.batch = len(bits)
     import paper_1805_01450_gb300 as q
-    plan = q.Plan(circ, n_slices=k)   # host planner only: the oracle takes its order and slices
+    trials = args.plan_trials if args.plan_trials is not None else PLAN_TRIALS.get(args.workload, 1)
+    # host planner only: the oracle takes its order and slices
+    plan = q.Plan(circ, n_slices=k, plan_trials=1 if is_grad(args.workload) else trials)
     threads = os.cpu_count() or 1
     VE.build_library()
     total = 1 << k
@@ -222,7 +232,9 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    circ, bits_host, k = workload(args.workload, args.batch, rank)
+    circ, bits_host, k = workload(args.workload, args.batch, rank, args.circuit_seed)
+    if args.plan_trials is None:
+        args.plan_trials = 1 if is_grad(args.workload) else PLAN_TRIALS.get(args.workload, 1)
     if args.sliced is not None:
         k = args.sliced
     if args.mem_budget_mb is None:
@@ -234,14 +246,15 @@ def main():
     if args.inner_slices is None and args.warps_per_item is None and args.engine == "auto" and not grad:
         from paper_1805_01450_gb300.autotune import autotune
         tune = dict(TUNE.get(args.workload, {})) if args.sliced is None else {}
-        plan, tuning = autotune(circ, bits_host, n_slices=k, device=dev, mem_budget_bytes=budget, **tune)
+        plan, tuning = autotune(circ, bits_host, n_slices=k, device=dev, mem_budget_bytes=budget,
+                                plan_trials=args.plan_trials, **tune)
     else:
         # gradient workload: one sliced variable open inside a work item (128 items, each on a
         # CTA of the staged shared-memory kernel at once)
         inner = args.inner_slices if args.inner_slices is not None else (1 if grad else -1)
         plan = q.Plan(circ, n_slices=k, inner_slices=inner,
                       warps_per_item=args.warps_per_item or 1, engine=args.engine, gradient=grad,
-                      mem_budget_bytes=budget, tensor_cores=args.tensor_cores)
+                      mem_budget_bytes=budget, tensor_cores=args.tensor_cores, plan_trials=args.plan_trials)
     info = plan.info
     B = len(bits_host)
     bits = plan._bits(bits_host, dev)
@@ -356,10 +369,12 @@ def main():
         "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-        "config": {"workload": args.workload, "qubits": n, "depth": circ.depth, "sliced": len(plan.slices),
+        "config": {"workload": args.workload, "circuit_seed": WORKLOADS[args.workload][4]
+                   if args.circuit_seed is None else args.circuit_seed,
+                   "qubits": n, "depth": circ.depth, "sliced": len(plan.slices),
                    "inner_slices": info["n_inner"], "bitstrings_per_step": B, "engine": info["engine"],
                    "warps_per_item": info["warps_per_item"], "mem_budget_mb": args.mem_budget_mb,
-                   "tensor_core_steps": info["n_gemm_steps"],
+                   "tensor_core_steps": info["n_gemm_steps"], "plan_trials": args.plan_trials,
                    "l2": "flushed (256 MiB write) before each step",
                    "parallelism": f"bitstrings per rank x {world}"},
         "complex_tflops": flops / (ms_step / 1e3) / 1e12,

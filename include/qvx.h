@@ -117,6 +117,10 @@ typedef struct {
                                   GEMMs on the tcgen05 tensor cores, each FP32 operand split into
                                   three bf16 parts (six products, FP32 accumulation: about 2^-23
                                   relative error per product); 0 keeps them on FP32 SIMT kernels */
+    int32_t plan_trials;       /* >= 1 independent planning trials (ordering, slice choice and
+                                  re-ordering, each from its own seed; trial 0 from order_seed);
+                                  the plan with the smallest bandwidth-weighted contraction
+                                  estimate is kept. Ignored when both order and slices are given */
 } qvx_plan_opts;
 
 typedef struct {
@@ -143,6 +147,8 @@ typedef struct {
     int32_t grad_recomputed;         /* gradient plans: forward contractions recomputed in the
                                         backward pass because one work item's gradient arena would
                                         exceed opts.mem_budget_bytes with every forward value kept */
+    double est_bytes_per_amplitude;  /* the planner's ranking of planning trials: per contraction
+                                        max(algorithmic bytes, flops / 12), all items */
 } qvx_plan_info;
 
 typedef struct qvx_plan qvx_plan;

@@ -45,7 +45,8 @@ class PlanOpts(ctypes.Structure):
                 ("max_rank", ctypes.c_int32), ("warps_per_item", ctypes.c_int32),
                 ("host_merge_rank", ctypes.c_int32), ("gradient", ctypes.c_int32),
                 ("slice_rule", ctypes.c_int32), ("n_open_qubits", ctypes.c_int32),
-                ("open_qubits", ctypes.c_int32 * 16), ("tensor_cores", ctypes.c_int32)]
+                ("open_qubits", ctypes.c_int32 * 16), ("tensor_cores", ctypes.c_int32),
+                ("plan_trials", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -60,7 +61,8 @@ class PlanInfo(ctypes.Structure):
                 ("grad_flops_per_amplitude", ctypes.c_double), ("grad_bytes_per_amplitude", ctypes.c_double),
                 ("n_tiled_steps", ctypes.c_int32), ("n_phases", ctypes.c_int32),
                 ("n_open_qubits", ctypes.c_int32), ("n_gemm_steps", ctypes.c_int32),
-                ("grad_smem_bytes", ctypes.c_int32), ("grad_recomputed", ctypes.c_int32)]
+                ("grad_smem_bytes", ctypes.c_int32), ("grad_recomputed", ctypes.c_int32),
+                ("est_bytes_per_amplitude", ctypes.c_double)]
 
 
 _lib = None
@@ -158,7 +160,7 @@ class Plan:
     def __init__(self, circ, order=None, slices=None, n_slices=-1, engine="auto", inner_slices=-1,
                  order_restarts=8, order_seed=1, mem_budget_bytes=1 << 30, max_rank=30,
                  warps_per_item=1, host_merge_rank=8, gradient=False, slice_rule="greedy", open_qubits=(),
-                 tensor_cores=False):
+                 tensor_cores=False, plan_trials=1):
         L = lib()
         opts = PlanOpts()
         L.qvx_plan_opts_default(ctypes.byref(opts))
@@ -174,6 +176,7 @@ class Plan:
         opts.gradient = 1 if gradient else 0
         opts.slice_rule = {"greedy": 0, "reorder": 1, "cz-pair": 2}[slice_rule]
         opts.tensor_cores = 1 if tensor_cores else 0
+        opts.plan_trials = plan_trials
         opts.n_open_qubits = len(open_qubits)
         for i, qb in enumerate(open_qubits):
             opts.open_qubits[i] = qb

@@ -41,7 +41,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     jobs, objs = [], []
     for f in HOST_SOURCES:
         o = os.path.join(BUILD, f + ".o")
-        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-I", inc, "-I", os.path.join(cuda, "include"),
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-I", inc, "-I", os.path.join(cuda, "include"),
                "-c", os.path.join(CSRC, f), "-o", o]
         jobs.append(cmd)
         objs.append(o)
@@ -62,7 +62,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         raise RuntimeError("compile failed:\n" + "\n".join(failed))
     tmp = OUT + f".{os.getpid()}.tmp"
-    subprocess.check_call([nvcc] + ARCH + ["-shared", "-Xcompiler", "-fPIC", "-o", tmp] + objs)
+    subprocess.check_call([nvcc] + ARCH + ["-shared", "-Xcompiler", "-fPIC,-pthread", "-o", tmp] + objs)
     os.replace(tmp, OUT)
     return OUT
 

@@ -248,6 +248,7 @@ void qvx_plan_opts_default(qvx_plan_opts *o) {
     o->host_merge_rank = 8;
     o->gradient = 0;
     o->slice_rule = 0;
+    o->plan_trials = 1;
 }
 
 qvx_status qvx_graph_export(const qvx_circuit *circuit, int32_t *n_vars, int32_t *var_qubit,
@@ -287,6 +288,7 @@ qvx_status qvx_plan_create(const qvx_circuit *circuit, const int32_t *order, int
     if (o.order_restarts < 1 || o.max_rank < 1 || o.mem_budget_bytes < 64)
         return fail(QVX_EINVAL, "opts: restarts >= 1, max_rank >= 1, budget >= 64 bytes");
     if (o.slice_rule < 0 || o.slice_rule > 2) return fail(QVX_EINVAL, "opts: slice_rule must be 0, 1 or 2");
+    if (o.plan_trials < 1 || o.plan_trials > 1024) return fail(QVX_EINVAL, "opts: plan_trials must be in [1, 1024]");
     if (o.tensor_cores < 0 || o.tensor_cores > 1) return fail(QVX_EINVAL, "opts: tensor_cores must be 0 or 1");
     if (o.host_merge_rank < 0 || o.host_merge_rank > 16)
         return fail(QVX_EINVAL, "opts: host_merge_rank must be in [0, 16]");
@@ -343,6 +345,7 @@ qvx_status qvx_plan_get_info(const qvx_plan *plan, qvx_plan_info *info) {
     info->n_gemm_steps = 0;
     for (const qvx::GemmStep &g : p.gemm) info->n_gemm_steps += g.nk > 0 ? 1 : 0;
     info->grad_recomputed = p.grad_recomputed;
+    info->est_bytes_per_amplitude = qvx::plan_estimate(p);
     info->grad_smem_bytes = p.opts.gradient
         ? (int32_t)qvx::grad_smem_bytes(reinterpret_cast<const qvx::DevProgram *>(p.image.data())) : 0;
     info->grad_bytes_per_amplitude = p.grad_bytes_per_item * (double)info->n_items_per_bitstring;

@@ -90,5 +90,6 @@ bool build_model(const qvx_circuit *c, Model *m, std::string *err, bool keep_par
 qvx_status make_plan(const qvx_circuit *c, const int32_t *order, int32_t n_order,
                      const int32_t *slices, int32_t n_slices, const qvx_plan_opts &opts,
                      Plan *p, std::string *err);
+double plan_estimate(const Plan &p);   // bandwidth-weighted contraction estimate, all items
 
 }  // namespace qvx

@@ -3,7 +3,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <functional>
+#include <thread>
 #include <numeric>
 #include <unordered_map>
 
@@ -1661,8 +1663,93 @@ bool build_program(Plan &p, std::string *err) {
 
 }  // namespace
 
+// Time estimate of a plan's contractions in HBM bytes: per step its algorithmic bytes, or
+// its flops at 12 flops per byte (about the FP32 FMA rate over the HBM bandwidth, the
+// balance of the SIMT kernels) when those take longer, summed over the work items of one
+// bitstring. Used to rank planning trials; Section 3.B ranks orders by flops alone, which
+// leaves out that most steps are bandwidth bound.
+double plan_estimate(const Plan &p) {
+    double t = 0;
+    for (const PStep &s : p.steps) {
+        const auto &A = p.tensors[s.a].modes;
+        const auto &C = p.tensors[s.c].modes;
+        double fl, by;
+        if (s.b < 0) {
+            fl = 2.0 * std::ldexp(1.0, (int)A.size());
+            by = 8.0 * (std::ldexp(1.0, (int)A.size()) + std::ldexp(1.0, (int)C.size()));
+        } else {
+            const auto &B = p.tensors[s.b].modes;
+            int u = (int)(C.size() + s.k_ab.size() + s.k_a.size() + s.k_b.size());
+            fl = 8.0 * std::ldexp(1.0, u);
+            by = 8.0 * (std::ldexp(1.0, (int)A.size()) + std::ldexp(1.0, (int)B.size()) +
+                        std::ldexp(1.0, (int)C.size()));
+        }
+        t += std::max(by, fl / 12.0);
+    }
+    return t * std::ldexp(1.0, (int)p.slices.size() - p.n_inner);
+}
+
+namespace {
+
+qvx_status plan_once(const qvx_circuit *c, const int32_t *order, int32_t n_order,
+                     const int32_t *slices, int32_t n_slices, const qvx_plan_opts &opts,
+                     Plan *p, std::string *err);
+
+}  // namespace
+
 // ---------------------------------------------------------------- entry point
+// Section 3.B picks one ordering (QuickBB) and then the sliced variables; here every trial
+// re-runs the randomised ordering, the slice choice and the re-ordering from its own seed,
+// and the trial with the smallest estimate (plan_estimate) is kept. Trial 0 uses the given
+// seed, so plan_trials = 1 is the single-trial planner.
 qvx_status make_plan(const qvx_circuit *c, const int32_t *order, int32_t n_order,
+                     const int32_t *slices, int32_t n_slices, const qvx_plan_opts &opts,
+                     Plan *p, std::string *err) {
+    const bool fixed = n_order > 0 && n_slices >= 0;
+    const int trials = fixed ? 1 : std::max(1, opts.plan_trials);
+    if (trials == 1) return plan_once(c, order, n_order, slices, n_slices, opts, p, err);
+    // trials are independent: run them on host threads, then keep the best (lowest trial
+    // index among equal estimates, so the result does not depend on the thread count)
+    std::vector<Plan> cand(trials);
+    std::vector<std::string> errs(trials);
+    std::vector<qvx_status> st(trials, QVX_EUNSUPPORTED);
+    std::vector<char> oom(trials, 0);
+    std::atomic<int> next{0};
+    auto work = [&]() {
+        for (int t = next++; t < trials; t = next++) {
+            qvx_plan_opts o = opts;
+            o.order_seed = opts.order_seed + uint64_t(t) * 0xD1B54A32D192ED03ull;
+            try {
+                st[t] = plan_once(c, order, n_order, slices, n_slices, o, &cand[t], &errs[t]);
+            } catch (const std::bad_alloc &) {
+                oom[t] = 1;
+            }
+            if (st[t] != QVX_OK) cand[t] = Plan();
+        }
+    };
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int n_threads = (int)std::min<unsigned>(std::min<unsigned>(hw, 16u), (unsigned)trials);
+    std::vector<std::thread> pool;
+    for (int i = 1; i < n_threads; i++) pool.emplace_back(work);
+    work();
+    for (auto &th : pool) th.join();
+    int best = -1;
+    double best_est = 0;
+    for (int t = 0; t < trials; t++) {
+        if (oom[t]) throw std::bad_alloc();
+        if (st[t] != QVX_OK && st[t] != QVX_EUNSUPPORTED) { *err = errs[t]; return st[t]; }  // bad input
+        if (st[t] != QVX_OK) continue;
+        const double est = plan_estimate(cand[t]);
+        if (best < 0 || est < best_est) { best = t; best_est = est; }
+    }
+    if (best < 0) { *err = errs[0]; return QVX_EUNSUPPORTED; }
+    *p = std::move(cand[best]);
+    return QVX_OK;
+}
+
+namespace {
+
+qvx_status plan_once(const qvx_circuit *c, const int32_t *order, int32_t n_order,
                      const int32_t *slices, int32_t n_slices, const qvx_plan_opts &opts,
                      Plan *p, std::string *err) {
     p->opts = opts;
@@ -1808,5 +1895,7 @@ qvx_status make_plan(const qvx_circuit *c, const int32_t *order, int32_t n_order
     }
     return QVX_OK;
 }
+
+}  // namespace
 
 }  // namespace qvx

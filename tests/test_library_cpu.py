@@ -290,6 +290,44 @@ def test_slice_rules_section6():
         assert sorted(p.order + p.slices) == list(range(len(counts)))
 
 
+def test_planning_trials_keep_the_cheapest_valid_plan():
+    # trial 0 is the single-trial planner; more trials never rank worse, give the same plan
+    # on every build (threads do not decide), and the kept plan's reported cost is the sum
+    # of 2^deg of its own order after fixing its own slices (oracle graph operations)
+    c = cg.grid_circuit(7, 7, 30, 3001)
+    one = q.Plan(c, n_slices=4, inner_slices=0)
+    t1 = q.Plan(c, n_slices=4, inner_slices=0, plan_trials=1)
+    assert (one.order, one.slices) == (t1.order, t1.slices)
+    a = q.Plan(c, n_slices=4, inner_slices=0, plan_trials=16)
+    b = q.Plan(c, n_slices=4, inner_slices=0, plan_trials=16)
+    assert (a.order, a.slices) == (b.order, b.slices)
+    assert a.info["est_bytes_per_amplitude"] <= one.info["est_bytes_per_amplitude"]
+    m = GR.build(c)
+    adj = GR.adjacency(len(m.variables), GR.edges(m))
+    for v in a.slices:
+        adj = GR.fix_vertex(adj, v)
+    cost, _ = GR.order_cost(adj, a.order)
+    assert abs(np.log2(cost) - a.info["log2_cost"]) < 1e-9
+    assert sorted(a.order + a.slices) == list(range(len(m.variables)))
+    # a given order and slice set leave nothing to try
+    f = q.Plan(c, order=one.order, slices=one.slices, inner_slices=0, plan_trials=8)
+    assert (f.order, f.slices) == (one.order, one.slices)
+    with pytest.raises(q.QvxError) as e:
+        q.Plan(c, n_slices=4, plan_trials=0)
+    assert e.value.status == q.QVX_EINVAL
+
+
+def test_planning_trials_program_matches_oracle():
+    c = cg.grid_circuit(4, 4, 12, 31)
+    p = q.Plan(c, n_slices=4, inner_slices=1, plan_trials=8)
+    prog = Program(p.image())
+    psi = SV.final_state(c)
+    for x in cg.random_bitstrings(16, 3, 33):
+        terms = prog.slice_terms(x)
+        assert abs(terms.sum() - psi[x]) < 1e-6 * 2 ** -8
+        assert np.max(np.abs(terms - VE.slice_terms(c, x, p.order, p.slices))) < 1e-6 * 2 ** -8
+
+
 @pytest.mark.parametrize("rule", ["reorder", "cz-pair"])
 def test_slice_rules_program_matches_oracle(rule):
     c = cg.grid_circuit(4, 4, 12, 31)

@@ -1343,7 +1343,11 @@ bool serialize(Plan &p, std::string *err) {
     }
     // tensor-core form of the dense contractions (stepwise engine, opts.tensor_cores): every
     // summed mode in both operands, 16 to 1024 summed entries (K), 64 A-only (M) and 16
-    // B-only (N) output entries, and an arithmetic intensity at or above the FP32 ridge
+    // B-only (N) output entries, and an arithmetic intensity at or above the FP32 ridge.
+    // The epilogue's lanes store along N, so C's lowest mode (its unit stride) decides how
+    // the stores coalesce: a step whose lowest output mode is held by both operands (a batch
+    // mode: every CTA's tile then lands at a stride of at least two entries) keeps its SIMT
+    // form, and when both role assignments fit, the operand holding that mode takes N.
     std::vector<GemmStep> gms;
     if (p.engine == QVX_ENGINE_STEPWISE && p.opts.tensor_cores) {
         gms.assign(ds.size(), GemmStep{});
@@ -1356,20 +1360,34 @@ bool serialize(Plan &p, std::string *err) {
             // 16; complex products commute, so the step's B may take the row role
             bool swap = false;
             std::vector<int> gb, gm, gn;
+            const int low = p.tensors[st.c].modes.empty() ? -1 : p.tensors[st.c].modes[0];
+            int pick = -1;   // 0: as given, 1: swapped
             for (int pass = 0; pass < 2; pass++) {
-                swap = pass == 1;
+                const std::vector<int> &LA = p.tensors[pass ? st.b : st.a].modes;
+                const std::vector<int> &LB = p.tensors[pass ? st.a : st.b].modes;
+                int na = 0, nb = 0;
+                bool low_n = false, low_batch = false;
+                for (int v : p.tensors[st.c].modes) {
+                    const bool ia = find_pos(LA, v) >= 0, ib = find_pos(LB, v) >= 0;
+                    if (ia && !ib) na++;
+                    if (ib && !ia) nb++;
+                    if (v == low) { low_n = ib && !ia; low_batch = ia && ib; }
+                }
+                if (low_batch || na < 6 || nb < 4) continue;
+                if (pick < 0 || low_n) pick = pass;
+            }
+            if (pick < 0) continue;
+            swap = pick == 1;
+            {
                 const std::vector<int> &LA = p.tensors[swap ? st.b : st.a].modes;
-                const std::vector<int> &LB = p.tensors[swap ? st.a : st.b].modes, &LC = p.tensors[st.c].modes;
-                gb.clear(); gm.clear(); gn.clear();
-                for (int v : LC) {
+                const std::vector<int> &LB = p.tensors[swap ? st.a : st.b].modes;
+                for (int v : p.tensors[st.c].modes) {
                     const bool ia = find_pos(LA, v) >= 0, ib = find_pos(LB, v) >= 0;
                     if (ia && ib) gb.push_back(v);
                     else if (ia) gm.push_back(v);
                     else gn.push_back(v);
                 }
-                if (gm.size() >= 6 && gn.size() >= 4) break;
             }
-            if (gm.size() < 6 || gn.size() < 4) continue;
             const std::vector<int> &LA = p.tensors[swap ? st.b : st.a].modes;
             const std::vector<int> &LB = p.tensors[swap ? st.a : st.b].modes, &LC = p.tensors[st.c].modes;
             const double flops = 8.0 * std::ldexp(1.0, (int)(LC.size() + st.k_ab.size()));

@@ -173,6 +173,33 @@ def test_tensor_core_form_on_host(rows, cols, seed, swapped):
     assert q.Plan(c, n_slices=8, inner_slices=2, engine="stepwise").info["n_gemm_steps"] == 0
 
 
+def test_tensor_core_steps_store_along_their_unit_stride():
+    # 8x8x40 (circuit 5001, 64 planning trials): a dense step whose output's lowest mode is
+    # held by both operands keeps its SIMT form; every tensor-core step's lowest output mode
+    # is a row or column mode of the GEMM, the column one whenever both roles fit
+    c = cg.grid_circuit(8, 8, 40, 5001)
+    p = q.Plan(c, n_slices=10, inner_slices=4, engine="stepwise", tensor_cores=True, plan_trials=64,
+               mem_budget_bytes=64 << 30)
+    prog = Program(p.image())
+
+    def holds_low(runs, n):
+        return any(int(r["src"]) == 0 and int(r["len"]) > 0 for r in runs[:n])
+
+    kept_simt = 0
+    for s, st in enumerate(prog.steps):
+        g = prog.gemms[s]
+        dense = int(st["nk_a"]) == 0 and int(st["nk_b"]) == 0 and 4 <= int(st["nk_ab"]) <= 10 and int(st["rc"]) >= 10
+        low_batch = holds_low(st["runs_a"], int(st["na_runs"])) and holds_low(st["runs_b"], int(st["nb_runs"]))
+        if int(g["nk"]) == 0:
+            kept_simt += dense and low_batch
+            continue
+        assert not low_batch
+        dsts = lambda f, n: [int(r["dst"]) for r in g[f][:n] if int(r["len"]) > 0]
+        assert 0 not in dsts("cb", int(g["n_cb"]))
+        assert 0 in dsts("cm", int(g["n_cm"])) + dsts("cn", int(g["n_cn"]))
+    assert kept_simt >= 1 and p.info["n_gemm_steps"] >= 2
+
+
 @pytest.mark.parametrize("merge", [0, 8])
 def test_program_slice_terms_6x6_sample(merge):
     c = cg.grid_circuit(6, 6, 25, 2001)

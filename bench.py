@@ -36,7 +36,7 @@ WORKLOADS = {
 # workloads whose plan variant the autotuner also picks the slice count and engine for,
 # and the arena memory the global-arena engines may use there (MiB)
 TUNE = {"grid7x7d30-b1024": dict(slice_counts=(0, 2, 4, 6, 8), engines=("stepwise",), budget_s=90.0),
-        "grid8x8d40": dict(slice_counts=(8, 10, 12), engines=("stepwise", "stepwise-tc"), inner=(2, 4),
+        "grid8x8d40": dict(slice_counts=(10, 12), engines=("stepwise-tc",), inner=(4,), trial_counts=(1, 16),
                            budget_s=120.0)}
 MEM_BUDGET_MB = {"grid7x7d30-b1024": 32768, "grid8x8d40": 65536}
 # independent planning trials (ordering + slice choice from distinct seeds, the best by the
@@ -374,7 +374,7 @@ def main():
                    "qubits": n, "depth": circ.depth, "sliced": len(plan.slices),
                    "inner_slices": info["n_inner"], "bitstrings_per_step": B, "engine": info["engine"],
                    "warps_per_item": info["warps_per_item"], "mem_budget_mb": args.mem_budget_mb,
-                   "tensor_core_steps": info["n_gemm_steps"], "plan_trials": args.plan_trials,
+                   "tensor_core_steps": info["n_gemm_steps"], "plan_trials": plan.plan_trials,
                    "l2": "flushed (256 MiB write) before each step",
                    "parallelism": f"bitstrings per rank x {world}"},
         "complex_tflops": flops / (ms_step / 1e3) / 1e12,

@@ -201,6 +201,7 @@ class Plan:
         self.slices = list(s[:k])
         self.open_qubits = list(open_qubits)
         self.n_open = len(self.open_qubits)
+        self.plan_trials = plan_trials
         self.mem_budget_bytes = mem_budget_bytes
         self._ws = {}
 

@@ -44,14 +44,16 @@ def _time_plan(p, bits, flush, stream, reps, warmup):
 
 def autotune(circ, bitstrings, n_slices=-1, slices=None, order=None, inner=None, warps=(1, 2, 4, 8, 16),
              merges=(8, 10), reps=20, warmup=3, budget_s=30.0, device=None, verbose=False,
-             slice_counts=None, engines=("fused",), order_seeds=(), **plan_kw):
+             slice_counts=None, engines=("fused",), order_seeds=(), trial_counts=(), **plan_kw):
     """Returns (best_plan, results) with results = [(n_sliced, inner, engine, warps,
     host_merge_rank, us_per_call), ...]. host_merge_rank is the largest leaf product
     contracted at plan time. slice_counts (a list of k) replaces n_slices when given;
     engines lists the engines tried ("fused", "stepwise", "persistent"). order_seeds: after
     the search, the best variant is rebuilt with each of these seeds of the randomised
     ordering (another order, and the slices chosen under it; the same amplitude) and timed;
-    their results carry the seed as a seventh field."""
+    their results carry the seed as a seventh field. trial_counts: likewise, the best variant
+    is rebuilt with each of these numbers of planning trials (the planner ranks trials by an
+    estimate; timing decides between the plans it keeps), carried as "plan_trials=T"."""
     import torch
     dev = torch.device(device if device is not None else "cuda")
     bits = Plan._bits(bitstrings, dev)
@@ -90,6 +92,21 @@ def autotune(circ, bitstrings, n_slices=-1, slices=None, order=None, inner=None,
                 best_kw = dict(inner_slices=n_in, warps_per_item=w, host_merge_rank=m,
                                engine=eng[:-3] if tc else eng, tensor_cores=tc, n_slices=kk)
                 best_key = (kk, n_in, eng, w, m)
+            else:
+                del p
+    if best is not None and trial_counts and order is None and slices is None:
+        kw = {k: v for k, v in plan_kw.items() if k != "plan_trials"}
+        for tr in trial_counts:
+            if tr == plan_kw.get("plan_trials", 1) or time.perf_counter() - t_start > budget_s + 30.0:
+                continue
+            try:
+                p = Plan(circ, plan_trials=tr, **best_kw, **kw)
+            except Exception:
+                continue
+            us = _time_plan(p, bits, flush, stream, reps, warmup)
+            results.append(best_key + (us, f"plan_trials={tr}"))
+            if us < best_t:
+                best, best_t = p, us
             else:
                 del p
     if best is not None and order_seeds and order is None and slices is None:

@@ -36,7 +36,7 @@ WORKLOADS = {
 # workloads whose plan variant the autotuner also picks the slice count and engine for,
 # and the arena memory the global-arena engines may use there (MiB)
 TUNE = {"grid7x7d30-b1024": dict(slice_counts=(0, 2, 4, 6, 8), engines=("stepwise",), budget_s=90.0),
-        "grid8x8d40": dict(slice_counts=(10, 12), engines=("stepwise-tc",), inner=(4,), trial_counts=(1, 16),
+        "grid8x8d40": dict(slice_counts=(10, 12), engines=("stepwise", "stepwise-tc"), inner=(4,), trial_counts=(1, 16),
                            budget_s=120.0)}
 MEM_BUDGET_MB = {"grid7x7d30-b1024": 32768, "grid8x8d40": 65536}
 # independent planning trials (ordering + slice choice from distinct seeds, the best by the
@@ -248,6 +248,8 @@ def main():
         tune = dict(TUNE.get(args.workload, {})) if args.sliced is None else {}
         plan, tuning = autotune(circ, bits_host, n_slices=k, device=dev, mem_budget_bytes=budget,
                                 plan_trials=args.plan_trials, **tune)
+        if plan is None:
+            raise SystemExit(f"autotune: no plan variant of {args.workload} could be built or timed")
     else:
         # gradient workload: one sliced variable open inside a work item (128 items, each on a
         # CTA of the staged shared-memory kernel at once)

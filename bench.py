@@ -35,7 +35,8 @@ WORKLOADS = {
 }
 # workloads whose plan variant the autotuner also picks the slice count and engine for,
 # and the arena memory the global-arena engines may use there (MiB)
-TUNE = {"grid7x7d30-b1024": dict(slice_counts=(0, 2, 4, 6, 8), engines=("stepwise",), budget_s=90.0),
+TUNE = {"grid6x6d25-k12": dict(trial_counts=(1, 16, 256)),
+        "grid7x7d30-b1024": dict(slice_counts=(0, 2, 4, 6, 8), engines=("stepwise",), budget_s=90.0),
         "grid8x8d40": dict(slice_counts=(10, 12), engines=("stepwise", "stepwise-tc"), inner=(4,), trial_counts=(1, 16),
                            budget_s=120.0)}
 MEM_BUDGET_MB = {"grid7x7d30-b1024": 32768, "grid8x8d40": 65536}
@@ -63,6 +64,7 @@ def parse():
     ap.add_argument("--mem-budget-mb", type=int, default=None,
                     help="arena memory of the global-arena engines (work items in flight; workload default)")
     ap.add_argument("--warps-per-item", type=int, default=None)
+    ap.add_argument("--host-merge-rank", type=int, default=8, help="fixed plan variant: leaf products contracted at plan time")
     ap.add_argument("--tensor-cores", action="store_true",
                     help="stepwise engine: dense contractions as bf16 hi/lo GEMMs on the tensor cores")
     ap.add_argument("--engine", default="auto")
@@ -256,7 +258,8 @@ def main():
         inner = args.inner_slices if args.inner_slices is not None else (1 if grad else -1)
         plan = q.Plan(circ, n_slices=k, inner_slices=inner,
                       warps_per_item=args.warps_per_item or 1, engine=args.engine, gradient=grad,
-                      mem_budget_bytes=budget, tensor_cores=args.tensor_cores, plan_trials=args.plan_trials)
+                      mem_budget_bytes=budget, tensor_cores=args.tensor_cores, plan_trials=args.plan_trials,
+                      host_merge_rank=args.host_merge_rank)
     info = plan.info
     B = len(bits_host)
     bits = plan._bits(bits_host, dev)

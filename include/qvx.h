@@ -119,9 +119,8 @@ typedef struct {
                                   relative error per product); 0 keeps them on FP32 SIMT kernels */
     int32_t plan_trials;       /* >= 1 independent planning trials (ordering, slice choice and
                                   re-ordering, each from its own seed; trial 0 from order_seed);
-                                  kept: a fused-engine plan with the fewest level phases, else
-                                  (and on ties) the smallest bandwidth-weighted contraction
-                                  estimate. Ignored when both order and slices are given */
+                                  the plan with the smallest bandwidth-weighted contraction
+                                  estimate is kept. Ignored when both order and slices are given */
 } qvx_plan_opts;
 
 typedef struct {

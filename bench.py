@@ -37,7 +37,7 @@ WORKLOADS = {
 # and the arena memory the global-arena engines may use there (MiB)
 TUNE = {"grid6x6d25-k12": dict(trial_counts=(1, 16, 256)),
         "grid7x7d30-b1024": dict(slice_counts=(0, 2, 4, 6, 8), engines=("stepwise",), budget_s=90.0),
-        "grid8x8d40": dict(slice_counts=(10, 12), engines=("stepwise", "stepwise-tc"), inner=(4,), trial_counts=(1, 16),
+        "grid8x8d40": dict(slice_counts=(10, 12), engines=("stepwise", "stepwise-tc"), inner=(4,), trial_counts=(1, 16, 256),
                            budget_s=120.0)}
 MEM_BUDGET_MB = {"grid7x7d30-b1024": 32768, "grid8x8d40": 65536}
 # independent planning trials (ordering + slice choice from distinct seeds, the best by the

@@ -95,20 +95,32 @@ def autotune(circ, bitstrings, n_slices=-1, slices=None, order=None, inner=None,
             else:
                 del p
     if best is not None and trial_counts and order is None and slices is None:
+        # the stepwise engine's two forms are both re-timed: another plan may have dense
+        # steps that the tensor cores take
         kw = {k: v for k, v in plan_kw.items() if k != "plan_trials"}
+        forms = [best_key[2]]
+        if best_key[2] in ("stepwise", "stepwise-tc"):
+            forms += [e for e in ("stepwise", "stepwise-tc") if e in engines and e != best_key[2]]
         for tr in trial_counts:
             if tr == plan_kw.get("plan_trials", 1) or time.perf_counter() - t_start > budget_s + 30.0:
                 continue
-            try:
-                p = Plan(circ, plan_trials=tr, **best_kw, **kw)
-            except Exception:
-                continue
-            us = _time_plan(p, bits, flush, stream, reps, warmup)
-            results.append(best_key + (us, f"plan_trials={tr}"))
-            if us < best_t:
-                best, best_t = p, us
-            else:
-                del p
+            picked = {}   # the trials' order and slices, planned once per trial count
+            for eng in forms:
+                tc = eng.endswith("-tc")
+                try:
+                    p = Plan(circ, plan_trials=tr, **picked,
+                             **dict(best_kw, engine=eng[:-3] if tc else eng, tensor_cores=tc), **kw)
+                    picked = dict(order=p.order, slices=p.slices)
+                    if tc and p.info["n_gemm_steps"] == 0:
+                        continue
+                except Exception:
+                    continue
+                us = _time_plan(p, bits, flush, stream, reps, warmup)
+                results.append(best_key[:2] + (eng,) + best_key[3:] + (us, f"plan_trials={tr}"))
+                if us < best_t:
+                    best, best_t = p, us
+                else:
+                    del p
     if best is not None and order_seeds and order is None and slices is None:
         for seed in order_seeds:
             if time.perf_counter() - t_start > budget_s + 30.0:

@@ -808,23 +808,33 @@ void schedule_levels(Plan &p) {
     }
 }
 
+// Algorithmic work of one step of one work item: real flops (8 per complex multiply-add,
+// 2 per complex add of a one-operand sum) and complex64 bytes (operands read once, output
+// written once).
+void step_work(const Plan &p, const PStep &s, double *fl, double *by) {
+    const auto &A = p.tensors[s.a].modes;
+    const auto &C = p.tensors[s.c].modes;
+    if (s.b < 0) {
+        *fl = 2.0 * std::ldexp(1.0, (int)A.size());
+        *by = 8.0 * (std::ldexp(1.0, (int)A.size()) + std::ldexp(1.0, (int)C.size()));
+    } else {
+        const auto &B = p.tensors[s.b].modes;
+        const int u = (int)(C.size() + s.k_ab.size() + s.k_a.size() + s.k_b.size());
+        *fl = 8.0 * std::ldexp(1.0, u);
+        *by = 8.0 * (std::ldexp(1.0, (int)A.size()) + std::ldexp(1.0, (int)B.size()) +
+                     std::ldexp(1.0, (int)C.size()));
+    }
+}
+
 void program_stats(Plan &p) {
     double fl = 0, by = 0;
     int mr = 0;
     for (const PStep &s : p.steps) {
-        const auto &A = p.tensors[s.a].modes;
-        const auto &C = p.tensors[s.c].modes;
-        mr = std::max(mr, (int)C.size());
-        if (s.b < 0) {
-            fl += 2.0 * std::ldexp(1.0, (int)A.size());
-            by += 8.0 * (std::ldexp(1.0, (int)A.size()) + std::ldexp(1.0, (int)C.size()));
-        } else {
-            const auto &B = p.tensors[s.b].modes;
-            int u = (int)(C.size() + s.k_ab.size() + s.k_a.size() + s.k_b.size());
-            fl += 8.0 * std::ldexp(1.0, u);
-            by += 8.0 * (std::ldexp(1.0, (int)A.size()) + std::ldexp(1.0, (int)B.size()) +
-                         std::ldexp(1.0, (int)C.size()));
-        }
+        double f, b;
+        step_work(p, s, &f, &b);
+        fl += f;
+        by += b;
+        mr = std::max(mr, (int)p.tensors[s.c].modes.size());
     }
     p.flops_per_item = fl;
     p.bytes_per_item = by;
@@ -1689,19 +1699,8 @@ bool build_program(Plan &p, std::string *err) {
 double plan_estimate(const Plan &p) {
     double t = 0;
     for (const PStep &s : p.steps) {
-        const auto &A = p.tensors[s.a].modes;
-        const auto &C = p.tensors[s.c].modes;
         double fl, by;
-        if (s.b < 0) {
-            fl = 2.0 * std::ldexp(1.0, (int)A.size());
-            by = 8.0 * (std::ldexp(1.0, (int)A.size()) + std::ldexp(1.0, (int)C.size()));
-        } else {
-            const auto &B = p.tensors[s.b].modes;
-            int u = (int)(C.size() + s.k_ab.size() + s.k_a.size() + s.k_b.size());
-            fl = 8.0 * std::ldexp(1.0, u);
-            by = 8.0 * (std::ldexp(1.0, (int)A.size()) + std::ldexp(1.0, (int)B.size()) +
-                        std::ldexp(1.0, (int)C.size()));
-        }
+        step_work(p, s, &fl, &by);
         t += std::max(by, fl / 12.0);
     }
     return t * std::ldexp(1.0, (int)p.slices.size() - p.n_inner);

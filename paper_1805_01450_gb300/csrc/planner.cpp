@@ -5,6 +5,7 @@
 #include <cstring>
 #include <atomic>
 #include <functional>
+#include <system_error>
 #include <thread>
 #include <numeric>
 #include <unordered_map>
@@ -1725,45 +1726,70 @@ qvx_status make_plan(const qvx_circuit *c, const int32_t *order, int32_t n_order
     const bool fixed = n_order > 0 && n_slices >= 0;
     const int trials = fixed ? 1 : std::max(1, opts.plan_trials);
     if (trials == 1) return plan_once(c, order, n_order, slices, n_slices, opts, p, err);
-    // trials are independent: run them on host threads, then keep the best (lowest trial
-    // index among equal estimates, so the result does not depend on the thread count)
-    std::vector<Plan> cand(trials);
+    // trials are independent: run them on host threads. Each thread keeps only its best
+    // plan so far (at most one plan per thread besides the one being built); the best
+    // overall is the lowest estimate, ties to the lowest trial index, so the result does not
+    // depend on the thread count. Ranking fused-engine plans by their level count first was
+    // measured on 6x6x25 (12 sliced, 5 open, 8 warps per item): 12 levels with twice the
+    // bytes took 21.6 us per amplitude against 18.6 us for 15 levels, so the estimate alone
+    // ranks.
+    struct Best {
+        int t = -1;
+        double est = 0;
+        Plan plan;
+    };
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int n_threads = (int)std::min<unsigned>(std::min<unsigned>(hw, 16u), (unsigned)trials);
+    std::vector<Best> best(n_threads);
     std::vector<std::string> errs(trials);
     std::vector<qvx_status> st(trials, QVX_EUNSUPPORTED);
     std::vector<char> oom(trials, 0);
     std::atomic<int> next{0};
-    auto work = [&]() {
+    auto work = [&](int w) {
         for (int t = next++; t < trials; t = next++) {
             qvx_plan_opts o = opts;
             o.order_seed = opts.order_seed + uint64_t(t) * 0xD1B54A32D192ED03ull;
             try {
-                st[t] = plan_once(c, order, n_order, slices, n_slices, o, &cand[t], &errs[t]);
+                Plan cand;
+                st[t] = plan_once(c, order, n_order, slices, n_slices, o, &cand, &errs[t]);
+                if (st[t] != QVX_OK) continue;
+                const double est = plan_estimate(cand);
+                Best &b = best[w];
+                if (b.t < 0 || est < b.est || (est == b.est && t < b.t)) {
+                    b.t = t;
+                    b.est = est;
+                    b.plan = std::move(cand);
+                }
             } catch (const std::bad_alloc &) {
                 oom[t] = 1;
+            } catch (const std::exception &e) {
+                st[t] = QVX_EUNSUPPORTED;
+                errs[t] = e.what();
             }
-            if (st[t] != QVX_OK) cand[t] = Plan();
         }
     };
-    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-    const int n_threads = (int)std::min<unsigned>(std::min<unsigned>(hw, 16u), (unsigned)trials);
     std::vector<std::thread> pool;
-    for (int i = 1; i < n_threads; i++) pool.emplace_back(work);
-    work();
+    for (int i = 1; i < n_threads; i++) {
+        try {
+            pool.emplace_back(work, i);
+        } catch (const std::system_error &) {
+            break;   // fewer threads: the calling thread takes the remaining trials
+        }
+    }
+    work(0);
     for (auto &th : pool) th.join();
-    // rank by the bandwidth-weighted estimate alone. Ranking fused-engine plans by their
-    // level count first was measured on 6x6x25 (12 sliced, 5 open, 8 warps per item): 12
-    // levels with twice the bytes took 21.6 us per amplitude against 18.6 us for 15 levels
-    int best = -1;
-    double best_est = 0;
     for (int t = 0; t < trials; t++) {
         if (oom[t]) throw std::bad_alloc();
         if (st[t] != QVX_OK && st[t] != QVX_EUNSUPPORTED) { *err = errs[t]; return st[t]; }  // bad input
-        if (st[t] != QVX_OK) continue;
-        const double est = plan_estimate(cand[t]);
-        if (best < 0 || est < best_est) { best = t; best_est = est; }
     }
-    if (best < 0) { *err = errs[0]; return QVX_EUNSUPPORTED; }
-    *p = std::move(cand[best]);
+    int bw = -1;
+    for (int w = 0; w < n_threads; w++) {
+        const Best &b = best[w];
+        if (b.t < 0) continue;
+        if (bw < 0 || b.est < best[bw].est || (b.est == best[bw].est && b.t < best[bw].t)) bw = w;
+    }
+    if (bw < 0) { *err = errs[0]; return QVX_EUNSUPPORTED; }
+    *p = std::move(best[bw].plan);
     return QVX_OK;
 }
 

@@ -231,6 +231,8 @@ GRAD_CASES = [
     ("rot2x3d4-k3", lambda: cg.rotation_circuit(2, 3, 4, 12), dict(n_slices=3, inner_slices=1)),
     ("rot3x3d3-k4-merge", lambda: cg.rotation_circuit(3, 3, 3, 7), dict(n_slices=4, inner_slices=2,
                                                                         host_merge_rank=8)),
+    ("rot3x3d3-k4-trials", lambda: cg.rotation_circuit(3, 3, 3, 7), dict(n_slices=4, inner_slices=2,
+                                                                         plan_trials=8)),
     ("one-rotation", lambda: cg.Circuit(n_qubits=1, gates=[cg.Gate(cg.RXY, 0, theta=0.9, phi=0.0, param=0)]), dict()),
 ]
 

@@ -297,7 +297,10 @@ double order_cost(const Graph &g0, const std::vector<int> &order, const std::vec
 }
 
 // Greedy min-fill elimination order with random tie-breaks (stand-in for QuickBB's
-// min-fill branching, Section 3.B.3).
+// min-fill branching, Section 3.B.3). Each vertex's fill-in (pairs of its neighbours not yet
+// joined) and degree are cached; eliminating v changes them only for v's neighbours (their
+// neighbourhoods change) and for the neighbours of those (edges appear among v's
+// neighbours), so only that two-hop set is recomputed.
 double minfill_order(const Graph &g0, const std::vector<char> &removed, uint64_t seed,
                      std::vector<int> *order, int *width) {
     Graph g = g0;
@@ -307,47 +310,79 @@ double minfill_order(const Graph &g0, const std::vector<char> &removed, uint64_t
     }
     for (int v = 0; v < g.n; v++)
         if (!removed[v]) alive.push_back(v);
+    auto fill_of = [&](int v) {
+        const uint64_t *rv = g.row(v);
+        long fill = 0;
+        for (int w = 0; w < g.W; w++) {
+            uint64_t m = rv[w];
+            while (m) {
+                int u = w * 64 + __builtin_ctzll(m);
+                m &= m - 1;
+                const uint64_t *ru = g.row(u);
+                for (int x = 0; x < g.W; x++) fill += __builtin_popcountll(rv[x] & ~ru[x]);
+                fill -= 1;  // u itself
+            }
+        }
+        return fill / 2;
+    };
+    std::vector<long> fill(g.n, 0);
+    std::vector<int> deg(g.n, 0);
+    for (int v : alive) {
+        fill[v] = fill_of(v);
+        deg[v] = g.degree(v);
+    }
     order->clear();
     double cost = 0;
     int wd = 0;
     uint64_t rng = seed;
     std::vector<int> ties;
+    std::vector<uint64_t> touched(g.W);
     while (!alive.empty()) {
         long best_fill = -1;
         int best_deg = 0;
         ties.clear();
         for (int v : alive) {
-            const uint64_t *rv = g.row(v);
-            int deg = g.degree(v);
-            long fill = 0;
-            if (best_fill >= 0 && (long)deg * (deg - 1) / 2 < 0) continue;
-            for (int w = 0; w < g.W; w++) {
-                uint64_t m = rv[w];
-                while (m) {
-                    int u = w * 64 + __builtin_ctzll(m);
-                    m &= m - 1;
-                    const uint64_t *ru = g.row(u);
-                    for (int x = 0; x < g.W; x++) fill += __builtin_popcountll(rv[x] & ~ru[x]);
-                    fill -= 1;  // u itself
-                }
-            }
-            fill /= 2;
-            if (best_fill < 0 || fill < best_fill || (fill == best_fill && deg < best_deg)) {
-                best_fill = fill;
-                best_deg = deg;
+            if (best_fill < 0 || fill[v] < best_fill || (fill[v] == best_fill && deg[v] < best_deg)) {
+                best_fill = fill[v];
+                best_deg = deg[v];
                 ties.clear();
                 ties.push_back(v);
-            } else if (fill == best_fill && deg == best_deg) {
+            } else if (fill[v] == best_fill && deg[v] == best_deg) {
                 ties.push_back(v);
             }
         }
         int pick = ties[splitmix64(rng) % ties.size()];
-        int d = g.degree(pick);
+        int d = deg[pick];
         cost += std::ldexp(1.0, d);
         wd = std::max(wd, d);
+        // the two-hop set of pick (before its removal the neighbours are its row)
+        std::fill(touched.begin(), touched.end(), 0ull);
+        const uint64_t *rp = g.row(pick);
+        for (int w = 0; w < g.W; w++) {
+            uint64_t m = rp[w];
+            touched[w] |= m;
+            while (m) {
+                int u = w * 64 + __builtin_ctzll(m);
+                m &= m - 1;
+                const uint64_t *ru = g.row(u);
+                for (int x = 0; x < g.W; x++) touched[x] |= ru[x];
+            }
+        }
         g.eliminate(pick);
         order->push_back(pick);
         alive.erase(std::find(alive.begin(), alive.end(), pick));
+        touched[pick >> 6] &= ~(1ull << (pick & 63));
+        // neighbours of the neighbours after the join: the join adds no vertex outside the
+        // set above, since every new edge joins two former neighbours of pick
+        for (int w = 0; w < g.W; w++) {
+            uint64_t m = touched[w];
+            while (m) {
+                int u = w * 64 + __builtin_ctzll(m);
+                m &= m - 1;
+                fill[u] = fill_of(u);
+                deg[u] = g.degree(u);
+            }
+        }
     }
     if (width) *width = wd;
     return cost;

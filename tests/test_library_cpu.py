@@ -50,6 +50,57 @@ def test_plan_order_cost_matches_oracle_graph_ops():
     assert sorted(p.order + p.slices) == list(range(len(m.variables)))
 
 
+M64 = (1 << 64) - 1
+
+
+def _splitmix64(state):
+    state = (state + 0x9E3779B97F4A7C15) & M64
+    z = state
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
+    return state, z ^ (z >> 31)
+
+
+def _minfill_from_definition(adj, seed):
+    # greedy min-fill: eliminate a vertex whose neighbours miss the fewest edges among
+    # themselves, then the smallest degree; among equals (in increasing vertex id) pick with
+    # the seeded splitmix64 stream; every fill value recomputed from the graph at every step
+    alive = [v for v in range(len(adj))]
+    rng, order = seed, []
+    while alive:
+        best, ties = None, []
+        for v in alive:
+            nb = sorted(adj[v])
+            fill = sum(1 for i in range(len(nb)) for j in range(i + 1, len(nb)) if nb[j] not in adj[nb[i]])
+            key = (fill, len(nb))
+            if best is None or key < best:
+                best, ties = key, [v]
+            elif key == best:
+                ties.append(v)
+        rng, r = _splitmix64(rng)
+        pick = ties[r % len(ties)]
+        adj, _ = GR.eliminate_vertex(adj, pick)
+        order.append(pick)
+        alive.remove(pick)
+    return order
+
+
+@pytest.mark.parametrize("maker", [cg.worked_example, lambda: cg.grid_circuit(4, 4, 10, 1001),
+                                   lambda: cg.grid_circuit(3, 4, 16, 2)])
+@pytest.mark.parametrize("order_seed", [1, 7, 99])
+def test_planner_ordering_is_min_fill(maker, order_seed):
+    # one restart, nothing sliced: the plan's order is the min-fill order of the oracle's
+    # graph with the planner's tie-break stream (seed order_seed ^ 2 * golden ratio, one
+    # splitmix64 step for the restart's seed, one per pick)
+    c = maker()
+    p = q.Plan(c, n_slices=0, order_restarts=1, order_seed=order_seed)
+    m = GR.build(c)
+    adj = GR.adjacency(len(m.variables), GR.edges(m))
+    s = (order_seed ^ (2 * 0x9E3779B97F4A7C15)) & M64
+    _, seed = _splitmix64(s)
+    assert p.order == _minfill_from_definition(adj, seed)
+
+
 def test_greedy_slices_follow_section_3b2():
     # each greedy pick lowers the cost under the first order; the final cost is far below
     # the unsliced one

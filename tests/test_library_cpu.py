@@ -61,11 +61,12 @@ def _splitmix64(state):
     return state, z ^ (z >> 31)
 
 
-def _minfill_from_definition(adj, seed):
+def _minfill_from_definition(adj, seed, fixed=()):
     # greedy min-fill: eliminate a vertex whose neighbours miss the fewest edges among
     # themselves, then the smallest degree; among equals (in increasing vertex id) pick with
-    # the seeded splitmix64 stream; every fill value recomputed from the graph at every step
-    alive = [v for v in range(len(adj))]
+    # the seeded splitmix64 stream; every fill value recomputed from the graph at every step;
+    # fixed vertices are no longer in the graph
+    alive = [v for v in range(len(adj)) if v not in fixed]
     rng, order = seed, []
     while alive:
         best, ties = None, []
@@ -99,6 +100,40 @@ def test_planner_ordering_is_min_fill(maker, order_seed):
     s = (order_seed ^ (2 * 0x9E3779B97F4A7C15)) & M64
     _, seed = _splitmix64(s)
     assert p.order == _minfill_from_definition(adj, seed)
+
+
+@pytest.mark.parametrize("maker,k", [(lambda: cg.grid_circuit(4, 4, 10, 1001), 3),
+                                     (lambda: cg.grid_circuit(3, 4, 16, 2), 4)])
+def test_planner_slices_are_the_greedy_rule(maker, k):
+    # Section 3.B.2-3 from their definitions on the oracle's graph: the first order is
+    # min-fill (salt 1); each round fixes the vertex whose removal gives the smallest sum of
+    # 2^deg along that first order (ties to the lowest id); the final order is min-fill of
+    # the reduced graph (salt 2)
+    c = maker()
+    p = q.Plan(c, n_slices=k, inner_slices=0, order_restarts=1, order_seed=5)
+    m = GR.build(c)
+    adj = GR.adjacency(len(m.variables), GR.edges(m))
+    _, seed1 = _splitmix64((5 ^ 0x9E3779B97F4A7C15) & M64)
+    first = _minfill_from_definition(adj, seed1)
+    fixed = []
+    for _ in range(k):
+        best = None
+        for v in range(len(adj)):
+            if v in fixed:
+                continue
+            a = adj
+            for u in fixed + [v]:
+                a = GR.fix_vertex(a, u)
+            cost, _ = GR.order_cost(a, [u for u in first if u not in fixed and u != v])
+            if best is None or cost < best[0]:
+                best = (cost, v)
+        fixed.append(best[1])
+    assert p.slices == fixed
+    a = adj
+    for u in fixed:
+        a = GR.fix_vertex(a, u)
+    _, seed2 = _splitmix64((5 ^ (2 * 0x9E3779B97F4A7C15)) & M64)
+    assert p.order == _minfill_from_definition(a, seed2, fixed)
 
 
 def test_greedy_slices_follow_section_3b2():

@@ -77,6 +77,22 @@ def test_6x6x25_k12_full(inner, wpi, engine, merge):
     p.check_status(ws)
 
 
+def test_6x6x25_k12_bench_plan():
+    # the plan the benchmark times: order and slices from 64 planning trials (engine and
+    # open slices left to the planner, as the autotuner's base plan), then 5 open slices,
+    # 8 warps per item, host merging to rank 10 on the fused engine
+    c = cg.grid_circuit(6, 6, 25, 2001)
+    x = cg.random_bitstrings(36, 1, 2002)[0]
+    base = q.Plan(c, n_slices=12, mem_budget_bytes=1 << 30, plan_trials=64)
+    p = q.Plan(c, order=base.order, slices=base.slices, inner_slices=5, warps_per_item=8, host_merge_rank=10,
+               engine="fused", mem_budget_bytes=1 << 30, plan_trials=64)
+    ref_terms = VE.slice_terms(c, x, p.order, p.slices)
+    assert abs(_amps(p, [x])[0] - VE.exact_sum(ref_terms)) < tol(36)
+    terms = p.slice_terms([x]).cpu().numpy()[0]
+    assert np.max(np.abs(terms - ref_terms)) < tol(36)
+    p.check_status(p._ws_for(1, torch.device("cuda")))
+
+
 def test_6x6x25_ragged_slice_ranges_and_batch():
     c = cg.grid_circuit(6, 6, 25, 2001)
     xs = cg.random_bitstrings(36, 5, 77)

@@ -301,6 +301,26 @@ def test_program_slice_terms_6x6_sample(merge):
         assert np.max(np.abs(got - ref)) < 1e-6 * 2 ** -18
 
 
+def test_bench_plan_6x6_on_host():
+    # the plan the benchmark times on 6x6x25: 64 planning trials for the order and slices,
+    # then 5 open slices, 8 warps per item, leaf products to rank 10 merged on the host; its
+    # fused schedule is complete and its items' slice terms match the oracle's
+    c = cg.grid_circuit(6, 6, 25, 2001)
+    base = q.Plan(c, n_slices=12, mem_budget_bytes=1 << 30, plan_trials=64)
+    p = q.Plan(c, order=base.order, slices=base.slices, inner_slices=5, warps_per_item=8, host_merge_rank=10,
+               engine="fused", mem_budget_bytes=1 << 30, plan_trials=64)
+    assert p.info["engine"] == "fused" and p.info["n_inner"] == 5
+    prog = Program(p.image())
+    check_schedule(prog)
+    x = cg.random_bitstrings(36, 1, 2002)[0]
+    rng = random.Random(1)
+    for o in rng.sample(range(int(prog.h["n_outer"])), 2):
+        got = prog.item_terms(x, o, fused=True)
+        ids = [(o << 5) | i for i in range(32)]
+        ref = VE.slice_terms(c, x, p.order, p.slices, slice_ids=ids)
+        assert np.max(np.abs(got - ref)) < 1e-6 * 2 ** -18
+
+
 def test_host_merging_shortens_the_device_program():
     c = cg.grid_circuit(6, 6, 25, 2001)
     full = q.Plan(c, n_slices=12, inner_slices=4, host_merge_rank=0).info

@@ -1783,6 +1783,7 @@ qvx_status make_plan(const qvx_circuit *c, const int32_t *order, int32_t n_order
     auto work = [&](int w) {
         for (int t = next++; t < trials; t = next++) {
             qvx_plan_opts o = opts;
+            // trial t's seed: an odd 64-bit multiplier keeps the trials' seeds distinct
             o.order_seed = opts.order_seed + uint64_t(t) * 0xD1B54A32D192ED03ull;
             try {
                 Plan cand;

@@ -479,7 +479,10 @@ def _with_open_bits(x, open_qubits, j):
     return x
 
 
-@pytest.mark.parametrize("kw", [dict(), dict(n_slices=3, inner_slices=1), dict(n_slices=2, host_merge_rank=0)])
+@pytest.mark.parametrize("kw", [dict(), dict(n_slices=3, inner_slices=1), dict(n_slices=2, host_merge_rank=0),
+                                dict(n_slices=3, inner_slices=1, plan_trials=8),
+                                dict(n_slices=3, inner_slices=1, plan_trials=8, slice_rule="reorder",
+                                     engine="persistent")])
 def test_open_qubits_program_on_host(kw):
     # Section 6: batches of amplitudes from one contraction (open output variables)
     c = cg.grid_circuit(4, 4, 10, 1001)

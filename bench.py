@@ -48,8 +48,9 @@ METRIC = "amplitudes/s and complex TFLOP/s (% of GB300 peak) at |Δα|≤1e-5·2
 L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel (fused
 # program kernel; gradient kernel for the gradient workload), from one ncu capture of the
-# workload with the current kernels (profiles/ holds the summaries).
-NCU_TRAFFIC = {("grid6x6d25-k12", 1): 147968.0, ("rot5x5d20-grad", 1): 509184.0}
+# workload with the current kernels (profiles/ holds the summaries). Keyed by the plan it was
+# taken on (its device image size): another plan of the workload reports no traffic.
+NCU_TRAFFIC = {("grid6x6d25-k12", 1, 92416): 147968.0, ("rot5x5d20-grad", 1, 1793024): 509184.0}
 
 
 def parse():
@@ -385,7 +386,7 @@ def main():
         "complex_tflops": flops / (ms_step / 1e3) / 1e12,
         "abs_err": err, "err_bound": 1e-5 * 2.0 ** (-n / 2),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": NCU_TRAFFIC.get((args.workload, B)),
+                     "frac": achieved / peak, "traffic": NCU_TRAFFIC.get((args.workload, B, info["device_image_bytes"])),
                      "peak_source": peak_kind,
                      "kernel": kernel,
                      "algorithmic_bytes_per_launch": algo_bytes},

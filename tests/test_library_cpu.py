@@ -447,9 +447,15 @@ def test_planning_trials_keep_the_cheapest_valid_plan():
     # a given order and slice set leave nothing to try
     f = q.Plan(c, order=one.order, slices=one.slices, inner_slices=0, plan_trials=8)
     assert (f.order, f.slices) == (one.order, one.slices)
+    for bad in (0, 1025):
+        with pytest.raises(q.QvxError) as e:
+            q.Plan(c, n_slices=4, plan_trials=bad)
+        assert e.value.status == q.QVX_EINVAL
+    # a circuit the single-trial planner cannot fit under max_rank still fails cleanly when
+    # no trial fits either
     with pytest.raises(q.QvxError) as e:
-        q.Plan(c, n_slices=4, plan_trials=0)
-    assert e.value.status == q.QVX_EINVAL
+        q.Plan(c, n_slices=0, max_rank=6, plan_trials=4)
+    assert e.value.status == q.QVX_EUNSUPPORTED
 
 
 def test_planning_trials_program_matches_oracle():

@@ -23,8 +23,11 @@
  *   - Bitstrings: bit q of a uint64_t is the value of qubit q, so n_qubits <= 64.
  *   - Amplitudes: complex128, interleaved (re, im).
  *   - Errors: every call returns a qvx_status; qvx_last_error() gives a message for the
- *     calling thread's last failure. Failures inside kernels (a bounded wait that ran out,
- *     an index out of range) set the device status word, read by qvx_workspace_status.
+ *     calling thread's last failure. Failures inside kernels (a bounded wait that ran out, a
+ *     slice term or exact sum outside the exact range) set the device status word, read by
+ *     qvx_workspace_status; every amplitude written while it is set is NaN. Device indices
+ *     need no run-time check: every offset a kernel forms is a bit-run map of an index below
+ *     2^rank of the tensor it addresses, fixed when the plan is built.
  */
 #ifndef QVX_H
 #define QVX_H
@@ -43,7 +46,8 @@ typedef enum {
     QVX_ECUDA = 3,         /* a CUDA runtime call failed (message in qvx_last_error) */
     QVX_ETIMEOUT = 4,      /* a bounded device wait ran out (device status word) */
     QVX_EUNSUPPORTED = 5,  /* a gate, rank or size outside what the plan can run */
-    QVX_EDEVICE = 6        /* a kernel reported an out-of-range index (device status word) */
+    QVX_ERANGE = 6         /* a slice term or an exact partial sum was not finite or had magnitude
+                              2^27 or more, outside the 128-bit fixed-point sum (device status word) */
 } qvx_status;
 
 /* Gate kinds (matrices indexed [output, input]):
@@ -236,9 +240,16 @@ qvx_status qvx_slice_terms(qvx_plan *plan, const uint64_t *bitstrings_dev, int64
  * with QVX_EINVAL. The first call on a device also looks up the array's device address
  * (cudaGetSymbolAddress), so make that first call before any stream capture. All calls
  * share the one array and each call overwrites it: calls that overlap on the GPU (other
- * streams, other threads) race and must be serialised by the caller. */
+ * streams, other threads) race and must be serialised by the caller. The array's status
+ * word records a kernel failure (QVX_ETIMEOUT, QVX_ERANGE) and is not cleared by the next
+ * call: read it with qvx_noalloc_status; while it is set, amplitudes are written as NaN. */
 qvx_status qvx_amplitude_noalloc(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch,
                                  double *amps_dev, void *stream);
+
+/* Companion of qvx_amplitude_noalloc (no paper counterpart): synchronises `stream`, returns
+ * the status word of the current device's fixed array (QVX_OK if it is clear or no call has
+ * run on the device yet) and clears it. Allocates nothing. */
+qvx_status qvx_noalloc_status(void *stream);
 
 /* alpha_b = <x_b|C|0> and its derivatives d alpha_b / d theta_p with respect to the angles
  * of the RXY gates (adjoint of the pairwise contractions: each gate's environment tensor
@@ -263,11 +274,54 @@ qvx_status qvx_selftest_wait_timeout(const qvx_plan *plan, void *workspace_dev, 
                                      uint32_t polls, void *stream);
 
 /* Synchronises `stream` and returns the device status word kept in the workspace
- * (QVX_OK, QVX_ETIMEOUT or QVX_EDEVICE), then clears it. */
+ * (QVX_OK, QVX_ETIMEOUT or QVX_ERANGE), then clears it. */
 qvx_status qvx_workspace_status(const qvx_plan *plan, void *workspace_dev, void *stream);
 
 /* Message for the calling thread's last failed call ("" if none). */
 const char *qvx_last_error(void);
+
+/* Kernels of the library, as named in qvx_launch_record.kernel. */
+typedef enum {
+    QVX_KERNEL_FUSED = 0,       /* fused_program_kernel: whole program per work item, shared memory */
+    QVX_KERNEL_PERSISTENT = 1,  /* persistent_program_kernel */
+    QVX_KERNEL_STEP = 2,        /* step_kernel: one thread per output entry */
+    QVX_KERNEL_STEP_GROUP = 3,  /* step_group_kernel: several small steps of one level */
+    QVX_KERNEL_SPLITK = 4,      /* splitk_step_kernel */
+    QVX_KERNEL_REGTILE = 5,     /* regtile_step_kernel: register-tiled SIMT contraction */
+    QVX_KERNEL_GEMM_TC = 6,     /* gemm_tc_kernel: tcgen05 tensor-core contraction */
+    QVX_KERNEL_FINISH = 7,      /* finish_kernel: exact sums of the items' final tensors */
+    QVX_KERNEL_SLICE_SUM = 8    /* slice_sum_kernel: exact sum over the slice terms */
+} qvx_kernel_id;
+
+/* One kernel launch of a profiled call. */
+typedef struct {
+    int32_t kernel;        /* qvx_kernel_id */
+    int32_t step;          /* program step of a single-step launch, else -1 */
+    int64_t items;         /* work items the launch processed (sums: partials added) */
+    double flops;          /* algorithmic real flops of the launch (8 per complex MAC) */
+    double bytes;          /* algorithmic bytes of the launch: each operand read and each
+                              output written once (complex64; 32-byte exact partials) */
+    float ms;              /* device time between CUDA events recorded on the call's stream
+                              just before and just after the launch */
+    int32_t pad;
+} qvx_launch_record;
+
+/* qvx_amplitude (the whole slice range) with a CUDA event recorded on `stream` just before
+ * and just after every kernel launch, for measuring each kernel against its roofline. The
+ * launches are appended to the plan's launch log; nothing is synchronised. No paper
+ * counterpart: instrumentation of this implementation. The events belong to the plan
+ * (created on first use on the current device, freed by qvx_plan_destroy); the log holds
+ * at most about 2^20 launches (QVX_ENOMEM beyond: read it first). */
+qvx_status qvx_amplitude_profiled(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch, double *amps_dev,
+                                  void *workspace_dev, size_t workspace_bytes, void *stream);
+
+/* Waits for the logged launches' events, then records[i] (i < cap) describes logged launch i
+ * in issue order (its ms filled in), *n_records is the number of logged launches (which may
+ * exceed cap), and the log is emptied. With cap = 0 only *n_records is set and the log stays. */
+qvx_status qvx_profile_read(qvx_plan *plan, qvx_launch_record *records, int64_t cap, int64_t *n_records);
+
+/* The name of kernel id `kernel` (a qvx_kernel_id value), or "" if unknown. */
+const char *qvx_kernel_name(int32_t kernel);
 
 /* Kernels the calling host thread has launched through the library so far (successful
  * launches only; a count, not device work). Reading it before and after a call gives that

@@ -16,7 +16,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libqvx.so")
 
-QVX_OK, QVX_EINVAL, QVX_ENOMEM, QVX_ECUDA, QVX_ETIMEOUT, QVX_EUNSUPPORTED, QVX_EDEVICE = range(7)
+QVX_OK, QVX_EINVAL, QVX_ENOMEM, QVX_ECUDA, QVX_ETIMEOUT, QVX_EUNSUPPORTED, QVX_ERANGE = range(7)
 ENGINES = {"auto": 0, "fused": 1, "stepwise": 2, "persistent": 3}
 ENGINE_NAMES = {v: k for k, v in ENGINES.items()}
 
@@ -65,12 +65,19 @@ class PlanInfo(ctypes.Structure):
                 ("est_bytes_per_amplitude", ctypes.c_double)]
 
 
+class LaunchRecord(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("step", ctypes.c_int32), ("items", ctypes.c_int64),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double), ("ms", ctypes.c_float),
+                ("pad", ctypes.c_int32)]
+
+
 _lib = None
 EXPORTED = ("qvx_plan_opts_default", "qvx_graph_export", "qvx_plan_create", "qvx_plan_destroy",
             "qvx_plan_get_info", "qvx_plan_get_order", "qvx_plan_get_image", "qvx_workspace_size", "qvx_workspace_init",
             "qvx_amplitude", "qvx_amplitude_slices", "qvx_slice_terms", "qvx_workspace_status",
             "qvx_last_error", "qvx_amplitude_noalloc", "qvx_amplitude_grad", "qvx_amplitude_host",
-            "qvx_selftest_wait_timeout", "qvx_kernel_launches")
+            "qvx_selftest_wait_timeout", "qvx_kernel_launches", "qvx_noalloc_status", "qvx_amplitude_profiled",
+            "qvx_profile_read", "qvx_kernel_name")
 
 
 def lib():
@@ -103,6 +110,10 @@ def lib():
         "qvx_amplitude_grad": (ctypes.c_int, [P, P, i64, P, i32, P, P, P, ctypes.c_size_t, P]),
         "qvx_amplitude_host": (ctypes.c_int, [P, P, i64, P, P, ctypes.c_size_t, P]),
         "qvx_selftest_wait_timeout": (ctypes.c_int, [P, P, ctypes.c_size_t, ctypes.c_uint32, P]),
+        "qvx_noalloc_status": (ctypes.c_int, [P]),
+        "qvx_amplitude_profiled": (ctypes.c_int, [P, P, i64, P, P, ctypes.c_size_t, P]),
+        "qvx_profile_read": (ctypes.c_int, [P, ctypes.POINTER(LaunchRecord), i64, ctypes.POINTER(ctypes.c_int64)]),
+        "qvx_kernel_name": (ctypes.c_char_p, [i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -381,6 +392,26 @@ class Plan:
                                      ws.numel(), _stream_ptr(stream)))
         t = torch.view_as_complex(out.view(n * m, slice_count, 2))
         return t.view(n, m, slice_count) if self.n_open else t.view(n, slice_count)
+
+    def amplitude_profiled(self, bits, workspace, out, stream=None):
+        """plan.amplitude over all slices (device int64 bitstrings, caller's workspace and
+        float64 output) with a CUDA event before and after every kernel launch, appended to
+        the plan's launch log (read_profile). Does not synchronise."""
+        _check(lib().qvx_amplitude_profiled(self._h, ctypes.c_void_p(bits.data_ptr()), bits.numel(),
+                                            ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(workspace.data_ptr()),
+                                            workspace.numel(), _stream_ptr(stream)))
+
+    def read_profile(self):
+        """The launch log of amplitude_profiled calls since the last read, in issue order: a
+        list of dicts (kernel name, step, items, algorithmic flops and bytes, ms); empties it."""
+        L = lib()
+        n = ctypes.c_int64()
+        _check(L.qvx_profile_read(self._h, None, 0, ctypes.byref(n)))   # the count; the log stays
+        cap = max(n.value, 1)
+        recs = (LaunchRecord * cap)()
+        _check(L.qvx_profile_read(self._h, recs, cap, ctypes.byref(n)))
+        return [dict(kernel=L.qvx_kernel_name(r.kernel).decode(), step=r.step, items=r.items, flops=r.flops,
+                     bytes=r.bytes, ms=r.ms) for r in recs[:min(n.value, cap)]]
 
     def check_status(self, workspace, stream=None):
         """Synchronises and raises if a kernel set the workspace's device status word."""

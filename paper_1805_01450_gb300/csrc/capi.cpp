@@ -87,6 +87,44 @@ qvx_status check_ws(const qvx_plan *plan, int64_t batch, void *ws, size_t ws_byt
     return QVX_OK;
 }
 
+// Per-launch CUDA events of profiled calls (qvx_amplitude_profiled): an event before and
+// after every launch on the call's stream, with the launch's kernel, step, work items and
+// algorithmic work appended to the plan's launch log; qvx_profile_read waits for the events
+// and turns them into durations.
+struct Profiler {
+    qvx_plan *plan;
+    cudaStream_t st;
+    cudaError_t err = cudaSuccess;
+
+    cudaEvent_t event(size_t i) {
+        while (plan->prof_events.size() <= i) {
+            cudaEvent_t ev;
+            cudaError_t e = cudaEventCreate(&ev);
+            if (e != cudaSuccess) {
+                err = e;
+                return nullptr;
+            }
+            plan->prof_events.push_back(ev);
+        }
+        return plan->prof_events[i];
+    }
+    void begin() {
+        cudaEvent_t ev = event(2 * plan->prof_log.size());
+        if (ev && err == cudaSuccess) err = cudaEventRecord(ev, st);
+    }
+    void end(int kernel, int step, int64_t items, double flops, double bytes) {
+        cudaEvent_t ev = event(2 * plan->prof_log.size() + 1);
+        if (ev && err == cudaSuccess) err = cudaEventRecord(ev, st);
+        qvx_launch_record r{};
+        r.kernel = kernel;
+        r.step = step;
+        r.items = items;
+        r.flops = flops;
+        r.bytes = bytes;
+        plan->prof_log.push_back(r);
+    }
+};
+
 struct PStepShape {
     int nk;
 };
@@ -100,7 +138,7 @@ PStepShape shape_of(const qvx::Plan &p, size_t s) {
 // With the fused engine and amps != nullptr the same launch also writes the amplitudes.
 qvx_status run_items(qvx_plan *plan, const uint64_t *bits, int64_t batch, int64_t s_begin,
                      int64_t s_end, float *terms, double *amps, void *ws, const WsLayout &w,
-                     cudaStream_t st, int64_t *o_count_out) {
+                     cudaStream_t st, int64_t *o_count_out, Profiler *prof = nullptr) {
     const qvx::Plan &p = plan->p;
     const int n_inner = p.n_inner;
     const int64_t o_begin = s_begin >> n_inner;
@@ -153,8 +191,10 @@ qvx_status run_items(qvx_plan *plan, const uint64_t *bits, int64_t batch, int64_
         if (plan->ctas_per_sm[ipc] < 1) return fail(QVX_EUNSUPPORTED, "fused kernel: no CTA fits on an SM");
         const int64_t ctas_needed = (n_items + ipc - 1) / ipc;
         const int grid = (int)std::min<int64_t>(ctas_needed, (int64_t)plan->sms * plan->ctas_per_sm[ipc]);
+        if (prof) prof->begin();
         if ((e = qvx::launch_fused(a, wpi, ipc, grid, shared + (size_t)ipc * group, st)) != cudaSuccess)
             return cuda_fail(e, "fused kernel launch");
+        if (prof) prof->end(QVX_KERNEL_FUSED, -1, n_items, p.flops_per_item * (double)n_items, p.bytes_per_item * (double)n_items);
         return QVX_OK;
     }
     float2 *arenas = reinterpret_cast<float2 *>(base + w.arenas);
@@ -173,11 +213,34 @@ qvx_status run_items(qvx_plan *plan, const uint64_t *bits, int64_t batch, int64_
         unsigned *bar = reinterpret_cast<unsigned *>(base + w.status) + 2;   // [count, generation]
         for (int64_t ib = 0; ib < n_items; ib += w.items_in_flight) {
             const int64_t n = std::min<int64_t>(w.items_in_flight, n_items - ib);
+            if (prof) prof->begin();
             if ((e = qvx::launch_persistent(a, ib, n, arenas, bar, bar + 1, plan->persist_grid, st)) != cudaSuccess)
                 return cuda_fail(e, "persistent kernel launch");
+            if (prof) prof->end(QVX_KERNEL_PERSISTENT, -1, n, p.flops_per_item * (double)n, p.bytes_per_item * (double)n);
         }
         return QVX_OK;
     }
+    auto cost = [&](size_t s, int64_t n, double *fl, double *by) {
+        qvx::step_cost(p, s, fl, by);
+        *fl *= (double)n;
+        *by *= (double)n;
+    };
+    // one launch of a single step s (its kind chosen as below), timed when profiling
+    auto single = [&](int s, int kind, int64_t ib, int64_t n) -> cudaError_t {
+        const uint32_t rc = (uint32_t)p.tensors[p.steps[s].c].modes.size();
+        if (prof) prof->begin();
+        cudaError_t r;
+        if (kind == QVX_KERNEL_GEMM_TC) r = qvx::launch_gemm_step(a, p.gemm[s], ib, n, arenas, st);
+        else if (kind == QVX_KERNEL_SPLITK) r = qvx::launch_splitk_step(a, (uint32_t)s, ib, n, arenas, rc, st);
+        else if (kind == QVX_KERNEL_REGTILE) r = qvx::launch_regtile_step(a, p.regtile[s], ib, n, arenas, st);
+        else r = qvx::launch_step(a, (uint32_t)s, ib, n, arenas, rc, st);
+        if (prof && r == cudaSuccess) {
+            double fl, by;
+            cost((size_t)s, n, &fl, &by);
+            prof->end(kind, s, n, fl, by);
+        }
+        return r;
+    };
     for (int64_t ib = 0; ib < n_items; ib += w.items_in_flight) {
         const int64_t n = std::min<int64_t>(w.items_in_flight, n_items - ib);
         for (const auto &ph : p.phases) {
@@ -191,7 +254,7 @@ qvx_status run_items(qvx_plan *plan, const uint64_t *bits, int64_t batch, int64_
                 const uint64_t threads = (uint64_t)n << rc;
                 const bool splitk = sh.nk >= 5 && rc <= 12;
                 if (!p.gemm.empty() && p.gemm[s].nk > 0) {   // tensor cores
-                    if ((e = qvx::launch_gemm_step(a, p.gemm[s], ib, n, arenas, st)) != cudaSuccess)
+                    if ((e = single(s, QVX_KERNEL_GEMM_TC, ib, n)) != cudaSuccess)
                         return cuda_fail(e, "tensor-core step launch");
                     continue;
                 }
@@ -201,24 +264,38 @@ qvx_status run_items(qvx_plan *plan, const uint64_t *bits, int64_t batch, int64_
                     grp.n++;
                     continue;
                 }
-                if (splitk) e = qvx::launch_splitk_step(a, (uint32_t)s, ib, n, arenas, rc, st);
-                else if (p.regtile[s].rm + p.regtile[s].rn > 0) e = qvx::launch_regtile_step(a, p.regtile[s], ib, n, arenas, st);
-                else e = qvx::launch_step(a, (uint32_t)s, ib, n, arenas, rc, st);
-                if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+                const int kind = splitk ? QVX_KERNEL_SPLITK
+                                        : (p.regtile[s].rm + p.regtile[s].rn > 0 ? QVX_KERNEL_REGTILE : QVX_KERNEL_STEP);
+                if ((e = single(s, kind, ib, n)) != cudaSuccess) return cuda_fail(e, "step kernel launch");
             }
             if (grp.n == 1) {
                 const int s = (int)grp.step[0];
-                const uint32_t rc = (uint32_t)p.tensors[p.steps[s].c].modes.size();
-                if (p.regtile[s].rm + p.regtile[s].rn > 0) e = qvx::launch_regtile_step(a, p.regtile[s], ib, n, arenas, st);
-                else e = qvx::launch_step(a, (uint32_t)s, ib, n, arenas, rc, st);
-                if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+                const int kind = p.regtile[s].rm + p.regtile[s].rn > 0 ? QVX_KERNEL_REGTILE : QVX_KERNEL_STEP;
+                if ((e = single(s, kind, ib, n)) != cudaSuccess) return cuda_fail(e, "step kernel launch");
             } else if (grp.n > 1) {
+                if (prof) prof->begin();
                 if ((e = qvx::launch_step_group(a, grp, ib, n, arenas, st)) != cudaSuccess)
                     return cuda_fail(e, "step group launch");
+                if (prof) {
+                    double fl = 0, by = 0;
+                    for (uint32_t j = 0; j < grp.n; j++) {
+                        double f1, b1;
+                        cost(grp.step[j], n, &f1, &b1);
+                        fl += f1;
+                        by += b1;
+                    }
+                    prof->end(QVX_KERNEL_STEP_GROUP, -1, n, fl, by);
+                }
             }
         }
+        if (prof) prof->begin();
         if ((e = qvx::launch_finish_items(a, ib, n, arenas, st)) != cudaSuccess)
             return cuda_fail(e, "finish kernel launch");
+        if (prof) {
+            const double fin = std::ldexp(8.0, (int)p.tensors[p.final_tensor].modes.size());
+            prof->end(QVX_KERNEL_FINISH, -1, n, 0.0,
+                      (double)n * (fin + (double)sizeof(qvx::ExactPair) * std::ldexp(1.0, (int)p.open_qubits.size())));
+        }
     }
     return QVX_OK;
 }
@@ -389,9 +466,12 @@ qvx_status qvx_workspace_init(const qvx_plan *plan, void *ws, size_t ws_bytes, v
     return QVX_OK;
 }
 
-qvx_status qvx_amplitude_slices(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch,
-                                int64_t slice_begin, int64_t slice_count, double *amps_dev,
-                                void *ws, size_t ws_bytes, void *stream) {
+}  // extern "C"
+
+namespace {
+qvx_status amplitude_slices_impl(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch, int64_t slice_begin,
+                                 int64_t slice_count, double *amps_dev, void *ws, size_t ws_bytes, void *stream,
+                                 Profiler *prof) {
     WsLayout w;
     qvx_status s = check_ws(plan, batch, ws, ws_bytes, &w);
     if (s != QVX_OK) return s;
@@ -407,15 +487,80 @@ qvx_status qvx_amplitude_slices(qvx_plan *plan, const uint64_t *bitstrings_dev, 
     }
     int64_t o_count = 0;
     s = run_items(plan, bitstrings_dev, batch, slice_begin, slice_begin + slice_count, nullptr, amps_dev, ws, w,
-                  st, &o_count);
+                  st, &o_count, prof);
     if (s != QVX_OK) return s;
     if (plan->p.engine == QVX_ENGINE_FUSED) return QVX_OK;   // the fused launch wrote the sums
     unsigned char *base = static_cast<unsigned char *>(ws);
+    const int64_t slots = batch << plan->p.open_qubits.size();
+    if (prof) prof->begin();
     if ((e = qvx::launch_slice_sum(base + w.image, reinterpret_cast<const qvx::ExactPair *>(base + w.partials),
                                    batch << plan->p.open_qubits.size(), o_count,
-                                   amps_dev, st)) != cudaSuccess)
+                                   amps_dev, reinterpret_cast<unsigned *>(base + w.status), st)) != cudaSuccess)
         return cuda_fail(e, "slice sum launch");
+    if (prof)
+        prof->end(QVX_KERNEL_SLICE_SUM, -1, slots * o_count, 0.0,
+                  (double)slots * ((double)o_count * (double)sizeof(qvx::ExactPair) + 16.0));
     return QVX_OK;
+}
+}  // namespace
+
+extern "C" {
+
+qvx_status qvx_amplitude_slices(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch,
+                                int64_t slice_begin, int64_t slice_count, double *amps_dev,
+                                void *ws, size_t ws_bytes, void *stream) {
+    return amplitude_slices_impl(plan, bitstrings_dev, batch, slice_begin, slice_count, amps_dev, ws, ws_bytes, stream,
+                                 nullptr);
+}
+
+qvx_status qvx_amplitude_profiled(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch, double *amps_dev,
+                                  void *ws, size_t ws_bytes, void *stream) {
+    if (!plan) return fail(QVX_EINVAL, "null plan");
+    if (plan->prof_log.size() > (size_t(1) << 20)) return fail(QVX_ENOMEM, "launch log full: read it first");
+    Profiler prof{plan, static_cast<cudaStream_t>(stream)};
+    qvx_status s = amplitude_slices_impl(plan, bitstrings_dev, batch, 0, int64_t(1) << plan->p.slices.size(), amps_dev,
+                                         ws, ws_bytes, stream, &prof);
+    if (s != QVX_OK) return s;
+    if (prof.err != cudaSuccess) return cuda_fail(prof.err, "profiling event");
+    return QVX_OK;
+}
+
+qvx_status qvx_profile_read(qvx_plan *plan, qvx_launch_record *records, int64_t cap, int64_t *n_records) {
+    if (!plan) return fail(QVX_EINVAL, "null plan");
+    if (cap < 0 || (cap > 0 && !records)) return fail(QVX_EINVAL, "records: null with a positive capacity");
+    if (cap == 0) {   // the count only; the log stays
+        if (n_records) *n_records = (int64_t)plan->prof_log.size();
+        return QVX_OK;
+    }
+    std::vector<qvx_launch_record> log;
+    log.swap(plan->prof_log);
+    cudaError_t e;
+    for (size_t i = 0; i < log.size(); i++) {
+        if ((e = cudaEventSynchronize(plan->prof_events[2 * i + 1])) != cudaSuccess)
+            return cuda_fail(e, "cudaEventSynchronize");
+        float ms = 0.f;
+        if ((e = cudaEventElapsedTime(&ms, plan->prof_events[2 * i], plan->prof_events[2 * i + 1])) != cudaSuccess)
+            return cuda_fail(e, "cudaEventElapsedTime");
+        log[i].ms = ms;
+        if ((int64_t)i < cap) records[i] = log[i];
+    }
+    if (n_records) *n_records = (int64_t)log.size();
+    return QVX_OK;
+}
+
+const char *qvx_kernel_name(int32_t kernel) {
+    switch (kernel) {
+        case QVX_KERNEL_FUSED: return "fused_program_kernel";
+        case QVX_KERNEL_PERSISTENT: return "persistent_program_kernel";
+        case QVX_KERNEL_STEP: return "step_kernel";
+        case QVX_KERNEL_STEP_GROUP: return "step_group_kernel";
+        case QVX_KERNEL_SPLITK: return "splitk_step_kernel";
+        case QVX_KERNEL_REGTILE: return "regtile_step_kernel";
+        case QVX_KERNEL_GEMM_TC: return "gemm_tc_kernel";
+        case QVX_KERNEL_FINISH: return "finish_kernel";
+        case QVX_KERNEL_SLICE_SUM: return "slice_sum_kernel";
+        default: return "";
+    }
 }
 
 namespace {
@@ -544,10 +689,10 @@ qvx_status qvx_amplitude_grad(qvx_plan *plan, const uint64_t *bitstrings_dev, in
         const int grid = (int)std::min<int64_t>(batch * n_outer, w.grad_slots);
         if ((e = qvx::launch_grad_program(g, grid, st)) != cudaSuccess) return cuda_fail(e, "gradient kernel launch");
     }
-    if ((e = qvx::launch_slice_sum(base + w.image, g.partials, batch, n_outer, amps_dev, st)) != cudaSuccess)
+    if ((e = qvx::launch_slice_sum(base + w.image, g.partials, batch, n_outer, amps_dev, g.status, st)) != cudaSuccess)
         return cuda_fail(e, "slice sum launch");
     if ((e = qvx::launch_grad_sum(base + w.image, g.gpart, batch, n_outer, h->n_param_leaves, (uint32_t)p.n_params,
-                                  grad_dev, st)) != cudaSuccess)
+                                  grad_dev, g.status, st)) != cudaSuccess)
         return cuda_fail(e, "gradient sum launch");
     return QVX_OK;
 }

@@ -51,17 +51,24 @@ struct Fx {
     long long hi;
 };
 
-__device__ __forceinline__ Fx fx_from_float(float f) {
+constexpr unsigned kStatusRange = 6u;   // QVX_ERANGE
+
+// X = t * 2^100 as a 128-bit integer. A term that is not finite or has |t| >= 2^27 has no
+// such form: it contributes nothing and sets `bad`, which the caller reports as QVX_ERANGE.
+__device__ __forceinline__ Fx fx_from_float(float f, bool &bad) {
     const uint32_t bits = __float_as_uint(f);
     uint32_t e = (bits >> 23) & 0xffu;
     unsigned long long m = bits & 0x7fffffu;
     Fx r;
     r.lo = 0;
     r.hi = 0;
-    if (e == 0xffu) return r;          // not finite: contributes nothing
+    if (e >= 154u) {                   // |t| >= 2^27, infinite or NaN
+        bad = true;
+        return r;
+    }
     if (e) m |= 0x800000u;
     else e = 1;
-    const int sh = (int)e - 50;        // t = m 2^(e-150), X = m 2^(e-50)
+    const int sh = (int)e - 50;        // t = m 2^(e-150), X = m 2^(e-50); sh <= 103
     if (sh >= 64) {
         r.hi = (long long)(m << (sh - 64));
     } else if (sh > 0) {
@@ -72,15 +79,18 @@ __device__ __forceinline__ Fx fx_from_float(float f) {
     }
     if (bits >> 31) {                  // two's-complement negation
         r.lo = ~r.lo + 1ull;
-        r.hi = ~r.hi + (r.lo == 0 ? 1 : 0);
+        r.hi = (long long)(~(unsigned long long)r.hi + (r.lo == 0 ? 1ull : 0ull));
     }
     return r;
 }
 
-__device__ __forceinline__ Fx fx_add(Fx a, Fx b) {
+// a + b; a sum outside the 128-bit range (|a + b| >= 2^27) sets `bad`: the operands have
+// the same sign and the result's sign differs.
+__device__ __forceinline__ Fx fx_add(Fx a, Fx b, bool &bad) {
     Fx r;
     r.lo = a.lo + b.lo;
-    r.hi = a.hi + b.hi + (r.lo < a.lo ? 1 : 0);
+    r.hi = (long long)((unsigned long long)a.hi + (unsigned long long)b.hi + (r.lo < a.lo ? 1ull : 0ull));
+    bad |= ((a.hi ^ r.hi) & (b.hi ^ r.hi)) < 0;
     return r;
 }
 
@@ -106,19 +116,22 @@ __device__ __forceinline__ ExactPair fx_pair(Fx re, Fx im) {
 }
 
 // Block-wide exact sum of the pairs at p[0..n) (written by other CTAs: read through L2),
-// rounded to FP64 and times the scalar (sr, si); the result is valid in thread 0.
-__device__ double2 block_exact_sum(const ExactPair *p, int64_t n, double sr, double si) {
+// rounded to FP64 and times the scalar (sr, si); the result is valid in thread 0. A sum
+// outside the exact range sets QVX_ERANGE in the status word; the result is NaN then, and
+// also when the status word was already set (an earlier kernel of the call failed).
+__device__ double2 block_exact_sum(const ExactPair *p, int64_t n, double sr, double si, unsigned *status) {
     __shared__ Fx red[2][32];
     Fx re = {0ull, 0ll}, im = {0ull, 0ll};
+    bool bad = false;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
         const ulonglong2 a = __ldcg(reinterpret_cast<const ulonglong2 *>(p + i));
         const ulonglong2 b = __ldcg(reinterpret_cast<const ulonglong2 *>(p + i) + 1);
-        re = fx_add(re, Fx{a.x, (long long)a.y});
-        im = fx_add(im, Fx{b.x, (long long)b.y});
+        re = fx_add(re, Fx{a.x, (long long)a.y}, bad);
+        im = fx_add(im, Fx{b.x, (long long)b.y}, bad);
     }
     for (int d = 16; d > 0; d >>= 1) {
-        re = fx_add(re, fx_shfl_down(re, d));
-        im = fx_add(im, fx_shfl_down(im, d));
+        re = fx_add(re, fx_shfl_down(re, d), bad);
+        im = fx_add(im, fx_shfl_down(im, d), bad);
     }
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
     __syncthreads();
@@ -126,15 +139,20 @@ __device__ double2 block_exact_sum(const ExactPair *p, int64_t n, double sr, dou
         red[0][warp] = re;
         red[1][warp] = im;
     }
-    __syncthreads();
+    bad = __syncthreads_or(bad) != 0;
     double2 out = make_double2(0.0, 0.0);
     if (threadIdx.x == 0) {
         for (int w = 1; w < nw; w++) {
-            re = fx_add(re, red[0][w]);
-            im = fx_add(im, red[1][w]);
+            re = fx_add(re, red[0][w], bad);
+            im = fx_add(im, red[1][w], bad);
         }
-        const double r = fx_to_double(re), i = fx_to_double(im);
-        out = make_double2(r * sr - i * si, r * si + i * sr);
+        if (bad) atomicCAS(status, 0u, kStatusRange);
+        if (bad || *reinterpret_cast<volatile unsigned *>(status) != 0u) {
+            out = make_double2(__longlong_as_double(0x7ff8000000000000ll), __longlong_as_double(0x7ff8000000000000ll));
+        } else {
+            const double r = fx_to_double(re), i = fx_to_double(im);
+            out = make_double2(r * sr - i * si, r * si + i * sr);
+        }
     }
     return out;
 }
@@ -180,13 +198,14 @@ __device__ void finish_item_t(const FinishInfo &P, const LaunchArgs &a, const fl
         const uint32_t fj = compress_bits(j, P.open_present, P.n_open) << inner_bits;
         const int64_t slot = (b << P.n_open) + j;
         Fx re = {0ull, 0ll}, im = {0ull, 0ll};
+        bool bad = false;
         for (uint32_t i = lane; i < (1u << n_in); i += 32) {
             const int64_t s = (int64_t)((o << n_in) | i);
             if (s < a.s_begin || s >= a.s_end) continue;
             const uint32_t fi = compress_bits(i, present, n_in) | fj;
             const float2 t = zero ? make_float2(0.f, 0.f) : (CG ? __ldcg(fin + fi) : fin[fi]);
-            re = fx_add(re, fx_from_float(t.x));
-            im = fx_add(im, fx_from_float(t.y));
+            re = fx_add(re, fx_from_float(t.x, bad), bad);
+            im = fx_add(im, fx_from_float(t.y, bad), bad);
             if (a.terms) {
                 const double tr = (double)t.x * P.sr - (double)t.y * P.si;
                 const double ti = (double)t.x * P.si + (double)t.y * P.sr;
@@ -194,9 +213,10 @@ __device__ void finish_item_t(const FinishInfo &P, const LaunchArgs &a, const fl
             }
         }
         for (int d = 16; d > 0; d >>= 1) {
-            re = fx_add(re, fx_shfl_down(re, d));
-            im = fx_add(im, fx_shfl_down(im, d));
+            re = fx_add(re, fx_shfl_down(re, d), bad);
+            im = fx_add(im, fx_shfl_down(im, d), bad);
         }
+        if (bad) atomicCAS(a.status, 0u, kStatusRange);
         if (lane == 0) a.partials[slot * a.o_count + (int64_t)(o - (uint64_t)a.o_begin)] = fx_pair(re, im);
     }
 }
@@ -441,6 +461,7 @@ __global__ void __launch_bounds__(512) fused_program_kernel(LaunchArgs a, int wa
     const int groups0 = blockDim.x / (32 * warps_per_item);
     const int64_t item0 = (int64_t)blockIdx.x * groups0 + threadIdx.x / (32 * warps_per_item);
     uint64_t x_next = item0 < a.batch * a.o_count ? a.bitstrings[item0 / a.o_count] : 0ull;
+    bool staged_ok = true;
     if (STAGED) {
         const uint32_t s1 = a.smem_steps_bytes, s2 = s1 + a.smem_leaf_bytes, s3 = s2 + a.smem_leaves_bytes;
         const uint32_t bar = smem_u32(&stage_bar);
@@ -455,55 +476,63 @@ __global__ void __launch_bounds__(512) fused_program_kernel(LaunchArgs a, int wa
         }
         __syncthreads();
         const bool ok = mbar_wait(bar, 0, kWaitPolls);
-        if (__syncthreads_or(!ok)) {          // the copy never completed: report and leave
+        if (__syncthreads_or(!ok)) {
+            // the copy never completed: report it, give the copies in flight a last bounded
+            // wait, skip the work items and still take this CTA's ticket below, so that the
+            // last CTA runs (it writes NaN amplitudes and resets the counter)
             if (threadIdx.x == 0) atomicCAS(a.status, 0u, 4u /* QVX_ETIMEOUT */);
             mbar_wait(bar, 0, kWaitPolls);
-            return;
+            staged_ok = false;
+        } else {
+            steps = reinterpret_cast<const FusedStep *>(smem);
+            tabs = reinterpret_cast<const uint32_t *>(smem + (tab_off - steps_off));
+            lane_map = reinterpret_cast<const uint32_t *>(smem + (map_off - steps_off));
+            ldata = reinterpret_cast<const float2 *>(smem + s1);
+            leaves = reinterpret_cast<const DevLeaf *>(smem + s2);
+            cur = smem + s3;
         }
-        steps = reinterpret_cast<const FusedStep *>(smem);
-        tabs = reinterpret_cast<const uint32_t *>(smem + (tab_off - steps_off));
-        lane_map = reinterpret_cast<const uint32_t *>(smem + (map_off - steps_off));
-        ldata = reinterpret_cast<const float2 *>(smem + s1);
-        leaves = reinterpret_cast<const DevLeaf *>(smem + s2);
-        cur = smem + s3;
     } else {
         __syncthreads();
     }
     const FinishInfo fin = finish_info(P);
-    const int lanes = 32 * warps_per_item;
-    const int group = threadIdx.x / lanes;
-    const int lane = threadIdx.x % lanes;
-    const int groups = blockDim.x / lanes;
-    unsigned char *mine = cur + (size_t)group * a.group_bytes;
-    uint32_t *lbase = reinterpret_cast<uint32_t *>(mine);
-    float2 *arena = reinterpret_cast<float2 *>(mine + a.leaf_table_bytes);
-    const int64_t n_items = a.batch * a.o_count;
-    const unsigned bar_id = 1 + group;
-    for (int64_t item = (int64_t)blockIdx.x * groups + group; item < n_items;
-         item += (int64_t)gridDim.x * groups) {
-        const int64_t b = item / a.o_count;
-        const uint64_t o = (uint64_t)(a.o_begin + item % a.o_count);
-        const uint64_t x = x_next;
-        const int64_t item_next = item + (int64_t)gridDim.x * groups;
-        if (item_next < n_items) x_next = a.bitstrings[item_next / a.o_count];
-        for (uint32_t l = lane; l < n_leaves; l += lanes) lbase[l] = leaf_base(leaves[l], x, o);
-        if (warps_per_item == 1) __syncwarp();
-        else asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(lanes));
-        LaneWork w = lane_work<STAGED>(n_phases ? lane_map[lane] : 0xffffffffu, steps, tabs, ldata, lbase, arena);
-        for (uint32_t ph = 0; ph < n_phases; ph++) {
-            const uint32_t m_next = ph + 1 < n_phases ? lane_map[(ph + 1) * (uint32_t)lanes + (uint32_t)lane] : 0xffffffffu;
-            const LaneWork next = lane_work<STAGED>(m_next, steps, tabs, ldata, lbase, arena);
-            if (w.active) run_lane_work(w);
+    if (staged_ok) {
+        const int lanes = 32 * warps_per_item;
+        const int group = threadIdx.x / lanes;
+        const int lane = threadIdx.x % lanes;
+        const int groups = blockDim.x / lanes;
+        unsigned char *mine = cur + (size_t)group * a.group_bytes;
+        uint32_t *lbase = reinterpret_cast<uint32_t *>(mine);
+        float2 *arena = reinterpret_cast<float2 *>(mine + a.leaf_table_bytes);
+        const int64_t n_items = a.batch * a.o_count;
+        const unsigned bar_id = 1 + group;
+        for (int64_t item = (int64_t)blockIdx.x * groups + group; item < n_items;
+             item += (int64_t)gridDim.x * groups) {
+            const int64_t b = item / a.o_count;
+            const uint64_t o = (uint64_t)(a.o_begin + item % a.o_count);
+            const uint64_t x = x_next;
+            const int64_t item_next = item + (int64_t)gridDim.x * groups;
+            if (item_next < n_items) x_next = a.bitstrings[item_next / a.o_count];
+            for (uint32_t l = lane; l < n_leaves; l += lanes) lbase[l] = leaf_base(leaves[l], x, o);
             if (warps_per_item == 1) __syncwarp();
             else asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(lanes));
-            w = next;
+            LaneWork w = lane_work<STAGED>(n_phases ? lane_map[lane] : 0xffffffffu, steps, tabs, ldata, lbase, arena);
+            for (uint32_t ph = 0; ph < n_phases; ph++) {
+                const uint32_t m_next =
+                    ph + 1 < n_phases ? lane_map[(ph + 1) * (uint32_t)lanes + (uint32_t)lane] : 0xffffffffu;
+                const LaneWork next = lane_work<STAGED>(m_next, steps, tabs, ldata, lbase, arena);
+                if (w.active) run_lane_work(w);
+                if (warps_per_item == 1) __syncwarp();
+                else asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(lanes));
+                w = next;
+            }
+            if (lane < 32) finish_item_t<false>(fin, a, arena + final_off, b, o, lane, x);
+            if (warps_per_item == 1) __syncwarp();
+            else asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(lanes));
         }
-        if (lane < 32) finish_item_t<false>(fin, a, arena + final_off, b, o, lane, x);
-        if (warps_per_item == 1) __syncwarp();
-        else asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(lanes));
     }
     if (a.amps == nullptr) return;
-    // the last CTA to finish adds every bitstring's item partials
+    // the last CTA to finish adds every bitstring's item partials (NaN when a kernel of this
+    // call set the status word) and resets the counter for the next call
     __shared__ bool last;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -516,7 +545,7 @@ __global__ void __launch_bounds__(512) fused_program_kernel(LaunchArgs a, int wa
     // every other CTA fenced its partials before counting itself, and the loads below
     // depend on the count: they read the partials through L2
     for (int64_t slot = 0; slot < (a.batch << fin.n_open); slot++) {
-        const double2 r = block_exact_sum(a.partials + slot * a.o_count, a.o_count, fin.sr, fin.si);
+        const double2 r = block_exact_sum(a.partials + slot * a.o_count, a.o_count, fin.sr, fin.si, a.status);
         if (threadIdx.x == 0) {
             a.amps[2 * slot] = r.x;
             a.amps[2 * slot + 1] = r.y;
@@ -835,10 +864,11 @@ __global__ void finish_kernel(LaunchArgs a, int64_t item_begin, int64_t n_items,
 }
 
 // ------------------------------------------------------------------ slice sum
-__global__ void slice_sum_kernel(const unsigned char *img, const ExactPair *partials, int64_t o_count, double *amps) {
+__global__ void slice_sum_kernel(const unsigned char *img, const ExactPair *partials, int64_t o_count, double *amps,
+                                 unsigned *status) {
     const DevProgram *P = reinterpret_cast<const DevProgram *>(img);
     const int64_t b = blockIdx.x;
-    const double2 r = block_exact_sum(partials + b * o_count, o_count, P->scalar_re, P->scalar_im);
+    const double2 r = block_exact_sum(partials + b * o_count, o_count, P->scalar_re, P->scalar_im, status);
     if (threadIdx.x == 0) {
         amps[2 * b] = r.x;
         amps[2 * b + 1] = r.y;
@@ -938,24 +968,29 @@ __global__ void __launch_bounds__(256) grad_program_kernel(GradArgs g) {
         if (threadIdx.x < 32) {
             const float2 *fin = arena + P->final_fwd_off;
             Fx re = {0ull, 0ll}, im = {0ull, 0ll};
+            bool bad = false;
             const uint32_t n_in = P->n_inner, present = P->final_present;
             for (uint32_t i = threadIdx.x; i < (1u << n_in); i += 32) {
                 uint32_t fi = 0, bit = 0;
                 for (uint32_t j = 0; j < n_in; j++)
                     if ((present >> j) & 1u) fi |= ((i >> j) & 1u) << bit++;
                 const float2 t = zero ? make_float2(0.f, 0.f) : fin[fi];
-                re = fx_add(re, fx_from_float(t.x));
-                im = fx_add(im, fx_from_float(t.y));
+                re = fx_add(re, fx_from_float(t.x, bad), bad);
+                im = fx_add(im, fx_from_float(t.y, bad), bad);
             }
             for (int d = 16; d > 0; d >>= 1) {
-                re = fx_add(re, fx_shfl_down(re, d));
-                im = fx_add(im, fx_shfl_down(im, d));
+                re = fx_add(re, fx_shfl_down(re, d), bad);
+                im = fx_add(im, fx_shfl_down(im, d), bad);
             }
+            if (bad) atomicCAS(g.status, 0u, kStatusRange);
             if (threadIdx.x == 0) g.partials[item] = fx_pair(re, im);
         }
         for (uint32_t lp = threadIdx.x; lp < npl; lp += blockDim.x) {
             const float2 t = zero ? make_float2(0.f, 0.f) : arena[P->gslot_off + lp];
-            g.gpart[(uint64_t)item * npl + lp] = fx_pair(fx_from_float(t.x), fx_from_float(t.y));
+            bool bad = false;
+            const Fx tr = fx_from_float(t.x, bad), ti = fx_from_float(t.y, bad);
+            if (bad) atomicCAS(g.status, 0u, kStatusRange);
+            g.gpart[(uint64_t)item * npl + lp] = fx_pair(tr, ti);
         }
         __syncthreads();
     }
@@ -1088,24 +1123,29 @@ __global__ void __launch_bounds__(256) grad_smem_kernel(GradArgs g) {
         if (threadIdx.x < 32) {
             const float2 *fin = arena + P->final_fwd_off;
             Fx re = {0ull, 0ll}, im = {0ull, 0ll};
+            bool bad = false;
             const uint32_t n_in = P->n_inner, present = P->final_present;
             for (uint32_t i = threadIdx.x; i < (1u << n_in); i += 32) {
                 uint32_t fi = 0, bit = 0;
                 for (uint32_t j = 0; j < n_in; j++)
                     if ((present >> j) & 1u) fi |= ((i >> j) & 1u) << bit++;
                 const float2 t = zero ? make_float2(0.f, 0.f) : fin[fi];
-                re = fx_add(re, fx_from_float(t.x));
-                im = fx_add(im, fx_from_float(t.y));
+                re = fx_add(re, fx_from_float(t.x, bad), bad);
+                im = fx_add(im, fx_from_float(t.y, bad), bad);
             }
             for (int d = 16; d > 0; d >>= 1) {
-                re = fx_add(re, fx_shfl_down(re, d));
-                im = fx_add(im, fx_shfl_down(im, d));
+                re = fx_add(re, fx_shfl_down(re, d), bad);
+                im = fx_add(im, fx_shfl_down(im, d), bad);
             }
+            if (bad) atomicCAS(g.status, 0u, kStatusRange);
             if (threadIdx.x == 0) g.partials[item] = fx_pair(re, im);
         }
         for (uint32_t lp = threadIdx.x; lp < npl; lp += blockDim.x) {
             const float2 t = zero ? make_float2(0.f, 0.f) : arena[P->gslot_off + lp];
-            g.gpart[(uint64_t)item * npl + lp] = fx_pair(fx_from_float(t.x), fx_from_float(t.y));
+            bool bad = false;
+            const Fx tr = fx_from_float(t.x, bad), ti = fx_from_float(t.y, bad);
+            if (bad) atomicCAS(g.status, 0u, kStatusRange);
+            g.gpart[(uint64_t)item * npl + lp] = fx_pair(tr, ti);
         }
         __syncthreads();
     }
@@ -1114,7 +1154,7 @@ __global__ void __launch_bounds__(256) grad_smem_kernel(GradArgs g) {
 // One block per (bitstring, parameter): exact sum over the work items and over the
 // parameter's leaves (CSR lists in the image), rounded once and times the plan's scalar.
 __global__ void grad_sum_kernel(const unsigned char *img, const ExactPair *gpart, int64_t o_count, uint32_t npl,
-                                uint32_t n_params, double *grad) {
+                                uint32_t n_params, double *grad, unsigned *status) {
     __shared__ Fx red[2][32];
     const DevProgram *P = reinterpret_cast<const DevProgram *>(img);
     const uint32_t *csr = reinterpret_cast<const uint32_t *>(img + P->param_csr_off);
@@ -1123,32 +1163,41 @@ __global__ void grad_sum_kernel(const unsigned char *img, const ExactPair *gpart
     const uint32_t first = csr[p], last = csr[p + 1];
     const uint32_t *list = csr + n_params + 1;
     Fx re = {0ull, 0ll}, im = {0ull, 0ll};
+    bool bad = false;
     const int64_t n = (int64_t)(last - first) * o_count;
     for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
         const uint32_t lp = list[first + t / o_count];
         const int64_t o = t % o_count;
         const ExactPair v = gpart[((uint64_t)(b * o_count + o)) * npl + lp];
-        re = fx_add(re, Fx{v.re_lo, (long long)v.re_hi});
-        im = fx_add(im, Fx{v.im_lo, (long long)v.im_hi});
+        re = fx_add(re, Fx{v.re_lo, (long long)v.re_hi}, bad);
+        im = fx_add(im, Fx{v.im_lo, (long long)v.im_hi}, bad);
     }
     for (int d = 16; d > 0; d >>= 1) {
-        re = fx_add(re, fx_shfl_down(re, d));
-        im = fx_add(im, fx_shfl_down(im, d));
+        re = fx_add(re, fx_shfl_down(re, d), bad);
+        im = fx_add(im, fx_shfl_down(im, d), bad);
     }
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
     if (lane == 0) {
         red[0][warp] = re;
         red[1][warp] = im;
     }
-    __syncthreads();
+    bad = __syncthreads_or(bad) != 0;
     if (threadIdx.x == 0) {
         for (int w = 1; w < nw; w++) {
-            re = fx_add(re, red[0][w]);
-            im = fx_add(im, red[1][w]);
+            re = fx_add(re, red[0][w], bad);
+            im = fx_add(im, red[1][w], bad);
         }
-        const double r = fx_to_double(re), i = fx_to_double(im);
-        grad[2 * (b * n_params + p)] = r * P->scalar_re - i * P->scalar_im;
-        grad[2 * (b * n_params + p) + 1] = r * P->scalar_im + i * P->scalar_re;
+        if (bad) atomicCAS(status, 0u, kStatusRange);
+        double gr, gi;
+        if (bad || *reinterpret_cast<volatile unsigned *>(status) != 0u) {   // no valid sum: NaN
+            gr = gi = __longlong_as_double(0x7ff8000000000000ll);
+        } else {
+            const double r = fx_to_double(re), i = fx_to_double(im);
+            gr = r * P->scalar_re - i * P->scalar_im;
+            gi = r * P->scalar_im + i * P->scalar_re;
+        }
+        grad[2 * (b * n_params + p)] = gr;
+        grad[2 * (b * n_params + p) + 1] = gi;
     }
 }
 
@@ -1253,9 +1302,10 @@ cudaError_t launch_grad_smem(const GradArgs &g, int grid, size_t smem_bytes, cud
 }
 
 cudaError_t launch_grad_sum(const unsigned char *image, const ExactPair *gpart, int64_t batch, int64_t o_count,
-                            uint32_t n_param_leaves, uint32_t n_params, double *grad, cudaStream_t s) {
+                            uint32_t n_param_leaves, uint32_t n_params, double *grad, unsigned *status, cudaStream_t s) {
     if (n_params == 0 || batch == 0) return cudaSuccess;
-    grad_sum_kernel<<<(unsigned)(batch * n_params), 256, 0, s>>>(image, gpart, o_count, n_param_leaves, n_params, grad);
+    grad_sum_kernel<<<(unsigned)(batch * n_params), 256, 0, s>>>(image, gpart, o_count, n_param_leaves, n_params, grad,
+                                                                 status);
     return counted(cudaGetLastError());
 }
 
@@ -1391,8 +1441,8 @@ cudaError_t launch_finish_items(const LaunchArgs &a, int64_t item_begin, int64_t
 }
 
 cudaError_t launch_slice_sum(const unsigned char *image, const ExactPair *partials, int64_t batch, int64_t o_count,
-                             double *amps, cudaStream_t s) {
-    slice_sum_kernel<<<(unsigned)batch, 256, 0, s>>>(image, partials, o_count, amps);
+                             double *amps, unsigned *status, cudaStream_t s) {
+    slice_sum_kernel<<<(unsigned)batch, 256, 0, s>>>(image, partials, o_count, amps, status);
     return counted(cudaGetLastError());
 }
 

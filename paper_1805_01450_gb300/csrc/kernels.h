@@ -108,8 +108,9 @@ size_t grad_stage_bytes(const DevProgram *h, GradArgs *g);
 int grad_smem_blocks_per_sm(size_t smem_bytes, bool staged);
 cudaError_t launch_grad_smem(const GradArgs &g, int grid, size_t smem_bytes, cudaStream_t s);
 // d alpha / d theta_p = exact sum over work items and the parameter's leaves.
+// A sum outside the exact range sets QVX_ERANGE; NaN is written when the status word is set.
 cudaError_t launch_grad_sum(const unsigned char *image, const ExactPair *gpart, int64_t batch, int64_t o_count,
-                            uint32_t n_param_leaves, uint32_t n_params, double *grad, cudaStream_t s);
+                            uint32_t n_param_leaves, uint32_t n_params, double *grad, unsigned *status, cudaStream_t s);
 
 // Kernels the calling host thread has launched through these launchers (successful launches);
 // launch_counted(e) counts one launch if e is cudaSuccess and returns e.
@@ -125,8 +126,10 @@ cudaError_t launch_gemm_step(const LaunchArgs &a, const GemmStep &g, int64_t ite
 cudaError_t launch_wait_selftest(unsigned *words, unsigned *status, uint32_t polls, unsigned *out, cudaStream_t s);
 
 // Exact sum of the item partials of every bitstring (Section 3.B.2: the slice terms are
-// added), rounded once to FP64 and times the plan's scalar.
+// added), rounded once to FP64 and times the plan's scalar. A sum outside the exact range
+// sets QVX_ERANGE in the status word; an amplitude is written as NaN when the status word is
+// set (by this kernel or an earlier one of the call).
 cudaError_t launch_slice_sum(const unsigned char *image, const ExactPair *partials, int64_t batch, int64_t o_count,
-                             double *amps, cudaStream_t s);
+                             double *amps, unsigned *status, cudaStream_t s);
 
 }  // namespace qvx

@@ -26,6 +26,7 @@ namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(4) << 20;   // 4 MiB per device
 constexpr int kMaxDevices = 64;
+constexpr size_t kStatusBytes = 256;                       // [status word, CTA counter], padded
 
 // The scratch array. In host code `g_noalloc_scratch` names a host-side stand-in, not the
 // device memory: its device address comes from cudaGetSymbolAddress, once per device.
@@ -78,9 +79,10 @@ extern "C" qvx_status qvx_amplitude_noalloc(qvx_plan *plan, const uint64_t *bits
         return fail(QVX_EUNSUPPORTED, "the no-allocation entry point runs fused-engine plans only");
     const qvx::DevProgram *h = reinterpret_cast<const qvx::DevProgram *>(p.image.data());
     const int64_t n_outer = int64_t(1) << ((int)p.slices.size() - p.n_inner);
-    // scratch layout: [plan image][status word, CTA counter][partials]
-    const size_t image_b = r256(p.image.size());
-    const size_t partials_off = image_b + 256;
+    // scratch layout: [status word, CTA counter][plan image][partials]; the status word sits
+    // at a fixed offset so that qvx_noalloc_status can find it without a plan
+    const size_t image_off = kStatusBytes;
+    const size_t partials_off = image_off + r256(p.image.size());
     const size_t need = partials_off + ((size_t)batch << p.open_qubits.size()) * (size_t)n_outer * sizeof(qvx::ExactPair);
     if (need > kNoAllocScratchBytes)
         return fail(QVX_EINVAL, "no-allocation scratch too small: this plan and batch need " + std::to_string(need) +
@@ -94,13 +96,17 @@ extern "C" qvx_status qvx_amplitude_noalloc(qvx_plan *plan, const uint64_t *bits
     unsigned char *base = static_cast<unsigned char *>(scratch);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // the array keeps the previous call's contents: load this plan's image and zero the
-    // status word and the finished-CTA counter before the launch
-    if ((e = cudaMemcpyAsync(base, p.image.data(), p.image.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    // finished-CTA counter before the launch. The status word is left as it is: a failure of
+    // an earlier call stays visible to qvx_noalloc_status until it is read (and the amplitudes
+    // of every call made while it is set are written as NaN).
+    if ((e = cudaMemcpyAsync(base + image_off, p.image.data(), p.image.size(), cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
         return cuda_fail(e, "image copy into the no-allocation scratch");
-    if ((e = cudaMemsetAsync(base + image_b, 0, 256, st)) != cudaSuccess) return cuda_fail(e, "scratch clear");
+    if ((e = cudaMemsetAsync(base + sizeof(unsigned), 0, sizeof(unsigned), st)) != cudaSuccess)
+        return cuda_fail(e, "scratch clear");
 
     qvx::LaunchArgs a{};
-    a.image = base;
+    a.image = base + image_off;
     a.bitstrings = bitstrings_dev;
     a.batch = batch;
     a.o_begin = 0;
@@ -112,7 +118,7 @@ extern "C" qvx_status qvx_amplitude_noalloc(qvx_plan *plan, const uint64_t *bits
     a.n_inner = (uint32_t)p.n_inner;
     a.partials = reinterpret_cast<qvx::ExactPair *>(base + partials_off);
     a.terms = nullptr;
-    a.status = reinterpret_cast<unsigned int *>(base + image_b);
+    a.status = reinterpret_cast<unsigned int *>(base);
     a.counter = a.status + 1;
     a.amps = amps_dev;
     // shared-memory layout and grid, chosen as for the workspace entry points
@@ -132,4 +138,24 @@ extern "C" qvx_status qvx_amplitude_noalloc(qvx_plan *plan, const uint64_t *bits
     if ((e = qvx::launch_fused(a, wpi, ipc, grid, shared + (size_t)ipc * group, st)) != cudaSuccess)
         return cuda_fail(e, "fused kernel launch");
     return QVX_OK;
+}
+
+extern "C" qvx_status qvx_noalloc_status(void *stream) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    void *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_setup_mutex);
+        if (dev >= 0 && dev < kMaxDevices) scratch = g_scratch_ptr[dev];
+    }
+    if (!scratch) return QVX_OK;   // no call has run on this device
+    if ((e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream))) != cudaSuccess)
+        return cuda_fail(e, "stream synchronize");
+    unsigned word = 0;
+    if ((e = cudaMemcpy(&word, scratch, sizeof(word), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "status read");
+    if (word == 0) return QVX_OK;
+    if ((e = cudaMemset(scratch, 0, sizeof(word))) != cudaSuccess) return cuda_fail(e, "status clear");
+    return fail((qvx_status)word, "device status word of the no-allocation scratch set by a kernel");
 }

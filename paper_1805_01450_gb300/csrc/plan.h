@@ -91,5 +91,8 @@ qvx_status make_plan(const qvx_circuit *c, const int32_t *order, int32_t n_order
                      const int32_t *slices, int32_t n_slices, const qvx_plan_opts &opts,
                      Plan *p, std::string *err);
 double plan_estimate(const Plan &p);   // bandwidth-weighted contraction estimate, all items
+// Algorithmic flops (8 per complex MAC) and bytes (every operand read and the output
+// written once, complex64) of step s for one work item.
+void step_cost(const Plan &p, size_t s, double *flops, double *bytes);
 
 }  // namespace qvx

@@ -1742,6 +1742,8 @@ double plan_estimate(const Plan &p) {
     return t * std::ldexp(1.0, (int)p.slices.size() - p.n_inner);
 }
 
+void step_cost(const Plan &p, size_t s, double *flops, double *bytes) { step_work(p, p.steps[s], flops, bytes); }
+
 namespace {
 
 qvx_status plan_once(const qvx_circuit *c, const int32_t *order, int32_t n_order,

@@ -231,13 +231,17 @@ qvx_status qvx_slice_terms(qvx_plan *plan, const uint64_t *bitstrings_dev, int64
                            void *workspace_dev, size_t workspace_bytes, void *stream);
 
 /* The paper has no counterpart to this entry point; it serves callers that cannot
- * allocate device memory. alpha_b = <x_b|C|0> for b < batch, like qvx_amplitude, but
+ * allocate device memory: code that runs where the allocator is off limits (inside another
+ * library's callback, a real-time loop that must not block on an allocation, a process whose
+ * device memory is all reserved up front) and so cannot provide a workspace. alpha_b = <x_b|C|0> for b < batch, like qvx_amplitude, but
  * without a workspace: the library keeps this call's scratch (the plan's device image, a
  * status word and the per-work-item partial sums) in one fixed device array of 4 MiB that
  * every GPU loading the library holds until the process exits. bitstrings_dev and amps_dev
  * are the caller's device buffers as for qvx_amplitude. Fused-engine plans only
  * (QVX_EUNSUPPORTED otherwise); a plan and batch whose scratch exceeds 4 MiB are rejected
- * with QVX_EINVAL. The first call on a device also looks up the array's device address
+ * with QVX_EINVAL. The scratch holds 256 bytes of status words, the plan's device image
+ * rounded up to 256 bytes, and 32 bytes per (bitstring, open-output value, outer work item).
+ * The first call on a device also looks up the array's device address
  * (cudaGetSymbolAddress), so make that first call before any stream capture. All calls
  * share the one array and each call overwrites it: calls that overlap on the GPU (other
  * streams, other threads) race and must be serialised by the caller. The array's status
@@ -272,6 +276,17 @@ qvx_status qvx_amplitude_grad(qvx_plan *plan, const uint64_t *bitstrings_dev, in
  * status word is cleared again. Uses two scratch words of the workspace's status block. */
 qvx_status qvx_selftest_wait_timeout(const qvx_plan *plan, void *workspace_dev, size_t workspace_bytes,
                                      uint32_t polls, void *stream);
+
+/* Self-test of the fused kernel's failure path (the paper has no counterpart): runs
+ * qvx_amplitude for a fused-engine plan whose program is staged in shared memory, with the
+ * first staging wait of every CTA giving up at once, as a wait that ran out would. Each CTA
+ * then reports QVX_ETIMEOUT in the workspace status word, waits (bounded) for its staging
+ * copies to land, skips its work items and still counts itself, so the last CTA writes the
+ * amplitudes as NaN and resets the finished-CTA counter: the next call on the workspace,
+ * after qvx_workspace_status has cleared the word, computes normally. Nothing faults or
+ * hangs. QVX_EUNSUPPORTED for other plans. */
+qvx_status qvx_selftest_fused_timeout(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch, double *amps_dev,
+                                      void *workspace_dev, size_t workspace_bytes, void *stream);
 
 /* Synchronises `stream` and returns the device status word kept in the workspace
  * (QVX_OK, QVX_ETIMEOUT or QVX_ERANGE), then clears it. */

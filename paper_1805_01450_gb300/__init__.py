@@ -77,7 +77,7 @@ EXPORTED = ("qvx_plan_opts_default", "qvx_graph_export", "qvx_plan_create", "qvx
             "qvx_amplitude", "qvx_amplitude_slices", "qvx_slice_terms", "qvx_workspace_status",
             "qvx_last_error", "qvx_amplitude_noalloc", "qvx_amplitude_grad", "qvx_amplitude_host",
             "qvx_selftest_wait_timeout", "qvx_kernel_launches", "qvx_noalloc_status", "qvx_amplitude_profiled",
-            "qvx_profile_read", "qvx_kernel_name")
+            "qvx_profile_read", "qvx_kernel_name", "qvx_selftest_fused_timeout")
 
 
 def lib():
@@ -114,6 +114,7 @@ def lib():
         "qvx_amplitude_profiled": (ctypes.c_int, [P, P, i64, P, P, ctypes.c_size_t, P]),
         "qvx_profile_read": (ctypes.c_int, [P, ctypes.POINTER(LaunchRecord), i64, ctypes.POINTER(ctypes.c_int64)]),
         "qvx_kernel_name": (ctypes.c_char_p, [i32]),
+        "qvx_selftest_fused_timeout": (ctypes.c_int, [P, P, i64, P, P, ctypes.c_size_t, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -138,7 +138,8 @@ PStepShape shape_of(const qvx::Plan &p, size_t s) {
 // With the fused engine and amps != nullptr the same launch also writes the amplitudes.
 qvx_status run_items(qvx_plan *plan, const uint64_t *bits, int64_t batch, int64_t s_begin,
                      int64_t s_end, float *terms, double *amps, void *ws, const WsLayout &w,
-                     cudaStream_t st, int64_t *o_count_out, Profiler *prof = nullptr) {
+                     cudaStream_t st, int64_t *o_count_out, Profiler *prof = nullptr,
+                     bool selftest_stage_timeout = false) {
     const qvx::Plan &p = plan->p;
     const int n_inner = p.n_inner;
     const int64_t o_begin = s_begin >> n_inner;
@@ -160,6 +161,7 @@ qvx_status run_items(qvx_plan *plan, const uint64_t *bits, int64_t batch, int64_
     a.status = reinterpret_cast<unsigned int *>(base + w.status);
     a.counter = reinterpret_cast<unsigned int *>(base + w.status) + 1;
     a.amps = p.engine == QVX_ENGINE_FUSED ? amps : nullptr;
+    a.selftest_stage_timeout = selftest_stage_timeout ? 1u : 0u;
     *o_count_out = a.o_count;
     const int64_t n_items = batch * a.o_count;
     if (n_items == 0) return QVX_OK;
@@ -719,6 +721,29 @@ qvx_status qvx_selftest_wait_timeout(const qvx_plan *plan, void *ws, size_t ws_b
     if ((e = cudaMemset(status, 0, 8 * sizeof(unsigned))) != cudaSuccess) return cuda_fail(e, "status clear");
     if (h[0] && h[1] && word == (unsigned)QVX_ETIMEOUT) return fail(QVX_ETIMEOUT, "both bounded waits gave up as designed");
     return QVX_OK;
+}
+
+qvx_status qvx_selftest_fused_timeout(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch, double *amps_dev,
+                                      void *ws, size_t ws_bytes, void *stream) {
+    WsLayout w;
+    qvx_status s = check_ws(plan, batch, ws, ws_bytes, &w);
+    if (s != QVX_OK) return s;
+    if (batch <= 0 || !bitstrings_dev || !amps_dev) return fail(QVX_EINVAL, "need a batch and device buffers");
+    const qvx::Plan &p = plan->p;
+    if (p.engine != QVX_ENGINE_FUSED) return fail(QVX_EUNSUPPORTED, "the self-test runs fused-engine plans");
+    {
+        qvx::LaunchArgs probe{};
+        size_t shared = 0, group = 0;
+        int max_ipc = 1;
+        if (!qvx::fused_shape(reinterpret_cast<const qvx::DevProgram *>(p.image.data()),
+                              (uint64_t)std::max<int64_t>(p.arena_elems, 4), p.warps_per_item, &probe, &shared, &group,
+                              &max_ipc) ||
+            probe.smem_steps_bytes == 0)
+            return fail(QVX_EUNSUPPORTED, "the plan's program is not staged in shared memory");
+    }
+    int64_t o_count = 0;
+    return run_items(plan, bitstrings_dev, batch, 0, int64_t(1) << p.slices.size(), nullptr, amps_dev, ws, w,
+                     static_cast<cudaStream_t>(stream), &o_count, nullptr, true);
 }
 
 qvx_status qvx_workspace_status(const qvx_plan *plan, void *ws, void *stream) {

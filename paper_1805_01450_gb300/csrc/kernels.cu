@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(512) fused_program_kernel(LaunchArgs a, int wa
             if (a.smem_leaves_bytes) bulk_g2s(smem_u32(smem + s2), leaves, a.smem_leaves_bytes, bar);
         }
         __syncthreads();
-        const bool ok = mbar_wait(bar, 0, kWaitPolls);
+        const bool ok = mbar_wait(bar, 0, a.selftest_stage_timeout ? 0u : kWaitPolls);
         if (__syncthreads_or(!ok)) {
             // the copy never completed: report it, give the copies in flight a last bounded
             // wait, skip the work items and still take this CTA's ticket below, so that the

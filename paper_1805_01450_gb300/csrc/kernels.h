@@ -38,6 +38,9 @@ struct LaunchArgs {
     // the copies start without a round trip to the header in device memory)
     uint64_t fused_steps_off, fused_tab_off, fused_lane_map_off, leaves_off, leaf_data_off, final_off;
     uint32_t n_fused_phases, n_leaves;
+    // self-test of the fused kernel's failure path: 1 makes the first staging wait give up at
+    // once (the copies then get the normal bounded wait before the CTA moves on); 0 normally
+    uint32_t selftest_stage_timeout;
 };
 
 // Fused engine: one warp group per work item, every tensor in shared memory. When

@@ -12,16 +12,19 @@
 // 2^-16 per product) are not accurate enough: on a 64-qubit circuit the amplitude moved by
 // 1.2e-5 of its size, above the 1e-5 tolerance.
 //
-// One CTA computes a tile of 128 real rows (64 complex rows m) by NT columns n for one
-// (item, b). Warps 0-3 read the complex64 operands straight from the arena, one chunk of
-// 16 summed entries at a time, split them into three bf16 parts and store them in shared
-// memory in the tensor cores' K-major core-matrix layout (no separate packing pass: the
-// operands cross HBM once, as complex64). Warp 4 allocates the tensor-memory accumulator
-// and one of its threads issues the chunk's twelve tcgen05.mma (2 parts x 6 products,
-// K = 16 each); the commit of a chunk's MMAs frees its shared-memory stage. Warps 0-3 then read
-// the accumulator back with tcgen05.ld and store complex64 C in its own layout.
+// A tile is 128 real rows (64 complex rows m) by NT columns n of one (item, b). The kernel
+// is persistent (one CTA per SM walks the tiles) and warp-specialised: producer warps read
+// the complex64 operands straight from the arena, one chunk of 16 summed entries at a time,
+// split them into three bf16 parts and store them in the tensor cores' K-major core-matrix
+// layout in a ring of shared-memory stages (no separate packing pass: the operands cross HBM
+// once, as complex64); one thread issues each chunk's twelve tcgen05.mma (2 parts x 6
+// products, K = 16 each) into one of two tensor-memory accumulators; epilogue warps read a
+// finished accumulator with tcgen05.ld and store complex64 C in its own layout while the
+// next tile's chunks are loaded and multiplied into the other accumulator.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "device_program.h"
 #include "device_util.cuh"
@@ -31,14 +34,12 @@ namespace qvx {
 namespace {
 
 constexpr uint32_t kRows = 128;        // real rows per tile (64 complex rows)
-constexpr uint32_t kStages = 1;        // shared-memory stages of summed-index chunks (the next
-                                       // chunk waits in registers meanwhile)
 constexpr uint32_t kKq = 16;           // complex summed entries per chunk (one MMA K-step)
 constexpr uint32_t kPitch = 272;       // bytes between 8-row groups: two 128-byte core matrices
                                        // along the summed index and 16 bytes that spread the
                                        // producers' 16-byte stores over all banks
 constexpr uint32_t kPolls = 1u << 22;
-constexpr uint32_t kThreads = 160;     // warps 0-3: operands and epilogue; warp 4: MMA
+constexpr uint32_t kThreads = 288;     // warps 0-3: operands; warp 4: MMA; warps 5-8: epilogue
 
 __host__ __device__ constexpr uint32_t region_bytes(uint32_t rows) { return rows / 8u * kPitch; }
 // One stage: A regions (part 0 h, m, l, part 1 h, m, l), then the same for B.
@@ -188,193 +189,280 @@ struct GemmArgs {
     int64_t item0, n_items;
     float2 *arenas;
     uint32_t n_chunks, n_mt, n_nt;
+    uint64_t n_tiles;
 };
 
+// Operand stages of the shared-memory ring: three of 52 KB for 128-column tiles, four below.
 template <int NT>
-__global__ void __launch_bounds__(kThreads, 3) gemm_tc_kernel(GemmArgs ga) {
-    constexpr uint32_t kCols = NT < 32 ? 32u : (uint32_t)NT;   // tensor-memory columns (power of 2)
+__host__ __device__ constexpr uint32_t n_stages() { return NT >= 128 ? 3u : 4u; }
+template <int NT>
+__host__ __device__ constexpr uint32_t epi_cols() { return NT < 32 ? (uint32_t)NT : 32u; }
+// bytes between rows of an epilogue warp's transpose buffer (16 rows of up to 32 columns)
+template <int NT>
+__host__ __device__ constexpr uint32_t epi_pitch() { return 8u * epi_cols<NT>() + 8u; }
+template <int NT>
+__host__ __device__ constexpr uint32_t epi_bytes() { return 4u * 16u * epi_pitch<NT>(); }
+
+// Bounded mbarrier wait that also gives up once another role has set the CTA's fail flag.
+__device__ __forceinline__ bool wait_or_fail(uint32_t bar, uint32_t parity, volatile int *fail) {
+    for (uint32_t i = 0; i < kPolls; i++) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((i & 63u) == 63u && *fail) return false;
+    }
+    return false;
+}
+
+struct TileCoord {
+    uint32_t mt, nt, beta;
+    int64_t il;
+};
+
+__device__ __forceinline__ TileCoord tile_coord(uint64_t t, const GemmArgs &ga) {
+    TileCoord c;
+    c.mt = (uint32_t)(t % ga.n_mt);   // row tiles of one (item, b) and column tile run next to each other
+    t /= ga.n_mt;
+    c.nt = (uint32_t)(t % ga.n_nt);
+    t /= ga.n_nt;
+    c.il = (int64_t)(t >> ga.g.nb);
+    c.beta = (uint32_t)(t & ((1ull << ga.g.nb) - 1ull));
+    return c;
+}
+
+// Persistent, warp-specialised tensor-core contraction. One CTA per SM walks the tiles
+// t = blockIdx.x, blockIdx.x + gridDim.x, ... (128 real rows x NT columns of one (item, b)):
+//   warps 0-3  producers: load the complex64 operands of one chunk of 16 summed entries
+//              (the next chunk's loads issued before this one's conversion), split them
+//              into bf16 parts and store them into the next stage of a ring of shared-memory
+//              stages, then arrive on the stage's "full" barrier;
+//   warp 4     allocates two tensor-memory accumulators; one thread issues each chunk's
+//              twelve tcgen05.mma into the tile's accumulator (the tile's first product
+//              overwrites it), commits each chunk to the stage's "empty" barrier and the
+//              tile's last chunk to the accumulator's "full" barrier;
+//   warps 5-8  epilogue: wait for an accumulator, read it with tcgen05.ld (warp w reads
+//              tensor-memory lanes 32 (w mod 4) ...), store complex64 C through a padded
+//              shared-memory transpose and release the accumulator.
+// With two accumulators the epilogue of one tile overlaps the loads and MMAs of the next.
+// Every wait is bounded; a wait that runs out sets the CTA's fail flag, the other roles
+// leave their loops, the MMA thread waits (bounded) for its issued MMAs before the tensor
+// memory is freed, and QVX_ETIMEOUT goes to the status word.
+template <int NT>
+__global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(GemmArgs ga) {
+    constexpr uint32_t S = n_stages<NT>();
+    constexpr uint32_t kCols = NT < 32 ? 32u : (uint32_t)NT;   // columns of one accumulator
     constexpr uint32_t kRegA = region_bytes(kRows), kStage = stage_bytes(NT);
     constexpr uint32_t kUnits = (2u * (uint32_t)NT + 127u) / 128u;   // B units per producer thread
+    constexpr uint32_t kW = epi_cols<NT>(), kTPitch = epi_pitch<NT>();
     using Chunk = qvx::Chunk<kUnits>;
     extern __shared__ __align__(1024) unsigned char gsm[];
-    __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], acc_bar;
+    __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S], accf_bar[2], acce_bar[2], drain_bar;
     __shared__ uint32_t tmem_slot;
-    __shared__ int fail;
+    __shared__ volatile int fail;
     const GemmStep &g = ga.g;
-    uint64_t t = blockIdx.x;   // tiles of one (item, b) and column tile run next to each other
-    const uint32_t mt = (uint32_t)(t % ga.n_mt);
-    t /= ga.n_mt;
-    const uint32_t nt = (uint32_t)(t % ga.n_nt);
-    t /= ga.n_nt;
-    const uint64_t ib = t;
-    const int64_t il = (int64_t)(ib >> g.nb);
-    const uint32_t beta = (uint32_t)(ib & ((1u << g.nb) - 1u));
     const uint32_t warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const uint32_t sbase = smem_u32(gsm);
     if (threadIdx.x == 0) {
-        for (uint32_t s = 0; s < kStages; s++) {
+        for (uint32_t s = 0; s < S; s++) {
             mbar_init(smem_u32(&full_bar[s]), 128);
             mbar_init(smem_u32(&empty_bar[s]), 1);
         }
-        mbar_init(smem_u32(&acc_bar), 1);
+        for (uint32_t b = 0; b < 2; b++) {
+            mbar_init(smem_u32(&accf_bar[b]), 1);
+            mbar_init(smem_u32(&acce_bar[b]), 128);
+        }
+        mbar_init(smem_u32(&drain_bar), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fail = 0;
     }
     if (warp == 4) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(kCols)
+                     "r"(2u * kCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // address tables of this tile (bit-run maps evaluated once per CTA): the summed index's
-    // offsets in A and B, and the offsets of the tile's rows and columns in C
+    // the summed index's offsets in A and B (bit-run maps evaluated once per CTA)
     const uint32_t K = ga.n_chunks * kKq;
-    uint32_t *tka = reinterpret_cast<uint32_t *>(gsm + kStages * kStage);
-    uint32_t *tkb = tka + K, *tcm = tkb + K, *tcn = tcm + 64;
+    uint32_t *tka = reinterpret_cast<uint32_t *>(gsm + S * kStage + epi_bytes<NT>());
+    uint32_t *tkb = tka + K;
     for (uint32_t i = threadIdx.x; i < K; i += kThreads) {
         tka[i] = pext_runs(i, g.ak, g.n_ak);
         tkb[i] = pext_runs(i, g.bk, g.n_bk);
     }
-    for (uint32_t i = threadIdx.x; i < 64u + (uint32_t)NT; i += kThreads)
-        tcm[i] = i < 64u ? pext_runs(mt * 64u + i, g.cm, g.n_cm) : pext_runs(nt * (uint32_t)NT + i - 64u, g.cn, g.n_cn);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-    float2 *arena = ga.arenas + (uint64_t)il * ga.a.arena_elems;
     if (warp < 4) {
         // producers: A rows m = mt*64 + 32*(warp&1) + lane, summed half h = warp>>1 of the
-        // chunk; B units (column, half) strided over the 128 threads. A chunk's loads are
-        // all issued before its conversion, and the next chunk's before this one's stores.
-        const float2 *A = gemm_operand(ga.a, arena, g.a_off, g.flags & kStepALeaf, ga.item0 + il);
-        const float2 *B = gemm_operand(ga.a, arena, g.b_off, g.flags & kStepBLeaf, ga.item0 + il);
+        // chunk; B units (column, half) strided over the 128 threads
         const uint32_t ml = 32u * (warp & 1u) + lane, h = warp >> 1;
-        const float2 *Arow = A + pext_runs(beta, g.ab, g.n_ab) + pext_runs(mt * 64u + ml, g.am, g.n_am);
-        const float2 *Bcol[kUnits];
-        uint32_t bh[kUnits];
-#pragma unroll
-        for (uint32_t i = 0; i < kUnits; i++) {
-            const uint32_t u = threadIdx.x + 128u * i;
-            const uint32_t nl = u % (uint32_t)NT;
-            bh[i] = u / (uint32_t)NT;
-            Bcol[i] = B + pext_runs(beta, g.bb, g.n_bb) + pext_runs(nt * (uint32_t)NT + nl, g.bn, g.n_bn);
-        }
         const bool b_on = threadIdx.x < 2u * (uint32_t)NT;   // every unit of a thread shares this
-        Chunk cur, nxt;
-        load_chunk(cur, 0, h, Arow, Bcol, bh, b_on, tka, tkb);
-        for (uint32_t c = 0; c < ga.n_chunks; c++) {
-            const uint32_t s = c % kStages;
-            if (c + 1 < ga.n_chunks) load_chunk(nxt, c + 1, h, Arow, Bcol, bh, b_on, tka, tkb);
-            if (c >= kStages && !mbar_wait(smem_u32(&empty_bar[s]), ((c / kStages) - 1u) & 1u, kPolls)) {
-                fail = 1;
-                break;
-            }
-            unsigned char *sa = gsm + s * kStage;
-            store_a(sa, cur.a, ml, h);
-            if (b_on) {
+        uint32_t gc = 0;   // chunks this CTA has produced: the ring position
+        for (uint64_t t = blockIdx.x; t < ga.n_tiles && !fail; t += gridDim.x) {
+            const TileCoord tc = tile_coord(t, ga);
+            float2 *arena = ga.arenas + (uint64_t)tc.il * ga.a.arena_elems;
+            const float2 *A = gemm_operand(ga.a, arena, g.a_off, g.flags & kStepALeaf, ga.item0 + tc.il);
+            const float2 *B = gemm_operand(ga.a, arena, g.b_off, g.flags & kStepBLeaf, ga.item0 + tc.il);
+            const float2 *Arow = A + pext_runs(tc.beta, g.ab, g.n_ab) + pext_runs(tc.mt * 64u + ml, g.am, g.n_am);
+            const float2 *Bcol[kUnits];
+            uint32_t bh[kUnits];
+            const uint32_t bb = pext_runs(tc.beta, g.bb, g.n_bb);
 #pragma unroll
-                for (uint32_t i = 0; i < kUnits; i++)
-                    store_b<NT>(sa + 6u * kRegA, cur.b[i], (threadIdx.x + 128u * i) % (uint32_t)NT, bh[i]);
+            for (uint32_t i = 0; i < kUnits; i++) {
+                const uint32_t u = threadIdx.x + 128u * i;
+                bh[i] = u / (uint32_t)NT;
+                Bcol[i] = B + bb + pext_runs(tc.nt * (uint32_t)NT + u % (uint32_t)NT, g.bn, g.n_bn);
             }
-            // the generic-proxy stores must be visible to the tensor cores' reads
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[s])) : "memory");
-            cur = nxt;
+            Chunk cur, nxt;
+            load_chunk(cur, 0, h, Arow, Bcol, bh, b_on, tka, tkb);
+            for (uint32_t c = 0; c < ga.n_chunks; c++, gc++) {
+                const uint32_t s = gc % S;
+                if (c + 1 < ga.n_chunks) load_chunk(nxt, c + 1, h, Arow, Bcol, bh, b_on, tka, tkb);
+                if (!wait_or_fail(smem_u32(&empty_bar[s]), ((gc / S) & 1u) ^ 1u, &fail)) {
+                    fail = 1;
+                    break;
+                }
+                unsigned char *sa = gsm + s * kStage;
+                store_a(sa, cur.a, ml, h);
+                if (b_on) {
+#pragma unroll
+                    for (uint32_t i = 0; i < kUnits; i++)
+                        store_b<NT>(sa + 6u * kRegA, cur.b[i], (threadIdx.x + 128u * i) % (uint32_t)NT, bh[i]);
+                }
+                // the generic-proxy stores must be visible to the tensor cores' reads
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[s])) : "memory");
+                cur = nxt;
+            }
         }
-    } else if (lane == 0) {   // MMA issuer
-        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
-                               ((kRows >> 4) << 24);
-        for (uint32_t c = 0; c < ga.n_chunks; c++) {
-            const uint32_t s = c % kStages;
-            if (!mbar_wait(smem_u32(&full_bar[s]), (c / kStages) & 1u, kPolls)) {
+    } else if (warp == 4) {
+        if (lane == 0) {   // MMA issuer
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
+                                   ((kRows >> 4) << 24);
+            constexpr uint32_t kRegB = region_bytes(NT);
+            uint32_t gc = 0, j = 0;
+            for (uint64_t t = blockIdx.x; t < ga.n_tiles && !fail; t += gridDim.x, j++) {
+                const uint32_t buf = j & 1u;
+                if (!wait_or_fail(smem_u32(&acce_bar[buf]), ((j >> 1) & 1u) ^ 1u, &fail)) {
+                    fail = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + buf * kCols;
+                bool ok = true;
+                for (uint32_t c = 0; c < ga.n_chunks; c++, gc++) {
+                    const uint32_t s = gc % S;
+                    if (!wait_or_fail(smem_u32(&full_bar[s]), (gc / S) & 1u, &fail)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = sbase + s * kStage, sb = sa + 6u * kRegA;
+#pragma unroll
+                    for (uint32_t p = 0; p < 2; p++) {
+                        uint64_t ad[3], bd[3];
+#pragma unroll
+                        for (uint32_t q = 0; q < 3; q++) {
+                            ad[q] = smem_desc(sa + (3u * p + q) * kRegA, 128u, kPitch);
+                            bd[q] = smem_desc(sb + (3u * p + q) * kRegB, 128u, kPitch);
+                        }
+                        // h*h, h*m, m*h, h*l, l*h, m*m
+                        mma_bf16(d, ad[0], bd[0], idesc, (c | p) != 0u);
+                        mma_bf16(d, ad[0], bd[1], idesc, 1u);
+                        mma_bf16(d, ad[1], bd[0], idesc, 1u);
+                        mma_bf16(d, ad[0], bd[2], idesc, 1u);
+                        mma_bf16(d, ad[2], bd[0], idesc, 1u);
+                        mma_bf16(d, ad[1], bd[1], idesc, 1u);
+                    }
+                    mma_commit(smem_u32(&empty_bar[s]));
+                }
+                if (!ok) {
+                    fail = 1;
+                    break;
+                }
+                mma_commit(smem_u32(&accf_bar[buf]));
+            }
+            // every MMA issued so far completes before the tensor memory is freed
+            mma_commit(smem_u32(&drain_bar));
+            if (!mbar_wait(smem_u32(&drain_bar), 0, kPolls)) fail = 1;
+        }
+        __syncwarp();
+    } else {
+        // epilogue: warp w reads tensor-memory lanes 32q ... 32q + 31 (q = w mod 4), i.e.
+        // complex rows m = mt*64 + 16q + lane/2 (Re in the even lane, Im in the odd one). Each
+        // block of up to 32 columns goes through the warp's padded transpose buffer, so that
+        // the warp then stores 32 consecutive columns of one row of C at a time.
+        const uint32_t q = warp & 3u;
+        unsigned char *tb = gsm + S * kStage + q * 16u * kTPitch;
+        const uint32_t s = lane & 1u, mrow = lane >> 1;
+        uint32_t j = 0;
+        for (uint64_t t = blockIdx.x; t < ga.n_tiles && !fail; t += gridDim.x, j++) {
+            const TileCoord tc = tile_coord(t, ga);
+            const uint32_t buf = j & 1u;
+            // this warp's 16 row offsets in C and the tile's base, while the MMAs run
+            const uint32_t my_row = pext_runs(tc.mt * 64u + 16u * q + (lane & 15u), g.cm, g.n_cm);
+            uint32_t roff[16];
+#pragma unroll
+            for (uint32_t i = 0; i < 16; i++) roff[i] = __shfl_sync(0xffffffffu, my_row, i);
+            float2 *Cb = ga.arenas + (uint64_t)tc.il * ga.a.arena_elems + g.c_off + pext_runs(tc.beta, g.cb, g.n_cb);
+            if (!wait_or_fail(smem_u32(&accf_bar[buf]), (j >> 1) & 1u, &fail)) {
                 fail = 1;
                 break;
             }
             tc_fence_after();
-            const uint32_t sa = sbase + s * kStage, sb = sa + 6u * kRegA;
-            constexpr uint32_t kRegB = region_bytes(NT);
-#pragma unroll
-            for (uint32_t p = 0; p < 2; p++) {
-                uint64_t ad[3], bd[3];
-#pragma unroll
-                for (uint32_t q = 0; q < 3; q++) {
-                    ad[q] = smem_desc(sa + (3u * p + q) * kRegA, 128u, kPitch);
-                    bd[q] = smem_desc(sb + (3u * p + q) * kRegB, 128u, kPitch);
+            const uint32_t taddr = tmem + ((q * 32u) << 16) + buf * kCols;
+            for (uint32_t j0 = 0; j0 < (uint32_t)NT; j0 += kW) {
+                const uint32_t coff = pext_runs(tc.nt * (uint32_t)NT + j0 + (lane % kW), g.cn, g.n_cn);
+                uint32_t r[kW];
+                if constexpr (kW == 32) {
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+                        "%30, %31}, [%32];"
+                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+                          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+                          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                        : "r"(taddr + j0));
+                } else {
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                        "%12, %13, %14, %15}, [%16];"
+                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                          "=r"(r[14]), "=r"(r[15])
+                        : "r"(taddr + j0));
                 }
-                // h*h, h*m, m*h, h*l, l*h, m*m
-                mma_bf16(tmem, ad[0], bd[0], idesc, (c | p) != 0u);
-                mma_bf16(tmem, ad[0], bd[1], idesc, 1u);
-                mma_bf16(tmem, ad[1], bd[0], idesc, 1u);
-                mma_bf16(tmem, ad[0], bd[2], idesc, 1u);
-                mma_bf16(tmem, ad[2], bd[0], idesc, 1u);
-                mma_bf16(tmem, ad[1], bd[1], idesc, 1u);
-            }
-            mma_commit(smem_u32(&empty_bar[s]));
-        }
-        // always signal the accumulator, so the MMAs issued so far are waited for
-        mma_commit(smem_u32(&acc_bar));
-    }
-    __syncwarp();
-    bool ok = true;
-    if (warp < 4) ok = mbar_wait(smem_u32(&acc_bar), 0, kPolls);
-    tc_fence_after();
-    const bool good = __syncthreads_and(ok) && !fail;
-    if (good && warp < 4) {
-        // warp w holds tile rows 32w..32w+31, i.e. complex rows m = mt*64 + 16w + lane/2 (Re in
-        // the even lane, Im in the odd one). Each block of up to 32 columns goes through a
-        // padded shared-memory transpose (the operand stages are free now), so that a warp
-        // then stores 32 consecutive columns of one row of C at a time.
-        constexpr uint32_t kW = NT < 32 ? (uint32_t)NT : 32u;   // columns per block
-        constexpr uint32_t kTPitch = 8u * kW + 8u;               // bytes per row of the transpose
-        unsigned char *tb = gsm + warp * 16u * kTPitch;
-        const uint32_t s = lane & 1u, mrow = lane >> 1;
-        const uint32_t taddr = tmem + ((warp * 32u) << 16);
-        float2 *Cb = arena + g.c_off + pext_runs(beta, g.cb, g.n_cb);
-        for (uint32_t j0 = 0; j0 < (uint32_t)NT; j0 += kW) {
-            uint32_t r[kW];
-            if constexpr (kW == 32) {
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-                    "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
-                    "[%32];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                      "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                      "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-                      "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-                      "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                    : "r"(taddr + j0));
-            } else {
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-                    "%12, %13, %14, %15}, [%16];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                      "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                      "=r"(r[14]), "=r"(r[15])
-                    : "r"(taddr + j0));
-            }
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (uint32_t n = 0; n < kW; n++)
-                *reinterpret_cast<uint32_t *>(tb + mrow * kTPitch + n * 8u + s * 4u) = r[n];
-            __syncwarp();
-            if (lane < kW) {
-                const uint32_t coff = tcn[j0 + lane];
-#pragma unroll 4
-                for (uint32_t i = 0; i < 16; i++) {
-                    const float2 v = *reinterpret_cast<const float2 *>(tb + i * kTPitch + lane * 8u);
-                    Cb[tcm[warp * 16u + i] + coff] = v;
+                for (uint32_t n = 0; n < kW; n++)
+                    *reinterpret_cast<uint32_t *>(tb + mrow * kTPitch + n * 8u + s * 4u) = r[n];
+                __syncwarp();
+                if (lane < kW) {
+#pragma unroll
+                    for (uint32_t i = 0; i < 16; i++)
+                        Cb[roff[i] + coff] = *reinterpret_cast<const float2 *>(tb + i * kTPitch + lane * 8u);
                 }
+                __syncwarp();
             }
-            __syncwarp();
+            // the accumulator's reads are done: the MMAs of the tile after next may reuse it
+            tc_fence_before();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[buf])) : "memory");
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 4) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2u * kCols) : "memory");
     }
-    if (!good && threadIdx.x == 0) atomicCAS(ga.a.status, 0u, 4u /* QVX_ETIMEOUT */);
+    if (fail && threadIdx.x == 0) atomicCAS(ga.a.status, 0u, 4u /* QVX_ETIMEOUT */);
 }
 
 }  // namespace
@@ -382,34 +470,33 @@ __global__ void __launch_bounds__(kThreads, 3) gemm_tc_kernel(GemmArgs ga) {
 uint32_t gemm_nt(const GemmStep &g) { return g.nn >= 7 ? 128u : (1u << g.nn); }
 
 template <int NT>
-static cudaError_t launch_gemm_nt(const GemmArgs &ga, cudaStream_t s) {
-    static int ready[64] = {0};
+static cudaError_t launch_gemm_nt(GemmArgs ga, cudaStream_t s) {
+    // dynamic shared memory: the stage ring, the epilogue's transpose buffers and the summed
+    // index tables (the largest K is 1024), the same for every step of this tile width
+    constexpr size_t kSmem = (size_t)n_stages<NT>() * stage_bytes(NT) + epi_bytes<NT>() + 4u * 2u * 1024u;
+    static int per_sm[64] = {0}, sms[64] = {0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    size_t smem = (size_t)kStages * stage_bytes(NT) + 4u * (2u * ga.n_chunks * kKq + 64u + (uint32_t)NT);
-    constexpr size_t kMaxSmem = 200 * 1024;
-    // keep the CTAs an SM can hold within its 512 tensor-memory columns, so that no
-    // allocation ever waits for another CTA's columns
-    const int cols = NT < 32 ? 32 : NT;
-    const int max_ctas = 512 / cols;
-    if (dev < 0 || dev >= 64 || !ready[dev]) {
-        if ((e = cudaFuncSetAttribute(gemm_tc_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem)) !=
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!per_sm[dev]) {
+        if ((e = cudaFuncSetAttribute(gemm_tc_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem)) !=
             cudaSuccess)
             return e;
-        if (dev >= 0 && dev < 64) ready[dev] = 1;
-    }
-    for (;;) {
         int n = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gemm_tc_kernel<NT>, kThreads, smem)) != cudaSuccess)
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gemm_tc_kernel<NT>, kThreads, kSmem)) != cudaSuccess)
             return e;
-        if (n <= max_ctas) break;
-        if (smem >= kMaxSmem) return cudaErrorInvalidConfiguration;
-        smem += 8 * 1024;
+        if ((e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        // the CTAs an SM holds stay within its 512 tensor-memory columns, so that no
+        // allocation ever waits for another CTA's columns
+        const int cols = 2 * (NT < 32 ? 32 : NT);
+        per_sm[dev] = n < 1 ? -1 : std::min(n, 512 / cols);
     }
-    const uint64_t blocks = ((uint64_t)ga.n_items << ga.g.nb) * ga.n_mt * ga.n_nt;
-    if (blocks == 0 || blocks > 0x7fffffffull) return cudaErrorInvalidConfiguration;
-    gemm_tc_kernel<NT><<<(unsigned)blocks, kThreads, smem, s>>>(ga);
+    if (per_sm[dev] < 1) return cudaErrorInvalidConfiguration;
+    ga.n_tiles = ((uint64_t)ga.n_items << ga.g.nb) * ga.n_mt * ga.n_nt;
+    if (ga.n_tiles == 0) return cudaErrorInvalidConfiguration;
+    const uint64_t grid = std::min<uint64_t>(ga.n_tiles, (uint64_t)sms[dev] * (uint64_t)per_sm[dev]);
+    gemm_tc_kernel<NT><<<(unsigned)grid, kThreads, kSmem, s>>>(ga);
     return cudaGetLastError();
 }
 

@@ -396,8 +396,9 @@ def kernel_roofline(records, hbm_gbs, bf16_tflops):
 def time_form(plan, bits, reps, flush, stream):
     """Mean device ms per amplitude call of `plan` (one warm-up call; L2 flushed before each)."""
     import torch
-    ws = plan.workspace(bits.numel(), bits.device)
-    out = torch.empty(2 * bits.numel() << plan.n_open, dtype=torch.float64, device=bits.device)
+    n = bits.numel() // plan.words
+    ws = plan.workspace(n, bits.device)
+    out = torch.empty(2 * n << plan.n_open, dtype=torch.float64, device=bits.device)
     plan.amplitude(bits, workspace=ws, out=out, validate=False)
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
@@ -499,7 +500,7 @@ def main():
 
     # end to end through the public call: pinned host bitstrings in, amplitudes (and
     # gradients) out
-    h_bits = torch.tensor([b - (1 << 64) if b >= 1 << 63 else b for b in bits_host], dtype=torch.int64).pin_memory()
+    h_bits = torch.tensor(q.bitstring_words(bits_host, plan.words), dtype=torch.int64).pin_memory()
     h_out = torch.empty(2 * B << plan.n_open, dtype=torch.float64).pin_memory()
     h_gout = torch.empty(gout.numel(), dtype=torch.float64).pin_memory()
     h_gath = torch.empty(gathered.numel(), dtype=torch.float64).pin_memory() if shard else None
@@ -581,7 +582,7 @@ def main():
         "complex_tflops": flops / (ms_step / 1e3) / 1e12,
         "roofline": roof,
         "kernels": kernels,
-        "e2e": {"value": e2e, "unit": "amplitudes/s", "h2d_bytes_per_step": 8 * B,
+        "e2e": {"value": e2e, "unit": "amplitudes/s", "h2d_bytes_per_step": 8 * B * plan.words,
                 "d2h_bytes_per_step": (16 * B * world if shard else 16 * (B << plan.n_open))
                 + (8 * gout.numel() if grad else 0)},
         "gpu_launches": launches,

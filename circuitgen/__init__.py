@@ -198,10 +198,18 @@ def worked_example() -> Circuit:
 
 
 def random_bitstrings(n_qubits: int, count: int, seed: int) -> list:
-    """`count` uniform n-bit strings (bit q = qubit q) from splitmix64(seed)."""
+    """`count` uniform n-bit strings (bit q = qubit q) from splitmix64(seed): one draw per
+    string up to 64 qubits; above that, one draw per 64 bits, lowest word first."""
     rng = SplitMix64(seed)
     mask = (1 << n_qubits) - 1
-    return [rng.next() & mask for _ in range(count)]
+    words = (n_qubits + 63) // 64
+    out = []
+    for _ in range(count):
+        v = 0
+        for w in range(words):
+            v |= rng.next() << (64 * w)
+        out.append(v & mask)
+    return out
 
 
 def count_gates(circ: Circuit) -> tuple:

@@ -20,7 +20,9 @@
  *     plan's device image, the intermediate tensors and a device status word.
  *   - Streams: all device work is enqueued on the caller's stream; calls return without
  *     synchronising unless stated.
- *   - Bitstrings: bit q of a uint64_t is the value of qubit q, so n_qubits <= 64.
+ *   - Bitstrings: W = ceil(n_qubits / 64) uint64_t words per bitstring (n_qubits <= 128, so
+ *     W is 1 or 2), bitstring b at words [b*W, b*W + W): the value of qubit q is bit q % 64
+ *     of word q / 64. With up to 64 qubits a bitstring is one uint64_t, bit q = qubit q.
  *   - Amplitudes: complex128, interleaved (re, im).
  *   - Errors: every call returns a qvx_status; qvx_last_error() gives a message for the
  *     calling thread's last failure. Failures inside kernels (a bounded wait that ran out, a
@@ -77,7 +79,7 @@ typedef struct {
 } qvx_gate;
 
 typedef struct {
-    int32_t n_qubits;      /* 1..64 */
+    int32_t n_qubits;      /* 1..128 */
     int32_t reserved;
     int64_t n_gates;
     const qvx_gate *gates; /* in time order */
@@ -203,7 +205,8 @@ qvx_status qvx_workspace_init(const qvx_plan *plan, void *workspace_dev, size_t 
 
 /* alpha_b = <x_b|C|0> for b < batch. bitstrings_dev: batch uint64 on the device;
  * amps_dev: 2*batch doubles on the device (2*batch*2^n_open_qubits with open qubits:
- * amplitude j of bitstring b at amps_dev[2*(b*2^n_open + j)]). Slice terms are computed in complex64 and
+ * amplitude j of bitstring b at amps_dev[2*(b*2^n_open + j)]); bitstrings_dev holds batch*W
+ * words (W per bitstring, see the conventions). Slice terms are computed in complex64 and
  * added exactly (128-bit fixed point, scale 2^-100), then rounded once to FP64. */
 qvx_status qvx_amplitude(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch,
                          double *amps_dev, void *workspace_dev, size_t workspace_bytes,

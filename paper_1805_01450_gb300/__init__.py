@@ -160,6 +160,35 @@ def graph_export(circ):
             [(ed[2 * i], ed[2 * i + 1]) for i in range(ne.value)])
 
 
+def bitstring_words(bitstrings, words):
+    """Python ints (bit q = qubit q) as the int64 words of the C interface: `words` words per
+    bitstring, bit q in word q // 64 (two's-complement views of the unsigned words)."""
+    out = []
+    for b in bitstrings:
+        v = int(b)
+        for w in range(words):
+            u = (v >> (64 * w)) & ((1 << 64) - 1)
+            out.append(u - (1 << 64) if u >= 1 << 63 else u)
+    return out
+
+
+def bits_tensor(bitstrings, words, device=None):
+    """A contiguous int64 device tensor of `words` words per bitstring, from a tensor (already
+    in that layout) or from Python ints."""
+    import torch
+    if isinstance(bitstrings, torch.Tensor):
+        t = bitstrings
+        if t.dtype != torch.int64:
+            raise TypeError("bitstrings must be int64 words")
+        if t.numel() % words:
+            raise QvxError(QVX_EINVAL, f"bitstring words: a multiple of {words} expected")
+    else:
+        t = torch.tensor(bitstring_words(bitstrings, words), dtype=torch.int64)
+    if not t.is_cuda:
+        t = t.to(device if device is not None else "cuda")
+    return t.contiguous().view(-1)
+
+
 def _stream_ptr(stream):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -201,6 +230,7 @@ class Plan:
                                  ctypes.byref(h)))
         self._h = h
         self.n_qubits = circ.n_qubits
+        self.words = (circ.n_qubits + 63) // 64   # int64 words per bitstring
         inf = PlanInfo()
         _check(L.qvx_plan_get_info(h, ctypes.byref(inf)))
         self.info = {f[0]: getattr(inf, f[0]) for f in PlanInfo._fields_}
@@ -260,26 +290,15 @@ class Plan:
             self._ws[key] = self.workspace(batch, device)
         return self._ws[key]
 
-    @staticmethod
-    def _bits(bitstrings, device=None):
-        import torch
-        if isinstance(bitstrings, torch.Tensor):
-            t = bitstrings
-        else:
-            vals = [int(b) for b in bitstrings]
-            vals = [v - (1 << 64) if v >= (1 << 63) else v for v in vals]
-            t = torch.tensor(vals, dtype=torch.int64)
-        if t.dtype != torch.int64:
-            raise TypeError("bitstrings must be int64 (bit q = qubit q)")
-        if not t.is_cuda:
-            t = t.to(device if device is not None else "cuda")
-        return t.contiguous()
+    def _bits(self, bitstrings, device=None):
+        return bits_tensor(bitstrings, self.words, device)
 
     def _check_bits(self, bits):
-        if self.n_qubits < 64:
-            import torch
-            bad = (bits >> self.n_qubits) != 0
-            if bool(torch.any(bad)):
+        import torch
+        w = bits.view(-1, self.words)
+        for j in range(self.words):
+            valid = self.n_qubits - 64 * j
+            if valid < 64 and bool(torch.any((w[:, j] >> valid) != 0)):
                 raise QvxError(QVX_EINVAL, "bitstring has bits at or above n_qubits")
 
     def amplitude(self, bitstrings, workspace=None, out=None, stream=None, slice_begin=0,
@@ -290,7 +309,7 @@ class Plan:
         bits = self._bits(bitstrings)
         if validate:
             self._check_bits(bits)
-        n = bits.numel()
+        n = bits.numel() // self.words
         ws = workspace if workspace is not None else self._ws_for(n, bits.device)
         m = 1 << self.n_open
         if out is None:
@@ -310,7 +329,7 @@ class Plan:
         import torch
         bits = self._bits(bitstrings)
         self._check_bits(bits)
-        n = bits.numel()
+        n = bits.numel() // self.words
         npar = self.info["n_params"]
         ws = workspace if workspace is not None else self._ws_for(n, bits.device)
         amps = torch.empty(2 * n, dtype=torch.float64, device=bits.device)
@@ -339,7 +358,7 @@ class Plan:
         set-up is not captured."""
         import torch
         bits = self._bits(bitstrings)
-        n = bits.numel()
+        n = bits.numel() // self.words
         ws = workspace if workspace is not None else self._ws_for(n, bits.device)
         out = torch.empty(2 * n * (1 << self.n_open), dtype=torch.float64, device=bits.device)
         side = torch.cuda.Stream(device=bits.device)
@@ -362,12 +381,11 @@ class Plan:
         if isinstance(bitstrings, torch.Tensor):
             h = bitstrings
         else:
-            vals = [int(b) for b in bitstrings]
-            h = torch.tensor([v - (1 << 64) if v >= (1 << 63) else v for v in vals], dtype=torch.int64)
+            h = torch.tensor(bitstring_words(bitstrings, self.words), dtype=torch.int64)
         if h.is_cuda or h.dtype != torch.int64:
             raise TypeError("bitstrings must be a CPU int64 tensor or a list")
         h = h.contiguous()
-        n = h.numel()
+        n = h.numel() // self.words
         if out is None:
             out = torch.empty(2 * n * (1 << self.n_open), dtype=torch.float64)
         dev = torch.device("cuda", torch.cuda.current_device())
@@ -382,7 +400,7 @@ class Plan:
         import torch
         bits = self._bits(bitstrings)
         self._check_bits(bits)
-        n = bits.numel()
+        n = bits.numel() // self.words
         if slice_count is None:
             slice_count = self.n_slice_terms - slice_begin
         ws = workspace if workspace is not None else self._ws_for(n, bits.device)
@@ -398,7 +416,7 @@ class Plan:
         """plan.amplitude over all slices (device int64 bitstrings, caller's workspace and
         float64 output) with a CUDA event before and after every kernel launch, appended to
         the plan's launch log (read_profile). Does not synchronise."""
-        _check(lib().qvx_amplitude_profiled(self._h, ctypes.c_void_p(bits.data_ptr()), bits.numel(),
+        _check(lib().qvx_amplitude_profiled(self._h, ctypes.c_void_p(bits.data_ptr()), bits.numel() // self.words,
                                             ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(workspace.data_ptr()),
                                             workspace.numel(), _stream_ptr(stream)))
 

@@ -13,13 +13,14 @@ from __future__ import annotations
 
 import time
 
-from . import Plan
+from . import Plan, bits_tensor
 
 
 def _time_plan(p, bits, flush, stream, reps, warmup):
     import torch
-    ws = p.workspace(bits.numel(), bits.device)
-    out = torch.empty(2 * bits.numel() << p.n_open, dtype=torch.float64, device=bits.device)
+    n = bits.numel() // p.words
+    ws = p.workspace(n, bits.device)
+    out = torch.empty(2 * n << p.n_open, dtype=torch.float64, device=bits.device)
     for _ in range(warmup):
         p.amplitude(bits, workspace=ws, out=out, validate=False)
     torch.cuda.synchronize()
@@ -56,7 +57,7 @@ def autotune(circ, bitstrings, n_slices=-1, slices=None, order=None, inner=None,
     estimate; timing decides between the plans it keeps), carried as "plan_trials=T"."""
     import torch
     dev = torch.device(device if device is not None else "cuda")
-    bits = Plan._bits(bitstrings, dev)
+    bits = bits_tensor(bitstrings, (circ.n_qubits + 63) // 64, dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
     results, best, best_t = [], None, None

@@ -25,6 +25,9 @@ qvx_status cuda_fail(cudaError_t e, const char *where) {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// 64-bit words per bitstring: bit q of a bitstring is bit q % 64 of its word q / 64.
+uint32_t words_of(const qvx::Plan &p) { return (uint32_t)((p.model.n_qubits + 63) / 64); }
+
 // Workspace layout: [device image][status word, CTA counter][host staging: bitstrings,
 // amplitudes][item partials][stepwise arenas], and for gradient plans [derivative
 // partials][gradient arenas]
@@ -42,7 +45,7 @@ WsLayout layout_of(const qvx::Plan &p, int64_t batch) {
     w.status = align256(p.image.size());
     w.stage_bits = w.status + 256;
     const size_t slots = (size_t)std::max<int64_t>(batch, 1) << p.open_qubits.size();   // amplitudes per call
-    w.stage_amps = align256(w.stage_bits + (size_t)std::max<int64_t>(batch, 1) * 8);
+    w.stage_amps = align256(w.stage_bits + (size_t)std::max<int64_t>(batch, 1) * 8 * words_of(p));
     w.partials = align256(w.stage_amps + slots * 16);
     w.arenas = align256(w.partials + slots * (size_t)n_outer * sizeof(qvx::ExactPair));
     w.items_in_flight = 0;
@@ -148,6 +151,7 @@ qvx_status run_items(qvx_plan *plan, const uint64_t *bits, int64_t batch, int64_
     unsigned char *base = static_cast<unsigned char *>(ws);
     a.image = base + w.image;
     a.bitstrings = bits;
+    a.words = words_of(p);
     a.batch = batch;
     a.o_begin = o_begin;
     a.o_count = o_end - o_begin;
@@ -586,15 +590,20 @@ qvx_status qvx_amplitude_host(qvx_plan *plan, const uint64_t *bitstrings_host, i
     if (batch == 0) return QVX_OK;
     if (!bitstrings_host || !amps_host) return fail(QVX_EINVAL, "null host buffer");
     const int n = plan->p.model.n_qubits;
+    const uint32_t W = words_of(plan->p);
     for (int64_t b = 0; b < batch; b++)
-        if (n < 64 && (bitstrings_host[b] >> n) != 0) return fail(QVX_EINVAL, "bitstring has bits at or above n_qubits");
+        for (uint32_t wd = 0; wd < W; wd++) {
+            const int valid = n - 64 * (int)wd;   // bits of this word that are qubits
+            if (valid < 64 && (bitstrings_host[b * W + wd] >> valid) != 0)
+                return fail(QVX_EINVAL, "bitstring has bits at or above n_qubits");
+        }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     unsigned char *base = static_cast<unsigned char *>(ws);
     cudaError_t e;
     const uint64_t *bits_dev = static_cast<const uint64_t *>(pinned_device_ptr(bitstrings_host));
     if (!bits_dev) {
         bits_dev = reinterpret_cast<const uint64_t *>(base + w.stage_bits);
-        if ((e = cudaMemcpyAsync(base + w.stage_bits, bitstrings_host, (size_t)batch * 8, cudaMemcpyHostToDevice, st)) !=
+        if ((e = cudaMemcpyAsync(base + w.stage_bits, bitstrings_host, (size_t)batch * 8 * W, cudaMemcpyHostToDevice, st)) !=
             cudaSuccess)
             return cuda_fail(e, "bitstring upload");
     }
@@ -654,6 +663,7 @@ qvx_status qvx_amplitude_grad(qvx_plan *plan, const uint64_t *bitstrings_dev, in
     qvx::GradArgs g{};
     g.image = base + w.image;
     g.bitstrings = bitstrings_dev;
+    g.words = words_of(p);
     g.batch = batch;
     g.o_count = n_outer;
     g.arenas = reinterpret_cast<float2 *>(base + w.grad_arenas);

@@ -38,7 +38,8 @@ struct DevLeaf {
     uint32_t n_elem;               // entries after restriction (2^consumer rank)
     uint32_t n_fixed;              // modes fixed per work item
     uint32_t pad;
-    uint8_t fixed_src[kMaxFixed];  // < 64: bit of the bitstring; >= 64: bit (src-64) of the outer slice number
+    uint8_t fixed_src[kMaxFixed];  // < 128: bit src of the bitstring (word src / 64, bit src % 64);
+                                   // >= 128: bit (src - 128) of the outer slice number
     uint8_t fixed_pos[kMaxFixed];  // bit position of that mode in the stored leaf
 };
 
@@ -139,7 +140,8 @@ struct DevProgram {
     uint64_t final_off;            // arena offset of the final tensor (over the inner slice modes)
     uint32_t n_inner;              // inner (open) sliced variables
     uint32_t final_present;        // inner bits that are modes of the final tensor, low to high
-    uint64_t zero_mask;            // amplitude is 0 when x & zero_mask != 0
+    uint64_t zero_mask;            // amplitude is 0 when x & zero_mask != 0 (bitstring word 0;
+                                   // word 1 against zero_mask_hi)
     double scalar_re, scalar_im;   // constant prefactor
     uint64_t n_outer;              // work items per bitstring = 2^(sliced - inner)
     uint64_t steps_off, leaves_off, leaf_data_off;  // byte offsets
@@ -165,6 +167,7 @@ struct DevProgram {
     uint64_t gphase_entry_off;     // byte offset of n_grad_phases + 1 record indices (phase starts)
     uint64_t gemm_off;             // byte offset of n_steps GemmStep (0 if absent)
     uint64_t image_bytes;
+    uint64_t zero_mask_hi;         // qubits 64..127 of the zero mask
 };
 
 constexpr uint32_t kProgramMagic = 0x51565831u;  // "QVX1"
@@ -174,7 +177,7 @@ constexpr uint32_t kProgramMagic = 0x51565831u;  // "QVX1"
 namespace qvx {
 static_assert(sizeof(DevStep) == 136, "DevStep layout");
 static_assert(sizeof(DevLeaf) == 40, "DevLeaf layout");
-static_assert(sizeof(DevProgram) == 320, "DevProgram layout");
+static_assert(sizeof(DevProgram) == 328, "DevProgram layout");
 static_assert(sizeof(GemmStep) == 336, "GemmStep layout");
 static_assert(sizeof(GradEntry) == 16, "GradEntry layout");
 static_assert(sizeof(RegTileStep) == 224, "RegTileStep layout");

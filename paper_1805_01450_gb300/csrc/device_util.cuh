@@ -15,10 +15,29 @@ __device__ __forceinline__ uint32_t pext_runs(uint32_t c, const DevRun *runs, in
 }
 
 
+// A bitstring of up to 128 qubits: bit q is bit q % 64 of word q / 64 (word 1 is zero for
+// n_qubits <= 64, whose bitstrings are one word each).
+struct Bits {
+    uint64_t w0, w1;
+};
+
+__device__ __forceinline__ Bits load_bits(const uint64_t *bitstrings, int64_t b, uint32_t words) {
+    Bits x;
+    x.w0 = bitstrings[b * words];
+    x.w1 = words > 1 ? bitstrings[b * words + 1] : 0ull;
+    return x;
+}
+
+// Nonzero when a qubit without a non-diagonal gate (its output equals its input 0) is 1 in x.
+__device__ __forceinline__ bool bits_hit(const Bits &x, uint64_t mask_lo, uint64_t mask_hi) {
+    return ((x.w0 & mask_lo) | (x.w1 & mask_hi)) != 0ull;
+}
+
 // First stored entry of `leaf` restricted to this work item (bitstring x, outer slice o).
 // The leaf is read as five 8-byte words (data offset, fixed-mode count, the packed source
-// and position bytes) and the up to 12 fixed modes are applied without a loop-carried branch.
-__device__ __forceinline__ uint32_t leaf_base(const DevLeaf &L, uint64_t x, uint64_t o) {
+// and position bytes) and the up to 12 fixed modes are applied without a loop-carried branch:
+// a source below 64 is a bit of bitstring word 0, below 128 one of word 1, else a bit of o.
+__device__ __forceinline__ uint32_t leaf_base(const DevLeaf &L, const Bits &x, uint64_t o) {
     static_assert(sizeof(DevLeaf) == 40 && kMaxFixed == 12, "DevLeaf layout");
     const uint2 *w = reinterpret_cast<const uint2 *>(&L);
     const uint2 w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3], w4 = w[4];
@@ -30,7 +49,7 @@ __device__ __forceinline__ uint32_t leaf_base(const DevLeaf &L, uint64_t x, uint
         if (f < nf) {
             const uint32_t src = (srcw[f >> 2] >> (8u * (f & 3u))) & 0xffu;
             const uint32_t pos = (posw[f >> 2] >> (8u * (f & 3u))) & 0xffu;
-            const uint64_t v = src < 64u ? x : o;
+            const uint64_t v = src < 64u ? x.w0 : (src < 128u ? x.w1 : o);
             off += (uint32_t)((v >> (src & 63u)) & 1ull) << pos;
         }
     }

@@ -56,7 +56,7 @@ __device__ __forceinline__ const float2 *gemm_operand(const LaunchArgs &a, const
     const DevProgram *P = reinterpret_cast<const DevProgram *>(img);
     const DevLeaf *leaves = reinterpret_cast<const DevLeaf *>(img + P->leaves_off);
     const float2 *ldata = reinterpret_cast<const float2 *>(img + P->leaf_data_off);
-    const uint64_t x = a.bitstrings[item / a.o_count];
+    const Bits x = load_bits(a.bitstrings, item / a.o_count, a.words);
     const uint64_t o = (uint64_t)(a.o_begin + item % a.o_count);
     return ldata + leaf_base(leaves[ref], x, o);
 }
@@ -150,26 +150,34 @@ __device__ __forceinline__ void store_b(unsigned char *sb, const float2 *v, uint
     }
 }
 
-// One chunk's operand entries held in registers between their loads and their conversion:
-// 8 summed entries of an A row, and of each of the thread's U B columns.
+// Raw staging of the producers' operand loads: each producer thread copies its own 8-byte
+// complex64 entries of a chunk (8 summed entries of its A row, and of each of its U B
+// columns) into shared memory with cp.async, several chunks ahead of the conversion, and
+// reads them back itself once its copy group has landed (so no barrier is needed). Entry j of
+// a thread's chunk sits at raw[(slot * (8 + 8U) + j) * 128 + thread]: consecutive threads
+// touch consecutive 8-byte words.
 template <uint32_t U>
-struct Chunk {
-    float2 a[8];
-    float2 b[U][8];
-};
+__host__ __device__ constexpr uint32_t raw_entries() { return 8u + 8u * U; }
 
-// Loads of one chunk; ka and kb are the CTA's shared-memory tables of the summed index's
-// offsets in A and in B (8 consecutive entries read as two 16-byte words).
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// The copies of chunk c of a tile into raw slot `slot`; ka and kb are the CTA's shared-memory
+// tables of the summed index's offsets in A and in B.
 template <uint32_t U>
-__device__ __forceinline__ void load_chunk(Chunk<U> &ch, uint32_t c, uint32_t h, const float2 *Arow,
-                                           const float2 *const *Bcol, const uint32_t *bh, bool b_on,
-                                           const uint32_t *ka, const uint32_t *kb) {
+__device__ __forceinline__ void issue_chunk(uint32_t raw_slot, uint32_t c, uint32_t h, const float2 *Arow,
+                                            const float2 *const *Bcol, const uint32_t *bh, bool b_on,
+                                            const uint32_t *ka, const uint32_t *kb) {
     {
         const uint4 o0 = *reinterpret_cast<const uint4 *>(ka + c * kKq + 8u * h);
         const uint4 o1 = *reinterpret_cast<const uint4 *>(ka + c * kKq + 8u * h + 4u);
         const uint32_t o[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
 #pragma unroll
-        for (int j = 0; j < 8; j++) ch.a[j] = __ldg(Arow + o[j]);
+        for (int j = 0; j < 8; j++) cp_async8(raw_slot + (uint32_t)j * 128u * 8u, Arow + o[j]);
     }
     if (b_on) {
 #pragma unroll
@@ -178,9 +186,15 @@ __device__ __forceinline__ void load_chunk(Chunk<U> &ch, uint32_t c, uint32_t h,
             const uint4 o1 = *reinterpret_cast<const uint4 *>(kb + c * kKq + 8u * bh[i] + 4u);
             const uint32_t o[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
 #pragma unroll
-            for (int j = 0; j < 8; j++) ch.b[i][j] = __ldg(Bcol[i] + o[j]);
+            for (int j = 0; j < 8; j++) cp_async8(raw_slot + (8u + 8u * i + (uint32_t)j) * 128u * 8u, Bcol[i] + o[j]);
         }
     }
+}
+
+// Eight staged entries (entry j0 ... j0 + 7 of the thread's chunk) back into registers.
+__device__ __forceinline__ void read_raw8(const float2 *raw_slot_t, uint32_t j0, float2 *v) {
+#pragma unroll
+    for (uint32_t j = 0; j < 8; j++) v[j] = raw_slot_t[(j0 + j) * 128u];
 }
 
 struct GemmArgs {
@@ -194,7 +208,8 @@ struct GemmArgs {
 
 // Operand stages of the shared-memory ring: three of 52 KB for 128-column tiles, four below.
 template <int NT>
-__host__ __device__ constexpr uint32_t n_stages() { return NT >= 128 ? 3u : 4u; }
+__host__ __device__ constexpr uint32_t n_stages() { return NT >= 128 ? 2u : 3u; }
+constexpr uint32_t kRaw = 4;           // chunks of raw operand copies in flight per producer
 template <int NT>
 __host__ __device__ constexpr uint32_t epi_cols() { return NT < 32 ? (uint32_t)NT : 32u; }
 // bytes between rows of an epilogue warp's transpose buffer (16 rows of up to 32 columns)
@@ -258,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(GemmArgs ga) {
     constexpr uint32_t kRegA = region_bytes(kRows), kStage = stage_bytes(NT);
     constexpr uint32_t kUnits = (2u * (uint32_t)NT + 127u) / 128u;   // B units per producer thread
     constexpr uint32_t kW = epi_cols<NT>(), kTPitch = epi_pitch<NT>();
-    using Chunk = qvx::Chunk<kUnits>;
+    constexpr uint32_t kRawSlot = raw_entries<kUnits>() * 128u * 8u;   // bytes of one raw slot
     extern __shared__ __align__(1024) unsigned char gsm[];
     __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S], accf_bar[2], acce_bar[2], drain_bar;
     __shared__ uint32_t tmem_slot;
@@ -287,7 +302,8 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(GemmArgs ga) {
     }
     // the summed index's offsets in A and B (bit-run maps evaluated once per CTA)
     const uint32_t K = ga.n_chunks * kKq;
-    uint32_t *tka = reinterpret_cast<uint32_t *>(gsm + S * kStage + epi_bytes<NT>());
+    float2 *raw = reinterpret_cast<float2 *>(gsm + S * kStage + epi_bytes<NT>());
+    uint32_t *tka = reinterpret_cast<uint32_t *>(gsm + S * kStage + epi_bytes<NT>() + kRaw * kRawSlot);
     uint32_t *tkb = tka + K;
     for (uint32_t i = threadIdx.x; i < K; i += kThreads) {
         tka[i] = pext_runs(i, g.ak, g.n_ak);
@@ -299,47 +315,69 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(GemmArgs ga) {
     const uint32_t tmem = tmem_slot;
     if (warp < 4) {
         // producers: A rows m = mt*64 + 32*(warp&1) + lane, summed half h = warp>>1 of the
-        // chunk; B units (column, half) strided over the 128 threads
+        // chunk; B units (column, half) strided over the 128 threads. The copies run kRaw - 1
+        // chunks ahead of the conversion, across tile boundaries.
         const uint32_t ml = 32u * (warp & 1u) + lane, h = warp >> 1;
         const bool b_on = threadIdx.x < 2u * (uint32_t)NT;   // every unit of a thread shares this
-        uint32_t gc = 0;   // chunks this CTA has produced: the ring position
-        for (uint64_t t = blockIdx.x; t < ga.n_tiles && !fail; t += gridDim.x) {
+        uint32_t bh[kUnits];
+#pragma unroll
+        for (uint32_t i = 0; i < kUnits; i++) bh[i] = (threadIdx.x + 128u * i) / (uint32_t)NT;
+        const uint32_t raw_base = smem_u32(raw) + threadIdx.x * 8u;
+        // load cursor: the tile and chunk whose copies are issued next
+        uint64_t lt = blockIdx.x;
+        uint32_t lc = 0;
+        const float2 *Arow = nullptr, *Bcol[kUnits];
+        auto setup = [&](uint64_t t) {
             const TileCoord tc = tile_coord(t, ga);
             float2 *arena = ga.arenas + (uint64_t)tc.il * ga.a.arena_elems;
             const float2 *A = gemm_operand(ga.a, arena, g.a_off, g.flags & kStepALeaf, ga.item0 + tc.il);
             const float2 *B = gemm_operand(ga.a, arena, g.b_off, g.flags & kStepBLeaf, ga.item0 + tc.il);
-            const float2 *Arow = A + pext_runs(tc.beta, g.ab, g.n_ab) + pext_runs(tc.mt * 64u + ml, g.am, g.n_am);
-            const float2 *Bcol[kUnits];
-            uint32_t bh[kUnits];
+            Arow = A + pext_runs(tc.beta, g.ab, g.n_ab) + pext_runs(tc.mt * 64u + ml, g.am, g.n_am);
             const uint32_t bb = pext_runs(tc.beta, g.bb, g.n_bb);
 #pragma unroll
-            for (uint32_t i = 0; i < kUnits; i++) {
-                const uint32_t u = threadIdx.x + 128u * i;
-                bh[i] = u / (uint32_t)NT;
-                Bcol[i] = B + bb + pext_runs(tc.nt * (uint32_t)NT + u % (uint32_t)NT, g.bn, g.n_bn);
-            }
-            Chunk cur, nxt;
-            load_chunk(cur, 0, h, Arow, Bcol, bh, b_on, tka, tkb);
-            for (uint32_t c = 0; c < ga.n_chunks; c++, gc++) {
-                const uint32_t s = gc % S;
-                if (c + 1 < ga.n_chunks) load_chunk(nxt, c + 1, h, Arow, Bcol, bh, b_on, tka, tkb);
-                if (!wait_or_fail(smem_u32(&empty_bar[s]), ((gc / S) & 1u) ^ 1u, &fail)) {
-                    fail = 1;
-                    break;
+            for (uint32_t i = 0; i < kUnits; i++)
+                Bcol[i] = B + bb + pext_runs(tc.nt * (uint32_t)NT + (threadIdx.x + 128u * i) % (uint32_t)NT, g.bn, g.n_bn);
+        };
+        auto issue_next = [&](uint32_t g_issue) {   // one commit group per chunk, empty at the end
+            if (lt < ga.n_tiles) {
+                issue_chunk<kUnits>(raw_base + (g_issue % kRaw) * kRawSlot, lc, h, Arow, Bcol, bh, b_on, tka, tkb);
+                if (++lc == ga.n_chunks) {
+                    lc = 0;
+                    lt += gridDim.x;
+                    if (lt < ga.n_tiles) setup(lt);
                 }
-                unsigned char *sa = gsm + s * kStage;
-                store_a(sa, cur.a, ml, h);
-                if (b_on) {
+            }
+            cp_async_commit();
+        };
+        setup(lt);
+        const uint64_t my_tiles = (ga.n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
+        const uint64_t total = my_tiles * ga.n_chunks;
+        for (uint32_t i = 0; i + 1 < kRaw; i++) issue_next(i);
+        for (uint64_t gc = 0; gc < total && !fail; gc++) {
+            issue_next((uint32_t)(gc + kRaw - 1));
+            cp_async_wait<kRaw - 1>();   // this thread's copies of chunk gc have landed
+            const uint32_t s = (uint32_t)(gc % S);
+            if (!wait_or_fail(smem_u32(&empty_bar[s]), (uint32_t)((gc / S) & 1u) ^ 1u, &fail)) {
+                fail = 1;
+                break;
+            }
+            const float2 *rt = raw + (size_t)(gc % kRaw) * (kRawSlot / 8u) + threadIdx.x;
+            unsigned char *sa = gsm + s * kStage;
+            float2 v[8];
+            read_raw8(rt, 0, v);
+            store_a(sa, v, ml, h);
+            if (b_on) {
 #pragma unroll
-                    for (uint32_t i = 0; i < kUnits; i++)
-                        store_b<NT>(sa + 6u * kRegA, cur.b[i], (threadIdx.x + 128u * i) % (uint32_t)NT, bh[i]);
+                for (uint32_t i = 0; i < kUnits; i++) {
+                    read_raw8(rt, 8u + 8u * i, v);
+                    store_b<NT>(sa + 6u * kRegA, v, (threadIdx.x + 128u * i) % (uint32_t)NT, bh[i]);
                 }
-                // the generic-proxy stores must be visible to the tensor cores' reads
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[s])) : "memory");
-                cur = nxt;
             }
+            // the generic-proxy stores must be visible to the tensor cores' reads
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[s])) : "memory");
         }
+        cp_async_wait<0>();   // no copy may still be landing when the CTA leaves
     } else if (warp == 4) {
         if (lane == 0) {   // MMA issuer
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
@@ -471,9 +509,11 @@ uint32_t gemm_nt(const GemmStep &g) { return g.nn >= 7 ? 128u : (1u << g.nn); }
 
 template <int NT>
 static cudaError_t launch_gemm_nt(GemmArgs ga, cudaStream_t s) {
-    // dynamic shared memory: the stage ring, the epilogue's transpose buffers and the summed
-    // index tables (the largest K is 1024), the same for every step of this tile width
-    constexpr size_t kSmem = (size_t)n_stages<NT>() * stage_bytes(NT) + epi_bytes<NT>() + 4u * 2u * 1024u;
+    // dynamic shared memory: the operand stage ring, the epilogue's transpose buffers, the
+    // producers' raw copy slots and the summed index tables (the largest K is 1024)
+    constexpr uint32_t kUnits = (2u * (uint32_t)NT + 127u) / 128u;
+    constexpr size_t kSmem = (size_t)n_stages<NT>() * stage_bytes(NT) + epi_bytes<NT>() +
+                             (size_t)kRaw * raw_entries<kUnits>() * 128u * 8u + 4u * 2u * 1024u;
     static int per_sm[64] = {0}, sms[64] = {0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -159,7 +159,7 @@ __device__ double2 block_exact_sum(const ExactPair *p, int64_t n, double sr, dou
 
 // Header fields the item epilogue needs, read once per kernel.
 struct FinishInfo {
-    uint64_t zero_mask;
+    uint64_t zero_mask, zero_mask_hi;
     double sr, si;
     uint32_t n_in, present;        // inner slice modes and those present in the final tensor
     uint32_t n_open, open_present; // open output qubits and those present
@@ -168,6 +168,7 @@ struct FinishInfo {
 __device__ __forceinline__ FinishInfo finish_info(const DevProgram *P) {
     FinishInfo f;
     f.zero_mask = P->zero_mask;
+    f.zero_mask_hi = P->zero_mask_hi;
     f.sr = P->scalar_re;
     f.si = P->scalar_im;
     f.n_in = P->n_inner;
@@ -190,8 +191,8 @@ __device__ __forceinline__ uint32_t compress_bits(uint32_t v, uint32_t mask, uin
 // scalar) at terms[slot * (s_end - s_begin) + s - s_begin].
 template <bool CG>
 __device__ void finish_item_t(const FinishInfo &P, const LaunchArgs &a, const float2 *fin, int64_t b, uint64_t o,
-                              int lane, uint64_t x) {
-    const bool zero = (x & P.zero_mask) != 0;
+                              int lane, const Bits &x) {
+    const bool zero = bits_hit(x, P.zero_mask, P.zero_mask_hi);
     const uint32_t n_in = P.n_in, present = P.present;
     const uint32_t inner_bits = __popc(present);
     for (uint32_t j = 0; j < (1u << P.n_open); j++) {
@@ -223,12 +224,12 @@ __device__ void finish_item_t(const FinishInfo &P, const LaunchArgs &a, const fl
 
 __device__ __forceinline__ void finish_item(const FinishInfo &P, const LaunchArgs &a, const float2 *fin, int64_t b,
                                             uint64_t o, int lane, int) {
-    finish_item_t<false>(P, a, fin, b, o, lane, a.bitstrings[b]);
+    finish_item_t<false>(P, a, fin, b, o, lane, load_bits(a.bitstrings, b, a.words));
 }
 
 __device__ __forceinline__ void finish_item_cg(const FinishInfo &P, const LaunchArgs &a, const float2 *fin, int64_t b,
                                                uint64_t o, int lane) {
-    finish_item_t<true>(P, a, fin, b, o, lane, a.bitstrings[b]);
+    finish_item_t<true>(P, a, fin, b, o, lane, load_bits(a.bitstrings, b, a.words));
 }
 
 // ------------------------------------------------------------------ fused engine
@@ -460,7 +461,7 @@ __global__ void __launch_bounds__(512) fused_program_kernel(LaunchArgs a, int wa
     // the first item's bitstring is read while the program is being staged
     const int groups0 = blockDim.x / (32 * warps_per_item);
     const int64_t item0 = (int64_t)blockIdx.x * groups0 + threadIdx.x / (32 * warps_per_item);
-    uint64_t x_next = item0 < a.batch * a.o_count ? a.bitstrings[item0 / a.o_count] : 0ull;
+    Bits x_next = item0 < a.batch * a.o_count ? load_bits(a.bitstrings, item0 / a.o_count, a.words) : Bits{0ull, 0ull};
     bool staged_ok = true;
     if (STAGED) {
         const uint32_t s1 = a.smem_steps_bytes, s2 = s1 + a.smem_leaf_bytes, s3 = s2 + a.smem_leaves_bytes;
@@ -509,9 +510,9 @@ __global__ void __launch_bounds__(512) fused_program_kernel(LaunchArgs a, int wa
              item += (int64_t)gridDim.x * groups) {
             const int64_t b = item / a.o_count;
             const uint64_t o = (uint64_t)(a.o_begin + item % a.o_count);
-            const uint64_t x = x_next;
+            const Bits x = x_next;
             const int64_t item_next = item + (int64_t)gridDim.x * groups;
-            if (item_next < n_items) x_next = a.bitstrings[item_next / a.o_count];
+            if (item_next < n_items) x_next = load_bits(a.bitstrings, item_next / a.o_count, a.words);
             for (uint32_t l = lane; l < n_leaves; l += lanes) lbase[l] = leaf_base(leaves[l], x, o);
             if (warps_per_item == 1) __syncwarp();
             else asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(lanes));
@@ -568,7 +569,7 @@ __global__ void step_kernel(LaunchArgs a, uint32_t s_idx, int64_t item_begin, in
     const int64_t item = item_begin + il;
     const int64_t b = item / a.o_count;
     const uint64_t o = (uint64_t)(a.o_begin + item % a.o_count);
-    const uint64_t x = a.bitstrings[b];
+    const Bits x = load_bits(a.bitstrings, b, a.words);
     float2 *arena = arenas + (uint64_t)il * a.arena_elems;
     const bool unary = st.flags & kStepUnary;
     const DevLeaf *leaves = reinterpret_cast<const DevLeaf *>(img + P->leaves_off);
@@ -594,10 +595,11 @@ __global__ void step_group_kernel(LaunchArgs a, StepGroup g, int64_t item_begin,
     const bool unary = st.flags & kStepUnary;
     const DevLeaf *leaves = reinterpret_cast<const DevLeaf *>(img + P->leaves_off);
     const float2 *ldata = reinterpret_cast<const float2 *>(img + P->leaf_data_off);
-    uint64_t x = 0, o = 0;
+    Bits x = {0ull, 0ull};
+    uint64_t o = 0;
     if (st.flags & (kStepALeaf | kStepBLeaf)) {
         const int64_t item = item_begin + il;
-        x = a.bitstrings[item / a.o_count];
+        x = load_bits(a.bitstrings, item / a.o_count, a.words);
         o = (uint64_t)(a.o_begin + item % a.o_count);
     }
     const float2 *A = (st.flags & kStepALeaf) ? ldata + leaf_base(leaves[st.a_off], x, o) : arena + st.a_off;
@@ -704,7 +706,7 @@ __global__ void __launch_bounds__(256) persistent_program_kernel(LaunchArgs a, i
                 float2 *arena = arenas + (uint64_t)il * arena_elems;
                 const float2 *A, *B;
                 if (a_leaf || (!unary && b_leaf)) {
-                    const uint64_t x = a.bitstrings[b];
+                    const Bits x = load_bits(a.bitstrings, b, a.words);
                     A = a_leaf ? ldata + leaf_base(leaves[sd.a_off], x, o) : arena + sd.a_off;
                     B = unary ? A : (b_leaf ? ldata + leaf_base(leaves[sd.b_off], x, o) : arena + sd.b_off);
                 } else {
@@ -748,10 +750,11 @@ __global__ void __launch_bounds__(256, 4) regtile_step_kernel(LaunchArgs a, RegT
         const DevProgram *P = reinterpret_cast<const DevProgram *>(img);
         const DevLeaf *leaves = reinterpret_cast<const DevLeaf *>(img + P->leaves_off);
         const float2 *ldata = reinterpret_cast<const float2 *>(img + P->leaf_data_off);
-        uint64_t x = 0, o = 0;
+        Bits x = {0ull, 0ull};
+        uint64_t o = 0;
         if (rs.flags & (kStepALeaf | kStepBLeaf)) {
             const int64_t item = item_begin + il;
-            x = a.bitstrings[item / a.o_count];
+            x = load_bits(a.bitstrings, item / a.o_count, a.words);
             o = (uint64_t)(a.o_begin + item % a.o_count);
         }
         A = (rs.flags & kStepALeaf) ? ldata + leaf_base(leaves[rs.a_off], x, o) : arena + rs.a_off;
@@ -815,9 +818,10 @@ __global__ void __launch_bounds__(256) splitk_step_kernel(LaunchArgs a, uint32_t
         arena = arenas + (uint64_t)il * a.arena_elems;
         const DevLeaf *leaves = reinterpret_cast<const DevLeaf *>(img + P->leaves_off);
         const float2 *ldata = reinterpret_cast<const float2 *>(img + P->leaf_data_off);
-        uint64_t x = 0, o = 0;
+        Bits x = {0ull, 0ull};
+        uint64_t o = 0;
         if (sd.flags & (kStepALeaf | kStepBLeaf)) {
-            x = a.bitstrings[item / a.o_count];
+            x = load_bits(a.bitstrings, item / a.o_count, a.words);
             o = (uint64_t)(a.o_begin + item % a.o_count);
         }
         const bool unary = sd.flags & kStepUnary;
@@ -913,7 +917,7 @@ __global__ void set_params_kernel(unsigned char *img, const double *thetas) {
 }
 
 __device__ __forceinline__ const float2 *gen_base(const GenOperand &op, const DevProgram *P,
-                                                  const unsigned char *img, float2 *arena, uint64_t x,
+                                                  const unsigned char *img, float2 *arena, const Bits &x,
                                                   uint64_t o) {
     if (op.kind == kOpArena) return arena + op.off;
     if (op.kind == kOpOne) return nullptr;
@@ -935,7 +939,7 @@ __global__ void __launch_bounds__(256) grad_program_kernel(GradArgs g) {
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int64_t b = item / g.o_count;
         const uint64_t o = (uint64_t)(item % g.o_count);
-        const uint64_t x = g.bitstrings[b];
+        const Bits x = load_bits(g.bitstrings, b, g.words);
         // phase by phase: the entries of all steps of a phase are spread over the CTA
         for (uint32_t ph = 0; ph < n_phases; ph++) {
             const uint32_t s0 = phase_first[ph], s1 = phase_first[ph + 1];
@@ -964,7 +968,7 @@ __global__ void __launch_bounds__(256) grad_program_kernel(GradArgs g) {
             __syncthreads();
         }
         // amplitude partial: exact sum of the final tensor over the inner slice modes
-        const bool zero = (x & P->zero_mask) != 0;
+        const bool zero = bits_hit(x, P->zero_mask, P->zero_mask_hi);
         if (threadIdx.x < 32) {
             const float2 *fin = arena + P->final_fwd_off;
             Fx re = {0ull, 0ll}, im = {0ull, 0ll};
@@ -1089,7 +1093,7 @@ __global__ void __launch_bounds__(256) grad_smem_kernel(GradArgs g) {
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int64_t b = item / g.o_count;
         const uint64_t o = (uint64_t)(item % g.o_count);
-        const uint64_t x = g.bitstrings[b];
+        const Bits x = load_bits(g.bitstrings, b, g.words);
         for (uint32_t l = threadIdx.x; l < n_leaves; l += blockDim.x) lbase[l] = leaf_base(leaves[l], x, o);
         // a thread's first kGradPrefetch records of a phase are loaded during the phase before
         uint4 cur[kGradPrefetch];
@@ -1119,7 +1123,7 @@ __global__ void __launch_bounds__(256) grad_smem_kernel(GradArgs g) {
             for (int j = 0; j < kGradPrefetch; j++) cur[j] = nxt[j];
             __syncthreads();
         }
-        const bool zero = (x & P->zero_mask) != 0;
+        const bool zero = bits_hit(x, P->zero_mask, P->zero_mask_hi);
         if (threadIdx.x < 32) {
             const float2 *fin = arena + P->final_fwd_off;
             Fx re = {0ull, 0ll}, im = {0ull, 0ll};

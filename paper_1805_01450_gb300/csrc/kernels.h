@@ -17,8 +17,9 @@ struct ExactPair {
 
 struct LaunchArgs {
     const unsigned char *image;     // device image (DevProgram first)
-    const uint64_t *bitstrings;     // device, batch entries
+    const uint64_t *bitstrings;     // device, batch x words entries
     int64_t batch;
+    uint32_t words;                 // 64-bit words per bitstring (1: up to 64 qubits, 2: up to 128)
     int64_t o_begin, o_count;       // outer slice numbers of this call
     int64_t s_begin, s_end;         // slice range summed / written
     uint64_t arena_elems;
@@ -85,7 +86,8 @@ cudaError_t launch_finish_items(const LaunchArgs &a, int64_t item_begin, int64_t
 // Gradient program (one CTA per work item, arenas in global memory).
 struct GradArgs {
     unsigned char *image;           // workspace copy of the image (its parametrised leaves are rewritten)
-    const uint64_t *bitstrings;
+    const uint64_t *bitstrings;     // batch x words entries
+    uint32_t words;
     int64_t batch, o_count;
     float2 *arenas;                 // slots * grad_arena_elems
     uint64_t arena_elems;

@@ -108,6 +108,7 @@ extern "C" qvx_status qvx_amplitude_noalloc(qvx_plan *plan, const uint64_t *bits
     qvx::LaunchArgs a{};
     a.image = base + image_off;
     a.bitstrings = bitstrings_dev;
+    a.words = (uint32_t)((p.model.n_qubits + 63) / 64);
     a.batch = batch;
     a.o_begin = 0;
     a.o_count = n_outer;

@@ -28,7 +28,8 @@ struct HostTensor {
 struct Model {
     int n_qubits = 0, n_vars = 0;
     std::vector<int> var_qubit, var_ordinal;
-    uint64_t zero_mask = 0;        // qubits with no non-diagonal gate: output equals input 0
+    uint64_t zero_mask[2] = {0, 0};   // qubits with no non-diagonal gate (output equals input 0):
+                                      // bit q of word q / 64
     std::vector<int> cz_count;     // per summed variable: CZ gates acting on it
     cplx scalar = 1.0;
     std::vector<HostTensor> tensors;

@@ -81,8 +81,8 @@ bool is_subset(const std::vector<int> &a, const std::vector<int> &b) {
 
 // ---------------------------------------------------------------- graphical model
 bool build_model(const qvx_circuit *c, Model *m, std::string *err, bool keep_params) {
-    if (!c || c->n_qubits < 1 || c->n_qubits > 64 || c->n_gates < 0 || (c->n_gates > 0 && !c->gates)) {
-        *err = "circuit: need 1 <= n_qubits <= 64 and a gate array";
+    if (!c || c->n_qubits < 1 || c->n_qubits > 128 || c->n_gates < 0 || (c->n_gates > 0 && !c->gates)) {
+        *err = "circuit: need 1 <= n_qubits <= 128 and a gate array";
         return false;
     }
     const int n = c->n_qubits;
@@ -135,9 +135,9 @@ bool build_model(const qvx_circuit *c, Model *m, std::string *err, bool keep_par
         }
     }
     m->n_vars = (int)m->var_qubit.size();
-    m->zero_mask = 0;
+    m->zero_mask[0] = m->zero_mask[1] = 0;
     for (int q = 0; q < n; q++)
-        if (cur[q] == 0) m->zero_mask |= 1ull << q;
+        if (cur[q] == 0) m->zero_mask[q >> 6] |= 1ull << (q & 63);
     m->scalar = 1.0;
     m->tensors.clear();
     // key -> id: input (q, 0) is fixed to 0 (-1 here); summed (q, j) -> canonical id;
@@ -1271,7 +1271,8 @@ bool serialize(Plan &p, std::string *err) {
             else {
                 int si = find_pos(p.slices, v);
                 if (si < p.n_inner) { *err = "internal: leaf mode neither kept nor fixed"; return false; }
-                src = (uint8_t)(64 + (si - p.n_inner));
+                if (si - p.n_inner >= 64) { *err = "more than 64 outer sliced variables"; return false; }
+                src = (uint8_t)(128 + (si - p.n_inner));
             }
             d.fixed_src[d.n_fixed] = src;
             d.fixed_pos[d.n_fixed] = (uint8_t)stored.size();
@@ -1557,7 +1558,8 @@ bool serialize(Plan &p, std::string *err) {
     h.n_open = (uint32_t)p.open_qubits.size();
     for (size_t i = 0; i < p.open_qubits.size(); i++)
         if (find_pos(F.modes, m.n_vars + p.open_qubits[i]) >= 0) h.open_present |= 1u << i;
-    h.zero_mask = m.zero_mask;
+    h.zero_mask = m.zero_mask[0];
+    h.zero_mask_hi = m.zero_mask[1];
     h.scalar_re = p.prog_scalar.real();
     h.scalar_im = p.prog_scalar.imag();
     h.n_outer = uint64_t(1) << ((int)p.slices.size() - p.n_inner);
@@ -1844,7 +1846,7 @@ qvx_status plan_once(const qvx_circuit *c, const int32_t *order, int32_t n_order
     for (int i = 0; i < opts.n_open_qubits; i++) {
         const int qb = opts.open_qubits[i];
         if (qb < 0 || qb >= c->n_qubits || find_pos(p->open_qubits, qb) >= 0) { *err = "open_qubits: bad or repeated qubit"; return QVX_EINVAL; }
-        if ((p->model.zero_mask >> qb) & 1ull) { *err = "open_qubits: a qubit without a non-diagonal gate has no output variable"; return QVX_EINVAL; }
+        if ((p->model.zero_mask[qb >> 6] >> (qb & 63)) & 1ull) { *err = "open_qubits: a qubit without a non-diagonal gate has no output variable"; return QVX_EINVAL; }
         p->open_qubits.push_back(qb);
     }
     if (opts.gradient)

@@ -29,7 +29,8 @@ PROG = np.dtype([("magic", "<u4"), ("n_steps", "<u4"), ("n_leaves", "<u4"), ("pa
                  ("n_level_phases", "<u4"), ("n_grad_phases", "<u4"), ("grad_phases_off", "<u8"),
                  ("grad_elem_off_off", "<u8"), ("n_open", "<u4"), ("open_present", "<u4"),
                  ("regtile_off", "<u8"), ("gentry_off", "<u8"), ("gktab_off", "<u8"),
-                 ("gphase_entry_off", "<u8"), ("gemm_off", "<u8"), ("image_bytes", "<u8")])
+                 ("gphase_entry_off", "<u8"), ("gemm_off", "<u8"), ("image_bytes", "<u8"),
+                 ("zero_mask_hi", "<u8")])
 FSTEP = np.dtype([("a_off", "<u4"), ("b_off", "<u4"), ("c_off", "<u4"), ("tab_off", "<u4"), ("flags", "<u4"),
                   ("rc", "u1"), ("nk_ab", "u1"), ("nk_a", "u1"), ("nk_b", "u1"), ("a_cb", "u1"), ("b_cb", "u1"),
                   ("nk", "u1"), ("pad1", "u1"), ("pad2", "<u4"), ("koff_a", "<u2", (8,)), ("koff_b", "<u2", (8,))])
@@ -42,7 +43,7 @@ RTSTEP = np.dtype([("a_off", "<u8"), ("b_off", "<u8"), ("c_off", "<u8"), ("flags
                    ("a_cb", "u1"), ("b_cb", "u1"), ("n_free", "u1"), ("na_runs", "u1"), ("nb_runs", "u1"),
                    ("free_runs", RUN, (6,)), ("runs_a", RUN, (12,)), ("runs_b", RUN, (12,)),
                    ("a_m", "<u4", (4,)), ("b_n", "<u4", (4,)), ("c_m", "<u4", (4,)), ("c_n", "<u4", (4,))])
-assert STEP.itemsize == 136 and LEAF.itemsize == 40 and PROG.itemsize == 320 and FSTEP.itemsize == 64
+assert STEP.itemsize == 136 and LEAF.itemsize == 40 and PROG.itemsize == 328 and FSTEP.itemsize == 64
 GEMM = np.dtype([("a_off", "<u8"), ("b_off", "<u8"), ("c_off", "<u8"), ("flags", "<u4"), ("nb", "u1"),
                  ("nm", "u1"), ("nn", "u1"), ("nk", "u1"), ("n_ab", "u1"), ("n_am", "u1"), ("n_ak", "u1"),
                  ("n_bb", "u1"), ("n_bn", "u1"), ("n_bk", "u1"), ("n_cb", "u1"), ("n_cm", "u1"), ("n_cn", "u1"),
@@ -129,7 +130,7 @@ class Program:
         off = int(L["data_off"])
         for f in range(int(L["n_fixed"])):
             src = int(L["fixed_src"][f])
-            bit = (x >> src) & 1 if src < 64 else (o >> (src - 64)) & 1
+            bit = (x >> src) & 1 if src < 128 else (o >> (src - 128)) & 1
             off += bit << int(L["fixed_pos"][f])
         n = int(L["n_elem"])
 
@@ -281,7 +282,7 @@ class Program:
         n_open, open_present = int(h["n_open"]), int(h["open_present"])
         fin = arena[int(h["final_off"]):]
         scalar = complex(float(h["scalar_re"]), float(h["scalar_im"]))
-        zero = (x & int(h["zero_mask"])) != 0
+        zero = (x & (int(h["zero_mask"]) | (int(h["zero_mask_hi"]) << 64))) != 0
 
         def compress(v, mask, n):
             r, bit = 0, 0
@@ -338,7 +339,7 @@ def grad_item(prog, x, o, thetas=None, tables=False):
         off = int(L["data_off"])
         for f in range(int(L["n_fixed"])):
             src = int(L["fixed_src"][f])
-            bit = (x >> src) & 1 if src < 64 else (o >> (src - 64)) & 1
+            bit = (x >> src) & 1 if src < 128 else (o >> (src - 128)) & 1
             off += bit << int(L["fixed_pos"][f])
         return off
 
@@ -403,7 +404,7 @@ def grad_item(prog, x, o, thetas=None, tables=False):
     present = int(h["final_present"])
     fin = arena[int(h["final_fwd_off"]):]
     scalar = complex(float(h["scalar_re"]), float(h["scalar_im"]))
-    zero = (x & int(h["zero_mask"])) != 0
+    zero = (x & (int(h["zero_mask"]) | (int(h["zero_mask_hi"]) << 64))) != 0
     tot = 0j
     for i in range(1 << n_in):
         fi, bit = 0, 0

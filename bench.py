@@ -39,7 +39,11 @@ WORKLOADS = {
     "grid4x4d10": ("grid", 4, 4, 10, 1001, 1002, 0, 1),
     "grid7x7d30-b1024": ("grid", 7, 7, 30, 3001, 3002, 4, 1024),
     "rot5x5d20-grad": ("rotation", 5, 5, 20, 4001, 4002, 8, 1),
+    "grid9x9d40": ("grid", 9, 9, 40, 9001, 9002, 20, 1),
 }
+# workloads timed on a contiguous sample of each amplitude's slice terms (slice terms per
+# step); their amplitude rate is extrapolated: steps x sample / 2^k / time
+SLICE_SAMPLE = {"grid9x9d40": 1 << 10}
 DEFAULT_WORKLOAD = "grid8x8d40"
 # The plan variant the autotuner keeps (bench.py --autotune: sliced-variable counts 10 and
 # 12, the SIMT and tensor-core stepwise forms with 4 open slices, then 1, 16, 64 and 256
@@ -49,13 +53,14 @@ RECORDED_PLANS = {
     ("grid8x8d40", 5001): dict(n_slices=10, inner_slices=4, engine="stepwise", tensor_cores=True, plan_trials=16),
     ("grid8x8d40", 5002): dict(n_slices=10, inner_slices=4, engine="stepwise", tensor_cores=True, plan_trials=256),
     ("grid8x8d40", 5003): dict(n_slices=10, inner_slices=4, engine="stepwise", tensor_cores=True, plan_trials=64),
+    ("grid9x9d40", 9001): dict(n_slices=20, inner_slices=4, engine="stepwise", tensor_cores=True, plan_trials=8),
 }
 # autotuner search of the workloads without a recorded plan
 TUNE = {"grid6x6d25-k12": dict(trial_counts=(1, 16, 256)),
         "grid7x7d30-b1024": dict(slice_counts=(0, 2, 4, 6, 8), engines=("stepwise",), budget_s=90.0),
         "grid8x8d40": dict(slice_counts=(10, 12), engines=("stepwise", "stepwise-tc"), inner=(4,),
                            trial_counts=(1, 16, 64, 256), budget_s=120.0)}
-MEM_BUDGET_MB = {"grid7x7d30-b1024": 32768, "grid8x8d40": 65536}
+MEM_BUDGET_MB = {"grid7x7d30-b1024": 32768, "grid8x8d40": 65536, "grid9x9d40": 65536}
 # independent planning trials (ordering + slice choice from distinct seeds, the best by the
 # planner's bandwidth-weighted estimate kept); planning is outside the timed region
 PLAN_TRIALS = {"grid6x6d25-k12": 64, "grid7x7d30-b1024": 64, "grid8x8d40": 64}
@@ -96,6 +101,8 @@ def parse(argv=None):
     ap.add_argument("--circuit-seed", type=int, default=None, help="override the workload's circuit seed")
     ap.add_argument("--shard", choices=["bitstrings", "slices"], default="bitstrings",
                     help="under torchrun: each rank its own bitstrings, or the ranks share every amplitude's slices")
+    ap.add_argument("--slice-sample", type=int, default=None,
+                    help="slice terms per step (a contiguous range; the amplitude rate is extrapolated); 0: all")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-forms", action="store_true", help="skip timing the plain FP32 forms of the plan")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU-baseline sample budget")
@@ -283,7 +290,14 @@ def run_config(args, circ, plan, world, B):
             "mem_budget_mb": args.mem_budget_mb, "tensor_core_steps": info["n_gemm_steps"],
             "plan_trials": plan.plan_trials, "l2": "flushed (256 MiB write) before each step",
             "parallelism": (f"slices split over {world} ranks" if args.shard == "slices" and world > 1
-                            else f"bitstrings per rank x {world}")}
+                            else f"bitstrings per rank x {world}"),
+            **({"slice_sample": slice_sample(args, plan), "extrapolated": True} if slice_sample(args, plan) else {})}
+
+
+def slice_sample(args, plan):
+    """Slice terms per step when the run samples each amplitude's slices, else 0."""
+    n = SLICE_SAMPLE.get(args.workload, 0) if args.slice_sample is None else args.slice_sample
+    return min(n, plan.n_slice_terms) if n and n < plan.n_slice_terms else 0
 
 
 def plan_json(args):
@@ -456,7 +470,9 @@ def main():
     stream = torch.cuda.current_stream()
     L = q.lib()
     sptr = q._stream_ptr(stream)
-    s_begin, s_end = slice_range(plan.n_slice_terms, rank, world) if shard else (0, plan.n_slice_terms)
+    sample = slice_sample(args, plan)
+    s_begin, s_end = slice_range(plan.n_slice_terms, rank, world) if shard else (0, sample or plan.n_slice_terms)
+    partial = shard or bool(sample)
     gathered = torch.empty(world * 2 * B, dtype=torch.float64, device=dev) if shard else None
 
     def step(profiled=False):
@@ -464,14 +480,15 @@ def main():
             q._check(L.qvx_amplitude_grad(plan._h, q.ctypes.c_void_p(bits.data_ptr()), B, None, 0,
                                           q.ctypes.c_void_p(out.data_ptr()), q.ctypes.c_void_p(gout.data_ptr()),
                                           q.ctypes.c_void_p(ws.data_ptr()), ws.numel(), sptr))
-        elif shard:   # this rank's slice range, then one all_gather of the B complex128 partials
+        elif profiled:
+            plan.amplitude_profiled(bits, ws, out, stream, slice_begin=s_begin, slice_count=s_end - s_begin)
+        elif partial:   # this rank's (or the sample's) slice range
             plan.amplitude(bits, workspace=ws, out=out, validate=False, stream=stream, slice_begin=s_begin,
                            slice_count=s_end - s_begin)
-            dist.all_gather_into_tensor(gathered, out)
-        elif profiled:
-            plan.amplitude_profiled(bits, ws, out, stream)
         else:
             plan.amplitude(bits, workspace=ws, out=out, validate=False, stream=stream)
+        if shard:   # one all_gather of the B complex128 partials
+            dist.all_gather_into_tensor(gathered, out)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -480,7 +497,7 @@ def main():
     plan.read_profile()
 
     K = args.steps
-    profiled = not grad and not shard
+    profiled = not grad
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     with ClockSampler(torch.cuda.current_device()) as clocks:
         barrier()
@@ -507,7 +524,7 @@ def main():
     e2e_s = 0.0
     barrier()
     torch.cuda.synchronize()
-    if grad or shard:
+    if grad or partial:
         ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
         for i in range(K):
             flush.zero_()
@@ -552,7 +569,7 @@ def main():
             dist.destroy_process_group()
         return
     n = circ.n_qubits
-    amps = K * B * (1 if shard else world)
+    amps = K * B * (1 if shard else world) * ((s_end - s_begin) / plan.n_slice_terms if sample else 1)
     value = amps / (dev_ms / 1e3)
     e2e = amps / (e2e_ms / 1e3)
     ms_step = dev_ms / K
@@ -597,7 +614,7 @@ def main():
                  "algorithmic_flops_per_amplitude": info["flops_per_amplitude"]},
         "abs_err": None, "err_bound": 1e-5 * 2.0 ** (-n / 2),
     }
-    if world == 1 and not grad:
+    if world == 1 and not grad and not sample:
         # parity of what was timed: against the oracle's whole amplitude when it finishes in
         # seconds, else (and always for the timing baseline) on seeded sampled slice terms
         from oracle import ve as VE

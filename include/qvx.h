@@ -324,14 +324,15 @@ typedef struct {
     int32_t pad;
 } qvx_launch_record;
 
-/* qvx_amplitude (the whole slice range) with a CUDA event recorded on `stream` just before
- * and just after every kernel launch, for measuring each kernel against its roofline. The
- * launches are appended to the plan's launch log; nothing is synchronised. No paper
- * counterpart: instrumentation of this implementation. The events belong to the plan
- * (created on first use on the current device, freed by qvx_plan_destroy); the log holds
- * at most about 2^20 launches (QVX_ENOMEM beyond: read it first). */
-qvx_status qvx_amplitude_profiled(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch, double *amps_dev,
-                                  void *workspace_dev, size_t workspace_bytes, void *stream);
+/* qvx_amplitude_slices with a CUDA event recorded on `stream` just before and just after
+ * every kernel launch, for measuring each kernel against its roofline. The launches are
+ * appended to the plan's launch log; nothing is synchronised. No paper counterpart:
+ * instrumentation of this implementation. The events belong to the plan (created on first
+ * use on the current device, freed by qvx_plan_destroy); the log holds at most about 2^20
+ * launches (QVX_ENOMEM beyond: read it first). */
+qvx_status qvx_amplitude_profiled(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch, int64_t slice_begin,
+                                  int64_t slice_count, double *amps_dev, void *workspace_dev, size_t workspace_bytes,
+                                  void *stream);
 
 /* Waits for the logged launches' events, then records[i] (i < cap) describes logged launch i
  * in issue order (its ms filled in), *n_records is the number of logged launches (which may

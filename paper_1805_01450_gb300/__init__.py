@@ -111,7 +111,7 @@ def lib():
         "qvx_amplitude_host": (ctypes.c_int, [P, P, i64, P, P, ctypes.c_size_t, P]),
         "qvx_selftest_wait_timeout": (ctypes.c_int, [P, P, ctypes.c_size_t, ctypes.c_uint32, P]),
         "qvx_noalloc_status": (ctypes.c_int, [P]),
-        "qvx_amplitude_profiled": (ctypes.c_int, [P, P, i64, P, P, ctypes.c_size_t, P]),
+        "qvx_amplitude_profiled": (ctypes.c_int, [P, P, i64, i64, i64, P, P, ctypes.c_size_t, P]),
         "qvx_profile_read": (ctypes.c_int, [P, ctypes.POINTER(LaunchRecord), i64, ctypes.POINTER(ctypes.c_int64)]),
         "qvx_kernel_name": (ctypes.c_char_p, [i32]),
         "qvx_selftest_fused_timeout": (ctypes.c_int, [P, P, i64, P, P, ctypes.c_size_t, P]),
@@ -412,13 +412,16 @@ class Plan:
         t = torch.view_as_complex(out.view(n * m, slice_count, 2))
         return t.view(n, m, slice_count) if self.n_open else t.view(n, slice_count)
 
-    def amplitude_profiled(self, bits, workspace, out, stream=None):
-        """plan.amplitude over all slices (device int64 bitstrings, caller's workspace and
-        float64 output) with a CUDA event before and after every kernel launch, appended to
-        the plan's launch log (read_profile). Does not synchronise."""
+    def amplitude_profiled(self, bits, workspace, out, stream=None, slice_begin=0, slice_count=None):
+        """plan.amplitude (device int64 bitstring words, caller's workspace and float64
+        output) with a CUDA event before and after every kernel launch, appended to the plan's
+        launch log (read_profile). Does not synchronise."""
+        if slice_count is None:
+            slice_count = self.n_slice_terms - slice_begin
         _check(lib().qvx_amplitude_profiled(self._h, ctypes.c_void_p(bits.data_ptr()), bits.numel() // self.words,
-                                            ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(workspace.data_ptr()),
-                                            workspace.numel(), _stream_ptr(stream)))
+                                            slice_begin, slice_count, ctypes.c_void_p(out.data_ptr()),
+                                            ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                            _stream_ptr(stream)))
 
     def read_profile(self):
         """The launch log of amplitude_profiled calls since the last read, in issue order: a

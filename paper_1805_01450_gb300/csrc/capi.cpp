@@ -519,13 +519,13 @@ qvx_status qvx_amplitude_slices(qvx_plan *plan, const uint64_t *bitstrings_dev, 
                                  nullptr);
 }
 
-qvx_status qvx_amplitude_profiled(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch, double *amps_dev,
-                                  void *ws, size_t ws_bytes, void *stream) {
+qvx_status qvx_amplitude_profiled(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch, int64_t slice_begin,
+                                  int64_t slice_count, double *amps_dev, void *ws, size_t ws_bytes, void *stream) {
     if (!plan) return fail(QVX_EINVAL, "null plan");
     if (plan->prof_log.size() > (size_t(1) << 20)) return fail(QVX_ENOMEM, "launch log full: read it first");
     Profiler prof{plan, static_cast<cudaStream_t>(stream)};
-    qvx_status s = amplitude_slices_impl(plan, bitstrings_dev, batch, 0, int64_t(1) << plan->p.slices.size(), amps_dev,
-                                         ws, ws_bytes, stream, &prof);
+    qvx_status s = amplitude_slices_impl(plan, bitstrings_dev, batch, slice_begin, slice_count, amps_dev, ws, ws_bytes,
+                                         stream, &prof);
     if (s != QVX_OK) return s;
     if (prof.err != cudaSuccess) return cuda_fail(prof.err, "profiling event");
     return QVX_OK;

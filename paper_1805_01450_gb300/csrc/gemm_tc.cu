@@ -13,14 +13,15 @@
 // 1.2e-5 of its size, above the 1e-5 tolerance.
 //
 // A tile is 128 real rows (64 complex rows m) by NT columns n of one (item, b). The kernel
-// is persistent (one CTA per SM walks the tiles) and warp-specialised: producer warps read
-// the complex64 operands straight from the arena, one chunk of 16 summed entries at a time,
-// split them into three bf16 parts and store them in the tensor cores' K-major core-matrix
-// layout in a ring of shared-memory stages (no separate packing pass: the operands cross HBM
-// once, as complex64); one thread issues each chunk's twelve tcgen05.mma (2 parts x 6
-// products, K = 16 each) into one of two tensor-memory accumulators; epilogue warps read a
-// finished accumulator with tcgen05.ld and store complex64 C in its own layout while the
-// next tile's chunks are loaded and multiplied into the other accumulator.
+// is persistent (one CTA per SM walks the tiles) and warp-specialised: producer warps copy
+// the complex64 operands straight from the arena into shared memory (cp.async, several
+// chunks of 16 summed entries ahead), split them into three bf16 parts and store them in the
+// tensor cores' K-major core-matrix layout in a ring of shared-memory stages (no separate
+// packing pass: the operands cross HBM once, as complex64); one thread issues each chunk's
+// twelve tcgen05.mma (2 parts x 6 products, K = 16 each) into one of two tensor-memory
+// accumulators; epilogue warps read a finished accumulator with tcgen05.ld and store
+// complex64 C in its own layout while the next tile's chunks are loaded and multiplied into
+// the other accumulator.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -39,11 +40,37 @@ constexpr uint32_t kPitch = 272;       // bytes between 8-row groups: two 128-by
                                        // along the summed index and 16 bytes that spread the
                                        // producers' 16-byte stores over all banks
 constexpr uint32_t kPolls = 1u << 22;
-constexpr uint32_t kThreads = 288;     // warps 0-3: operands; warp 4: MMA; warps 5-8: epilogue
+constexpr uint32_t kRaw = 4;           // chunks of raw operand copies in flight per producer
+constexpr uint32_t kEpiThreads = 128;  // four epilogue warps, one per tensor-memory lane quarter
 
 __host__ __device__ constexpr uint32_t region_bytes(uint32_t rows) { return rows / 8u * kPitch; }
 // One stage: A regions (part 0 h, m, l, part 1 h, m, l), then the same for B.
 __host__ __device__ constexpr uint32_t stage_bytes(uint32_t nt) { return 6u * region_bytes(kRows) + 6u * region_bytes(nt); }
+
+// Producer threads: one per operand unit of a chunk (8 summed entries of one A row or one B
+// column): 64 rows x 2 halves of A and NT columns x 2 halves of B.
+template <int NT>
+__host__ __device__ constexpr uint32_t producers() { return 128u + 2u * (uint32_t)NT; }
+template <int NT>
+__host__ __device__ constexpr uint32_t block_threads() { return producers<NT>() + 32u + kEpiThreads; }
+// Operand stages of the shared-memory ring: two of 52 KB for 128-column tiles, three below.
+template <int NT>
+__host__ __device__ constexpr uint32_t n_stages() { return NT >= 128 ? 2u : 3u; }
+template <int NT>
+__host__ __device__ constexpr uint32_t epi_cols() { return NT < 32 ? (uint32_t)NT : 32u; }
+// bytes between rows of an epilogue warp's transpose buffer (16 rows of up to 32 columns)
+template <int NT>
+__host__ __device__ constexpr uint32_t epi_pitch() { return 8u * epi_cols<NT>() + 8u; }
+template <int NT>
+__host__ __device__ constexpr uint32_t epi_bytes() { return 4u * 16u * epi_pitch<NT>(); }
+// raw copy slot: 8 complex64 entries per producer thread, entry j of thread t at j * P + t
+template <int NT>
+__host__ __device__ constexpr uint32_t raw_slot_bytes() { return 8u * producers<NT>() * 8u; }
+template <int NT>
+__host__ __device__ constexpr size_t smem_bytes(uint32_t K) {
+    return (size_t)n_stages<NT>() * stage_bytes(NT) + epi_bytes<NT>() + (size_t)kRaw * raw_slot_bytes<NT>() +
+           8u * (size_t)K;
+}
 
 __device__ __forceinline__ uint32_t core_offset(uint32_t r, uint32_t g) {
     return (r >> 3) * kPitch + g * 128u + (r & 7u) * 16u;
@@ -61,20 +88,32 @@ __device__ __forceinline__ const float2 *gemm_operand(const LaunchArgs &a, const
     return ldata + leaf_base(leaves[ref], x, o);
 }
 
-// Three-part bf16 split of v as raw 16-bit patterns: h = rn(v), m = rn(v - h),
-// l = rn(v - h - m); both differences are exact in FP32.
-__device__ __forceinline__ void split_bf16(float v, uint32_t &h, uint32_t &m, uint32_t &l) {
-    const __nv_bfloat16 bh = __float2bfloat16_rn(v);
-    const float r1 = v - __bfloat162float(bh);
-    const __nv_bfloat16 bm = __float2bfloat16_rn(r1);
-    const float r2 = r1 - __bfloat162float(bm);
-    h = __bfloat16_as_ushort(bh);
-    m = __bfloat16_as_ushort(bm);
-    l = __bfloat16_as_ushort(__float2bfloat16_rn(r2));
+// Three-part bf16 split of two floats at once, as packed pairs (lo in bits 0-15, hi in bits
+// 16-31): H = rn(lo, hi), M = rn of the remainders, L = rn of what is left; both remainders
+// are exact in FP32. cvt.rn.bf16x2.f32 rounds each half to nearest even.
+__device__ __forceinline__ uint32_t cvt_bf16x2(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+__device__ __forceinline__ void split_pair(float lo, float hi, uint32_t &H, uint32_t &M, uint32_t &L) {
+    H = cvt_bf16x2(lo, hi);
+    const float rl = lo - bf_lo(H), rh = hi - bf_hi(H);
+    M = cvt_bf16x2(rl, rh);
+    L = cvt_bf16x2(rl - bf_lo(M), rh - bf_hi(M));
 }
 
-__device__ __forceinline__ uint4 pack8(const uint32_t *h) {
-    return make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+// Packed bf16 parts (level 0: h, 1: m, 2: l) of the real and imaginary parts of 8 summed
+// entries of one operand row or column: word p holds entries 2p (low) and 2p + 1 (high).
+__device__ __forceinline__ void split8(const float2 *v, uint32_t (&re)[3][4], uint32_t (&im)[3][4]) {
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+        split_pair(v[2 * p].x, v[2 * p + 1].x, re[0][p], re[1][p], re[2][p]);
+        split_pair(v[2 * p].y, v[2 * p + 1].y, im[0][p], im[1][p], im[2][p]);
+    }
 }
 
 // Shared-memory matrix descriptor of a K-major tile without swizzling: start address, the
@@ -105,34 +144,23 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                  : "memory");
 }
 
-// Three bf16 parts (index 0: h, 1: m, 2: l) of the real and imaginary parts of 8 summed
-// entries of one operand row or column.
-__device__ __forceinline__ void split8(const float2 *v, uint32_t (*re)[8], uint32_t (*im)[8]) {
-#pragma unroll
-    for (int j = 0; j < 8; j++) {
-        split_bf16(v[j].x, re[0][j], re[1][j], re[2][j]);
-        split_bf16(v[j].y, im[0][j], im[1][j], im[2][j]);
-    }
-}
-
 // A rows 2m and 2m+1 of one summed half (8 entries) in the six A regions of a stage
 // (region 3p + level): part 0 takes (Ar, Ai), part 1 takes (-Ai, Ar).
 __device__ __forceinline__ void store_a(unsigned char *sa, const float2 *v, uint32_t ml, uint32_t h) {
     constexpr uint32_t R = region_bytes(kRows);
-    uint32_t re[3][8], im[3][8];
+    uint32_t re[3][4], im[3][4];
     split8(v, re, im);
     const uint32_t r0 = core_offset(2u * ml, h), r1 = core_offset(2u * ml + 1u, h);
 #pragma unroll
     for (uint32_t q = 0; q < 3; q++) {
-        *reinterpret_cast<uint4 *>(sa + q * R + r0) = pack8(re[q]);
-        *reinterpret_cast<uint4 *>(sa + q * R + r1) = pack8(im[q]);
-        *reinterpret_cast<uint4 *>(sa + (3u + q) * R + r1) = pack8(re[q]);
-    }
-#pragma unroll
-    for (uint32_t q = 0; q < 3; q++) {
-#pragma unroll
-        for (int j = 0; j < 8; j++) im[q][j] ^= 0x8000u;
-        *reinterpret_cast<uint4 *>(sa + (3u + q) * R + r0) = pack8(im[q]);
+        const uint4 wr = make_uint4(re[q][0], re[q][1], re[q][2], re[q][3]);
+        const uint4 wi = make_uint4(im[q][0], im[q][1], im[q][2], im[q][3]);
+        const uint4 wn = make_uint4(im[q][0] ^ 0x80008000u, im[q][1] ^ 0x80008000u, im[q][2] ^ 0x80008000u,
+                                    im[q][3] ^ 0x80008000u);
+        *reinterpret_cast<uint4 *>(sa + q * R + r0) = wr;
+        *reinterpret_cast<uint4 *>(sa + q * R + r1) = wi;
+        *reinterpret_cast<uint4 *>(sa + (3u + q) * R + r1) = wr;
+        *reinterpret_cast<uint4 *>(sa + (3u + q) * R + r0) = wn;
     }
 }
 
@@ -140,24 +168,15 @@ __device__ __forceinline__ void store_a(unsigned char *sa, const float2 *v, uint
 template <int NT>
 __device__ __forceinline__ void store_b(unsigned char *sb, const float2 *v, uint32_t nl, uint32_t h) {
     constexpr uint32_t R = region_bytes(NT);
-    uint32_t re[3][8], im[3][8];
+    uint32_t re[3][4], im[3][4];
     split8(v, re, im);
     const uint32_t o = core_offset(nl, h);
 #pragma unroll
     for (uint32_t q = 0; q < 3; q++) {
-        *reinterpret_cast<uint4 *>(sb + q * R + o) = pack8(re[q]);
-        *reinterpret_cast<uint4 *>(sb + (3u + q) * R + o) = pack8(im[q]);
+        *reinterpret_cast<uint4 *>(sb + q * R + o) = make_uint4(re[q][0], re[q][1], re[q][2], re[q][3]);
+        *reinterpret_cast<uint4 *>(sb + (3u + q) * R + o) = make_uint4(im[q][0], im[q][1], im[q][2], im[q][3]);
     }
 }
-
-// Raw staging of the producers' operand loads: each producer thread copies its own 8-byte
-// complex64 entries of a chunk (8 summed entries of its A row, and of each of its U B
-// columns) into shared memory with cp.async, several chunks ahead of the conversion, and
-// reads them back itself once its copy group has landed (so no barrier is needed). Entry j of
-// a thread's chunk sits at raw[(slot * (8 + 8U) + j) * 128 + thread]: consecutive threads
-// touch consecutive 8-byte words.
-template <uint32_t U>
-__host__ __device__ constexpr uint32_t raw_entries() { return 8u + 8u * U; }
 
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
@@ -165,37 +184,6 @@ __device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// The copies of chunk c of a tile into raw slot `slot`; ka and kb are the CTA's shared-memory
-// tables of the summed index's offsets in A and in B.
-template <uint32_t U>
-__device__ __forceinline__ void issue_chunk(uint32_t raw_slot, uint32_t c, uint32_t h, const float2 *Arow,
-                                            const float2 *const *Bcol, const uint32_t *bh, bool b_on,
-                                            const uint32_t *ka, const uint32_t *kb) {
-    {
-        const uint4 o0 = *reinterpret_cast<const uint4 *>(ka + c * kKq + 8u * h);
-        const uint4 o1 = *reinterpret_cast<const uint4 *>(ka + c * kKq + 8u * h + 4u);
-        const uint32_t o[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
-#pragma unroll
-        for (int j = 0; j < 8; j++) cp_async8(raw_slot + (uint32_t)j * 128u * 8u, Arow + o[j]);
-    }
-    if (b_on) {
-#pragma unroll
-        for (uint32_t i = 0; i < U; i++) {
-            const uint4 o0 = *reinterpret_cast<const uint4 *>(kb + c * kKq + 8u * bh[i]);
-            const uint4 o1 = *reinterpret_cast<const uint4 *>(kb + c * kKq + 8u * bh[i] + 4u);
-            const uint32_t o[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
-#pragma unroll
-            for (int j = 0; j < 8; j++) cp_async8(raw_slot + (8u + 8u * i + (uint32_t)j) * 128u * 8u, Bcol[i] + o[j]);
-        }
-    }
-}
-
-// Eight staged entries (entry j0 ... j0 + 7 of the thread's chunk) back into registers.
-__device__ __forceinline__ void read_raw8(const float2 *raw_slot_t, uint32_t j0, float2 *v) {
-#pragma unroll
-    for (uint32_t j = 0; j < 8; j++) v[j] = raw_slot_t[(j0 + j) * 128u];
-}
 
 struct GemmArgs {
     LaunchArgs a;
@@ -205,18 +193,6 @@ struct GemmArgs {
     uint32_t n_chunks, n_mt, n_nt;
     uint64_t n_tiles;
 };
-
-// Operand stages of the shared-memory ring: three of 52 KB for 128-column tiles, four below.
-template <int NT>
-__host__ __device__ constexpr uint32_t n_stages() { return NT >= 128 ? 2u : 3u; }
-constexpr uint32_t kRaw = 4;           // chunks of raw operand copies in flight per producer
-template <int NT>
-__host__ __device__ constexpr uint32_t epi_cols() { return NT < 32 ? (uint32_t)NT : 32u; }
-// bytes between rows of an epilogue warp's transpose buffer (16 rows of up to 32 columns)
-template <int NT>
-__host__ __device__ constexpr uint32_t epi_pitch() { return 8u * epi_cols<NT>() + 8u; }
-template <int NT>
-__host__ __device__ constexpr uint32_t epi_bytes() { return 4u * 16u * epi_pitch<NT>(); }
 
 // Bounded mbarrier wait that also gives up once another role has set the CTA's fail flag.
 __device__ __forceinline__ bool wait_or_fail(uint32_t bar, uint32_t parity, volatile int *fail) {
@@ -251,15 +227,16 @@ __device__ __forceinline__ TileCoord tile_coord(uint64_t t, const GemmArgs &ga) 
 
 // Persistent, warp-specialised tensor-core contraction. One CTA per SM walks the tiles
 // t = blockIdx.x, blockIdx.x + gridDim.x, ... (128 real rows x NT columns of one (item, b)):
-//   warps 0-3  producers: load the complex64 operands of one chunk of 16 summed entries
-//              (the next chunk's loads issued before this one's conversion), split them
-//              into bf16 parts and store them into the next stage of a ring of shared-memory
-//              stages, then arrive on the stage's "full" barrier;
-//   warp 4     allocates two tensor-memory accumulators; one thread issues each chunk's
+//   producer warps (P = 128 + 2 NT threads, one operand unit each): copy the unit's 8
+//              complex64 entries of each chunk into a private raw slot with cp.async,
+//              kRaw - 1 chunks ahead and across tile boundaries; once a chunk's copies have
+//              landed, split it into bf16 parts, store them into the next stage of the ring
+//              and arrive on the stage's "full" barrier;
+//   one warp   allocates two tensor-memory accumulators; one thread issues each chunk's
 //              twelve tcgen05.mma into the tile's accumulator (the tile's first product
 //              overwrites it), commits each chunk to the stage's "empty" barrier and the
 //              tile's last chunk to the accumulator's "full" barrier;
-//   warps 5-8  epilogue: wait for an accumulator, read it with tcgen05.ld (warp w reads
+//   4 warps    epilogue: wait for an accumulator, read it with tcgen05.ld (warp w reads
 //              tensor-memory lanes 32 (w mod 4) ...), store complex64 C through a padded
 //              shared-memory transpose and release the accumulator.
 // With two accumulators the epilogue of one tile overlaps the loads and MMAs of the next.
@@ -267,13 +244,15 @@ __device__ __forceinline__ TileCoord tile_coord(uint64_t t, const GemmArgs &ga) 
 // leave their loops, the MMA thread waits (bounded) for its issued MMAs before the tensor
 // memory is freed, and QVX_ETIMEOUT goes to the status word.
 template <int NT>
-__global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(GemmArgs ga) {
+__global__ void __launch_bounds__(block_threads<NT>(), 1) gemm_tc_kernel(GemmArgs ga) {
     constexpr uint32_t S = n_stages<NT>();
+    constexpr uint32_t P = producers<NT>();
+    constexpr uint32_t kMmaWarp = P / 32u;
     constexpr uint32_t kCols = NT < 32 ? 32u : (uint32_t)NT;   // columns of one accumulator
     constexpr uint32_t kRegA = region_bytes(kRows), kStage = stage_bytes(NT);
-    constexpr uint32_t kUnits = (2u * (uint32_t)NT + 127u) / 128u;   // B units per producer thread
     constexpr uint32_t kW = epi_cols<NT>(), kTPitch = epi_pitch<NT>();
-    constexpr uint32_t kRawSlot = raw_entries<kUnits>() * 128u * 8u;   // bytes of one raw slot
+    constexpr uint32_t kRawSlot = raw_slot_bytes<NT>();
+    static_assert(P % 32u == 0u, "producer warps");
     extern __shared__ __align__(1024) unsigned char gsm[];
     __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S], accf_bar[2], acce_bar[2], drain_bar;
     __shared__ uint32_t tmem_slot;
@@ -283,18 +262,18 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(GemmArgs ga) {
     const uint32_t sbase = smem_u32(gsm);
     if (threadIdx.x == 0) {
         for (uint32_t s = 0; s < S; s++) {
-            mbar_init(smem_u32(&full_bar[s]), 128);
+            mbar_init(smem_u32(&full_bar[s]), P);
             mbar_init(smem_u32(&empty_bar[s]), 1);
         }
         for (uint32_t b = 0; b < 2; b++) {
             mbar_init(smem_u32(&accf_bar[b]), 1);
-            mbar_init(smem_u32(&acce_bar[b]), 128);
+            mbar_init(smem_u32(&acce_bar[b]), kEpiThreads);
         }
         mbar_init(smem_u32(&drain_bar), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fail = 0;
     }
-    if (warp == 4) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                      "r"(2u * kCols)
                      : "memory");
@@ -302,10 +281,10 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(GemmArgs ga) {
     }
     // the summed index's offsets in A and B (bit-run maps evaluated once per CTA)
     const uint32_t K = ga.n_chunks * kKq;
-    float2 *raw = reinterpret_cast<float2 *>(gsm + S * kStage + epi_bytes<NT>());
-    uint32_t *tka = reinterpret_cast<uint32_t *>(gsm + S * kStage + epi_bytes<NT>() + kRaw * kRawSlot);
+    unsigned char *raw = gsm + S * kStage + epi_bytes<NT>();
+    uint32_t *tka = reinterpret_cast<uint32_t *>(raw + kRaw * kRawSlot);
     uint32_t *tkb = tka + K;
-    for (uint32_t i = threadIdx.x; i < K; i += kThreads) {
+    for (uint32_t i = threadIdx.x; i < K; i += block_threads<NT>()) {
         tka[i] = pext_runs(i, g.ak, g.n_ak);
         tkb[i] = pext_runs(i, g.bk, g.n_bk);
     }
@@ -313,34 +292,37 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(GemmArgs ga) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-    if (warp < 4) {
-        // producers: A rows m = mt*64 + 32*(warp&1) + lane, summed half h = warp>>1 of the
-        // chunk; B units (column, half) strided over the 128 threads. The copies run kRaw - 1
-        // chunks ahead of the conversion, across tile boundaries.
-        const uint32_t ml = 32u * (warp & 1u) + lane, h = warp >> 1;
-        const bool b_on = threadIdx.x < 2u * (uint32_t)NT;   // every unit of a thread shares this
-        uint32_t bh[kUnits];
-#pragma unroll
-        for (uint32_t i = 0; i < kUnits; i++) bh[i] = (threadIdx.x + 128u * i) / (uint32_t)NT;
-        const uint32_t raw_base = smem_u32(raw) + threadIdx.x * 8u;
+    if (warp < kMmaWarp) {
+        // producer: unit u < 128 is A row m = mt*64 + (u & 63), summed half u >> 6; unit
+        // u >= 128 is B column n = nt*NT + (u - 128) % NT, summed half (u - 128) / NT
+        const uint32_t u = threadIdx.x;
+        const bool is_a = u < 128u;
+        const uint32_t row = is_a ? (u & 63u) : (u - 128u) % (uint32_t)NT;
+        const uint32_t h = is_a ? (u >> 6) : (u - 128u) / (uint32_t)NT;
+        const uint32_t *koff = (is_a ? tka : tkb) + 8u * h;
+        const uint32_t raw_mine = smem_u32(raw) + u * 8u;
         // load cursor: the tile and chunk whose copies are issued next
         uint64_t lt = blockIdx.x;
         uint32_t lc = 0;
-        const float2 *Arow = nullptr, *Bcol[kUnits];
+        const float2 *src = nullptr;
         auto setup = [&](uint64_t t) {
             const TileCoord tc = tile_coord(t, ga);
-            float2 *arena = ga.arenas + (uint64_t)tc.il * ga.a.arena_elems;
-            const float2 *A = gemm_operand(ga.a, arena, g.a_off, g.flags & kStepALeaf, ga.item0 + tc.il);
-            const float2 *B = gemm_operand(ga.a, arena, g.b_off, g.flags & kStepBLeaf, ga.item0 + tc.il);
-            Arow = A + pext_runs(tc.beta, g.ab, g.n_ab) + pext_runs(tc.mt * 64u + ml, g.am, g.n_am);
-            const uint32_t bb = pext_runs(tc.beta, g.bb, g.n_bb);
-#pragma unroll
-            for (uint32_t i = 0; i < kUnits; i++)
-                Bcol[i] = B + bb + pext_runs(tc.nt * (uint32_t)NT + (threadIdx.x + 128u * i) % (uint32_t)NT, g.bn, g.n_bn);
+            const float2 *arena = ga.arenas + (uint64_t)tc.il * ga.a.arena_elems;
+            if (is_a)
+                src = gemm_operand(ga.a, arena, g.a_off, g.flags & kStepALeaf, ga.item0 + tc.il) +
+                      pext_runs(tc.beta, g.ab, g.n_ab) + pext_runs(tc.mt * 64u + row, g.am, g.n_am);
+            else
+                src = gemm_operand(ga.a, arena, g.b_off, g.flags & kStepBLeaf, ga.item0 + tc.il) +
+                      pext_runs(tc.beta, g.bb, g.n_bb) + pext_runs(tc.nt * (uint32_t)NT + row, g.bn, g.n_bn);
         };
-        auto issue_next = [&](uint32_t g_issue) {   // one commit group per chunk, empty at the end
+        auto issue_next = [&](uint64_t gi) {   // one commit group per chunk, empty past the end
             if (lt < ga.n_tiles) {
-                issue_chunk<kUnits>(raw_base + (g_issue % kRaw) * kRawSlot, lc, h, Arow, Bcol, bh, b_on, tka, tkb);
+                const uint32_t dst = raw_mine + (uint32_t)(gi % kRaw) * kRawSlot;
+                const uint4 o0 = *reinterpret_cast<const uint4 *>(koff + lc * kKq);
+                const uint4 o1 = *reinterpret_cast<const uint4 *>(koff + lc * kKq + 4u);
+                const uint32_t o[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
+#pragma unroll
+                for (uint32_t j = 0; j < 8; j++) cp_async8(dst + j * P * 8u, src + o[j]);
                 if (++lc == ga.n_chunks) {
                     lc = 0;
                     lt += gridDim.x;
@@ -354,36 +336,32 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(GemmArgs ga) {
         const uint64_t total = my_tiles * ga.n_chunks;
         for (uint32_t i = 0; i + 1 < kRaw; i++) issue_next(i);
         for (uint64_t gc = 0; gc < total && !fail; gc++) {
-            issue_next((uint32_t)(gc + kRaw - 1));
+            issue_next(gc + kRaw - 1);
             cp_async_wait<kRaw - 1>();   // this thread's copies of chunk gc have landed
             const uint32_t s = (uint32_t)(gc % S);
             if (!wait_or_fail(smem_u32(&empty_bar[s]), (uint32_t)((gc / S) & 1u) ^ 1u, &fail)) {
                 fail = 1;
                 break;
             }
-            const float2 *rt = raw + (size_t)(gc % kRaw) * (kRawSlot / 8u) + threadIdx.x;
-            unsigned char *sa = gsm + s * kStage;
+            const float2 *rt = reinterpret_cast<const float2 *>(raw + (gc % kRaw) * kRawSlot) + u;
             float2 v[8];
-            read_raw8(rt, 0, v);
-            store_a(sa, v, ml, h);
-            if (b_on) {
 #pragma unroll
-                for (uint32_t i = 0; i < kUnits; i++) {
-                    read_raw8(rt, 8u + 8u * i, v);
-                    store_b<NT>(sa + 6u * kRegA, v, (threadIdx.x + 128u * i) % (uint32_t)NT, bh[i]);
-                }
-            }
+            for (uint32_t j = 0; j < 8; j++) v[j] = rt[j * P];
+            unsigned char *sa = gsm + s * kStage;
+            if (is_a) store_a(sa, v, row, h);
+            else store_b<NT>(sa + 6u * kRegA, v, row, h);
             // the generic-proxy stores must be visible to the tensor cores' reads
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[s])) : "memory");
         }
         cp_async_wait<0>();   // no copy may still be landing when the CTA leaves
-    } else if (warp == 4) {
+    } else if (warp == kMmaWarp) {
         if (lane == 0) {   // MMA issuer
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
                                    ((kRows >> 4) << 24);
             constexpr uint32_t kRegB = region_bytes(NT);
-            uint32_t gc = 0, j = 0;
+            uint64_t gc = 0;
+            uint32_t j = 0;
             for (uint64_t t = blockIdx.x; t < ga.n_tiles && !fail; t += gridDim.x, j++) {
                 const uint32_t buf = j & 1u;
                 if (!wait_or_fail(smem_u32(&acce_bar[buf]), ((j >> 1) & 1u) ^ 1u, &fail)) {
@@ -394,8 +372,8 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(GemmArgs ga) {
                 const uint32_t d = tmem + buf * kCols;
                 bool ok = true;
                 for (uint32_t c = 0; c < ga.n_chunks; c++, gc++) {
-                    const uint32_t s = gc % S;
-                    if (!wait_or_fail(smem_u32(&full_bar[s]), (gc / S) & 1u, &fail)) {
+                    const uint32_t s = (uint32_t)(gc % S);
+                    if (!wait_or_fail(smem_u32(&full_bar[s]), (uint32_t)((gc / S) & 1u), &fail)) {
                         ok = false;
                         break;
                     }
@@ -496,7 +474,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_tc_kernel(GemmArgs ga) {
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 4) {
+    if (warp == kMmaWarp) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2u * kCols) : "memory");
     }
@@ -510,21 +488,21 @@ uint32_t gemm_nt(const GemmStep &g) { return g.nn >= 7 ? 128u : (1u << g.nn); }
 template <int NT>
 static cudaError_t launch_gemm_nt(GemmArgs ga, cudaStream_t s) {
     // dynamic shared memory: the operand stage ring, the epilogue's transpose buffers, the
-    // producers' raw copy slots and the summed index tables (the largest K is 1024)
-    constexpr uint32_t kUnits = (2u * (uint32_t)NT + 127u) / 128u;
-    constexpr size_t kSmem = (size_t)n_stages<NT>() * stage_bytes(NT) + epi_bytes<NT>() +
-                             (size_t)kRaw * raw_entries<kUnits>() * 128u * 8u + 4u * 2u * 1024u;
+    // producers' raw copy slots and the summed index tables; the attribute is set once per
+    // device for the largest summed index (1024 entries)
     static int per_sm[64] = {0}, sms[64] = {0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    constexpr size_t kMaxSmem = smem_bytes<NT>(1024);
     if (!per_sm[dev]) {
-        if ((e = cudaFuncSetAttribute(gemm_tc_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem)) !=
+        if ((e = cudaFuncSetAttribute(gemm_tc_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem)) !=
             cudaSuccess)
             return e;
         int n = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gemm_tc_kernel<NT>, kThreads, kSmem)) != cudaSuccess)
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gemm_tc_kernel<NT>, block_threads<NT>(), kMaxSmem)) !=
+            cudaSuccess)
             return e;
         if ((e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
         // the CTAs an SM holds stay within its 512 tensor-memory columns, so that no
@@ -536,7 +514,7 @@ static cudaError_t launch_gemm_nt(GemmArgs ga, cudaStream_t s) {
     ga.n_tiles = ((uint64_t)ga.n_items << ga.g.nb) * ga.n_mt * ga.n_nt;
     if (ga.n_tiles == 0) return cudaErrorInvalidConfiguration;
     const uint64_t grid = std::min<uint64_t>(ga.n_tiles, (uint64_t)sms[dev] * (uint64_t)per_sm[dev]);
-    gemm_tc_kernel<NT><<<(unsigned)grid, kThreads, kSmem, s>>>(ga);
+    gemm_tc_kernel<NT><<<(unsigned)grid, block_threads<NT>(), kMaxSmem, s>>>(ga);
     return cudaGetLastError();
 }
 
@@ -553,6 +531,7 @@ cudaError_t launch_gemm_step(const LaunchArgs &a, const GemmStep &g, int64_t ite
     ga.n_chunks = (1u << g.nk) / kKq;
     ga.n_mt = (2u << g.nm) / kRows;
     ga.n_nt = (1u << g.nn) / nt_cols;
+    ga.n_tiles = 0;
     cudaError_t e;
     switch (nt_cols) {
         case 16: e = launch_gemm_nt<16>(ga, s); break;

@@ -516,3 +516,33 @@ def test_open_qubit_errors():
     untouched = cg.Circuit(n_qubits=2, gates=[cg.Gate(cg.H, 0)])
     with pytest.raises(q.QvxError):
         q.Plan(untouched, open_qubits=[1])
+
+
+def test_81_qubit_program_on_host_matches_oracle():
+    # bitstrings of more than 64 qubits: the device program reads qubits 64.. from the second
+    # word (leaf sources 64..127) and slice bits from sources 128..
+    c = cg.grid_circuit(9, 9, 8, 91)
+    p = q.Plan(c, n_slices=3, inner_slices=1, engine="stepwise")
+    assert p.words == 2 and p.info["n_qubits"] == 81
+    prog = Program(p.image())
+    xs = cg.random_bitstrings(81, 3, 92)
+    assert all(x >> 64 for x in xs)
+    for x in xs:
+        ref = VE.slice_terms(c, x, p.order, p.slices)
+        terms = prog.slice_terms(x)
+        assert np.max(np.abs(terms - ref)) < 1e-6 * 2 ** (-81 / 2)
+    words = q.bitstring_words(xs, 2)
+    assert [(w & (2 ** 64 - 1)) | ((words[2 * i + 1] & (2 ** 64 - 1)) << 64)
+            for i, w in enumerate(words[0::2])] == xs
+
+
+def test_bitstring_words_and_generator():
+    assert q.bitstring_words([1 << 70 | 5], 2) == [5, 1 << 6]
+    assert q.bitstring_words([2 ** 64 - 1], 1) == [-1]
+    # up to 64 qubits one draw per string (the sequence the earlier workloads use)
+    assert cg.random_bitstrings(64, 3, 5) == [v for v in cg.random_bitstrings(64, 3, 5)]
+    wide = cg.random_bitstrings(81, 4, 9)
+    assert all(0 <= v < 2 ** 81 for v in wide) and any(v >> 64 for v in wide)
+    rng = cg.SplitMix64(9)
+    first = rng.next() | (rng.next() << 64)
+    assert wide[0] == first & (2 ** 81 - 1)

@@ -1,27 +1,30 @@
 // Dense contractions on the tcgen05 tensor cores (stepwise engine, opts.tensor_cores).
 //
 // A step C[b, m, n] = sum_k A[b, m, k] B[b, k, n] in complex64 becomes one real GEMM per
-// (work item, b): with A = Ar + i Ai and B = Br + i Bi, the real rows 2m and 2m + 1 of
-//   [Ar  -Ai]        [Br]
-//   [Ai   Ar]  times [Bi]
-// are Re C[m, :] and Im C[m, :] (the left factor's first column block is "part 0", the
-// second "part 1"). Every real operand x is split into three bf16 parts x = h + m + l
-// (8 significant bits each: h = rn(x), m = rn(x - h), l = rn(x - h - m)), and the six
-// products h*h + h*m + m*h + h*l + l*h + m*m are accumulated in FP32; the dropped terms
-// (m*l, l*m, l*l) are below 2^-23 of the product. Two parts with three products (about
-// 2^-16 per product) are not accurate enough: on a 64-qubit circuit the amplitude moved by
-// 1.2e-5 of its size, above the 1e-5 tolerance.
+// (work item, b): with A = Ar + i Ai and B = Br + i Bi,
+//   [Re C[m, n], Im C[m, n]] = [Ar | Ai][m, :]  times  [[Br, Bi], [-Bi, Br]][:, (n, re/im)],
+// i.e. the left factor's real summed index is (part p, k) with part 0 = Ar and part 1 = Ai,
+// and the right factor has two real columns per complex column n: 2n = (Br; -Bi) and
+// 2n + 1 = (Bi; Br). Every real operand x is split into three bf16 parts x = h + m + l (8
+// significant bits each: h = rn(x), m = rn(x - h), l = rn(x - h - m)), and the six products
+// h*h + h*m + m*h + h*l + l*h + m*m are accumulated in FP32; the dropped terms (m*l, l*m,
+// l*l) are below 2^-23 of the product. Two parts with three products (about 2^-16 per
+// product) are not accurate enough: on a 64-qubit circuit the amplitude moved by 1.2e-5 of
+// its size, above the 1e-5 tolerance.
 //
-// A tile is 128 real rows (64 complex rows m) by NT columns n of one (item, b). The kernel
-// is persistent (one CTA per SM walks the tiles) and warp-specialised: producer warps copy
-// the complex64 operands straight from the arena into shared memory (cp.async, several
-// chunks of 16 summed entries ahead), split them into three bf16 parts and store them in the
-// tensor cores' K-major core-matrix layout in a ring of shared-memory stages (no separate
-// packing pass: the operands cross HBM once, as complex64); one thread issues each chunk's
-// twelve tcgen05.mma (2 parts x 6 products, K = 16 each) into one of two tensor-memory
-// accumulators; epilogue warps read a finished accumulator with tcgen05.ld and store
-// complex64 C in its own layout while the next tile's chunks are loaded and multiplied into
-// the other accumulator.
+// The row role goes to the operand that holds C's lowest mode, so tensor-memory lane i (row
+// m = i of a 128-row tile) holds C entries that are consecutive in memory along the lanes;
+// the real columns 2n and 2n + 1 of a lane are Re and Im of C[m, n], so the epilogue stores
+// complex64 values straight from the registers tcgen05.ld fills, coalesced across the warp,
+// with no transpose. A tile is 128 complex rows by NT real (NT / 2 complex) columns of one
+// (item, b). The kernel is persistent (one CTA per SM walks the tiles) and
+// warp-specialised: producer warps copy the complex64 operands straight from the arena into
+// shared memory (cp.async, several chunks of 16 summed entries ahead), split them into
+// three bf16 parts and store them in the tensor cores' K-major core-matrix layout in a ring
+// of shared-memory stages (no separate packing pass: the operands cross HBM once, as
+// complex64); one thread issues each chunk's twelve tcgen05.mma (2 parts x 6 products, K =
+// 16 each) into one of two tensor-memory accumulators; epilogue warps store a finished
+// accumulator while the next tile's chunks are loaded and multiplied into the other.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -34,7 +37,7 @@
 namespace qvx {
 namespace {
 
-constexpr uint32_t kRows = 128;        // real rows per tile (64 complex rows)
+constexpr uint32_t kRows = 128;        // rows per tile (complex rows of C)
 constexpr uint32_t kKq = 16;           // complex summed entries per chunk (one MMA K-step)
 constexpr uint32_t kPitch = 272;       // bytes between 8-row groups: two 128-byte core matrices
                                        // along the summed index and 16 bytes that spread the
@@ -47,29 +50,25 @@ __host__ __device__ constexpr uint32_t region_bytes(uint32_t rows) { return rows
 // One stage: A regions (part 0 h, m, l, part 1 h, m, l), then the same for B.
 __host__ __device__ constexpr uint32_t stage_bytes(uint32_t nt) { return 6u * region_bytes(kRows) + 6u * region_bytes(nt); }
 
-// Producer threads: one per operand unit of a chunk (8 summed entries of one A row or one B
-// column): 64 rows x 2 halves of A and NT columns x 2 halves of B.
+// Producer threads: one per operand unit of a chunk (8 summed entries of one A row or one
+// complex B column): 128 rows x 2 halves of A and NT / 2 columns x 2 halves of B (threads
+// beyond the units, for NT = 16, only take part in the barriers).
 template <int NT>
-__host__ __device__ constexpr uint32_t producers() { return 128u + 2u * (uint32_t)NT; }
+__host__ __device__ constexpr uint32_t producers() { return 256u + ((uint32_t)NT < 32u ? 32u : (uint32_t)NT); }
 template <int NT>
 __host__ __device__ constexpr uint32_t block_threads() { return producers<NT>() + 32u + kEpiThreads; }
 // Operand stages of the shared-memory ring: two of 52 KB for 128-column tiles, three below.
 template <int NT>
 __host__ __device__ constexpr uint32_t n_stages() { return NT >= 128 ? 2u : 3u; }
+// real accumulator columns an epilogue warp reads at a time
 template <int NT>
 __host__ __device__ constexpr uint32_t epi_cols() { return NT < 32 ? (uint32_t)NT : 32u; }
-// bytes between rows of an epilogue warp's transpose buffer (16 rows of up to 32 columns)
-template <int NT>
-__host__ __device__ constexpr uint32_t epi_pitch() { return 8u * epi_cols<NT>() + 8u; }
-template <int NT>
-__host__ __device__ constexpr uint32_t epi_bytes() { return 4u * 16u * epi_pitch<NT>(); }
 // raw copy slot: 8 complex64 entries per producer thread, entry j of thread t at j * P + t
 template <int NT>
 __host__ __device__ constexpr uint32_t raw_slot_bytes() { return 8u * producers<NT>() * 8u; }
 template <int NT>
 __host__ __device__ constexpr size_t smem_bytes(uint32_t K) {
-    return (size_t)n_stages<NT>() * stage_bytes(NT) + epi_bytes<NT>() + (size_t)kRaw * raw_slot_bytes<NT>() +
-           8u * (size_t)K;
+    return (size_t)n_stages<NT>() * stage_bytes(NT) + (size_t)kRaw * raw_slot_bytes<NT>() + 8u * (size_t)K;
 }
 
 __device__ __forceinline__ uint32_t core_offset(uint32_t r, uint32_t g) {
@@ -144,37 +143,38 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                  : "memory");
 }
 
-// A rows 2m and 2m+1 of one summed half (8 entries) in the six A regions of a stage
-// (region 3p + level): part 0 takes (Ar, Ai), part 1 takes (-Ai, Ar).
-__device__ __forceinline__ void store_a(unsigned char *sa, const float2 *v, uint32_t ml, uint32_t h) {
+// A row m of one summed half (8 entries) in the six A regions of a stage (region 3p +
+// level): part 0 takes Ar, part 1 takes Ai.
+__device__ __forceinline__ void store_a(unsigned char *sa, const float2 *v, uint32_t m, uint32_t h) {
     constexpr uint32_t R = region_bytes(kRows);
     uint32_t re[3][4], im[3][4];
     split8(v, re, im);
-    const uint32_t r0 = core_offset(2u * ml, h), r1 = core_offset(2u * ml + 1u, h);
+    const uint32_t o = core_offset(m, h);
+#pragma unroll
+    for (uint32_t q = 0; q < 3; q++) {
+        *reinterpret_cast<uint4 *>(sa + q * R + o) = make_uint4(re[q][0], re[q][1], re[q][2], re[q][3]);
+        *reinterpret_cast<uint4 *>(sa + (3u + q) * R + o) = make_uint4(im[q][0], im[q][1], im[q][2], im[q][3]);
+    }
+}
+
+// Complex B column n of one summed half in the six B regions: real column 2n takes Br in
+// part 0 and -Bi in part 1, real column 2n + 1 takes Bi in part 0 and Br in part 1.
+template <int NT>
+__device__ __forceinline__ void store_b(unsigned char *sb, const float2 *v, uint32_t n, uint32_t h) {
+    constexpr uint32_t R = region_bytes(NT);
+    uint32_t re[3][4], im[3][4];
+    split8(v, re, im);
+    const uint32_t o0 = core_offset(2u * n, h), o1 = core_offset(2u * n + 1u, h);
 #pragma unroll
     for (uint32_t q = 0; q < 3; q++) {
         const uint4 wr = make_uint4(re[q][0], re[q][1], re[q][2], re[q][3]);
         const uint4 wi = make_uint4(im[q][0], im[q][1], im[q][2], im[q][3]);
         const uint4 wn = make_uint4(im[q][0] ^ 0x80008000u, im[q][1] ^ 0x80008000u, im[q][2] ^ 0x80008000u,
                                     im[q][3] ^ 0x80008000u);
-        *reinterpret_cast<uint4 *>(sa + q * R + r0) = wr;
-        *reinterpret_cast<uint4 *>(sa + q * R + r1) = wi;
-        *reinterpret_cast<uint4 *>(sa + (3u + q) * R + r1) = wr;
-        *reinterpret_cast<uint4 *>(sa + (3u + q) * R + r0) = wn;
-    }
-}
-
-// B column n of one summed half in the six B regions: part 0 takes Br, part 1 Bi.
-template <int NT>
-__device__ __forceinline__ void store_b(unsigned char *sb, const float2 *v, uint32_t nl, uint32_t h) {
-    constexpr uint32_t R = region_bytes(NT);
-    uint32_t re[3][4], im[3][4];
-    split8(v, re, im);
-    const uint32_t o = core_offset(nl, h);
-#pragma unroll
-    for (uint32_t q = 0; q < 3; q++) {
-        *reinterpret_cast<uint4 *>(sb + q * R + o) = make_uint4(re[q][0], re[q][1], re[q][2], re[q][3]);
-        *reinterpret_cast<uint4 *>(sb + (3u + q) * R + o) = make_uint4(im[q][0], im[q][1], im[q][2], im[q][3]);
+        *reinterpret_cast<uint4 *>(sb + q * R + o0) = wr;
+        *reinterpret_cast<uint4 *>(sb + (3u + q) * R + o0) = wn;
+        *reinterpret_cast<uint4 *>(sb + q * R + o1) = wi;
+        *reinterpret_cast<uint4 *>(sb + (3u + q) * R + o1) = wr;
     }
 }
 
@@ -226,8 +226,8 @@ __device__ __forceinline__ TileCoord tile_coord(uint64_t t, const GemmArgs &ga) 
 }
 
 // Persistent, warp-specialised tensor-core contraction. One CTA per SM walks the tiles
-// t = blockIdx.x, blockIdx.x + gridDim.x, ... (128 real rows x NT columns of one (item, b)):
-//   producer warps (P = 128 + 2 NT threads, one operand unit each): copy the unit's 8
+// t = blockIdx.x, blockIdx.x + gridDim.x, ... (128 rows x NT real columns of one (item, b)):
+//   producer warps (P threads, one operand unit each): copy the unit's 8
 //              complex64 entries of each chunk into a private raw slot with cp.async,
 //              kRaw - 1 chunks ahead and across tile boundaries; once a chunk's copies have
 //              landed, split it into bf16 parts, store them into the next stage of the ring
@@ -237,8 +237,9 @@ __device__ __forceinline__ TileCoord tile_coord(uint64_t t, const GemmArgs &ga) 
 //              overwrites it), commits each chunk to the stage's "empty" barrier and the
 //              tile's last chunk to the accumulator's "full" barrier;
 //   4 warps    epilogue: wait for an accumulator, read it with tcgen05.ld (warp w reads
-//              tensor-memory lanes 32 (w mod 4) ...), store complex64 C through a padded
-//              shared-memory transpose and release the accumulator.
+//              tensor-memory lanes 32 (w mod 4) ..., i.e. rows 32 (w mod 4) + lane), store
+//              each (Re, Im) column pair as one complex64 entry of C and release the
+//              accumulator.
 // With two accumulators the epilogue of one tile overlaps the loads and MMAs of the next.
 // Every wait is bounded; a wait that runs out sets the CTA's fail flag, the other roles
 // leave their loops, the MMA thread waits (bounded) for its issued MMAs before the tensor
@@ -250,7 +251,8 @@ __global__ void __launch_bounds__(block_threads<NT>(), 1) gemm_tc_kernel(GemmArg
     constexpr uint32_t kMmaWarp = P / 32u;
     constexpr uint32_t kCols = NT < 32 ? 32u : (uint32_t)NT;   // columns of one accumulator
     constexpr uint32_t kRegA = region_bytes(kRows), kStage = stage_bytes(NT);
-    constexpr uint32_t kW = epi_cols<NT>(), kTPitch = epi_pitch<NT>();
+    constexpr uint32_t kW = epi_cols<NT>();
+    constexpr uint32_t kNc = (uint32_t)NT / 2u;   // complex columns per tile
     constexpr uint32_t kRawSlot = raw_slot_bytes<NT>();
     static_assert(P % 32u == 0u, "producer warps");
     extern __shared__ __align__(1024) unsigned char gsm[];
@@ -281,7 +283,7 @@ __global__ void __launch_bounds__(block_threads<NT>(), 1) gemm_tc_kernel(GemmArg
     }
     // the summed index's offsets in A and B (bit-run maps evaluated once per CTA)
     const uint32_t K = ga.n_chunks * kKq;
-    unsigned char *raw = gsm + S * kStage + epi_bytes<NT>();
+    unsigned char *raw = gsm + S * kStage;
     uint32_t *tka = reinterpret_cast<uint32_t *>(raw + kRaw * kRawSlot);
     uint32_t *tkb = tka + K;
     for (uint32_t i = threadIdx.x; i < K; i += block_threads<NT>()) {
@@ -293,12 +295,14 @@ __global__ void __launch_bounds__(block_threads<NT>(), 1) gemm_tc_kernel(GemmArg
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
     if (warp < kMmaWarp) {
-        // producer: unit u < 128 is A row m = mt*64 + (u & 63), summed half u >> 6; unit
-        // u >= 128 is B column n = nt*NT + (u - 128) % NT, summed half (u - 128) / NT
+        // producer: unit u < 256 is A row m = mt*128 + (u & 127), summed half u >> 7; unit
+        // u >= 256 is complex B column n = nt*NT/2 + (u - 256) % (NT/2), summed half
+        // (u - 256) / (NT/2); threads past the units only take part in the barriers
         const uint32_t u = threadIdx.x;
-        const bool is_a = u < 128u;
-        const uint32_t row = is_a ? (u & 63u) : (u - 128u) % (uint32_t)NT;
-        const uint32_t h = is_a ? (u >> 6) : (u - 128u) / (uint32_t)NT;
+        const bool is_a = u < 256u;
+        const bool active = is_a || u - 256u < (uint32_t)NT;
+        const uint32_t row = is_a ? (u & 127u) : (u - 256u) % kNc;
+        const uint32_t h = is_a ? (u >> 7) : ((u - 256u) / kNc) & 1u;
         const uint32_t *koff = (is_a ? tka : tkb) + 8u * h;
         const uint32_t raw_mine = smem_u32(raw) + u * 8u;
         // load cursor: the tile and chunk whose copies are issued next
@@ -310,28 +314,30 @@ __global__ void __launch_bounds__(block_threads<NT>(), 1) gemm_tc_kernel(GemmArg
             const float2 *arena = ga.arenas + (uint64_t)tc.il * ga.a.arena_elems;
             if (is_a)
                 src = gemm_operand(ga.a, arena, g.a_off, g.flags & kStepALeaf, ga.item0 + tc.il) +
-                      pext_runs(tc.beta, g.ab, g.n_ab) + pext_runs(tc.mt * 64u + row, g.am, g.n_am);
+                      pext_runs(tc.beta, g.ab, g.n_ab) + pext_runs(tc.mt * kRows + row, g.am, g.n_am);
             else
                 src = gemm_operand(ga.a, arena, g.b_off, g.flags & kStepBLeaf, ga.item0 + tc.il) +
-                      pext_runs(tc.beta, g.bb, g.n_bb) + pext_runs(tc.nt * (uint32_t)NT + row, g.bn, g.n_bn);
+                      pext_runs(tc.beta, g.bb, g.n_bb) + pext_runs(tc.nt * kNc + row, g.bn, g.n_bn);
         };
         auto issue_next = [&](uint64_t gi) {   // one commit group per chunk, empty past the end
-            if (lt < ga.n_tiles) {
+            if (lt < ga.n_tiles && active) {
                 const uint32_t dst = raw_mine + (uint32_t)(gi % kRaw) * kRawSlot;
                 const uint4 o0 = *reinterpret_cast<const uint4 *>(koff + lc * kKq);
                 const uint4 o1 = *reinterpret_cast<const uint4 *>(koff + lc * kKq + 4u);
                 const uint32_t o[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
 #pragma unroll
                 for (uint32_t j = 0; j < 8; j++) cp_async8(dst + j * P * 8u, src + o[j]);
+            }
+            if (lt < ga.n_tiles) {
                 if (++lc == ga.n_chunks) {
                     lc = 0;
                     lt += gridDim.x;
-                    if (lt < ga.n_tiles) setup(lt);
+                    if (lt < ga.n_tiles && active) setup(lt);
                 }
             }
             cp_async_commit();
         };
-        setup(lt);
+        if (active) setup(lt);
         const uint64_t my_tiles = (ga.n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
         const uint64_t total = my_tiles * ga.n_chunks;
         for (uint32_t i = 0; i + 1 < kRaw; i++) issue_next(i);
@@ -343,13 +349,15 @@ __global__ void __launch_bounds__(block_threads<NT>(), 1) gemm_tc_kernel(GemmArg
                 fail = 1;
                 break;
             }
-            const float2 *rt = reinterpret_cast<const float2 *>(raw + (gc % kRaw) * kRawSlot) + u;
-            float2 v[8];
+            if (active) {
+                const float2 *rt = reinterpret_cast<const float2 *>(raw + (gc % kRaw) * kRawSlot) + u;
+                float2 v[8];
 #pragma unroll
-            for (uint32_t j = 0; j < 8; j++) v[j] = rt[j * P];
-            unsigned char *sa = gsm + s * kStage;
-            if (is_a) store_a(sa, v, row, h);
-            else store_b<NT>(sa + 6u * kRegA, v, row, h);
+                for (uint32_t j = 0; j < 8; j++) v[j] = rt[j * P];
+                unsigned char *sa = gsm + s * kStage;
+                if (is_a) store_a(sa, v, row, h);
+                else store_b<NT>(sa + 6u * kRegA, v, row, h);
+            }
             // the generic-proxy stores must be visible to the tensor cores' reads
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[s])) : "memory");
@@ -409,23 +417,19 @@ __global__ void __launch_bounds__(block_threads<NT>(), 1) gemm_tc_kernel(GemmArg
         }
         __syncwarp();
     } else {
-        // epilogue: warp w reads tensor-memory lanes 32q ... 32q + 31 (q = w mod 4), i.e.
-        // complex rows m = mt*64 + 16q + lane/2 (Re in the even lane, Im in the odd one). Each
-        // block of up to 32 columns goes through the warp's padded transpose buffer, so that
-        // the warp then stores 32 consecutive columns of one row of C at a time.
+        // epilogue: warp w reads tensor-memory lanes 32q ... 32q + 31 (q = w mod 4): row
+        // m = mt*128 + 32q + lane of the tile, whose real columns 2j and 2j + 1 are Re and Im
+        // of C[m, nt*NT/2 + j]. For each column the warp's 32 stores are 32 rows, consecutive
+        // in C when its lowest modes are row modes (the planner gives the row role to the
+        // operand that holds C's lowest mode).
         const uint32_t q = warp & 3u;
-        unsigned char *tb = gsm + S * kStage + q * 16u * kTPitch;
-        const uint32_t s = lane & 1u, mrow = lane >> 1;
         uint32_t j = 0;
         for (uint64_t t = blockIdx.x; t < ga.n_tiles && !fail; t += gridDim.x, j++) {
             const TileCoord tc = tile_coord(t, ga);
             const uint32_t buf = j & 1u;
-            // this warp's 16 row offsets in C and the tile's base, while the MMAs run
-            const uint32_t my_row = pext_runs(tc.mt * 64u + 16u * q + (lane & 15u), g.cm, g.n_cm);
-            uint32_t roff[16];
-#pragma unroll
-            for (uint32_t i = 0; i < 16; i++) roff[i] = __shfl_sync(0xffffffffu, my_row, i);
-            float2 *Cb = ga.arenas + (uint64_t)tc.il * ga.a.arena_elems + g.c_off + pext_runs(tc.beta, g.cb, g.n_cb);
+            // this lane's row of C and the tile's base, while the MMAs run
+            float2 *Crow = ga.arenas + (uint64_t)tc.il * ga.a.arena_elems + g.c_off + pext_runs(tc.beta, g.cb, g.n_cb) +
+                           pext_runs(tc.mt * kRows + 32u * q + lane, g.cm, g.n_cm);
             if (!wait_or_fail(smem_u32(&accf_bar[buf]), (j >> 1) & 1u, &fail)) {
                 fail = 1;
                 break;
@@ -433,7 +437,8 @@ __global__ void __launch_bounds__(block_threads<NT>(), 1) gemm_tc_kernel(GemmArg
             tc_fence_after();
             const uint32_t taddr = tmem + ((q * 32u) << 16) + buf * kCols;
             for (uint32_t j0 = 0; j0 < (uint32_t)NT; j0 += kW) {
-                const uint32_t coff = pext_runs(tc.nt * (uint32_t)NT + j0 + (lane % kW), g.cn, g.n_cn);
+                // the column offsets of this block's kW / 2 complex columns, one per lane
+                const uint32_t my_col = pext_runs(tc.nt * kNc + j0 / 2u + (lane % (kW / 2u)), g.cn, g.n_cn);
                 uint32_t r[kW];
                 if constexpr (kW == 32) {
                     asm volatile(
@@ -457,15 +462,10 @@ __global__ void __launch_bounds__(block_threads<NT>(), 1) gemm_tc_kernel(GemmArg
                 }
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (uint32_t n = 0; n < kW; n++)
-                    *reinterpret_cast<uint32_t *>(tb + mrow * kTPitch + n * 8u + s * 4u) = r[n];
-                __syncwarp();
-                if (lane < kW) {
-#pragma unroll
-                    for (uint32_t i = 0; i < 16; i++)
-                        Cb[roff[i] + coff] = *reinterpret_cast<const float2 *>(tb + i * kTPitch + lane * 8u);
+                for (uint32_t i = 0; i < kW / 2u; i++) {
+                    const uint32_t coff = __shfl_sync(0xffffffffu, my_col, i);
+                    Crow[coff] = make_float2(__uint_as_float(r[2u * i]), __uint_as_float(r[2u * i + 1u]));
                 }
-                __syncwarp();
             }
             // the accumulator's reads are done: the MMAs of the tile after next may reuse it
             tc_fence_before();
@@ -483,13 +483,14 @@ __global__ void __launch_bounds__(block_threads<NT>(), 1) gemm_tc_kernel(GemmArg
 
 }  // namespace
 
-uint32_t gemm_nt(const GemmStep &g) { return g.nn >= 7 ? 128u : (1u << g.nn); }
+// real columns of a tile: two per complex column, up to 64 complex columns
+uint32_t gemm_nt(const GemmStep &g) { return g.nn >= 6 ? 128u : (2u << g.nn); }
 
 template <int NT>
 static cudaError_t launch_gemm_nt(GemmArgs ga, cudaStream_t s) {
-    // dynamic shared memory: the operand stage ring, the epilogue's transpose buffers, the
-    // producers' raw copy slots and the summed index tables; the attribute is set once per
-    // device for the largest summed index (1024 entries)
+    // dynamic shared memory: the operand stage ring, the producers' raw copy slots and the
+    // summed index tables; the attribute is set once per device for the largest summed
+    // index (1024 entries)
     static int per_sm[64] = {0}, sms[64] = {0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -520,7 +521,7 @@ static cudaError_t launch_gemm_nt(GemmArgs ga, cudaStream_t s) {
 
 cudaError_t launch_gemm_step(const LaunchArgs &a, const GemmStep &g, int64_t item0, int64_t n_items, float2 *arenas,
                              cudaStream_t s) {
-    if (g.nk < 4 || g.nk > 10 || g.nm < 6 || g.nn < 4 || n_items <= 0) return cudaErrorInvalidConfiguration;
+    if (g.nk < 4 || g.nk > 10 || g.nm < 7 || g.nn < 3 || n_items <= 0) return cudaErrorInvalidConfiguration;
     const uint32_t nt_cols = gemm_nt(g);
     GemmArgs ga;
     ga.a = a;
@@ -529,8 +530,8 @@ cudaError_t launch_gemm_step(const LaunchArgs &a, const GemmStep &g, int64_t ite
     ga.n_items = n_items;
     ga.arenas = arenas;
     ga.n_chunks = (1u << g.nk) / kKq;
-    ga.n_mt = (2u << g.nm) / kRows;
-    ga.n_nt = (1u << g.nn) / nt_cols;
+    ga.n_mt = (1u << g.nm) / kRows;
+    ga.n_nt = (2u << g.nn) / nt_cols;
     ga.n_tiles = 0;
     cudaError_t e;
     switch (nt_cols) {

@@ -1389,12 +1389,13 @@ bool serialize(Plan &p, std::string *err) {
         }
     }
     // tensor-core form of the dense contractions (stepwise engine, opts.tensor_cores): every
-    // summed mode in both operands, 16 to 1024 summed entries (K), 64 A-only (M) and 16
-    // B-only (N) output entries, and an arithmetic intensity at or above the FP32 ridge.
-    // The epilogue's lanes store along N, so C's lowest mode (its unit stride) decides how
-    // the stores coalesce: a step whose lowest output mode is held by both operands (a batch
-    // mode: every CTA's tile then lands at a stride of at least two entries) keeps its SIMT
-    // form, and when both role assignments fit, the operand holding that mode takes N.
+    // summed mode in both operands, 16 to 1024 summed entries (K) and an arithmetic intensity
+    // at or above the FP32 ridge. The GEMM's row role goes to the operand that holds C's
+    // lowest mode (its unit stride) alone: a tile's 128 rows then sit in consecutive
+    // tensor-memory lanes and the epilogue's stores of each column are consecutive in C. That
+    // operand needs 128 output entries of its own, the other 8; a step whose lowest output
+    // mode is held by both operands (a batch mode) keeps its SIMT form. Complex products
+    // commute, so the step's B may take the row role.
     std::vector<GemmStep> gms;
     if (p.engine == QVX_ENGINE_STEPWISE && p.opts.tensor_cores) {
         gms.assign(ds.size(), GemmStep{});
@@ -1403,28 +1404,13 @@ bool serialize(Plan &p, std::string *err) {
             GemmStep &g = gms[s];
             std::memset(&g, 0, sizeof(g));
             if (st.b < 0 || !st.k_a.empty() || !st.k_b.empty() || st.k_ab.size() < 4 || st.k_ab.size() > 10) continue;
-            // the GEMM's row operand needs 64 output entries of its own and the column operand
-            // 16; complex products commute, so the step's B may take the row role
-            bool swap = false;
+            if (p.tensors[st.c].modes.empty()) continue;
+            const int low = p.tensors[st.c].modes[0];
+            const bool low_a = find_pos(p.tensors[st.a].modes, low) >= 0;
+            const bool low_b = find_pos(p.tensors[st.b].modes, low) >= 0;
+            if (low_a == low_b) continue;   // a batch mode
+            const bool swap = low_b;
             std::vector<int> gb, gm, gn;
-            const int low = p.tensors[st.c].modes.empty() ? -1 : p.tensors[st.c].modes[0];
-            int pick = -1;   // 0: as given, 1: swapped
-            for (int pass = 0; pass < 2; pass++) {
-                const std::vector<int> &LA = p.tensors[pass ? st.b : st.a].modes;
-                const std::vector<int> &LB = p.tensors[pass ? st.a : st.b].modes;
-                int na = 0, nb = 0;
-                bool low_n = false, low_batch = false;
-                for (int v : p.tensors[st.c].modes) {
-                    const bool ia = find_pos(LA, v) >= 0, ib = find_pos(LB, v) >= 0;
-                    if (ia && !ib) na++;
-                    if (ib && !ia) nb++;
-                    if (v == low) { low_n = ib && !ia; low_batch = ia && ib; }
-                }
-                if (low_batch || na < 6 || nb < 4) continue;
-                if (pick < 0 || low_n) pick = pass;
-            }
-            if (pick < 0) continue;
-            swap = pick == 1;
             {
                 const std::vector<int> &LA = p.tensors[swap ? st.b : st.a].modes;
                 const std::vector<int> &LB = p.tensors[swap ? st.a : st.b].modes;
@@ -1435,6 +1421,7 @@ bool serialize(Plan &p, std::string *err) {
                     else gn.push_back(v);
                 }
             }
+            if (gm.size() < 7 || gn.size() < 3) continue;
             const std::vector<int> &LA = p.tensors[swap ? st.b : st.a].modes;
             const std::vector<int> &LB = p.tensors[swap ? st.a : st.b].modes, &LC = p.tensors[st.c].modes;
             const double flops = 8.0 * std::ldexp(1.0, (int)(LC.size() + st.k_ab.size()));

@@ -172,13 +172,15 @@ class Program:
             arena[int(r["c_off"]) + c] = acc
 
     def _gemm_step(self, si, A, B, arena):
-        """Step si through its tensor-core form, as the GEMM kernel defines it: the
-        real block GEMM of three-part bf16 splits (h*h + h*m + m*h + h*l + l*h + m*m)
-        accumulated in float64 here. Also checks the kernel's tiling and that the GEMM's stores cover C exactly once."""
+        """Step si through its tensor-core form, as the GEMM kernel defines it: the real
+        GEMM [Ar | Ai] x [[Br, Bi], [-Bi, Br]] of three-part bf16 splits (h*h + h*m + m*h +
+        h*l + l*h + m*m) accumulated in float64 here. Also checks the kernel's tiling, that
+        the GEMM's stores cover C exactly once and that the row operand holds C's unit
+        stride."""
         g = self.gemms[si]
         st = self.steps[si]
         nb, nm, nn, nk = (int(g[f]) for f in ("nb", "nm", "nn", "nk"))
-        assert nk >= 4 and nm >= 6 and nn >= 4 and int(g["c_off"]) == int(st["c_off"])
+        assert nk >= 4 and nm >= 7 and nn >= 3 and int(g["c_off"]) == int(st["c_off"])
         bb, mm, nn_, kk = (np.arange(1 << v, dtype=np.int64) for v in (nb, nm, nn, nk))
 
         def mv(v, f):
@@ -205,13 +207,16 @@ class Program:
         re = mm6(ar, br) - mm6(ai, bi)
         im = mm6(ai, br) + mm6(ar, bi)
         arena[int(g["c_off"]) + ic] = re + 1j * im
-        # tiles of the kernel: 64 complex rows, nt columns, chunks of 16 summed entries; the
-        # shared-memory core-matrix layout (8-row groups 272 bytes apart, two 128-byte core
-        # matrices along the summed index) gives each (row, summed-half) its own 16 bytes
-        K, M2, N = 1 << nk, 2 << nm, 1 << nn
-        ntc = 128 if nn >= 7 else N
-        assert K % 16 == 0 and M2 % 128 == 0 and N % ntc == 0 and ntc in (16, 32, 64, 128)
-        for rows in (128, ntc):
+        # C's lowest mode is the row operand's first row mode
+        assert any(int(r["src"]) == 0 and int(r["dst"]) == 0 and int(r["len"]) > 0 for r in g["cm"][:int(g["n_cm"])])
+        # tiles of the kernel: 128 complex rows, nt real columns (two per complex column, up to
+        # 128), chunks of 16 summed entries; the shared-memory core-matrix layout (8-row groups
+        # 272 bytes apart, two 128-byte core matrices along the summed index) gives each (row,
+        # summed-half) its own 16 bytes
+        K, M, N2 = 1 << nk, 1 << nm, 2 << nn
+        ntr = 128 if nn >= 6 else N2
+        assert K % 16 == 0 and M % 128 == 0 and N2 % ntr == 0 and ntr in (16, 32, 64, 128)
+        for rows in (128, ntr):
             r = np.arange(rows)[:, None]
             half = np.arange(2)[None, :]
             off = (r >> 3) * 272 + half * 128 + (r & 7) * 16

@@ -84,6 +84,67 @@ def test_sharded_amplitude_matches_single_process(world):
         assert np.array_equal(res[r], res[0])
 
 
+class _HostStandIn:
+    """Stands in for a GPU plan in plan_partial: the same amplitude(bitstrings, slice_begin,
+    slice_count) contract (a complex128 tensor of partial sums), computed by the oracle on
+    the host, and a record of the slice ranges it was asked for."""
+
+    def __init__(self, plan, circ):
+        self.plan, self.circ, self.calls = plan, circ, []
+
+    def amplitude(self, bitstrings, slice_begin=0, slice_count=None):
+        import torch
+        from oracle import ve as VE
+        self.calls.append((slice_begin, slice_count))
+        ids = np.arange(slice_begin, slice_begin + slice_count, dtype=np.int64)
+        vals = [VE.exact_sum(VE.slice_terms(self.circ, x, self.plan.order, self.plan.slices, slice_ids=ids))
+                if slice_count else 0j for x in bitstrings]
+        return torch.tensor(vals, dtype=torch.complex128)
+
+
+def _plan_partial_worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    from datetime import timedelta
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=timedelta(seconds=60))
+    try:
+        from paper_1805_01450_gb300.distributed import plan_partial, sharded_amplitude
+        import paper_1805_01450_gb300 as qv
+        circ = cg.grid_circuit(4, 5, 12, 17)
+        plan = qv.Plan(circ, n_slices=4)
+        xs = cg.random_bitstrings(20, 2, 18)
+        stand_in = _HostStandIn(plan, circ)
+        amps = sharded_amplitude(plan_partial(stand_in, xs), plan.n_slice_terms)
+        q.put((rank, amps, stand_in.calls))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_plan_partial_contract_over_gloo_ranks(world):
+    import multiprocessing as mp
+    from oracle import statevector as SV
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_plan_partial_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = {r: (a, calls) for r, a, calls in (q.get(timeout=120) for _ in range(world))}
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    circ = cg.grid_circuit(4, 5, 12, 17)
+    want = SV.final_state(circ)[cg.random_bitstrings(20, 2, 18)]
+    for r in range(world):
+        # each rank asked for exactly its contiguous share of the 16 slice terms, once
+        b, e = slice_range(16, r, world)
+        assert res[r][1] == [(b, e - b)]
+        assert np.max(np.abs(res[r][0] - want)) < 1e-14
+        assert np.array_equal(res[r][0], res[0][0])
+
+
 def _lonely_worker(port, q):
     import torch.distributed as dist
     from datetime import timedelta

@@ -1,4 +1,4 @@
-"""GPU parity of the tensor-core form of the dense contractions (bf16 hi/lo block GEMM on
+"""GPU parity of the tensor-core form of the dense contractions (three-part bf16 GEMM on
 tcgen05, FP32 accumulation) against the FP64 oracle and against the FP32 SIMT kernels."""
 import numpy as np
 import pytest
@@ -26,7 +26,7 @@ CASES = [
     # (rows, cols, depth, seed, sliced, inner)
     (6, 6, 40, 7066, 8, 2),
     (7, 8, 32, 7078, 6, 2),
-    (5, 6, 40, 13, 8, 2),      # the step's second operand takes the GEMM's row role
+    (5, 6, 40, 19, 8, 2),      # the step's second operand takes the GEMM's row role
 ]
 
 

@@ -232,21 +232,23 @@ def test_register_tiled_forms_7x7x30():
     assert np.max(np.abs(got - ref)) < 1e-6 * 2 ** -24.5
 
 
-@pytest.mark.parametrize("rows,cols,seed,swapped", [(6, 6, 7066, False), (5, 6, 13, True)])
-def test_tensor_core_form_on_host(rows, cols, seed, swapped):
-    # depth 40, 8 sliced variables (2 open): one contraction qualifies for the tensor cores;
-    # its block GEMM of three-part bf16 splits stays within 2^-21 of the exact product and
-    # the slice terms within the amplitude tolerance of the oracle's. On the 5x6 circuit the
-    # step's second operand takes the GEMM's row role (the first has too few output modes of
-    # its own).
+@pytest.mark.parametrize("rows,cols,seed", [(6, 6, 7066), (6, 6, 16)])
+def test_tensor_core_form_on_host(rows, cols, seed):
+    # depth 40, 8 sliced variables (2 open): contractions that qualify for the tensor cores;
+    # their GEMMs of three-part bf16 splits stay within 2^-21 of the exact product and the
+    # slice terms within the amplitude tolerance of the oracle's. The GEMM's row role goes to
+    # the operand that holds the output's lowest mode (the host form checks it): on circuit
+    # 16 one step keeps the operands' order and one swaps them.
     c = cg.grid_circuit(rows, cols, 40, seed)
     n = rows * cols
     p = q.Plan(c, n_slices=8, inner_slices=2, engine="stepwise", tensor_cores=True)
     assert p.info["n_gemm_steps"] >= 1
     prog = Program(p.image())
-    sw = [i for i, g in enumerate(prog.gemms) if int(g["nk"]) > 0 and
-          (int(g["flags"]) & 6, int(g["a_off"])) != (int(prog.steps[i]["flags"]) & 6, int(prog.steps[i]["a_off"]))]
-    assert bool(sw) == swapped
+    gem = [i for i, g in enumerate(prog.gemms) if int(g["nk"]) > 0]
+    sw = [i for i in gem if (int(prog.gemms[i]["flags"]) & 6, int(prog.gemms[i]["a_off"])) !=
+          (int(prog.steps[i]["flags"]) & 6, int(prog.steps[i]["a_off"]))]
+    if seed == 16:
+        assert len(gem) == 2 and len(sw) == 1
     # the first seeded (bitstring, work item) whose slice terms are not all zero (many
     # terms of these circuits cancel exactly)
     x, o = next((x, o) for x in cg.random_bitstrings(n, 64, seed + 1) for o in range(4)
@@ -262,7 +264,7 @@ def test_tensor_core_form_on_host(rows, cols, seed, swapped):
 def test_tensor_core_steps_store_along_their_unit_stride():
     # 8x8x40 (circuit 5001, 64 planning trials): a dense step whose output's lowest mode is
     # held by both operands keeps its SIMT form; every tensor-core step's lowest output mode
-    # is a row or column mode of the GEMM, the column one whenever both roles fit
+    # is a row mode of the GEMM (the row operand holds the output's unit stride)
     c = cg.grid_circuit(8, 8, 40, 5001)
     p = q.Plan(c, n_slices=10, inner_slices=4, engine="stepwise", tensor_cores=True, plan_trials=64,
                mem_budget_bytes=64 << 30)
@@ -282,7 +284,7 @@ def test_tensor_core_steps_store_along_their_unit_stride():
         assert not low_batch
         dsts = lambda f, n: [int(r["dst"]) for r in g[f][:n] if int(r["len"]) > 0]
         assert 0 not in dsts("cb", int(g["n_cb"]))
-        assert 0 in dsts("cm", int(g["n_cm"])) + dsts("cn", int(g["n_cn"]))
+        assert 0 in dsts("cm", int(g["n_cm"]))
     assert kept_simt >= 1 and p.info["n_gemm_steps"] >= 2
 
 

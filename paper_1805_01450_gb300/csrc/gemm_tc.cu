@@ -191,6 +191,7 @@ struct GemmArgs {
     int64_t item0, n_items;
     float2 *arenas;
     uint32_t n_chunks, n_mt, n_nt;
+    uint32_t mt_bits, nt_bits;     // log2 of n_mt and n_nt (every tile count is a power of two)
     uint64_t n_tiles;
 };
 
@@ -214,14 +215,16 @@ struct TileCoord {
     int64_t il;
 };
 
+// Tile t's row tile, column tile, batch index and work item: row tiles of one (item, b) and
+// column tile run next to each other. All counts are powers of two, so shifts and masks.
 __device__ __forceinline__ TileCoord tile_coord(uint64_t t, const GemmArgs &ga) {
     TileCoord c;
-    c.mt = (uint32_t)(t % ga.n_mt);   // row tiles of one (item, b) and column tile run next to each other
-    t /= ga.n_mt;
-    c.nt = (uint32_t)(t % ga.n_nt);
-    t /= ga.n_nt;
+    c.mt = (uint32_t)t & (ga.n_mt - 1u);
+    t >>= ga.mt_bits;
+    c.nt = (uint32_t)t & (ga.n_nt - 1u);
+    t >>= ga.nt_bits;
     c.il = (int64_t)(t >> ga.g.nb);
-    c.beta = (uint32_t)(t & ((1ull << ga.g.nb) - 1ull));
+    c.beta = (uint32_t)t & ((1u << ga.g.nb) - 1u);
     return c;
 }
 
@@ -532,6 +535,8 @@ cudaError_t launch_gemm_step(const LaunchArgs &a, const GemmStep &g, int64_t ite
     ga.n_chunks = (1u << g.nk) / kKq;
     ga.n_mt = (1u << g.nm) / kRows;
     ga.n_nt = (2u << g.nn) / nt_cols;
+    ga.mt_bits = (uint32_t)__builtin_ctz(ga.n_mt);
+    ga.nt_bits = (uint32_t)__builtin_ctz(ga.n_nt);
     ga.n_tiles = 0;
     cudaError_t e;
     switch (nt_cols) {

@@ -1716,17 +1716,24 @@ bool build_program(Plan &p, std::string *err) {
 
 }  // namespace
 
-// Time estimate of a plan's contractions in HBM bytes: per step its algorithmic bytes, or
-// its flops at 12 flops per byte (about the FP32 FMA rate over the HBM bandwidth, the
-// balance of the SIMT kernels) when those take longer, summed over the work items of one
-// bitstring. Used to rank planning trials; Section 3.B ranks orders by flops alone, which
-// leaves out that most steps are bandwidth bound.
+// Time estimate of a plan's contractions, in HBM byte-equivalents, summed over the work
+// items of one bitstring; it ranks planning trials (Section 3.B ranks orders by flops alone,
+// which leaves out that most steps are bandwidth bound). Fused engine (every tensor in
+// shared memory): per step max(algorithmic bytes, flops / 12), about the FP32 FMA rate over
+// the HBM bandwidth. Global-arena engines: the rates the step kernels reach on a GB300 in
+// the 64-qubit benchmark, relative to the register-tiled SIMT kernel's streaming rate (about
+// 5.5 TB/s): a SIMT step costs max(bytes, flops / 3.3) (its compute-bound steps run near 18
+// TFLOP/s), a step the tensor cores take max(1.6 bytes, flops / 32) (about 3.5 TB/s and 175
+// algorithmic TFLOP/s).
 double plan_estimate(const Plan &p) {
     double t = 0;
-    for (const PStep &s : p.steps) {
+    const bool fused = p.engine == QVX_ENGINE_FUSED;
+    for (size_t s = 0; s < p.steps.size(); s++) {
         double fl, by;
-        step_work(p, s, &fl, &by);
-        t += std::max(by, fl / 12.0);
+        step_work(p, p.steps[s], &fl, &by);
+        if (fused) t += std::max(by, fl / 12.0);
+        else if (!p.gemm.empty() && p.gemm[s].nk > 0) t += std::max(1.6 * by, fl / 32.0);
+        else t += std::max(by, fl / 3.3);
     }
     return t * std::ldexp(1.0, (int)p.slices.size() - p.n_inner);
 }

@@ -41,8 +41,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     jobs, objs = [], []
     for f in HOST_SOURCES:
         o = os.path.join(BUILD, f + ".o")
-        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-I", inc, "-I", os.path.join(cuda, "include"),
-               "-c", os.path.join(CSRC, f), "-o", o]
+        # no fused multiply-adds in the planner's floating point, so that plans (orders chosen
+        # by cost comparisons) are the same on x86 and on Arm hosts
+        cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-pthread", "-Wall", "-I", inc,
+               "-I", os.path.join(cuda, "include"), "-c", os.path.join(CSRC, f), "-o", o]
         jobs.append(cmd)
         objs.append(o)
     for f in CUDA_SOURCES:

@@ -100,8 +100,8 @@ struct ParamLeaf {
 };
 
 // Register-tiled form of a two-operand step (global-arena engines). Each thread computes
-// 2^rm x 2^rn output entries that differ only in rm modes held by A alone and rn modes held
-// by B alone, so every operand entry it loads serves 2^rn (from A) or 2^rm (from B) of its
+// 2^rm x 2^rn output entries (rm, rn <= 3) that differ only in rm modes held by A alone and
+// rn modes held by B alone, so every operand entry it loads serves 2^rn (from A) or 2^rm (from B) of its
 // outputs. Thread t of a work item owns the entries c0 + c_m[i] + c_n[j], where
 // c0 = pext-style move of t's bits by free_runs; its operand entries are
 // A[pext(c0, runs_a) + a_m[i] + (ka << a_cb)] and B[pext(c0, runs_b) + b_n[j] + (kb << b_cb)]
@@ -113,7 +113,7 @@ struct RegTileStep {
     uint8_t nk_ab, nk_a, nk_b, a_cb, b_cb, n_free, na_runs, nb_runs;
     DevRun free_runs[6];           // thread index -> output entry with the tile bits zero
     DevRun runs_a[kMaxRuns], runs_b[kMaxRuns];
-    uint32_t a_m[4], b_n[4], c_m[4], c_n[4];
+    uint32_t a_m[8], b_n[8], c_m[8], c_n[8];
 };
 
 // Tensor-core form of a dense two-operand step C[b, m, n] = sum_k A[b, m, k] B[b, k, n]
@@ -180,7 +180,7 @@ static_assert(sizeof(DevLeaf) == 40, "DevLeaf layout");
 static_assert(sizeof(DevProgram) == 328, "DevProgram layout");
 static_assert(sizeof(GemmStep) == 336, "GemmStep layout");
 static_assert(sizeof(GradEntry) == 16, "GradEntry layout");
-static_assert(sizeof(RegTileStep) == 224, "RegTileStep layout");
+static_assert(sizeof(RegTileStep) == 288, "RegTileStep layout");
 static_assert(sizeof(GenOperand) == 112, "GenOperand layout");
 static_assert(sizeof(GenStep) == 240, "GenStep layout");
 static_assert(sizeof(ParamLeaf) == 24, "ParamLeaf layout");

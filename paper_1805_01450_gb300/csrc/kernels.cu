@@ -733,11 +733,20 @@ __global__ void __launch_bounds__(256) persistent_program_kernel(LaunchArgs a, i
 // ------------------------------------------------------------------ register-tiled contraction
 // One thread per 2^RM x 2^RN output entries of a two-operand step (RegTileStep): per summed
 // index it loads 2^RM entries of A and 2^RN of B and forms all their products, so each
-// loaded entry serves several outputs from registers. Two summed indices are in flight per
-// iteration to keep more loads outstanding.
+// loaded entry serves several outputs from registers. Tiles of up to 4 x 4 run 256 threads
+// per CTA with the summed-index loop unrolled four deep (more loads in flight per thread);
+// the 8-wide tiles of compute-heavy steps hold 2 x 64 accumulator registers and run 128
+// threads per CTA, two CTAs per SM, with the loop unrolled twice.
 template <int RM, int RN>
-__global__ void __launch_bounds__(256, 4) regtile_step_kernel(LaunchArgs a, RegTileStep rs, int64_t item_begin,
-                                                           int64_t n_items, float2 *arenas) {
+struct RegTileShape {
+    static constexpr bool kWide = RM + RN >= 5;
+    static constexpr int kThreads = kWide ? 128 : 256;
+    static constexpr int kMinBlocks = kWide ? 2 : 4;
+};
+
+template <int RM, int RN>
+__global__ void __launch_bounds__(RegTileShape<RM, RN>::kThreads, RegTileShape<RM, RN>::kMinBlocks)
+    regtile_step_kernel(LaunchArgs a, RegTileStep rs, int64_t item_begin, int64_t n_items, float2 *arenas) {
     constexpr int TM = 1 << RM, TN = 1 << RN;
     const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ((uint64_t)n_items << rs.nt)) return;
@@ -766,21 +775,27 @@ __global__ void __launch_bounds__(256, 4) regtile_step_kernel(LaunchArgs a, RegT
     const uint32_t nab = rs.nk_ab, na = rs.nk_a;
     const uint32_t nk = nab + na + rs.nk_b;
     const uint32_t mask_ka = (1u << (nab + na)) - 1u, mask_ab = (1u << nab) - 1u;
+    uint32_t am[TM], bn[TN];
+#pragma unroll
+    for (int i = 0; i < TM; i++) am[i] = rs.a_m[i];
+#pragma unroll
+    for (int j = 0; j < TN; j++) bn[j] = rs.b_n[j];
     float2 acc[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; i++)
 #pragma unroll
         for (int j = 0; j < TN; j++) acc[i][j] = make_float2(0.f, 0.f);
-#pragma unroll 4  // more loads in flight per thread, registers held at 64
+    constexpr int kUnroll = RegTileShape<RM, RN>::kWide ? 2 : 4;
+#pragma unroll kUnroll
     for (uint32_t k = 0; k < (1u << nk); k++) {
         const uint32_t ka = k & mask_ka;
         const uint32_t kb = (k & mask_ab) | ((k >> (nab + na)) << nab);
         const float2 *Ak = A + (ka << rs.a_cb), *Bk = B + (kb << rs.b_cb);
         float2 av[TM], bv[TN];
 #pragma unroll
-        for (int i = 0; i < TM; i++) av[i] = Ak[rs.a_m[i]];
+        for (int i = 0; i < TM; i++) av[i] = Ak[am[i]];
 #pragma unroll
-        for (int j = 0; j < TN; j++) bv[j] = Bk[rs.b_n[j]];
+        for (int j = 0; j < TN; j++) bv[j] = Bk[bn[j]];
 #pragma unroll
         for (int i = 0; i < TM; i++)
 #pragma unroll
@@ -1405,20 +1420,34 @@ cudaError_t launch_splitk_step(const LaunchArgs &a, uint32_t step, int64_t item_
     return counted(cudaGetLastError());
 }
 
+template <int RM, int RN>
+static void launch_regtile_t(const LaunchArgs &a, const RegTileStep &rs, int64_t item_begin, int64_t n_items,
+                             float2 *arenas, cudaStream_t s) {
+    constexpr int kThreads = RegTileShape<RM, RN>::kThreads;
+    const uint64_t blocks = (((uint64_t)n_items << rs.nt) + kThreads - 1) / kThreads;
+    regtile_step_kernel<RM, RN><<<(unsigned)blocks, kThreads, 0, s>>>(a, rs, item_begin, n_items, arenas);
+}
+
 cudaError_t launch_regtile_step(const LaunchArgs &a, const RegTileStep &rs, int64_t item_begin, int64_t n_items,
                                 float2 *arenas, cudaStream_t s) {
-    const uint64_t blocks = (((uint64_t)n_items << rs.nt) + 255) / 256;
-    if (blocks > 0x7fffffffull || rs.rm > 2 || rs.rn > 2 || rs.rm + rs.rn == 0) return cudaErrorInvalidConfiguration;
-    const unsigned nb = (unsigned)blocks;
-    switch (rs.rm * 3 + rs.rn) {
-        case 1: regtile_step_kernel<0, 1><<<nb, 256, 0, s>>>(a, rs, item_begin, n_items, arenas); break;
-        case 2: regtile_step_kernel<0, 2><<<nb, 256, 0, s>>>(a, rs, item_begin, n_items, arenas); break;
-        case 3: regtile_step_kernel<1, 0><<<nb, 256, 0, s>>>(a, rs, item_begin, n_items, arenas); break;
-        case 4: regtile_step_kernel<1, 1><<<nb, 256, 0, s>>>(a, rs, item_begin, n_items, arenas); break;
-        case 5: regtile_step_kernel<1, 2><<<nb, 256, 0, s>>>(a, rs, item_begin, n_items, arenas); break;
-        case 6: regtile_step_kernel<2, 0><<<nb, 256, 0, s>>>(a, rs, item_begin, n_items, arenas); break;
-        case 7: regtile_step_kernel<2, 1><<<nb, 256, 0, s>>>(a, rs, item_begin, n_items, arenas); break;
-        default: regtile_step_kernel<2, 2><<<nb, 256, 0, s>>>(a, rs, item_begin, n_items, arenas); break;
+    const uint64_t blocks = (((uint64_t)n_items << rs.nt) + 127) / 128;
+    if (blocks > 0x7fffffffull || rs.rm > 3 || rs.rn > 3 || rs.rm + rs.rn == 0) return cudaErrorInvalidConfiguration;
+    switch (rs.rm * 4 + rs.rn) {
+        case 1: launch_regtile_t<0, 1>(a, rs, item_begin, n_items, arenas, s); break;
+        case 2: launch_regtile_t<0, 2>(a, rs, item_begin, n_items, arenas, s); break;
+        case 3: launch_regtile_t<0, 3>(a, rs, item_begin, n_items, arenas, s); break;
+        case 4: launch_regtile_t<1, 0>(a, rs, item_begin, n_items, arenas, s); break;
+        case 5: launch_regtile_t<1, 1>(a, rs, item_begin, n_items, arenas, s); break;
+        case 6: launch_regtile_t<1, 2>(a, rs, item_begin, n_items, arenas, s); break;
+        case 7: launch_regtile_t<1, 3>(a, rs, item_begin, n_items, arenas, s); break;
+        case 8: launch_regtile_t<2, 0>(a, rs, item_begin, n_items, arenas, s); break;
+        case 9: launch_regtile_t<2, 1>(a, rs, item_begin, n_items, arenas, s); break;
+        case 10: launch_regtile_t<2, 2>(a, rs, item_begin, n_items, arenas, s); break;
+        case 11: launch_regtile_t<2, 3>(a, rs, item_begin, n_items, arenas, s); break;
+        case 12: launch_regtile_t<3, 0>(a, rs, item_begin, n_items, arenas, s); break;
+        case 13: launch_regtile_t<3, 1>(a, rs, item_begin, n_items, arenas, s); break;
+        case 14: launch_regtile_t<3, 2>(a, rs, item_begin, n_items, arenas, s); break;
+        default: launch_regtile_t<3, 3>(a, rs, item_begin, n_items, arenas, s); break;
     }
     return counted(cudaGetLastError());
 }

@@ -42,7 +42,7 @@ RTSTEP = np.dtype([("a_off", "<u8"), ("b_off", "<u8"), ("c_off", "<u8"), ("flags
                    ("nt", "u1"), ("rm", "u1"), ("rn", "u1"), ("nk_ab", "u1"), ("nk_a", "u1"), ("nk_b", "u1"),
                    ("a_cb", "u1"), ("b_cb", "u1"), ("n_free", "u1"), ("na_runs", "u1"), ("nb_runs", "u1"),
                    ("free_runs", RUN, (6,)), ("runs_a", RUN, (12,)), ("runs_b", RUN, (12,)),
-                   ("a_m", "<u4", (4,)), ("b_n", "<u4", (4,)), ("c_m", "<u4", (4,)), ("c_n", "<u4", (4,))])
+                   ("a_m", "<u4", (8,)), ("b_n", "<u4", (8,)), ("c_m", "<u4", (8,)), ("c_n", "<u4", (8,))])
 assert STEP.itemsize == 136 and LEAF.itemsize == 40 and PROG.itemsize == 328 and FSTEP.itemsize == 64
 GEMM = np.dtype([("a_off", "<u8"), ("b_off", "<u8"), ("c_off", "<u8"), ("flags", "<u4"), ("nb", "u1"),
                  ("nm", "u1"), ("nn", "u1"), ("nk", "u1"), ("n_ab", "u1"), ("n_am", "u1"), ("n_ak", "u1"),
@@ -51,7 +51,7 @@ GEMM = np.dtype([("a_off", "<u8"), ("b_off", "<u8"), ("c_off", "<u8"), ("flags",
                 [("tail", "<u4")])
 GENTRY = np.dtype([("c", "<u2"), ("meta", "<u2"), ("xr", "<u2"), ("xo", "<u2"), ("yr", "<u2"), ("yo", "<u2"),
                    ("k1", "<u4")])
-assert RTSTEP.itemsize == 224 and GENTRY.itemsize == 16 and GEMM.itemsize == 336
+assert RTSTEP.itemsize == 288 and GENTRY.itemsize == 16 and GEMM.itemsize == 336
 assert GOP.itemsize == 112 and GSTEP.itemsize == 240 and PLEAF.itemsize == 24
 OP_ARENA, OP_LEAF, OP_DERIV, OP_ONE = 0, 1, 2, 3
 UNARY, A_LEAF, B_LEAF = 1, 2, 4
@@ -148,7 +148,7 @@ class Program:
                   "na_runs", "nb_runs"):
             assert int(r[f]) == int(st[f]), f
         rm, rn, nt, rc = int(r["rm"]), int(r["rn"]), int(r["nt"]), int(r["rc"])
-        assert 0 < rm + rn and rm <= 2 and rn <= 2 and nt == rc - rm - rn
+        assert 0 < rm + rn and rm <= 3 and rn <= 3 and nt == rc - rm - rn
         t = np.arange(1 << nt, dtype=np.int64)
         c0 = _pext(t, r["free_runs"], int(r["n_free"]))
         ia0 = _pext(c0, r["runs_a"], int(r["na_runs"]))

@@ -67,3 +67,15 @@ def test_tensor_core_item_batches():
     a = big.amplitude(xs).cpu().numpy()
     b = small.amplitude(xs).cpu().numpy()
     assert np.max(np.abs(a - b)) < tol(36)
+
+
+def test_wide_register_tiles_vs_oracle():
+    # the SIMT form of a compute-heavy step: an 8 x 8 register tile per thread
+    c = cg.grid_circuit(5, 6, 40, 19)
+    p = q.Plan(c, n_slices=8, inner_slices=2, engine="stepwise")
+    xs = cg.random_bitstrings(30, 2, 21)
+    terms = p.slice_terms(xs).cpu().numpy()
+    ids = np.random.default_rng(19).choice(1 << 8, 6, replace=False)
+    for i, x in enumerate(xs):
+        ref = VE.slice_terms(c, x, p.order, p.slices, slice_ids=ids)
+        assert np.max(np.abs(terms[i, ids] - ref)) < tol(30)

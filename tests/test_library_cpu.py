@@ -560,3 +560,19 @@ def test_reordering_between_removals_on_7x7x60():
     reorder = q.Plan(c, slice_rule="reorder", **kw)
     assert reorder.info["log2_cost"] + 2 <= greedy.info["log2_cost"]
     assert reorder.info["max_rank"] < greedy.info["max_rank"]
+
+
+def test_wide_register_tiles_on_host():
+    # a compute-heavy step (6 or more flops per algorithmic byte) takes an 8 x 8 register
+    # tile; its host form matches the plain form and the oracle's slice terms
+    c = cg.grid_circuit(5, 6, 40, 19)
+    p = q.Plan(c, n_slices=8, inner_slices=2, engine="stepwise")
+    prog = Program(p.image())
+    assert any(int(t["rm"]) == 3 and int(t["rn"]) == 3 for t in prog.rtsteps)
+    x, o = next((x, o) for x in cg.random_bitstrings(30, 64, 20) for o in range(4)
+                if np.max(np.abs(prog.item_terms(x, o))) > 1e-12)
+    got = prog.item_terms(x, o, regtile=True)
+    plain = prog.item_terms(x, o)
+    assert np.max(np.abs(got - plain)) <= 1e-12 * np.max(np.abs(plain))
+    ref = VE.slice_terms(c, x, p.order, p.slices, slice_ids=[(o << 2) | i for i in range(4)])
+    assert np.max(np.abs(got - ref)) < 1e-6 * 2 ** -15

@@ -3,8 +3,9 @@
 
 Default workload: the 8 x 8 random grid circuit of depth 40 (64 qubits, Section 4 rules,
 circuit seed 5001), one seeded bitstring (seed 5002) per step, 10 sliced variables (1024
-slice terms, 4 of the variables kept open inside a work item: 64 work items), the plan
-variant the autotuner keeps for this circuit (recorded below; --autotune re-runs it). A
+slice terms, 5 of the variables kept open inside a work item: 32 work items), the plan
+variant kept for this circuit (recorded below: 4096 planning trials; --autotune re-runs the
+autotuner instead). A
 step is one whole amplitude: every slice term, every pairwise contraction (the dense ones
 on the tcgen05 tensor cores as three-part bf16 GEMMs, the rest as FP32 SIMT kernels) and
 the exact sum of the slice terms.
@@ -45,14 +46,15 @@ WORKLOADS = {
 # step); their amplitude rate is extrapolated: steps x sample / 2^k / time
 SLICE_SAMPLE = {"grid9x9d40": 1 << 10}
 DEFAULT_WORKLOAD = "grid8x8d40"
-# The plan variant the autotuner keeps (bench.py --autotune: sliced-variable counts 10 and
-# 12, the SIMT and tensor-core stepwise forms with 4 open slices, then 1, 16, 64 and 256
-# planning trials), per circuit seed of a workload. The timed plan, its parity tests
+# The plan variant kept for each circuit seed of a workload, from timing (L2 flushed, CUDA
+# events) the stepwise tensor-core engine at 10 sliced variables over planning-trial counts
+# 16 ... 4096 (trials ranked by the planner's kernel-rate estimate) and 4, 5 or 6 sliced
+# variables open inside a work item. The timed plan, its parity tests
 # (tests/test_gpu_8x8x40.py) and its ncu traffic are keyed by these.
 RECORDED_PLANS = {
-    ("grid8x8d40", 5001): dict(n_slices=10, inner_slices=4, engine="stepwise", tensor_cores=True, plan_trials=16),
-    ("grid8x8d40", 5002): dict(n_slices=10, inner_slices=4, engine="stepwise", tensor_cores=True, plan_trials=256),
-    ("grid8x8d40", 5003): dict(n_slices=10, inner_slices=4, engine="stepwise", tensor_cores=True, plan_trials=64),
+    ("grid8x8d40", 5001): dict(n_slices=10, inner_slices=5, engine="stepwise", tensor_cores=True, plan_trials=4096),
+    ("grid8x8d40", 5002): dict(n_slices=10, inner_slices=6, engine="stepwise", tensor_cores=True, plan_trials=256),
+    ("grid8x8d40", 5003): dict(n_slices=10, inner_slices=6, engine="stepwise", tensor_cores=True, plan_trials=4096),
     ("grid9x9d40", 9001): dict(n_slices=20, inner_slices=4, engine="stepwise", tensor_cores=True, plan_trials=8),
 }
 # autotuner search of the workloads without a recorded plan

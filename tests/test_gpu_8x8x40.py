@@ -1,11 +1,11 @@
 """GPU parity at the full size of the 8x8 grid circuit of depth 40 (64 qubits, 525 path
-variables, 10 sliced of which 4 stay open inside a work item, tensors up to rank 27), for
-the three seeded circuits the benchmark reports, each with exactly the plan the benchmark
-times (bench.RECORDED_PLANS: the stepwise engine with the dense contractions on the tensor
-cores, and the planning-trial count the autotuner kept).
+variables, 10 sliced of which 5 or 6 stay open inside a work item, tensors up to rank 28),
+for the three seeded circuits the benchmark reports, each with exactly the plan the
+benchmark times (bench.RECORDED_PLANS: the stepwise engine with the dense contractions on
+the tensor cores, and the planning-trial count kept by timing).
 
 Pass condition (the random-phase reading of the amplitude tolerance on sampled slices):
-every slice term of a seeded work item (16 terms) is compared element by element with the
+16 seeded slice terms of a seeded work item are compared element by element with the
 FP64 oracle, and sqrt(2^k) * rms |d beta| <= 1e-5 * 2^{-N/2}, which bounds the error of the
 whole amplitude when the terms' errors have random phases. Each term is also held to a
 relative error of 1e-4 (the three-part bf16 split leaves about 2^-23 per product). The
@@ -44,14 +44,17 @@ def case(request):
 
 def test_8x8x40_timed_plan_slice_terms_vs_oracle(case):
     seed, c, x, p = case
-    assert p.info["n_gemm_steps"] >= 1 and p.info["max_rank"] >= 24 and p.info["n_inner"] == 4
+    assert p.info["n_gemm_steps"] >= 1 and p.info["max_rank"] >= 24
+    per = 1 << p.info["n_inner"]                                   # slice terms per work item
     rng = np.random.default_rng(seed)
-    o = int(rng.integers(0, p.info["n_items_per_bitstring"]))   # work item o: slices 16 o ... 16 o + 15
-    ids = list(range(16 * o, 16 * o + 16))
-    got = p.slice_terms([x], slice_begin=ids[0], slice_count=16).cpu().numpy()[0]
+    o = int(rng.integers(0, p.info["n_items_per_bitstring"]))   # work item o: slices per*o ... per*o + per - 1
+    ids = list(range(per * o, per * o + per))
+    got = p.slice_terms([x], slice_begin=ids[0], slice_count=per).cpu().numpy()[0]
     p.check_status(p._ws_for(1, torch.device("cuda")))
-    ref = VE.slice_terms(c, x, p.order, p.slices, slice_ids=ids, threads=min(16, os.cpu_count() or 1))
-    d = np.abs(got - ref)
+    local = sorted(int(i) for i in rng.choice(per, min(per, 16), replace=False))
+    ref = VE.slice_terms(c, x, p.order, p.slices, slice_ids=[ids[i] for i in local],
+                         threads=min(16, os.cpu_count() or 1))
+    d = np.abs(got[local] - ref)
     assert math.sqrt(p.n_slice_terms) * math.sqrt(np.mean(d * d)) <= TOL
     assert np.max(d) <= 1e-4 * np.max(np.abs(ref))
 
@@ -59,7 +62,8 @@ def test_8x8x40_timed_plan_slice_terms_vs_oracle(case):
 def test_8x8x40_timed_plan_amplitude_tensor_cores_vs_simt(case):
     # a consistency check of the two device forms of the same plan (not the parity bar)
     seed, c, x, p = case
-    simt = q.Plan(c, order=p.order, slices=p.slices, inner_slices=4, engine="stepwise", mem_budget_bytes=BUDGET)
+    simt = q.Plan(c, order=p.order, slices=p.slices, inner_slices=p.info["n_inner"], engine="stepwise",
+                  mem_budget_bytes=BUDGET)
     assert simt.info["n_gemm_steps"] == 0
     a = p.amplitude([x]).cpu().numpy()
     b = simt.amplitude([x]).cpu().numpy()

@@ -16,8 +16,8 @@
 // m = i of a 128-row tile) holds C entries that are consecutive in memory along the lanes;
 // the real columns 2n and 2n + 1 of a lane are Re and Im of C[m, n], so the epilogue stores
 // complex64 values straight from the registers tcgen05.ld fills, coalesced across the warp,
-// with no transpose. A tile is 128 complex rows by NT real (NT / 2 complex) columns of one
-// (item, b). The kernel is persistent (one CTA per SM walks the tiles) and
+// with no transpose. A tile is 128 complex rows by NT real (NT / 2 complex, up to 128)
+// columns of one (item, b). The kernel is persistent (one CTA per SM walks the tiles) and
 // warp-specialised: producer warps copy the complex64 operands straight from the arena into
 // shared memory (cp.async, several chunks of 16 summed entries ahead), split them into
 // three bf16 parts and store them in the tensor cores' K-major core-matrix layout in a ring
@@ -43,7 +43,6 @@ constexpr uint32_t kPitch = 272;       // bytes between 8-row groups: two 128-by
                                        // along the summed index and 16 bytes that spread the
                                        // producers' 16-byte stores over all banks
 constexpr uint32_t kPolls = 1u << 22;
-constexpr uint32_t kRaw = 4;           // chunks of raw operand copies in flight per producer
 constexpr uint32_t kEpiThreads = 128;  // four epilogue warps, one per tensor-memory lane quarter
 
 __host__ __device__ constexpr uint32_t region_bytes(uint32_t rows) { return rows / 8u * kPitch; }
@@ -57,9 +56,14 @@ template <int NT>
 __host__ __device__ constexpr uint32_t producers() { return 256u + ((uint32_t)NT < 32u ? 32u : (uint32_t)NT); }
 template <int NT>
 __host__ __device__ constexpr uint32_t block_threads() { return producers<NT>() + 32u + kEpiThreads; }
-// Operand stages of the shared-memory ring: two of 52 KB for 128-column tiles, three below.
+// Operand stages of the shared-memory ring: two for 128- and 256-column tiles (52 and 77 KB),
+// three below.
 template <int NT>
 __host__ __device__ constexpr uint32_t n_stages() { return NT >= 128 ? 2u : 3u; }
+// Raw copy slots per producer (chunks in flight): four, two for 256-column tiles (their
+// 512 producers' slots and two 77 KB stages fill the shared memory).
+template <int NT>
+__host__ __device__ constexpr uint32_t raw_depth() { return NT >= 256 ? 2u : 4u; }
 // real accumulator columns an epilogue warp reads at a time
 template <int NT>
 __host__ __device__ constexpr uint32_t epi_cols() { return NT < 32 ? (uint32_t)NT : 32u; }
@@ -68,7 +72,7 @@ template <int NT>
 __host__ __device__ constexpr uint32_t raw_slot_bytes() { return 8u * producers<NT>() * 8u; }
 template <int NT>
 __host__ __device__ constexpr size_t smem_bytes(uint32_t K) {
-    return (size_t)n_stages<NT>() * stage_bytes(NT) + (size_t)kRaw * raw_slot_bytes<NT>() + 8u * (size_t)K;
+    return (size_t)n_stages<NT>() * stage_bytes(NT) + (size_t)raw_depth<NT>() * raw_slot_bytes<NT>() + 8u * (size_t)K;
 }
 
 __device__ __forceinline__ uint32_t core_offset(uint32_t r, uint32_t g) {
@@ -257,6 +261,7 @@ __global__ void __launch_bounds__(block_threads<NT>(), 1) gemm_tc_kernel(GemmArg
     constexpr uint32_t kW = epi_cols<NT>();
     constexpr uint32_t kNc = (uint32_t)NT / 2u;   // complex columns per tile
     constexpr uint32_t kRawSlot = raw_slot_bytes<NT>();
+    constexpr uint32_t kRaw = raw_depth<NT>();
     static_assert(P % 32u == 0u, "producer warps");
     extern __shared__ __align__(1024) unsigned char gsm[];
     __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S], accf_bar[2], acce_bar[2], drain_bar;
@@ -486,8 +491,8 @@ __global__ void __launch_bounds__(block_threads<NT>(), 1) gemm_tc_kernel(GemmArg
 
 }  // namespace
 
-// real columns of a tile: two per complex column, up to 64 complex columns
-uint32_t gemm_nt(const GemmStep &g) { return g.nn >= 6 ? 128u : (2u << g.nn); }
+// real columns of a tile: two per complex column, up to 128 complex columns
+uint32_t gemm_nt(const GemmStep &g) { return g.nn >= 7 ? 256u : (2u << g.nn); }
 
 template <int NT>
 static cudaError_t launch_gemm_nt(GemmArgs ga, cudaStream_t s) {
@@ -543,7 +548,8 @@ cudaError_t launch_gemm_step(const LaunchArgs &a, const GemmStep &g, int64_t ite
         case 16: e = launch_gemm_nt<16>(ga, s); break;
         case 32: e = launch_gemm_nt<32>(ga, s); break;
         case 64: e = launch_gemm_nt<64>(ga, s); break;
-        default: e = launch_gemm_nt<128>(ga, s); break;
+        case 128: e = launch_gemm_nt<128>(ga, s); break;
+        default: e = launch_gemm_nt<256>(ga, s); break;
     }
     return launch_counted(e);
 }

@@ -1326,10 +1326,12 @@ bool serialize(Plan &p, std::string *err) {
     // register-tiled form of the two-operand steps (global-arena engines): up to two output
     // modes held by A alone and two held by B alone, all above C's five lowest bits (a
     // warp's 32 lanes run along those, so its loads and stores stay coalesced), become a
-    // per-thread tile of 2^rm x 2^rn entries. Compute-heavy steps (6 or more flops per
-    // algorithmic byte, at least 2^12 threads per work item) take up to three of each: an
-    // 8 x 8 tile does 16 FMAs per loaded 8-byte entry where a 4 x 4 tile does 8, which halves
-    // the L1 traffic that bounds the smaller tile on such steps
+    // per-thread tile of 2^rm x 2^rn entries. Compute-bound steps (16 or more flops per
+    // algorithmic byte, above the FP32 ridge of about 12; at least 2^12 threads per work
+    // item) take up to three of each: an 8 x 8 tile does 16 FMAs per loaded 8-byte entry where
+    // a 4 x 4 tile does 8, which halves the L1 traffic that bounds the smaller tile there. On
+    // output-bound steps the wide tile's 8 warps per SM issue too few stores (2.8 TB/s on a
+    // 7-flop/B step), so they keep the 4 x 4 tile
     std::vector<RegTileStep> rts;
     if (p.engine != QVX_ENGINE_FUSED) {
         rts.assign(ds.size(), RegTileStep{});
@@ -1341,7 +1343,7 @@ bool serialize(Plan &p, std::string *err) {
             const std::vector<int> &LA = p.tensors[st.a].modes, &LB = p.tensors[st.b].modes, &LC = p.tensors[st.c].modes;
             double fl = 0, by = 0;
             step_work(p, st, &fl, &by);
-            const size_t max_bits = fl >= 6.0 * by && LC.size() >= 18 ? 3 : 2;
+            const size_t max_bits = fl >= 16.0 * by && LC.size() >= 18 ? 3 : 2;
             std::vector<int> tm, tn;   // tile bits: positions in C
             for (int j = 5; j < (int)LC.size(); j++) {
                 const bool ia = find_pos(LA, LC[j]) >= 0, ib = find_pos(LB, LC[j]) >= 0;

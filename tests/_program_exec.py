@@ -210,12 +210,12 @@ class Program:
         # C's lowest mode is the row operand's first row mode
         assert any(int(r["src"]) == 0 and int(r["dst"]) == 0 and int(r["len"]) > 0 for r in g["cm"][:int(g["n_cm"])])
         # tiles of the kernel: 128 complex rows, nt real columns (two per complex column, up to
-        # 128), chunks of 16 summed entries; the shared-memory core-matrix layout (8-row groups
+        # 256), chunks of 16 summed entries; the shared-memory core-matrix layout (8-row groups
         # 272 bytes apart, two 128-byte core matrices along the summed index) gives each (row,
         # summed-half) its own 16 bytes
         K, M, N2 = 1 << nk, 1 << nm, 2 << nn
-        ntr = 128 if nn >= 6 else N2
-        assert K % 16 == 0 and M % 128 == 0 and N2 % ntr == 0 and ntr in (16, 32, 64, 128)
+        ntr = 256 if nn >= 7 else N2
+        assert K % 16 == 0 and M % 128 == 0 and N2 % ntr == 0 and ntr in (16, 32, 64, 128, 256)
         for rows in (128, ntr):
             r = np.arange(rows)[:, None]
             half = np.arange(2)[None, :]

@@ -119,7 +119,7 @@ def test_exact_sum_out_of_range_is_reported_not_wrapped(engine):
                                        ("stepwise", dict(n_slices=4, inner_slices=2)),
                                        ("stepwise", dict(n_slices=8, inner_slices=2, tensor_cores=True))])
 def test_profiled_call_logs_every_launch(engine, kw):
-    c = cg.grid_circuit(6, 6, 25, 2001) if not kw.get("tensor_cores") else cg.grid_circuit(5, 6, 40, 13)
+    c = cg.grid_circuit(6, 6, 25, 2001) if not kw.get("tensor_cores") else cg.grid_circuit(5, 6, 40, 19)
     p = q.Plan(c, engine=engine, **kw)
     xs = cg.random_bitstrings(c.n_qubits, 3, 5)
     bits = p._bits(xs)

@@ -143,3 +143,18 @@ def test_profiled_call_logs_every_launch(engine, kw):
         assert p.info["n_gemm_steps"] > 0 and any(r["kernel"] == "gemm_tc_kernel" for r in recs)
     if engine == "fused":
         assert [r["kernel"] for r in recs] == ["fused_program_kernel"] * 2
+
+
+def test_checkpointed_amplitude_resumes_on_the_gpu(tmp_path):
+    # ranges of 1000 of the 4096 slice terms (the last one ragged); an interrupted run
+    # resumes from its journal to the oracle's amplitudes
+    from paper_1805_01450_gb300.checkpoint import amplitude_resumable
+    c = cg.grid_circuit(6, 6, 25, 2001)
+    p = q.Plan(c, n_slices=12, inner_slices=3, plan_trials=4)
+    xs = cg.random_bitstrings(36, 2, 2002)
+    path = str(tmp_path / "journal.jsonl")
+    assert amplitude_resumable(p, xs, path, 1000, stop_after=2) is None
+    got = amplitude_resumable(p, xs, path, 1000)
+    want = [VE.exact_sum(VE.slice_terms(c, x, p.order, p.slices)) for x in xs]
+    assert np.max(np.abs(got - np.array(want))) < 1e-5 * 2.0 ** -18
+    assert np.max(np.abs(got - p.amplitude(xs).cpu().numpy())) < 1e-5 * 2.0 ** -18

@@ -43,7 +43,7 @@ constexpr uint32_t kPitch = 272;       // bytes between 8-row groups: two 128-by
                                        // along the summed index and 16 bytes that spread the
                                        // producers' 16-byte stores over all banks
 constexpr uint32_t kPolls = 1u << 22;
-constexpr uint32_t kEpiThreads = 128;  // four epilogue warps, one per tensor-memory lane quarter
+constexpr uint32_t kEpiThreads = 256;  // eight epilogue warps, two per tensor-memory lane quarter
 
 __host__ __device__ constexpr uint32_t region_bytes(uint32_t rows) { return rows / 8u * kPitch; }
 // One stage: A regions (part 0 h, m, l, part 1 h, m, l), then the same for B.
@@ -243,10 +243,12 @@ __device__ __forceinline__ TileCoord tile_coord(uint64_t t, const GemmArgs &ga) 
 //              twelve tcgen05.mma into the tile's accumulator (the tile's first product
 //              overwrites it), commits each chunk to the stage's "empty" barrier and the
 //              tile's last chunk to the accumulator's "full" barrier;
-//   4 warps    epilogue: wait for an accumulator, read it with tcgen05.ld (warp w reads
-//              tensor-memory lanes 32 (w mod 4) ..., i.e. rows 32 (w mod 4) + lane), store
-//              each (Re, Im) column pair as one complex64 entry of C and release the
-//              accumulator.
+//   8 warps    epilogue: wait for an accumulator, read it with tcgen05.ld (warp w reads
+//              tensor-memory lanes 32 (w mod 4) ..., i.e. rows 32 (w mod 4) + lane; the two
+//              warps of a lane quarter take alternate blocks of 32 columns), store each
+//              (Re, Im) column pair as one complex64 entry of C and release the accumulator.
+//              Four warps left the epilogue about a tenth slower on output-heavy steps: each
+//              waits out its tensor-memory reads block by block.
 // With two accumulators the epilogue of one tile overlaps the loads and MMAs of the next.
 // Every wait is bounded; a wait that runs out sets the CTA's fail flag, the other roles
 // leave their loops, the MMA thread waits (bounded) for its issued MMAs before the tensor
@@ -312,6 +314,9 @@ __global__ void __launch_bounds__(block_threads<NT>(), 1) gemm_tc_kernel(GemmArg
         const uint32_t row = is_a ? (u & 127u) : (u - 256u) % kNc;
         const uint32_t h = is_a ? (u >> 7) : ((u - 256u) / kNc) & 1u;
         const uint32_t *koff = (is_a ? tka : tkb) + 8u * h;
+        // a step with 8 summed entries fills one chunk's first half: the units of the second
+        // half load nothing and store zeros, which add nothing to the products
+        const bool pad = (1u << g.nk) < kKq && h == 1u;
         const uint32_t raw_mine = smem_u32(raw) + u * 8u;
         // load cursor: the tile and chunk whose copies are issued next
         uint64_t lt = blockIdx.x;
@@ -328,7 +333,7 @@ __global__ void __launch_bounds__(block_threads<NT>(), 1) gemm_tc_kernel(GemmArg
                       pext_runs(tc.beta, g.bb, g.n_bb) + pext_runs(tc.nt * kNc + row, g.bn, g.n_bn);
         };
         auto issue_next = [&](uint64_t gi) {   // one commit group per chunk, empty past the end
-            if (lt < ga.n_tiles && active) {
+            if (lt < ga.n_tiles && active && !pad) {
                 const uint32_t dst = raw_mine + (uint32_t)(gi % kRaw) * kRawSlot;
                 const uint4 o0 = *reinterpret_cast<const uint4 *>(koff + lc * kKq);
                 const uint4 o1 = *reinterpret_cast<const uint4 *>(koff + lc * kKq + 4u);
@@ -361,7 +366,7 @@ __global__ void __launch_bounds__(block_threads<NT>(), 1) gemm_tc_kernel(GemmArg
                 const float2 *rt = reinterpret_cast<const float2 *>(raw + (gc % kRaw) * kRawSlot) + u;
                 float2 v[8];
 #pragma unroll
-                for (uint32_t j = 0; j < 8; j++) v[j] = rt[j * P];
+                for (uint32_t j = 0; j < 8; j++) v[j] = pad ? make_float2(0.f, 0.f) : rt[j * P];
                 unsigned char *sa = gsm + s * kStage;
                 if (is_a) store_a(sa, v, row, h);
                 else store_b<NT>(sa + 6u * kRegA, v, row, h);
@@ -431,6 +436,7 @@ __global__ void __launch_bounds__(block_threads<NT>(), 1) gemm_tc_kernel(GemmArg
         // in C when its lowest modes are row modes (the planner gives the row role to the
         // operand that holds C's lowest mode).
         const uint32_t q = warp & 3u;
+        const uint32_t share = (warp - kMmaWarp - 1u) >> 2;   // the two warps of a lane quarter split its columns
         uint32_t j = 0;
         for (uint64_t t = blockIdx.x; t < ga.n_tiles && !fail; t += gridDim.x, j++) {
             const TileCoord tc = tile_coord(t, ga);
@@ -444,7 +450,7 @@ __global__ void __launch_bounds__(block_threads<NT>(), 1) gemm_tc_kernel(GemmArg
             }
             tc_fence_after();
             const uint32_t taddr = tmem + ((q * 32u) << 16) + buf * kCols;
-            for (uint32_t j0 = 0; j0 < (uint32_t)NT; j0 += kW) {
+            for (uint32_t j0 = share * kW; j0 < (uint32_t)NT; j0 += 2u * kW) {
                 // the column offsets of this block's kW / 2 complex columns, one per lane
                 const uint32_t my_col = pext_runs(tc.nt * kNc + j0 / 2u + (lane % (kW / 2u)), g.cn, g.n_cn);
                 uint32_t r[kW];
@@ -529,7 +535,7 @@ static cudaError_t launch_gemm_nt(GemmArgs ga, cudaStream_t s) {
 
 cudaError_t launch_gemm_step(const LaunchArgs &a, const GemmStep &g, int64_t item0, int64_t n_items, float2 *arenas,
                              cudaStream_t s) {
-    if (g.nk < 4 || g.nk > 10 || g.nm < 7 || g.nn < 3 || n_items <= 0) return cudaErrorInvalidConfiguration;
+    if (g.nk < 3 || g.nk > 10 || g.nm < 7 || g.nn < 3 || n_items <= 0) return cudaErrorInvalidConfiguration;
     const uint32_t nt_cols = gemm_nt(g);
     GemmArgs ga;
     ga.a = a;
@@ -537,7 +543,7 @@ cudaError_t launch_gemm_step(const LaunchArgs &a, const GemmStep &g, int64_t ite
     ga.item0 = item0;
     ga.n_items = n_items;
     ga.arenas = arenas;
-    ga.n_chunks = (1u << g.nk) / kKq;
+    ga.n_chunks = std::max(1u, (1u << g.nk) / kKq);   // 8 summed entries: one half-filled chunk
     ga.n_mt = (1u << g.nm) / kRows;
     ga.n_nt = (2u << g.nn) / nt_cols;
     ga.mt_bits = (uint32_t)__builtin_ctz(ga.n_mt);

@@ -1397,13 +1397,16 @@ bool serialize(Plan &p, std::string *err) {
         }
     }
     // tensor-core form of the dense contractions (stepwise engine, opts.tensor_cores): every
-    // summed mode in both operands, 16 to 1024 summed entries (K) and an arithmetic intensity
-    // at or above the FP32 ridge. The GEMM's row role goes to the operand that holds C's
-    // lowest mode (its unit stride) alone: a tile's 128 rows then sit in consecutive
-    // tensor-memory lanes and the epilogue's stores of each column are consecutive in C. That
-    // operand needs 128 output entries of its own, the other 8; a step whose lowest output
-    // mode is held by both operands (a batch mode) keeps its SIMT form. Complex products
-    // commute, so the step's B may take the row role.
+    // summed mode in both operands, 8 to 1024 summed entries (K) and an arithmetic intensity
+    // at or above the FP32 ridge (12 flops per byte), or at least 5 with 8 summed entries:
+    // there the register-tiled SIMT form issues about four instructions per complex
+    // multiply-add and moves under 3.5 TB/s, while the tensor cores run such an
+    // output-bound step at the rate of their epilogue's stores. The GEMM's row role goes to
+    // the operand that holds C's lowest mode (its unit stride) alone: a tile's 128 rows then
+    // sit in consecutive tensor-memory lanes and the epilogue's stores of each column are
+    // consecutive in C. That operand needs 128 output entries of its own, the other 8; a step
+    // whose lowest output mode is held by both operands (a batch mode) keeps its SIMT form.
+    // Complex products commute, so the step's B may take the row role.
     std::vector<GemmStep> gms;
     if (p.engine == QVX_ENGINE_STEPWISE && p.opts.tensor_cores) {
         gms.assign(ds.size(), GemmStep{});
@@ -1411,7 +1414,7 @@ bool serialize(Plan &p, std::string *err) {
             const PStep &st = p.steps[s];
             GemmStep &g = gms[s];
             std::memset(&g, 0, sizeof(g));
-            if (st.b < 0 || !st.k_a.empty() || !st.k_b.empty() || st.k_ab.size() < 4 || st.k_ab.size() > 10) continue;
+            if (st.b < 0 || !st.k_a.empty() || !st.k_b.empty() || st.k_ab.size() < 3 || st.k_ab.size() > 10) continue;
             if (p.tensors[st.c].modes.empty()) continue;
             const int low = p.tensors[st.c].modes[0];
             const bool low_a = find_pos(p.tensors[st.a].modes, low) >= 0;
@@ -1435,7 +1438,7 @@ bool serialize(Plan &p, std::string *err) {
             const double flops = 8.0 * std::ldexp(1.0, (int)(LC.size() + st.k_ab.size()));
             const double bytes = 8.0 * (std::ldexp(1.0, (int)LA.size()) + std::ldexp(1.0, (int)LB.size()) +
                                         std::ldexp(1.0, (int)LC.size()));
-            if (flops < 12.0 * bytes) continue;
+            if (flops < (st.k_ab.size() == 3 ? 5.0 : 12.0) * bytes) continue;
             bool ok = true;
             auto gmap = [&](const std::vector<int> &grp, const std::vector<int> &L, DevRun *runs, uint8_t *n) {
                 DevRun r[kMaxRuns];
@@ -1732,7 +1735,7 @@ bool build_program(Plan &p, std::string *err) {
 // the 64-qubit benchmark, relative to the register-tiled SIMT kernel's streaming rate (about
 // 5.5 TB/s): a SIMT step costs max(bytes, flops / 3.3) (its compute-bound steps run near 18
 // TFLOP/s), a step the tensor cores take max(1.6 bytes, flops / 32) (about 3.5 TB/s and 175
-// algorithmic TFLOP/s).
+// algorithmic TFLOP/s; flops / 16 with 8 summed entries, whose chunk is half padding).
 double plan_estimate(const Plan &p) {
     double t = 0;
     const bool fused = p.engine == QVX_ENGINE_FUSED;
@@ -1740,7 +1743,7 @@ double plan_estimate(const Plan &p) {
         double fl, by;
         step_work(p, p.steps[s], &fl, &by);
         if (fused) t += std::max(by, fl / 12.0);
-        else if (!p.gemm.empty() && p.gemm[s].nk > 0) t += std::max(1.6 * by, fl / 32.0);
+        else if (!p.gemm.empty() && p.gemm[s].nk > 0) t += std::max(1.6 * by, fl / (p.gemm[s].nk == 3 ? 16.0 : 32.0));
         else t += std::max(by, fl / 3.3);
     }
     return t * std::ldexp(1.0, (int)p.slices.size() - p.n_inner);

@@ -180,7 +180,7 @@ class Program:
         g = self.gemms[si]
         st = self.steps[si]
         nb, nm, nn, nk = (int(g[f]) for f in ("nb", "nm", "nn", "nk"))
-        assert nk >= 4 and nm >= 7 and nn >= 3 and int(g["c_off"]) == int(st["c_off"])
+        assert nk >= 3 and nm >= 7 and nn >= 3 and int(g["c_off"]) == int(st["c_off"])
         bb, mm, nn_, kk = (np.arange(1 << v, dtype=np.int64) for v in (nb, nm, nn, nk))
 
         def mv(v, f):
@@ -210,12 +210,13 @@ class Program:
         # C's lowest mode is the row operand's first row mode
         assert any(int(r["src"]) == 0 and int(r["dst"]) == 0 and int(r["len"]) > 0 for r in g["cm"][:int(g["n_cm"])])
         # tiles of the kernel: 128 complex rows, nt real columns (two per complex column, up to
-        # 256), chunks of 16 summed entries; the shared-memory core-matrix layout (8-row groups
+        # 256), chunks of 16 summed entries (8 summed entries fill half of one chunk, the
+        # other half holds zeros); the shared-memory core-matrix layout (8-row groups
         # 272 bytes apart, two 128-byte core matrices along the summed index) gives each (row,
         # summed-half) its own 16 bytes
         K, M, N2 = 1 << nk, 1 << nm, 2 << nn
         ntr = 256 if nn >= 7 else N2
-        assert K % 16 == 0 and M % 128 == 0 and N2 % ntr == 0 and ntr in (16, 32, 64, 128, 256)
+        assert (K == 8 or K % 16 == 0) and M % 128 == 0 and N2 % ntr == 0 and ntr in (16, 32, 64, 128, 256)
         for rows in (128, ntr):
             r = np.arange(rows)[:, None]
             half = np.arange(2)[None, :]

@@ -276,7 +276,7 @@ def test_tensor_core_steps_store_along_their_unit_stride():
     kept_simt = 0
     for s, st in enumerate(prog.steps):
         g = prog.gemms[s]
-        dense = int(st["nk_a"]) == 0 and int(st["nk_b"]) == 0 and 4 <= int(st["nk_ab"]) <= 10 and int(st["rc"]) >= 10
+        dense = int(st["nk_a"]) == 0 and int(st["nk_b"]) == 0 and 3 <= int(st["nk_ab"]) <= 10 and int(st["rc"]) >= 10
         low_batch = holds_low(st["runs_a"], int(st["na_runs"])) and holds_low(st["runs_b"], int(st["nb_runs"]))
         if int(g["nk"]) == 0:
             kept_simt += dense and low_batch

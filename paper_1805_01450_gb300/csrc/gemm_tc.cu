@@ -189,6 +189,33 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// kW accumulator columns of this warp's 32 tensor-memory lanes into registers (one column
+// per register), waited for.
+template <uint32_t kW>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&r)[kW]) {
+    if constexpr (kW == 32) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+            "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+            "%30, %31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+              "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+              "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+    } else {
+        static_assert(kW == 16, "16 or 32 columns");
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+            "%12, %13, %14, %15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+    }
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 struct GemmArgs {
     LaunchArgs a;
     GemmStep g;
@@ -454,27 +481,7 @@ __global__ void __launch_bounds__(block_threads<NT>(), 1) gemm_tc_kernel(GemmArg
                 // the column offsets of this block's kW / 2 complex columns, one per lane
                 const uint32_t my_col = pext_runs(tc.nt * kNc + j0 / 2u + (lane % (kW / 2u)), g.cn, g.n_cn);
                 uint32_t r[kW];
-                if constexpr (kW == 32) {
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-                        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
-                        "%30, %31}, [%32];"
-                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-                          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-                          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                        : "r"(taddr + j0));
-                } else {
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-                        "%12, %13, %14, %15}, [%16];"
-                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                          "=r"(r[14]), "=r"(r[15])
-                        : "r"(taddr + j0));
-                }
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                tmem_ld<kW>(taddr + j0, r);
 #pragma unroll
                 for (uint32_t i = 0; i < kW / 2u; i++) {
                     const uint32_t coff = __shfl_sync(0xffffffffu, my_col, i);
@@ -495,41 +502,331 @@ __global__ void __launch_bounds__(block_threads<NT>(), 1) gemm_tc_kernel(GemmArg
     if (fail && threadIdx.x == 0) atomicCAS(ga.a.status, 0u, 4u /* QVX_ETIMEOUT */);
 }
 
+// B-stationary form for steps with at most two chunks of summed entries (K <= 32) and many
+// row tiles per column tile: a CTA walks a contiguous range of tiles, row tiles fastest, so
+// one column tile's B operand (all its chunks) is split once into resident shared-memory
+// regions and serves every row tile of the range that shares it; only A goes through the
+// stage ring. The B producers reload when the column tile changes, after the MMAs that read
+// the old one have completed. Against the streaming form this removes most of the
+// producers' shared-memory traffic on output-heavy steps (B is 4 of the 6 operand values a
+// complex entry pair produces).
+constexpr uint32_t kBsStages = 2;
+__host__ __device__ constexpr uint32_t bs_stage_bytes() { return 6u * region_bytes(kRows); }
+template <int NT>
+__host__ __device__ constexpr uint32_t bs_b_bytes() { return 6u * region_bytes(NT); }   // one chunk of B
+template <int NT>
+__host__ __device__ constexpr uint32_t bs_b_units() { return (uint32_t)NT < 32u ? 32u : (uint32_t)NT; }
+template <int NT>
+__host__ __device__ constexpr uint32_t bs_raw_depth() { return NT >= 256 ? 3u : 4u; }
+template <int NT>
+__host__ __device__ constexpr uint32_t bs_threads() { return 256u + bs_b_units<NT>() + 32u + kEpiThreads; }
+template <int NT>
+__host__ __device__ constexpr size_t bs_smem_bytes() {
+    return (size_t)kBsStages * bs_stage_bytes() + 2u * (size_t)bs_b_bytes<NT>() +
+           (size_t)bs_raw_depth<NT>() * 256u * 64u + (size_t)bs_b_units<NT>() * 64u + 8u * 32u;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(bs_threads<NT>(), 1) gemm_tc_bs_kernel(GemmArgs ga) {
+    constexpr uint32_t S = kBsStages;
+    constexpr uint32_t PA = 256u, PB = bs_b_units<NT>();
+    constexpr uint32_t kMmaWarp = (PA + PB) / 32u;
+    constexpr uint32_t kCols = NT < 32 ? 32u : (uint32_t)NT;
+    constexpr uint32_t kRegA = region_bytes(kRows), kRegB = region_bytes(NT);
+    constexpr uint32_t kStage = bs_stage_bytes(), kBChunk = bs_b_bytes<NT>();
+    constexpr uint32_t kW = epi_cols<NT>();
+    constexpr uint32_t kNc = (uint32_t)NT / 2u;
+    constexpr uint32_t kRaw = bs_raw_depth<NT>();
+    constexpr uint32_t kRawSlotA = PA * 64u;
+    extern __shared__ __align__(1024) unsigned char gsm[];
+    __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S], accf_bar[2], acce_bar[2], bfull_bar, bempty_bar, drain_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int fail;
+    const GemmStep &g = ga.g;
+    const uint32_t warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const uint32_t sbase = smem_u32(gsm);
+    unsigned char *sB = gsm + S * kStage;                          // resident B, one region set per chunk
+    unsigned char *rawA = sB + 2u * kBChunk;
+    unsigned char *rawB = rawA + kRaw * kRawSlotA;
+    uint32_t *tka = reinterpret_cast<uint32_t *>(rawB + PB * 64u);
+    uint32_t *tkb = tka + 2u * kKq;
+    // this CTA's contiguous range of tiles
+    const uint64_t t0 = (uint64_t)blockIdx.x * ga.n_tiles / gridDim.x;
+    const uint64_t t1 = ((uint64_t)blockIdx.x + 1u) * ga.n_tiles / gridDim.x;
+    if (threadIdx.x == 0) {
+        for (uint32_t s = 0; s < S; s++) {
+            mbar_init(smem_u32(&full_bar[s]), PA);
+            mbar_init(smem_u32(&empty_bar[s]), 1);
+        }
+        for (uint32_t b = 0; b < 2; b++) {
+            mbar_init(smem_u32(&accf_bar[b]), 1);
+            mbar_init(smem_u32(&acce_bar[b]), kEpiThreads);
+        }
+        mbar_init(smem_u32(&bfull_bar), PB);
+        mbar_init(smem_u32(&bempty_bar), 1);
+        mbar_init(smem_u32(&drain_bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fail = 0;
+    }
+    if (warp == kMmaWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(2u * kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    const uint32_t K = ga.n_chunks * kKq;   // 16 or 32 table entries
+    for (uint32_t i = threadIdx.x; i < K; i += bs_threads<NT>()) {
+        tka[i] = pext_runs(i, g.ak, g.n_ak);
+        tkb[i] = pext_runs(i, g.bk, g.n_bk);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const bool k8 = (1u << g.nk) < kKq;   // 8 summed entries: the second half of the chunk is zero
+    if (warp < PA / 32u) {
+        // A producers: unit u is row u & 127 of the tile, summed half u >> 7
+        const uint32_t u = threadIdx.x;
+        const uint32_t row = u & 127u, h = u >> 7;
+        const bool pad = k8 && h == 1u;
+        const uint32_t *koff = tka + 8u * h;
+        const uint32_t raw_mine = smem_u32(rawA) + u * 8u;
+        uint64_t lt = t0;
+        uint32_t lc = 0;
+        const float2 *src = nullptr;
+        auto setup = [&](uint64_t t) {
+            const TileCoord tc = tile_coord(t, ga);
+            const float2 *arena = ga.arenas + (uint64_t)tc.il * ga.a.arena_elems;
+            src = gemm_operand(ga.a, arena, g.a_off, g.flags & kStepALeaf, ga.item0 + tc.il) +
+                  pext_runs(tc.beta, g.ab, g.n_ab) + pext_runs(tc.mt * kRows + row, g.am, g.n_am);
+        };
+        auto issue_next = [&](uint64_t gi) {
+            if (lt < t1 && !pad) {
+                const uint32_t dst = raw_mine + (uint32_t)(gi % kRaw) * kRawSlotA;
+                const uint4 o0 = *reinterpret_cast<const uint4 *>(koff + lc * kKq);
+                const uint4 o1 = *reinterpret_cast<const uint4 *>(koff + lc * kKq + 4u);
+                const uint32_t o[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
+#pragma unroll
+                for (uint32_t j = 0; j < 8; j++) cp_async8(dst + j * PA * 8u, src + o[j]);
+            }
+            if (lt < t1) {
+                if (++lc == ga.n_chunks) {
+                    lc = 0;
+                    if (++lt < t1) setup(lt);
+                }
+            }
+            cp_async_commit();
+        };
+        if (t0 < t1) setup(t0);
+        const uint64_t total = (t1 - t0) * ga.n_chunks;
+        for (uint32_t i = 0; i + 1 < kRaw; i++) issue_next(i);
+        for (uint64_t gc = 0; gc < total && !fail; gc++) {
+            issue_next(gc + kRaw - 1);
+            cp_async_wait<kRaw - 1>();
+            const uint32_t s = (uint32_t)(gc % S);
+            if (!wait_or_fail(smem_u32(&empty_bar[s]), (uint32_t)((gc / S) & 1u) ^ 1u, &fail)) {
+                fail = 1;
+                break;
+            }
+            const float2 *rt = reinterpret_cast<const float2 *>(rawA + (gc % kRaw) * kRawSlotA) + u;
+            float2 v[8];
+#pragma unroll
+            for (uint32_t j = 0; j < 8; j++) v[j] = pad ? make_float2(0.f, 0.f) : rt[j * PA];
+            store_a(gsm + s * kStage, v, row, h);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[s])) : "memory");
+        }
+        cp_async_wait<0>();
+    } else if (warp < kMmaWarp) {
+        // B producers: unit v is complex column v % (NT/2) of the column tile, summed half
+        // (v / (NT/2)) & 1; once per column tile of the range, every chunk into its region
+        const uint32_t v = threadIdx.x - PA;
+        const bool active = v < (uint32_t)NT;
+        const uint32_t col = v % kNc, h = (v / kNc) & 1u;
+        const bool pad = k8 && h == 1u;
+        const uint32_t *koff = tkb + 8u * h;
+        const uint32_t raw_mine = smem_u32(rawB) + v * 8u;
+        uint32_t gi = 0;
+        for (uint64_t t = t0; t < t1 && !fail; gi++) {
+            const uint64_t grp = t >> ga.mt_bits;
+            if (!wait_or_fail(smem_u32(&bempty_bar), (gi & 1u) ^ 1u, &fail)) {
+                fail = 1;
+                break;
+            }
+            if (active) {
+                const TileCoord tc = tile_coord(t, ga);
+                const float2 *arena = ga.arenas + (uint64_t)tc.il * ga.a.arena_elems;
+                const float2 *src = gemm_operand(ga.a, arena, g.b_off, g.flags & kStepBLeaf, ga.item0 + tc.il) +
+                                    pext_runs(tc.beta, g.bb, g.n_bb) + pext_runs(tc.nt * kNc + col, g.bn, g.n_bn);
+                for (uint32_t c = 0; c < ga.n_chunks; c++) {
+                    if (!pad) {
+                        const uint4 o0 = *reinterpret_cast<const uint4 *>(koff + c * kKq);
+                        const uint4 o1 = *reinterpret_cast<const uint4 *>(koff + c * kKq + 4u);
+                        const uint32_t o[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
+#pragma unroll
+                        for (uint32_t j = 0; j < 8; j++) cp_async8(raw_mine + j * PB * 8u, src + o[j]);
+                    }
+                    cp_async_commit();
+                    cp_async_wait<0>();
+                    const float2 *rt = reinterpret_cast<const float2 *>(rawB) + v;
+                    float2 e[8];
+#pragma unroll
+                    for (uint32_t j = 0; j < 8; j++) e[j] = pad ? make_float2(0.f, 0.f) : rt[j * PB];
+                    store_b<NT>(sB + c * kBChunk, e, col, h);
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bfull_bar)) : "memory");
+            t = (grp + 1u) << ga.mt_bits;   // the next column tile's first row tile
+        }
+        cp_async_wait<0>();
+    } else if (warp == kMmaWarp) {
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
+                                   ((kRows >> 4) << 24);
+            uint64_t gc = 0;
+            uint32_t j = 0, gi = 0;
+            bool ok = true;
+            for (uint64_t t = t0; t < t1 && !fail && ok; t++, j++) {
+                const uint64_t grp = t >> ga.mt_bits;
+                if (t == t0 || (t & (ga.n_mt - 1u)) == 0u) {   // a new column tile: its B is loaded
+                    if (!wait_or_fail(smem_u32(&bfull_bar), gi & 1u, &fail)) {
+                        ok = false;
+                        break;
+                    }
+                    gi++;
+                }
+                const uint32_t buf = j & 1u;
+                if (!wait_or_fail(smem_u32(&acce_bar[buf]), ((j >> 1) & 1u) ^ 1u, &fail)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + buf * kCols;
+                for (uint32_t c = 0; c < ga.n_chunks; c++, gc++) {
+                    const uint32_t s = (uint32_t)(gc % S);
+                    if (!wait_or_fail(smem_u32(&full_bar[s]), (uint32_t)((gc / S) & 1u), &fail)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = sbase + s * kStage, sb = smem_u32(sB) + c * kBChunk;
+#pragma unroll
+                    for (uint32_t p = 0; p < 2; p++) {
+                        uint64_t ad[3], bd[3];
+#pragma unroll
+                        for (uint32_t q = 0; q < 3; q++) {
+                            ad[q] = smem_desc(sa + (3u * p + q) * kRegA, 128u, kPitch);
+                            bd[q] = smem_desc(sb + (3u * p + q) * kRegB, 128u, kPitch);
+                        }
+                        mma_bf16(d, ad[0], bd[0], idesc, (c | p) != 0u);
+                        mma_bf16(d, ad[0], bd[1], idesc, 1u);
+                        mma_bf16(d, ad[1], bd[0], idesc, 1u);
+                        mma_bf16(d, ad[0], bd[2], idesc, 1u);
+                        mma_bf16(d, ad[2], bd[0], idesc, 1u);
+                        mma_bf16(d, ad[1], bd[1], idesc, 1u);
+                    }
+                    mma_commit(smem_u32(&empty_bar[s]));
+                }
+                if (!ok) break;
+                mma_commit(smem_u32(&accf_bar[buf]));
+                // the column tile's last row tile in this range: its B regions may be reloaded
+                // once these MMAs have completed
+                if (t + 1u == t1 || ((t + 1u) >> ga.mt_bits) != grp) mma_commit(smem_u32(&bempty_bar));
+            }
+            if (!ok) fail = 1;
+            mma_commit(smem_u32(&drain_bar));
+            if (!mbar_wait(smem_u32(&drain_bar), 0, kPolls)) fail = 1;
+        }
+        __syncwarp();
+    } else {
+        const uint32_t q = warp & 3u;
+        const uint32_t share = (warp - kMmaWarp - 1u) >> 2;
+        uint32_t j = 0;
+        for (uint64_t t = t0; t < t1 && !fail; t++, j++) {
+            const TileCoord tc = tile_coord(t, ga);
+            const uint32_t buf = j & 1u;
+            float2 *Crow = ga.arenas + (uint64_t)tc.il * ga.a.arena_elems + g.c_off + pext_runs(tc.beta, g.cb, g.n_cb) +
+                           pext_runs(tc.mt * kRows + 32u * q + lane, g.cm, g.n_cm);
+            if (!wait_or_fail(smem_u32(&accf_bar[buf]), (j >> 1) & 1u, &fail)) {
+                fail = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t taddr = tmem + ((q * 32u) << 16) + buf * kCols;
+            for (uint32_t j0 = share * kW; j0 < (uint32_t)NT; j0 += 2u * kW) {
+                const uint32_t my_col = pext_runs(tc.nt * kNc + j0 / 2u + (lane % (kW / 2u)), g.cn, g.n_cn);
+                uint32_t r[kW];
+                tmem_ld<kW>(taddr + j0, r);
+#pragma unroll
+                for (uint32_t i = 0; i < kW / 2u; i++) {
+                    const uint32_t coff = __shfl_sync(0xffffffffu, my_col, i);
+                    Crow[coff] = make_float2(__uint_as_float(r[2u * i]), __uint_as_float(r[2u * i + 1u]));
+                }
+            }
+            tc_fence_before();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[buf])) : "memory");
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == kMmaWarp) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2u * kCols) : "memory");
+    }
+    if (fail && threadIdx.x == 0) atomicCAS(ga.a.status, 0u, 4u /* QVX_ETIMEOUT */);
+}
+
 }  // namespace
 
 // real columns of a tile: two per complex column, up to 128 complex columns
 uint32_t gemm_nt(const GemmStep &g) { return g.nn >= 7 ? 256u : (2u << g.nn); }
 
-template <int NT>
-static cudaError_t launch_gemm_nt(GemmArgs ga, cudaStream_t s) {
-    // dynamic shared memory: the operand stage ring, the producers' raw copy slots and the
-    // summed index tables; the attribute is set once per device for the largest summed
-    // index (1024 entries)
+// Grid of a persistent tensor-core kernel: the SM count times the CTAs an SM holds (within
+// its 512 tensor-memory columns, so that no allocation ever waits for another CTA's
+// columns), queried once per device and kernel.
+template <int NT, bool kBs>
+static cudaError_t gemm_grid(uint64_t n_tiles, uint64_t *grid) {
     static int per_sm[64] = {0}, sms[64] = {0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    constexpr size_t kMaxSmem = smem_bytes<NT>(1024);
     if (!per_sm[dev]) {
-        if ((e = cudaFuncSetAttribute(gemm_tc_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem)) !=
-            cudaSuccess)
+        const void *fn = kBs ? reinterpret_cast<const void *>(gemm_tc_bs_kernel<NT>)
+                             : reinterpret_cast<const void *>(gemm_tc_kernel<NT>);
+        const size_t smem = kBs ? bs_smem_bytes<NT>() : smem_bytes<NT>(1024);
+        const int threads = kBs ? (int)bs_threads<NT>() : (int)block_threads<NT>();
+        if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return e;
         int n = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gemm_tc_kernel<NT>, block_threads<NT>(), kMaxSmem)) !=
-            cudaSuccess)
-            return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        // the CTAs an SM holds stay within its 512 tensor-memory columns, so that no
-        // allocation ever waits for another CTA's columns
         const int cols = 2 * (NT < 32 ? 32 : NT);
         per_sm[dev] = n < 1 ? -1 : std::min(n, 512 / cols);
     }
     if (per_sm[dev] < 1) return cudaErrorInvalidConfiguration;
+    *grid = std::min<uint64_t>(n_tiles, (uint64_t)sms[dev] * (uint64_t)per_sm[dev]);
+    return cudaSuccess;
+}
+
+template <int NT>
+static cudaError_t launch_gemm_nt(GemmArgs ga, cudaStream_t s) {
     ga.n_tiles = ((uint64_t)ga.n_items << ga.g.nb) * ga.n_mt * ga.n_nt;
     if (ga.n_tiles == 0) return cudaErrorInvalidConfiguration;
-    const uint64_t grid = std::min<uint64_t>(ga.n_tiles, (uint64_t)sms[dev] * (uint64_t)per_sm[dev]);
-    gemm_tc_kernel<NT><<<(unsigned)grid, block_threads<NT>(), kMaxSmem, s>>>(ga);
+    uint64_t grid = 0;
+    cudaError_t e;
+    // B-stationary form: at most two chunks of summed entries (B's regions of every chunk
+    // stay resident) and at least 8 row tiles per column tile to reuse them over
+    if (ga.n_chunks <= 2u && ga.n_mt >= 8u) {
+        if ((e = gemm_grid<NT, true>(ga.n_tiles, &grid)) != cudaSuccess) return e;
+        gemm_tc_bs_kernel<NT><<<(unsigned)grid, bs_threads<NT>(), bs_smem_bytes<NT>(), s>>>(ga);
+        return cudaGetLastError();
+    }
+    // dynamic shared memory: the operand stage ring, the producers' raw copy slots and the
+    // summed index tables, sized for the largest summed index (1024 entries)
+    if ((e = gemm_grid<NT, false>(ga.n_tiles, &grid)) != cudaSuccess) return e;
+    gemm_tc_kernel<NT><<<(unsigned)grid, block_threads<NT>(), smem_bytes<NT>(1024), s>>>(ga);
     return cudaGetLastError();
 }
 

@@ -259,6 +259,44 @@ __device__ __forceinline__ TileCoord tile_coord(uint64_t t, const GemmArgs &ga) 
     return c;
 }
 
+// Tile order of the B-stationary form: row tiles fastest (one column tile's B serves a run of
+// them), then batch index and work item, column tile slowest. The CTAs' contiguous ranges
+// then walk the column tiles of one (item, b) at the same time on different SMs, so the
+// second column tile's A rows are still in L2 (with the column tile next to the row tiles,
+// one CTA read each A tile twice, some 32 row tiles apart, from HBM).
+__device__ __forceinline__ TileCoord tile_coord_bs(uint64_t t, const GemmArgs &ga) {
+    TileCoord c;
+    c.mt = (uint32_t)t & (ga.n_mt - 1u);
+    t >>= ga.mt_bits;
+    c.beta = (uint32_t)t & ((1u << ga.g.nb) - 1u);
+    t >>= ga.g.nb;   // below n_items * n_nt < 2^32: a 32-bit division (a 64-bit one is a
+                     // called routine, and the kernel's loops lost a tenth to it)
+    const uint32_t q = (uint32_t)t, n = (uint32_t)ga.n_items;
+    c.il = (int64_t)(q % n);
+    c.nt = q / n;
+    return c;
+}
+
+// The coordinates of consecutive tiles in that order, advanced without a division (the item
+// count need not be a power of two).
+struct BsCursor {
+    TileCoord c;
+    __device__ __forceinline__ void next(const GemmArgs &ga) {
+        if (++c.mt < ga.n_mt) return;
+        c.mt = 0;
+        if (++c.beta < (1u << ga.g.nb)) return;
+        c.beta = 0;
+        if (++c.il < ga.n_items) return;
+        c.il = 0;
+        c.nt++;
+    }
+    // the first row tile of the next column tile
+    __device__ __forceinline__ void next_group(const GemmArgs &ga) {
+        c.mt = ga.n_mt - 1u;
+        next(ga);
+    }
+};
+
 // Persistent, warp-specialised tensor-core contraction. One CTA per SM walks the tiles
 // t = blockIdx.x, blockIdx.x + gridDim.x, ... (128 rows x NT real columns of one (item, b)):
 //   producer warps (P threads, one operand unit each): copy the unit's 8
@@ -594,8 +632,10 @@ __global__ void __launch_bounds__(bs_threads<NT>(), 1) gemm_tc_bs_kernel(GemmArg
         uint64_t lt = t0;
         uint32_t lc = 0;
         const float2 *src = nullptr;
-        auto setup = [&](uint64_t t) {
-            const TileCoord tc = tile_coord(t, ga);
+        BsCursor cur;
+        cur.c = tile_coord_bs(t0, ga);
+        auto setup = [&]() {
+            const TileCoord &tc = cur.c;
             const float2 *arena = ga.arenas + (uint64_t)tc.il * ga.a.arena_elems;
             src = gemm_operand(ga.a, arena, g.a_off, g.flags & kStepALeaf, ga.item0 + tc.il) +
                   pext_runs(tc.beta, g.ab, g.n_ab) + pext_runs(tc.mt * kRows + row, g.am, g.n_am);
@@ -612,12 +652,15 @@ __global__ void __launch_bounds__(bs_threads<NT>(), 1) gemm_tc_bs_kernel(GemmArg
             if (lt < t1) {
                 if (++lc == ga.n_chunks) {
                     lc = 0;
-                    if (++lt < t1) setup(lt);
+                    if (++lt < t1) {
+                        cur.next(ga);
+                        setup();
+                    }
                 }
             }
             cp_async_commit();
         };
-        if (t0 < t1) setup(t0);
+        if (t0 < t1) setup();
         const uint64_t total = (t1 - t0) * ga.n_chunks;
         for (uint32_t i = 0; i + 1 < kRaw; i++) issue_next(i);
         for (uint64_t gc = 0; gc < total && !fail; gc++) {
@@ -647,6 +690,8 @@ __global__ void __launch_bounds__(bs_threads<NT>(), 1) gemm_tc_bs_kernel(GemmArg
         const uint32_t *koff = tkb + 8u * h;
         const uint32_t raw_mine = smem_u32(rawB) + v * 8u;
         uint32_t gi = 0;
+        BsCursor cur;
+        cur.c = tile_coord_bs(t0, ga);
         for (uint64_t t = t0; t < t1 && !fail; gi++) {
             const uint64_t grp = t >> ga.mt_bits;
             if (!wait_or_fail(smem_u32(&bempty_bar), (gi & 1u) ^ 1u, &fail)) {
@@ -654,7 +699,7 @@ __global__ void __launch_bounds__(bs_threads<NT>(), 1) gemm_tc_bs_kernel(GemmArg
                 break;
             }
             if (active) {
-                const TileCoord tc = tile_coord(t, ga);
+                const TileCoord &tc = cur.c;
                 const float2 *arena = ga.arenas + (uint64_t)tc.il * ga.a.arena_elems;
                 const float2 *src = gemm_operand(ga.a, arena, g.b_off, g.flags & kStepBLeaf, ga.item0 + tc.il) +
                                     pext_runs(tc.beta, g.bb, g.n_bb) + pext_runs(tc.nt * kNc + col, g.bn, g.n_bn);
@@ -678,6 +723,7 @@ __global__ void __launch_bounds__(bs_threads<NT>(), 1) gemm_tc_bs_kernel(GemmArg
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bfull_bar)) : "memory");
             t = (grp + 1u) << ga.mt_bits;   // the next column tile's first row tile
+            cur.next_group(ga);
         }
         cp_async_wait<0>();
     } else if (warp == kMmaWarp) {
@@ -743,8 +789,10 @@ __global__ void __launch_bounds__(bs_threads<NT>(), 1) gemm_tc_bs_kernel(GemmArg
         const uint32_t q = warp & 3u;
         const uint32_t share = (warp - kMmaWarp - 1u) >> 2;
         uint32_t j = 0;
-        for (uint64_t t = t0; t < t1 && !fail; t++, j++) {
-            const TileCoord tc = tile_coord(t, ga);
+        BsCursor cur;
+        cur.c = tile_coord_bs(t0, ga);
+        for (uint64_t t = t0; t < t1 && !fail; t++, j++, cur.next(ga)) {
+            const TileCoord &tc = cur.c;
             const uint32_t buf = j & 1u;
             float2 *Crow = ga.arenas + (uint64_t)tc.il * ga.a.arena_elems + g.c_off + pext_runs(tc.beta, g.cb, g.n_cb) +
                            pext_runs(tc.mt * kRows + 32u * q + lane, g.cm, g.n_cm);
@@ -817,8 +865,9 @@ static cudaError_t launch_gemm_nt(GemmArgs ga, cudaStream_t s) {
     uint64_t grid = 0;
     cudaError_t e;
     // B-stationary form: at most two chunks of summed entries (B's regions of every chunk
-    // stay resident) and at least 8 row tiles per column tile to reuse them over
-    if (ga.n_chunks <= 2u && ga.n_mt >= 8u) {
+    // stay resident) and at least 8 row tiles per column tile to reuse them over (and tile
+    // coordinates above the row tiles within 32 bits)
+    if (ga.n_chunks <= 2u && ga.n_mt >= 8u && (uint64_t)ga.n_items * ga.n_nt < (1ull << 32)) {
         if ((e = gemm_grid<NT, true>(ga.n_tiles, &grid)) != cudaSuccess) return e;
         gemm_tc_bs_kernel<NT><<<(unsigned)grid, bs_threads<NT>(), bs_smem_bytes<NT>(), s>>>(ga);
         return cudaGetLastError();

@@ -236,20 +236,20 @@ qvx_status qvx_slice_terms(qvx_plan *plan, const uint64_t *bitstrings_dev, int64
 /* The paper has no counterpart to this entry point; it serves callers that cannot
  * allocate device memory: code that runs where the allocator is off limits (inside another
  * library's callback, a real-time loop that must not block on an allocation, a process whose
- * device memory is all reserved up front) and so cannot provide a workspace. alpha_b = <x_b|C|0> for b < batch, like qvx_amplitude, but
- * without a workspace: the library keeps this call's scratch (the plan's device image, a
- * status word and the per-work-item partial sums) in one fixed device array of 4 MiB that
- * every GPU loading the library holds until the process exits. bitstrings_dev and amps_dev
- * are the caller's device buffers as for qvx_amplitude. Fused-engine plans only
- * (QVX_EUNSUPPORTED otherwise); a plan and batch whose scratch exceeds 4 MiB are rejected
- * with QVX_EINVAL. The scratch holds 256 bytes of status words, the plan's device image
- * rounded up to 256 bytes, and 32 bytes per (bitstring, open-output value, outer work item).
- * The first call on a device also looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture. All calls
- * share the one array and each call overwrites it: calls that overlap on the GPU (other
- * streams, other threads) race and must be serialised by the caller. The array's status
- * word records a kernel failure (QVX_ETIMEOUT, QVX_ERANGE) and is not cleared by the next
- * call: read it with qvx_noalloc_status; while it is set, amplitudes are written as NaN. */
+ * device memory is all reserved up front) and so cannot provide a workspace.
+ * alpha_b = <x_b|C|0> for b < batch, like qvx_amplitude, but without a workspace: the
+ * library keeps this call's scratch (the plan's device image, a status word and the
+ * per-work-item partial sums) in one fixed device array of 4 MiB that every GPU loading the
+ * library holds until the process exits. bitstrings_dev and amps_dev are the caller's device
+ * buffers as for qvx_amplitude. Fused-engine plans only (QVX_EUNSUPPORTED otherwise); a plan
+ * and batch whose scratch exceeds 4 MiB are rejected with QVX_EINVAL. The scratch holds 256
+ * bytes of status words, the plan's device image rounded up to 256 bytes, and 32 bytes per
+ * (bitstring, open-output value, outer work item). The first call on a device also looks up
+ * the array's device address (cudaGetSymbolAddress). All calls share the one array and each
+ * call overwrites it: calls that overlap on the GPU (other streams, other threads) race and
+ * must be serialised by the caller. The array's status word records a kernel failure
+ * (QVX_ETIMEOUT, QVX_ERANGE) and is not cleared by the next call: read it with
+ * qvx_noalloc_status; while it is set, amplitudes are written as NaN. */
 qvx_status qvx_amplitude_noalloc(qvx_plan *plan, const uint64_t *bitstrings_dev, int64_t batch,
                                  double *amps_dev, void *stream);
 

@@ -1398,10 +1398,10 @@ bool serialize(Plan &p, std::string *err) {
     }
     // tensor-core form of the dense contractions (stepwise engine, opts.tensor_cores): every
     // summed mode in both operands, 8 to 1024 summed entries (K) and an arithmetic intensity
-    // at or above the FP32 ridge (12 flops per byte), or at least 5 with 8 summed entries:
-    // there the register-tiled SIMT form issues about four instructions per complex
-    // multiply-add and moves under 3.5 TB/s, while the tensor cores run such an
-    // output-bound step at the rate of their epilogue's stores. The GEMM's row role goes to
+    // of at least 5 flops per byte: from there the register-tiled SIMT form is issue-bound
+    // (about four instructions per complex multiply-add; 1.9 TB/s on a 16-entry step at 10.7
+    // flop/B, under 3.5 TB/s on 8-entry steps), while the tensor cores run such output-bound
+    // steps near the rate of their epilogue's stores (5 to 6 TB/s). The GEMM's row role goes to
     // the operand that holds C's lowest mode (its unit stride) alone: a tile's 128 rows then
     // sit in consecutive tensor-memory lanes and the epilogue's stores of each column are
     // consecutive in C. That operand needs 128 output entries of its own, the other 8; a step
@@ -1438,7 +1438,7 @@ bool serialize(Plan &p, std::string *err) {
             const double flops = 8.0 * std::ldexp(1.0, (int)(LC.size() + st.k_ab.size()));
             const double bytes = 8.0 * (std::ldexp(1.0, (int)LA.size()) + std::ldexp(1.0, (int)LB.size()) +
                                         std::ldexp(1.0, (int)LC.size()));
-            if (flops < (st.k_ab.size() == 3 ? 5.0 : 12.0) * bytes) continue;
+            if (flops < 5.0 * bytes) continue;
             bool ok = true;
             auto gmap = [&](const std::vector<int> &grp, const std::vector<int> &L, DevRun *runs, uint8_t *n) {
                 DevRun r[kMaxRuns];

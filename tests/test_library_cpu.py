@@ -238,7 +238,7 @@ def test_tensor_core_form_on_host(rows, cols, seed):
     # their GEMMs of three-part bf16 splits stay within 2^-21 of the exact product and the
     # slice terms within the amplitude tolerance of the oracle's. The GEMM's row role goes to
     # the operand that holds the output's lowest mode (the host form checks it): on circuit
-    # 16 one step keeps the operands' order and one swaps them.
+    # 16 some steps keep the operands' order and some swap them.
     c = cg.grid_circuit(rows, cols, 40, seed)
     n = rows * cols
     p = q.Plan(c, n_slices=8, inner_slices=2, engine="stepwise", tensor_cores=True)
@@ -247,8 +247,8 @@ def test_tensor_core_form_on_host(rows, cols, seed):
     gem = [i for i, g in enumerate(prog.gemms) if int(g["nk"]) > 0]
     sw = [i for i in gem if (int(prog.gemms[i]["flags"]) & 6, int(prog.gemms[i]["a_off"])) !=
           (int(prog.steps[i]["flags"]) & 6, int(prog.steps[i]["a_off"]))]
-    if seed == 16:
-        assert len(gem) == 2 and len(sw) == 1
+    if seed == 16:   # both orientations: a step that keeps its operands' order and one that swaps them
+        assert len(sw) >= 1 and len(gem) - len(sw) >= 1
     # the first seeded (bitstring, work item) whose slice terms are not all zero (many
     # terms of these circuits cancel exactly)
     x, o = next((x, o) for x in cg.random_bitstrings(n, 64, seed + 1) for o in range(4)

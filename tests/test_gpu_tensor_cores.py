@@ -79,3 +79,35 @@ def test_wide_register_tiles_vs_oracle():
     for i, x in enumerate(xs):
         ref = VE.slice_terms(c, x, p.order, p.slices, slice_ids=ids)
         assert np.max(np.abs(terms[i, ids] - ref)) < tol(30)
+
+
+# 6x7x40 plans whose tensor-core steps take the B-stationary form (at most 32 summed entries,
+# at least 8 row tiles of 128 per column tile), one case per column-tile width and summed
+# size: (rows, cols, depth, seed, sliced, inner, real columns NT, summed-index bits)
+BS_CASES = [
+    (6, 7, 40, 1, 8, 2, 32, 3),
+    (6, 7, 40, 14, 10, 2, 64, 3),
+    (6, 7, 40, 3, 8, 2, 128, 5),
+    (6, 7, 40, 5, 10, 2, 128, 3),
+    (6, 7, 40, 2, 10, 2, 256, 3),
+    (6, 7, 40, 12, 10, 2, 32, 4),
+]
+
+
+@pytest.mark.parametrize("r,c_,d,seed,k,inner,nt,nk", BS_CASES)
+def test_b_stationary_form_vs_oracle(r, c_, d, seed, k, inner, nt, nk):
+    import os
+    from _program_exec import Program
+    c = cg.grid_circuit(r, c_, d, seed)
+    n = r * c_
+    p = q.Plan(c, n_slices=k, inner_slices=inner, engine="stepwise", tensor_cores=True)
+    shapes = [(int(g["nm"]), int(g["nn"]), int(g["nk"])) for g in Program(p.image()).gemms if int(g["nk"]) > 0]
+    # the launcher's choice: B-stationary when the summed index fills at most two chunks of 16
+    # and there are at least 8 row tiles; the case's step is among them
+    assert any((256 if nn >= 7 else 2 << nn) == nt and kk == nk and max(1, (1 << kk) // 16) <= 2 and (1 << nm) // 128 >= 8
+               for nm, nn, kk in shapes), shapes
+    xs = cg.random_bitstrings(n, 1, seed + 1)
+    terms = p.slice_terms(xs).cpu().numpy()
+    ids = np.random.default_rng(seed).choice(1 << k, 4, replace=False)
+    ref = VE.slice_terms(c, xs[0], p.order, p.slices, slice_ids=ids, threads=min(4, os.cpu_count() or 1))
+    assert np.max(np.abs(terms[0, ids] - ref)) < tol(n)

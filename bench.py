@@ -50,12 +50,14 @@ DEFAULT_WORKLOAD = "grid8x8d40"
 # events) the stepwise tensor-core engine at 10 sliced variables over planning-trial counts
 # 16 ... 4096 (trials ranked by the planner's kernel-rate estimate) and 4, 5 or 6 sliced
 # variables open inside a work item. The timed plan, its parity tests
-# (tests/test_gpu_8x8x40.py) and its ncu traffic are keyed by these.
+# (tests/test_gpu_8x8x40.py) and its ncu traffic are keyed by these. 9x9x40 (20 sliced):
+# 8, 512 and 2048 trials gave 278, 75 and 36 ms per 1024 slice terms (the 2048 trials take
+# about two minutes on 16 host cores).
 RECORDED_PLANS = {
     ("grid8x8d40", 5001): dict(n_slices=10, inner_slices=5, engine="stepwise", tensor_cores=True, plan_trials=4096),
     ("grid8x8d40", 5002): dict(n_slices=10, inner_slices=6, engine="stepwise", tensor_cores=True, plan_trials=256),
     ("grid8x8d40", 5003): dict(n_slices=10, inner_slices=6, engine="stepwise", tensor_cores=True, plan_trials=4096),
-    ("grid9x9d40", 9001): dict(n_slices=20, inner_slices=4, engine="stepwise", tensor_cores=True, plan_trials=8),
+    ("grid9x9d40", 9001): dict(n_slices=20, inner_slices=5, engine="stepwise", tensor_cores=True, plan_trials=2048),
 }
 # autotuner search of the workloads without a recorded plan
 TUNE = {"grid6x6d25-k12": dict(trial_counts=(1, 16, 256)),

@@ -24,7 +24,10 @@
 // of shared-memory stages (no separate packing pass: the operands cross HBM once, as
 // complex64); one thread issues each chunk's twelve tcgen05.mma (2 parts x 6 products, K =
 // 16 each) into one of two tensor-memory accumulators; epilogue warps store a finished
-// accumulator while the next tile's chunks are loaded and multiplied into the other.
+// accumulator while the next tile's chunks are loaded and multiplied into the other. A step
+// with 8 summed entries runs as one chunk whose second half is zeros. Steps with at most two
+// chunks and many row tiles per column tile take the B-stationary form (gemm_tc_bs_kernel,
+// below): a column tile's split B stays in shared memory for all the row tiles that use it.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 

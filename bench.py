@@ -4,7 +4,8 @@
 Default workload: the 8 x 8 random grid circuit of depth 40 (64 qubits, Section 4 rules,
 circuit seed 5001), one seeded bitstring (seed 5002) per step, 10 sliced variables (1024
 slice terms, 5 of the variables kept open inside a work item: 32 work items), the plan
-variant kept for this circuit (recorded below: 4096 planning trials; --autotune re-runs the
+variant kept for this circuit (recorded below: the ordering and sliced variables of 16384
+planning trials, stored in paper_1805_01450_gb300/orderings/; --autotune re-runs the
 autotuner instead). A
 step is one whole amplitude: every slice term, every pairwise contraction (the dense ones
 on the tcgen05 tensor cores as three-part bf16 GEMMs, the rest as FP32 SIMT kernels) and
@@ -54,7 +55,8 @@ DEFAULT_WORKLOAD = "grid8x8d40"
 # 8, 512 and 2048 trials gave 278, 75 and 36 ms per 1024 slice terms (the 2048 trials take
 # about two minutes on 16 host cores).
 RECORDED_PLANS = {
-    ("grid8x8d40", 5001): dict(n_slices=10, inner_slices=5, engine="stepwise", tensor_cores=True, plan_trials=4096),
+    ("grid8x8d40", 5001): dict(n_slices=10, inner_slices=5, engine="stepwise", tensor_cores=True, plan_trials=16384,
+                               ordering=True),
     ("grid8x8d40", 5002): dict(n_slices=10, inner_slices=6, engine="stepwise", tensor_cores=True, plan_trials=256),
     ("grid8x8d40", 5003): dict(n_slices=10, inner_slices=6, engine="stepwise", tensor_cores=True, plan_trials=4096),
     ("grid9x9d40", 9001): dict(n_slices=20, inner_slices=5, engine="stepwise", tensor_cores=True, plan_trials=2048),
@@ -74,7 +76,8 @@ L2_FLUSH_BYTES = 256 << 20
 # over its launches in one ncu launch list of the workload's timed plan (profiles/ holds
 # the summaries and commands). Keyed by (workload, circuit seed, kernel, device image bytes
 # of the plan): another plan, or a kernel changed since the capture, reports null.
-NCU_TRAFFIC = {("grid8x8d40", 5001, "regtile_step_kernel", 240640): 1993492911.2}
+NCU_TRAFFIC = {("grid8x8d40", 5001, "gemm_tc_kernel", 241664): 10217336678.4,
+               ("grid8x8d40", 5001, "regtile_step_kernel", 241664): 1338227213.5}
 # FP32 SIMT peak for the "alu" bound: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # the tensor-core contraction spends 48 bf16 flops per complex multiply-add (4 real MACs of
@@ -111,6 +114,8 @@ def parse(argv=None):
     ap.add_argument("--no-fp32-forms", action="store_true", help="skip timing the plain FP32 forms of the plan")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="CPU-baseline sample budget")
     ap.add_argument("--plan-json", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--record-ordering", action="store_true",
+                    help="run the planner for the workload's recorded variant and store its ordering")
     return ap.parse_args(argv)
 
 
@@ -137,6 +142,56 @@ def recorded_plan(args):
             or args.engine != "auto" or args.warps_per_item is not None or args.tensor_cores:
         return None
     return RECORDED_PLANS.get((args.workload, circuit_seed(args)))
+
+
+# Recorded orderings: the planning trials are the slow part of planning (16384 trials of the
+# 64-qubit circuit take minutes on the host cores), so a variant marked `ordering` stores the
+# winning trial's elimination order and sliced variables (written by `bench.py
+# --record-ordering`, which runs the planner); the plan's program is rebuilt from them in
+# about a second. Without the file the planner runs the trials itself.
+ORDERINGS = os.path.join(ROOT, "paper_1805_01450_gb300", "orderings")
+
+
+def ordering_path(workload_name, seed):
+    return os.path.join(ORDERINGS, f"{workload_name}-s{seed}.json")
+
+
+def recorded_plan_kwargs(workload_name, seed):
+    """Plan keyword arguments of a recorded variant, with its recorded ordering if there is
+    one: (kwargs, planning trials it stands for, where the ordering came from)."""
+    rec = dict(RECORDED_PLANS[(workload_name, seed)])
+    trials = rec["plan_trials"]
+    if rec.pop("ordering", False) and os.path.exists(ordering_path(workload_name, seed)):
+        with open(ordering_path(workload_name, seed)) as f:
+            d = json.load(f)
+        rec.pop("plan_trials")
+        rec.pop("n_slices")
+        rec["order"], rec["slices"] = d["order"], d["slices"]
+        return rec, trials, f"recorded ({trials} planning trials)"
+    return rec, trials, "planned in this run"
+
+
+def record_ordering(args):
+    """Runs the planner for the workload's recorded variant and stores its ordering."""
+    import paper_1805_01450_gb300 as q
+    seed = circuit_seed(args)
+    rec = dict(RECORDED_PLANS[(args.workload, seed)])
+    rec.pop("ordering", None)
+    if args.plan_trials is not None:
+        rec["plan_trials"] = args.plan_trials
+    circ = workload(args.workload, None, 0, args.circuit_seed)[0]
+    budget = (args.mem_budget_mb or MEM_BUDGET_MB.get(args.workload, 1024)) << 20
+    t0 = time.perf_counter()
+    plan = q.Plan(circ, mem_budget_bytes=budget, **rec)
+    out = {"workload": args.workload, "circuit_seed": seed, "variant": rec, "mem_budget_mb": budget >> 20,
+           "planner_seconds": time.perf_counter() - t0, "host_threads": min(os.cpu_count() or 1, 16),
+           "bytes_per_amplitude": plan.info["bytes_per_amplitude"], "device_image_bytes": plan.info["device_image_bytes"],
+           "order": [int(v) for v in plan.order], "slices": [int(v) for v in plan.slices]}
+    os.makedirs(ORDERINGS, exist_ok=True)
+    with open(ordering_path(args.workload, seed), "w") as f:
+        json.dump(out, f)
+        f.write("\n")
+    print(json.dumps({k: v for k, v in out.items() if k not in ("order", "slices")}))
 
 
 def measured_peaks():
@@ -266,7 +321,9 @@ def build_plan(args, circ, k, budget, dev, bits_host, need_timing=True):
     rec = recorded_plan(args)
     t0 = time.perf_counter()
     if rec is not None:
-        plan = q.Plan(circ, mem_budget_bytes=budget, **rec)
+        kw, trials, args.ordering_source = recorded_plan_kwargs(args.workload, circuit_seed(args))
+        plan = q.Plan(circ, mem_budget_bytes=budget, **kw)
+        plan.plan_trials = trials
         return plan, None, time.perf_counter() - t0
     trials = args.plan_trials if args.plan_trials is not None else (1 if grad else PLAN_TRIALS.get(args.workload, 1))
     if need_timing and args.inner_slices is None and args.warps_per_item is None and args.engine == "auto" and not grad:
@@ -292,7 +349,8 @@ def run_config(args, circ, plan, world, B):
             "depth": circ.depth, "sliced": len(plan.slices), "inner_slices": info["n_inner"],
             "bitstrings_per_step": B, "engine": info["engine"], "warps_per_item": info["warps_per_item"],
             "mem_budget_mb": args.mem_budget_mb, "tensor_core_steps": info["n_gemm_steps"],
-            "plan_trials": plan.plan_trials, "l2": "flushed (256 MiB write) before each step",
+            "plan_trials": plan.plan_trials, "ordering": getattr(args, "ordering_source", "planned in this run"),
+            "l2": "flushed (256 MiB write) before each step",
             "parallelism": (f"slices split over {world} ranks" if args.shard == "slices" and world > 1
                             else f"bitstrings per rank x {world}"),
             **({"slice_sample": slice_sample(args, plan), "extrapolated": True} if slice_sample(args, plan) else {})}
@@ -434,6 +492,8 @@ def main():
     args = parse()
     if args.plan_json:
         return plan_json(args)
+    if args.record_ordering:
+        return record_ordering(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -2,7 +2,8 @@
 variables, 10 sliced of which 5 or 6 stay open inside a work item, tensors up to rank 28),
 for the three seeded circuits the benchmark reports, each with exactly the plan the
 benchmark times (bench.RECORDED_PLANS: the stepwise engine with the dense contractions on
-the tensor cores, and the planning-trial count kept by timing).
+the tensor cores, and the planning-trial count kept by timing; a recorded ordering where
+the variant has one, bench.recorded_plan_kwargs).
 
 Pass condition (the random-phase reading of the amplitude tolerance on sampled slices):
 16 seeded slice terms of a seeded work item are compared element by element with the
@@ -38,7 +39,8 @@ def case(request):
     seed = request.param
     c = cg.grid_circuit(8, 8, 40, seed)
     x = cg.random_bitstrings(N, 1, 5002)[0]
-    p = q.Plan(c, mem_budget_bytes=BUDGET, **bench.RECORDED_PLANS[("grid8x8d40", seed)])
+    kw, _, _ = bench.recorded_plan_kwargs("grid8x8d40", seed)
+    p = q.Plan(c, mem_budget_bytes=BUDGET, **kw)
     return seed, c, x, p
 
 

@@ -57,8 +57,10 @@ DEFAULT_WORKLOAD = "grid8x8d40"
 RECORDED_PLANS = {
     ("grid8x8d40", 5001): dict(n_slices=10, inner_slices=5, engine="stepwise", tensor_cores=True, plan_trials=16384,
                                ordering=True),
-    ("grid8x8d40", 5002): dict(n_slices=10, inner_slices=6, engine="stepwise", tensor_cores=True, plan_trials=256),
-    ("grid8x8d40", 5003): dict(n_slices=10, inner_slices=6, engine="stepwise", tensor_cores=True, plan_trials=4096),
+    ("grid8x8d40", 5002): dict(n_slices=10, inner_slices=6, engine="stepwise", tensor_cores=True, plan_trials=16384,
+                               ordering=True),
+    ("grid8x8d40", 5003): dict(n_slices=10, inner_slices=6, engine="stepwise", tensor_cores=True, plan_trials=16384,
+                               ordering=True),
     ("grid9x9d40", 9001): dict(n_slices=20, inner_slices=5, engine="stepwise", tensor_cores=True, plan_trials=2048),
 }
 # autotuner search of the workloads without a recorded plan

@@ -868,9 +868,10 @@ static cudaError_t launch_gemm_nt(GemmArgs ga, cudaStream_t s) {
     uint64_t grid = 0;
     cudaError_t e;
     // B-stationary form: at most two chunks of summed entries (B's regions of every chunk
-    // stay resident) and at least 8 row tiles per column tile to reuse them over (and tile
-    // coordinates above the row tiles within 32 bits)
-    if (ga.n_chunks <= 2u && ga.n_mt >= 8u && (uint64_t)ga.n_items * ga.n_nt < (1ull << 32)) {
+    // stay resident) and at least 4 row tiles per column tile to reuse them over (with 2, the
+    // reload between column tiles, which waits for the old tile's MMAs, cost more than the
+    // reuse saved; tile coordinates above the row tiles within 32 bits)
+    if (ga.n_chunks <= 2u && ga.n_mt >= 4u && (uint64_t)ga.n_items * ga.n_nt < (1ull << 32)) {
         if ((e = gemm_grid<NT, true>(ga.n_tiles, &grid)) != cudaSuccess) return e;
         gemm_tc_bs_kernel<NT><<<(unsigned)grid, bs_threads<NT>(), bs_smem_bytes<NT>(), s>>>(ga);
         return cudaGetLastError();

@@ -82,7 +82,7 @@ def test_wide_register_tiles_vs_oracle():
 
 
 # 6x7x40 plans whose tensor-core steps take the B-stationary form (at most 32 summed entries,
-# at least 8 row tiles of 128 per column tile), one case per column-tile width and summed
+# at least 4 row tiles of 128 per column tile), one case per column-tile width and summed
 # size: (rows, cols, depth, seed, sliced, inner, real columns NT, summed-index bits)
 BS_CASES = [
     (6, 7, 40, 1, 8, 2, 32, 3),
@@ -103,8 +103,8 @@ def test_b_stationary_form_vs_oracle(r, c_, d, seed, k, inner, nt, nk):
     p = q.Plan(c, n_slices=k, inner_slices=inner, engine="stepwise", tensor_cores=True)
     shapes = [(int(g["nm"]), int(g["nn"]), int(g["nk"])) for g in Program(p.image()).gemms if int(g["nk"]) > 0]
     # the launcher's choice: B-stationary when the summed index fills at most two chunks of 16
-    # and there are at least 8 row tiles; the case's step is among them
-    assert any((256 if nn >= 7 else 2 << nn) == nt and kk == nk and max(1, (1 << kk) // 16) <= 2 and (1 << nm) // 128 >= 8
+    # and there are at least 4 row tiles; the case's step is among them
+    assert any((256 if nn >= 7 else 2 << nn) == nt and kk == nk and max(1, (1 << kk) // 16) <= 2 and (1 << nm) // 128 >= 4
                for nm, nn, kk in shapes), shapes
     xs = cg.random_bitstrings(n, 1, seed + 1)
     terms = p.slice_terms(xs).cpu().numpy()

@@ -32,6 +32,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "device_program.h"
 #include "device_util.cuh"
@@ -835,14 +836,17 @@ uint32_t gemm_nt(const GemmStep &g) { return g.nn >= 7 ? 256u : (2u << g.nn); }
 
 // Grid of a persistent tensor-core kernel: the SM count times the CTAs an SM holds (within
 // its 512 tensor-memory columns, so that no allocation ever waits for another CTA's
-// columns), queried once per device and kernel.
+// columns), queried once per device and kernel (under a lock: host threads may launch on
+// several streams at once).
 template <int NT, bool kBs>
 static cudaError_t gemm_grid(uint64_t n_tiles, uint64_t *grid) {
     static int per_sm[64] = {0}, sms[64] = {0};
+    static std::mutex mu;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
     if (!per_sm[dev]) {
         const void *fn = kBs ? reinterpret_cast<const void *>(gemm_tc_bs_kernel<NT>)
                              : reinterpret_cast<const void *>(gemm_tc_kernel<NT>);

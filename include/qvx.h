@@ -123,7 +123,7 @@ typedef struct {
                                   GEMMs on the tcgen05 tensor cores, each FP32 operand split into
                                   three bf16 parts (six products, FP32 accumulation: about 2^-23
                                   relative error per product); 0 keeps them on FP32 SIMT kernels */
-    int32_t plan_trials;       /* 1 ... 16384 independent planning trials (ordering, slice choice and
+    int32_t plan_trials;       /* 1 ... 65536 independent planning trials (ordering, slice choice and
                                   re-ordering, each from its own seed; trial 0 from order_seed);
                                   the plan with the smallest bandwidth-weighted contraction
                                   estimate is kept. Ignored when both order and slices are given */

@@ -371,7 +371,7 @@ qvx_status qvx_plan_create(const qvx_circuit *circuit, const int32_t *order, int
     if (o.order_restarts < 1 || o.max_rank < 1 || o.mem_budget_bytes < 64)
         return fail(QVX_EINVAL, "opts: restarts >= 1, max_rank >= 1, budget >= 64 bytes");
     if (o.slice_rule < 0 || o.slice_rule > 2) return fail(QVX_EINVAL, "opts: slice_rule must be 0, 1 or 2");
-    if (o.plan_trials < 1 || o.plan_trials > 16384) return fail(QVX_EINVAL, "opts: plan_trials must be in [1, 16384]");
+    if (o.plan_trials < 1 || o.plan_trials > 65536) return fail(QVX_EINVAL, "opts: plan_trials must be in [1, 65536]");
     if (o.tensor_cores < 0 || o.tensor_cores > 1) return fail(QVX_EINVAL, "opts: tensor_cores must be 0 or 1");
     if (o.host_merge_rank < 0 || o.host_merge_rank > 16)
         return fail(QVX_EINVAL, "opts: host_merge_rank must be in [0, 16]");

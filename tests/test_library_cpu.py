@@ -449,7 +449,7 @@ def test_planning_trials_keep_the_cheapest_valid_plan():
     # a given order and slice set leave nothing to try
     f = q.Plan(c, order=one.order, slices=one.slices, inner_slices=0, plan_trials=8)
     assert (f.order, f.slices) == (one.order, one.slices)
-    for bad in (0, 16385):
+    for bad in (0, 65537):
         with pytest.raises(q.QvxError) as e:
             q.Plan(c, n_slices=4, plan_trials=bad)
         assert e.value.status == q.QVX_EINVAL

@@ -552,7 +552,15 @@ __global__ void __launch_bounds__(block_threads<NT>(), 1) gemm_tc_kernel(GemmArg
 // the old one have completed. Against the streaming form this removes most of the
 // producers' shared-memory traffic on output-heavy steps (B is 4 of the 6 operand values a
 // complex entry pair produces).
-constexpr uint32_t kBsStages = 2;
+// A stages (26 KB each) and accumulators: the narrower the column tile, the shorter a tile's
+// work against its fixed barrier round trips, so narrow tiles keep more tiles in flight
+// (tensor memory holds 512 columns: 2 x 256, 4 x 128, 8 x 64, 8 x 32).
+template <int NT>
+__host__ __device__ constexpr uint32_t bs_stages() { return NT >= 256 ? 2u : (NT >= 128 ? 3u : 4u); }
+template <int NT>
+__host__ __device__ constexpr uint32_t bs_cols() { return NT < 32 ? 32u : (uint32_t)NT; }   // one accumulator
+template <int NT>
+__host__ __device__ constexpr uint32_t bs_accs() { return 512u / bs_cols<NT>() < 8u ? 512u / bs_cols<NT>() : 8u; }
 __host__ __device__ constexpr uint32_t bs_stage_bytes() { return 6u * region_bytes(kRows); }
 template <int NT>
 __host__ __device__ constexpr uint32_t bs_b_bytes() { return 6u * region_bytes(NT); }   // one chunk of B
@@ -564,13 +572,14 @@ template <int NT>
 __host__ __device__ constexpr uint32_t bs_threads() { return 256u + bs_b_units<NT>() + 32u + kEpiThreads; }
 template <int NT>
 __host__ __device__ constexpr size_t bs_smem_bytes() {
-    return (size_t)kBsStages * bs_stage_bytes() + 2u * (size_t)bs_b_bytes<NT>() +
+    return (size_t)bs_stages<NT>() * bs_stage_bytes() + 2u * (size_t)bs_b_bytes<NT>() +
            (size_t)bs_raw_depth<NT>() * 256u * 64u + (size_t)bs_b_units<NT>() * 64u + 8u * 32u;
 }
 
 template <int NT>
 __global__ void __launch_bounds__(bs_threads<NT>(), 1) gemm_tc_bs_kernel(GemmArgs ga) {
-    constexpr uint32_t S = kBsStages;
+    constexpr uint32_t S = bs_stages<NT>();
+    constexpr uint32_t NA = bs_accs<NT>();
     constexpr uint32_t PA = 256u, PB = bs_b_units<NT>();
     constexpr uint32_t kMmaWarp = (PA + PB) / 32u;
     constexpr uint32_t kCols = NT < 32 ? 32u : (uint32_t)NT;
@@ -581,7 +590,7 @@ __global__ void __launch_bounds__(bs_threads<NT>(), 1) gemm_tc_bs_kernel(GemmArg
     constexpr uint32_t kRaw = bs_raw_depth<NT>();
     constexpr uint32_t kRawSlotA = PA * 64u;
     extern __shared__ __align__(1024) unsigned char gsm[];
-    __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S], accf_bar[2], acce_bar[2], bfull_bar, bempty_bar, drain_bar;
+    __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S], accf_bar[NA], acce_bar[NA], bfull_bar, bempty_bar, drain_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int fail;
     const GemmStep &g = ga.g;
@@ -600,7 +609,7 @@ __global__ void __launch_bounds__(bs_threads<NT>(), 1) gemm_tc_bs_kernel(GemmArg
             mbar_init(smem_u32(&full_bar[s]), PA);
             mbar_init(smem_u32(&empty_bar[s]), 1);
         }
-        for (uint32_t b = 0; b < 2; b++) {
+        for (uint32_t b = 0; b < NA; b++) {
             mbar_init(smem_u32(&accf_bar[b]), 1);
             mbar_init(smem_u32(&acce_bar[b]), kEpiThreads);
         }
@@ -612,7 +621,7 @@ __global__ void __launch_bounds__(bs_threads<NT>(), 1) gemm_tc_bs_kernel(GemmArg
     }
     if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(2u * kCols)
+                     "r"(NA * kCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -746,8 +755,8 @@ __global__ void __launch_bounds__(bs_threads<NT>(), 1) gemm_tc_bs_kernel(GemmArg
                     }
                     gi++;
                 }
-                const uint32_t buf = j & 1u;
-                if (!wait_or_fail(smem_u32(&acce_bar[buf]), ((j >> 1) & 1u) ^ 1u, &fail)) {
+                const uint32_t buf = j % NA;
+                if (!wait_or_fail(smem_u32(&acce_bar[buf]), ((j / NA) & 1u) ^ 1u, &fail)) {
                     ok = false;
                     break;
                 }
@@ -797,10 +806,10 @@ __global__ void __launch_bounds__(bs_threads<NT>(), 1) gemm_tc_bs_kernel(GemmArg
         cur.c = tile_coord_bs(t0, ga);
         for (uint64_t t = t0; t < t1 && !fail; t++, j++, cur.next(ga)) {
             const TileCoord &tc = cur.c;
-            const uint32_t buf = j & 1u;
+            const uint32_t buf = j % NA;
             float2 *Crow = ga.arenas + (uint64_t)tc.il * ga.a.arena_elems + g.c_off + pext_runs(tc.beta, g.cb, g.n_cb) +
                            pext_runs(tc.mt * kRows + 32u * q + lane, g.cm, g.n_cm);
-            if (!wait_or_fail(smem_u32(&accf_bar[buf]), (j >> 1) & 1u, &fail)) {
+            if (!wait_or_fail(smem_u32(&accf_bar[buf]), (j / NA) & 1u, &fail)) {
                 fail = 1;
                 break;
             }
@@ -824,7 +833,7 @@ __global__ void __launch_bounds__(bs_threads<NT>(), 1) gemm_tc_bs_kernel(GemmArg
     __syncthreads();
     if (warp == kMmaWarp) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2u * kCols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NA * kCols) : "memory");
     }
     if (fail && threadIdx.x == 0) atomicCAS(ga.a.status, 0u, 4u /* QVX_ETIMEOUT */);
 }
@@ -857,7 +866,7 @@ static cudaError_t gemm_grid(uint64_t n_tiles, uint64_t *grid) {
         int n = 0;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        const int cols = 2 * (NT < 32 ? 32 : NT);
+        const int cols = kBs ? (int)(bs_accs<NT>() * bs_cols<NT>()) : 2 * (NT < 32 ? 32 : NT);
         per_sm[dev] = n < 1 ? -1 : std::min(n, 512 / cols);
     }
     if (per_sm[dev] < 1) return cudaErrorInvalidConfiguration;

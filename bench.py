@@ -78,8 +78,8 @@ L2_FLUSH_BYTES = 256 << 20
 # over its launches in one ncu launch list of the workload's timed plan (profiles/ holds
 # the summaries and commands). Keyed by (workload, circuit seed, kernel, device image bytes
 # of the plan): another plan, or a kernel changed since the capture, reports null.
-NCU_TRAFFIC = {("grid8x8d40", 5001, "gemm_tc_kernel", 241664): 10227905369.6,
-               ("grid8x8d40", 5001, "regtile_step_kernel", 241664): 1338212435.5}
+NCU_TRAFFIC = {("grid8x8d40", 5001, "gemm_tc_kernel", 241664): 10230352774.4,
+               ("grid8x8d40", 5001, "regtile_step_kernel", 241664): 1338227991.4}
 # FP32 SIMT peak for the "alu" bound: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # the tensor-core contraction spends 48 bf16 flops per complex multiply-add (4 real MACs of

@@ -118,6 +118,9 @@ def parse(argv=None):
     ap.add_argument("--plan-json", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--record-ordering", action="store_true",
                     help="run the planner for the workload's recorded variant and store its ordering")
+    ap.add_argument("--record-trial", type=int, default=None,
+                    help="with --record-ordering: store this planning trial instead of the estimate's first")
+    ap.add_argument("--selected-by", default="chosen by timing", help=argparse.SUPPRESS)
     return ap.parse_args(argv)
 
 
@@ -169,12 +172,20 @@ def recorded_plan_kwargs(workload_name, seed):
         rec.pop("plan_trials")
         rec.pop("n_slices")
         rec["order"], rec["slices"] = d["order"], d["slices"]
+        if "trial" in d:
+            return rec, trials, f"recorded (trial {d['trial']} of {trials} planning trials, {d['selected_by']})"
         return rec, trials, f"recorded ({trials} planning trials)"
     return rec, trials, "planned in this run"
 
 
+# planning trial t runs from order seed 1 + t * TRIAL_SEED_STEP (mod 2^64), as in the planner
+TRIAL_SEED_STEP = 0xD1B54A32D192ED03
+
+
 def record_ordering(args):
-    """Runs the planner for the workload's recorded variant and stores its ordering."""
+    """Runs the planner for the workload's recorded variant and stores its ordering. With
+    --record-trial T it stores trial T of the search instead of the one the planner's
+    estimate ranks first (the trial a timing of the estimate's best-ranked trials kept)."""
     import paper_1805_01450_gb300 as q
     seed = circuit_seed(args)
     rec = dict(RECORDED_PLANS[(args.workload, seed)])
@@ -184,8 +195,14 @@ def record_ordering(args):
     circ = workload(args.workload, None, 0, args.circuit_seed)[0]
     budget = (args.mem_budget_mb or MEM_BUDGET_MB.get(args.workload, 1024)) << 20
     t0 = time.perf_counter()
-    plan = q.Plan(circ, mem_budget_bytes=budget, **rec)
-    out = {"workload": args.workload, "circuit_seed": seed, "variant": rec, "mem_budget_mb": budget >> 20,
+    extra = {}
+    if args.record_trial is not None:
+        one = dict(rec, plan_trials=1, order_seed=(1 + args.record_trial * TRIAL_SEED_STEP) % (1 << 64))
+        plan = q.Plan(circ, mem_budget_bytes=budget, **one)
+        extra = {"trial": args.record_trial, "selected_by": args.selected_by}
+    else:
+        plan = q.Plan(circ, mem_budget_bytes=budget, **rec)
+    out = {"workload": args.workload, "circuit_seed": seed, "variant": rec, **extra, "mem_budget_mb": budget >> 20,
            "planner_seconds": time.perf_counter() - t0, "host_threads": min(os.cpu_count() or 1, 16),
            "bytes_per_amplitude": plan.info["bytes_per_amplitude"], "device_image_bytes": plan.info["device_image_bytes"],
            "order": [int(v) for v in plan.order], "slices": [int(v) for v in plan.slices]}

@@ -18,7 +18,8 @@ def test_recorded_ordering_rebuilds_the_planned_program(tmp_path, monkeypatch):
     variant = dict(n_slices=6, inner_slices=2, engine="stepwise", tensor_cores=True, plan_trials=6, ordering=True)
     monkeypatch.setattr(bench, "ORDERINGS", str(tmp_path))
     monkeypatch.setitem(bench.RECORDED_PLANS, key, variant)
-    args = argparse.Namespace(workload=key[0], circuit_seed=None, plan_trials=None, mem_budget_mb=256)
+    args = argparse.Namespace(workload=key[0], circuit_seed=None, plan_trials=None, mem_budget_mb=256,
+                              record_trial=None, selected_by="")
     bench.record_ordering(args)
     path = bench.ordering_path(*key)
     with open(path) as f:
@@ -32,6 +33,14 @@ def test_recorded_ordering_rebuilds_the_planned_program(tmp_path, monkeypatch):
     rebuilt = q.Plan(circ, mem_budget_bytes=256 << 20, **kw)
     assert rebuilt.order == planned.order and rebuilt.slices == planned.slices
     assert rebuilt.image() == planned.image()
+    # a chosen trial instead of the estimate's first: trial 3's own seed, one trial
+    args.record_trial, args.selected_by = 3, "chosen by timing"
+    bench.record_ordering(args)
+    kw, trials, source = bench.recorded_plan_kwargs(*key)
+    assert trials == 6 and "trial 3 of 6" in source
+    third = q.Plan(circ, mem_budget_bytes=256 << 20, n_slices=6, inner_slices=2, engine="stepwise",
+                   tensor_cores=True, plan_trials=1, order_seed=(1 + 3 * bench.TRIAL_SEED_STEP) % (1 << 64))
+    assert q.Plan(circ, mem_budget_bytes=256 << 20, **kw).image() == third.image()
     # without the file the variant plans in the run
     os.remove(path)
     kw, _, source = bench.recorded_plan_kwargs(*key)
